@@ -1,0 +1,110 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module only draws random numbers and fixes workload sizes; it holds none
+of the method's arithmetic (no basis, quadrature, operator, factorisation or
+solver).  Both sides receive the same parameters and evaluate them on their own.
+
+Velocity fields are described by parameters, not values: component ``c`` is
+
+    a_c(x) = a0[c] + sum_m amp[c, m] * cos(2*pi * kvec[c, m, :] . x + phase[c, m])
+
+with integer wavevectors, so every field is periodic on the unit cube.  The
+random-Fourier recipe draws ``amp ~ U(-1, 1)``, each wavevector component
+uniformly from ``{1..kmax}`` and ``phase ~ U(0, 2*pi)``.  A separable field
+(each component depends only on its own coordinate, the case in which the
+paper's Eq. (adv-kron-cart) makes the diagonal block an exact two-term
+Kronecker sum) sets every wavevector component except the c-th to zero.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Velocity:
+    dim: int
+    a0: np.ndarray                       # [dim]
+    amp: np.ndarray                      # [dim, M]
+    kvec: np.ndarray                     # [dim, M, dim] int32
+    phase: np.ndarray                    # [dim, M]
+
+    @property
+    def n_modes(self) -> int:
+        return int(self.amp.shape[1])
+
+
+def constant_velocity(a) -> Velocity:
+    a = np.asarray(a, dtype=np.float64)
+    d = a.shape[0]
+    return Velocity(d, a.copy(), np.zeros((d, 0)), np.zeros((d, 0, d), np.int32),
+                    np.zeros((d, 0)))
+
+
+def fourier_velocity(seed: int, dim: int, n_modes: int = 8, kmax: int = 4,
+                     a0=None, separable: bool = False) -> Velocity:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amp = rng.uniform(-1.0, 1.0, size=(dim, n_modes))
+    kvec = rng.integers(1, kmax + 1, size=(dim, n_modes, dim)).astype(np.int32)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=(dim, n_modes))
+    if separable:
+        for c in range(dim):
+            for d in range(dim):
+                if d != c:
+                    kvec[c, :, d] = 0
+    a0 = np.zeros(dim) if a0 is None else np.asarray(a0, dtype=np.float64)
+    return Velocity(dim, a0, amp, kvec, phase)
+
+
+def rhs(seed: int, ndof: int) -> np.ndarray:
+    """Right-hand side b ~ N(0, 1), float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(ndof)
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: int                     # Gauss-Legendre nodes per direction (p + 1)
+    nel: tuple                 # elements per direction (periodic)
+    dt: float
+    velocity: Velocity
+    rhs_seed: int
+    h: float = field(default=0.0)
+
+    def __post_init__(self):
+        if self.h == 0.0:
+            self.h = 1.0 / self.nel[0]
+
+    @property
+    def num_elem(self) -> int:
+        return int(np.prod(self.nel))
+
+    @property
+    def ndof(self) -> int:
+        return self.num_elem * self.n ** self.dim
+
+    def b(self) -> np.ndarray:
+        return rhs(self.rhs_seed, self.ndof)
+
+
+def advection_2d_const(n: int = 8, nel: int = 8, dt: float = 0.1) -> Workload:
+    """8x8 periodic quads, p = 7, constant velocity (1, 0.5), dt = 0.1."""
+    return Workload(f"adv2d-const-{nel}x{nel}-n{n}", 2, n, (nel, nel), dt,
+                    constant_velocity([1.0, 0.5]), rhs_seed=1704)
+
+
+def advection_2d_fourier(n: int = 16, nel: int = 64, dt: float = 0.05,
+                         vel_seed: int = 1705, rhs_seed: int = 1706) -> Workload:
+    """64x64 periodic quads, n = 16 or 31, random-Fourier velocity, dt = 0.05."""
+    return Workload(f"adv2d-fourier-{nel}x{nel}-n{n}", 2, n, (nel, nel), dt,
+                    fourier_velocity(vel_seed, 2), rhs_seed=rhs_seed)
+
+
+def advection_3d_fourier(n: int = 11, nel: int = 16, dt: float = 0.05,
+                         vel_seed: int = 1707, rhs_seed: int = 1708) -> Workload:
+    """16^3 periodic hexes, n = 11, random-Fourier velocity, dt = 0.05."""
+    return Workload(f"adv3d-fourier-{nel}^3-n{n}", 3, n, (nel, nel, nel), dt,
+                    fourier_velocity(vel_seed, 3), rhs_seed=rhs_seed)
