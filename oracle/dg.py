@@ -19,6 +19,10 @@ block gets dt h^(d-1) E_f^T diag(w_f max(a.n, 0)) E_f and the neighbour block
 dt h^(d-1) E_f^T diag(w_f min(a.n, 0)) E'_f, with E_f (E'_f) the own
 (neighbour) basis evaluated at the face quadrature points.
 
+The velocity is a field on the periodic domain [0, L_1] x ... with
+L_d = N_d h: it is evaluated at the normalised point x / L (a function of
+the unit cube), so it is periodic on the mesh whatever h is.
+
 DOF ordering: element-major, inside an element i + n j (+ n^2 k), x fastest,
 so the slowest direction is the LEFT Kronecker factor.  Face order: -x, +x,
 -y, +y, -z, +z.  The physical coordinate of a face is taken from the element
@@ -154,9 +158,16 @@ class AdvectionDG:
         w = self.basis.w
         return _kron_all([w] * (self.dim - 1)) if self.dim > 1 else np.ones(1)
 
+    def domain_length(self) -> np.ndarray:
+        return np.array([N * self.mesh.h for N in self.mesh.nel])
+
+    def velocity_at(self, X: np.ndarray) -> np.ndarray:
+        """a at physical points X (field defined on the normalised domain)."""
+        return velocity_eval(self.vel, X / self.domain_length())
+
     def face_normal_velocity(self, e: int, face: int) -> np.ndarray:
         d, side = divmod(face, 2)
-        a = velocity_eval(self.vel, self.face_points(e, face))
+        a = self.velocity_at(self.face_points(e, face))
         return a[:, d] * (1.0 if side == 1 else -1.0)
 
     def mass_block(self, e: int) -> np.ndarray:
@@ -170,7 +181,7 @@ class AdvectionDG:
         """J_v: derivative of int F(u) . grad v dx (Table tab:dg-ops, Eq. adv-kron)."""
         b = self.basis
         GtW, DtW = b.G.T @ b.W, b.D.T @ b.W
-        a = velocity_eval(self.vel, self.volume_points(e))
+        a = self.velocity_at(self.volume_points(e))
         G = _kron_all([b.G] * self.dim)
         Jv = np.zeros((self.nloc, self.nloc))
         for comp in range(self.dim):
@@ -242,7 +253,7 @@ class AdvectionDG:
             u = X[e]
             for ax in range(d):
                 u = contract(u, b.G, ax)                # values at quadrature points
-            a = velocity_eval(self.vel, self.volume_points(e)).reshape([mu] * d + [d])
+            a = self.velocity_at(self.volume_points(e)).reshape([mu] * d + [d])
             ye = np.zeros([n] * d)
             # mass
             t = u * wq * h ** d

@@ -8,16 +8,25 @@ Velocity fields are described by parameters, not values: component ``c`` is
 
     a_c(x) = a0[c] + sum_m amp[c, m] * cos(2*pi * kvec[c, m, :] . x + phase[c, m])
 
-with integer wavevectors, so every field is periodic on the unit cube.  The
-random-Fourier recipe draws ``amp ~ U(-1, 1)``, each wavevector component
-uniformly from ``{1..kmax}`` and ``phase ~ U(0, 2*pi)``.  A separable field
-(each component depends only on its own coordinate, the case in which the
-paper's Eq. (adv-kron-cart) makes the diagonal block an exact two-term
-Kronecker sum) sets every wavevector component except the c-th to zero.
+with integer wavevectors, so every field is periodic on the unit cube.
+
+Random-Fourier recipe (default, divergence-free like the paper's advection
+fields of Sec. 5.1): mode m draws a scalar amplitude A_m ~ U(-1, 1), a
+wavevector k_m with components uniform in {1..kmax} and a phase
+phi_m ~ U(0, 2 pi), and contributes A_m e_m cos(2 pi k_m . x + phi_m) with
+e_m a unit vector perpendicular to k_m (2D: (k_y, -k_x)/|k|; 3D: a random
+unit vector orthogonalised against k_m), so div a = 0 exactly.  Every
+component of one mode shares its wavevector and phase.
+
+``solenoidal=False`` draws an independent amplitude, wavevector and phase per
+component instead (not divergence-free).  A separable field (each component
+depends only on its own coordinate, the case in which Eq. adv-kron-cart makes
+the diagonal block an exact two-term Kronecker sum) keeps only the c-th
+wavevector component of component c.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -43,17 +52,33 @@ def constant_velocity(a) -> Velocity:
 
 
 def fourier_velocity(seed: int, dim: int, n_modes: int = 8, kmax: int = 4,
-                     a0=None, separable: bool = False) -> Velocity:
+                     a0=None, separable: bool = False, solenoidal: bool = True) -> Velocity:
     rng = np.random.Generator(np.random.PCG64(seed))
-    amp = rng.uniform(-1.0, 1.0, size=(dim, n_modes))
-    kvec = rng.integers(1, kmax + 1, size=(dim, n_modes, dim)).astype(np.int32)
-    phase = rng.uniform(0.0, 2.0 * np.pi, size=(dim, n_modes))
-    if separable:
-        for c in range(dim):
-            for d in range(dim):
-                if d != c:
-                    kvec[c, :, d] = 0
     a0 = np.zeros(dim) if a0 is None else np.asarray(a0, dtype=np.float64)
+    if separable or not solenoidal:
+        amp = rng.uniform(-1.0, 1.0, size=(dim, n_modes))
+        kvec = rng.integers(1, kmax + 1, size=(dim, n_modes, dim)).astype(np.int32)
+        phase = rng.uniform(0.0, 2.0 * np.pi, size=(dim, n_modes))
+        if separable:
+            for c in range(dim):
+                for d in range(dim):
+                    if d != c:
+                        kvec[c, :, d] = 0
+        return Velocity(dim, a0, amp, kvec, phase)
+    A = rng.uniform(-1.0, 1.0, size=n_modes)
+    k = rng.integers(1, kmax + 1, size=(n_modes, dim)).astype(np.int32)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    amp = np.zeros((dim, n_modes))
+    for m in range(n_modes):
+        km = k[m].astype(np.float64)
+        if dim == 2:
+            e = np.array([km[1], -km[0]])
+        else:
+            e = rng.standard_normal(3)
+            e -= (e @ km) / (km @ km) * km
+        amp[:, m] = A[m] * e / np.linalg.norm(e)
+    kvec = np.broadcast_to(k[None], (dim, n_modes, dim)).astype(np.int32).copy()
+    phase = np.broadcast_to(phi[None], (dim, n_modes)).copy()
     return Velocity(dim, a0, amp, kvec, phase)
 
 
@@ -72,11 +97,7 @@ class Workload:
     dt: float
     velocity: Velocity
     rhs_seed: int
-    h: float = field(default=0.0)
-
-    def __post_init__(self):
-        if self.h == 0.0:
-            self.h = 1.0 / self.nel[0]
+    h: float = 1.0          # unit-square (unit-cube) elements; domain [0, N h]^d
 
     @property
     def num_elem(self) -> int:
@@ -91,20 +112,20 @@ class Workload:
 
 
 def advection_2d_const(n: int = 8, nel: int = 8, dt: float = 0.1) -> Workload:
-    """8x8 periodic quads, p = 7, constant velocity (1, 0.5), dt = 0.1."""
+    """8x8 periodic unit-square quads, p = 7, constant velocity (1, 0.5), dt = 0.1."""
     return Workload(f"adv2d-const-{nel}x{nel}-n{n}", 2, n, (nel, nel), dt,
                     constant_velocity([1.0, 0.5]), rhs_seed=1704)
 
 
 def advection_2d_fourier(n: int = 16, nel: int = 64, dt: float = 0.05,
                          vel_seed: int = 1705, rhs_seed: int = 1706) -> Workload:
-    """64x64 periodic quads, n = 16 or 31, random-Fourier velocity, dt = 0.05."""
+    """64x64 periodic unit-square quads, n = 16 or 31, random-Fourier velocity, dt = 0.05."""
     return Workload(f"adv2d-fourier-{nel}x{nel}-n{n}", 2, n, (nel, nel), dt,
                     fourier_velocity(vel_seed, 2), rhs_seed=rhs_seed)
 
 
 def advection_3d_fourier(n: int = 11, nel: int = 16, dt: float = 0.05,
                          vel_seed: int = 1707, rhs_seed: int = 1708) -> Workload:
-    """16^3 periodic hexes, n = 11, random-Fourier velocity, dt = 0.05."""
+    """16^3 periodic unit-cube hexes, n = 11, random-Fourier velocity, dt = 0.05."""
     return Workload(f"adv3d-fourier-{nel}^3-n{n}", 3, n, (nel, nel, nel), dt,
                     fourier_velocity(vel_seed, 3), rhs_seed=rhs_seed)
