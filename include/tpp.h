@@ -1,0 +1,234 @@
+/*
+ * tpp.h - C ABI of libtpp: approximate tensor-product (Kronecker SVD)
+ * preconditioned, matrix-free GMRES for very-high-order DG advection on GB300.
+ *
+ * Method: W. Pazner and P.-O. Persson, "Approximate tensor-product
+ * preconditioners for very high order discontinuous Galerkin methods".
+ *
+ * Problem (Sec. 3.4, Sec. 5.1 Eq. adv): linear advection u_t + div(a u) = 0 on a
+ * periodic Cartesian mesh of nel[0] x nel[1] (x nel[2]) elements of width h,
+ * n = p + 1 Gauss-Legendre nodes per direction, quadrature collocated with the
+ * nodes, upwind numerical flux.  One implicit step gives the system
+ *     S x = (M - dt J) x = (M + dt A) x = b,        A = -J.
+ *
+ * Data layout of every solution-sized vector (device, float64): element-major,
+ * element e = ex + nel[0] * (ey + nel[1] * ez), and inside an element the DOF
+ * index i + n j (+ n^2 k) with x fastest.  Kronecker factors act as
+ * A (x) B (2D: A on y, B on x) and A (x) B (x) C (3D: z, y, x).
+ *
+ * Conventions shared by all entry points:
+ *  - Every pointer argument documented as "device" must point to memory on the
+ *    current CUDA device; "host" pointers are read before the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on it and return without synchronising, except where a
+ *    host-side report is filled (tpp_create, tpp_build_factors, gmres_solve).
+ *  - The library never allocates device memory: all device state lives in the
+ *    caller's workspace (size from tpp_workspace_bytes), owned by the caller and
+ *    valid for the lifetime of the context.
+ *  - Errors: a non-zero tpp_status is returned and a message is available from
+ *    tpp_last_error() (thread-local).  Device kernels never trap; failures they
+ *    detect are written to status words and reported by the next reporting call.
+ *  - There is no CPU fallback: without a usable GB300 device every call fails
+ *    with TPP_ERR_CUDA.
+ */
+#ifndef TPP_H
+#define TPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPP_OK = 0,
+  TPP_ERR_INVALID_ARG = 1,     /* bad size, null pointer, aliasing, option out of range */
+  TPP_ERR_CUDA = 2,            /* a CUDA runtime call failed (message has the CUDA error) */
+  TPP_ERR_SINGULAR_FACTOR = 3, /* an inverted Kronecker factor is numerically singular */
+  TPP_ERR_NOT_CONVERGED = 4,   /* GMRES hit max_iters before rtol */
+  TPP_ERR_BREAKDOWN = 5,       /* Arnoldi breakdown before convergence */
+  TPP_ERR_SCHUR = 6,           /* Francis QR did not converge within its iteration cap */
+  TPP_ERR_NAN = 7,             /* NaN or Inf met in a residual */
+  TPP_ERR_UNSUPPORTED = 8,     /* valid request this build does not implement */
+  TPP_ERR_WORKSPACE = 9        /* workspace too small or misaligned */
+} tpp_status;
+
+typedef enum { TPP_FP64 = 0, TPP_FP32 = 1 } tpp_prec;
+
+typedef enum {
+  TPP_PC_NONE = 0,         /* unpreconditioned */
+  TPP_PC_KRON = 1,         /* KSVD Kronecker preconditioner (Alg. 2d-apply / 3d-apply) */
+  TPP_PC_BLOCK_JACOBI = 2  /* exact block Jacobi (dense LU of each diagonal block) */
+} tpp_pc;
+
+/* Feature bits for tpp_workspace_bytes / tpp_create. */
+#define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^(2d) doubles per element for exact block Jacobi */
+#define TPP_FEAT_MIXED        2u  /* reserve float32 copies of the Kronecker apply factors */
+
+/*
+ * Problem description.  Velocity field (component c) at the normalised point
+ * xi = x / L of the periodic domain [0, L_1] x ... (L_d = nel[d] h):
+ *   a_c(x) = a0[c] + sum_m amp[c*n_modes + m] * cos(2 pi kvec[(c*n_modes + m)*dim + .] . xi
+ *                                                  + phase[c*n_modes + m])
+ * All pointers are host pointers, read during tpp_create only.
+ * Mesh: element (ex, ey[, ez]) covers [ex h, (ex+1) h] x ...; periodic wrap in
+ * every direction.  Limits: dim in {2, 3}; 1 <= n <= 32; nel[d] >= 1;
+ * h > 0; dt >= 0; 0 <= n_modes <= 64.
+ */
+typedef struct {
+  int32_t dim;
+  int32_t n;
+  int32_t nel[3];
+  double h;
+  double dt;
+  int32_t n_modes;
+  const double* a0;     /* [dim] */
+  const double* amp;    /* [dim * n_modes] */
+  const int32_t* kvec;  /* [dim * n_modes * dim] */
+  const double* phase;  /* [dim * n_modes] */
+} tpp_problem;
+
+typedef struct {
+  int32_t restart;      /* GMRES(m) restart length, 1 <= m <= max_restart of the context */
+  int32_t max_iters;    /* total Arnoldi steps over all cycles, >= 1 */
+  double rtol;          /* stop when ||b - A x|| <= rtol ||b||, rtol > 0 */
+  int32_t pc;           /* tpp_pc */
+  int32_t inner_prec;   /* tpp_prec of the Kronecker apply; TPP_FP32 needs TPP_FEAT_MIXED */
+  int32_t flexible;     /* 1: flexible GMRES (stores Z = P^-1 V); forced to 1 when inner_prec != FP64 */
+} tpp_gmres_opts;
+
+typedef struct {
+  int32_t iters;        /* Arnoldi steps taken */
+  int32_t cycles;       /* restart cycles */
+  int32_t status;       /* tpp_status of the solve */
+  int32_t converged;    /* 1 when the true relative residual <= rtol */
+  double true_rel_res;  /* ||b - A x|| / ||b|| of the returned x */
+  double est_rel_res;   /* last Arnoldi (Givens) estimate */
+} tpp_gmres_result;
+
+typedef struct {
+  int32_t num_elem;
+  int32_t num_shifted;     /* elements that inverted A2 + alpha A1 and B1 - alpha B2 with
+                              alpha != 0 (same P; chosen for conditioning) */
+  int32_t num_rank1;       /* elements with sigma_2 <= 1e-14 sigma_1 (P = A1 (x) B1) */
+  int32_t num_schur_fail;  /* elements whose Francis iteration hit its cap */
+  double max_cond;         /* largest cond_1(L_A) * cond_1(L_B) of the inverted factor pair */
+  double min_sigma_ratio;  /* min over elements of sigma_2 / sigma_1 */
+} tpp_build_report;
+
+typedef struct tpp_ctx tpp_ctx;
+
+/*
+ * Bytes of device workspace a context needs (256-byte aligned start required).
+ * max_restart bounds the GMRES restart length later requested; features is a
+ * mask of TPP_FEAT_*.  Returns 0 when the problem is invalid.
+ */
+size_t tpp_workspace_bytes(const tpp_problem* prob, int32_t max_restart, uint32_t features);
+
+/*
+ * Create a context on the caller's workspace and run the precomputation step of
+ * Alg. matrix-free-matvec (steps 1-2): 1D Gauss-Legendre tables, the flux
+ * Jacobians dF/du = a at volume nodes and dF^/du^- = max(a.n, 0) at face nodes
+ * (Sec. 3.4.1), and the element-independent basis of the rearranged block used
+ * by the factor build.  Synchronises `stream` before returning.
+ * workspace: device, ws_bytes >= tpp_workspace_bytes(prob, max_restart, features).
+ */
+tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restart,
+                      uint32_t features, void* workspace, size_t ws_bytes, void* stream);
+
+/* Release the host-side context (the workspace stays the caller's). */
+void tpp_destroy(tpp_ctx* ctx);
+
+/*
+ * Form the Kronecker preconditioner of every element (Alg. 2d-form in 2D,
+ * Alg. 3d-form in 3D): best rank-2 (3D: nested rank-1 then rank-2) Kronecker
+ * approximation of the exact diagonal block by a Golub-Kahan-Lanczos SVD of its
+ * Van Loan-Pitsianis rearrangement (Sec. 4.1, Alg. lanczos), LU inverses of the
+ * factors the paper inverts, real Schur forms of the two factor products
+ * (Eq. quad-triang).  2D: the inverted pair is (A2 + alpha A1, B1 - alpha B2),
+ * which leaves P = A1 (x) B1 + A2 (x) B2 unchanged; alpha = 0 is the paper's
+ * choice and a nonzero alpha is taken only when it lowers the condition
+ * numbers of the inverted factors.  Factors are stored in the workspace.  `report` (host, may
+ * be NULL) is filled after a stream synchronisation.
+ * Returns TPP_ERR_SINGULAR_FACTOR / TPP_ERR_SCHUR when an element could not be
+ * factored (the report counts them).
+ */
+tpp_status tpp_build_factors(tpp_ctx* ctx, tpp_build_report* report, void* stream);
+
+/*
+ * Exact block-Jacobi comparator: assemble each n^d x n^d diagonal block from the
+ * flux Jacobians and LU-factor it (dense, partial pivoting).  Needs
+ * TPP_FEAT_BLOCK_JACOBI.  Asynchronous.
+ */
+tpp_status tpp_build_block_jacobi(tpp_ctx* ctx, void* stream);
+
+/*
+ * x = P^-1 b, element by element (Alg. 2d-apply / 3d-apply): b~ = S_B B S_A^T,
+ * quasi-triangular Sylvester solve T2 Y + Y T1^T = b~, x = Q2 Y Q1^T (2D; the
+ * 3D form applies the A1^-1 factor along z and one Sylvester solve per z-slice).
+ * b, x: device float64 [num_dofs], must not alias.  prec selects the arithmetic
+ * and factor precision (TPP_FP32 needs TPP_FEAT_MIXED).  Asynchronous.
+ */
+tpp_status tpp_apply_inverse(const tpp_ctx* ctx, const double* b, double* x, int32_t prec,
+                             void* stream);
+
+/* x = (block-Jacobi)^-1 b with the exact block LU factors.  Asynchronous. */
+tpp_status tpp_apply_block_jacobi(const tpp_ctx* ctx, const double* b, double* x, void* stream);
+
+/*
+ * y = (M + dt A) x by sum factorisation (Alg. matrix-free-matvec step 3): mass
+ * h^d w(x)w, volume -dt h^(d-1) sum_c (D^T along c) of w a_c x, upwind face
+ * fluxes lifted by the endpoint values.  x, y: device float64 [num_dofs], must
+ * not alias.  Asynchronous.
+ */
+tpp_status dg_apply_sumfact(const tpp_ctx* ctx, const double* x, double* y, void* stream);
+
+/*
+ * Solve S x = b by restarted right-preconditioned GMRES(m) (Sec. 5 opening;
+ * classical Gram-Schmidt with one reorthogonalisation, Givens rotations on
+ * the device).  b: device float64 [num_dofs]; x: device float64 [num_dofs],
+ * on entry the initial guess, on exit the solution.  Synchronises `stream`
+ * and fills `result` (host, required).
+ */
+tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres_opts* opts,
+                       tpp_gmres_result* result, void* stream);
+
+/* Device pointers into the workspace for inspection (tests); NULL if absent. */
+typedef struct {
+  const double* sigma;   /* [E][2] top singular values of the rearranged block (2D) */
+  const double* A1;      /* [E][n*n] column-major factors, A on y (2D) */
+  const double* B1;
+  const double* A2;
+  const double* B2;
+  const double* SA;      /* [E][n*n] Q1^T L_A^-1 */
+  const double* SB;      /* [E][n*n] Q2^T L_B^-1 */
+  const double* Q1;
+  const double* Q2;
+  const double* T1;
+  const double* T2;
+  const int32_t* flags;  /* [E] bit0 shifted pair, bit1 rank-1, bit2 schur fail, bit3 singular */
+  const double* cond;    /* [E] cond_1(L_A) * cond_1(L_B) of the inverted factor pair */
+  const double* gl_x;    /* [n] Gauss-Legendre nodes on [0, 1] */
+  const double* gl_w;    /* [n] weights */
+  const double* D;       /* [n*n] D[a*n + j] = phi_j'(x_a) */
+} tpp_views;
+
+tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);
+
+/* Stream-ordered device-to-device copy of `bytes` bytes (for callers that read
+ * the views above without a CUDA runtime of their own).  Asynchronous. */
+tpp_status tpp_copy_device(void* dst, const void* src, size_t bytes, void* stream);
+
+/* Number of DOFs and elements of the context's problem. */
+int64_t tpp_num_dofs(const tpp_ctx* ctx);
+int64_t tpp_num_elem(const tpp_ctx* ctx);
+
+/* Thread-local message of the last error (never NULL). */
+const char* tpp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPP_H */

@@ -1,0 +1,19 @@
+"""GB300-native Kronecker-SVD preconditioned matrix-free GMRES for high-order DG.
+
+The compute path is libtpp.so (CUDA, sm_103a) behind the C ABI of
+include/tpp.h; this package only marshals arguments to it (ctypes) and uses
+PyTorch for device memory and streams.  Importing ``Context`` loads the
+library and fails loudly when it has not been built.
+"""
+from ._lib import (TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, TPP_PC_BLOCK_JACOBI,
+                   TPP_PC_KRON, TPP_PC_NONE, TppError)
+
+__all__ = ["Context", "TppError", "TPP_FP64", "TPP_FP32", "TPP_PC_NONE", "TPP_PC_KRON",
+           "TPP_PC_BLOCK_JACOBI", "TPP_FEAT_MIXED", "TPP_FEAT_BLOCK_JACOBI"]
+
+
+def __getattr__(name):
+    if name == "Context":
+        from .solver import Context
+        return Context
+    raise AttributeError(name)

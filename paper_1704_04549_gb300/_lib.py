@@ -1,0 +1,97 @@
+"""ctypes declarations of the libtpp C ABI (include/tpp.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtpp.so")
+
+TPP_OK = 0
+STATUS_NAMES = {0: "TPP_OK", 1: "TPP_ERR_INVALID_ARG", 2: "TPP_ERR_CUDA",
+                3: "TPP_ERR_SINGULAR_FACTOR", 4: "TPP_ERR_NOT_CONVERGED", 5: "TPP_ERR_BREAKDOWN",
+                6: "TPP_ERR_SCHUR", 7: "TPP_ERR_NAN", 8: "TPP_ERR_UNSUPPORTED",
+                9: "TPP_ERR_WORKSPACE"}
+TPP_FP64, TPP_FP32 = 0, 1
+TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
+TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED = 1, 2
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("nel", C.c_int32 * 3),
+                ("h", C.c_double), ("dt", C.c_double), ("n_modes", C.c_int32),
+                ("a0", C.POINTER(C.c_double)), ("amp", C.POINTER(C.c_double)),
+                ("kvec", C.POINTER(C.c_int32)), ("phase", C.POINTER(C.c_double))]
+
+
+class GmresOpts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
+                ("pc", C.c_int32), ("inner_prec", C.c_int32), ("flexible", C.c_int32)]
+
+
+class GmresResult(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("status", C.c_int32),
+                ("converged", C.c_int32), ("true_rel_res", C.c_double),
+                ("est_rel_res", C.c_double)]
+
+
+class BuildReport(C.Structure):
+    _fields_ = [("num_elem", C.c_int32), ("num_shifted", C.c_int32), ("num_rank1", C.c_int32),
+                ("num_schur_fail", C.c_int32), ("max_cond", C.c_double),
+                ("min_sigma_ratio", C.c_double)]
+
+
+class Views(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in
+                ("sigma", "A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2", "flags",
+                 "cond", "gl_x", "gl_w", "D")]
+
+
+EXPORTS = {
+    "tpp_workspace_bytes": (C.c_size_t, [C.POINTER(Problem), C.c_int32, C.c_uint32]),
+    "tpp_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Problem), C.c_int32, C.c_uint32,
+                             C.c_void_p, C.c_size_t, C.c_void_p]),
+    "tpp_destroy": (None, [C.c_void_p]),
+    "tpp_build_factors": (C.c_int, [C.c_void_p, C.POINTER(BuildReport), C.c_void_p]),
+    "tpp_build_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tpp_apply_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "tpp_apply_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_apply_sumfact": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
+                              C.POINTER(GmresResult), C.c_void_p]),
+    "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),
+    "tpp_copy_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "tpp_num_dofs": (C.c_int64, [C.c_void_p]),
+    "tpp_num_elem": (C.c_int64, [C.c_void_p]),
+    "tpp_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtpp.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_1704_04549_gb300.build.build() first")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TppError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().tpp_last_error().decode()
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != TPP_OK:
+        raise TppError(status, where)

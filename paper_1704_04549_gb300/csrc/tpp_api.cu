@@ -1,0 +1,566 @@
+// Host side of the C ABI declared in include/tpp.h: validation, workspace
+// layout, launch sequencing and the restarted GMRES driver.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tpp_internal.cuh"
+
+namespace tpp {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tpp_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TPP_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return TPP_ERR_CUDA;
+}
+
+// GMRES kernels (k_gmres.cu)
+cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
+                       int stride, int nblk, const int32_t* skip, cudaStream_t s);
+cudaError_t gmres_reduce(const double* partials, int nblk, int stride, int nvec, double* h,
+                         const int32_t* skip, cudaStream_t s);
+cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
+                         double* partials, int stride, int mode, int nblk, const int32_t* skip,
+                         cudaStream_t s);
+cudaError_t gmres_finish(GmresState* st, double* H, double* cs, double* sn, double* g,
+                         const double* h1, const double* h2, const double* partials, int nblk,
+                         int stride, int j, double* inv_beta, cudaStream_t s);
+cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, double* y,
+                      cudaStream_t s);
+cudaError_t gmres_combine(const double* B, int64_t N, const GmresState* st, const double* y,
+                          double* out, int accumulate, cudaStream_t s);
+cudaError_t vec_scale(double* out, const double* in, int64_t N, const double* sptr, double sval,
+                      const int32_t* skip, cudaStream_t s);
+cudaError_t vec_sub(double* out, const double* a, const double* b, int64_t N, cudaStream_t s);
+cudaError_t vec_norm(const double* x, int64_t N, double* partials, int stride, int nblk,
+                     double* out, cudaStream_t s);
+cudaError_t gmres_cycle_init(GmresState* st, double* g, double beta, int m, double bnorm,
+                             double rtol, cudaStream_t s);
+cudaError_t vec_axpy(double* out, const double* in, double a, int64_t N, cudaStream_t s);
+
+namespace {
+
+constexpr int kPartialBlocks = 152 * 4;
+constexpr int kPartialStride = 64;
+constexpr int kMaxRestart = 63;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct GBuf {   // offsets (doubles) inside the gbuf region
+  size_t H, cs, sn, g, h1, h2, y, invb, scal, total;
+};
+
+GBuf gbuf_layout(int m) {
+  GBuf b;
+  b.H = 0;
+  b.cs = b.H + (size_t)(m + 1) * m;
+  b.sn = b.cs + m;
+  b.g = b.sn + m;
+  b.h1 = b.g + m + 1;
+  b.h2 = b.h1 + m + 1;
+  b.y = b.h2 + m + 1;
+  b.invb = b.y + m;
+  b.scal = b.invb + 1;
+  b.total = b.scal + 8;
+  return b;
+}
+
+const char* validate(const tpp_problem* p, int32_t max_restart) {
+  if (!p) return "problem is NULL";
+  if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
+  if (p->n < 1 || p->n > TPP_MAX_N) return "n must be in [1, 32]";
+  for (int d = 0; d < p->dim; ++d)
+    if (p->nel[d] < 1) return "nel[d] must be >= 1";
+  if (!(p->h > 0.0) || !std::isfinite(p->h)) return "h must be positive and finite";
+  if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return "dt must be >= 0 and finite";
+  if (p->n_modes < 0 || p->n_modes > TPP_MAX_MODES) return "n_modes must be in [0, 64]";
+  if (!p->a0) return "a0 is NULL";
+  if (p->n_modes > 0 && (!p->amp || !p->kvec || !p->phase)) return "Fourier arrays are NULL";
+  if (max_restart < 1 || max_restart > kMaxRestart) return "max_restart must be in [1, 63]";
+  return nullptr;
+}
+
+Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t features,
+                      int* rz_out) {
+  const int n = p->n, d = p->dim;
+  const int64_t E = (int64_t)p->nel[0] * p->nel[1] * (d == 3 ? p->nel[2] : 1);
+  const int64_t nloc = (d == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t nfl = (d == 2) ? n : (int64_t)n * n;
+  const int64_t N = E * nloc;
+  const int nc = n + 3, Ro = n * n - n;
+  const int rz = Ro < nc ? Ro : nc;
+  if (rz_out) *rz_out = rz;
+  const int m = max_restart;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + (bytes ? bytes : 8));
+    return o;
+  };
+  L.vel = take(sizeof(VelParams));
+  L.tables = take(sizeof(Tables));
+  L.status = take(sizeof(DevStatus));
+  L.gstate = take(sizeof(GmresState));
+  L.gbuf = take(gbuf_layout(m).total * sizeof(double));
+  L.zd = take((size_t)n * nc * 8);
+  L.rz = take((size_t)nc * nc * 8);
+  L.qo = take((size_t)Ro * nc * 8);
+  L.qr_work = take((size_t)Ro * nc * 8);
+  L.qr_tau = take((size_t)nc * 8);
+  L.cx = take((size_t)N * 8);
+  L.cy = take((size_t)N * 8);
+  L.cz = (d == 3) ? take((size_t)N * 8) : 0;
+  L.sx = take((size_t)E * nfl * 8);
+  L.sy = take((size_t)E * nfl * 8);
+  L.sz = (d == 3) ? take((size_t)E * nfl * 8) : 0;
+  L.traces = take((size_t)E * 2 * d * nfl * 8);
+  const size_t fsz = (size_t)E * n * n * 8;
+  L.sigma = take((size_t)E * 2 * 8);
+  L.fA1 = take(fsz);
+  L.fB1 = take(fsz);
+  L.fA2 = take(fsz);
+  L.fB2 = take(fsz);
+  L.fC1 = (d == 3) ? take(fsz) : 0;
+  L.fC2 = (d == 3) ? take(fsz) : 0;
+  L.fSA = take(fsz);
+  L.fSB = take(fsz);
+  L.fQ1 = take(fsz);
+  L.fQ2 = take(fsz);
+  L.fT1 = take(fsz);
+  L.fT2 = take(fsz);
+  L.fSC = take((size_t)E * 8 * ((d == 3) ? n * n : 1));
+  L.flags = take((size_t)E * 4);
+  L.masks = take((size_t)E * 2 * 4);
+  L.f32 = (features & TPP_FEAT_MIXED) ? take((size_t)7 * E * n * n * 4) : 0;
+  L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
+  L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
+  L.V = take((size_t)(m + 1) * N * 8);
+  L.Z = take((size_t)m * N * 8);
+  L.vtmp = take((size_t)N * 8);
+  L.vtmp2 = take((size_t)N * 8);
+  L.partials = take((size_t)kPartialBlocks * kPartialStride * 8);
+  L.hbuf = 0;
+  L.total = off;
+  return L;
+}
+
+#define TPP_TRY_CUDA(expr, what)                          \
+  do {                                                    \
+    tpp_status _s = cuda_check((expr), what);             \
+    if (_s != TPP_OK) return _s;                          \
+  } while (0)
+
+tpp_status check_ctx(const tpp_ctx* c) {
+  if (!c) {
+    set_error("context is NULL");
+    return TPP_ERR_INVALID_ARG;
+  }
+  return TPP_OK;
+}
+
+DevStatus fresh_status() {
+  DevStatus st;
+  std::memset(&st, 0, sizeof(st));
+  st.max_cond = 0.0;
+  st.min_sigma_ratio = 1.0;
+  return st;
+}
+
+// y = S x through the sum-factorised operator (traces then element kernel)
+cudaError_t apply_operator(const tpp_ctx* c, const double* x, double* y, const int32_t* skip,
+                           cudaStream_t s) {
+  cudaError_t e = launch_traces(c, x, c->p<double>(c->L.traces), s);
+  if (e != cudaSuccess) return e;
+  return launch_dg_apply(c, x, c->p<double>(c->L.traces), y, skip, s);
+}
+
+cudaError_t apply_precond(const tpp_ctx* c, int pc, int prec, const double* b, double* x,
+                          const int32_t* skip, cudaStream_t s) {
+  if (pc == TPP_PC_NONE) {
+    return cudaMemcpyAsync(x, b, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  if (pc == TPP_PC_BLOCK_JACOBI) return launch_bj_apply(c, b, x, skip, s);
+  if (c->dim == 2) return launch_apply_2d(c, b, x, prec, skip, s);
+  return launch_apply_3d(c, b, x, prec, skip, s);
+}
+
+}  // namespace
+}  // namespace tpp
+
+using namespace tpp;
+
+extern "C" {
+
+const char* tpp_last_error(void) { return g_last_error.c_str(); }
+
+size_t tpp_workspace_bytes(const tpp_problem* prob, int32_t max_restart, uint32_t features) {
+  if (validate(prob, max_restart)) return 0;
+  return compute_layout(prob, max_restart, features, nullptr).total;
+}
+
+tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restart,
+                      uint32_t features, void* workspace, size_t ws_bytes, void* stream) {
+  if (!out) {
+    set_error("out is NULL");
+    return TPP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (const char* why = validate(prob, max_restart)) {
+    set_error(why);
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (prob->dim == 3) {
+    set_error("3D problems are not implemented in this build");
+    return TPP_ERR_UNSUPPORTED;
+  }
+  int rz = 0;
+  const Layout L = compute_layout(prob, max_restart, features, &rz);
+  if (!workspace || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+    set_error("workspace NULL, smaller than tpp_workspace_bytes() or not 256-byte aligned");
+    return TPP_ERR_WORKSPACE;
+  }
+  int dev = 0;
+  TPP_TRY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaPointerAttributes attr;
+  TPP_TRY_CUDA(cudaPointerGetAttributes(&attr, workspace), "cudaPointerGetAttributes");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+    set_error("workspace is not device memory");
+    return TPP_ERR_INVALID_ARG;
+  }
+  tpp_ctx* c = new tpp_ctx();
+  c->prob = *prob;
+  c->prob.a0 = nullptr;
+  c->prob.amp = nullptr;
+  c->prob.kvec = nullptr;
+  c->prob.phase = nullptr;
+  c->n = prob->n;
+  c->dim = prob->dim;
+  c->E = (int64_t)prob->nel[0] * prob->nel[1] * (prob->dim == 3 ? prob->nel[2] : 1);
+  c->nloc = (prob->dim == 2) ? prob->n * prob->n : prob->n * prob->n * prob->n;
+  c->N = c->E * c->nloc;
+  c->max_restart = max_restart;
+  c->features = features;
+  c->rz = rz;
+  c->r = prob->n + rz;
+  c->ws = static_cast<char*>(workspace);
+  c->ws_bytes = ws_bytes;
+  c->L = L;
+  c->factors_built = false;
+  c->bj_built = false;
+  c->partial_blocks = kPartialBlocks;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // velocity parameters
+  VelParams vp;
+  std::memset(&vp, 0, sizeof(vp));
+  vp.dim = prob->dim;
+  vp.n_modes = prob->n_modes;
+  for (int cc = 0; cc < prob->dim; ++cc) vp.a0[cc] = prob->a0[cc];
+  for (int i = 0; i < prob->dim * prob->n_modes; ++i) {
+    vp.amp[i] = prob->amp[i];
+    vp.phase[i] = prob->phase[i];
+  }
+  for (int i = 0; i < prob->dim * prob->n_modes * prob->dim; ++i) vp.kvec[i] = prob->kvec[i];
+  const DevStatus st0 = fresh_status();
+  tpp_status rc = TPP_OK;
+  do {
+    if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.vel, &vp, sizeof(vp), cudaMemcpyHostToDevice, s),
+                         "copy velocity parameters")) != TPP_OK) break;
+    if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.status, &st0, sizeof(st0),
+                                         cudaMemcpyHostToDevice, s), "init status")) != TPP_OK) break;
+    if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.tables, 0, sizeof(Tables), s), "memset")) != TPP_OK) break;
+    if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
+    if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
+    if ((rc = cuda_check(launch_precompute(c, s), "k_precompute")) != TPP_OK) break;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "tpp_create sync")) != TPP_OK) break;
+  } while (0);
+  if (rc != TPP_OK) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return TPP_OK;
+}
+
+void tpp_destroy(tpp_ctx* ctx) { delete ctx; }
+
+int64_t tpp_num_dofs(const tpp_ctx* ctx) { return ctx ? ctx->N : -1; }
+int64_t tpp_num_elem(const tpp_ctx* ctx) { return ctx ? ctx->E : -1; }
+
+tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevStatus st0 = fresh_status();
+  TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
+               "reset status");
+  TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
+  if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_to_f32(c, s), "k_to_f32");
+  DevStatus st;
+  TPP_TRY_CUDA(cudaMemcpyAsync(&st, c->ws + c->L.status, sizeof(st), cudaMemcpyDeviceToHost, s),
+               "read status");
+  TPP_TRY_CUDA(cudaStreamSynchronize(s), "tpp_build_factors sync");
+  if (report) {
+    report->num_elem = (int32_t)c->E;
+    report->num_shifted = st.build_shifted;
+    report->num_rank1 = st.build_rank1;
+    report->num_schur_fail = st.build_schur_fail;
+    report->max_cond = st.max_cond;
+    report->min_sigma_ratio = st.min_sigma_ratio;
+  }
+  c->factors_built = true;
+  if (st.build_schur_fail) {
+    set_error("Francis QR hit its iteration cap on " + std::to_string(st.build_schur_fail) +
+              " element(s)");
+    return TPP_ERR_SCHUR;
+  }
+  if (st.build_singular) {
+    set_error(std::to_string(st.build_singular) + " element(s) have singular Kronecker factors");
+    return TPP_ERR_SINGULAR_FACTOR;
+  }
+  return TPP_OK;
+}
+
+tpp_status tpp_build_block_jacobi(tpp_ctx* c, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!(c->features & TPP_FEAT_BLOCK_JACOBI)) {
+    set_error("context was created without TPP_FEAT_BLOCK_JACOBI");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(launch_bj_build(c, static_cast<cudaStream_t>(stream)), "block Jacobi build");
+  c->bj_built = true;
+  return TPP_OK;
+}
+
+tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32_t prec,
+                             void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!b || !x || b == x) {
+    set_error("b and x must be non-NULL and distinct");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (prec != TPP_FP64 && prec != TPP_FP32) {
+    set_error("prec must be TPP_FP64 or TPP_FP32");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (prec == TPP_FP32 && !(c->features & TPP_FEAT_MIXED)) {
+    set_error("TPP_FP32 apply needs a context created with TPP_FEAT_MIXED");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (!c->factors_built) {
+    set_error("tpp_build_factors has not been called");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(apply_precond(c, TPP_PC_KRON, prec, b, x, nullptr,
+                             static_cast<cudaStream_t>(stream)), "tpp_apply_inverse");
+  return TPP_OK;
+}
+
+tpp_status tpp_apply_block_jacobi(const tpp_ctx* c, const double* b, double* x, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!b || !x || b == x) {
+    set_error("b and x must be non-NULL and distinct");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (!c->bj_built) {
+    set_error("tpp_build_block_jacobi has not been called");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(launch_bj_apply(c, b, x, nullptr, static_cast<cudaStream_t>(stream)),
+               "tpp_apply_block_jacobi");
+  return TPP_OK;
+}
+
+tpp_status dg_apply_sumfact(const tpp_ctx* c, const double* x, double* y, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!x || !y || x == y) {
+    set_error("x and y must be non-NULL and distinct");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(apply_operator(c, x, y, nullptr, static_cast<cudaStream_t>(stream)),
+               "dg_apply_sumfact");
+  return TPP_OK;
+}
+
+tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!o) {
+    set_error("out is NULL");
+    return TPP_ERR_INVALID_ARG;
+  }
+  std::memset(o, 0, sizeof(*o));
+  o->sigma = c->p<double>(c->L.sigma);
+  o->A1 = c->p<double>(c->L.fA1);
+  o->B1 = c->p<double>(c->L.fB1);
+  o->A2 = c->p<double>(c->L.fA2);
+  o->B2 = c->p<double>(c->L.fB2);
+  o->SA = c->p<double>(c->L.fSA);
+  o->SB = c->p<double>(c->L.fSB);
+  o->Q1 = c->p<double>(c->L.fQ1);
+  o->Q2 = c->p<double>(c->L.fQ2);
+  o->T1 = c->p<double>(c->L.fT1);
+  o->T2 = c->p<double>(c->L.fT2);
+  o->flags = c->p<int32_t>(c->L.flags);
+  o->cond = c->p<double>(c->L.fSC);
+  const Tables* T = c->p<Tables>(c->L.tables);
+  o->gl_x = T->x;
+  o->gl_w = T->w;
+  o->D = T->D;
+  return TPP_OK;
+}
+
+tpp_status tpp_copy_device(void* dst, const void* src, size_t bytes, void* stream) {
+  if (bytes == 0) return TPP_OK;
+  if (!dst || !src) {
+    set_error("dst and src must be non-NULL");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(stream)), "tpp_copy_device");
+  return TPP_OK;
+}
+
+tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_opts* opts,
+                       tpp_gmres_result* res, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!b || !x || b == x || !opts || !res) {
+    set_error("b, x, opts, result must be non-NULL and b != x");
+    return TPP_ERR_INVALID_ARG;
+  }
+  const int m = opts->restart;
+  if (m < 1 || m > c->max_restart || opts->max_iters < 1 || !(opts->rtol > 0.0) ||
+      opts->pc < TPP_PC_NONE || opts->pc > TPP_PC_BLOCK_JACOBI ||
+      (opts->inner_prec != TPP_FP64 && opts->inner_prec != TPP_FP32)) {
+    set_error("invalid GMRES options (restart, max_iters, rtol, pc or inner_prec)");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (opts->pc == TPP_PC_KRON && !c->factors_built) {
+    set_error("TPP_PC_KRON needs tpp_build_factors first");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (opts->pc == TPP_PC_BLOCK_JACOBI && !c->bj_built) {
+    set_error("TPP_PC_BLOCK_JACOBI needs tpp_build_block_jacobi first");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (opts->inner_prec == TPP_FP32 && !(c->features & TPP_FEAT_MIXED)) {
+    set_error("inner_prec TPP_FP32 needs TPP_FEAT_MIXED");
+    return TPP_ERR_INVALID_ARG;
+  }
+  const bool flexible = opts->flexible || opts->inner_prec != TPP_FP64;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t N = c->N;
+  const int nblk = c->partial_blocks, stride = kPartialStride;
+  double* V = c->p<double>(c->L.V);
+  double* Z = c->p<double>(c->L.Z);
+  double* t1 = c->p<double>(c->L.vtmp);
+  double* t2 = c->p<double>(c->L.vtmp2);
+  double* partials = c->p<double>(c->L.partials);
+  GmresState* st = c->p<GmresState>(c->L.gstate);
+  const int32_t* done = &st->done;
+  const GBuf gb = gbuf_layout(c->max_restart);
+  double* gbuf = c->p<double>(c->L.gbuf);
+  double *H = gbuf + gb.H, *cs = gbuf + gb.cs, *sn = gbuf + gb.sn, *g = gbuf + gb.g;
+  double *h1 = gbuf + gb.h1, *h2 = gbuf + gb.h2, *y = gbuf + gb.y, *invb = gbuf + gb.invb;
+  double* scal = gbuf + gb.scal;
+  std::memset(res, 0, sizeof(*res));
+  auto read_scalar = [&](const double* dptr, double* hv) -> tpp_status {
+    TPP_TRY_CUDA(cudaMemcpyAsync(hv, dptr, sizeof(double), cudaMemcpyDeviceToHost, s), "read");
+    TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
+    return TPP_OK;
+  };
+  // ||b||
+  double bnorm = 0.0;
+  TPP_TRY_CUDA(vec_norm(b, N, partials, stride, nblk, scal, s), "norm b");
+  if (tpp_status r = read_scalar(scal, &bnorm)) return r;
+  if (!std::isfinite(bnorm)) {
+    set_error("right-hand side contains NaN or Inf");
+    res->status = TPP_ERR_NAN;
+    return TPP_ERR_NAN;
+  }
+  if (bnorm == 0.0) {
+    TPP_TRY_CUDA(cudaMemsetAsync(x, 0, (size_t)N * sizeof(double), s), "zero x");
+    TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
+    res->converged = 1;
+    res->status = TPP_OK;
+    return TPP_OK;
+  }
+  // r0 = b - A x0 into V[0]
+  auto residual = [&](double* beta) -> tpp_status {
+    TPP_TRY_CUDA(apply_operator(c, x, t1, nullptr, s), "operator");
+    TPP_TRY_CUDA(vec_sub(V, b, t1, N, s), "residual");
+    TPP_TRY_CUDA(vec_norm(V, N, partials, stride, nblk, scal, s), "norm r");
+    return read_scalar(scal, beta);
+  };
+  double beta = 0.0;
+  if (tpp_status r = residual(&beta)) return r;
+  res->true_rel_res = beta / bnorm;
+  res->est_rel_res = beta / bnorm;
+  int total = 0;
+  tpp_status final_status = TPP_ERR_NOT_CONVERGED;
+  if (beta <= opts->rtol * bnorm) final_status = TPP_OK;
+  while (final_status != TPP_OK && total < opts->max_iters) {
+    if (!std::isfinite(beta)) {
+      final_status = TPP_ERR_NAN;
+      break;
+    }
+    res->cycles += 1;
+    TPP_TRY_CUDA(vec_scale(V, V, N, nullptr, 1.0 / beta, nullptr, s), "scale v0");
+    TPP_TRY_CUDA(gmres_cycle_init(st, g, beta, m, bnorm, opts->rtol, s), "cycle init");
+    GmresState hs;
+    for (int j = 0; j < m && total < opts->max_iters; ++j) {
+      double* vj = V + (size_t)j * N;
+      double* w = V + (size_t)(j + 1) * N;
+      double* z = flexible ? Z + (size_t)j * N : t1;
+      TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, vj, z, done, s), "precond");
+      TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s), "traces");
+      TPP_TRY_CUDA(launch_dg_apply(c, z, c->p<double>(c->L.traces), w, done, s), "operator");
+      TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, s), "dots");
+      TPP_TRY_CUDA(gmres_reduce(partials, nblk, stride, j + 1, h1, done, s), "reduce");
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h1, w, partials, stride, 0, nblk, done, s), "update");
+      TPP_TRY_CUDA(gmres_reduce(partials, nblk, stride, j + 1, h2, done, s), "reduce");
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, done, s), "norm");
+      TPP_TRY_CUDA(gmres_finish(st, H, cs, sn, g, h1, h2, partials, nblk, stride, j, invb, s),
+                   "givens");
+      TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, nullptr, s), "scale");
+      ++total;
+      TPP_TRY_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s), "read state");
+      TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
+      res->est_rel_res = hs.est;
+      if (hs.done) break;
+    }
+    // x += P^-1 (V y) or x += Z y
+    TPP_TRY_CUDA(gmres_lsq(st, H, g, y, s), "lsq");
+    if (flexible) {
+      TPP_TRY_CUDA(gmres_combine(Z, N, st, y, x, 1, s), "x update");
+    } else {
+      TPP_TRY_CUDA(gmres_combine(V, N, st, y, t2, 0, s), "V y");
+      TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, t2, t1, nullptr, s), "precond");
+      TPP_TRY_CUDA(vec_axpy(x, t1, 1.0, N, s), "x update");
+    }
+    if (tpp_status r = residual(&beta)) return r;
+    res->true_rel_res = beta / bnorm;
+    if (beta <= opts->rtol * bnorm) {
+      final_status = TPP_OK;
+      break;
+    }
+    if (hs.breakdown == 2 || !std::isfinite(beta)) {
+      final_status = TPP_ERR_NAN;
+      break;
+    }
+  }
+  res->iters = total;
+  res->converged = (final_status == TPP_OK);
+  res->status = final_status;
+  if (final_status == TPP_ERR_NOT_CONVERGED)
+    set_error("GMRES did not reach rtol within max_iters");
+  if (final_status == TPP_ERR_NAN) set_error("NaN or Inf in the GMRES residual");
+  return final_status;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal definitions shared by the libtpp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tpp.h"
+
+#define TPP_MAX_N 32
+#define TPP_MAX_MODES 64
+
+namespace tpp {
+
+// Velocity-field parameters as stored in the workspace (see tpp_problem).
+struct VelParams {
+  int dim;
+  int n_modes;
+  double a0[3];
+  double amp[3 * TPP_MAX_MODES];
+  double kvec[3 * TPP_MAX_MODES * 3];
+  double phase[3 * TPP_MAX_MODES];
+};
+
+// 1D tables of the nodal basis (Sec. 3.2): Gauss-Legendre nodes x and weights
+// w on [0, 1], D[a*n + j] = phi_j'(x_a), l0[j] = phi_j(0), l1[j] = phi_j(1).
+struct Tables {
+  double x[TPP_MAX_N];
+  double w[TPP_MAX_N];
+  double l0[TPP_MAX_N];
+  double l1[TPP_MAX_N];
+  double D[TPP_MAX_N * TPP_MAX_N];
+};
+
+// Device-side status words written by kernels (never trap).
+struct DevStatus {
+  int32_t build_singular;   // elements whose inverted factors were singular
+  int32_t build_schur_fail; // elements whose Francis iteration hit the cap
+  int32_t build_shifted;
+  int32_t build_rank1;
+  double max_cond;          // stored as ordered bits via atomicMax on long long
+  double min_sigma_ratio;
+  int32_t nan_seen;
+  int32_t pad;
+};
+
+// GMRES device state (one solve at a time per context).
+struct GmresState {
+  int32_t j;          // current Arnoldi column
+  int32_t done;       // 1 when the current cycle must stop
+  int32_t k;          // columns completed in this cycle
+  int32_t breakdown;
+  double bnorm;
+  double beta;        // ||r0|| of the cycle
+  double est;         // |g_{k}| / ||b||
+  double rtol;
+  int32_t m;          // restart length
+  int32_t pad2;
+};
+
+struct Layout {
+  // offsets in bytes from workspace start
+  size_t vel, tables, status, gstate;
+  size_t zd, rz, qo, qr_work, qr_tau;   // structure basis of the rearranged block (2D)
+  size_t cx, cy, cz, sx, sy, sz;        // flux Jacobians (scaled) at nodes / faces
+  size_t traces;
+  size_t sigma, fA1, fB1, fA2, fB2, fC1, fC2;
+  size_t fSA, fSB, fQ1, fQ2, fT1, fT2, fSC;  // fSC: 3D A1^-1 factor
+  size_t flags, masks;
+  size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
+  size_t bj_lu, bj_piv;
+  size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
+  size_t total;
+};
+
+}  // namespace tpp
+
+struct tpp_ctx {
+  tpp_problem prob;        // copy (host pointers cleared)
+  int32_t n, dim;
+  int64_t E, N;            // elements, DOFs
+  int32_t nloc;            // n^dim
+  int32_t max_restart;
+  uint32_t features;
+  int32_t rz;              // rank of the off-diagonal structure block
+  int32_t r;               // size of the core matrix M = n + rz
+  char* ws;
+  size_t ws_bytes;
+  tpp::Layout L;
+  bool factors_built;
+  bool bj_built;
+  int32_t partial_blocks;  // number of CTAs of the reduction kernels
+  template <typename T> T* p(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+namespace tpp {
+
+void set_error(const std::string& msg);
+tpp_status cuda_check(cudaError_t e, const char* what);
+
+// kernels launchers (defined in the .cu files)
+cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s);
+cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                            const int32_t* skip, cudaStream_t s);
+cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
+                            const int32_t* skip, cudaStream_t s);
+cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,
+                            const int32_t* skip, cudaStream_t s);
+cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
+                            cudaStream_t s);
+
+}  // namespace tpp
+
+// ---------------------------------------------------------------------------
+// small device helpers
+namespace tpp {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; `red` must hold blockDim.x/32 doubles.  All threads get the result.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];   // same order in every thread: deterministic
+  return t;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) mapped to [-1, 1): deterministic
+// "random" start vectors for the Lanczos iteration.
+__device__ __forceinline__ double splitmix_unit(uint64_t salt, uint64_t i) {
+  uint64_t z = salt * 0x9E3779B97F4A7C15ull + (i + 1) * 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27; z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+}  // namespace tpp

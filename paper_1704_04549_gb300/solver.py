@@ -1,0 +1,163 @@
+"""Thin PyTorch binding of libtpp with the names of the C ABI.
+
+Every numerical step runs in libtpp's CUDA kernels; this file only allocates
+device memory with torch, converts arguments and checks status codes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: torch.Tensor) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One DG advection problem on one GPU (a tpp_ctx and its workspace).
+
+    velocity: object with attributes dim, a0 [dim], amp [dim, M], kvec [dim, M, dim],
+    phase [dim, M] describing a_c(x) = a0_c + sum_m amp cos(2 pi k . x + phase).
+    """
+
+    def __init__(self, dim: int, n: int, nel, h: float, dt: float, velocity,
+                 max_restart: int = 30, features: int = 0, device: str = "cuda:0",
+                 stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        self.dim, self.n, self.dt, self.h = dim, n, float(dt), float(h)
+        nel = tuple(int(v) for v in nel) + (1,) * (3 - len(nel))
+        self.nel = nel[:dim]
+        self._a0 = np.ascontiguousarray(velocity.a0, dtype=np.float64)
+        self._amp = np.ascontiguousarray(velocity.amp, dtype=np.float64).reshape(-1)
+        self._kvec = np.ascontiguousarray(velocity.kvec, dtype=np.int32).reshape(-1)
+        self._phase = np.ascontiguousarray(velocity.phase, dtype=np.float64).reshape(-1)
+        M = int(np.asarray(velocity.amp).shape[1]) if np.asarray(velocity.amp).ndim == 2 else 0
+        P = L.Problem()
+        P.dim, P.n = dim, n
+        for d in range(3):
+            P.nel[d] = nel[d]
+        P.h, P.dt, P.n_modes = self.h, self.dt, M
+        P.a0 = self._a0.ctypes.data_as(C.POINTER(C.c_double))
+        P.amp = self._amp.ctypes.data_as(C.POINTER(C.c_double))
+        P.kvec = self._kvec.ctypes.data_as(C.POINTER(C.c_int32))
+        P.phase = self._phase.ctypes.data_as(C.POINTER(C.c_double))
+        self._prob = P
+        nbytes = self.lib.tpp_workspace_bytes(C.byref(P), max_restart, features)
+        if nbytes == 0:
+            raise L.TppError(1, "tpp_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.ws_bytes = nbytes
+        self.max_restart = max_restart
+        self.features = features
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.tpp_create(C.byref(ctx), C.byref(P), max_restart, features,
+                                        C.c_void_p(self._ws_ptr), nbytes, _stream(stream)),
+                    "tpp_create")
+        self._ctx = ctx
+        self.num_dofs = int(self.lib.tpp_num_dofs(ctx))
+        self.num_elem = int(self.lib.tpp_num_elem(ctx))
+
+    def __del__(self):
+        ctx = getattr(self, "_ctx", None)
+        if ctx is not None and ctx.value:
+            self.lib.tpp_destroy(ctx)
+            self._ctx = None
+
+    # -- C ABI calls ---------------------------------------------------------
+    def _vec(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == self.num_dofs):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {self.num_dofs}")
+        return t
+
+    def tpp_build_factors(self, stream=None) -> dict:
+        rep = L.BuildReport()
+        st = self.lib.tpp_build_factors(self._ctx, C.byref(rep), _stream(stream))
+        out = {k: getattr(rep, k) for k, _ in L.BuildReport._fields_}
+        out["status"] = st
+        if st not in (L.TPP_OK,):
+            raise L.TppError(st, "tpp_build_factors")
+        return out
+
+    def tpp_build_block_jacobi(self, stream=None):
+        L.check(self.lib.tpp_build_block_jacobi(self._ctx, _stream(stream)),
+                "tpp_build_block_jacobi")
+
+    def tpp_apply_inverse(self, b, x=None, prec: int = L.TPP_FP64, stream=None):
+        b = self._vec(b, "b")
+        x = torch.empty_like(b) if x is None else self._vec(x, "x")
+        L.check(self.lib.tpp_apply_inverse(self._ctx, _ptr(b), _ptr(x), prec, _stream(stream)),
+                "tpp_apply_inverse")
+        return x
+
+    def tpp_apply_block_jacobi(self, b, x=None, stream=None):
+        b = self._vec(b, "b")
+        x = torch.empty_like(b) if x is None else self._vec(x, "x")
+        L.check(self.lib.tpp_apply_block_jacobi(self._ctx, _ptr(b), _ptr(x), _stream(stream)),
+                "tpp_apply_block_jacobi")
+        return x
+
+    def dg_apply_sumfact(self, x, y=None, stream=None):
+        x = self._vec(x, "x")
+        y = torch.empty_like(x) if y is None else self._vec(y, "y")
+        L.check(self.lib.dg_apply_sumfact(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
+                "dg_apply_sumfact")
+        return y
+
+    def gmres_solve(self, b, x=None, restart: int = 30, rtol: float = 1e-8,
+                    max_iters: int = 3000, pc: int = L.TPP_PC_KRON, inner_prec: int = L.TPP_FP64,
+                    flexible: bool = False, stream=None, check: bool = True):
+        b = self._vec(b, "b")
+        x = torch.zeros_like(b) if x is None else self._vec(x, "x")
+        o = L.GmresOpts(restart, max_iters, rtol, pc, inner_prec, int(flexible))
+        r = L.GmresResult()
+        st = self.lib.gmres_solve(self._ctx, _ptr(b), _ptr(x), C.byref(o), C.byref(r),
+                                  _stream(stream))
+        res = {k: getattr(r, k) for k, _ in L.GmresResult._fields_}
+        if check and st != L.TPP_OK:
+            raise L.TppError(st, "gmres_solve")
+        return x, res
+
+    def views(self) -> dict:
+        """Copies of the factor arrays (torch tensors) for inspection."""
+        v = L.Views()
+        L.check(self.lib.tpp_get_views(self._ctx, C.byref(v)), "tpp_get_views")
+        E, n = self.num_elem, self.n
+        torch.cuda.synchronize(self.device)
+
+        def grab(addr, count, dtype):
+            out = torch.empty(count, dtype=dtype, device=self.device)
+            L.check(self.lib.tpp_copy_device(_ptr(out), C.c_void_p(addr),
+                                             count * out.element_size(), _stream(None)),
+                    "tpp_copy_device")
+            return out
+
+        res = {"sigma": grab(v.sigma, 2 * E, torch.float64).view(E, 2)}
+        for name in ("A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2"):
+            # column-major n x n per element -> [E, n, n] with [e, row, col]
+            res[name] = grab(getattr(v, name), E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
+        res["flags"] = grab(v.flags, E, torch.int32)
+        res["cond"] = grab(v.cond, E, torch.float64)
+        res["gl_x"] = grab(v.gl_x, n, torch.float64)
+        res["gl_w"] = grab(v.gl_w, n, torch.float64)
+        res["D"] = grab(v.D, n * n, torch.float64).view(n, n)
+        torch.cuda.synchronize(self.device)
+        return res
+
+

@@ -1,0 +1,88 @@
+"""GPU parity: GMRES solves vs the oracle's GMRES and direct solves."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import synthetic
+from oracle.gmres import gmres
+from oracle.precond import block_jacobi, kron_dense
+from paper_1704_04549_gb300 import TPP_FEAT_BLOCK_JACOBI, TPP_PC_BLOCK_JACOBI, TPP_PC_KRON, TPP_PC_NONE
+from tests.gpu_util import make_pair, rel, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("h", [1.0, 1.0 / 8])
+def test_config_8x8_constant_jacobi_vs_kron(h):
+    """8x8 periodic unit-square quads (and the h = 1/8 reading), n = 8,
+    a = (1, 0.5), dt = 0.1: J and K give the same iteration counts."""
+    ctx, dg = make_pair(8, (8, 8), 0.1, synthetic.constant_velocity([1.0, 0.5]),
+                        features=TPP_FEAT_BLOCK_JACOBI, h=h)
+    ctx.tpp_build_factors()
+    ctx.tpp_build_block_jacobi()
+    b = synthetic.rhs(1704, dg.ndof)
+    S = dg.global_matrix()
+    xs = spla.spsolve(S.tocsc(), b)
+    xK, rK = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    xJ, rJ = ctx.gmres_solve(to_dev(b), pc=TPP_PC_BLOCK_JACOBI, rtol=1e-8)
+    _, oK = gmres(lambda v: S @ v, b, M=kron_dense(dg), rtol=1e-8)
+    _, oJ = gmres(lambda v: S @ v, b, M=block_jacobi(dg), rtol=1e-8)
+    assert rK["converged"] and rJ["converged"]
+    assert rK["true_rel_res"] <= 1e-8 and rJ["true_rel_res"] <= 1e-8
+    assert rK["iters"] == rJ["iters"]
+    assert abs(rK["iters"] - oK["iters"]) <= 1 and abs(rJ["iters"] - oJ["iters"]) <= 1
+    assert rel(to_host(xK), xs) <= 1e-6 and rel(to_host(xJ), xs) <= 1e-6
+    # block-Jacobi apply vs the oracle's exact block inverse
+    r = synthetic.rhs(3, dg.ndof)
+    assert rel(to_host(ctx.tpp_apply_block_jacobi(to_dev(r))), block_jacobi(dg)(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,nel,kmax", [(5, (3, 5), 1), (8, (4, 4), 1), (12, (4, 4), 1),
+                                         (5, (6, 6), 2)])
+def test_fourier_gmres_matches_oracle(n, nel, kmax):
+    ctx, dg = make_pair(n, nel, 0.05, synthetic.fourier_velocity(1705, 2, kmax=kmax), h=1.0)
+    ctx.tpp_build_factors()
+    b = synthetic.rhs(1706, dg.ndof)
+    S = dg.global_matrix()
+    x_ref, o = gmres(lambda v: S @ v, b, M=kron_dense(dg), rtol=1e-8)
+    assert o["converged"]
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    assert r["converged"] and r["true_rel_res"] <= 1e-8
+    assert abs(r["iters"] - o["iters"]) <= 1
+    assert rel(to_host(x), x_ref) <= 1e-6
+    x12, r12 = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-12)
+    xs = spla.spsolve(S.tocsc(), b)
+    assert r12["true_rel_res"] <= 1e-12 and rel(to_host(x12), xs) <= 1e-9
+
+
+def test_unpreconditioned_restarted():
+    ctx, dg = make_pair(3, (3, 3), 0.05, synthetic.fourier_velocity(6, 2))
+    b = synthetic.rhs(2, dg.ndof)
+    S = dg.global_matrix()
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_NONE, restart=5, rtol=1e-10, max_iters=5000)
+    _, o = gmres(lambda v: S @ v, b, restart=5, rtol=1e-10, max_iters=5000)
+    assert r["converged"] and abs(r["iters"] - o["iters"]) <= 2
+    assert np.linalg.norm(S @ to_host(x) - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_zero_rhs_and_max_iters():
+    ctx, dg = make_pair(4, (2, 2), 0.05, synthetic.fourier_velocity(6, 2))
+    ctx.tpp_build_factors()
+    import torch
+    x, r = ctx.gmres_solve(torch.zeros(dg.ndof, dtype=torch.float64, device="cuda:0"))
+    assert r["converged"] and r["iters"] == 0 and not to_host(x).any()
+    b = synthetic.rhs(2, dg.ndof)
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_NONE, max_iters=3, rtol=1e-14, check=False)
+    assert r["status"] == 4 and r["iters"] == 3 and not r["converged"]
+
+
+def test_full_size_fourier_n16_converges():
+    """64 x 64 unit-square quads, n = 16, random-Fourier field, dt = 0.05."""
+    ctx, dg = make_pair(16, (64, 64), 0.05, synthetic.fourier_velocity(1705, 2), h=1.0)
+    ctx.tpp_build_factors()
+    b = synthetic.rhs(1706, dg.ndof)
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    assert r["converged"] and r["true_rel_res"] <= 1e-8
+    # residual recomputed through the operator entry point
+    Ax = to_host(ctx.dg_apply_sumfact(x))
+    assert np.linalg.norm(Ax - b) <= 1.0001e-8 * np.linalg.norm(b)
