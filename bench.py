@@ -1,0 +1,382 @@
+"""Benchmark: KSVD-preconditioned matrix-free GMRES for 2D DG advection on GB300.
+
+One step = one pass of the whole hot path over the 64 x 64 workload: the
+Kronecker-SVD factor build of every element (Alg. 2d-form) followed by a
+restarted right-preconditioned GMRES(30) solve of (M + dt A) x = b to a
+1e-8 relative residual (Kronecker apply, sum-factorised operator, CGS2
+Arnoldi).  The flux-Jacobian precomputation runs once per context, as in
+Alg. matrix-free-matvec.
+
+Default: one GPU, n = 16 (p = 15), 64 x 64 periodic unit-square quads,
+divergence-free random-Fourier velocity (seed 1705), dt = 0.05, b ~ N(0, 1)
+(seed 1706).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 16|31] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "GMRES time to 1e-8 rel. residual (factor build + solve), 1 GB300"
+FP64_PEAK_NOTE = ("FP64 peak = 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 1258.6 GFLOP/s "
+                  "(FP64 pipe unit count and max clock; 1.19 TFLOP/s measured by a DFMA loop)")
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def workload(n: int):
+    return dict(dim=2, n=n, nel=(64, 64), h=1.0, dt=0.05,
+                velocity=synthetic.fourier_velocity(1705, 2), rhs_seed=1706)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_oracle(n: int, gmres_iters: int, budget_s: float = 20.0):
+    """The oracle, as it stands, on a bounded sample of the same workload.
+
+    Sample: the first k elements of the 64 x 64 mesh.  Per element the oracle
+    assembles the exact block, takes the dense SVD of its rearrangement,
+    LU-factors P (the factor build) and then, per GMRES iteration, applies
+    P^-1 (LU solve) and one block row of the assembled operator; the MGS
+    Arnoldi work on full-length vectors is timed on vectors of the full size
+    for the average basis length.  Extrapolated linearly to 4096 elements
+    and to the GPU run's iteration count."""
+    import scipy.linalg as sla
+
+    from oracle.dg import AdvectionDG, PeriodicMesh
+    from oracle.ksvd import ksvd_2d, kron_sum
+    w = workload(n)
+    dg = AdvectionDG(PeriodicMesh(w["nel"], w["h"]), n, w["dt"], w["velocity"])
+    nl, E = dg.nloc, dg.mesh.num_elem
+    rng = np.random.default_rng(0)
+    t_build, t_iter, k = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and k < E:
+        e = k
+        tb = time.perf_counter()
+        S = dg.element_block(e)
+        _, As, Bs = ksvd_2d(S, n)
+        lu = sla.lu_factor(kron_sum(As, Bs))
+        t_build += time.perf_counter() - tb
+        Fd, nbrs = dg.face_blocks(e)
+        v = rng.standard_normal(nl)
+        ti = time.perf_counter()
+        z = sla.lu_solve(lu, v)
+        y = S @ z
+        for _, (nb, F) in nbrs.items():
+            y += dg.dt * F @ z
+        t_iter += time.perf_counter() - ti
+        k += 1
+    N = dg.ndof
+    V = rng.standard_normal((16, N))
+    wv = rng.standard_normal(N)
+    ta = time.perf_counter()
+    for i in range(16):                         # MGS at the average basis length
+        h = np.dot(V[i], wv)
+        wv -= h * V[i]
+    t_arnoldi = time.perf_counter() - ta
+    total_s = (t_build / k) * E + gmres_iters * ((t_iter / k) * E + t_arnoldi)
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": total_s * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": (f"{k} of {E} elements (exact block, dense SVD of the rearrangement, LU of P; "
+                       f"per iteration LU solve + block-row matvec) and full-length MGS at basis "
+                       f"length 16, extrapolated to {E} elements x {gmres_iters} iterations"),
+            "sample_seconds": round(time.perf_counter() - t0, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    iters = args.ref_iters
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline_oracle(args.n, iters, budget_s=2.0)
+    t0 = time.time()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_oracle(args.n, iters, budget_s=args.ref_budget)
+        vals.append(last["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"adv2d-fourier-64x64-n{args.n}", "n": args.n,
+                       "nel": [64, 64], "h": 1.0, "dt": 0.05, "rtol": 1e-8, "restart": 30},
+            "cpu_baseline": {**last, "value": value},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(time.time() - t0, 1)}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if torch.cuda.is_available() else 0)
+    torch.cuda.set_device(dev)
+    from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, TPP_PC_KRON, Context
+    from paper_1704_04549_gb300 import _lib
+
+    lib = _lib.load()
+    w = workload(args.n)
+    ctx = Context(2, args.n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                  features=TPP_FEAT_MIXED, device=str(dev))
+    N, E, n = ctx.num_dofs, ctx.num_elem, args.n
+    b_host = synthetic.rhs(w["rhs_seed"], N)
+    b = torch.as_tensor(b_host, device=dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream(dev)
+    inner = TPP_FP32 if args.prec == "mixed" else TPP_FP64
+
+    def step():
+        ctx.tpp_build_factors()
+        x.zero_()
+        _, res = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters,
+                                 pc=TPP_PC_KRON, inner_prec=inner, flexible=(inner != TPP_FP64),
+                                 check=False)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    # timed region: K full steps, barrier + synchronize on both sides
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        results = [step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = lib.tpp_kernel_launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    res = results[-1]
+    converged = all(r["converged"] for r in results)
+
+    # split of one step: build vs solve (CUDA events)
+    torch.cuda.synchronize(dev)
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record(stream)
+    ctx.tpp_build_factors()
+    eb1.record(stream)
+    torch.cuda.synchronize(dev)
+    build_ms = eb0.elapsed_time(eb1)
+
+    # preconditioner apply throughput, FP64 and FP32 (dominant kernel), on the bench stream
+    z = torch.empty_like(b)
+    apply = {}
+    for name, prec in (("fp64", TPP_FP64), ("fp32", TPP_FP32)):
+        for _ in range(3):
+            ctx.tpp_apply_inverse(b, z, prec=prec)
+        reps = 20
+        torch.cuda.synchronize(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            ctx.tpp_apply_inverse(b, z, prec=prec)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_ms = a0.elapsed_time(a1) / reps
+        apply[name] = {"ms": t_ms, "gdofs": N / (t_ms * 1e-3) / 1e9}
+    # algorithmic work of the apply: 4 dense n x n x n products (8 n^3) + the
+    # quasi-triangular Sylvester solve (2 n^3) per element; bytes: b, x and the
+    # six n x n factors
+    flops = 10.0 * n ** 3 * E
+    achieved = flops / (apply["fp64"]["ms"] * 1e-3) / 1e9
+    roofline = {"kernel": "k_apply_2d<double>", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": None, "peak_note": FP64_PEAK_NOTE,
+                "algorithmic": "10 n^3 flop per element (8 n^3 GEMM stages + 2 n^3 Sylvester)"}
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty(N, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t_e2e = []
+    for it in range(max(1, min(args.steps, 3)) + 1):
+        t0 = time.perf_counter()
+        bd = b_pin.to(dev, non_blocking=True)
+        ctx.tpp_build_factors()
+        xd = torch.zeros_like(bd)
+        ctx.gmres_solve(bd, xd, restart=30, rtol=1e-8, max_iters=args.max_iters, pc=TPP_PC_KRON,
+                        inner_prec=inner, flexible=(inner != TPP_FP64), check=False)
+        x_pin.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if it > 0:
+            t_e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.median(t_e2e)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(n, res["iters"], budget_s=args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if inner == TPP_FP64 else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": f"adv2d-fourier-64x64-n{n} (p={n - 1}), unit-square quads, "
+                               f"dt=0.05, solenoidal random-Fourier velocity seed 1705, "
+                               f"b~N(0,1) seed 1706",
+                   "n": n, "nel": [64, 64], "h": 1.0, "dt": 0.05, "dofs": N, "rtol": 1e-8,
+                   "restart": 30, "preconditioner": "KSVD rank-2 (Alg. 2d-form / 2d-apply)",
+                   "inner_prec": args.prec,
+                   "l2": "inputs larger than L2 (Krylov basis %.0f MB + factors %.0f MB)"
+                         % (31 * N * 8 / 1e6, 6 * N * 8 / 1e6),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "gmres": {"iters": res["iters"], "cycles": res["cycles"], "converged": converged,
+                  "true_rel_res": res["true_rel_res"], "build_ms": build_ms,
+                  "solve_ms": ms - build_ms},
+        "precond_apply": {"fp64_gdofs": apply["fp64"]["gdofs"], "fp64_ms": apply["fp64"]["ms"],
+                          "fp32_gdofs": apply["fp32"]["gdofs"], "fp32_ms": apply["fp32"]["ms"]},
+        "roofline": roofline,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": N * 8,
+                "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_kernels(args):
+    """Kernel-only pass for profilers: one factor build, then a few launches of
+    each hot-path kernel on the same workload (no GMRES loop)."""
+    import torch
+    from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, Context
+    w = workload(args.n)
+    ctx = Context(2, args.n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                  features=TPP_FEAT_MIXED)
+    b = torch.as_tensor(synthetic.rhs(w["rhs_seed"], ctx.num_dofs), device="cuda:0")
+    z = torch.empty_like(b)
+    ctx.tpp_build_factors()
+    for _ in range(3):
+        ctx.tpp_apply_inverse(b, z, prec=TPP_FP64)
+    for _ in range(3):
+        ctx.tpp_apply_inverse(b, z, prec=TPP_FP32)
+    for _ in range(3):
+        ctx.dg_apply_sumfact(b, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "kernels", "n": args.n, "dofs": ctx.num_dofs}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--prec", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
+                    help="kernels: one build and a few launches of each kernel (for ncu)")
+    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=34,
+                    help="GMRES iterations the reference arm extrapolates to")
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.mode == "kernels":
+        return run_kernels(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

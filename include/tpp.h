@@ -224,6 +224,10 @@ tpp_status tpp_copy_device(void* dst, const void* src, size_t bytes, void* strea
 int64_t tpp_num_dofs(const tpp_ctx* ctx);
 int64_t tpp_num_elem(const tpp_ctx* ctx);
 
+/* Number of CUDA kernels libtpp has launched since it was loaded (all contexts
+ * and threads; instrumentation for benchmarks). */
+int64_t tpp_kernel_launch_count(void);
+
 /* Thread-local message of the last error (never NULL). */
 const char* tpp_last_error(void);
 

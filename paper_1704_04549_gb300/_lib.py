@@ -64,6 +64,7 @@ EXPORTS = {
     "tpp_num_dofs": (C.c_int64, [C.c_void_p]),
     "tpp_num_elem": (C.c_int64, [C.c_void_p]),
     "tpp_last_error": (C.c_char_p, []),
+    "tpp_kernel_launch_count": (C.c_int64, []),
 }
 
 _lib = None

@@ -186,12 +186,14 @@ cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int pr
         n, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB), c->p<double>(c->L.fQ1),
         c->p<double>(c->L.fQ2), c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), masks, b, x,
         skip);
+    count_launch();
   } else {
     const size_t smem = 4 * (size_t)nn * sizeof(float);
     const float* f = c->p<float>(c->L.f32);
     const size_t st = (size_t)c->E * nn;
     k_apply_2d<float><<<(unsigned)c->E, kApplyThreads, smem, s>>>(
         n, f, f + st, f + 2 * st, f + 3 * st, f + 4 * st, f + 5 * st, masks, b, x, skip);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -215,6 +217,7 @@ cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
                                    c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
                                    c->p<double>(c->L.fT1), c->p<double>(c->L.fT2),
                                    c->p<float>(c->L.f32), st);
+  count_launch();
   return cudaGetLastError();
 }
 

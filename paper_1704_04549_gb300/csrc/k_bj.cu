@@ -127,10 +127,12 @@ cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s) {
       c->p<Tables>(c->L.tables), c->n, c->prob.nel[0], c->prob.nel[1], c->prob.h,
       c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx), c->p<double>(c->L.sy),
       c->p<double>(c->L.bj_lu));
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_bj_lu<<<(unsigned)c->E, 256, 0, s>>>(c->nloc, c->p<double>(c->L.bj_lu),
                                          c->p<int32_t>(c->L.bj_piv));
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -138,6 +140,7 @@ cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const 
                             cudaStream_t s) {
   k_bj_solve<<<(unsigned)c->E, 256, c->nloc * sizeof(double), s>>>(
       c->nloc, c->p<double>(c->L.bj_lu), c->p<int32_t>(c->L.bj_piv), b, x, skip);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -851,6 +851,7 @@ cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
       c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx),
       c->p<double>(c->L.sy), c->p<double>(c->L.zd), c->p<double>(c->L.rz),
       c->p<double>(c->L.qo), o);
+  count_launch();
   return cudaGetLastError();
 }
 

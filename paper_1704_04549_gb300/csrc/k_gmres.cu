@@ -199,53 +199,64 @@ __global__ void k_cycle_init(GmresState* st, double* g, double beta, int m, doub
 cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
                        int stride, int nblk, const int32_t* skip, cudaStream_t s) {
   k_dots<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_reduce(const double* partials, int nblk, int stride, int nvec, double* h,
                          const int32_t* skip, cudaStream_t s) {
   k_reduce<<<1, 64, 0, s>>>(partials, nblk, stride, nvec, h, skip);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
                          double* partials, int stride, int mode, int nblk, const int32_t* skip,
                          cudaStream_t s) {
   k_update<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_finish(GmresState* st, double* H, double* cs, double* sn, double* g,
                          const double* h1, const double* h2, const double* partials, int nblk,
                          int stride, int j, double* inv_beta, cudaStream_t s) {
   k_finish_column<<<1, 32, 0, s>>>(st, H, cs, sn, g, h1, h2, partials, nblk, stride, j, inv_beta);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, double* y,
                       cudaStream_t s) {
   k_lsq<<<1, 32, 0, s>>>(st, H, g, y);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_combine(const double* B, int64_t N, const GmresState* st, const double* y,
                           double* out, int accumulate, cudaStream_t s) {
   k_combine<<<152 * 4, 256, 0, s>>>(B, N, st, y, out, accumulate);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t vec_scale(double* out, const double* in, int64_t N, const double* sptr, double sval,
                       const int32_t* skip, cudaStream_t s) {
   k_scale<<<152 * 4, 256, 0, s>>>(out, in, N, sptr, sval, skip);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t vec_sub(double* out, const double* a, const double* b, int64_t N, cudaStream_t s) {
   k_sub<<<152 * 4, 256, 0, s>>>(out, a, b, N);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t vec_norm(const double* x, int64_t N, double* partials, int stride, int nblk,
                      double* out, cudaStream_t s) {
   k_norm_partials<<<nblk, kRedThreads, 0, s>>>(x, N, partials, stride);
+  count_launch();
   k_norm_finish<<<1, 32, 0, s>>>(partials, nblk, stride, out);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_cycle_init(GmresState* st, double* g, double beta, int m, double bnorm,
                              double rtol, cudaStream_t s) {
   k_cycle_init<<<1, 32, 0, s>>>(st, g, beta, m, bnorm, rtol);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -262,6 +273,7 @@ __global__ void k_axpy(double* __restrict__ out, const double* __restrict__ in, 
 
 cudaError_t vec_axpy(double* out, const double* in, double a, int64_t N, cudaStream_t s) {
   k_axpy<<<152 * 4, 256, 0, s>>>(out, in, a, N);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ __global__ void k_tables(Tables* T, int n) {
 
 cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s) {
   k_tables<<<1, 32, 0, s>>>(c->p<Tables>(c->L.tables), c->n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -192,6 +193,7 @@ cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s) {
   k_struct_qr<<<1, 1024, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->p<double>(c->L.qr_work),
                                  c->p<double>(c->L.qr_tau), c->p<double>(c->L.zd),
                                  c->p<double>(c->L.rz), c->p<double>(c->L.qo));
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -270,6 +272,7 @@ cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s) {
       c->prob.nel[1], nz, c->prob.h, c->prob.dt, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
       c->dim == 3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.sx),
       c->p<double>(c->L.sy), c->dim == 3 ? c->p<double>(c->L.sz) : nullptr);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -318,6 +321,7 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
     k_traces<2><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, nullptr);
   else
     k_traces<3><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, nullptr);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -399,6 +403,7 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
         c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.h,
         c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx),
         c->p<double>(c->L.sy), x, tr, y, skip);
+    count_launch();
     return cudaGetLastError();
   }
   return cudaErrorNotSupported;

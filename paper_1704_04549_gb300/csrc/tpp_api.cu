@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <atomic>
 
 #include "tpp_internal.cuh"
 
@@ -14,6 +15,9 @@ namespace tpp {
 static thread_local std::string g_last_error = "no error";
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 tpp_status cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return TPP_OK;
@@ -200,6 +204,8 @@ using namespace tpp;
 extern "C" {
 
 const char* tpp_last_error(void) { return g_last_error.c_str(); }
+
+int64_t tpp_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 size_t tpp_workspace_bytes(const tpp_problem* prob, int32_t max_restart, uint32_t features) {
   if (validate(prob, max_restart)) return 0;

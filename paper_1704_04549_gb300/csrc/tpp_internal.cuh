@@ -97,6 +97,8 @@ struct tpp_ctx {
 namespace tpp {
 
 void set_error(const std::string& msg);
+// Number of kernels this library has launched (all threads, since load).
+void count_launch(int k = 1);
 tpp_status cuda_check(cudaError_t e, const char* what);
 
 // kernels launchers (defined in the .cu files)
