@@ -194,6 +194,22 @@ tpp_status dg_apply_sumfact(const tpp_ctx* ctx, const double* x, double* y, void
 tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres_opts* opts,
                        tpp_gmres_result* result, void* stream);
 
+/*
+ * dg_apply_sumfact_static: the same y = (M + dt A) x as dg_apply_sumfact, for
+ * callers that cannot allocate device memory themselves (their device memory is
+ * handed out by an allocator they do not control, or fixed once at start-up) and
+ * so cannot provide scratch beyond the vectors they pass.  The face-trace scratch
+ * lives in a static 4 MiB device array inside libtpp (held by every GPU that
+ * loads the library until exit) instead of the context workspace; no device
+ * memory is allocated.  The paper has no counterpart to this entry point.
+ * x, y: device float64 [num_dofs], must not alias.  2D contexts with
+ * num_elem * 4 * n <= 524288 only; larger ones return TPP_ERR_INVALID_ARG.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.  Asynchronous.
+ */
+tpp_status dg_apply_sumfact_static(const tpp_ctx* ctx, const double* x, double* y, void* stream);
+
 /* Device pointers into the workspace for inspection (tests); NULL if absent. */
 typedef struct {
   const double* sigma;   /* [E][2] top singular values of the rearranged block (2D) */

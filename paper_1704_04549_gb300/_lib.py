@@ -57,6 +57,7 @@ EXPORTS = {
     "tpp_apply_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "tpp_apply_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_apply_sumfact": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_apply_sumfact_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),

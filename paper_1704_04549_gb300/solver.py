@@ -120,6 +120,15 @@ class Context:
                 "dg_apply_sumfact")
         return y
 
+    def dg_apply_sumfact_static(self, x, y=None, stream=None):
+        """dg_apply_sumfact with its trace scratch in libtpp's static device array
+        (for callers that cannot allocate device scratch; overlapping calls race)."""
+        x = self._vec(x, "x")
+        y = torch.empty_like(x) if y is None else self._vec(y, "y")
+        L.check(self.lib.dg_apply_sumfact_static(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
+                "dg_apply_sumfact_static")
+        return y
+
     def gmres_solve(self, b, x=None, restart: int = 30, rtol: float = 1e-8,
                     max_iters: int = 3000, pc: int = L.TPP_PC_KRON, inner_prec: int = L.TPP_FP64,
                     flexible: bool = False, stream=None, check: bool = True):
