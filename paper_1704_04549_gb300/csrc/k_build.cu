@@ -203,40 +203,86 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
   return true;
 }
 
-// ---- tridiagonal helpers (single thread) ----------------------------------
-// Golub-Kahan tridiagonal: zero diagonal, off-diagonal e[0..m-2].
-__device__ int sturm_count(const double* e, int m, double x, double tiny) {
-  int cnt = 0;
-  double q = -x;
-  if (q < 0.0) ++cnt;
-  for (int i = 1; i < m; ++i) {
-    if (q == 0.0) q = -tiny;
-    q = -x - e[i - 1] * e[i - 1] / q;
-    if (q < 0.0) ++cnt;
+// ---- block / warp helpers --------------------------------------------------
+// Sum of squares of v[0..len) computed by warp 0 and broadcast through *slot.
+// FP64 warp instructions cost the full pipe width whatever their lane mask on
+// this GPU, so short reductions run on one warp instead of the whole block.
+__device__ double norm2_w0(const double* v, int len, double* slot) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < len; t += 32) s += v[t] * v[t];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *slot = s;
+  }
+  __syncthreads();
+  return *slot;
+}
+
+__device__ double sum_w0(const double* v, int len, double* slot) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < len; t += 32) s += v[t];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *slot = s;
+  }
+  __syncthreads();
+  return *slot;
+}
+
+// Reorthogonalise p (length r) against the first k vectors of B (vector-major,
+// B[i*r + t]) twice: one warp per coefficient, then one thread per entry.
+__device__ void reorth(double* p, const double* B, int k, int r, double* cf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    __syncthreads();
+    for (int i = wid; i < k; i += nw) {
+      double s = 0.0;
+      for (int t = lane; t < r; t += 32) s += B[i * r + t] * p[t];
+      s = warp_sum(s);
+      if (lane == 0) cf[i] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r; t += blockDim.x) {
+      double s = p[t];
+      for (int i = 0; i < k; ++i) s -= cf[i] * B[i * r + t];
+      p[t] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---- Golub-Kahan tridiagonal T (zero diagonal, off-diagonal e, size m) ------
+// Number of eigenvalues of T below x by the sign changes of the leading
+// principal minors of T - x I (Sturm sequence): D_0 = 1, D_1 = -x,
+// D_k = -x D_{k-1} - e_{k-2}^2 D_{k-2}.  e2 holds e^2 of the tridiagonal
+// scaled to spectral radius <= 1, so no division is needed; an occasional
+// rescale keeps D in range.
+__device__ int sturm_count_df(const double* e2, int m, double x) {
+  double d0 = 1.0, d1 = -x;
+  int cnt = (d1 < 0.0) ? 1 : 0;
+  bool neg_prev = d1 < 0.0;
+  for (int k = 2; k <= m; ++k) {
+    double d2 = fma(-x, d1, -e2[k - 2] * d0);
+    bool neg = d2 < 0.0;
+    if (d2 == 0.0) neg = !neg_prev;              // a zero minor counts as a sign change
+    cnt += (neg != neg_prev) ? 1 : 0;
+    neg_prev = neg;
+    d0 = d1;
+    d1 = d2;
+    if ((k & 31) == 0 && fabs(d1) < 1e-200 && fabs(d0) < 1e-200) {
+      d0 *= 1e200;
+      d1 *= 1e200;
+    }
   }
   return cnt;
 }
 
-// idx-th smallest eigenvalue (1-based) by bisection on [0, bound].
-__device__ double bisect_eig(const double* e, int m, int idx, double bound) {
-  double lo = 0.0, hi = bound * (1.0 + 1e-12) + 1e-300;
-  const double tiny = kEps * bound + 1e-300;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.0 * kEps * hi) break;
-    if (sturm_count(e, m, mid, tiny) >= idx) hi = mid;
-    else lo = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
-// Inverse iteration on T - lam I (T the GK tridiagonal) by Gaussian
-// elimination with partial pivoting; z in/out (length m).  Work arrays:
-// d, du, du2, dl (m each), piv (m).
+// Inverse iteration on T - lam I (Gaussian elimination with partial pivoting,
+// pivots inverted once); z in/out, work arrays of length m each.
 __device__ void inverse_iteration(const double* e, int m, double lam, double* z, double* d,
-                                  double* du, double* du2, double* dl, int* piv,
-                                  const double* other, double tiny) {
+                                  double* du, double* du2, double* dl, int* piv, double tiny) {
   for (int i = 0; i < m; ++i) {
     d[i] = -lam;
     du[i] = (i + 1 < m) ? e[i] : 0.0;
@@ -265,6 +311,7 @@ __device__ void inverse_iteration(const double* e, int m, double lam, double* z,
     }
   }
   if (d[m - 1] == 0.0) d[m - 1] = tiny;
+  for (int i = 0; i < m; ++i) d[i] = 1.0 / d[i];     // reciprocal pivots
   for (int it = 0; it < 3; ++it) {
     for (int i = 0; i + 1 < m; ++i) {     // L solve
       if (piv[i]) {
@@ -278,39 +325,13 @@ __device__ void inverse_iteration(const double* e, int m, double lam, double* z,
       double s = z[i];
       if (i + 1 < m) s -= du[i] * z[i + 1];
       if (i + 2 < m) s -= du2[i] * z[i + 2];
-      z[i] = s / d[i];
-    }
-    if (other) {
-      double dt = 0.0;
-      for (int i = 0; i < m; ++i) dt += other[i] * z[i];
-      for (int i = 0; i < m; ++i) z[i] -= dt * other[i];
+      z[i] = s * d[i];
     }
     double nr = 0.0;
     for (int i = 0; i < m; ++i) nr += z[i] * z[i];
     nr = 1.0 / sqrt(nr);
     for (int i = 0; i < m; ++i) z[i] *= nr;
   }
-}
-
-// Block: reorthogonalise p (length r) against the first k columns of B
-// (vector-major, B[i*r + t]) twice.  cf: scratch length >= k.
-__device__ void reorth(double* p, const double* B, int k, int r, double* cf) {
-  const int tid = threadIdx.x;
-  for (int pass = 0; pass < 2; ++pass) {
-    __syncthreads();
-    for (int i = tid; i < k; i += blockDim.x) {
-      double s = 0.0;
-      for (int t = 0; t < r; ++t) s += B[i * r + t] * p[t];
-      cf[i] = s;
-    }
-    __syncthreads();
-    for (int t = tid; t < r; t += blockDim.x) {
-      double s = p[t];
-      for (int i = 0; i < k; ++i) s -= cf[i] * B[i * r + t];
-      p[t] = s;
-    }
-  }
-  __syncthreads();
 }
 
 // Gauss-Jordan inverses of two n x n matrices at once (partial pivoting).
@@ -320,17 +341,25 @@ __device__ void gauss_jordan2(double* aug0, double* aug1, int n, int* pivrow, do
                               int* sing) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = 0; k < n; ++k) {
-    if (tid == 0 || tid == 32) {
-      const int mIdx = tid >> 5;
-      double* a = mIdx ? aug1 : aug0;
+    if (tid < 64) {                 // warp 0: matrix 0, warp 1: matrix 1 (lanes over rows)
+      const int mIdx = tid >> 5, lane = tid & 31;
+      const double* a = mIdx ? aug1 : aug0;
+      double best = -1.0;
       int p = k;
-      double best = fabs(a[k + n * k]);
-      for (int i = k + 1; i < n; ++i) {
+      for (int i = k + lane; i < n; i += 32) {
         const double v = fabs(a[i + n * k]);
         if (v > best) { best = v; p = i; }
       }
-      pivrow[mIdx] = p;
-      if (best == 0.0) sing[mIdx] = 1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (lane == 0) {
+        pivrow[mIdx] = p;
+        if (best == 0.0) sing[mIdx] = 1;
+      }
     }
     __syncthreads();
     for (int q = tid; q < 2 * 2 * n; q += nt) {     // row swap
@@ -371,13 +400,17 @@ __device__ void gauss_jordan2(double* aug0, double* aug1, int n, int* pivrow, do
   }
 }
 
-__device__ double norm1(const double* A, int n) {   // single thread
+// 1-norm (max column sum) of an n x n column-major matrix by one warp.
+__device__ double norm1_warp(const double* A, int n) {
+  const int lane = threadIdx.x & 31;
   double best = 0.0;
-  for (int c = 0; c < n; ++c) {
-    double s = 0.0;
-    for (int r = 0; r < n; ++r) s += fabs(A[r + n * c]);
-    best = fmax(best, s);
+  for (int c = lane; c < n; c += 32) {
+    double sv = 0.0;
+    for (int r = 0; r < n; ++r) sv += fabs(A[r + n * c]);
+    best = fmax(best, sv);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
   return best;
 }
 
@@ -409,7 +442,7 @@ __host__ __device__ inline BuildSmem build_smem_layout(int n, int rz) {
   const size_t need2 = (size_t)8 * nn + (size_t)4 * n * ld + 2 * n + 2 + 64;
   if (need2 > big) big = need2;
   L.vec = L.big + big;
-  const size_t nvec = (size_t)14 * r + 1 + 16 + (size_t)16 * r;
+  const size_t nvec = (size_t)16 * r + 1 + 16 + (size_t)16 * r;
   L.ints = L.vec + nvec;
   L.total_bytes = L.ints * sizeof(double) + (size_t)(4 * r + 8) * sizeof(int);
   return L;
@@ -446,7 +479,8 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
   double* ee = be + r + 1;             // 2r
   double* z1 = ee + 2 * r;             // 2r
   double* z2 = z1 + 2 * r;             // 2r
-  double* mu1 = z2 + 2 * r;            // r  (Ritz vectors in M space)
+  double* e2s = z2 + 2 * r;            // 2r (squared scaled off-diagonal)
+  double* mu1 = e2s + 2 * r;           // r  (Ritz vectors in M space)
   double* mv1 = mu1 + r;
   double* mu2 = mv1 + r;
   double* mv2 = mu2 + r;
@@ -498,127 +532,166 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
   const double tol = 1e-12 * fro;
 
   // ---- 3. Golub-Kahan-Lanczos with full reorthogonalisation (Alg. lanczos)
+  // Run J0 = min(r, 24) steps, take the top-2 Ritz triplets of the bidiagonal
+  // and accept them when both residuals beta_J |u'_J| are below 1e-14 sigma_1;
+  // otherwise continue to the full size r (a complete orthogonal reduction).
   {
-    double part = 0.0;
-    for (int t = tid; t < r; t += nt) {
-      const double v = splitmix_unit(1, t);
-      V[t] = v;
-      part += v * v;
-    }
-    const double nv = sqrt(block_sum(part, red));
+    for (int t = tid; t < r; t += nt) V[t] = splitmix_unit(1, t);
+    const double nv = sqrt(norm2_w0(V, r, &scal[3]));
     for (int t = tid; t < r; t += nt) V[t] /= nv;
     if (tid == 0) be[0] = 0.0;
     __syncthreads();
   }
-  for (int j = 0; j < r; ++j) {
-    // p = M v_j - beta_j u_{j-1}
-    for (int t = tid; t < r; t += nt) {
-      double s = 0.0;
-      for (int q = 0; q < r; ++q) s += Mm[t * r + q] * V[j * r + q];
-      if (j > 0) s -= be[j] * U[(j - 1) * r + t];
-      pv[t] = s;
-    }
-    reorth(pv, U, j, r, cf);
-    double part = 0.0;
-    for (int t = tid; t < r; t += nt) part += pv[t] * pv[t];
-    double a = sqrt(block_sum(part, red));
-    if (a <= tol) {       // invariant subspace: continue with a fresh direction
-      for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(1000 + j, t);
-      reorth(pv, U, j, r, cf);
-      part = 0.0;
-      for (int t = tid; t < r; t += nt) part += pv[t] * pv[t];
-      const double nrm = sqrt(block_sum(part, red));
-      for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] / nrm;
-      a = 0.0;
-    } else {
-      for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] / a;
-    }
-    if (tid == 0) al[j] = a;
-    __syncthreads();
-    if (j + 1 < r) {
-      // q = M^T u_j - alpha_j v_j
+  int J = (r < 24) ? r : 24;
+  int jdone = 0;
+  const int lane = tid & 31;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = jdone; j < J; ++j) {
+      // p = M v_j - beta_j u_{j-1}
       for (int t = tid; t < r; t += nt) {
-        double s = 0.0;
-        for (int q = 0; q < r; ++q) s += Mm[q * r + t] * U[j * r + q];
-        pv[t] = s - a * V[j * r + t];
+        double sacc = 0.0;
+        for (int q = 0; q < r; ++q) sacc += Mm[t * r + q] * V[j * r + q];
+        if (j > 0) sacc -= be[j] * U[(j - 1) * r + t];
+        pv[t] = sacc;
       }
-      reorth(pv, V, j + 1, r, cf);
-      part = 0.0;
-      for (int t = tid; t < r; t += nt) part += pv[t] * pv[t];
-      double b = sqrt(block_sum(part, red));
-      if (b <= tol) {
-        for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(2000 + j, t);
-        reorth(pv, V, j + 1, r, cf);
-        part = 0.0;
-        for (int t = tid; t < r; t += nt) part += pv[t] * pv[t];
-        const double nrm = sqrt(block_sum(part, red));
-        for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] / nrm;
-        b = 0.0;
+      reorth(pv, U, j, r, cf);
+      double a = sqrt(norm2_w0(pv, r, &scal[3]));
+      if (a <= tol) {       // invariant subspace: continue with a fresh direction
+        for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(1000 + j, t);
+        reorth(pv, U, j, r, cf);
+        const double nrm = sqrt(norm2_w0(pv, r, &scal[3]));
+        for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] / nrm;
+        a = 0.0;
       } else {
-        for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] / b;
+        const double ia = 1.0 / a;
+        for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] * ia;
       }
-      if (tid == 0) be[j + 1] = b;
+      if (tid == 0) al[j] = a;
       __syncthreads();
+      if (j + 1 < r) {
+        // q = M^T u_j - alpha_j v_j
+        for (int t = tid; t < r; t += nt) {
+          double sacc = 0.0;
+          for (int q = 0; q < r; ++q) sacc += Mm[q * r + t] * U[j * r + q];
+          pv[t] = sacc - a * V[j * r + t];
+        }
+        reorth(pv, V, j + 1, r, cf);
+        double b = sqrt(norm2_w0(pv, r, &scal[3]));
+        if (b <= tol) {
+          for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(2000 + j, t);
+          reorth(pv, V, j + 1, r, cf);
+          const double nrm = sqrt(norm2_w0(pv, r, &scal[3]));
+          for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] / nrm;
+          b = 0.0;
+        } else {
+          const double ib = 1.0 / b;
+          for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] * ib;
+        }
+        if (tid == 0) be[j + 1] = b;
+        __syncthreads();
+      }
     }
-  }
+    jdone = J;
 
-  // ---- 4. top-2 singular values / vectors of the bidiagonal matrix
-  const int m = 2 * r;
-  for (int t = tid; t < m - 1; t += nt) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
-  __syncthreads();
-  if (tid < 2) {
-    double bound = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double s = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < m - 1 ? fabs(ee[i]) : 0.0);
-      bound = fmax(bound, s);
-    }
-    scal[4] = bound;
-    scal[tid] = (m - tid > 0 && (tid < r)) ? bisect_eig(ee, m, m - tid, bound) : 0.0;
-  }
-  __syncthreads();
-  const int nsv = (r >= 2) ? 2 : 1;
-  for (int k = 0; k < nsv; ++k) {
-    if (tid == 0) {
-      double* z = k ? z2 : z1;
-      for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + k, i);
-      double* w0 = tw + k * 4 * m;
-      inverse_iteration(ee, m, scal[k], z, w0, w0 + m, w0 + 2 * m, w0 + 3 * m, piv + k * m,
-                        k ? z1 : nullptr, kEps * scal[4] + 1e-300);
+    // ---- 4. top-2 singular values / vectors of the J x J bidiagonal matrix
+    const int m = 2 * J;
+    for (int t = tid; t < m - 1; t += nt) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
+    __syncthreads();
+    if (tid < 32) {
+      // Gershgorin bound of the spectrum, then e^2 of the scaled matrix
+      double bnd = 0.0;
+      for (int i = lane; i < m; i += 32) {
+        const double sv = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < m - 1 ? fabs(ee[i]) : 0.0);
+        bnd = fmax(bnd, sv);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+      if (bnd == 0.0) bnd = 1.0;
+      const double ib = 1.0 / bnd;
+      for (int i = lane; i < m - 1; i += 32) {
+        const double es = ee[i] * ib;
+        e2s[i] = es * es;
+      }
+      __syncwarp();
+      // multisection: lanes 0-15 bracket the largest eigenvalue, 16-31 the second
+      const int grp = lane >> 4, gl = lane & 15;
+      const int idx = m - grp;
+      double lo = 0.0, hi = 1.0 + 1e-12;
+      for (int it = 0; it < 14; ++it) {
+        const double x = lo + (hi - lo) * (double)(gl + 1) * (1.0 / 17.0);
+        const int cnt = sturm_count_df(e2s, m, x);
+        const unsigned ge = __ballot_sync(0xffffffffu, cnt >= idx);
+        const unsigned mine = (ge >> (grp * 16)) & 0xffffu;
+        const int f = mine ? (__ffs(mine) - 1) : 16;
+        const double w = hi - lo;
+        const double nlo = (f == 0) ? lo : lo + w * (double)f * (1.0 / 17.0);
+        const double nhi = (f == 16) ? hi : lo + w * (double)(f + 1) * (1.0 / 17.0);
+        lo = nlo;
+        hi = nhi;
+      }
+      if (gl == 0) scal[grp] = (grp < J) ? 0.5 * (lo + hi) * bnd : 0.0;
+      if (lane == 0) scal[4] = bnd;
+      __syncwarp();
+      // inverse iteration for both vectors in lockstep lanes 0 and 1
+      if (lane < 2 && lane < J) {
+        double* z = lane ? z2 : z1;
+        for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + lane, i);
+        double* w0 = tw + lane * 4 * m;
+        inverse_iteration(ee, m, scal[lane], z, w0, w0 + m, w0 + 2 * m, w0 + 3 * m, piv + lane * m,
+                          kEps * bnd + 1e-300);
+      }
+      __syncwarp();
+      if (lane == 0 && J >= 2) {          // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
+        double dt = 0.0;
+        for (int i = 0; i < m; ++i) dt += z1[i] * z2[i];
+        double nr = 0.0;
+        for (int i = 0; i < m; ++i) {
+          z2[i] -= dt * z1[i];
+          nr += z2[i] * z2[i];
+        }
+        nr = 1.0 / sqrt(nr);
+        for (int i = 0; i < m; ++i) z2[i] *= nr;
+      }
+      if (lane == 0) {
+        // residual of the Ritz triplets: beta_J |u'_{J-1}| with ||u'|| = 1/sqrt(2)
+        const double bJ = (J < r) ? be[J] : 0.0;
+        const double r1 = bJ * fabs(z1[m - 1]) * 1.4142135623730951;
+        const double r2 = (J >= 2) ? bJ * fabs(z2[m - 1]) * 1.4142135623730951 : 0.0;
+        scal[2] = (r1 <= 1e-14 * scal[0] && r2 <= 1e-14 * scal[0]) ? 1.0 : 0.0;
+      }
     }
     __syncthreads();
+    if (scal[2] != 0.0 || J == r) break;
+    J = r;
   }
+  const int nsv = (J >= 2) ? 2 : 1;
   // Ritz vectors: M v = sigma u with v = V v', u = U u'
   for (int k = 0; k < nsv; ++k) {
     const double* z = k ? z2 : z1;
     double* mu = k ? mu2 : mu1;
     double* mv = k ? mv2 : mv1;
-    double pu = 0.0, pvv = 0.0;
-    for (int s = tid; s < r; s += nt) {
+    for (int sidx = tid; sidx < r; sidx += nt) {
       double a = 0.0, b = 0.0;
-      for (int t = 0; t < r; ++t) {
-        a += z[2 * t + 1] * U[t * r + s];
-        b += z[2 * t] * V[t * r + s];
+      for (int t = 0; t < J; ++t) {
+        a += z[2 * t + 1] * U[t * r + sidx];
+        b += z[2 * t] * V[t * r + sidx];
       }
-      mu[s] = a;
-      mv[s] = b;
-      pu += a * a;
-      pvv += b * b;
+      mu[sidx] = a;
+      mv[sidx] = b;
     }
-    pu = block_sum(pu, red);
-    pvv = block_sum(pvv, red);
-    double tr = 0.0;
-    for (int s = tid; s < n; s += nt) tr += mu[s];
-    tr = block_sum(tr, red);
+    const double pu = norm2_w0(mu, r, &scal[5]);
+    const double pvv = norm2_w0(mv, r, &scal[6]);
+    const double tr = sum_w0(mu, n, &scal[7]);
     const double sgn = (tr < 0.0) ? -1.0 : 1.0;     // gauge: trace(A_k) >= 0
     const double fu = sgn / sqrt(pu), fv = sgn / sqrt(pvv);
-    for (int s = tid; s < r; s += nt) {
-      mu[s] *= fu;
-      mv[s] *= fv;
+    for (int sidx = tid; sidx < r; sidx += nt) {
+      mu[sidx] *= fu;
+      mv[sidx] *= fv;
     }
     __syncthreads();
   }
   if (nsv == 1) {
-    for (int s = tid; s < r; s += nt) { mu2[s] = 0.0; mv2[s] = 0.0; }
+    for (int sidx = tid; sidx < r; sidx += nt) { mu2[sidx] = 0.0; mv2[sidx] = 0.0; }
     if (tid == 0) scal[1] = 0.0;
     __syncthreads();
   }
@@ -717,21 +790,19 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
     }
     if (tid < 2) ish[2 + tid] = 0;
     __syncthreads();
-    if (tid == 0) {     // 1-norms of the matrices before elimination
-      double na = 0.0, nb = 0.0;
-      for (int c = 0; c < n; ++c) {
-        double sa = 0.0, sb = 0.0;
-        for (int rr = 0; rr < n; ++rr) { sa += fabs(aug0[rr + n * c]); sb += fabs(aug1[rr + n * c]); }
-        na = fmax(na, sa);
-        nb = fmax(nb, sb);
-      }
-      scal[6] = na;
-      scal[7] = nb;
+    if (tid < 64) {     // 1-norms of the matrices before elimination (warp 0: A, warp 1: B)
+      const double nv = norm1_warp((tid >> 5) ? aug1 : aug0, n);
+      if ((tid & 31) == 0) scal[6 + (tid >> 5)] = nv;
     }
     __syncthreads();
     gauss_jordan2(aug0, aug1, n, ish, facv, ish + 2);
+    if (tid < 64) {
+      const double ni = norm1_warp((tid >> 5) ? aug1 + nn : aug0 + nn, n);
+      if ((tid & 31) == 0) facv[2 * n + (tid >> 5)] = ni;   // scratch after elimination
+    }
+    __syncthreads();
     if (tid == 0) {
-      double cp = scal[6] * norm1(aug0 + nn, n) * scal[7] * norm1(aug1 + nn, n);
+      double cp = scal[6] * facv[2 * n] * scal[7] * facv[2 * n + 1];
       if (ish[2] || ish[3] || !(cp < 1e300)) cp = INFINITY;
       scal[5] = cp;
     }

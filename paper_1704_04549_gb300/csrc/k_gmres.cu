@@ -28,40 +28,111 @@ __device__ void dot_block(const double* __restrict__ V, int64_t N, int nvec,
       for (int i = 0; i < 16; ++i)
         if (i < gcount) acc[i] += V[(size_t)(g0 + i) * N + t] * wv;
     }
-    for (int i = 0; i < gcount; ++i) {
-      const double s = block_sum(acc[i], red);
-      if (threadIdx.x == 0) partials[blockIdx.x * stride + g0 + i] = s;
+    // per-warp partial sums, then one warp per value folds the 8 warp sums
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < gcount) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) red[i * 8 + wid] = v;
+      }
     }
+    __syncthreads();
+    if (threadIdx.x < gcount) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x * 8 + k];
+      partials[blockIdx.x * stride + g0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
+// Last block of a grid: sum partials[b * stride + i] over all b (fixed order:
+// lane-strided per warp, then a warp tree) into out[i] for i < nvec.
+__device__ bool last_block(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return is_last;
+}
+
+__device__ void final_reduce(const double* partials, int nblk, int stride, int nvec,
+                             double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < nvec; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += __ldcg(partials + (size_t)b * stride + i);
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+struct ArnoldiArgs {
+  GmresState* st;
+  double *H, *cs, *sn, *g, *h1, *h2, *inv_beta;
+  int j;
+};
+
+// Close Arnoldi column j (single thread): H[0..j, j] = h1 + h2,
+// H[j+1, j] = ||w||, previous Givens rotations, new rotation, g, flags.
+// H is column-major (m+1) x m.
+__device__ void finish_column(const ArnoldiArgs& a, double nrm2) {
+  GmresState* st = a.st;
+  const int m = st->m, j = a.j;
+  const double hj1 = sqrt(nrm2);
+  double* col = a.H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = a.h1[i] + a.h2[i];
+  col[j + 1] = hj1;
+  for (int i = 0; i < j; ++i) {
+    const double t = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
+    col[i + 1] = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rho = hypot(col[j], col[j + 1]);
+  double c = 1.0, s = 0.0;
+  if (rho > 0.0) { c = col[j] / rho; s = col[j + 1] / rho; }
+  a.cs[j] = c;
+  a.sn[j] = s;
+  col[j] = rho;
+  col[j + 1] = 0.0;
+  a.g[j + 1] = -s * a.g[j];
+  a.g[j] = c * a.g[j];
+  st->k = j + 1;
+  st->est = fabs(a.g[j + 1]) / st->bnorm;
+  *a.inv_beta = (hj1 > 0.0) ? 1.0 / hj1 : 0.0;
+  if (!(hj1 > 0.0)) st->breakdown = 1;
+  if (!(st->est == st->est)) st->breakdown = 2;
+  if (st->est <= st->rtol || j + 1 >= m || st->breakdown) st->done = 1;
+}
+
+// pass 1 of CGS2: h1 = V^T w
 __global__ void __launch_bounds__(kRedThreads)
 k_dots(const double* V, int64_t N, int nvec, const double* w, double* partials, int stride,
-       const int32_t* skip) {
+       const int32_t* skip, double* h_out, unsigned int* ticket) {
   if (skip && *skip) return;
-  __shared__ double red[kRedThreads / 32];
+  __shared__ double red[16 * (kRedThreads / 32)];
   dot_block(V, N, nvec, w, partials, stride, red);
-}
-
-// h[i] = sum_b partials[b][i] (one block); optional accumulate into hacc
-__global__ void k_reduce(const double* partials, int nblk, int stride, int nvec, double* h,
-                         const int32_t* skip) {
-  if (skip && *skip) return;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partials[b * stride + i];
-    h[i] = s;
+  if (last_block(ticket)) {
+    final_reduce(partials, gridDim.x, stride, nvec, h_out);
+    if (threadIdx.x == 0) *ticket = 0;
   }
 }
 
-// w -= sum_i h[i] V_i, then partials of V_i . w (mode 0) or of w . w (mode 1)
+// w -= V h_in; mode 0: h_out = V^T w (pass 2 of CGS2);
+// mode 1: ||w||^2 and the Givens update of column a.j
 __global__ void __launch_bounds__(kRedThreads)
-k_update(const double* __restrict__ V, int64_t N, int nvec, const double* __restrict__ h,
-         double* __restrict__ w, double* partials, int stride, int mode, const int32_t* skip) {
+k_update(const double* __restrict__ V, int64_t N, int nvec, const double* __restrict__ h_in,
+         double* __restrict__ w, double* partials, int stride, int mode, const int32_t* skip,
+         double* h_out, unsigned int* ticket, ArnoldiArgs aa) {
   if (skip && *skip) return;
   __shared__ double hs[kMaxBasis];
-  __shared__ double red[kRedThreads / 32];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h[i];
+  __shared__ double red[16 * (kRedThreads / 32)];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h_in[i];
   __syncthreads();
   double nrm = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
@@ -74,46 +145,23 @@ k_update(const double* __restrict__ V, int64_t N, int nvec, const double* __rest
   if (mode == 0) {
     __syncthreads();
     dot_block(V, N, nvec, w, partials, stride, red);
+    if (last_block(ticket)) {
+      final_reduce(partials, gridDim.x, stride, nvec, h_out);
+      if (threadIdx.x == 0) *ticket = 0;
+    }
   } else {
     const double s = block_sum(nrm, red);
     if (threadIdx.x == 0) partials[blockIdx.x * stride] = s;
+    if (last_block(ticket)) {
+      __shared__ double tot;
+      final_reduce(partials, gridDim.x, stride, 1, &tot);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        finish_column(aa, tot);
+        *ticket = 0;
+      }
+    }
   }
-}
-
-// Close Arnoldi column j: H[0..j, j] = h1 + h2, H[j+1, j] = ||w||, apply the
-// previous Givens rotations, form the new one, update g and the convergence
-// flag.  Single thread.  Layout: H column-major (m+1) x m.
-__global__ void k_finish_column(GmresState* st, double* H, double* cs, double* sn, double* g,
-                                const double* h1, const double* h2, const double* partials,
-                                int nblk, int stride, int j, double* inv_beta) {
-  if (threadIdx.x != 0 || st->done) return;
-  const int m = st->m;
-  double nrm2 = 0.0;
-  for (int b = 0; b < nblk; ++b) nrm2 += partials[b * stride];
-  const double hj1 = sqrt(nrm2);
-  double* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  col[j + 1] = hj1;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double rho = hypot(col[j], col[j + 1]);
-  double c = 1.0, s = 0.0;
-  if (rho > 0.0) { c = col[j] / rho; s = col[j + 1] / rho; }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = rho;
-  col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  st->k = j + 1;
-  st->est = fabs(g[j + 1]) / st->bnorm;
-  *inv_beta = (hj1 > 0.0) ? 1.0 / hj1 : 0.0;
-  if (!(hj1 > 0.0)) st->breakdown = 1;
-  if (!(st->est == st->est)) st->breakdown = 2;
-  if (st->est <= st->rtol || j + 1 >= m || st->breakdown) st->done = 1;
 }
 
 // y = R^-1 g for the k x k upper-triangular part of the rotated H.  Single thread.
@@ -197,28 +245,20 @@ __global__ void k_cycle_init(GmresState* st, double* g, double beta, int m, doub
 // ---------------------------------------------------------------------------
 // launch helpers used by the host solver
 cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
-                       int stride, int nblk, const int32_t* skip, cudaStream_t s) {
-  k_dots<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip);
-  count_launch();
-  return cudaGetLastError();
-}
-cudaError_t gmres_reduce(const double* partials, int nblk, int stride, int nvec, double* h,
-                         const int32_t* skip, cudaStream_t s) {
-  k_reduce<<<1, 64, 0, s>>>(partials, nblk, stride, nvec, h, skip);
+                       int stride, int nblk, const int32_t* skip, double* h_out,
+                       unsigned int* ticket, cudaStream_t s) {
+  k_dots<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
   count_launch();
   return cudaGetLastError();
 }
 cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
                          double* partials, int stride, int mode, int nblk, const int32_t* skip,
-                         cudaStream_t s) {
-  k_update<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip);
-  count_launch();
-  return cudaGetLastError();
-}
-cudaError_t gmres_finish(GmresState* st, double* H, double* cs, double* sn, double* g,
-                         const double* h1, const double* h2, const double* partials, int nblk,
-                         int stride, int j, double* inv_beta, cudaStream_t s) {
-  k_finish_column<<<1, 32, 0, s>>>(st, H, cs, sn, g, h1, h2, partials, nblk, stride, j, inv_beta);
+                         double* h_out, unsigned int* ticket, GmresState* st, double* H,
+                         double* cs, double* sn, double* g, double* h1, double* h2,
+                         double* inv_beta, int j, cudaStream_t s) {
+  ArnoldiArgs aa{st, H, cs, sn, g, h1, h2, inv_beta, j};
+  k_update<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip, h_out,
+                                        ticket, aa);
   count_launch();
   return cudaGetLastError();
 }

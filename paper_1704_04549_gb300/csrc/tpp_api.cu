@@ -27,15 +27,13 @@ tpp_status cuda_check(cudaError_t e, const char* what) {
 
 // GMRES kernels (k_gmres.cu)
 cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
-                       int stride, int nblk, const int32_t* skip, cudaStream_t s);
-cudaError_t gmres_reduce(const double* partials, int nblk, int stride, int nvec, double* h,
-                         const int32_t* skip, cudaStream_t s);
+                       int stride, int nblk, const int32_t* skip, double* h_out,
+                       unsigned int* ticket, cudaStream_t s);
 cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
                          double* partials, int stride, int mode, int nblk, const int32_t* skip,
-                         cudaStream_t s);
-cudaError_t gmres_finish(GmresState* st, double* H, double* cs, double* sn, double* g,
-                         const double* h1, const double* h2, const double* partials, int nblk,
-                         int stride, int j, double* inv_beta, cudaStream_t s);
+                         double* h_out, unsigned int* ticket, GmresState* st, double* H,
+                         double* cs, double* sn, double* g, double* h1, double* h2,
+                         double* inv_beta, int j, cudaStream_t s);
 cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, double* y,
                       cudaStream_t s);
 cudaError_t gmres_combine(const double* B, int64_t N, const GmresState* st, const double* y,
@@ -282,6 +280,7 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.status, &st0, sizeof(st0),
                                          cudaMemcpyHostToDevice, s), "init status")) != TPP_OK) break;
     if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.tables, 0, sizeof(Tables), s), "memset")) != TPP_OK) break;
+    if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.gstate, 0, sizeof(GmresState), s), "memset")) != TPP_OK) break;
     if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
     if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
     if ((rc = cuda_check(launch_precompute(c, s), "k_precompute")) != TPP_OK) break;
@@ -526,13 +525,14 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
       TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, vj, z, done, s), "precond");
       TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s), "traces");
       TPP_TRY_CUDA(launch_dg_apply(c, z, c->p<double>(c->L.traces), w, done, s), "operator");
-      TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, s), "dots");
-      TPP_TRY_CUDA(gmres_reduce(partials, nblk, stride, j + 1, h1, done, s), "reduce");
-      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h1, w, partials, stride, 0, nblk, done, s), "update");
-      TPP_TRY_CUDA(gmres_reduce(partials, nblk, stride, j + 1, h2, done, s), "reduce");
-      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, done, s), "norm");
-      TPP_TRY_CUDA(gmres_finish(st, H, cs, sn, g, h1, h2, partials, nblk, stride, j, invb, s),
-                   "givens");
+      TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, h1,
+                              &st->tickets[0], s), "dots");
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h1, w, partials, stride, 0, nblk, done, h2,
+                                &st->tickets[1], st, H, cs, sn, g, h1, h2, invb, j, s),
+                   "update");
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, done, nullptr,
+                                &st->tickets[2], st, H, cs, sn, g, h1, h2, invb, j, s),
+                   "norm+givens");
       TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, nullptr, s), "scale");
       ++total;
       TPP_TRY_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s), "read state");

@@ -57,6 +57,7 @@ struct GmresState {
   double rtol;
   int32_t m;          // restart length
   int32_t pad2;
+  unsigned int tickets[4];   // last-block-done counters of the reduction kernels
 };
 
 struct Layout {
