@@ -15,7 +15,6 @@ namespace tpp {
 
 namespace {
 
-constexpr int kApplyThreads = 256;
 
 // Solve T2_II Y + Y T1_JJ^T = R for one ni x nj diagonal block pair
 // (ni, nj in {1, 2}); a = T2_II (a[r + 2 c]), bt = T1_JJ, y in: R, out: Y
@@ -83,194 +82,254 @@ __device__ __forceinline__ void small_sylvester(int ni, int nj, const T a[4], co
   }
 }
 
-// Quasi-triangular Sylvester solve T2 Y + Y T1^T = C in shared memory
-// (column-major, ld n; C is overwritten by Y), right-looking over the
-// anti-diagonals of the 1x1 / 2x2 diagonal-block grid: block (I, J) sits on
-// anti-diagonal (nbr - 1 - I) + (nbc - 1 - J).  At step s every block of that
-// anti-diagonal is final, so (A) one thread per block solves its small
-// system, then (B) every still-unsolved entry subtracts the contributions of
-// the blocks solved at this step in its column (T2[i, k] Y[k, j]) and in its
-// row (Y[i, l] T1[j, l]).  Each step has constant depth and phase B keeps all
-// threads busy.  rowblk / colblk map a row / column to its block; rdiag holds
-// 1 / (T2_ii + T1_jj) for the 1x1 solves.
-template <typename T>
-__device__ void sylvester_block(const T* T2, const T* T1, T* Y, int n, const int* rs,
-                                const int* cs, int nbr, int nbc, const int* rowblk,
-                                const int* colblk, const T* rdiag) {
-  const int tid = threadIdx.x, nt = blockDim.x, nn = n * n;
-  for (int s = 0; s < nbr + nbc - 1; ++s) {
-    for (int a = tid; a < nbr; a += nt) {                    // (A) solve this anti-diagonal
-      const int b = s - a;
-      if (b < 0 || b >= nbc) continue;
-      const int I = nbr - 1 - a, J = nbc - 1 - b;
-      const int i0 = rs[I], ni = rs[I + 1] - i0, j0 = cs[J], nj = cs[J + 1] - j0;
-      if (ni == 1 && nj == 1) {
-        Y[i0 + n * j0] *= rdiag[i0 + n * j0];
-      } else {
-        T ab[4] = {(T)0, (T)0, (T)0, (T)0}, bb[4] = {(T)0, (T)0, (T)0, (T)0};
-        T rhs[4] = {(T)0, (T)0, (T)0, (T)0};
-        ab[0] = T2[i0 + n * i0];
-        bb[0] = T1[j0 + n * j0];
-        rhs[0] = Y[i0 + n * j0];
-        if (ni == 2) {
-          ab[1] = T2[(i0 + 1) + n * i0];
-          ab[2] = T2[i0 + n * (i0 + 1)];
-          ab[3] = T2[(i0 + 1) + n * (i0 + 1)];
-          rhs[1] = Y[(i0 + 1) + n * j0];
-        }
-        if (nj == 2) {
-          bb[1] = T1[(j0 + 1) + n * j0];
-          bb[2] = T1[j0 + n * (j0 + 1)];
-          bb[3] = T1[(j0 + 1) + n * (j0 + 1)];
-          rhs[ni] = Y[i0 + n * (j0 + 1)];
-        }
-        if (ni == 2 && nj == 2) rhs[3] = Y[(i0 + 1) + n * (j0 + 1)];
-        small_sylvester<T>(ni, nj, ab, bb, rhs);
-        Y[i0 + n * j0] = rhs[0];
-        if (ni == 2) Y[(i0 + 1) + n * j0] = rhs[1];
-        if (nj == 2) Y[i0 + n * (j0 + 1)] = rhs[ni];
-        if (ni == 2 && nj == 2) Y[(i0 + 1) + n * (j0 + 1)] = rhs[3];
-      }
-    }
-    __syncthreads();
-    if (s + 1 < nbr + nbc - 1) {                               // (B) rank updates
-      for (int q = tid; q < nn; q += nt) {
-        const int i = q % n, j = q / n;
-        const int I = rowblk[i], J = colblk[j];
-        if ((nbr - 1 - I) + (nbc - 1 - J) <= s) continue;      // solved already
-        T v = (T)0;
-        const int a = s - (nbc - 1 - J);                        // block solved in column J
-        if (a >= 0 && a < nbr) {
-          const int Is = nbr - 1 - a;
-          for (int k = rs[Is]; k < rs[Is + 1]; ++k) v += T2[i + n * k] * Y[k + n * j];
-        }
-        const int b = s - (nbr - 1 - I);                        // block solved in row I
-        if (b >= 0 && b < nbc) {
-          const int Js = nbc - 1 - b;
-          for (int l = cs[Js]; l < cs[Js + 1]; ++l) v += Y[i + n * l] * T1[j + n * l];
-        }
-        Y[q] -= v;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ int blocks_from_mask(uint32_t mask, int n, int* starts, int* blk) {
-  int nb = 0, i = 0;
-  while (i < n) {
-    starts[nb] = i;
-    const int w = ((mask >> i) & 1u) && (i + 1 < n) ? 2 : 1;
-    for (int t = 0; t < w; ++t) blk[i + t] = nb;
-    ++nb;
-    i += w;
-  }
-  starts[nb] = n;
-  return nb;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kApplyThreads)
-k_apply_2d(int n, const T* __restrict__ SA, const T* __restrict__ SB, const T* __restrict__ Q1,
-           const T* __restrict__ Q2, const T* __restrict__ T1, const T* __restrict__ T2,
-           const uint32_t* __restrict__ masks, const double* __restrict__ b,
-           double* __restrict__ x, const int32_t* skip) {
+// One element per group of NM lanes (NM = 8, 16 or 32 >= n; 32 / NM elements
+// per warp), lane i owning row i.  Products A B^T / A B keep the row of the
+// left operand in registers and read the other operand from shared memory as
+// a broadcast; the Sylvester system is solved right-looking over the
+// anti-diagonals of the 1x1 / 2x2 block grid: at step s each row block solves
+// its block on anti-diagonal s, then every lane updates the unsolved entries
+// of its row with the contributions of the blocks solved at step s in their
+// columns (T2[i, k] Y[k, j]) and in its own row (Y[i, l] T1[j, l]).  Only
+// warp-level synchronisation is needed.
+template <typename T, int NM>
+__global__ void __launch_bounds__(128)
+k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ SB,
+             const T* __restrict__ Q1, const T* __restrict__ Q2, const T* __restrict__ T1,
+             const T* __restrict__ T2, const uint32_t* __restrict__ masks,
+             const double* __restrict__ b, double* __restrict__ x, const int32_t* skip) {
   if (skip && *skip) return;
+  constexpr int EPW = 32 / NM;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = lane / NM, i = lane % NM;
+  const int wpb = blockDim.x >> 5;
+  const int eslot = warp * EPW + slot;
+  const int64_t e = ((int64_t)blockIdx.x * wpb + warp) * EPW + slot;
+  const bool eok = e < E;
+  const bool rok = eok && i < n;
+  const unsigned gmask = (NM == 32) ? 0xffffffffu : (((1u << NM) - 1u) << (slot * NM));
   const int nn = n * n;
-  T* F0 = sm;           // factor buffer 0
-  T* F1 = F0 + nn;      // factor buffer 1
-  T* W0 = F1 + nn;      // work
-  T* W1 = W0 + nn;      // work
-  __shared__ int rs[TPP_MAX_N + 1], cs[TPP_MAX_N + 1];
-  __shared__ int rowblk[TPP_MAX_N], colblk[TPP_MAX_N];
-  __shared__ int nb[2];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t e = blockIdx.x;
-  const int64_t base = e * nn;
-  for (int q = tid; q < nn; q += nt) {
-    F0[q] = SA[base + q];
-    F1[q] = SB[base + q];
-    W0[q] = (T)b[base + q];
+  T* Fa = reinterpret_cast<T*>(smraw) + (size_t)eslot * 3 * NM * NM;   // SA, then T2, then Q1
+  T* Fb = Fa + NM * NM;                                                  // T1
+  T* Wm = Fb + NM * NM;                                                  // work / Y
+  int* isx = reinterpret_cast<int*>(reinterpret_cast<T*>(smraw) + (size_t)wpb * EPW * 3 * NM * NM) +
+             eslot * (3 * NM + 4);
+  int* rs = isx;                  // row block starts (T2), NM + 1
+  int* cs = rs + NM + 1;          // column block starts (T1), NM + 1
+  int* colblk = cs + NM + 1;      // block of each column, NM
+  int* nbs = colblk + NM;         // nbr, nbc
+  const int64_t g = eok ? e * nn : 0;
+
+  // ---- B S_A^T: lane i holds row i of B
+  T row[NM], acc[NM];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? (T)b[g + i + n * k] : (T)0;
+  if (eok)
+    for (int q = i; q < nn; q += NM) {
+      Fa[q] = SA[g + q];
+      Fb[q] = T1[g + q];
+    }
+  if (i == 0 && eok) {
+    const uint32_t m2 = masks[2 * e + 1], m1 = masks[2 * e];
+    int nb = 0, r = 0;
+    while (r < n) {
+      rs[nb++] = r;
+      r += (((m2 >> r) & 1u) && r + 1 < n) ? 2 : 1;
+    }
+    rs[nb] = n;
+    nbs[0] = nb;
+    nb = 0;
+    r = 0;
+    while (r < n) {
+      cs[nb] = r;
+      const int w = (((m1 >> r) & 1u) && r + 1 < n) ? 2 : 1;
+      for (int t = 0; t < w; ++t) colblk[r + t] = nb;
+      ++nb;
+      r += w;
+    }
+    cs[nb] = n;
+    nbs[1] = nb;
   }
-  if (tid == 0) nb[0] = blocks_from_mask(masks[2 * e + 1], n, rs, rowblk);   // T2 -> rows
-  if (tid == 32) nb[1] = blocks_from_mask(masks[2 * e], n, cs, colblk);      // T1 -> columns
-  __syncthreads();
-  // W1 = B S_A^T
-  for (int q = tid; q < nn; q += nt) {
-    const int i = q % n, j = q / n;
-    T s = (T)0;
-    for (int k = 0; k < n; ++k) s += W0[i + n * k] * F0[j + n * k];
-    W1[q] = s;
+  __syncwarp(gmask);
+  for (int j = 0; j < n; ++j) {
+    T sacc = (T)0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+      if (k < n) sacc += row[k] * Fa[j + n * k];
+    if (rok) Wm[i + n * j] = sacc;
   }
-  __syncthreads();
-  // W0 = S_B W1   (= C)
-  for (int q = tid; q < nn; q += nt) {
-    const int i = q % n, j = q / n;
-    T s = (T)0;
-    for (int k = 0; k < n; ++k) s += F1[i + n * k] * W1[k + n * j];
-    W0[q] = s;
+  __syncwarp(gmask);
+  // ---- C = S_B W: lane i holds row i of S_B
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? SB[g + i + n * k] : (T)0;
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    T sacc = (T)0;
+    if (j < n) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k)
+        if (k < n) sacc += row[k] * Wm[k + n * j];
+    }
+    acc[j] = sacc;
   }
-  __syncthreads();
-  for (int q = tid; q < nn; q += nt) {
-    F0[q] = T1[base + q];
-    F1[q] = T2[base + q];
+  __syncwarp(gmask);
+#pragma unroll
+  for (int j = 0; j < NM; ++j)
+    if (rok && j < n) Wm[i + n * j] = acc[j];
+  if (eok)
+    for (int q = i; q < nn; q += NM) Fa[q] = T2[g + q];   // SA no longer needed
+  __syncwarp(gmask);
+
+  // ---- Sylvester T2 Y + Y T1^T = C (in Wm), right-looking wavefront
+  {
+    const int nbr = eok ? nbs[0] : 1, nbc = eok ? nbs[1] : 1;
+    int I = 0;
+    if (rok)
+      while (rs[I + 1] <= i) ++I;
+    const int i0 = rok ? rs[I] : 0, ni = rok ? rs[I + 1] - i0 : 1;
+    const int aI = nbr - 1 - I;
+    const T t2ii = rok ? Fa[i + n * i] : (T)1;
+    const int steps = nbr + nbc - 1;
+    for (int st = 0; st < steps; ++st) {
+      const int bJ = st - aI;
+      const bool act = rok && bJ >= 0 && bJ < nbc;
+      int j0 = 0, nj = 0;
+      if (act) {
+        const int Js = nbc - 1 - bJ;
+        j0 = cs[Js];
+        nj = cs[Js + 1] - j0;
+      }
+      // (A) solve the block of this row block on anti-diagonal st
+      T y0 = (T)0, y1 = (T)0;
+      if (act) {
+        if (ni == 1 && nj == 1) {
+          y0 = Wm[i + n * j0] / (t2ii + Fb[j0 + n * j0]);
+        } else {
+          T ab[4] = {Fa[i0 + n * i0], (T)0, (T)0, (T)0}, bb[4] = {Fb[j0 + n * j0], (T)0, (T)0, (T)0};
+          T rhs[4] = {Wm[i0 + n * j0], (T)0, (T)0, (T)0};
+          if (ni == 2) {
+            ab[1] = Fa[(i0 + 1) + n * i0];
+            ab[2] = Fa[i0 + n * (i0 + 1)];
+            ab[3] = Fa[(i0 + 1) + n * (i0 + 1)];
+            rhs[1] = Wm[(i0 + 1) + n * j0];
+          }
+          if (nj == 2) {
+            bb[1] = Fb[(j0 + 1) + n * j0];
+            bb[2] = Fb[j0 + n * (j0 + 1)];
+            bb[3] = Fb[(j0 + 1) + n * (j0 + 1)];
+            rhs[ni] = Wm[i0 + n * (j0 + 1)];
+          }
+          if (ni == 2 && nj == 2) rhs[3] = Wm[(i0 + 1) + n * (j0 + 1)];
+          small_sylvester<T>(ni, nj, ab, bb, rhs);
+          const int rr = i - i0;           // this lane's row inside the block
+          y0 = rhs[rr];
+          if (nj == 2) y1 = rhs[rr + ni];
+        }
+      }
+      __syncwarp(gmask);                  // all reads of this block done
+      if (act) {
+        Wm[i + n * j0] = y0;
+        if (nj == 2) Wm[i + n * (j0 + 1)] = y1;
+      }
+      __syncwarp(gmask);
+      // (B) contributions of the blocks solved at step st to the unsolved entries of row i
+      if (rok && st + 1 < steps) {
+        for (int jp = 0; jp < n; ++jp) {
+          const int Jp = colblk[jp];
+          const int aJ = nbc - 1 - Jp;
+          if (aI + aJ <= st) continue;
+          T v = (T)0;
+          const int a = st - aJ;           // row block solved at st in column block Jp
+          if (a >= 0 && a < nbr) {
+            const int Is = nbr - 1 - a;
+            for (int k = rs[Is]; k < rs[Is + 1]; ++k) v += Fa[i + n * k] * Wm[k + n * jp];
+          }
+          if (act) {
+            v += y0 * Fb[jp + n * j0];
+            if (nj == 2) v += y1 * Fb[jp + n * (j0 + 1)];
+          }
+          Wm[i + n * jp] -= v;
+        }
+      }
+      __syncwarp(gmask);
+    }
   }
-  __syncthreads();
-  // reciprocals of the 1x1 block denominators T2_ii + T1_jj, all lanes busy
-  for (int q = tid; q < nn; q += nt) {
-    const int i = q % n, j = q / n;
-    W1[q] = (T)1 / (F1[i + n * i] + F0[j + n * j]);
+  if (eok)
+    for (int q = i; q < nn; q += NM) Fa[q] = Q1[g + q];
+  __syncwarp(gmask);
+  // ---- W = Y Q1^T: lane i holds row i of Y
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? Wm[i + n * k] : (T)0;
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    T sacc = (T)0;
+    if (j < n) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k)
+        if (k < n) sacc += row[k] * Fa[j + n * k];
+    }
+    acc[j] = sacc;
   }
-  __syncthreads();
-  sylvester_block<T>(F1, F0, W0, n, rs, cs, nb[0], nb[1], rowblk, colblk, W1);   // W0 = Y
-  __syncthreads();
-  for (int q = tid; q < nn; q += nt) {
-    F0[q] = Q1[base + q];
-    F1[q] = Q2[base + q];
+  __syncwarp(gmask);
+#pragma unroll
+  for (int j = 0; j < NM; ++j)
+    if (rok && j < n) Wm[i + n * j] = acc[j];
+  __syncwarp(gmask);
+  // ---- x = Q2 W: lane i holds row i of Q2
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? Q2[g + i + n * k] : (T)0;
+  for (int j = 0; j < n; ++j) {
+    T sacc = (T)0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+      if (k < n) sacc += row[k] * Wm[k + n * j];
+    if (rok) x[g + i + n * j] = (double)sacc;
   }
-  __syncthreads();
-  // W1 = Y Q1^T
-  for (int q = tid; q < nn; q += nt) {
-    const int i = q % n, j = q / n;
-    T s = (T)0;
-    for (int k = 0; k < n; ++k) s += W0[i + n * k] * F0[j + n * k];
-    W1[q] = s;
-  }
-  __syncthreads();
-  // x = Q2 W1
-  for (int q = tid; q < nn; q += nt) {
-    const int i = q % n, j = q / n;
-    T s = (T)0;
-    for (int k = 0; k < n; ++k) s += F1[i + n * k] * W1[k + n * j];
-    x[base + q] = (double)s;
-  }
+}
+
+template <typename T, int NM>
+cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, const T* Q2,
+                     const T* T1, const T* T2, const uint32_t* masks, const double* b, double* x,
+                     const int32_t* skip, cudaStream_t s) {
+  constexpr int EPW = 32 / NM;
+  const int warps = (NM == 32 && sizeof(T) == 8) ? 2 : 4;
+  const int64_t per_block = (int64_t)warps * EPW;
+  const int64_t blocks = (E + per_block - 1) / per_block;
+  const size_t smem = (size_t)warps * EPW * 3 * NM * NM * sizeof(T) +
+                      (size_t)warps * EPW * (3 * NM + 4) * sizeof(int);
+  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_w<T, NM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_apply_2d_w<T, NM><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, SB, Q1, Q2, T1, T2,
+                                                                  masks, b, x, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* Q1, const T* Q2,
+                           const T* T1, const T* T2, const double* b, double* x,
+                           const int32_t* skip, cudaStream_t s) {
+  const uint32_t* masks = c->p<uint32_t>(c->L.masks);
+  if (c->n <= 8) return launch_w<T, 8>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
+  if (c->n <= 16) return launch_w<T, 16>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
+  return launch_w<T, 32>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
 }
 
 cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
                             const int32_t* skip, cudaStream_t s) {
-  const int n = c->n, nn = n * n;
-  const uint32_t* masks = c->p<uint32_t>(c->L.masks);
   if (prec == TPP_FP64) {
-    const size_t smem = 4 * (size_t)nn * sizeof(double);
-    k_apply_2d<double><<<(unsigned)c->E, kApplyThreads, smem, s>>>(
-        n, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB), c->p<double>(c->L.fQ1),
-        c->p<double>(c->L.fQ2), c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), masks, b, x,
-        skip);
-    count_launch();
-  } else {
-    const size_t smem = 4 * (size_t)nn * sizeof(float);
-    const float* f = c->p<float>(c->L.f32);
-    const size_t st = (size_t)c->E * nn;
-    k_apply_2d<float><<<(unsigned)c->E, kApplyThreads, smem, s>>>(
-        n, f, f + st, f + 2 * st, f + 3 * st, f + 4 * st, f + 5 * st, masks, b, x, skip);
-    count_launch();
+    return launch_apply_t<double>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
+                                  c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
+                                  c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), b, x, skip, s);
   }
-  return cudaGetLastError();
+  const float* f = c->p<float>(c->L.f32);
+  const size_t st = (size_t)c->E * c->n * c->n;
+  return launch_apply_t<float>(c, f, f + st, f + 2 * st, f + 3 * st, f + 4 * st, f + 5 * st, b, x,
+                               skip, s);
 }
 
 // float copies of the apply factors (SA, SB, Q1, Q2, T1, T2), rounded to nearest
