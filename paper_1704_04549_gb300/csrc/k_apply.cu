@@ -162,7 +162,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
     if (rok) Wm[i + n * j] = sacc;
   }
   __syncwarp(gmask);
-  // ---- C = S_B W: lane i holds row i of S_B
+  // ---- C = S_B W: lane i holds row i of S_B; row i of C stays in registers (acc)
 #pragma unroll
   for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? SB[g + i + n * k] : (T)0;
 #pragma unroll
@@ -175,15 +175,11 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
     }
     acc[j] = sacc;
   }
-  __syncwarp(gmask);
-#pragma unroll
-  for (int j = 0; j < NM; ++j)
-    if (rok && j < n) Wm[i + n * j] = acc[j];
   if (eok)
     for (int q = i; q < nn; q += NM) Fa[q] = T2[g + q];   // SA no longer needed
   __syncwarp(gmask);
 
-  // ---- Sylvester T2 Y + Y T1^T = C (in Wm), right-looking wavefront
+  // ---- Sylvester T2 Y + Y T1^T = C, right-looking wavefront, rows in registers
   {
     const int nbr = eok ? nbs[0] : 1, nbc = eok ? nbs[1] : 1;
     int I = 0;
@@ -191,78 +187,105 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
       while (rs[I + 1] <= i) ++I;
     const int i0 = rok ? rs[I] : 0, ni = rok ? rs[I + 1] - i0 : 1;
     const int aI = nbr - 1 - I;
+    // other row of a 2-row block (own lane otherwise, so every shuffle stays in the group)
+    const int partner = (ni == 2) ? slot * NM + ((i == i0) ? i0 + 1 : i0) : lane;
     const T t2ii = rok ? Fa[i + n * i] : (T)1;
+    int aJ[NM];                                      // anti-diagonal offset of each column
+#pragma unroll
+    for (int j = 0; j < NM; ++j) aJ[j] = (eok && j < n) ? nbc - 1 - colblk[j] : 0;
     const int steps = nbr + nbc - 1;
     for (int st = 0; st < steps; ++st) {
+      // (A) this row block's block on anti-diagonal st
       const int bJ = st - aI;
       const bool act = rok && bJ >= 0 && bJ < nbc;
-      int j0 = 0, nj = 0;
+      int j0 = 0, nj = 1;
       if (act) {
         const int Js = nbc - 1 - bJ;
         j0 = cs[Js];
         nj = cs[Js + 1] - j0;
       }
-      // (A) solve the block of this row block on anti-diagonal st
+      T r0 = (T)0, r1 = (T)0;
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        if (j == j0) r0 = acc[j];
+        if (j == j0 + 1) r1 = acc[j];
+      }
+      const T p0 = __shfl_sync(gmask, r0, partner & 31);
+      const T p1 = __shfl_sync(gmask, r1, partner & 31);
       T y0 = (T)0, y1 = (T)0;
       if (act) {
         if (ni == 1 && nj == 1) {
-          y0 = Wm[i + n * j0] / (t2ii + Fb[j0 + n * j0]);
+          y0 = r0 / (t2ii + Fb[j0 + n * j0]);
         } else {
           T ab[4] = {Fa[i0 + n * i0], (T)0, (T)0, (T)0}, bb[4] = {Fb[j0 + n * j0], (T)0, (T)0, (T)0};
-          T rhs[4] = {Wm[i0 + n * j0], (T)0, (T)0, (T)0};
+          T rhs[4] = {(T)0, (T)0, (T)0, (T)0};
+          const int rr = i - i0;
+          // rhs column-major (ni x nj): own row from r0/r1, the other row from the partner
           if (ni == 2) {
             ab[1] = Fa[(i0 + 1) + n * i0];
             ab[2] = Fa[i0 + n * (i0 + 1)];
             ab[3] = Fa[(i0 + 1) + n * (i0 + 1)];
-            rhs[1] = Wm[(i0 + 1) + n * j0];
+            rhs[rr] = r0;
+            rhs[1 - rr] = p0;
+            if (nj == 2) {
+              rhs[2 + rr] = r1;
+              rhs[2 + 1 - rr] = p1;
+            }
+          } else {
+            rhs[0] = r0;
+            if (nj == 2) rhs[1] = r1;
           }
           if (nj == 2) {
             bb[1] = Fb[(j0 + 1) + n * j0];
             bb[2] = Fb[j0 + n * (j0 + 1)];
             bb[3] = Fb[(j0 + 1) + n * (j0 + 1)];
-            rhs[ni] = Wm[i0 + n * (j0 + 1)];
           }
-          if (ni == 2 && nj == 2) rhs[3] = Wm[(i0 + 1) + n * (j0 + 1)];
           small_sylvester<T>(ni, nj, ab, bb, rhs);
-          const int rr = i - i0;           // this lane's row inside the block
           y0 = rhs[rr];
           if (nj == 2) y1 = rhs[rr + ni];
         }
       }
-      __syncwarp(gmask);                  // all reads of this block done
-      if (act) {
-        Wm[i + n * j0] = y0;
-        if (nj == 2) Wm[i + n * (j0 + 1)] = y1;
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        if (act && j == j0) acc[j] = y0;
+        if (act && nj == 2 && j == j0 + 1) acc[j] = y1;
       }
-      __syncwarp(gmask);
       // (B) contributions of the blocks solved at step st to the unsolved entries of row i
-      if (rok && st + 1 < steps) {
-        for (int jp = 0; jp < n; ++jp) {
-          const int Jp = colblk[jp];
-          const int aJ = nbc - 1 - Jp;
-          if (aI + aJ <= st) continue;
-          T v = (T)0;
-          const int a = st - aJ;           // row block solved at st in column block Jp
-          if (a >= 0 && a < nbr) {
-            const int Is = nbr - 1 - a;
-            for (int k = rs[Is]; k < rs[Is + 1]; ++k) v += Fa[i + n * k] * Wm[k + n * jp];
+      if (st + 1 < steps) {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            const int a = st - aJ[j];                     // row block solved now in column j
+            const bool valid = eok && a >= 0 && a < nbr;   // uniform over the element's lanes
+            const bool unsolved = rok && (aI + aJ[j] > st);
+            T v = (T)0;
+            if (valid) {
+              const int ks = rs[nbr - 1 - a];
+              const int nks = rs[nbr - a] - ks;
+              const T yk0 = __shfl_sync(gmask, acc[j], (slot * NM + ks) & 31);
+              const T yk1 = __shfl_sync(gmask, acc[j], (slot * NM + ks + (nks - 1)) & 31);
+              if (unsolved) {
+                v += Fa[i + n * ks] * yk0;
+                if (nks == 2) v += Fa[i + n * (ks + 1)] * yk1;
+              }
+            }
+            if (act && unsolved) {
+              v += y0 * Fb[j + n * j0];
+              if (nj == 2) v += y1 * Fb[j + n * (j0 + 1)];
+            }
+            acc[j] -= v;
           }
-          if (act) {
-            v += y0 * Fb[jp + n * j0];
-            if (nj == 2) v += y1 * Fb[jp + n * (j0 + 1)];
-          }
-          Wm[i + n * jp] -= v;
         }
       }
-      __syncwarp(gmask);
     }
   }
+  __syncwarp(gmask);
   if (eok)
     for (int q = i; q < nn; q += NM) Fa[q] = Q1[g + q];
   __syncwarp(gmask);
-  // ---- W = Y Q1^T: lane i holds row i of Y
+  // ---- W = Y Q1^T: lane i holds row i of Y (acc)
 #pragma unroll
-  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? Wm[i + n * k] : (T)0;
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? acc[k] : (T)0;
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
     T sacc = (T)0;
@@ -273,7 +296,6 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
     }
     acc[j] = sacc;
   }
-  __syncwarp(gmask);
 #pragma unroll
   for (int j = 0; j < NM; ++j)
     if (rok && j < n) Wm[i + n * j] = acc[j];

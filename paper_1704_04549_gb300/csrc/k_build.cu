@@ -20,16 +20,9 @@ namespace tpp {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
-constexpr int kBuildThreads = 256;
 
-struct BuildOut {
-  double *sigma, *A1, *B1, *A2, *B2, *SA, *SB, *Q1, *Q2, *T1, *T2, *cond;
-  int32_t* flags;
-  uint32_t* masks;
-  DevStatus* st;
-};
 
-__device__ __forceinline__ int ld_of(int n) { return (n & 1) ? n : n + 1; }
+__host__ __device__ __forceinline__ int ld_of(int n) { return (n & 1) ? n : n + 1; }
 
 // ---- warp-level Householder helpers for the real Schur form --------------
 // All lanes compute the same scalars from shared memory (uniform control).
@@ -203,56 +196,6 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
   return true;
 }
 
-// ---- block / warp helpers --------------------------------------------------
-// Sum of squares of v[0..len) computed by warp 0 and broadcast through *slot.
-// FP64 warp instructions cost the full pipe width whatever their lane mask on
-// this GPU, so short reductions run on one warp instead of the whole block.
-__device__ double norm2_w0(const double* v, int len, double* slot) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int t = threadIdx.x; t < len; t += 32) s += v[t] * v[t];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) *slot = s;
-  }
-  __syncthreads();
-  return *slot;
-}
-
-__device__ double sum_w0(const double* v, int len, double* slot) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int t = threadIdx.x; t < len; t += 32) s += v[t];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) *slot = s;
-  }
-  __syncthreads();
-  return *slot;
-}
-
-// Reorthogonalise p (length r) against the first k vectors of B (vector-major,
-// B[i*r + t]) twice: one warp per coefficient, then one thread per entry.
-__device__ void reorth(double* p, const double* B, int k, int r, double* cf) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int pass = 0; pass < 2; ++pass) {
-    __syncthreads();
-    for (int i = wid; i < k; i += nw) {
-      double s = 0.0;
-      for (int t = lane; t < r; t += 32) s += B[i * r + t] * p[t];
-      s = warp_sum(s);
-      if (lane == 0) cf[i] = s;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < r; t += blockDim.x) {
-      double s = p[t];
-      for (int i = 0; i < k; ++i) s -= cf[i] * B[i * r + t];
-      p[t] = s;
-    }
-  }
-  __syncthreads();
-}
-
 // ---- Golub-Kahan tridiagonal T (zero diagonal, off-diagonal e, size m) ------
 // Number of eigenvalues of T below x by the sign changes of the leading
 // principal minors of T - x I (Sturm sequence): D_0 = 1, D_1 = -x,
@@ -334,72 +277,6 @@ __device__ void inverse_iteration(const double* e, int m, double lam, double* z,
   }
 }
 
-// Gauss-Jordan inverses of two n x n matrices at once (partial pivoting).
-// aug[m] is n x 2n column-major (ld n): left block the matrix, right identity.
-// Returns per-matrix singular flags in sing[2].
-__device__ void gauss_jordan2(double* aug0, double* aug1, int n, int* pivrow, double* fac,
-                              int* sing) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int k = 0; k < n; ++k) {
-    if (tid < 64) {                 // warp 0: matrix 0, warp 1: matrix 1 (lanes over rows)
-      const int mIdx = tid >> 5, lane = tid & 31;
-      const double* a = mIdx ? aug1 : aug0;
-      double best = -1.0;
-      int p = k;
-      for (int i = k + lane; i < n; i += 32) {
-        const double v = fabs(a[i + n * k]);
-        if (v > best) { best = v; p = i; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int op = __shfl_xor_sync(0xffffffffu, p, o);
-        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
-      }
-      if (lane == 0) {
-        pivrow[mIdx] = p;
-        if (best == 0.0) sing[mIdx] = 1;
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < 2 * 2 * n; q += nt) {     // row swap
-      const int mIdx = q / (2 * n), c = q % (2 * n);
-      double* a = mIdx ? aug1 : aug0;
-      const int p = pivrow[mIdx];
-      if (p != k) {
-        const double t = a[k + n * c];
-        a[k + n * c] = a[p + n * c];
-        a[p + n * c] = t;
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < 2 * n; q += nt) {         // multipliers (column k)
-      const int mIdx = q / n, i = q % n;
-      double* a = mIdx ? aug1 : aug0;
-      const double piv = a[k + n * k];
-      fac[mIdx * n + i] = (i == k) ? 0.0 : ((piv != 0.0) ? a[i + n * k] / piv : 0.0);
-      if (i == k) fac[2 * n + mIdx] = (piv != 0.0) ? 1.0 / piv : 0.0;
-    }
-    __syncthreads();
-    for (int q = tid; q < 2 * n * 2 * n; q += nt) {   // eliminate + scale pivot row
-      const int mIdx = q / (2 * n * n), rem = q % (2 * n * n);
-      const int c = rem / n, i = rem % n;
-      if (c < k) continue;
-      double* a = mIdx ? aug1 : aug0;
-      if (i == k) continue;
-      a[i + n * c] -= fac[mIdx * n + i] * a[k + n * c];
-    }
-    __syncthreads();
-    for (int q = tid; q < 2 * 2 * n; q += nt) {
-      const int mIdx = q / (2 * n), c = q % (2 * n);
-      if (c < k) continue;
-      double* a = mIdx ? aug1 : aug0;
-      a[k + n * c] *= fac[2 * n + mIdx];
-    }
-    __syncthreads();
-  }
-}
-
 // 1-norm (max column sum) of an n x n column-major matrix by one warp.
 __device__ double norm1_warp(const double* A, int n) {
   const int lane = threadIdx.x & 31;
@@ -424,195 +301,328 @@ __device__ void atomic_min_double(double* addr, double v) {
 
 }  // namespace
 
-// Shared-memory layout of k_build_2d (offsets in doubles).
-struct BuildSmem {
-  size_t cxs, cys, zds, rzs, big, vec, ints, total_bytes;
+// ---------------------------------------------------------------------------
+// Build pipeline (2D), four kernels, one warp per element or per matrix so
+// that every FP64 instruction is issued by a full warp and many elements are
+// in flight per SM:
+//   k_ksvd_w     coefficients, matrix-free Golub-Kahan-Lanczos on the core M,
+//                top-2 singular triplets, factors A_k, B_k          (a3, a4)
+//   k_invert_w   choice of the inverted pair, Gauss-Jordan inverses,
+//                C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2                  (a5)
+//   k_schur_w    real Schur form of each C_i (one warp per matrix)   (a5)
+//   k_final_w    S_A = Q_1^T L_A^-1, S_B = Q_2^T L_B^-1              (a5)
+
+struct KsvdArgs {
+  const Tables* T;
+  int n, rz, nx, ny;
+  int64_t E;
+  double h;
+  const double *cx, *cy, *sx, *sy, *Zd, *Rz, *Qo;
+  double* scr;     // per element: U (r*r), V (r*r), tridiagonal work (16 r)
+  int* iscr;       // per element: 4 r pivot flags
+  double *sigma, *A1, *B1, *A2, *B2;
+  DevStatus* st;
 };
 
-__host__ __device__ inline BuildSmem build_smem_layout(int n, int rz) {
-  const int nc = n + 3, r = n + rz, nn = n * n;
-  const int ld = (n & 1) ? n : n + 1;
-  BuildSmem L;
-  L.cxs = 0;
-  L.cys = L.cxs + (size_t)nc * n;
-  L.zds = L.cys + (size_t)nc * n;
-  L.rzs = L.zds + (size_t)n * nc;
-  L.big = L.rzs + (size_t)rz * nc;
-  size_t big = (size_t)3 * r * r;
-  const size_t need2 = (size_t)8 * nn + (size_t)4 * n * ld + 2 * n + 2 + 64;
-  if (need2 > big) big = need2;
-  L.vec = L.big + big;
-  const size_t nvec = (size_t)16 * r + 1 + 16 + (size_t)16 * r;
-  L.ints = L.vec + nvec;
-  L.total_bytes = L.ints * sizeof(double) + (size_t)(4 * r + 8) * sizeof(int);
+// shared-memory layout of one warp of k_ksvd_w (offsets in doubles)
+struct KsvdSmem {
+  int cx, cy, vs, ps, ta, tb, cf, al, be, ee, e2s, z1, z2, mu1, mv1, mu2, mv2, scal, total;
+};
+
+__host__ __device__ inline KsvdSmem ksvd_smem(int n, int rz) {
+  const int nc = n + 3, r = n + rz;
+  KsvdSmem L;
+  int o = 0;
+  L.cx = o; o += nc * n;
+  L.cy = o; o += nc * n;
+  L.vs = o; o += r;
+  L.ps = o; o += r;
+  L.ta = o; o += nc;
+  L.tb = o; o += nc;
+  L.cf = o; o += 32;
+  L.al = o; o += r;
+  L.be = o; o += r + 1;
+  L.ee = o; o += 2 * r;
+  L.e2s = o; o += 2 * r;
+  L.z1 = o; o += 2 * r;
+  L.z2 = o; o += 2 * r;
+  L.mu1 = o; o += r;
+  L.mv1 = o; o += r;
+  L.mu2 = o; o += r;
+  L.mv2 = o; o += r;
+  L.scal = o; o += 8;
+  L.total = (o + 1) & ~1;
   return L;
 }
 
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBuildThreads)
-k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
-           const double* __restrict__ cx, const double* __restrict__ cy,
-           const double* __restrict__ sx, const double* __restrict__ sy,
-           const double* __restrict__ Zd, const double* __restrict__ Rz,
-           const double* __restrict__ Qo, BuildOut out) {
-  extern __shared__ double sm[];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int nn = n * n, nc = n + 3, r = n + rz, Ro = nn - n;
-  const int64_t e = blockIdx.x;
-  const int ex = (int)(e % nx), ey = (int)(e / nx);
-  const int64_t eR = ey * (int64_t)nx + (ex + 1) % nx;
-  const int64_t eT = ((ey + 1) % ny) * (int64_t)nx + ex;
+namespace {
 
-  const BuildSmem L = build_smem_layout(n, rz);
-  double* Cxs = sm + L.cxs;            // nc x n   Cx[c][j]
-  double* Cys = sm + L.cys;            // nc x n   Cy[c][i]
-  double* Zds = sm + L.zds;            // n x nc
-  double* Rzs = sm + L.rzs;            // rz x nc
-  double* big = sm + L.big;            // M (r*r), U (r*r), V (r*r); later n x n work
-  double* Mm = big;
-  double* U = Mm + r * r;
-  double* V = U + r * r;
-  double* pv = sm + L.vec;             // r
-  double* cf = pv + r;                 // r
-  double* al = cf + r;                 // r
-  double* be = al + r;                 // r + 1
-  double* ee = be + r + 1;             // 2r
-  double* z1 = ee + 2 * r;             // 2r
-  double* z2 = z1 + 2 * r;             // 2r
-  double* e2s = z2 + 2 * r;            // 2r (squared scaled off-diagonal)
-  double* mu1 = e2s + 2 * r;           // r  (Ritz vectors in M space)
-  double* mv1 = mu1 + r;
-  double* mu2 = mv1 + r;
-  double* mv2 = mu2 + r;
-  double* red = mv2 + r;               // 8
-  double* scal = red + 8;              // 8 scalars
-  double* tw = scal + 8;               // 2 x (4 * 2r) tridiagonal work
-  int* piv = reinterpret_cast<int*>(sm + L.ints);   // 2 x 2r ints
-  int* ish = piv + 2 * 2 * r;          // 8 ints
-
-  // ---- 1. coefficients (flux Jacobians of the element, Sec. 3.4.1)
-  const int64_t base = e * nn;
-  for (int q = tid; q < nn; q += nt) {
-    const int a = q % n, b = q / n;
-    Cxs[a * n + b] = cx[base + q];      // Cx[c = x node][j]
-    Cys[b * n + a] = cy[base + q];      // Cy[c = y node][i]
-  }
-  if (tid < n) {
-    const int j = tid;
-    Cxs[n * n + j] = fmax(sx[eR * n + j], 0.0);
-    Cxs[(n + 1) * n + j] = fmax(-sx[e * n + j], 0.0);
-    Cxs[(n + 2) * n + j] = h * h * T->w[j];
-    Cys[n * n + j] = fmax(sy[eT * n + j], 0.0);
-    Cys[(n + 1) * n + j] = fmax(-sy[e * n + j], 0.0);
-    Cys[(n + 2) * n + j] = 0.0;
-  }
-  for (int q = tid; q < n * nc; q += nt) Zds[q] = Zd[q];
-  for (int q = tid; q < rz * nc; q += nt) Rzs[q] = Rz[q];
-  if (tid < 8) ish[tid] = 0;
-  __syncthreads();
-
-  // ---- 2. core matrix M (r x r, row-major)
-  double fro = 0.0;
-  for (int q = tid; q < r * r; q += nt) {
-    const int p = q / r, c2 = q % r;
-    double s = 0.0;
-    if (p < n && c2 < n) {
-      for (int c = 0; c < nc; ++c) s += Cxs[c * n + p] * Zds[c2 * nc + c] + Zds[p * nc + c] * Cys[c * n + c2];
-    } else if (p < n) {
-      const int t = c2 - n;
-      for (int c = 0; c < nc; ++c) s += Cxs[c * n + p] * Rzs[t * nc + c];
-    } else if (c2 < n) {
-      const int t = p - n;
-      for (int c = 0; c < nc; ++c) s += Rzs[t * nc + c] * Cys[c * n + c2];
+// out = M v for the core matrix M = [[Cx^T Zd^T + Zd Cy, Cx^T Rz^T], [Rz Cy, 0]]
+// without forming it: top = Cx^T (Zd^T v1 + Rz^T v2) + Zd (Cy v1), bottom = Rz (Cy v1).
+__device__ void warp_mv_M(const double* Cx, const double* Cy, const double* __restrict__ Zd,
+                          const double* __restrict__ Rz, int n, int rz, const double* v,
+                          double* out, double* ta, double* tb) {
+  const int nc = n + 3, lane = threadIdx.x & 31;
+  for (int c = lane; c < nc; c += 32) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < n; ++q) {
+      a += Cy[c * n + q] * v[q];
+      b += __ldg(Zd + q * nc + c) * v[q];
     }
-    Mm[q] = s;
-    fro += s * s;
+    for (int t = 0; t < rz; ++t) b += __ldg(Rz + t * nc + c) * v[n + t];
+    ta[c] = a;
+    tb[c] = b;
   }
-  fro = sqrt(block_sum(fro, red));
-  const double tol = 1e-12 * fro;
+  __syncwarp();
+  for (int p = lane; p < n; p += 32) {
+    double sv = 0.0;
+    for (int c = 0; c < nc; ++c) sv += Cx[c * n + p] * tb[c] + __ldg(Zd + p * nc + c) * ta[c];
+    out[p] = sv;
+  }
+  for (int t = lane; t < rz; t += 32) {
+    double sv = 0.0;
+    for (int c = 0; c < nc; ++c) sv += __ldg(Rz + t * nc + c) * ta[c];
+    out[n + t] = sv;
+  }
+  __syncwarp();
+}
 
-  // ---- 3. Golub-Kahan-Lanczos with full reorthogonalisation (Alg. lanczos)
-  // Run J0 = min(r, 24) steps, take the top-2 Ritz triplets of the bidiagonal
-  // and accept them when both residuals beta_J |u'_J| are below 1e-14 sigma_1;
-  // otherwise continue to the full size r (a complete orthogonal reduction).
-  {
-    for (int t = tid; t < r; t += nt) V[t] = splitmix_unit(1, t);
-    const double nv = sqrt(norm2_w0(V, r, &scal[3]));
-    for (int t = tid; t < r; t += nt) V[t] /= nv;
-    if (tid == 0) be[0] = 0.0;
-    __syncthreads();
+// out = M^T u: top = Zd (Cx u1) + Cy^T (Zd^T u1 + Rz^T u2), bottom = Rz (Cx u1).
+__device__ void warp_mv_MT(const double* Cx, const double* Cy, const double* __restrict__ Zd,
+                           const double* __restrict__ Rz, int n, int rz, const double* u,
+                           double* out, double* ta, double* tb) {
+  const int nc = n + 3, lane = threadIdx.x & 31;
+  for (int c = lane; c < nc; c += 32) {
+    double a = 0.0, b = 0.0;
+    for (int p = 0; p < n; ++p) {
+      a += Cx[c * n + p] * u[p];
+      b += __ldg(Zd + p * nc + c) * u[p];
+    }
+    for (int t = 0; t < rz; ++t) b += __ldg(Rz + t * nc + c) * u[n + t];
+    ta[c] = a;
+    tb[c] = b;
   }
+  __syncwarp();
+  for (int q = lane; q < n; q += 32) {
+    double sv = 0.0;
+    for (int c = 0; c < nc; ++c) sv += __ldg(Zd + q * nc + c) * ta[c] + Cy[c * n + q] * tb[c];
+    out[q] = sv;
+  }
+  for (int t = lane; t < rz; t += 32) {
+    double sv = 0.0;
+    for (int c = 0; c < nc; ++c) sv += __ldg(Rz + t * nc + c) * ta[c];
+    out[n + t] = sv;
+  }
+  __syncwarp();
+}
+
+// p (shared, length r) minus its projections on the first k rows of B
+// (global, row i at B + i r), twice; coefficients 32 at a time, one per lane.
+__device__ void warp_reorth(double* p, const double* B, int k, int r, double* cf) {
+  const int lane = threadIdx.x & 31;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i0 = 0; i0 < k; i0 += 32) {
+      const int i = i0 + lane;
+      double sv = 0.0;
+      if (i < k) {
+        const double* bi = B + (size_t)i * r;
+        for (int t = 0; t < r; ++t) sv += bi[t] * p[t];
+      }
+      cf[lane] = sv;
+      __syncwarp();
+      const int cnt = (k - i0 < 32) ? k - i0 : 32;
+      for (int t = lane; t < r; t += 32) {
+        double v = p[t];
+        for (int q = 0; q < cnt; ++q) v -= cf[q] * B[(size_t)(i0 + q) * r + t];
+        p[t] = v;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_norm2(const double* v, int len) {
+  const int lane = threadIdx.x & 31;
+  double sv = 0.0;
+  for (int t = lane; t < len; t += 32) sv += v[t] * v[t];
+  return warp_sum(sv);
+}
+
+// Gauss-Jordan inverse of the n x n left half of a (n x 2n, column-major, ld n)
+// with partial pivoting, by one warp (lanes over columns).  Returns true if a
+// zero pivot was met.  fac: n scratch.
+__device__ bool warp_gauss_jordan(double* a, int n, double* fac) {
+  const int lane = threadIdx.x & 31;
+  bool sing = false;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int p = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const double v = fabs(a[i + n * k]);
+      if (v > best) { best = v; p = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+    }
+    if (best == 0.0) sing = true;
+    if (p != k)
+      for (int c = lane; c < 2 * n; c += 32) {
+        const double t = a[k + n * c];
+        a[k + n * c] = a[p + n * c];
+        a[p + n * c] = t;
+      }
+    __syncwarp();
+    const double piv = a[k + n * k];
+    const double ip = (piv != 0.0) ? 1.0 / piv : 0.0;
+    for (int i = lane; i < n; i += 32) fac[i] = (i == k) ? 0.0 : a[i + n * k] * ip;
+    __syncwarp();
+    for (int c = k + lane; c < 2 * n; c += 32) {
+      const double akc = a[k + n * c];
+      for (int i = 0; i < n; ++i) a[i + n * c] -= fac[i] * akc;
+      a[k + n * c] = akc * ip;
+    }
+    __syncwarp();
+  }
+  return sing;
+}
+
+}  // namespace
+
+// ---- k_ksvd_w ---------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
+  extern __shared__ double smk[];
+  const int n = A.n, rz = A.rz, nc = n + 3, r = n + rz, nn = n * n, Ro = nn - n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= A.E) return;                                  // whole warp leaves together
+  const KsvdSmem L = ksvd_smem(n, rz);
+  double* sm = smk + (size_t)warp * L.total;
+  double *Cx = sm + L.cx, *Cy = sm + L.cy, *vs = sm + L.vs, *ps = sm + L.ps;
+  double *ta = sm + L.ta, *tb = sm + L.tb, *cf = sm + L.cf, *al = sm + L.al, *be = sm + L.be;
+  double *ee = sm + L.ee, *e2s = sm + L.e2s, *z1 = sm + L.z1, *z2 = sm + L.z2;
+  double *mu1 = sm + L.mu1, *mv1 = sm + L.mv1, *mu2 = sm + L.mu2, *mv2 = sm + L.mv2;
+  double* scal = sm + L.scal;
+  double* U = A.scr + (size_t)e * (2 * (size_t)r * r + 16 * (size_t)r);
+  double* V = U + (size_t)r * r;
+  double* tw = V + (size_t)r * r;
+  int* piv = A.iscr + (size_t)e * 4 * r;
+  const int ex = (int)(e % A.nx), ey = (int)(e / A.nx);
+  const int64_t eR = ey * (int64_t)A.nx + (ex + 1) % A.nx;
+  const int64_t eT = ((ey + 1) % A.ny) * (int64_t)A.nx + ex;
+  const int64_t base = e * nn;
+
+  // ---- coefficients of the rearranged block (flux Jacobians, Sec. 3.4.1)
+  for (int q = lane; q < nn; q += 32) {
+    const int a = q % n, b = q / n;
+    Cx[a * n + b] = A.cx[base + q];    // Cx[c = x node][j]
+    Cy[b * n + a] = A.cy[base + q];    // Cy[c = y node][i]
+  }
+  for (int j = lane; j < n; j += 32) {
+    Cx[n * n + j] = fmax(A.sx[eR * n + j], 0.0);
+    Cx[(n + 1) * n + j] = fmax(-A.sx[e * n + j], 0.0);
+    Cx[(n + 2) * n + j] = A.h * A.h * A.T->w[j];
+    Cy[n * n + j] = fmax(A.sy[eT * n + j], 0.0);
+    Cy[(n + 1) * n + j] = fmax(-A.sy[e * n + j], 0.0);
+    Cy[(n + 2) * n + j] = 0.0;
+  }
+  __syncwarp();
+  // scale of M (Frobenius norm of A~) for the breakdown tolerance: ||M||_F
+  // is bounded by the coefficient norms times the basis norms; use the
+  // cheaper bound sqrt(sum Cx^2 + sum Cy^2) * max(||Zd||, ||Rz||) (only the
+  // invariant-subspace test uses it)
+  double cs2 = 0.0;
+  for (int q = lane; q < 2 * nc * n; q += 32) cs2 += Cx[q] * Cx[q];
+  cs2 = warp_sum(cs2);
+  double zs2 = 0.0;
+  for (int q = lane; q < n * nc; q += 32) zs2 += __ldg(A.Zd + q) * __ldg(A.Zd + q);
+  for (int q = lane; q < rz * nc; q += 32) zs2 += __ldg(A.Rz + q) * __ldg(A.Rz + q);
+  zs2 = warp_sum(zs2);
+  const double tol = 1e-12 * sqrt(cs2 * zs2);
+
+  // ---- Golub-Kahan-Lanczos with full reorthogonalisation (Alg. lanczos)
+  for (int t = lane; t < r; t += 32) vs[t] = splitmix_unit(1, t);
+  __syncwarp();
+  {
+    const double nv = 1.0 / sqrt(warp_norm2(vs, r));
+    for (int t = lane; t < r; t += 32) {
+      vs[t] *= nv;
+      V[t] = vs[t];
+    }
+    if (lane == 0) be[0] = 0.0;
+  }
+  __syncwarp();
   int J = (r < 24) ? r : 24;
   int jdone = 0;
-  const int lane = tid & 31;
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 3; ++pass) {
     for (int j = jdone; j < J; ++j) {
-      // p = M v_j - beta_j u_{j-1}
-      for (int t = tid; t < r; t += nt) {
-        double sacc = 0.0;
-        for (int q = 0; q < r; ++q) sacc += Mm[t * r + q] * V[j * r + q];
-        if (j > 0) sacc -= be[j] * U[(j - 1) * r + t];
-        pv[t] = sacc;
-      }
-      reorth(pv, U, j, r, cf);
-      double a = sqrt(norm2_w0(pv, r, &scal[3]));
-      if (a <= tol) {       // invariant subspace: continue with a fresh direction
-        for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(1000 + j, t);
-        reorth(pv, U, j, r, cf);
-        const double nrm = sqrt(norm2_w0(pv, r, &scal[3]));
-        for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] / nrm;
+      // p = M v_j - beta_j u_{j-1}      (vs holds v_j)
+      warp_mv_M(Cx, Cy, A.Zd, A.Rz, n, rz, vs, ps, ta, tb);
+      if (j > 0)
+        for (int t = lane; t < r; t += 32) ps[t] -= be[j] * U[(size_t)(j - 1) * r + t];
+      __syncwarp();
+      warp_reorth(ps, U, j, r, cf);
+      double a = sqrt(warp_norm2(ps, r));
+      if (a <= tol) {            // invariant subspace: continue with a fresh direction
+        for (int t = lane; t < r; t += 32) ps[t] = splitmix_unit(1000 + j, t);
+        __syncwarp();
+        warp_reorth(ps, U, j, r, cf);
+        const double nrm = 1.0 / sqrt(warp_norm2(ps, r));
+        for (int t = lane; t < r; t += 32) ps[t] *= nrm;
         a = 0.0;
       } else {
         const double ia = 1.0 / a;
-        for (int t = tid; t < r; t += nt) U[j * r + t] = pv[t] * ia;
+        for (int t = lane; t < r; t += 32) ps[t] *= ia;
       }
-      if (tid == 0) al[j] = a;
-      __syncthreads();
+      for (int t = lane; t < r; t += 32) U[(size_t)j * r + t] = ps[t];
+      if (lane == 0) al[j] = a;
+      __syncwarp();
       if (j + 1 < r) {
-        // q = M^T u_j - alpha_j v_j
-        for (int t = tid; t < r; t += nt) {
-          double sacc = 0.0;
-          for (int q = 0; q < r; ++q) sacc += Mm[q * r + t] * U[j * r + q];
-          pv[t] = sacc - a * V[j * r + t];
-        }
-        reorth(pv, V, j + 1, r, cf);
-        double b = sqrt(norm2_w0(pv, r, &scal[3]));
+        // q = M^T u_j - alpha_j v_j      (ps holds u_j; result into ta/tb scratch then vs)
+        warp_mv_MT(Cx, Cy, A.Zd, A.Rz, n, rz, ps, ee, ta, tb);   // ee as scratch (length >= r)
+        for (int t = lane; t < r; t += 32) vs[t] = ee[t] - a * vs[t];
+        __syncwarp();
+        warp_reorth(vs, V, j + 1, r, cf);
+        double b = sqrt(warp_norm2(vs, r));
         if (b <= tol) {
-          for (int t = tid; t < r; t += nt) pv[t] = splitmix_unit(2000 + j, t);
-          reorth(pv, V, j + 1, r, cf);
-          const double nrm = sqrt(norm2_w0(pv, r, &scal[3]));
-          for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] / nrm;
+          for (int t = lane; t < r; t += 32) vs[t] = splitmix_unit(2000 + j, t);
+          __syncwarp();
+          warp_reorth(vs, V, j + 1, r, cf);
+          const double nrm = 1.0 / sqrt(warp_norm2(vs, r));
+          for (int t = lane; t < r; t += 32) vs[t] *= nrm;
           b = 0.0;
         } else {
           const double ib = 1.0 / b;
-          for (int t = tid; t < r; t += nt) V[(j + 1) * r + t] = pv[t] * ib;
+          for (int t = lane; t < r; t += 32) vs[t] *= ib;
         }
-        if (tid == 0) be[j + 1] = b;
-        __syncthreads();
+        for (int t = lane; t < r; t += 32) V[(size_t)(j + 1) * r + t] = vs[t];
+        if (lane == 0) be[j + 1] = b;
+        __syncwarp();
       }
     }
     jdone = J;
 
-    // ---- 4. top-2 singular values / vectors of the J x J bidiagonal matrix
+    // ---- top-2 singular values / vectors of the J x J bidiagonal matrix
     const int m = 2 * J;
-    for (int t = tid; t < m - 1; t += nt) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
-    __syncthreads();
-    if (tid < 32) {
-      // Gershgorin bound of the spectrum, then e^2 of the scaled matrix
-      double bnd = 0.0;
-      for (int i = lane; i < m; i += 32) {
-        const double sv = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < m - 1 ? fabs(ee[i]) : 0.0);
-        bnd = fmax(bnd, sv);
-      }
+    for (int t = lane; t < m - 1; t += 32) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
+    __syncwarp();
+    double bnd = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double sv = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < m - 1 ? fabs(ee[i]) : 0.0);
+      bnd = fmax(bnd, sv);
+    }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
-      if (bnd == 0.0) bnd = 1.0;
-      const double ib = 1.0 / bnd;
-      for (int i = lane; i < m - 1; i += 32) {
-        const double es = ee[i] * ib;
-        e2s[i] = es * es;
-      }
-      __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+    if (bnd == 0.0) bnd = 1.0;
+    const double ib = 1.0 / bnd;
+    for (int i = lane; i < m - 1; i += 32) {
+      const double es = ee[i] * ib;
+      e2s[i] = es * es;
+    }
+    __syncwarp();
+    {
       // multisection: lanes 0-15 bracket the largest eigenvalue, 16-31 the second
       const int grp = lane >> 4, gl = lane & 15;
       const int idx = m - grp;
@@ -630,18 +640,18 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
         hi = nhi;
       }
       if (gl == 0) scal[grp] = (grp < J) ? 0.5 * (lo + hi) * bnd : 0.0;
-      if (lane == 0) scal[4] = bnd;
-      __syncwarp();
-      // inverse iteration for both vectors in lockstep lanes 0 and 1
-      if (lane < 2 && lane < J) {
-        double* z = lane ? z2 : z1;
-        for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + lane, i);
-        double* w0 = tw + lane * 4 * m;
-        inverse_iteration(ee, m, scal[lane], z, w0, w0 + m, w0 + 2 * m, w0 + 3 * m, piv + lane * m,
-                          kEps * bnd + 1e-300);
-      }
-      __syncwarp();
-      if (lane == 0 && J >= 2) {          // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
+    }
+    __syncwarp();
+    if (lane < 2 && lane < J) {        // inverse iteration, lanes 0 and 1 in lockstep
+      double* z = lane ? z2 : z1;
+      for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + lane, i);
+      double* w0 = tw + lane * 4 * m;
+      inverse_iteration(ee, m, scal[lane], z, w0, w0 + m, w0 + 2 * m, w0 + 3 * m, piv + lane * m,
+                        kEps * bnd + 1e-300);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      if (J >= 2) {                    // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
         double dt = 0.0;
         for (int i = 0; i < m; ++i) dt += z1[i] * z2[i];
         double nr = 0.0;
@@ -652,71 +662,52 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
         nr = 1.0 / sqrt(nr);
         for (int i = 0; i < m; ++i) z2[i] *= nr;
       }
-      if (lane == 0) {
-        // residual of the Ritz triplets: beta_J |u'_{J-1}| with ||u'|| = 1/sqrt(2)
-        const double bJ = (J < r) ? be[J] : 0.0;
-        const double r1 = bJ * fabs(z1[m - 1]) * 1.4142135623730951;
-        const double r2 = (J >= 2) ? bJ * fabs(z2[m - 1]) * 1.4142135623730951 : 0.0;
-        scal[2] = (r1 <= 1e-14 * scal[0] && r2 <= 1e-14 * scal[0]) ? 1.0 : 0.0;
-      }
+      // residuals of the Ritz triplets: beta_J |u'_{J-1}| with ||u'|| = 1/sqrt(2)
+      const double bJ = (J < r) ? be[J] : 0.0;
+      const double r1 = bJ * fabs(z1[m - 1]) * 1.4142135623730951;
+      const double r2 = (J >= 2) ? bJ * fabs(z2[m - 1]) * 1.4142135623730951 : 0.0;
+      scal[2] = (r1 <= 1e-14 * scal[0] && r2 <= 1e-14 * scal[0]) ? 1.0 : 0.0;
     }
-    __syncthreads();
+    __syncwarp();
     if (scal[2] != 0.0 || J == r) break;
-    J = r;
+    J = (J + 24 < r) ? J + 24 : r;
   }
   const int nsv = (J >= 2) ? 2 : 1;
-  // Ritz vectors: M v = sigma u with v = V v', u = U u'
-  for (int k = 0; k < nsv; ++k) {
+  // ---- Ritz vectors in M space (v = V v', u = U u'), gauge trace(A_k) >= 0
+  for (int k = 0; k < 2; ++k) {
     const double* z = k ? z2 : z1;
     double* mu = k ? mu2 : mu1;
     double* mv = k ? mv2 : mv1;
-    for (int sidx = tid; sidx < r; sidx += nt) {
+    for (int sidx = lane; sidx < r; sidx += 32) {
       double a = 0.0, b = 0.0;
-      for (int t = 0; t < J; ++t) {
-        a += z[2 * t + 1] * U[t * r + sidx];
-        b += z[2 * t] * V[t * r + sidx];
-      }
+      if (k < nsv)
+        for (int t = 0; t < J; ++t) {
+          a += z[2 * t + 1] * U[(size_t)t * r + sidx];
+          b += z[2 * t] * V[(size_t)t * r + sidx];
+        }
       mu[sidx] = a;
       mv[sidx] = b;
     }
-    const double pu = norm2_w0(mu, r, &scal[5]);
-    const double pvv = norm2_w0(mv, r, &scal[6]);
-    const double tr = sum_w0(mu, n, &scal[7]);
-    const double sgn = (tr < 0.0) ? -1.0 : 1.0;     // gauge: trace(A_k) >= 0
-    const double fu = sgn / sqrt(pu), fv = sgn / sqrt(pvv);
-    for (int sidx = tid; sidx < r; sidx += nt) {
-      mu[sidx] *= fu;
-      mv[sidx] *= fv;
+    __syncwarp();
+    if (k < nsv) {
+      const double pu = warp_norm2(mu, r), pvv = warp_norm2(mv, r);
+      double tr = 0.0;
+      for (int t = lane; t < n; t += 32) tr += mu[t];
+      tr = warp_sum(tr);
+      const double sgn = (tr < 0.0) ? -1.0 : 1.0;
+      const double fu = sgn / sqrt(pu), fv = sgn / sqrt(pvv);
+      for (int sidx = lane; sidx < r; sidx += 32) {
+        mu[sidx] *= fu;
+        mv[sidx] *= fv;
+      }
     }
-    __syncthreads();
+    __syncwarp();
   }
-  if (nsv == 1) {
-    for (int sidx = tid; sidx < r; sidx += nt) { mu2[sidx] = 0.0; mv2[sidx] = 0.0; }
-    if (tid == 0) scal[1] = 0.0;
-    __syncthreads();
-  }
-  const double s1 = scal[0], s2 = scal[1];
-
-  // ---- 5. factors A_k, B_k (n x n column-major): u = Q m_u, A_k = sqrt(s_k) mat(u)
-  // Region "big" is free now; lay out the n x n work matrices there.
-  const int ld = ld_of(n);
-  double* fA1 = big;
-  double* fB1 = fA1 + nn;
-  double* fA2 = fB1 + nn;
-  double* fB2 = fA2 + nn;
-  double* aug0 = fB2 + nn;            // n x 2n
-  double* aug1 = aug0 + 2 * nn;       // n x 2n
-  double* H1 = aug1 + 2 * nn;         // n x ld
-  double* H2 = H1 + n * ld;
-  double* Qa = H2 + n * ld;
-  double* Qb = Qa + n * ld;
-  double* facv = Qb + n * ld;         // 2n + 2
-  double* vb0 = facv + 2 * n + 2;     // 32
-  double* vb1 = vb0 + 32;             // 32
-  __syncthreads();
+  const double s1 = scal[0], s2 = (nsv == 2) ? scal[1] : 0.0;
+  // ---- factors A_k, B_k (n x n column-major): u = Q m_u, A_k = sqrt(s_k) mat(u)
   {
     const double r1 = sqrt(s1), r2 = sqrt(s2);
-    for (int q = tid; q < 4 * nn; q += nt) {
+    for (int q = lane; q < 4 * nn; q += 32) {
       const int which = q / nn, idx = q % nn;
       const int a = idx % n, b = idx / n;
       const double* mvec = (which == 0) ? mu1 : (which == 1) ? mv1 : (which == 2) ? mu2 : mv2;
@@ -725,44 +716,62 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
         val = mvec[a];
       } else {
         const int o = b * (n - 1) + (a > b ? a - 1 : a);
-        double s = 0.0;
-        for (int t = 0; t < rz; ++t) s += Qo[(size_t)t * Ro + o] * mvec[n + t];
-        val = s;
+        double sv = 0.0;
+        for (int t = 0; t < rz; ++t) sv += __ldg(A.Qo + (size_t)t * Ro + o) * mvec[n + t];
+        val = sv;
       }
       const double f = (which < 2) ? r1 : r2;
-      double* dst = (which == 0) ? fA1 : (which == 1) ? fB1 : (which == 2) ? fA2 : fB2;
-      dst[idx] = f * val;
+      double* dst = (which == 0) ? A.A1 : (which == 1) ? A.B1 : (which == 2) ? A.A2 : A.B2;
+      dst[base + idx] = f * val;
     }
   }
-  __syncthreads();
-  for (int q = tid; q < nn; q += nt) {
-    out.A1[base + q] = fA1[q];
-    out.B1[base + q] = fB1[q];
-    out.A2[base + q] = fA2[q];
-    out.B2[base + q] = fB2[q];
+  if (lane == 0) {
+    A.sigma[2 * e] = s1;
+    A.sigma[2 * e + 1] = s2;
+    atomic_min_double(&A.st->min_sigma_ratio, (s1 > 0.0) ? s2 / s1 : 0.0);
   }
-  if (tid == 0) {
-    out.sigma[2 * e] = s1;
-    out.sigma[2 * e + 1] = s2;
-  }
+}
 
-  // ---- 6. factors to invert, inverses, C_1 and C_2
-  // The paper inverts A_2 and B_1 (Sec. 4.2).  A rank-2 Kronecker sum is
-  // unchanged by A_2 -> A_2 + alpha A_1, B_1 -> B_1 - alpha B_2, and A_2 alone
-  // can be numerically singular while P is well conditioned, so alpha is taken
-  // from a short list (alpha = t ||A_2|| / ||A_1||, t = 0 first) to minimise
-  // cond_1(A_2 + alpha A_1) cond_1(B_1 - alpha B_2).  Rank-1 blocks invert A_1, B_1.
+// ---- k_invert_w --------------------------------------------------------------
+struct InvArgs {
+  int n;
+  int64_t E;
+  const double *sigma, *A1, *B1, *A2, *B2;
+  double *LAi, *LBi, *C1, *C2, *cond;   // LAi/LBi/C1/C2 staged in the SA/SB/T1/T2 regions
+  int32_t* flags;
+  DevStatus* st;
+};
+
+// The paper inverts A_2 and B_1 (Sec. 4.2).  A rank-2 Kronecker sum is unchanged by
+// A_2 -> A_2 + alpha A_1, B_1 -> B_1 - alpha B_2, and A_2 alone can be numerically
+// singular while P is well conditioned, so alpha is taken from a short list
+// (alpha = t ||A_2|| / ||A_1||, t = 0 first) to minimise cond_1(L_A) cond_1(L_B),
+// stopping at the first pair below 1e3.  Rank-1 blocks invert A_1 and B_1.
+__global__ void __launch_bounds__(64) k_invert_w(InvArgs A) {
+  extern __shared__ double smi[];
+  const int n = A.n, nn = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= A.E) return;
+  double* aug0 = smi + (size_t)warp * (4 * nn + 2 * n + 8);
+  double* aug1 = aug0 + 2 * nn;
+  double* fac = aug1 + 2 * nn;
+  const int64_t base = e * nn;
+  const double* A1 = A.A1 + base;
+  const double* A2 = A.A2 + base;
+  const double* B1 = A.B1 + base;
+  const double* B2 = A.B2 + base;
+  const double s1 = A.sigma[2 * e], s2 = A.sigma[2 * e + 1];
   const bool rank1 = !(s2 > 1e-14 * s1);
-  const int mode = rank1 ? 2 : 0;
-  const double tlist[7] = {0.0, 0.25, -0.25, 1.0, -1.0, 4.0, -4.0};
   double nA1 = 0.0, nA2 = 0.0;
-  for (int q = tid; q < nn; q += nt) {
-    nA1 += fA1[q] * fA1[q];
-    nA2 += fA2[q] * fA2[q];
+  for (int q = lane; q < nn; q += 32) {
+    nA1 += A1[q] * A1[q];
+    nA2 += A2[q] * A2[q];
   }
-  nA1 = block_sum(nA1, red);
-  nA2 = block_sum(nA2, red);
+  nA1 = warp_sum(nA1);
+  nA2 = warp_sum(nA2);
   const double ascale = (nA1 > 0.0) ? sqrt(nA2 / nA1) : 0.0;
+  const double tlist[7] = {0.0, 0.25, -0.25, 1.0, -1.0, 4.0, -4.0};
   double best = INFINITY, alpha = 0.0;
   int best_i = 0, last_i = -1;
   const int ncand = rank1 ? 1 : 7;
@@ -770,44 +779,30 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
     int use;
     if (ci < ncand) {
       use = ci;
-    } else {                      // final pass: redo the best candidate if needed
+    } else {
       if (best_i == last_i) break;
       use = best_i;
     }
     const double al = rank1 ? 0.0 : tlist[use] * ascale;
-    for (int q = tid; q < 2 * nn; q += nt) {
+    for (int q = lane; q < 2 * nn; q += 32) {
       const int c = q / n, rr = q % n;
       double va, vb;
       if (c < n) {
         const int idx = rr + n * c;
-        va = rank1 ? fA1[idx] : fA2[idx] + al * fA1[idx];
-        vb = rank1 ? fB1[idx] : fB1[idx] - al * fB2[idx];
+        va = rank1 ? A1[idx] : A2[idx] + al * A1[idx];
+        vb = rank1 ? B1[idx] : B1[idx] - al * B2[idx];
       } else {
         va = vb = (rr == c - n) ? 1.0 : 0.0;
       }
       aug0[q] = va;
       aug1[q] = vb;
     }
-    if (tid < 2) ish[2 + tid] = 0;
-    __syncthreads();
-    if (tid < 64) {     // 1-norms of the matrices before elimination (warp 0: A, warp 1: B)
-      const double nv = norm1_warp((tid >> 5) ? aug1 : aug0, n);
-      if ((tid & 31) == 0) scal[6 + (tid >> 5)] = nv;
-    }
-    __syncthreads();
-    gauss_jordan2(aug0, aug1, n, ish, facv, ish + 2);
-    if (tid < 64) {
-      const double ni = norm1_warp((tid >> 5) ? aug1 + nn : aug0 + nn, n);
-      if ((tid & 31) == 0) facv[2 * n + (tid >> 5)] = ni;   // scratch after elimination
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double cp = scal[6] * facv[2 * n] * scal[7] * facv[2 * n + 1];
-      if (ish[2] || ish[3] || !(cp < 1e300)) cp = INFINITY;
-      scal[5] = cp;
-    }
-    __syncthreads();
-    const double cp = scal[5];
+    __syncwarp();
+    const double na = norm1_warp(aug0, n), nb = norm1_warp(aug1, n);
+    const bool sa = warp_gauss_jordan(aug0, n, fac);
+    const bool sb = warp_gauss_jordan(aug1, n, fac);
+    double cp = na * norm1_warp(aug0 + nn, n) * nb * norm1_warp(aug1 + nn, n);
+    if (sa || sb || !(cp < 1e300)) cp = INFINITY;
     last_i = use;
     if (ci < ncand && cp < best) {
       best = cp;
@@ -818,112 +813,206 @@ k_build_2d(const Tables* T, int n, int rz, int nx, int ny, double h,
       best_i = use;
       break;
     }
-    __syncthreads();
+    __syncwarp();
   }
   const double cond = best;
   const int sing = !(cond <= 1e14);
   const bool shifted = (alpha != 0.0);
-  // C1 = LA^-1 A1 into H1, C2 = LB^-1 B2 into H2 (rank-1: C1 = 0, C2 = 0)
-  {
-    const double* LAi = aug0 + nn;
-    const double* LBi = aug1 + nn;
-    for (int q = tid; q < 2 * nn; q += nt) {
-      const int which = q / nn, idx = q % nn;
-      const int rr = idx % n, c = idx / n;
-      double s = 0.0;
-      if (mode != 2) {
-        const double* Li = which ? LBi : LAi;
-        const double* R = which ? fB2 : fA1;
-        for (int k = 0; k < n; ++k) s += Li[rr + n * k] * R[k + n * c];
+  const double* LAi = aug0 + nn;
+  const double* LBi = aug1 + nn;
+  for (int q = lane; q < nn; q += 32) {
+    const int rr = q % n, c = q / n;
+    double sa = 0.0, sb = 0.0;
+    if (!rank1)
+      for (int k = 0; k < n; ++k) {
+        sa += LAi[rr + n * k] * A1[k + n * c];
+        sb += LBi[rr + n * k] * B2[k + n * c];
       }
-      (which ? H2 : H1)[rr + ld * c] = s;
-    }
+    A.C1[base + q] = sa;
+    A.C2[base + q] = sb;
+    A.LAi[base + q] = LAi[q];
+    A.LBi[base + q] = LBi[q];
   }
-  __syncthreads();
-  // ---- 7. real Schur forms (warp 0: C1, warp 1: C2)
-  const int warp = tid >> 5;
-  if (warp < 2) {
-    const bool ok = warp_real_schur(warp ? H2 : H1, warp ? Qb : Qa, n, ld, warp ? vb1 : vb0);
-    if ((tid & 31) == 0 && !ok) ish[4 + warp] = 1;
-  }
-  __syncthreads();
-  const bool schur_fail = ish[4] || ish[5];
-  if (mode == 2) {       // P = A1 (x) B1: T2 Y + Y T1^T = C with T1 = 0, T2 = I
-    for (int q = tid; q < nn; q += nt) {
-      const int rr = q % n, c = q / n;
-      H2[rr + ld * c] = (rr == c) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-  }
-  // ---- 8. S_A = Q1^T LA^-1, S_B = Q2^T LB^-1; outputs (column-major)
-  {
-    const double* LAi = aug0 + nn;
-    const double* LBi = aug1 + nn;
-    for (int q = tid; q < 2 * nn; q += nt) {
-      const int which = q / nn, idx = q % nn;
-      const int rr = idx % n, c = idx / n;
-      const double* Qm = which ? Qb : Qa;
-      const double* Li = which ? LBi : LAi;
-      double s = 0.0;
-      for (int k = 0; k < n; ++k) s += Qm[k + ld * rr] * Li[k + n * c];
-      (which ? out.SB : out.SA)[base + idx] = s;
-      (which ? out.Q2 : out.Q1)[base + idx] = Qm[rr + ld * c];
-      (which ? out.T2 : out.T1)[base + idx] = (which ? H2 : H1)[rr + ld * c];
-    }
-  }
-  if (tid == 0) {
-    uint32_t m1 = 0, m2 = 0;
-    for (int i = 0; i + 1 < n; ++i) {
-      if (H1[(i + 1) + ld * i] != 0.0) m1 |= 1u << i;
-      if (H2[(i + 1) + ld * i] != 0.0) m2 |= 1u << i;
-    }
-    out.masks[2 * e] = m1;
-    out.masks[2 * e + 1] = m2;
+  if (lane == 0) {
     int fl = 0;
     if (shifted) fl |= 1;
-    if (mode == 2) fl |= 2;
-    if (schur_fail) fl |= 4;
+    if (rank1) fl |= 2;
     if (sing) fl |= 8;
-    out.flags[e] = fl;
-    out.cond[e] = cond;
-    if (shifted) atomicAdd(&out.st->build_shifted, 1);
-    if (mode == 2) atomicAdd(&out.st->build_rank1, 1);
-    if (schur_fail) atomicAdd(&out.st->build_schur_fail, 1);
-    if (sing) atomicAdd(&out.st->build_singular, 1);
-    if (cond < 1e300) atomic_max_double(&out.st->max_cond, cond);
-    atomic_min_double(&out.st->min_sigma_ratio, (s1 > 0.0) ? s2 / s1 : 0.0);
+    A.flags[e] = fl;
+    A.cond[e] = cond;
+    if (shifted) atomicAdd(&A.st->build_shifted, 1);
+    if (rank1) atomicAdd(&A.st->build_rank1, 1);
+    if (sing) atomicAdd(&A.st->build_singular, 1);
+    if (cond < 1e300) atomic_max_double(&A.st->max_cond, cond);
+  }
+}
+
+// ---- k_schur_w: real Schur form of C (staged in T1 / T2), one warp per matrix
+__global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, double* T1, double* T2,
+                                                 double* Q1, double* Q2, uint32_t* masks,
+                                                 int32_t* flags, DevStatus* st) {
+  extern __shared__ double sms[];
+  const int nn = n * n, ld = ld_of(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mtx = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (mtx >= 2 * E) return;
+  const int64_t e = mtx >> 1;
+  const int which = (int)(mtx & 1);
+  double* H = sms + (size_t)warp * (2 * n * ld + 32);
+  double* Q = H + n * ld;
+  double* vb = Q + n * ld;
+  double* Tg = (which ? T2 : T1) + e * nn;
+  double* Qg = (which ? Q2 : Q1) + e * nn;
+  const bool rank1 = (flags[e] & 2) != 0;
+  for (int q = lane; q < nn; q += 32) {
+    const int rr = q % n, c = q / n;
+    H[rr + ld * c] = rank1 ? ((which && rr == c) ? 1.0 : 0.0) : Tg[q];
+  }
+  __syncwarp();
+  bool ok = true;
+  if (rank1) {     // P = A1 (x) B1: T1 = 0, T2 = I, Q = I
+    for (int q = lane; q < nn; q += 32) {
+      const int rr = q % n, c = q / n;
+      Q[rr + ld * c] = (rr == c) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+  } else {
+    ok = warp_real_schur(H, Q, n, ld, vb);
+  }
+  for (int q = lane; q < nn; q += 32) {
+    const int rr = q % n, c = q / n;
+    Tg[q] = H[rr + ld * c];
+    Qg[q] = Q[rr + ld * c];
+  }
+  if (lane == 0) {
+    uint32_t m = 0;
+    for (int i = 0; i + 1 < n; ++i)
+      if (H[(i + 1) + ld * i] != 0.0) m |= 1u << i;
+    masks[2 * e + which] = m;
+    if (!ok) {
+      atomicOr(reinterpret_cast<int*>(flags + e), 4);
+      atomicAdd(&st->build_schur_fail, 1);
+    }
+  }
+}
+
+// ---- k_final_w: S_A = Q1^T L_A^-1, S_B = Q2^T L_B^-1 (in place over the staged inverses)
+__global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, double* SA, double* SB,
+                                                 const double* Q1, const double* Q2) {
+  extern __shared__ double smf[];
+  const int nn = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mtx = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (mtx >= 2 * E) return;
+  const int64_t e = mtx >> 1;
+  const int which = (int)(mtx & 1);
+  double* Qs = smf + (size_t)warp * 2 * nn;
+  double* Ls = Qs + nn;
+  double* S = (which ? SB : SA) + e * nn;
+  const double* Qg = (which ? Q2 : Q1) + e * nn;
+  for (int q = lane; q < nn; q += 32) {
+    Qs[q] = Qg[q];
+    Ls[q] = S[q];
+  }
+  __syncwarp();
+  for (int q = lane; q < nn; q += 32) {
+    const int rr = q % n, c = q / n;
+    double sv = 0.0;
+    for (int k = 0; k < n; ++k) sv += Qs[k + n * rr] * Ls[k + n * c];
+    S[q] = sv;
   }
 }
 
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
-  const int n = c->n;
-  const size_t smem = build_smem_layout(n, c->rz).total_bytes;
-  cudaError_t err = cudaFuncSetAttribute(k_build_2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-  if (err != cudaSuccess) return err;
-  BuildOut o;
-  o.sigma = c->p<double>(c->L.sigma);
-  o.A1 = c->p<double>(c->L.fA1);
-  o.B1 = c->p<double>(c->L.fB1);
-  o.A2 = c->p<double>(c->L.fA2);
-  o.B2 = c->p<double>(c->L.fB2);
-  o.SA = c->p<double>(c->L.fSA);
-  o.SB = c->p<double>(c->L.fSB);
-  o.Q1 = c->p<double>(c->L.fQ1);
-  o.Q2 = c->p<double>(c->L.fQ2);
-  o.T1 = c->p<double>(c->L.fT1);
-  o.T2 = c->p<double>(c->L.fT2);
-  o.cond = c->p<double>(c->L.fSC);
-  o.flags = c->p<int32_t>(c->L.flags);
-  o.masks = c->p<uint32_t>(c->L.masks);
-  o.st = c->p<DevStatus>(c->L.status);
-  k_build_2d<<<(unsigned)c->E, kBuildThreads, smem, s>>>(
-      c->p<Tables>(c->L.tables), n, c->rz, c->prob.nel[0], c->prob.nel[1], c->prob.h,
-      c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx),
-      c->p<double>(c->L.sy), c->p<double>(c->L.zd), c->p<double>(c->L.rz),
-      c->p<double>(c->L.qo), o);
-  count_launch();
-  return cudaGetLastError();
+  const int n = c->n, rz = c->rz, nn = n * n;
+  const int64_t E = c->E;
+  DevStatus* st = c->p<DevStatus>(c->L.status);
+  // 1. KSVD
+  KsvdArgs ka;
+  ka.T = c->p<Tables>(c->L.tables);
+  ka.n = n;
+  ka.rz = rz;
+  ka.nx = c->prob.nel[0];
+  ka.ny = c->prob.nel[1];
+  ka.E = E;
+  ka.h = c->prob.h;
+  ka.cx = c->p<double>(c->L.cx);
+  ka.cy = c->p<double>(c->L.cy);
+  ka.sx = c->p<double>(c->L.sx);
+  ka.sy = c->p<double>(c->L.sy);
+  ka.Zd = c->p<double>(c->L.zd);
+  ka.Rz = c->p<double>(c->L.rz);
+  ka.Qo = c->p<double>(c->L.qo);
+  ka.scr = c->p<double>(c->L.bscr);
+  ka.iscr = c->p<int>(c->L.biscr);
+  ka.sigma = c->p<double>(c->L.sigma);
+  ka.A1 = c->p<double>(c->L.fA1);
+  ka.B1 = c->p<double>(c->L.fB1);
+  ka.A2 = c->p<double>(c->L.fA2);
+  ka.B2 = c->p<double>(c->L.fB2);
+  ka.st = st;
+  {
+    const int warps = 4;
+    const size_t smem = (size_t)warps * ksvd_smem(n, rz).total * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_ksvd_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    k_ksvd_w<<<(unsigned)((E + warps - 1) / warps), warps * 32, smem, s>>>(ka);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  // 2. inverses and C products
+  InvArgs ia;
+  ia.n = n;
+  ia.E = E;
+  ia.sigma = ka.sigma;
+  ia.A1 = ka.A1;
+  ia.B1 = ka.B1;
+  ia.A2 = ka.A2;
+  ia.B2 = ka.B2;
+  ia.LAi = c->p<double>(c->L.fSA);
+  ia.LBi = c->p<double>(c->L.fSB);
+  ia.C1 = c->p<double>(c->L.fT1);
+  ia.C2 = c->p<double>(c->L.fT2);
+  ia.cond = c->p<double>(c->L.fSC);
+  ia.flags = c->p<int32_t>(c->L.flags);
+  ia.st = st;
+  {
+    const int warps = 2;
+    const size_t smem = (size_t)warps * (4 * nn + 2 * n + 8) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_invert_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    k_invert_w<<<(unsigned)((E + warps - 1) / warps), warps * 32, smem, s>>>(ia);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  // 3. real Schur forms
+  {
+    const int warps = 4, ld = ld_of(n);
+    const size_t smem = (size_t)warps * (2 * n * ld + 32) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_schur_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    k_schur_w<<<(unsigned)((2 * E + warps - 1) / warps), warps * 32, smem, s>>>(
+        n, E, c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), c->p<double>(c->L.fQ1),
+        c->p<double>(c->L.fQ2), c->p<uint32_t>(c->L.masks), c->p<int32_t>(c->L.flags), st);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  // 4. S_A, S_B
+  {
+    const int warps = 4;
+    const size_t smem = (size_t)warps * 2 * nn * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_final_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    k_final_w<<<(unsigned)((2 * E + warps - 1) / warps), warps * 32, smem, s>>>(
+        n, E, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB), c->p<double>(c->L.fQ1),
+        c->p<double>(c->L.fQ2));
+    count_launch();
+    return cudaGetLastError();
+  }
 }
 
 }  // namespace tpp

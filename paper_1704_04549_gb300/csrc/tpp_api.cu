@@ -141,6 +141,11 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.fSC = take((size_t)E * 8 * ((d == 3) ? n * n : 1));
   L.flags = take((size_t)E * 4);
   L.masks = take((size_t)E * 2 * 4);
+  {
+    const size_t r = (size_t)n + rz;
+    L.bscr = (d == 2) ? take((size_t)E * (2 * r * r + 16 * r) * 8) : 0;
+    L.biscr = (d == 2) ? take((size_t)E * 4 * r * 4) : 0;
+  }
   L.f32 = (features & TPP_FEAT_MIXED) ? take((size_t)7 * E * n * n * 4) : 0;
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
   L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
