@@ -313,11 +313,10 @@ __device__ void atomic_min_double(double* addr, double v) {
 //   k_final_w    S_A = Q_1^T L_A^-1, S_B = Q_2^T L_B^-1              (a5)
 
 struct KsvdArgs {
-  const Tables* T;
-  int n, rz, nx, ny;
+  int n, rz;
   int64_t E;
-  double h;
-  const double *cx, *cy, *sx, *sy, *Zd, *Rz, *Qo;
+  const double* kco;   // per block: Cx ((n+2) x n), Cy ((n+2) x n), Dg (n x n)
+  const double *Zd, *Rz, *Qo;
   double* scr;     // per element: U (r*r), V (r*r), tridiagonal work (16 r)
   int* iscr;       // per element: 4 r pivot flags
   double *sigma, *A1, *B1, *A2, *B2;
@@ -326,15 +325,16 @@ struct KsvdArgs {
 
 // shared-memory layout of one warp of k_ksvd_w (offsets in doubles)
 struct KsvdSmem {
-  int cx, cy, vs, ps, ta, tb, cf, al, be, ee, e2s, z1, z2, mu1, mv1, mu2, mv2, scal, total;
+  int cx, cy, dg, vs, ps, ta, tb, cf, al, be, ee, e2s, z1, z2, mu1, mv1, mu2, mv2, scal, total;
 };
 
 __host__ __device__ inline KsvdSmem ksvd_smem(int n, int rz) {
-  const int nc = n + 3, r = n + rz;
+  const int nc = n + 2, r = n + rz;
   KsvdSmem L;
   int o = 0;
   L.cx = o; o += nc * n;
   L.cy = o; o += nc * n;
+  L.dg = o; o += n * n;
   L.vs = o; o += r;
   L.ps = o; o += r;
   L.ta = o; o += nc;
@@ -357,12 +357,13 @@ __host__ __device__ inline KsvdSmem ksvd_smem(int n, int rz) {
 
 namespace {
 
-// out = M v for the core matrix M = [[Cx^T Zd^T + Zd Cy, Cx^T Rz^T], [Rz Cy, 0]]
-// without forming it: top = Cx^T (Zd^T v1 + Rz^T v2) + Zd (Cy v1), bottom = Rz (Cy v1).
-__device__ void warp_mv_M(const double* Cx, const double* Cy, const double* __restrict__ Zd,
-                          const double* __restrict__ Rz, int n, int rz, const double* v,
-                          double* out, double* ta, double* tb) {
-  const int nc = n + 3, lane = threadIdx.x & 31;
+// out = M v for the core M = [[Cx^T Zd^T + Zd Cy + Dg^T, Cx^T Rz^T], [Rz Cy, 0]]
+// without forming it: top = Cx^T (Zd^T v1 + Rz^T v2) + Zd (Cy v1) + Dg^T v1,
+// bottom = Rz (Cy v1).  Dg[q + n p] is the block's diagonal at (i = q, j = p).
+__device__ void warp_mv_M(const double* Cx, const double* Cy, const double* Dg,
+                          const double* __restrict__ Zd, const double* __restrict__ Rz, int n,
+                          int rz, const double* v, double* out, double* ta, double* tb) {
+  const int nc = n + 2, lane = threadIdx.x & 31;
   for (int c = lane; c < nc; c += 32) {
     double a = 0.0, b = 0.0;
     for (int q = 0; q < n; ++q) {
@@ -377,6 +378,7 @@ __device__ void warp_mv_M(const double* Cx, const double* Cy, const double* __re
   for (int p = lane; p < n; p += 32) {
     double sv = 0.0;
     for (int c = 0; c < nc; ++c) sv += Cx[c * n + p] * tb[c] + __ldg(Zd + p * nc + c) * ta[c];
+    for (int q = 0; q < n; ++q) sv += Dg[q + n * p] * v[q];
     out[p] = sv;
   }
   for (int t = lane; t < rz; t += 32) {
@@ -387,11 +389,11 @@ __device__ void warp_mv_M(const double* Cx, const double* Cy, const double* __re
   __syncwarp();
 }
 
-// out = M^T u: top = Zd (Cx u1) + Cy^T (Zd^T u1 + Rz^T u2), bottom = Rz (Cx u1).
-__device__ void warp_mv_MT(const double* Cx, const double* Cy, const double* __restrict__ Zd,
-                           const double* __restrict__ Rz, int n, int rz, const double* u,
-                           double* out, double* ta, double* tb) {
-  const int nc = n + 3, lane = threadIdx.x & 31;
+// out = M^T u: top = Zd (Cx u1) + Cy^T (Zd^T u1 + Rz^T u2) + Dg u1, bottom = Rz (Cx u1).
+__device__ void warp_mv_MT(const double* Cx, const double* Cy, const double* Dg,
+                           const double* __restrict__ Zd, const double* __restrict__ Rz, int n,
+                           int rz, const double* u, double* out, double* ta, double* tb) {
+  const int nc = n + 2, lane = threadIdx.x & 31;
   for (int c = lane; c < nc; c += 32) {
     double a = 0.0, b = 0.0;
     for (int p = 0; p < n; ++p) {
@@ -406,6 +408,7 @@ __device__ void warp_mv_MT(const double* Cx, const double* Cy, const double* __r
   for (int q = lane; q < n; q += 32) {
     double sv = 0.0;
     for (int c = 0; c < nc; ++c) sv += __ldg(Zd + q * nc + c) * ta[c] + Cy[c * n + q] * tb[c];
+    for (int p = 0; p < n; ++p) sv += Dg[q + n * p] * u[p];
     out[q] = sv;
   }
   for (int t = lane; t < rz; t += 32) {
@@ -494,13 +497,13 @@ __device__ bool warp_gauss_jordan(double* a, int n, double* fac) {
 // ---- k_ksvd_w ---------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   extern __shared__ double smk[];
-  const int n = A.n, rz = A.rz, nc = n + 3, r = n + rz, nn = n * n, Ro = nn - n;
+  const int n = A.n, rz = A.rz, nc = n + 2, r = n + rz, nn = n * n, Ro = nn - n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (e >= A.E) return;                                  // whole warp leaves together
   const KsvdSmem L = ksvd_smem(n, rz);
   double* sm = smk + (size_t)warp * L.total;
-  double *Cx = sm + L.cx, *Cy = sm + L.cy, *vs = sm + L.vs, *ps = sm + L.ps;
+  double *Cx = sm + L.cx, *Cy = sm + L.cy, *Dg = sm + L.dg, *vs = sm + L.vs, *ps = sm + L.ps;
   double *ta = sm + L.ta, *tb = sm + L.tb, *cf = sm + L.cf, *al = sm + L.al, *be = sm + L.be;
   double *ee = sm + L.ee, *e2s = sm + L.e2s, *z1 = sm + L.z1, *z2 = sm + L.z2;
   double *mu1 = sm + L.mu1, *mv1 = sm + L.mv1, *mu2 = sm + L.mu2, *mv2 = sm + L.mv2;
@@ -509,38 +512,28 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   double* V = U + (size_t)r * r;
   double* tw = V + (size_t)r * r;
   int* piv = A.iscr + (size_t)e * 4 * r;
-  const int ex = (int)(e % A.nx), ey = (int)(e / A.nx);
-  const int64_t eR = ey * (int64_t)A.nx + (ex + 1) % A.nx;
-  const int64_t eT = ((ey + 1) % A.ny) * (int64_t)A.nx + ex;
   const int64_t base = e * nn;
 
-  // ---- coefficients of the rearranged block (flux Jacobians, Sec. 3.4.1)
-  for (int q = lane; q < nn; q += 32) {
-    const int a = q % n, b = q / n;
-    Cx[a * n + b] = A.cx[base + q];    // Cx[c = x node][j]
-    Cy[b * n + a] = A.cy[base + q];    // Cy[c = y node][i]
-  }
-  for (int j = lane; j < n; j += 32) {
-    Cx[n * n + j] = fmax(A.sx[eR * n + j], 0.0);
-    Cx[(n + 1) * n + j] = fmax(-A.sx[e * n + j], 0.0);
-    Cx[(n + 2) * n + j] = A.h * A.h * A.T->w[j];
-    Cy[n * n + j] = fmax(A.sy[eT * n + j], 0.0);
-    Cy[(n + 1) * n + j] = fmax(-A.sy[e * n + j], 0.0);
-    Cy[(n + 2) * n + j] = 0.0;
+  // ---- coefficients of the rearranged block
+  {
+    const double* src = A.kco + (size_t)e * (2 * nc * n + nn);
+    for (int q = lane; q < 2 * nc * n + nn; q += 32) Cx[q] = src[q];   // Cx, Cy, Dg contiguous
   }
   __syncwarp();
   // scale of M (Frobenius norm of A~) for the breakdown tolerance: ||M||_F
   // is bounded by the coefficient norms times the basis norms; use the
   // cheaper bound sqrt(sum Cx^2 + sum Cy^2) * max(||Zd||, ||Rz||) (only the
   // invariant-subspace test uses it)
-  double cs2 = 0.0;
+  double cs2 = 0.0, dg2 = 0.0;
   for (int q = lane; q < 2 * nc * n; q += 32) cs2 += Cx[q] * Cx[q];
+  for (int q = lane; q < nn; q += 32) dg2 += Dg[q] * Dg[q];
   cs2 = warp_sum(cs2);
+  dg2 = warp_sum(dg2);
   double zs2 = 0.0;
   for (int q = lane; q < n * nc; q += 32) zs2 += __ldg(A.Zd + q) * __ldg(A.Zd + q);
   for (int q = lane; q < rz * nc; q += 32) zs2 += __ldg(A.Rz + q) * __ldg(A.Rz + q);
   zs2 = warp_sum(zs2);
-  const double tol = 1e-12 * sqrt(cs2 * zs2);
+  const double tol = 1e-12 * (sqrt(cs2 * zs2) + sqrt(dg2));
 
   // ---- Golub-Kahan-Lanczos with full reorthogonalisation (Alg. lanczos)
   for (int t = lane; t < r; t += 32) vs[t] = splitmix_unit(1, t);
@@ -559,7 +552,7 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   for (int pass = 0; pass < 3; ++pass) {
     for (int j = jdone; j < J; ++j) {
       // p = M v_j - beta_j u_{j-1}      (vs holds v_j)
-      warp_mv_M(Cx, Cy, A.Zd, A.Rz, n, rz, vs, ps, ta, tb);
+      warp_mv_M(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, vs, ps, ta, tb);
       if (j > 0)
         for (int t = lane; t < r; t += 32) ps[t] -= be[j] * U[(size_t)(j - 1) * r + t];
       __syncwarp();
@@ -581,7 +574,7 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
       __syncwarp();
       if (j + 1 < r) {
         // q = M^T u_j - alpha_j v_j      (ps holds u_j; result into ta/tb scratch then vs)
-        warp_mv_MT(Cx, Cy, A.Zd, A.Rz, n, rz, ps, ee, ta, tb);   // ee as scratch (length >= r)
+        warp_mv_MT(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, ps, ee, ta, tb);   // ee as scratch (length >= r)
         for (int t = lane; t < r; t += 32) vs[t] = ee[t] - a * vs[t];
         __syncwarp();
         warp_reorth(vs, V, j + 1, r, cf);
@@ -923,23 +916,55 @@ __global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, double* SA, d
   }
 }
 
+// ---- k_coef_2d: KSVD coefficients of a 2D element block (flux Jacobians of
+// Sec. 3.4.1 in the basis of k_struct_qr): Cx[c][j] = cx[c + n j] (volume,
+// c < n), max(a.n, 0) on the +x and -x faces (c = n, n + 1); Cy likewise for
+// y; Dg[i + n j] = h^2 w_i w_j (mass).
+__global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, const double* cx,
+                          const double* cy, const double* sx, const double* sy, double* kco) {
+  const int nc = n + 2, nn = n * n, per = 2 * nc * n + nn;
+  const int64_t E = (int64_t)nx * ny;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E * per;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / per;
+    const int q = (int)(g % per);
+    const int ex = (int)(e % nx), ey = (int)(e / nx);
+    double v;
+    if (q < 2 * nc * n) {
+      const int which = q / (nc * n), rem = q % (nc * n);
+      const int c = rem / n, j = rem % n;
+      if (which == 0) {          // x-part, j = y index
+        if (c < n) v = cx[e * nn + c + n * j];
+        else if (c == n) v = fmax(sx[((int64_t)ey * nx + (ex + 1) % nx) * n + j], 0.0);
+        else v = fmax(-sx[e * n + j], 0.0);
+      } else {                   // y-part, j = x index
+        if (c < n) v = cy[e * nn + j + n * c];
+        else if (c == n) v = fmax(sy[((int64_t)((ey + 1) % ny) * nx + ex) * n + j], 0.0);
+        else v = fmax(-sy[e * n + j], 0.0);
+      }
+    } else {
+      const int d = q - 2 * nc * n, i = d % n, j = d / n;
+      v = h * h * T->w[i] * T->w[j];
+    }
+    kco[g] = v;
+  }
+}
+
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
   const int n = c->n, rz = c->rz, nn = n * n;
   const int64_t E = c->E;
   DevStatus* st = c->p<DevStatus>(c->L.status);
   // 1. KSVD
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1],
+                                    c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                    c->p<double>(c->L.sx), c->p<double>(c->L.sy),
+                                    c->p<double>(c->L.kco));
+  count_launch();
   KsvdArgs ka;
-  ka.T = c->p<Tables>(c->L.tables);
   ka.n = n;
   ka.rz = rz;
-  ka.nx = c->prob.nel[0];
-  ka.ny = c->prob.nel[1];
   ka.E = E;
-  ka.h = c->prob.h;
-  ka.cx = c->p<double>(c->L.cx);
-  ka.cy = c->p<double>(c->L.cy);
-  ka.sx = c->p<double>(c->L.sx);
-  ka.sy = c->p<double>(c->L.sy);
+  ka.kco = c->p<double>(c->L.kco);
   ka.Zd = c->p<double>(c->L.zd);
   ka.Rz = c->p<double>(c->L.rz);
   ka.Qo = c->p<double>(c->L.qo);

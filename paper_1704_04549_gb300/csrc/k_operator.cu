@@ -86,18 +86,19 @@ cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s) {
 // Element-independent basis of the 2D rearranged block.  With collocated
 // quadrature every x-term of the diagonal block carries delta_{l j} and every
 // y-term delta_{k i}, so (Sec. 4.1 rearrangement, row j + n l, column i + n k)
-//     A~ = E Cx^T Z^T + Z Cy E^T,
-// E selecting the n "diagonal" indices d (n + 1), Cx / Cy per-element
-// coefficients, and Z (n^2 x (n + 3)) a fixed basis: vec(D^T e_c e_c^T)
-// (c < n), vec(l1 l1^T), vec(l0 l0^T), vec(diag(w)).  Householder QR of the
-// off-diagonal rows of Z gives Z = E Zd + Qo Rz and A~ = Q M Q^T with
-// Q = [E | Qo] and the small core M (Sec. 4.1: only products with A~ are
-// needed; here they collapse onto M).  One CTA.
+//     A~ = E (Cx^T Z^T + Dg^T E^T) + Z Cy E^T,
+// E selecting the n "diagonal" indices d (n + 1), Cx / Cy per-block
+// coefficients, Dg the diagonal of the block (mass and anything else on it),
+// and Z (n^2 x (n + 2)) a fixed basis: vec(D^T e_c e_c^T) (c < n),
+// vec(l1 l1^T), vec(l0 l0^T).  Householder QR of the off-diagonal rows of Z
+// gives Z = E Zd + Qo Rz and A~ = Q M Q^T with Q = [E | Qo] and the small
+// core M (only products with A~ are needed; here they collapse onto M).
+// One CTA.
 __global__ void k_struct_qr(const Tables* T, int n, double* work, double* tau, double* Zd,
                             double* Rz, double* Qo) {
   __shared__ double red[32];
-  __shared__ double sh_s[TPP_MAX_N + 3];
-  const int nc = n + 3;
+  __shared__ double sh_s[TPP_MAX_N + 2];
+  const int nc = n + 2;
   const int Ro = n * n - n;
   const int rz = Ro < nc ? Ro : nc;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -107,8 +108,7 @@ __global__ void k_struct_qr(const Tables* T, int n, double* work, double* tau, d
     double v;
     if (cc < n) v = (cc == d) ? T->D[d * n + d] : 0.0;
     else if (cc == n) v = T->l1[d] * T->l1[d];
-    else if (cc == n + 1) v = T->l0[d] * T->l0[d];
-    else v = T->w[d];
+    else v = T->l0[d] * T->l0[d];
     Zd[q] = v;
   }
   // off-diagonal rows: o -> (a, b), a != b, increasing a + n b; column-major work
@@ -118,8 +118,7 @@ __global__ void k_struct_qr(const Tables* T, int n, double* work, double* tau, d
     double v;
     if (cc < n) v = (b == cc) ? T->D[cc * n + a] : 0.0;
     else if (cc == n) v = T->l1[a] * T->l1[b];
-    else if (cc == n + 1) v = T->l0[a] * T->l0[b];
-    else v = 0.0;
+    else v = T->l0[a] * T->l0[b];
     work[q] = v;
   }
   __syncthreads();
@@ -189,7 +188,6 @@ __global__ void k_struct_qr(const Tables* T, int n, double* work, double* tau, d
 }
 
 cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s) {
-  if (c->dim != 2) return cudaSuccess;
   k_struct_qr<<<1, 1024, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->p<double>(c->L.qr_work),
                                  c->p<double>(c->L.qr_tau), c->p<double>(c->L.zd),
                                  c->p<double>(c->L.rz), c->p<double>(c->L.qo));

@@ -96,7 +96,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   const int64_t nloc = (d == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t nfl = (d == 2) ? n : (int64_t)n * n;
   const int64_t N = E * nloc;
-  const int nc = n + 3, Ro = n * n - n;
+  const int nc = n + 2, Ro = n * n - n;
   const int rz = Ro < nc ? Ro : nc;
   if (rz_out) *rz_out = rz;
   const int m = max_restart;
@@ -143,8 +143,11 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.masks = take((size_t)E * 2 * 4);
   {
     const size_t r = (size_t)n + rz;
-    L.bscr = (d == 2) ? take((size_t)E * (2 * r * r + 16 * r) * 8) : 0;
-    L.biscr = (d == 2) ? take((size_t)E * 4 * r * 4) : 0;
+    L.bscr = take((size_t)E * (2 * r * r + 16 * r) * 8);
+    L.biscr = take((size_t)E * 4 * r * 4);
+    // coefficients of the 2D-structured block fed to the KSVD (2D: the element
+    // block; 3D: the second-stage block D1): Cx, Cy ((n+2) x n each), Dg (n x n)
+    L.kco = take((size_t)E * (2 * (size_t)nc * n + (size_t)n * n) * 8);
   }
   L.f32 = (features & TPP_FEAT_MIXED) ? take((size_t)7 * E * n * n * 4) : 0;
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;

@@ -70,6 +70,7 @@ struct Layout {
   size_t fSA, fSB, fQ1, fQ2, fT1, fT2, fSC;  // fSC: 3D A1^-1 factor
   size_t flags, masks;
   size_t bscr, biscr;                  // factor-build scratch (Lanczos bases, tridiagonal work)
+  size_t kco;                          // per-block KSVD coefficients (Cx, Cy, Dg)
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
