@@ -63,7 +63,7 @@ typedef enum {
 } tpp_pc;
 
 /* Feature bits for tpp_workspace_bytes / tpp_create. */
-#define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^(2d) doubles per element for exact block Jacobi */
+#define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^4 doubles per element for exact block Jacobi (2D only) */
 #define TPP_FEAT_MIXED        2u  /* reserve float32 copies of the Kronecker apply factors */
 
 /*
@@ -73,7 +73,7 @@ typedef enum {
  *                                                  + phase[c*n_modes + m])
  * All pointers are host pointers, read during tpp_create only.
  * Mesh: element (ex, ey[, ez]) covers [ex h, (ex+1) h] x ...; periodic wrap in
- * every direction.  Limits: dim in {2, 3}; 1 <= n <= 32; nel[d] >= 1;
+ * every direction.  Limits: dim in {2, 3}; 1 <= n <= 32 (2D), 1 <= n <= 16 (3D); nel[d] >= 1;
  * h > 0; dt >= 0; 0 <= n_modes <= 64.
  */
 typedef struct {
@@ -115,6 +115,10 @@ typedef struct {
   int32_t num_schur_fail;  /* elements whose Francis iteration hit its cap */
   double max_cond;         /* largest cond_1(L_A) * cond_1(L_B) of the inverted factor pair */
   double min_sigma_ratio;  /* min over elements of sigma_2 / sigma_1 */
+  double max_cond_z;       /* 3D: largest cond_1(A1) of the first-stage z factor (0 in 2D) */
+  int32_t num_z_unconverged;  /* 3D: elements whose first-stage Lanczos hit its step cap
+                                 (the factor is still the best Ritz pair found) */
+  int32_t reserved;
 } tpp_build_report;
 
 typedef struct tpp_ctx tpp_ctx;
@@ -228,6 +232,14 @@ typedef struct {
   const double* gl_x;    /* [n] Gauss-Legendre nodes on [0, 1] */
   const double* gl_w;    /* [n] weights */
   const double* D;       /* [n*n] D[a*n + j] = phi_j'(x_a) */
+  /* 3D only (NULL in 2D).  The nested form A1 (x) (B1 (x) C1 + B2 (x) C2): the
+   * second-stage factors of the y-x block D1 sit in A1/B1/A2/B2 above with A on
+   * y and B on x, i.e. A1 = B1(3D), B1 = C1(3D), A2 = B2(3D), B2 = C2(3D); sigma
+   * then holds the top two singular values of D1's rearrangement. */
+  const double* Az;      /* [E][n*n] first-stage z factor A1 (3D), column-major */
+  const double* Azi;     /* [E][n*n] its inverse */
+  const double* sigz;    /* [E] first-stage singular value sigma_1 */
+  const int32_t* zflags; /* [E] bit0 Lanczos not converged, bit1 A1 singular or cond_1 >= 1e14 */
 } tpp_views;
 
 tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);

@@ -38,13 +38,14 @@ class GmresResult(C.Structure):
 class BuildReport(C.Structure):
     _fields_ = [("num_elem", C.c_int32), ("num_shifted", C.c_int32), ("num_rank1", C.c_int32),
                 ("num_schur_fail", C.c_int32), ("max_cond", C.c_double),
-                ("min_sigma_ratio", C.c_double)]
+                ("min_sigma_ratio", C.c_double), ("max_cond_z", C.c_double),
+                ("num_z_unconverged", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Views(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in
                 ("sigma", "A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2", "flags",
-                 "cond", "gl_x", "gl_w", "D")]
+                 "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags")]
 
 
 EXPORTS = {

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(128)
 k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ SB,
              const T* __restrict__ Q1, const T* __restrict__ Q2, const T* __restrict__ T1,
              const T* __restrict__ T2, const uint32_t* __restrict__ masks,
-             const double* __restrict__ b, double* __restrict__ x, const int32_t* skip) {
+             const double* b, double* x, const int32_t* skip, int fdiv) {
   if (skip && *skip) return;
   constexpr int EPW = 32 / NM;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -121,7 +121,11 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   int* cs = rs + NM + 1;          // column block starts (T1), NM + 1
   int* colblk = cs + NM + 1;      // block of each column, NM
   int* nbs = colblk + NM;         // nbr, nbc
+  // vector block e; its factors are those of block e / fdiv (fdiv = 1 in 2D,
+  // n in 3D where the blocks are the z slices of an element, in place)
   const int64_t g = eok ? e * nn : 0;
+  const int64_t ef = eok ? e / fdiv : 0;
+  const int64_t gf = ef * nn;
 
   // ---- B S_A^T: lane i holds row i of B
   T row[NM], acc[NM];
@@ -129,11 +133,11 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? (T)b[g + i + n * k] : (T)0;
   if (eok)
     for (int q = i; q < nn; q += NM) {
-      Fa[q] = SA[g + q];
-      Fb[q] = T1[g + q];
+      Fa[q] = SA[gf + q];
+      Fb[q] = T1[gf + q];
     }
   if (i == 0 && eok) {
-    const uint32_t m2 = masks[2 * e + 1], m1 = masks[2 * e];
+    const uint32_t m2 = masks[2 * ef + 1], m1 = masks[2 * ef];
     int nb = 0, r = 0;
     while (r < n) {
       rs[nb++] = r;
@@ -164,7 +168,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   __syncwarp(gmask);
   // ---- C = S_B W: lane i holds row i of S_B; row i of C stays in registers (acc)
 #pragma unroll
-  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? SB[g + i + n * k] : (T)0;
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? SB[gf + i + n * k] : (T)0;
 #pragma unroll
   for (int j = 0; j < NM; ++j) {
     T sacc = (T)0;
@@ -176,7 +180,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
     acc[j] = sacc;
   }
   if (eok)
-    for (int q = i; q < nn; q += NM) Fa[q] = T2[g + q];   // SA no longer needed
+    for (int q = i; q < nn; q += NM) Fa[q] = T2[gf + q];   // SA no longer needed
   __syncwarp(gmask);
 
   // ---- Sylvester T2 Y + Y T1^T = C, right-looking wavefront, rows in registers
@@ -281,7 +285,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   }
   __syncwarp(gmask);
   if (eok)
-    for (int q = i; q < nn; q += NM) Fa[q] = Q1[g + q];
+    for (int q = i; q < nn; q += NM) Fa[q] = Q1[gf + q];
   __syncwarp(gmask);
   // ---- W = Y Q1^T: lane i holds row i of Y (acc)
 #pragma unroll
@@ -302,7 +306,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   __syncwarp(gmask);
   // ---- x = Q2 W: lane i holds row i of Q2
 #pragma unroll
-  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? Q2[g + i + n * k] : (T)0;
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? Q2[gf + i + n * k] : (T)0;
   for (int j = 0; j < n; ++j) {
     T sacc = (T)0;
 #pragma unroll
@@ -315,7 +319,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
 template <typename T, int NM>
 cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, const T* Q2,
                      const T* T1, const T* T2, const uint32_t* masks, const double* b, double* x,
-                     const int32_t* skip, cudaStream_t s) {
+                     const int32_t* skip, int fdiv, cudaStream_t s) {
   constexpr int EPW = 32 / NM;
   const int warps = (NM == 32 && sizeof(T) == 8) ? 2 : 4;
   const int64_t per_block = (int64_t)warps * EPW;
@@ -326,7 +330,7 @@ cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, co
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_apply_2d_w<T, NM><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, SB, Q1, Q2, T1, T2,
-                                                                  masks, b, x, skip);
+                                                                  masks, b, x, skip, fdiv);
   count_launch();
   return cudaGetLastError();
 }
@@ -336,9 +340,13 @@ cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* 
                            const T* T1, const T* T2, const double* b, double* x,
                            const int32_t* skip, cudaStream_t s) {
   const uint32_t* masks = c->p<uint32_t>(c->L.masks);
-  if (c->n <= 8) return launch_w<T, 8>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
-  if (c->n <= 16) return launch_w<T, 16>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
-  return launch_w<T, 32>(c->n, c->E, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, s);
+  const int fdiv = (c->dim == 3) ? c->n : 1;
+  const int64_t nb = c->E * fdiv;                  // 2D blocks: elements, or z slices in 3D
+  if (c->n <= 8)
+    return launch_w<T, 8>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
+  if (c->n <= 16)
+    return launch_w<T, 16>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
+  return launch_w<T, 32>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
 }
 
 cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
@@ -356,13 +364,14 @@ cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int pr
 
 // float copies of the apply factors (SA, SB, Q1, Q2, T1, T2), rounded to nearest
 __global__ void k_to_f32(const double* SA, const double* SB, const double* Q1, const double* Q2,
-                         const double* T1, const double* T2, float* out, int64_t st) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 6 * st;
+                         const double* T1, const double* T2, const double* Azi, float* out,
+                         int64_t st, int nmat) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nmat * st;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int which = (int)(g / st);
     const int64_t i = g % st;
     const double* src = which == 0 ? SA : which == 1 ? SB : which == 2 ? Q1 : which == 3 ? Q2
-                      : which == 4 ? T1 : T2;
+                      : which == 4 ? T1 : which == 5 ? T2 : Azi;
     out[g] = __double2float_rn(src[i]);
   }
 }
@@ -372,9 +381,66 @@ cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
   k_to_f32<<<152 * 4, 256, 0, s>>>(c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
                                    c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
                                    c->p<double>(c->L.fT1), c->p<double>(c->L.fT2),
-                                   c->p<float>(c->L.f32), st);
+                                   c->dim == 3 ? c->p<double>(c->L.fAzi) : nullptr,
+                                   c->p<float>(c->L.f32), st, c->dim == 3 ? 7 : 6);
   count_launch();
   return cudaGetLastError();
+}
+
+
+// ---- 3D (Alg. 3d-apply): x = (A1^-1 (x) D1^-1) b.  The z factor acts first,
+// x~ = (A1^-1 (x) I) b, one thread per z line (i, j) of an element with the
+// line in registers; then the 2D apply of D1^-1 = (B1 (x) C1 + B2 (x) C2)^-1
+// runs in place on each z slice (n slices per element share its factors).
+template <typename T, int NZ>
+__global__ void __launch_bounds__(128)
+k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const double* __restrict__ b,
+          double* __restrict__ x, const int32_t* skip) {
+  if (skip && *skip) return;
+  __shared__ T az[4][NZ * NZ];
+  const int nn = n * n, n3 = nn * n;
+  const int sub = threadIdx.x >> 5;                      // one element per warp
+  const int64_t e = (int64_t)blockIdx.x * 4 + sub;
+  if (e >= E) return;
+  const int lane = threadIdx.x & 31;
+  for (int q = lane; q < nn; q += 32) az[sub][q] = Azi[e * nn + q];
+  __syncwarp();
+  const double* be = b + e * n3;
+  double* xe = x + e * n3;
+  for (int q = lane; q < nn; q += 32) {
+    T line[NZ];
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) line[k] = (k < n) ? (T)be[q + (int64_t)nn * k] : (T)0;
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) {
+      if (k < n) {
+        T sv = (T)0;
+#pragma unroll
+        for (int k2 = 0; k2 < NZ; ++k2)
+          if (k2 < n) sv += az[sub][k + n * k2] * line[k2];
+        xe[q + (int64_t)nn * k] = (double)sv;
+      }
+    }
+  }
+}
+
+cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,
+                            const int32_t* skip, cudaStream_t s) {
+  const int n = c->n;
+  const unsigned blocks = (unsigned)((c->E + 3) / 4);
+  if (prec == TPP_FP64) {
+    const double* azi = c->p<double>(c->L.fAzi);
+    if (n <= 8) k_apply_z<double, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    else k_apply_z<double, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+  } else {
+    const float* azi = c->p<float>(c->L.f32) + (size_t)6 * c->E * n * n;
+    if (n <= 8) k_apply_z<float, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    else k_apply_z<float, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+  }
+  count_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_apply_2d(c, x, x, prec, skip, s);
 }
 
 }  // namespace tpp

@@ -144,11 +144,4 @@ cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const 
   return cudaGetLastError();
 }
 
-// 3D entry points are declared for the nested preconditioner; not built yet.
-cudaError_t launch_build_3d(const tpp_ctx*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_apply_3d(const tpp_ctx*, const double*, double*, int, const int32_t*,
-                            cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-
 }  // namespace tpp

@@ -950,16 +950,13 @@ __global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, cons
   }
 }
 
-cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
+// KSVD of the 2D-structured blocks in kco (2D elements, or the second stage
+// of the 3D nested form), inverses, Schur forms, S_A and S_B.
+cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s) {
   const int n = c->n, rz = c->rz, nn = n * n;
   const int64_t E = c->E;
   DevStatus* st = c->p<DevStatus>(c->L.status);
   // 1. KSVD
-  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1],
-                                    c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-                                    c->p<double>(c->L.sx), c->p<double>(c->L.sy),
-                                    c->p<double>(c->L.kco));
-  count_launch();
   KsvdArgs ka;
   ka.n = n;
   ka.rz = rz;
@@ -1038,6 +1035,426 @@ cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
     count_launch();
     return cudaGetLastError();
   }
+}
+
+
+cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->prob.nel[0],
+                                    c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx),
+                                    c->p<double>(c->L.cy), c->p<double>(c->L.sx),
+                                    c->p<double>(c->L.sy), c->p<double>(c->L.kco));
+  count_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_ksvd_pipeline(c, s);
+}
+
+// ---------------------------------------------------------------------------
+// 3D nested KSVD, stage 1 (Sec. 4.3, Alg. 3d-form step 1): best rank-1
+// A ~ A1 (x) D1 of the n^3 x n^3 block, A1 on z.  With collocated quadrature
+// the rearrangement A~ (rows: z pairs (k, k'), n^2 x n^4) is E_r X1 + Y1 E_c^T:
+// row (k, k) of X1 is vec of the xy block S_k of z slice k (mass, x- and
+// y-terms), column (i, j) of Y1 is vec of the z-operator H_ij of the line
+// (i, j).  G = A~ A~^T (n^2 x n^2) is applied without forming A~:
+//   G u = E_r (P u~ + Sd (Y1^T u)) + Y1 (Sd^T u~ + Y1^T u),
+// u~ = E_r^T u, P = X1 X1^T (Gram of the slices), Sd = X1 E_c (their
+// diagonals).  P and Sd come from the per-line coefficients in the basis of
+// k_struct_qr (off-diagonal parts through Rz, Qo orthonormal), so stage 1
+// costs O(n^4) per element.  The top eigenpair of G (symmetric Lanczos with
+// full reorthogonalisation) gives sigma_1^2 and u_1; A1 = sqrt(sigma_1)
+// mat(u_1) and D1 = (sum_k u~_k S_k + diag(Y1^T u_1)) / sqrt(sigma_1), whose
+// coefficients feed the 2D-structured stage 2 (k_ksvd_w).
+
+struct Stage1Args {
+  const Tables* T;
+  int n, rz, nx, ny, nz, Jmax;
+  int64_t E;
+  double h;
+  const double *cx, *cy, *cz, *sx, *sy, *sz, *Zd, *Rz;
+  double* scr;
+  double* kco;
+  double *Az, *Azi, *sigz;
+  int32_t* zflags;
+  DevStatus* st;
+};
+
+namespace {
+
+// out = G u for the stage-1 Gram operator (one warp; all arrays global scratch)
+__device__ void s1_apply_G(const Tables* T, int n, const double* Cz3, const double* sd,
+                           const double* P, const double* u, double* out, double* ut, double* zu,
+                           double* yu, double* wv, double* cw) {
+  const int lane = threadIdx.x & 31, nn = n * n, nc = n + 2;
+  for (int k = lane; k < n; k += 32) ut[k] = u[k + n * k];
+  for (int c = lane; c < nc; c += 32) {
+    double sv = 0.0;
+    if (c < n) {
+      for (int a = 0; a < n; ++a) sv += T->D[c * n + a] * u[a + n * c];
+    } else {
+      const double* lv = (c == n) ? T->l1 : T->l0;
+      for (int b = 0; b < n; ++b) {
+        double t = 0.0;
+        for (int a = 0; a < n; ++a) t += lv[a] * u[a + n * b];
+        sv += lv[b] * t;
+      }
+    }
+    zu[c] = sv;
+  }
+  __syncwarp();
+  for (int q = lane; q < nn; q += 32) {
+    double y = 0.0;
+    for (int c = 0; c < nc; ++c) y += Cz3[(size_t)c * nn + q] * zu[c];
+    yu[q] = y;
+    double w = y;
+    for (int k = 0; k < n; ++k) w += sd[(size_t)k * nn + q] * ut[k];
+    wv[q] = w;
+  }
+  __syncwarp();
+  for (int c = lane; c < nc; c += 32) {
+    double sv = 0.0;
+    for (int q = 0; q < nn; ++q) sv += wv[q] * Cz3[(size_t)c * nn + q];
+    cw[c] = sv;
+  }
+  __syncwarp();
+  for (int q = lane; q < nn; q += 32) {
+    const int a = q % n, b = q / n;
+    double v = T->D[b * n + a] * cw[b] + T->l1[a] * T->l1[b] * cw[n] + T->l0[a] * T->l0[b] * cw[n + 1];
+    if (a == b) {
+      const int k = a;
+      for (int k2 = 0; k2 < n; ++k2) v += P[k + n * k2] * ut[k2];
+      for (int r = 0; r < nn; ++r) v += sd[(size_t)k * nn + r] * yu[r];
+    }
+    out[q] = v;
+  }
+  __syncwarp();
+}
+
+// eigenvalues of the symmetric tridiagonal (diag al, off-diagonal be[1..m-1])
+// below x (Sturm count of the LDL^T pivots)
+__device__ int sturm_sym(const double* al, const double* be, int m, double x, double tiny) {
+  int cnt = 0;
+  double q = al[0] - x;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    if (q == 0.0) q = -tiny;
+    q = (al[i] - x) - be[i] * be[i] / q;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
+  extern __shared__ double sm1[];
+  const int n = A.n, nn = n * n, n3 = nn * n, nc = n + 2, rz = A.rz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= A.E) return;
+  const S1Layout L = s1_layout(n, rz, A.Jmax);
+  double* S = A.scr + (size_t)e * L.total;
+  double *Cx3 = S + L.cx3, *Cy3 = S + L.cy3, *Cz3 = S + L.cz3, *rx = S + L.rx, *ry = S + L.ry;
+  double *sd = S + L.sd, *P = S + L.P, *Q = S + L.Q, *ut = S + L.ut, *zu = S + L.zu;
+  double *yu = S + L.yu, *wv = S + L.wv, *cw = S + L.cw, *tmp = S + L.tmp;
+  double *al = S + L.al, *be = S + L.be, *yv = S + L.y;
+  double* aug = sm1 + (size_t)warp * (2 * nn + n + 40);
+  double* fac = aug + 2 * nn;
+  double* cfs = fac + n + 8;   // 32 reorthogonalisation coefficients
+  const int nx = A.nx, ny = A.ny, nz = A.nz;
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+  auto eid = [&](int a, int b, int c) -> int64_t {
+    return ((int64_t)((c + nz) % nz) * ny + (b + ny) % ny) * nx + (a + nx) % nx;
+  };
+  const int64_t eXp = eid(ex + 1, ey, ez), eYp = eid(ex, ey + 1, ez), eZp = eid(ex, ey, ez + 1);
+  const double h3 = A.h * A.h * A.h;
+  const Tables* T = A.T;
+  // ---- 1. line coefficients in the Z basis (flux Jacobians of Sec. 3.4.1)
+  for (int q = lane; q < nc * nn; q += 32) {
+    const int c = q / nn, t = q % nn, a = t % n, b = t / n;
+    double vx, vy, vz;
+    if (c < n) {
+      vx = A.cx[e * n3 + c + n * a + nn * b];        // x-line (j = a, k = b)
+      vy = A.cy[e * n3 + a + n * c + nn * b];        // y-line (i = a, k = b)
+      vz = A.cz[e * n3 + a + n * b + nn * c];        // z-line (i = a, j = b)
+    } else if (c == n) {
+      vx = fmax(A.sx[eXp * nn + t], 0.0);
+      vy = fmax(A.sy[eYp * nn + t], 0.0);
+      vz = fmax(A.sz[eZp * nn + t], 0.0);
+    } else {
+      vx = fmax(-A.sx[e * nn + t], 0.0);
+      vy = fmax(-A.sy[e * nn + t], 0.0);
+      vz = fmax(-A.sz[e * nn + t], 0.0);
+    }
+    Cx3[q] = vx;
+    Cy3[q] = vy;
+    Cz3[q] = vz;
+  }
+  __syncwarp();
+  // ---- 2. off-diagonal parts through Rz, slice diagonals, Gram P of the slices
+  for (int q = lane; q < rz * nn; q += 32) {
+    const int t = q / nn, rest = q % nn;
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const double rzc = __ldg(A.Rz + t * nc + c);
+      a += rzc * Cx3[(size_t)c * nn + rest];
+      b += rzc * Cy3[(size_t)c * nn + rest];
+    }
+    rx[q] = a;
+    ry[q] = b;
+  }
+  for (int q = lane; q < n3; q += 32) {
+    const int i = q % n, j = (q / n) % n, k = q / nn;
+    double v = h3 * T->w[i] * T->w[j] * T->w[k];
+    for (int c = 0; c < nc; ++c)
+      v += __ldg(A.Zd + i * nc + c) * Cx3[(size_t)c * nn + j + n * k] +
+           __ldg(A.Zd + j * nc + c) * Cy3[(size_t)c * nn + i + n * k];
+    sd[(size_t)k * nn + i + n * j] = v;
+  }
+  __syncwarp();
+  for (int q = lane; q < nn; q += 32) {
+    const int k = q % n, k2 = q / n;
+    double v = 0.0;
+    for (int t = 0; t < rz; ++t)
+      for (int a = 0; a < n; ++a)
+        v += rx[(size_t)t * nn + a + n * k] * rx[(size_t)t * nn + a + n * k2] +
+             ry[(size_t)t * nn + a + n * k] * ry[(size_t)t * nn + a + n * k2];
+    for (int r = 0; r < nn; ++r) v += sd[(size_t)k * nn + r] * sd[(size_t)k2 * nn + r];
+    P[q] = v;
+  }
+  __syncwarp();
+  // ---- 3. symmetric Lanczos on G with full reorthogonalisation
+  {
+    for (int t = lane; t < nn; t += 32) Q[t] = splitmix_unit(7, t);
+    __syncwarp();
+    double s2 = 0.0;
+    for (int t = lane; t < nn; t += 32) s2 += Q[t] * Q[t];
+    const double inv = 1.0 / sqrt(warp_sum(s2));
+    for (int t = lane; t < nn; t += 32) Q[t] *= inv;
+    if (lane == 0) be[0] = 0.0;
+    __syncwarp();
+  }
+  int J = 0;
+  double lam = 0.0;
+  bool conv = false;
+  const int Jmax = A.Jmax;
+  double gscale = 0.0;
+  for (int j = 0; j < Jmax; ++j) {
+    double* qj = Q + (size_t)j * nn;
+    double* w = Q + (size_t)(j + 1) * nn;
+    s1_apply_G(T, n, Cz3, sd, P, qj, w, ut, zu, yu, wv, cw);
+    double a = 0.0;
+    for (int t = lane; t < nn; t += 32) a += qj[t] * w[t];
+    a = warp_sum(a);
+    for (int t = lane; t < nn; t += 32) w[t] -= a * qj[t] + ((j > 0) ? be[j] * Q[(size_t)(j - 1) * nn + t] : 0.0);
+    __syncwarp();
+    warp_reorth(w, Q, j + 1, nn, cfs);
+    double b2 = 0.0;
+    for (int t = lane; t < nn; t += 32) b2 += w[t] * w[t];
+    const double b = sqrt(warp_sum(b2));
+    gscale = fmax(gscale, fabs(a) + b);
+    if (lane == 0) {
+      al[j] = a;
+      be[j + 1] = b;
+    }
+    J = j + 1;
+    const bool breakdown = !(b > 1e-13 * gscale);
+    if (!breakdown) {
+      const double ib = 1.0 / b;
+      for (int t = lane; t < nn; t += 32) w[t] *= ib;
+    }
+    __syncwarp();
+    const bool check = breakdown || J == Jmax || J == nn || (J >= 8 && (J % 8) == 0);
+    if (!check) continue;
+    // top eigenvalue of the J x J tridiagonal by 32-point multisection
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < J; ++i) {
+      const double rad = ((i > 0) ? fabs(be[i]) : 0.0) + ((i + 1 < J) ? fabs(be[i + 1]) : 0.0);
+      lo = fmin(lo, al[i] - rad);
+      hi = fmax(hi, al[i] + rad);
+    }
+    const double tiny = 1e-300 + kEps * fmax(fabs(lo), fabs(hi));
+    for (int it = 0; it < 12; ++it) {
+      const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+      const int cnt = sturm_sym(al, be, J, x, tiny);
+      const unsigned ge = __ballot_sync(0xffffffffu, cnt >= J);
+      const int f = ge ? (__ffs(ge) - 1) : 32;
+      const double wdt = hi - lo;
+      const double nlo = (f == 0) ? lo : lo + wdt * (double)f * (1.0 / 33.0);
+      const double nhi = (f == 32) ? hi : lo + wdt * (double)(f + 1) * (1.0 / 33.0);
+      lo = nlo;
+      hi = nhi;
+    }
+    lam = 0.5 * (lo + hi);
+    // eigenvector by inverse iteration (lane 0; tridiagonal with pivoting)
+    if (lane == 0) {
+      double *d = S + L.d, *du = S + L.du, *du2 = S + L.du2, *dl = S + L.dl;
+      int* pv = reinterpret_cast<int*>(S + L.pv);
+      for (int i = 0; i < J; ++i) {
+        d[i] = al[i] - lam;
+        du[i] = (i + 1 < J) ? be[i + 1] : 0.0;
+        dl[i] = (i + 1 < J) ? be[i + 1] : 0.0;
+        du2[i] = 0.0;
+        pv[i] = 0;
+        yv[i] = splitmix_unit(11, i);
+      }
+      for (int i = 0; i + 1 < J; ++i) {
+        if (fabs(d[i]) >= fabs(dl[i])) {
+          if (d[i] == 0.0) d[i] = tiny;
+          const double f = dl[i] / d[i];
+          dl[i] = f;
+          d[i + 1] -= f * du[i];
+        } else {
+          const double f = d[i] / dl[i];
+          d[i] = dl[i];
+          dl[i] = f;
+          const double t = du[i];
+          du[i] = d[i + 1];
+          d[i + 1] = t - f * d[i + 1];
+          if (i + 2 < J) {
+            du2[i] = du[i + 1];
+            du[i + 1] = -f * du[i + 1];
+          }
+          pv[i] = 1;
+        }
+      }
+      if (d[J - 1] == 0.0) d[J - 1] = tiny;
+      for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i + 1 < J; ++i) {
+          if (pv[i]) {
+            const double t = yv[i];
+            yv[i] = yv[i + 1];
+            yv[i + 1] = t;
+          }
+          yv[i + 1] -= dl[i] * yv[i];
+        }
+        for (int i = J - 1; i >= 0; --i) {
+          double sv = yv[i];
+          if (i + 1 < J) sv -= du[i] * yv[i + 1];
+          if (i + 2 < J) sv -= du2[i] * yv[i + 2];
+          yv[i] = sv / d[i];
+        }
+        double nr = 0.0;
+        for (int i = 0; i < J; ++i) nr += yv[i] * yv[i];
+        nr = 1.0 / sqrt(nr);
+        for (int i = 0; i < J; ++i) yv[i] *= nr;
+      }
+      tmp[0] = (breakdown ? 0.0 : be[J]) * fabs(yv[J - 1]);   // Ritz residual
+    }
+    __syncwarp();
+    conv = breakdown || tmp[0] <= 1e-14 * fabs(lam) || J == nn;
+    if (conv || J == Jmax) break;
+  }
+  // ---- 4. u_1, A1 and the stage-2 coefficients of D1
+  for (int t = lane; t < nn; t += 32) {
+    double sv = 0.0;
+    for (int i = 0; i < J; ++i) sv += yv[i] * Q[(size_t)i * nn + t];
+    tmp[t] = sv;
+  }
+  __syncwarp();
+  double nr = 0.0, tr = 0.0;
+  for (int t = lane; t < nn; t += 32) {
+    nr += tmp[t] * tmp[t];
+    if (t % (n + 1) == 0) tr += tmp[t];
+  }
+  nr = warp_sum(nr);
+  tr = warp_sum(tr);
+  const double sgn = (tr < 0.0) ? -1.0 : 1.0;          // gauge: trace(A1) >= 0
+  const double fu = sgn / sqrt(nr);
+  for (int t = lane; t < nn; t += 32) tmp[t] *= fu;
+  __syncwarp();
+  const double s1 = sqrt(fmax(lam, 0.0));
+  const double rs = sqrt(s1), irs = (rs > 0.0) ? 1.0 / rs : 0.0;
+  for (int t = lane; t < nn; t += 32) A.Az[e * nn + t] = rs * tmp[t];
+  // Y1^T u_1 (into yu) and u~ (ut) with u = u_1
+  for (int k = lane; k < n; k += 32) ut[k] = tmp[k + n * k];
+  for (int c = lane; c < nc; c += 32) {
+    double sv = 0.0;
+    if (c < n) {
+      for (int a = 0; a < n; ++a) sv += T->D[c * n + a] * tmp[a + n * c];
+    } else {
+      const double* lv = (c == n) ? T->l1 : T->l0;
+      for (int b = 0; b < n; ++b) {
+        double t = 0.0;
+        for (int a = 0; a < n; ++a) t += lv[a] * tmp[a + n * b];
+        sv += lv[b] * t;
+      }
+    }
+    zu[c] = sv;
+  }
+  __syncwarp();
+  double* kc = A.kco + (size_t)e * (2 * nc * n + nn);
+  for (int q = lane; q < 2 * nc * n + nn; q += 32) {
+    double v = 0.0;
+    if (q < nc * n) {                       // Cx of D1: x-lines by y index j
+      const int c = q / n, j = q % n;
+      for (int k = 0; k < n; ++k) v += ut[k] * Cx3[(size_t)c * nn + j + n * k];
+    } else if (q < 2 * nc * n) {            // Cy of D1: y-lines by x index i
+      const int c = (q - nc * n) / n, i = (q - nc * n) % n;
+      for (int k = 0; k < n; ++k) v += ut[k] * Cy3[(size_t)c * nn + i + n * k];
+    } else {                                // diagonal: mass and Y1^T u_1
+      const int d = q - 2 * nc * n, i = d % n, j = d / n;
+      for (int k = 0; k < n; ++k) v += ut[k] * h3 * T->w[i] * T->w[j] * T->w[k];
+      for (int c = 0; c < nc; ++c) v += Cz3[(size_t)c * nn + d] * zu[c];
+    }
+    kc[q] = irs * v;
+  }
+  // ---- 5. A1^-1 (Gauss-Jordan, one warp)
+  for (int q = lane; q < 2 * nn; q += 32) {
+    const int c = q / n, rr = q % n;
+    aug[q] = (c < n) ? rs * tmp[rr + n * c] : ((rr == c - n) ? 1.0 : 0.0);
+  }
+  __syncwarp();
+  const double na = norm1_warp(aug, n);
+  const bool sing = warp_gauss_jordan(aug, n, fac);
+  const double ni = norm1_warp(aug + nn, n);
+  for (int q = lane; q < nn; q += 32) A.Azi[e * nn + q] = aug[nn + q];
+  if (lane == 0) {
+    A.sigz[e] = s1;
+    const double cnd = na * ni;
+    int zf = 0;
+    if (!conv) zf |= 1;
+    if (sing || !(cnd < 1e14)) zf |= 2;
+    A.zflags[e] = zf;
+    if (zf & 1) atomicAdd(&A.st->z_unconverged, 1);
+    if (zf & 2) atomicAdd(&A.st->build_singular, 1);
+    if (cnd < 1e300) atomic_max_double(&A.st->max_cond_z, cnd);
+  }
+}
+
+cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s) {
+  const int n = c->n;
+  Stage1Args a;
+  a.T = c->p<Tables>(c->L.tables);
+  a.n = n;
+  a.rz = c->rz;
+  a.nx = c->prob.nel[0];
+  a.ny = c->prob.nel[1];
+  a.nz = c->prob.nel[2];
+  a.Jmax = s1_jmax(n);
+  a.E = c->E;
+  a.h = c->prob.h;
+  a.cx = c->p<double>(c->L.cx);
+  a.cy = c->p<double>(c->L.cy);
+  a.cz = c->p<double>(c->L.cz);
+  a.sx = c->p<double>(c->L.sx);
+  a.sy = c->p<double>(c->L.sy);
+  a.sz = c->p<double>(c->L.sz);
+  a.Zd = c->p<double>(c->L.zd);
+  a.Rz = c->p<double>(c->L.rz);
+  a.scr = c->p<double>(c->L.s1scr);
+  a.kco = c->p<double>(c->L.kco);
+  a.Az = c->p<double>(c->L.fAz);
+  a.Azi = c->p<double>(c->L.fAzi);
+  a.sigz = c->p<double>(c->L.sigz);
+  a.zflags = c->p<int32_t>(c->L.zflags);
+  a.st = c->p<DevStatus>(c->L.status);
+  const int warps = 4;
+  const size_t smem = (size_t)warps * (2 * n * n + n + 40) * sizeof(double);
+  k_stage1_3d<<<(unsigned)((c->E + warps - 1) / warps), warps * 32, smem, s>>>(a);
+  count_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_ksvd_pipeline(c, s);
 }
 
 }  // namespace tpp

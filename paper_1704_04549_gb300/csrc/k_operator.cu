@@ -390,6 +390,79 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
   }
 }
 
+// y = (M + dt A) x for one element per CTA (3D):
+//   y_ijk = h^3 w_i w_j w_k x + sum_a D_ai cx_ajk x_ajk + sum_b D_bj cy_ibk x_ibk
+//           + sum_c D_ck cz_ijc x_ijc + l1_i F^+x_jk - l0_i F^-x_jk + (same for y, z),
+// face fluxes pre-scaled by dt h^2 and the two tangential weights.
+__global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, double h,
+                              const double* __restrict__ cx, const double* __restrict__ cy,
+                              const double* __restrict__ cz, const double* __restrict__ sx,
+                              const double* __restrict__ sy, const double* __restrict__ sz,
+                              const double* __restrict__ x, const double* __restrict__ tr,
+                              double* __restrict__ y, const int32_t* skip) {
+  if (skip && *skip) return;
+  extern __shared__ double sm[];
+  const int nn = n * n, n3 = nn * n;
+  double* Ds = sm;              // n*n
+  double* px = Ds + nn;         // n^3 each
+  double* py = px + n3;
+  double* pz = py + n3;
+  double* fl = pz + n3;         // 6 n^2 fluxes: +x, -x, +y, -y, +z, -z
+  double* wl = fl + 6 * nn;     // w, l0, l1
+  const int64_t e = blockIdx.x;
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+  auto eid = [&](int a, int b, int c) -> int64_t {
+    return ((int64_t)((c + nz) % nz) * ny + (b + ny) % ny) * nx + (a + nx) % nx;
+  };
+  const int64_t eXp = eid(ex + 1, ey, ez), eXm = eid(ex - 1, ey, ez);
+  const int64_t eYp = eid(ex, ey + 1, ez), eYm = eid(ex, ey - 1, ez);
+  const int64_t eZp = eid(ex, ey, ez + 1), eZm = eid(ex, ey, ez - 1);
+  const int tid = threadIdx.x;
+  const int64_t base = e * n3;
+  for (int q = tid; q < nn; q += blockDim.x) Ds[q] = T->D[q];
+  for (int q = tid; q < n3; q += blockDim.x) {
+    const double xv = x[base + q];
+    px[q] = cx[base + q] * xv;
+    py[q] = cy[base + q] * xv;
+    pz[q] = cz[base + q] * xv;
+  }
+  if (tid < n) {
+    wl[tid] = T->w[tid];
+    wl[n + tid] = T->l0[tid];
+    wl[2 * n + tid] = T->l1[tid];
+  }
+  const double* te = tr + e * 6 * nn;
+  for (int q = tid; q < nn; q += blockDim.x) {
+    double s;
+    s = sx[eXp * nn + q];
+    fl[0 * nn + q] = fmax(s, 0.0) * te[1 * nn + q] + fmin(s, 0.0) * tr[eXp * 6 * nn + 0 * nn + q];
+    s = sx[e * nn + q];
+    fl[1 * nn + q] = fmax(s, 0.0) * tr[eXm * 6 * nn + 1 * nn + q] + fmin(s, 0.0) * te[0 * nn + q];
+    s = sy[eYp * nn + q];
+    fl[2 * nn + q] = fmax(s, 0.0) * te[3 * nn + q] + fmin(s, 0.0) * tr[eYp * 6 * nn + 2 * nn + q];
+    s = sy[e * nn + q];
+    fl[3 * nn + q] = fmax(s, 0.0) * tr[eYm * 6 * nn + 3 * nn + q] + fmin(s, 0.0) * te[2 * nn + q];
+    s = sz[eZp * nn + q];
+    fl[4 * nn + q] = fmax(s, 0.0) * te[5 * nn + q] + fmin(s, 0.0) * tr[eZp * 6 * nn + 4 * nn + q];
+    s = sz[e * nn + q];
+    fl[5 * nn + q] = fmax(s, 0.0) * tr[eZm * 6 * nn + 5 * nn + q] + fmin(s, 0.0) * te[4 * nn + q];
+  }
+  __syncthreads();
+  const double h3 = h * h * h;
+  for (int q = tid; q < n3; q += blockDim.x) {
+    const int i = q % n, j = (q / n) % n, k = q / nn;
+    double acc = h3 * wl[i] * wl[j] * wl[k] * x[base + q];
+    for (int a = 0; a < n; ++a) acc += Ds[a * n + i] * px[a + n * j + nn * k];
+    for (int b = 0; b < n; ++b) acc += Ds[b * n + j] * py[i + n * b + nn * k];
+    for (int c = 0; c < n; ++c) acc += Ds[c * n + k] * pz[i + n * j + nn * c];
+    const int qx = j + n * k, qy = i + n * k, qz = i + n * j;
+    acc += wl[2 * n + i] * fl[0 * nn + qx] - wl[n + i] * fl[1 * nn + qx];
+    acc += wl[2 * n + j] * fl[2 * nn + qy] - wl[n + j] * fl[3 * nn + qy];
+    acc += wl[2 * n + k] * fl[4 * nn + qz] - wl[n + k] * fl[5 * nn + qz];
+    y[base + q] = acc;
+  }
+}
+
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
@@ -404,7 +477,17 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
     count_launch();
     return cudaGetLastError();
   }
-  return cudaErrorNotSupported;
+  const int nn = n * n, n3 = nn * n;
+  const size_t smem = (size_t)(nn + 3 * n3 + 6 * nn + 3 * n) * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(k_dg_apply_3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  k_dg_apply_3d<<<(unsigned)c->E, 256, smem, s>>>(
+      c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.nel[2], c->prob.h,
+      c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.cz), c->p<double>(c->L.sx),
+      c->p<double>(c->L.sy), c->p<double>(c->L.sz), x, tr, y, skip);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace tpp

@@ -78,6 +78,7 @@ const char* validate(const tpp_problem* p, int32_t max_restart) {
   if (!p) return "problem is NULL";
   if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
   if (p->n < 1 || p->n > TPP_MAX_N) return "n must be in [1, 32]";
+  if (p->dim == 3 && p->n > TPP_MAX_N_3D) return "n must be in [1, 16] in 3D";
   for (int d = 0; d < p->dim; ++d)
     if (p->nel[d] < 1) return "nel[d] must be >= 1";
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return "h must be positive and finite";
@@ -130,15 +131,13 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.fB1 = take(fsz);
   L.fA2 = take(fsz);
   L.fB2 = take(fsz);
-  L.fC1 = (d == 3) ? take(fsz) : 0;
-  L.fC2 = (d == 3) ? take(fsz) : 0;
   L.fSA = take(fsz);
   L.fSB = take(fsz);
   L.fQ1 = take(fsz);
   L.fQ2 = take(fsz);
   L.fT1 = take(fsz);
   L.fT2 = take(fsz);
-  L.fSC = take((size_t)E * 8 * ((d == 3) ? n * n : 1));
+  L.fSC = take((size_t)E * 8);
   L.flags = take((size_t)E * 4);
   L.masks = take((size_t)E * 2 * 4);
   {
@@ -148,6 +147,13 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
     // coefficients of the 2D-structured block fed to the KSVD (2D: the element
     // block; 3D: the second-stage block D1): Cx, Cy ((n+2) x n each), Dg (n x n)
     L.kco = take((size_t)E * (2 * (size_t)nc * n + (size_t)n * n) * 8);
+  }
+  if (d == 3) {
+    L.s1scr = take((size_t)E * s1_layout(n, rz, s1_jmax(n)).total * 8);
+    L.fAz = take(fsz);
+    L.fAzi = take(fsz);
+    L.sigz = take((size_t)E * 8);
+    L.zflags = take((size_t)E * 4);
   }
   L.f32 = (features & TPP_FEAT_MIXED) ? take((size_t)7 * E * n * n * 4) : 0;
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
@@ -229,8 +235,8 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     set_error(why);
     return TPP_ERR_INVALID_ARG;
   }
-  if (prob->dim == 3) {
-    set_error("3D problems are not implemented in this build");
+  if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
+    set_error("exact block Jacobi is implemented for 2D problems only");
     return TPP_ERR_UNSUPPORTED;
   }
   int rz = 0;
@@ -326,6 +332,9 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
     report->num_schur_fail = st.build_schur_fail;
     report->max_cond = st.max_cond;
     report->min_sigma_ratio = st.min_sigma_ratio;
+    report->max_cond_z = st.max_cond_z;
+    report->num_z_unconverged = st.z_unconverged;
+    report->reserved = 0;
   }
   c->factors_built = true;
   if (st.build_schur_fail) {
@@ -421,6 +430,12 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
   o->T2 = c->p<double>(c->L.fT2);
   o->flags = c->p<int32_t>(c->L.flags);
   o->cond = c->p<double>(c->L.fSC);
+  if (c->dim == 3) {
+    o->Az = c->p<double>(c->L.fAz);
+    o->Azi = c->p<double>(c->L.fAzi);
+    o->sigz = c->p<double>(c->L.sigz);
+    o->zflags = c->p<int32_t>(c->L.zflags);
+  }
   const Tables* T = c->p<Tables>(c->L.tables);
   o->gl_x = T->x;
   o->gl_w = T->w;

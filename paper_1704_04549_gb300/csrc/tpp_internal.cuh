@@ -9,6 +9,7 @@
 #include "tpp.h"
 
 #define TPP_MAX_N 32
+#define TPP_MAX_N_3D 16
 #define TPP_MAX_MODES 64
 
 namespace tpp {
@@ -42,7 +43,8 @@ struct DevStatus {
   double max_cond;          // stored as ordered bits via atomicMax on long long
   double min_sigma_ratio;
   int32_t nan_seen;
-  int32_t pad;
+  int32_t z_unconverged;    // 3D stage 1: elements whose Lanczos hit its step cap
+  double max_cond_z;        // 3D stage 1: largest cond_1(A1)
 };
 
 // GMRES device state (one solve at a time per context).
@@ -66,11 +68,12 @@ struct Layout {
   size_t zd, rz, qo, qr_work, qr_tau;   // structure basis of the rearranged block (2D)
   size_t cx, cy, cz, sx, sy, sz;        // flux Jacobians (scaled) at nodes / faces
   size_t traces;
-  size_t sigma, fA1, fB1, fA2, fB2, fC1, fC2;
+  size_t sigma, fA1, fB1, fA2, fB2;
   size_t fSA, fSB, fQ1, fQ2, fT1, fT2, fSC;  // fSC: 3D A1^-1 factor
   size_t flags, masks;
   size_t bscr, biscr;                  // factor-build scratch (Lanczos bases, tridiagonal work)
   size_t kco;                          // per-block KSVD coefficients (Cx, Cy, Dg)
+  size_t s1scr, fAz, fAzi, sigz, zflags;   // 3D stage 1: scratch, A1, A1^-1, sigma_1, flags
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
@@ -112,7 +115,47 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s);
+// per-element scratch of the 3D stage-1 kernel (doubles)
+struct S1Layout {
+  size_t cx3, cy3, cz3, rx, ry, sd, P, Q, ut, zu, yu, wv, cw, tmp, al, be, y, d, du, du2, dl, pv,
+      total;
+};
+
+__host__ __device__ inline S1Layout s1_layout(int n, int rz, int Jmax) {
+  const size_t nn = (size_t)n * n, n3 = nn * n, nc = n + 2;
+  S1Layout L;
+  size_t o = 0;
+  L.cx3 = o; o += nc * nn;
+  L.cy3 = o; o += nc * nn;
+  L.cz3 = o; o += nc * nn;
+  L.rx = o; o += (size_t)rz * nn;
+  L.ry = o; o += (size_t)rz * nn;
+  L.sd = o; o += n3;
+  L.P = o; o += nn;
+  L.Q = o; o += (size_t)(Jmax + 1) * nn;
+  L.ut = o; o += n;
+  L.zu = o; o += nc;
+  L.yu = o; o += nn;
+  L.wv = o; o += nn;
+  L.cw = o; o += nc;
+  L.tmp = o; o += nn;
+  L.al = o; o += Jmax + 1;
+  L.be = o; o += Jmax + 2;
+  L.y = o; o += Jmax + 1;
+  L.d = o; o += Jmax + 1;
+  L.du = o; o += Jmax + 1;
+  L.du2 = o; o += Jmax + 1;
+  L.dl = o; o += Jmax + 1;
+  L.pv = o; o += Jmax + 1;
+  L.total = (o + 3) & ~size_t(3);
+  return L;
+}
+
+// Lanczos steps allowed in the 3D stage 1 (the Gram operator has order n^2)
+__host__ __device__ inline int s1_jmax(int n) { return (n * n < 64) ? n * n : 64; }
+
 cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
                             const int32_t* skip, cudaStream_t s);
 cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,

@@ -166,6 +166,11 @@ class Context:
         res["gl_x"] = grab(v.gl_x, n, torch.float64)
         res["gl_w"] = grab(v.gl_w, n, torch.float64)
         res["D"] = grab(v.D, n * n, torch.float64).view(n, n)
+        if self.dim == 3:
+            res["Az"] = grab(v.Az, E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
+            res["Azi"] = grab(v.Azi, E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
+            res["sigz"] = grab(v.sigz, E, torch.float64)
+            res["zflags"] = grab(v.zflags, E, torch.int32)
         torch.cuda.synchronize(self.device)
         return res
 

@@ -6,7 +6,8 @@ import scipy.sparse.linalg as spla
 import synthetic
 from oracle.gmres import gmres
 from oracle.precond import block_jacobi, kron_dense
-from paper_1704_04549_gb300 import TPP_FEAT_BLOCK_JACOBI, TPP_PC_BLOCK_JACOBI, TPP_PC_KRON, TPP_PC_NONE
+from paper_1704_04549_gb300 import (TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FP32,
+                                    TPP_PC_BLOCK_JACOBI, TPP_PC_KRON, TPP_PC_NONE)
 from tests.gpu_util import make_pair, rel, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
@@ -86,3 +87,23 @@ def test_full_size_fourier_n16_converges():
     # residual recomputed through the operator entry point
     Ax = to_host(ctx.dg_apply_sumfact(x))
     assert np.linalg.norm(Ax - b) <= 1.0001e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_mixed_precision_2d(n):
+    """FP32 apply against the FP64 apply, and flexible GMRES with the FP32 inner
+    preconditioner reaching the same 1e-8 true residual."""
+    ctx, dg = make_pair(n, (4, 4), 0.05, synthetic.fourier_velocity(1705, 2, kmax=1),
+                        features=TPP_FEAT_MIXED, h=1.0)
+    ctx.tpp_build_factors()
+    b = synthetic.rhs(1706, dg.ndof)
+    x64 = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    x32 = to_host(ctx.tpp_apply_inverse(to_dev(b), prec=TPP_FP32))
+    cp = to_host(ctx.views()["cond"]).max()
+    # FP32 contractions and Sylvester solve: error ~ n u32 times the factor conditioning
+    assert rel(x32, x64) <= 1e-6 * n * max(1.0, np.sqrt(cp))
+    _, r64 = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    _, r32 = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8, inner_prec=TPP_FP32,
+                             flexible=True)
+    assert r32["converged"] and r32["true_rel_res"] <= 1e-8
+    assert r32["iters"] <= r64["iters"] + 3
