@@ -43,6 +43,32 @@ def workload(n: int):
                 velocity=synthetic.fourier_velocity(1705, 2), rhs_seed=1706)
 
 
+def workload_3d(n: int = 11):
+    return dict(dim=3, n=n, nel=(16, 16, 16), h=1.0, dt=0.05,
+                velocity=synthetic.fourier_velocity(1705, 3), rhs_seed=1706)
+
+
+def time_each(fn, reps, stream, flush):
+    """Mean device time (ms) of fn() over reps launches, with the L2 flushed
+    (a write of a buffer larger than L2) before each one, outside the events."""
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def form_bits(args) -> int:
+    from paper_1704_04549_gb300 import TPP_FEAT_TWO_SIDED
+    return TPP_FEAT_TWO_SIDED if args.form == "two-sided" else 0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -204,7 +230,7 @@ def run_ours(args):
     lib = _lib.load()
     w = workload(args.n)
     ctx = Context(2, args.n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
-                  features=TPP_FEAT_MIXED, device=str(dev))
+                  features=TPP_FEAT_MIXED | form_bits(args), device=str(dev))
     N, E, n = ctx.num_dofs, ctx.num_elem, args.n
     b_host = synthetic.rhs(w["rhs_seed"], N)
     b = torch.as_tensor(b_host, device=dev)
@@ -253,19 +279,12 @@ def run_ours(args):
 
     # preconditioner apply throughput, FP64 and FP32 (dominant kernel), on the bench stream
     z = torch.empty_like(b)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)     # 256 MB > L2
     apply = {}
     for name, prec in (("fp64", TPP_FP64), ("fp32", TPP_FP32)):
         for _ in range(3):
             ctx.tpp_apply_inverse(b, z, prec=prec)
-        reps = 20
-        torch.cuda.synchronize(dev)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(reps):
-            ctx.tpp_apply_inverse(b, z, prec=prec)
-        a1.record(stream)
-        torch.cuda.synchronize(dev)
-        t_ms = a0.elapsed_time(a1) / reps
+        t_ms = time_each(lambda: ctx.tpp_apply_inverse(b, z, prec=prec), 20, stream, flush)
         apply[name] = {"ms": t_ms, "gdofs": N / (t_ms * 1e-3) / 1e9}
     # algorithmic work of the apply: 4 dense n x n x n products (8 n^3) + the
     # quasi-triangular Sylvester solve (2 n^3) per element; bytes: b, x and the
@@ -310,8 +329,9 @@ def run_ours(args):
                                f"b~N(0,1) seed 1706",
                    "n": n, "nel": [64, 64], "h": 1.0, "dt": 0.05, "dofs": N, "rtol": 1e-8,
                    "restart": 30, "preconditioner": "KSVD rank-2 (Alg. 2d-form / 2d-apply)",
-                   "inner_prec": args.prec,
-                   "l2": "inputs larger than L2 (Krylov basis %.0f MB + factors %.0f MB)"
+                   "inner_prec": args.prec, "apply_form": args.form,
+                   "l2": "step: inputs larger than L2 (Krylov basis %.0f MB + factors %.0f MB); "
+                         "precond_apply: L2 flushed (256 MB write) before each timed launch"
                          % (31 * N * 8 / 1e6, 6 * N * 8 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gmres": {"iters": res["iters"], "cycles": res["cycles"], "converged": converged,
@@ -332,14 +352,89 @@ def run_ours(args):
     return 0
 
 
+def run_3d(args):
+    """The 3D configuration (16^3 periodic hexes, n = 11, 5.45M DOFs, dt = 0.05):
+    nested factor build (Alg. 3d-form), preconditioner apply (Alg. 3d-apply) in
+    FP64 and FP32, the sum-factorised operator, and GMRES(30) with the nested
+    preconditioner from b ~ N(0, 1), run for at most --max-iters iterations.
+    value = FP64 preconditioner-apply throughput (GDOF/s)."""
+    import torch
+    from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, TPP_PC_KRON, Context
+    from paper_1704_04549_gb300 import _lib
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    w = workload_3d(args.n if args.n != 16 else 11)
+    n = w["n"]
+    ctx = Context(3, n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                  features=TPP_FEAT_MIXED | form_bits(args), device=str(dev))
+    N, E = ctx.num_dofs, ctx.num_elem
+    b = torch.as_tensor(synthetic.rhs(w["rhs_seed"], N), device=dev)
+    z = torch.empty_like(b)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.tpp_build_factors()
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(0) as clk:
+        build_ms = time_each(lambda: ctx.tpp_build_factors(), args.steps, stream, flush)
+        apply = {}
+        for name, prec in (("fp64", TPP_FP64), ("fp32", TPP_FP32)):
+            for _ in range(args.warmup):
+                ctx.tpp_apply_inverse(b, z, prec=prec)
+            t_ms = time_each(lambda: ctx.tpp_apply_inverse(b, z, prec=prec), 10 * args.steps,
+                             stream, flush)
+            apply[name] = {"ms": t_ms, "gdofs": N / (t_ms * 1e-3) / 1e9}
+        for _ in range(args.warmup):
+            ctx.dg_apply_sumfact(b, z)
+        op_ms = time_each(lambda: ctx.dg_apply_sumfact(b, z), 10 * args.steps, stream, flush)
+    launches = lib.tpp_kernel_launch_count() - l0
+    gm = {}
+    for name, prec in (("fp64", TPP_FP64), ("mixed", TPP_FP32)):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters,
+                               pc=TPP_PC_KRON, inner_prec=prec, flexible=(prec != TPP_FP64),
+                               check=False)
+        gm[name] = {"iters": r["iters"], "converged": bool(r["converged"]),
+                    "true_rel_res": r["true_rel_res"],
+                    "wall_ms": (time.perf_counter() - t0) * 1e3}
+    flops = 12.0 * n ** 4 * E         # z transform 2 n^4 + n slice applies of 10 n^3
+    achieved = flops / (apply["fp64"]["ms"] * 1e-3) / 1e9
+    line = {
+        "metric": "precond-apply GDOF/s, 3D nested Kronecker preconditioner, 1 GB300",
+        "value": apply["fp64"]["gdofs"], "unit": "GDOF/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"adv3d-fourier-16x16x16-n{n} (p={n - 1}), unit hexes, dt=0.05, "
+                               f"solenoidal random-Fourier velocity seed 1705, b~N(0,1) seed 1706",
+                   "n": n, "nel": [16, 16, 16], "h": 1.0, "dt": 0.05, "dofs": N,
+                   "apply_form": args.form,
+                   "l2": "L2 flushed (256 MB write) before each timed launch"},
+        "build_ms": build_ms,
+        "precond_apply": {"fp64_gdofs": apply["fp64"]["gdofs"], "fp64_ms": apply["fp64"]["ms"],
+                          "fp32_gdofs": apply["fp32"]["gdofs"], "fp32_ms": apply["fp32"]["ms"]},
+        "operator": {"ms": op_ms, "gdofs": N / (op_ms * 1e-3) / 1e9},
+        "gmres": gm,
+        "roofline": {"kernel": "3D apply (k_apply_z + k_apply_2d_w<double> on z slices)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "peak_note": FP64_PEAK_NOTE, "algorithmic": "12 n^4 flop per element"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_kernels(args):
     """Kernel-only pass for profilers: one factor build, then a few launches of
     each hot-path kernel on the same workload (no GMRES loop)."""
     import torch
     from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, Context
-    w = workload(args.n)
-    ctx = Context(2, args.n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
-                  features=TPP_FEAT_MIXED)
+    w = workload_3d(args.n if args.n != 16 else 11) if args.workload == "adv3d" else workload(args.n)
+    ctx = Context(w["dim"], w["n"], w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                  features=TPP_FEAT_MIXED | form_bits(args))
     b = torch.as_tensor(synthetic.rhs(w["rhs_seed"], ctx.num_dofs), device="cuda:0")
     z = torch.empty_like(b)
     ctx.tpp_build_factors()
@@ -350,7 +445,8 @@ def run_kernels(args):
     for _ in range(3):
         ctx.dg_apply_sumfact(b, z)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "kernels", "n": args.n, "dofs": ctx.num_dofs}))
+    print(json.dumps({"mode": "kernels", "workload": args.workload, "n": w["n"],
+                      "dofs": ctx.num_dofs}))
     return 0
 
 
@@ -370,11 +466,18 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="GMRES iterations the reference arm extrapolates to")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--form", choices=["one-sided", "two-sided"], default="one-sided",
+                    help="apply form: one-sided (shifted inverses, default) or the paper's "
+                         "two-sided Schur / quasi-triangular Sylvester form")
+    ap.add_argument("--workload", choices=["adv2d", "adv3d"], default="adv2d",
+                    help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernels":
         return run_kernels(args)
+    if args.workload == "adv3d":
+        return run_3d(args)
     return run_ours(args)
 
 

@@ -65,6 +65,8 @@ typedef enum {
 /* Feature bits for tpp_workspace_bytes / tpp_create. */
 #define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^4 doubles per element for exact block Jacobi (2D only) */
 #define TPP_FEAT_MIXED        2u  /* reserve float32 copies of the Kronecker apply factors */
+#define TPP_FEAT_TWO_SIDED    4u  /* apply by the paper's two-sided Schur form (quasi-triangular
+                                     Sylvester solve) instead of the default one-sided form */
 
 /*
  * Problem description.  Velocity field (component c) at the normalised point
@@ -149,8 +151,13 @@ void tpp_destroy(tpp_ctx* ctx);
  * Alg. 3d-form in 3D): best rank-2 (3D: nested rank-1 then rank-2) Kronecker
  * approximation of the exact diagonal block by a Golub-Kahan-Lanczos SVD of its
  * Van Loan-Pitsianis rearrangement (Sec. 4.1, Alg. lanczos), LU inverses of the
- * factors the paper inverts, real Schur forms of the two factor products
- * (Eq. quad-triang).  2D: the inverted pair is (A2 + alpha A1, B1 - alpha B2),
+ * factors the paper inverts (L_A, L_B), and the factor products C1 = L_A^-1 A1,
+ * C2 = L_B^-1 B2.  With TPP_FEAT_TWO_SIDED: real Schur forms of C1 and C2
+ * (Eq. quad-triang, as in the paper).  Default (one-sided form): the real Schur
+ * form C1 = Q1 T1 Q1^T only, and for every 1x1 / 2x2 diagonal block J of T1 the
+ * inverse of the shifted system I (x) C2 + T1[J, J] (x) I (Gauss-Jordan, partial
+ * pivoting); the same P, stored in 2 n^3 extra doubles per element.
+ * 2D: the inverted pair is (A2 + alpha A1, B1 - alpha B2),
  * which leaves P = A1 (x) B1 + A2 (x) B2 unchanged; alpha = 0 is the paper's
  * choice and a nonzero alpha is taken only when it lowers the condition
  * numbers of the inverted factors.  Factors are stored in the workspace.  `report` (host, may
@@ -168,9 +175,13 @@ tpp_status tpp_build_factors(tpp_ctx* ctx, tpp_build_report* report, void* strea
 tpp_status tpp_build_block_jacobi(tpp_ctx* ctx, void* stream);
 
 /*
- * x = P^-1 b, element by element (Alg. 2d-apply / 3d-apply): b~ = S_B B S_A^T,
- * quasi-triangular Sylvester solve T2 Y + Y T1^T = b~, x = Q2 Y Q1^T (2D; the
- * 3D form applies the A1^-1 factor along z and one Sylvester solve per z-slice).
+ * x = P^-1 b, element by element (Alg. 2d-apply / 3d-apply).  P^-1 b is
+ * (C1 (x) I + I (x) C2)^-1 (L_A^-1 (x) L_B^-1) b, i.e. X solves C2 X + X C1^T =
+ * L_B^-1 B L_A^-T (B[i, j] = b[i + n j]).  Two-sided form: b~ = S_B B S_A^T,
+ * quasi-triangular Sylvester solve T2 Y + Y T1^T = b~, x = Q2 Y Q1^T.  One-sided
+ * form (default): R = L_B^-1 B S_A^T, then C2 Z + Z T1^T = R column block by
+ * column block from the last with the stored shifted inverses, x = Z Q1^T.
+ * 3D applies the A1^-1 factor along z first, then the 2D form on each z slice.
  * b, x: device float64 [num_dofs], must not alias.  prec selects the arithmetic
  * and factor precision (TPP_FP32 needs TPP_FEAT_MIXED).  Asynchronous.
  */
@@ -222,11 +233,11 @@ typedef struct {
   const double* A2;
   const double* B2;
   const double* SA;      /* [E][n*n] Q1^T L_A^-1 */
-  const double* SB;      /* [E][n*n] Q2^T L_B^-1 */
+  const double* SB;      /* [E][n*n] Q2^T L_B^-1 (two-sided form); L_B^-1 (one-sided form) */
   const double* Q1;
-  const double* Q2;
-  const double* T1;
-  const double* T2;
+  const double* Q2;      /* two-sided form only (NULL otherwise) */
+  const double* T1;      /* real Schur form of C1 */
+  const double* T2;      /* two-sided: real Schur form of C2; one-sided: C2 itself */
   const int32_t* flags;  /* [E] bit0 shifted pair, bit1 rank-1, bit2 schur fail, bit3 singular */
   const double* cond;    /* [E] cond_1(L_A) * cond_1(L_B) of the inverted factor pair */
   const double* gl_x;    /* [n] Gauss-Legendre nodes on [0, 1] */
@@ -240,6 +251,8 @@ typedef struct {
   const double* Azi;     /* [E][n*n] its inverse */
   const double* sigz;    /* [E] first-stage singular value sigma_1 */
   const int32_t* zflags; /* [E] bit0 Lanczos not converged, bit1 A1 singular or cond_1 >= 1e14 */
+  const double* G;       /* one-sided form: [E][n][2][n*n] shifted inverses Gs_j, Gp_j
+                            (column-major n x n), NULL in the two-sided form */
 } tpp_views;
 
 tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "TPP_OK", 1: "TPP_ERR_INVALID_ARG", 2: "TPP_ERR_CUDA",
                 9: "TPP_ERR_WORKSPACE"}
 TPP_FP64, TPP_FP32 = 0, 1
 TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
-TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED = 1, 2
+TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED = 1, 2, 4
 
 
 class Problem(C.Structure):
@@ -45,7 +45,7 @@ class BuildReport(C.Structure):
 class Views(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in
                 ("sigma", "A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2", "flags",
-                 "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags")]
+                 "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags", "G")]
 
 
 EXPORTS = {

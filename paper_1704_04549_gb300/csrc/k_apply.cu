@@ -316,6 +316,168 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-sided form (default).  X solves C2 X + X C1^T = L_B^-1 B L_A^-T; with
+// C1 = Q1 T1 Q1^T and Z = X Q1:
+//   R = L_B^-1 (B S_A^T)                      (S_A = Q1^T L_A^-1)
+//   C2 Z + Z T1^T = R, column blocks of T1 from the last:
+//     z_j = Gs_j r^_j + Gp_j r^_p,  r^_l = r_l - sum_{l' > l, outside the block} T1[l, l'] z_l'
+//   x = Z Q1^T.
+// Layout as in the two-sided kernel: NM lanes per element block, lane i owns
+// row i (of B, R, Z, X).  Each column step broadcasts the column's right-hand
+// side through shared memory, takes one (two for a 2x2 block) dense n x n
+// matvec with the stored inverse (rows read straight from global memory,
+// coalesced over the lanes), and updates the remaining columns of its own row
+// in registers.  Every FP64 instruction does useful work for all rows; there is
+// no per-step division and no cross-row dependency inside a column.
+template <typename T, int NM>
+__global__ void __launch_bounds__(128)
+k_apply_2d_g(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ LBi,
+             const T* __restrict__ Q1, const T* __restrict__ T1, const T* __restrict__ G,
+             const uint32_t* __restrict__ masks, const double* b, double* x,
+             const int32_t* skip, int fdiv) {
+  if (skip && *skip) return;
+  constexpr int EPW = 32 / NM;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = lane / NM, i = lane % NM;
+  const int wpb = blockDim.x >> 5;
+  const int eslot = warp * EPW + slot;
+  const int64_t e = ((int64_t)blockIdx.x * wpb + warp) * EPW + slot;
+  const bool eok = e < E;
+  const bool rok = eok && i < n;
+  const unsigned gmask = (NM == 32) ? 0xffffffffu : (((1u << NM) - 1u) << (slot * NM));
+  const int nn = n * n;
+  T* Fa = reinterpret_cast<T*>(smraw) + (size_t)eslot * 2 * NM * NM;   // S_A, then T1u, then Q1
+  T* Wm = Fa + NM * NM;                                                  // work, rhs broadcast
+  // vector block e; its factors are those of block e / fdiv (fdiv = 1 in 2D,
+  // n in 3D where the blocks are the z slices of an element, in place)
+  const int64_t g = eok ? e * nn : 0;
+  const int64_t ef = eok ? e / fdiv : 0;
+  const int64_t gf = ef * nn;
+  const T* Ge = G + (size_t)ef * 2 * n * nn;
+
+  // ---- W = B S_A^T: lane i holds row i of B
+  T row[NM], acc[NM];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? (T)b[g + i + n * k] : (T)0;
+  if (eok)
+    for (int q = i; q < nn; q += NM) Fa[q] = SA[gf + q];
+  __syncwarp(gmask);
+  for (int j = 0; j < n; ++j) {
+    T sacc = (T)0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+      if (k < n) sacc += row[k] * Fa[j + n * k];
+    if (rok) Wm[i + n * j] = sacc;
+  }
+  __syncwarp(gmask);
+  // ---- R = L_B^-1 W: lane i holds row i of L_B^-1; row i of R stays in registers
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? LBi[gf + i + n * k] : (T)0;
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    T sacc = (T)0;
+    if (j < n) {
+#pragma unroll
+      for (int k = 0; k < NM; ++k)
+        if (k < n) sacc += row[k] * Wm[k + n * j];
+    }
+    acc[j] = sacc;
+  }
+  __syncwarp(gmask);
+  // ---- T1 with its diagonal 1x1 / 2x2 blocks removed, and the block starts
+  uint32_t cst = 0;
+  {
+    const uint32_t m1 = eok ? masks[2 * ef] : 0u;
+    int r = 0;
+    while (r < n) {
+      const bool two = ((m1 >> r) & 1u) && r + 1 < n;
+      if (two) cst |= 1u << r;
+      r += two ? 2 : 1;
+    }
+  }
+  if (eok)
+    for (int q = i; q < nn; q += NM) {
+      const int rr = q % n, c = q / n;
+      const bool inblk = (rr == c) || (rr + 1 == c && ((cst >> rr) & 1u)) ||
+                         (c + 1 == rr && ((cst >> c) & 1u));
+      Fa[q] = inblk ? (T)0 : T1[gf + q];
+    }
+  __syncwarp(gmask);
+  // ---- column sweep, last column first
+  T rsave = (T)0;
+#pragma unroll
+  for (int jj = NM - 1; jj >= 0; --jj) {
+    if (jj < n) {
+      const T r = acc[jj];
+      const bool lo = ((cst >> jj) & 1u) != 0;                       // first column of a pair
+      const bool up = jj >= 1 && ((cst >> (jj - 1)) & 1u) != 0;      // second column of a pair
+      T rp = (T)0;
+      if (up) rp = acc[jj >= 1 ? jj - 1 : 0];
+      else if (lo) rp = rsave;
+      if (rok) {
+        Wm[i] = r;
+        Wm[NM + i] = rp;
+      }
+      __syncwarp(gmask);
+      const T* gs = Ge + (size_t)(2 * jj) * nn + (rok ? i : 0);   // idle lanes read row 0
+      T z0 = (T)0, z1 = (T)0;
+#pragma unroll
+      for (int k = 0; k < NM; k += 2) {
+        if (k < n) z0 += gs[(size_t)k * n] * Wm[k];
+        if (k + 1 < n) z1 += gs[(size_t)(k + 1) * n] * Wm[k + 1];
+      }
+      if (__any_sync(0xffffffffu, eok && (lo || up))) {
+        const T* gp = gs + nn;
+#pragma unroll
+        for (int k = 0; k < NM; k += 2) {
+          if (k < n) z0 += gp[(size_t)k * n] * Wm[NM + k];
+          if (k + 1 < n) z1 += gp[(size_t)(k + 1) * n] * Wm[NM + k + 1];
+        }
+      }
+      const T z = z0 + z1;
+      __syncwarp(gmask);
+      rsave = r;
+      acc[jj] = z;
+#pragma unroll
+      for (int jp = 0; jp < jj; ++jp) acc[jp] -= Fa[jp + n * jj] * z;
+    }
+  }
+  __syncwarp(gmask);
+  if (eok)
+    for (int q = i; q < nn; q += NM) Fa[q] = Q1[gf + q];
+  __syncwarp(gmask);
+  // ---- x = Z Q1^T: lane i holds row i of Z (acc)
+#pragma unroll
+  for (int k = 0; k < NM; ++k) row[k] = (rok && k < n) ? acc[k] : (T)0;
+  for (int j = 0; j < n; ++j) {
+    T sacc = (T)0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+      if (k < n) sacc += row[k] * Fa[j + n * k];
+    if (rok) x[g + i + n * j] = (double)sacc;
+  }
+}
+
+template <typename T, int NM>
+cudaError_t launch_g(int n, int64_t E, const T* SA, const T* LBi, const T* Q1, const T* T1,
+                     const T* G, const uint32_t* masks, const double* b, double* x,
+                     const int32_t* skip, int fdiv, cudaStream_t s) {
+  constexpr int EPW = 32 / NM;
+  const int warps = 4;
+  const int64_t per_block = (int64_t)warps * EPW;
+  const int64_t blocks = (E + per_block - 1) / per_block;
+  const size_t smem = (size_t)warps * EPW * 2 * NM * NM * sizeof(T);
+  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_g<T, NM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_apply_2d_g<T, NM><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, LBi, Q1, T1, G, masks,
+                                                                  b, x, skip, fdiv);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, int NM>
 cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, const T* Q2,
                      const T* T1, const T* T2, const uint32_t* masks, const double* b, double* x,
@@ -336,6 +498,18 @@ cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, co
 }
 
 template <typename T>
+cudaError_t launch_apply_one(const tpp_ctx* c, const T* SA, const T* LBi, const T* Q1,
+                             const T* T1, const T* G, const double* b, double* x,
+                             const int32_t* skip, cudaStream_t s) {
+  const uint32_t* masks = c->p<uint32_t>(c->L.masks);
+  const int fdiv = (c->dim == 3) ? c->n : 1;
+  const int64_t nb = c->E * fdiv;
+  if (c->n <= 8) return launch_g<T, 8>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+  if (c->n <= 16) return launch_g<T, 16>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+  return launch_g<T, 32>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+}
+
+template <typename T>
 cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* Q1, const T* Q2,
                            const T* T1, const T* T2, const double* b, double* x,
                            const int32_t* skip, cudaStream_t s) {
@@ -351,42 +525,70 @@ cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* 
 
 cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
                             const int32_t* skip, cudaStream_t s) {
+  const bool two = two_sided(c);
   if (prec == TPP_FP64) {
+    if (!two)
+      return launch_apply_one<double>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
+                                      c->p<double>(c->L.fQ1), c->p<double>(c->L.fT1),
+                                      c->p<double>(c->L.fG), b, x, skip, s);
     return launch_apply_t<double>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
                                   c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
                                   c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), b, x, skip, s);
   }
   const float* f = c->p<float>(c->L.f32);
-  const size_t st = (size_t)c->E * c->n * c->n;
-  return launch_apply_t<float>(c, f, f + st, f + 2 * st, f + 3 * st, f + 4 * st, f + 5 * st, b, x,
-                               skip, s);
+  const F32Layout F = f32_layout(c->n, c->E, c->dim, two);
+  if (!two)
+    return launch_apply_one<float>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.T1, f + F.G, b, x,
+                                   skip, s);
+  return launch_apply_t<float>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.Q2, f + F.T1, f + F.T2, b,
+                               x, skip, s);
 }
 
-// float copies of the apply factors (SA, SB, Q1, Q2, T1, T2), rounded to nearest
-__global__ void k_to_f32(const double* SA, const double* SB, const double* Q1, const double* Q2,
-                         const double* T1, const double* T2, const double* Azi, float* out,
-                         int64_t st, int nmat) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nmat * st;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int which = (int)(g / st);
-    const int64_t i = g % st;
-    const double* src = which == 0 ? SA : which == 1 ? SB : which == 2 ? Q1 : which == 3 ? Q2
-                      : which == 4 ? T1 : which == 5 ? T2 : Azi;
-    out[g] = __double2float_rn(src[i]);
+// float copies of the apply factors, rounded to nearest (up to 8 segments)
+struct F32Copy {
+  const double* src[8];
+  size_t dst[8], count[8];
+  int nseg;
+};
+
+__global__ void k_to_f32(F32Copy cp, float* out) {
+  for (int sg = 0; sg < cp.nseg; ++sg) {
+    const double* src = cp.src[sg];
+    float* dst = out + cp.dst[sg];
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < cp.count[sg];
+         g += (size_t)gridDim.x * blockDim.x)
+      dst[g] = __double2float_rn(src[g]);
   }
 }
 
 cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
-  const int64_t st = c->E * (int64_t)c->n * c->n;
-  k_to_f32<<<152 * 4, 256, 0, s>>>(c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
-                                   c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
-                                   c->p<double>(c->L.fT1), c->p<double>(c->L.fT2),
-                                   c->dim == 3 ? c->p<double>(c->L.fAzi) : nullptr,
-                                   c->p<float>(c->L.f32), st, c->dim == 3 ? 7 : 6);
+  const bool two = two_sided(c);
+  const F32Layout F = f32_layout(c->n, c->E, c->dim, two);
+  const size_t m = (size_t)c->E * c->n * c->n;
+  F32Copy cp{};
+  int k = 0;
+  auto add = [&](size_t off, const double* src, size_t count) {
+    cp.src[k] = src;
+    cp.dst[k] = off;
+    cp.count[k] = count;
+    ++k;
+  };
+  add(F.SA, c->p<double>(c->L.fSA), m);
+  add(F.SB, c->p<double>(c->L.fSB), m);
+  add(F.Q1, c->p<double>(c->L.fQ1), m);
+  add(F.T1, c->p<double>(c->L.fT1), m);
+  if (two) {
+    add(F.Q2, c->p<double>(c->L.fQ2), m);
+    add(F.T2, c->p<double>(c->L.fT2), m);
+  } else {
+    add(F.G, c->p<double>(c->L.fG), 2 * m * c->n);
+  }
+  if (c->dim == 3) add(F.Azi, c->p<double>(c->L.fAzi), m);
+  cp.nseg = k;
+  k_to_f32<<<152 * 4, 256, 0, s>>>(cp, c->p<float>(c->L.f32));
   count_launch();
   return cudaGetLastError();
 }
-
 
 // ---- 3D (Alg. 3d-apply): x = (A1^-1 (x) D1^-1) b.  The z factor acts first,
 // x~ = (A1^-1 (x) I) b, one thread per z line (i, j) of an element with the
@@ -433,7 +635,7 @@ cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int pr
     if (n <= 8) k_apply_z<double, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
     else k_apply_z<double, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
   } else {
-    const float* azi = c->p<float>(c->L.f32) + (size_t)6 * c->E * n * n;
+    const float* azi = c->p<float>(c->L.f32) + f32_layout(n, c->E, 3, two_sided(c)).Azi;
     if (n <= 8) k_apply_z<float, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
     else k_apply_z<float, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
   }

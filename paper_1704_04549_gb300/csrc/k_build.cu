@@ -302,15 +302,16 @@ __device__ void atomic_min_double(double* addr, double v) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Build pipeline (2D), four kernels, one warp per element or per matrix so
-// that every FP64 instruction is issued by a full warp and many elements are
-// in flight per SM:
-//   k_ksvd_w     coefficients, matrix-free Golub-Kahan-Lanczos on the core M,
-//                top-2 singular triplets, factors A_k, B_k          (a3, a4)
-//   k_invert_w   choice of the inverted pair, Gauss-Jordan inverses,
-//                C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2                  (a5)
-//   k_schur_w    real Schur form of each C_i (one warp per matrix)   (a5)
-//   k_final_w    S_A = Q_1^T L_A^-1, S_B = Q_2^T L_B^-1              (a5)
+// Build pipeline (2D), one warp per element or per matrix so that every FP64
+// instruction is issued by a full warp and many elements are in flight per SM:
+//   k_ksvd_w       coefficients, matrix-free Golub-Kahan-Lanczos on the core M,
+//                  top-2 singular triplets, factors A_k, B_k        (a3, a4)
+//   k_invert_w     choice of the inverted pair, Gauss-Jordan inverses,
+//                  C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2                (a5)
+//   k_schur_w      real Schur form of C_1 (and of C_2 in the two-sided form)
+//   k_shift_inv_w  one-sided form: inverses of the shifted diagonal systems
+//                  (C_2 + T_1[J, J]) of every column block of T_1
+//   k_final_w      S_A = Q_1^T L_A^-1 (two-sided: also S_B = Q_2^T L_B^-1)
 
 struct KsvdArgs {
   int n, rz;
@@ -490,6 +491,55 @@ __device__ bool warp_gauss_jordan(double* a, int n, double* fac) {
     __syncwarp();
   }
   return sing;
+}
+
+// Gauss-Jordan inverse of an m x m matrix (m <= M <= 32) held by rows in
+// registers: lane r < m holds row r in a[].  Pivot rows are chosen by largest
+// magnitude (compared on the upper 32 bits of |a|, integer pipe) and never
+// exchanged; rows are not normalised during the elimination (each step is one
+// FMA per remaining entry for every row but the pivot row), so at the end row r
+// of [A | I] reads [d_r e_{k_r} | d_r (row k_r of A^-1)].  On return b[] of lane
+// r holds row k_r of A^-1 and the function returns k_r (-1 for lanes >= m).
+// `sing` is set when a pivot is zero (its row of the inverse is then left 0).
+template <int M>
+__device__ __forceinline__ int warp_inverse_rows(double (&a)[M], double (&b)[M], int m, bool& sing) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < M; ++c) b[c] = (c == lane) ? 1.0 : 0.0;
+  bool used = lane >= m;
+  int kr = -1;
+  double d = 0.0;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    if (k < m) {
+      const int key = used ? -1 : (__double2hiint(a[k]) & 0x7fffffff);
+      const int mx = __reduce_max_sync(0xffffffffu, key);
+      unsigned bal = __ballot_sync(0xffffffffu, !used && key == mx);
+      if (mx <= 0) {
+        sing = true;
+        bal = __ballot_sync(0xffffffffu, !used);
+      }
+      const int p = __ffs(bal) - 1;
+      const double pv = __shfl_sync(0xffffffffu, a[k], p);
+      const double ip = (pv != 0.0) ? 1.0 / pv : 0.0;
+      const double f = (lane == p) ? 0.0 : a[k] * ip;
+      if (lane == p) {
+        used = true;
+        kr = k;
+        d = pv;
+      }
+#pragma unroll
+      for (int c = k + 1; c < M; ++c)
+        if (c < m) a[c] -= f * __shfl_sync(0xffffffffu, a[c], p);
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        if (c < m) b[c] -= f * __shfl_sync(0xffffffffu, b[c], p);
+    }
+  }
+  const double id = (d != 0.0) ? 1.0 / d : 0.0;
+#pragma unroll
+  for (int c = 0; c < M; ++c) b[c] *= id;
+  return kr;
 }
 
 }  // namespace
@@ -841,16 +891,17 @@ __global__ void __launch_bounds__(64) k_invert_w(InvArgs A) {
 }
 
 // ---- k_schur_w: real Schur form of C (staged in T1 / T2), one warp per matrix
-__global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, double* T1, double* T2,
-                                                 double* Q1, double* Q2, uint32_t* masks,
-                                                 int32_t* flags, DevStatus* st) {
+// (mpe = 2: C_1 and C_2 of every element; mpe = 1: C_1 only)
+__global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, double* T1,
+                                                 double* T2, double* Q1, double* Q2,
+                                                 uint32_t* masks, int32_t* flags, DevStatus* st) {
   extern __shared__ double sms[];
   const int nn = n * n, ld = ld_of(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t mtx = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (mtx >= 2 * E) return;
-  const int64_t e = mtx >> 1;
-  const int which = (int)(mtx & 1);
+  if (mtx >= mpe * E) return;
+  const int64_t e = mtx / mpe;
+  const int which = (int)(mtx % mpe);
   double* H = sms + (size_t)warp * (2 * n * ld + 32);
   double* Q = H + n * ld;
   double* vb = Q + n * ld;
@@ -882,6 +933,7 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, double* T1, d
     for (int i = 0; i + 1 < n; ++i)
       if (H[(i + 1) + ld * i] != 0.0) m |= 1u << i;
     masks[2 * e + which] = m;
+    if (mpe == 1) masks[2 * e + 1] = 0u;
     if (!ok) {
       atomicOr(reinterpret_cast<int*>(flags + e), 4);
       atomicAdd(&st->build_schur_fail, 1);
@@ -890,15 +942,16 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, double* T1, d
 }
 
 // ---- k_final_w: S_A = Q1^T L_A^-1, S_B = Q2^T L_B^-1 (in place over the staged inverses)
-__global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, double* SA, double* SB,
-                                                 const double* Q1, const double* Q2) {
+// (mpe = 2: both; mpe = 1: S_A only)
+__global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, int mpe, double* SA,
+                                                 double* SB, const double* Q1, const double* Q2) {
   extern __shared__ double smf[];
   const int nn = n * n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t mtx = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (mtx >= 2 * E) return;
-  const int64_t e = mtx >> 1;
-  const int which = (int)(mtx & 1);
+  if (mtx >= mpe * E) return;
+  const int64_t e = mtx / mpe;
+  const int which = (int)(mtx % mpe);
   double* Qs = smf + (size_t)warp * 2 * nn;
   double* Ls = Qs + nn;
   double* S = (which ? SB : SA) + e * nn;
@@ -913,6 +966,138 @@ __global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, double* SA, d
     double sv = 0.0;
     for (int k = 0; k < n; ++k) sv += Qs[k + n * rr] * Ls[k + n * c];
     S[q] = sv;
+  }
+}
+
+// ---- k_shift_inv_w: one-sided form of the quasi-triangular system.  With
+// C_1 = Q_1 T_1 Q_1^T only (C_2 left unreduced), (C_1 (x) I + I (x) C_2) vec(X)
+// = vec(R) becomes C_2 Z + Z T_1^T = R Q_1, Z = X Q_1, solved column block by
+// column block from the last: for a 1x1 diagonal block j of T_1,
+// (C_2 + T_1[j, j] I) z_j = r_j - sum_{l > j} T_1[j, l] z_l; for a 2x2 block
+// {j, j+1} the 2n x 2n system [[C_2 + t00 I, t01 I], [t10 I, C_2 + t11 I]].
+// This kernel inverts those diagonal systems (Gauss-Jordan with partial
+// pivoting, one warp per element) and stores, for every column j, the n x n
+// blocks Gs_j (own column) and Gp_j (partner column of its 2x2 block, zero for
+// 1x1): G[e][j][s][k][i], i fastest.  Rank-1 elements (C_1 = 0, C_2 = I)
+// store G = I.
+// entry (r, c) of the shifted system of the column block at j (size m = n or 2n)
+__device__ __forceinline__ double shifted_entry(const double* Tg, const double* Cg, bool rank1,
+                                                int n, int j, int r, int c) {
+  const int br = r / n, rr = r % n, bc = c / n, cc = c % n;
+  const double t = Tg[(j + br) + n * (j + bc)];
+  const double c2 = rank1 ? ((rr == cc) ? 1.0 : 0.0) : Cg[rr + n * cc];
+  return ((br == bc) ? c2 : 0.0) + ((rr == cc) ? t : 0.0);
+}
+
+// G entry for row `row`, column `col` of the inverse of the block at j
+__device__ __forceinline__ size_t g_index(int n, int j, int row, int col) {
+  const int nn = n * n, a = row / n, i = row % n, bc = col / n, k = col % n;
+  return ((size_t)(j + a) * 2 + (bc != a ? 1 : 0)) * nn + (size_t)k * n + i;
+}
+
+// Invert the shifted system of the column block at j (size m) and store its
+// rows in G.  Kept out of line: inside the block loop of the caller the fully
+// unrolled elimination would otherwise not stay in registers.
+template <int M>
+__device__ __noinline__ bool shift_inv_block(const double* Tg, const double* Cg, bool rank1, int n,
+                                             int j, int m, double* Ge) {
+  const int lane = threadIdx.x & 31;
+  bool sing = false;
+  double a[M], b[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c)
+    a[c] = (lane < m && c < m) ? shifted_entry(Tg, Cg, rank1, n, j, lane, c) : 0.0;
+  const int kr = warp_inverse_rows<M>(a, b, m, sing);
+  if (kr >= 0) {
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      if (c < m) Ge[g_index(n, j, kr, c)] = b[c];
+  }
+  return sing;
+}
+
+// n <= M / 2: one warp per element, register Gauss-Jordan (lanes own rows)
+template <int M>
+__global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const double* T1,
+                                                     const double* C2, const uint32_t* masks,
+                                                     int32_t* flags, double* G, DevStatus* st) {
+  const int nn = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;
+  const double* Tg = T1 + e * nn;
+  const double* Cg = C2 + e * nn;
+  const bool rank1 = (flags[e] & 2) != 0;
+  const uint32_t m1 = masks[2 * e];
+  double* Ge = G + (size_t)e * 2 * n * nn;
+  // block starts (the same walk as the apply), then Gp of 1x1 blocks is zero
+  uint32_t cst = 0;
+  for (int r = 0; r < n;) {
+    const bool two = ((m1 >> r) & 1u) && r + 1 < n;
+    if (two) cst |= 1u << r;
+    r += two ? 2 : 1;
+  }
+  for (int q = lane; q < 2 * n * nn; q += 32) {
+    const int j = q / (2 * nn), sblk = (q / nn) & 1;
+    const bool pairj = ((cst >> j) & 1u) || (j > 0 && ((cst >> (j - 1)) & 1u));
+    if (sblk == 1 && !pairj) Ge[q] = 0.0;
+  }
+  bool sing = false;
+  int j = 0;
+  while (j < n) {
+    const bool pair = ((m1 >> j) & 1u) && j + 1 < n;
+    sing |= pair ? shift_inv_block<M>(Tg, Cg, rank1, n, j, 2 * n, Ge)
+                 : shift_inv_block<M / 2>(Tg, Cg, rank1, n, j, n, Ge);
+    j += pair ? 2 : 1;
+  }
+  if (lane == 0 && sing) {
+    atomicOr(reinterpret_cast<int*>(flags + e), 8);
+    atomicAdd(&st->build_singular, 1);
+  }
+}
+
+// n > 16: shared-memory Gauss-Jordan (2n x 2n blocks exceed the register rows)
+__global__ void __launch_bounds__(128) k_shift_inv_w(int n, int64_t E, const double* T1,
+                                                     const double* C2, const uint32_t* masks,
+                                                     int32_t* flags, double* G, DevStatus* st) {
+  extern __shared__ double smg[];
+  const int nn = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;
+  double* aug = smg + (size_t)warp * (8 * nn + 2 * n + 8);
+  double* fac = aug + 8 * nn;
+  const double* Tg = T1 + e * nn;
+  const double* Cg = C2 + e * nn;
+  const bool rank1 = (flags[e] & 2) != 0;
+  const uint32_t m1 = masks[2 * e];
+  double* Ge = G + (size_t)e * 2 * n * nn;
+  bool sing = false;
+  int j = 0;
+  while (j < n) {
+    const bool pair = ((m1 >> j) & 1u) && j + 1 < n;
+    const int m = pair ? 2 * n : n;
+    for (int q = lane; q < 2 * m * m; q += 32) {
+      const int r = q % m, c = q / m;
+      aug[q] = (c < m) ? shifted_entry(Tg, Cg, rank1, n, j, r, c) : ((r == c - m) ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    sing |= warp_gauss_jordan(aug, m, fac);
+    const double* inv = aug + (size_t)m * m;
+    const int ncols = pair ? 2 : 1;
+    for (int q = lane; q < ncols * 2 * nn; q += 32) {
+      const int a = q / (2 * nn), sblk = (q / nn) & 1, rem = q % nn, k = rem / n, i = rem % n;
+      double v = 0.0;
+      if (sblk == 0) v = inv[(a * n + i) + m * (a * n + k)];
+      else if (pair) v = inv[(a * n + i) + m * ((1 - a) * n + k)];
+      Ge[((size_t)(j + a) * 2 + sblk) * nn + k * n + i] = v;
+    }
+    __syncwarp();
+    j += ncols;
+  }
+  if (lane == 0 && sing) {
+    atomicOr(reinterpret_cast<int*>(flags + e), 8);
+    atomicAdd(&st->build_singular, 1);
   }
 }
 
@@ -1009,29 +1194,54 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s) {
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  // 3. real Schur forms
+  // 3. real Schur forms: C_1 and C_2 (two-sided form), or C_1 only
+  const bool two = two_sided(c);
+  const int mpe = two ? 2 : 1;
   {
     const int warps = 4, ld = ld_of(n);
     const size_t smem = (size_t)warps * (2 * n * ld + 32) * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_schur_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
-    k_schur_w<<<(unsigned)((2 * E + warps - 1) / warps), warps * 32, smem, s>>>(
-        n, E, c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), c->p<double>(c->L.fQ1),
-        c->p<double>(c->L.fQ2), c->p<uint32_t>(c->L.masks), c->p<int32_t>(c->L.flags), st);
+    k_schur_w<<<(unsigned)((mpe * E + warps - 1) / warps), warps * 32, smem, s>>>(
+        n, E, mpe, c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), c->p<double>(c->L.fQ1),
+        two ? c->p<double>(c->L.fQ2) : nullptr, c->p<uint32_t>(c->L.masks),
+        c->p<int32_t>(c->L.flags), st);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  // 4. S_A, S_B
+  // 4. one-sided form: inverses of the shifted diagonal systems
+  if (!two) {
+    const double* T1p = c->p<double>(c->L.fT1);
+    const double* C2p = c->p<double>(c->L.fT2);
+    const uint32_t* mk = c->p<uint32_t>(c->L.masks);
+    int32_t* fl = c->p<int32_t>(c->L.flags);
+    double* Gp = c->p<double>(c->L.fG);
+    cudaError_t err;
+    if (n <= 8) {
+      k_shift_inv_r<16><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, st);
+    } else if (n <= 16) {
+      k_shift_inv_r<32><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, st);
+    } else {
+      const size_t smem = (size_t)(8 * nn + 2 * n + 8) * sizeof(double);
+      err = cudaFuncSetAttribute(k_shift_inv_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+      if (err != cudaSuccess) return err;
+      k_shift_inv_w<<<(unsigned)E, 32, smem, s>>>(n, E, T1p, C2p, mk, fl, Gp, st);
+    }
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  // 5. S_A = Q_1^T L_A^-1 (and S_B = Q_2^T L_B^-1 in the two-sided form)
   {
     const int warps = 4;
     const size_t smem = (size_t)warps * 2 * nn * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_final_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
-    k_final_w<<<(unsigned)((2 * E + warps - 1) / warps), warps * 32, smem, s>>>(
-        n, E, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB), c->p<double>(c->L.fQ1),
-        c->p<double>(c->L.fQ2));
+    k_final_w<<<(unsigned)((mpe * E + warps - 1) / warps), warps * 32, smem, s>>>(
+        n, E, mpe, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB), c->p<double>(c->L.fQ1),
+        two ? c->p<double>(c->L.fQ2) : nullptr);
     count_launch();
     return cudaGetLastError();
   }

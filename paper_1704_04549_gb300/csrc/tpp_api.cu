@@ -134,7 +134,8 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.fSA = take(fsz);
   L.fSB = take(fsz);
   L.fQ1 = take(fsz);
-  L.fQ2 = take(fsz);
+  const bool two = (features & TPP_FEAT_TWO_SIDED) != 0;
+  L.fQ2 = two ? take(fsz) : 0;
   L.fT1 = take(fsz);
   L.fT2 = take(fsz);
   L.fSC = take((size_t)E * 8);
@@ -155,7 +156,8 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
     L.sigz = take((size_t)E * 8);
     L.zflags = take((size_t)E * 4);
   }
-  L.f32 = (features & TPP_FEAT_MIXED) ? take((size_t)7 * E * n * n * 4) : 0;
+  L.fG = two ? 0 : take(fsz * 2 * n);
+  L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
   L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
   L.V = take((size_t)(m + 1) * N * 8);
@@ -425,7 +427,8 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
   o->SA = c->p<double>(c->L.fSA);
   o->SB = c->p<double>(c->L.fSB);
   o->Q1 = c->p<double>(c->L.fQ1);
-  o->Q2 = c->p<double>(c->L.fQ2);
+  o->Q2 = two_sided(c) ? c->p<double>(c->L.fQ2) : nullptr;
+  o->G = two_sided(c) ? nullptr : c->p<double>(c->L.fG);
   o->T1 = c->p<double>(c->L.fT1);
   o->T2 = c->p<double>(c->L.fT2);
   o->flags = c->p<int32_t>(c->L.flags);

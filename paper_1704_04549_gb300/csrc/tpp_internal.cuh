@@ -73,6 +73,7 @@ struct Layout {
   size_t flags, masks;
   size_t bscr, biscr;                  // factor-build scratch (Lanczos bases, tridiagonal work)
   size_t kco;                          // per-block KSVD coefficients (Cx, Cy, Dg)
+  size_t fG;                           // one-sided form: shifted inverses, 2 n^3 per element
   size_t s1scr, fAz, fAzi, sigz, zflags;   // 3D stage 1: scratch, A1, A1^-1, sigma_1, flags
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
@@ -156,6 +157,28 @@ __host__ __device__ inline int s1_jmax(int n) { return (n * n < 64) ? n * n : 64
 
 cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s);
+// float32 copies of the apply factors (offsets in floats from Layout::f32)
+struct F32Layout {
+  size_t SA, SB, Q1, Q2, T1, T2, Azi, G, total;
+};
+inline F32Layout f32_layout(int n, int64_t E, int dim, bool two) {
+  const size_t m = (size_t)E * n * n;
+  F32Layout L{};
+  size_t o = 0;
+  L.SA = o; o += m;
+  L.SB = o; o += m;
+  L.Q1 = o; o += m;
+  L.T1 = o; o += m;
+  if (two) { L.Q2 = o; o += m; L.T2 = o; o += m; }
+  if (dim == 3) { L.Azi = o; o += m; }
+  if (!two) { L.G = o; o += 2 * m * n; }
+  L.total = o;
+  return L;
+}
+
+// the paper's two-sided Schur form (both factor products reduced) instead of
+// the default one-sided form with shifted inverses
+inline bool two_sided(const tpp_ctx* c) { return (c->features & TPP_FEAT_TWO_SIDED) != 0; }
 cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
                             const int32_t* skip, cudaStream_t s);
 cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,

@@ -151,6 +151,8 @@ class Context:
         torch.cuda.synchronize(self.device)
 
         def grab(addr, count, dtype):
+            if not addr:
+                return None                    # array absent in this form / dimension
             out = torch.empty(count, dtype=dtype, device=self.device)
             L.check(self.lib.tpp_copy_device(_ptr(out), C.c_void_p(addr),
                                              count * out.element_size(), _stream(None)),
@@ -160,7 +162,8 @@ class Context:
         res = {"sigma": grab(v.sigma, 2 * E, torch.float64).view(E, 2)}
         for name in ("A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2"):
             # column-major n x n per element -> [E, n, n] with [e, row, col]
-            res[name] = grab(getattr(v, name), E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
+            t = grab(getattr(v, name), E * n * n, torch.float64)
+            res[name] = None if t is None else t.view(E, n, n).transpose(1, 2)
         res["flags"] = grab(v.flags, E, torch.int32)
         res["cond"] = grab(v.cond, E, torch.float64)
         res["gl_x"] = grab(v.gl_x, n, torch.float64)

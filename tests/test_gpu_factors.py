@@ -5,6 +5,7 @@ import pytest
 import synthetic
 from oracle.ksvd import ksvd_2d, kron_sum
 from oracle.precond import apply_dense
+from paper_1704_04549_gb300 import TPP_FEAT_TWO_SIDED
 from tests.gpu_util import make_pair, rel, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
@@ -42,10 +43,12 @@ def _check_elements(ctx, dg, elems, tol_sigma=1e-12, tol_P=1e-12, tol_x=1e-12):
                                          (5, (3, 5), "fourier"), (8, (8, 8), "const"),
                                          (8, (4, 4), "fourier"), (16, (3, 3), "fourier"),
                                          (31, (2, 2), "fourier"), (32, (1, 2), "fourier")])
-def test_factors_and_apply_match_oracle(n, nel, field):
+@pytest.mark.parametrize("form", ["one-sided", "two-sided"])
+def test_factors_and_apply_match_oracle(n, nel, field, form):
     vel = (synthetic.constant_velocity([1.0, 0.5]) if field == "const"
            else synthetic.fourier_velocity(1705, 2))
-    ctx, dg = make_pair(n, nel, 0.05, vel)
+    ctx, dg = make_pair(n, nel, 0.05, vel,
+                        features=TPP_FEAT_TWO_SIDED if form == "two-sided" else 0)
     rep = ctx.tpp_build_factors()
     assert rep["num_schur_fail"] == 0
     elems = list(range(dg.mesh.num_elem)) if dg.mesh.num_elem <= 16 else [0, 5, dg.mesh.num_elem - 1]
