@@ -304,8 +304,10 @@ __device__ void atomic_min_double(double* addr, double v) {
 // ---------------------------------------------------------------------------
 // Build pipeline (2D), one warp per element or per matrix so that every FP64
 // instruction is issued by a full warp and many elements are in flight per SM:
-//   k_ksvd_w       coefficients, matrix-free Golub-Kahan-Lanczos on the core M,
-//                  top-2 singular triplets, factors A_k, B_k        (a3, a4)
+//   k_ksvd_w       the core M of the rearranged block (r = n + rz), dense
+//                  Householder bidiagonalisation, top-2 singular triplets
+//                  of the bidiagonal (multisection + inverse iteration on
+//                  its Golub-Kahan tridiagonal), factors A_k, B_k    (a3, a4)
 //   k_invert_w     choice of the inverted pair, Gauss-Jordan inverses,
 //                  C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2                (a5)
 //   k_schur_w      real Schur form of C_1 (and of C_2 in the two-sided form)
@@ -324,23 +326,20 @@ struct KsvdArgs {
   DevStatus* st;
 };
 
-// shared-memory layout of one warp of k_ksvd_w (offsets in doubles)
+// shared-memory layout of one warp of k_ksvd_w (offsets in doubles): the core
+// M (r x r, odd leading dimension against bank conflicts), the bidiagonal,
+// the Golub-Kahan tridiagonal and its two eigenvectors, the singular vectors
+// in M coordinates and the Householder scalars
 struct KsvdSmem {
-  int cx, cy, dg, vs, ps, ta, tb, cf, al, be, ee, e2s, z1, z2, mu1, mv1, mu2, mv2, scal, total;
+  int M, ldm, al, be, ee, e2s, z1, z2, mu1, mv1, mu2, mv2, tl, tr, scal, total;
 };
 
 __host__ __device__ inline KsvdSmem ksvd_smem(int n, int rz) {
-  const int nc = n + 2, r = n + rz;
+  const int r = n + rz;
   KsvdSmem L;
   int o = 0;
-  L.cx = o; o += nc * n;
-  L.cy = o; o += nc * n;
-  L.dg = o; o += n * n;
-  L.vs = o; o += r;
-  L.ps = o; o += r;
-  L.ta = o; o += nc;
-  L.tb = o; o += nc;
-  L.cf = o; o += 32;
+  L.ldm = r | 1;
+  L.M = o; o += r * L.ldm;
   L.al = o; o += r;
   L.be = o; o += r + 1;
   L.ee = o; o += 2 * r;
@@ -351,74 +350,14 @@ __host__ __device__ inline KsvdSmem ksvd_smem(int n, int rz) {
   L.mv1 = o; o += r;
   L.mu2 = o; o += r;
   L.mv2 = o; o += r;
+  L.tl = o; o += r;
+  L.tr = o; o += r;
   L.scal = o; o += 8;
   L.total = (o + 1) & ~1;
   return L;
 }
 
 namespace {
-
-// out = M v for the core M = [[Cx^T Zd^T + Zd Cy + Dg^T, Cx^T Rz^T], [Rz Cy, 0]]
-// without forming it: top = Cx^T (Zd^T v1 + Rz^T v2) + Zd (Cy v1) + Dg^T v1,
-// bottom = Rz (Cy v1).  Dg[q + n p] is the block's diagonal at (i = q, j = p).
-__device__ void warp_mv_M(const double* Cx, const double* Cy, const double* Dg,
-                          const double* __restrict__ Zd, const double* __restrict__ Rz, int n,
-                          int rz, const double* v, double* out, double* ta, double* tb) {
-  const int nc = n + 2, lane = threadIdx.x & 31;
-  for (int c = lane; c < nc; c += 32) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < n; ++q) {
-      a += Cy[c * n + q] * v[q];
-      b += __ldg(Zd + q * nc + c) * v[q];
-    }
-    for (int t = 0; t < rz; ++t) b += __ldg(Rz + t * nc + c) * v[n + t];
-    ta[c] = a;
-    tb[c] = b;
-  }
-  __syncwarp();
-  for (int p = lane; p < n; p += 32) {
-    double sv = 0.0;
-    for (int c = 0; c < nc; ++c) sv += Cx[c * n + p] * tb[c] + __ldg(Zd + p * nc + c) * ta[c];
-    for (int q = 0; q < n; ++q) sv += Dg[q + n * p] * v[q];
-    out[p] = sv;
-  }
-  for (int t = lane; t < rz; t += 32) {
-    double sv = 0.0;
-    for (int c = 0; c < nc; ++c) sv += __ldg(Rz + t * nc + c) * ta[c];
-    out[n + t] = sv;
-  }
-  __syncwarp();
-}
-
-// out = M^T u: top = Zd (Cx u1) + Cy^T (Zd^T u1 + Rz^T u2) + Dg u1, bottom = Rz (Cx u1).
-__device__ void warp_mv_MT(const double* Cx, const double* Cy, const double* Dg,
-                           const double* __restrict__ Zd, const double* __restrict__ Rz, int n,
-                           int rz, const double* u, double* out, double* ta, double* tb) {
-  const int nc = n + 2, lane = threadIdx.x & 31;
-  for (int c = lane; c < nc; c += 32) {
-    double a = 0.0, b = 0.0;
-    for (int p = 0; p < n; ++p) {
-      a += Cx[c * n + p] * u[p];
-      b += __ldg(Zd + p * nc + c) * u[p];
-    }
-    for (int t = 0; t < rz; ++t) b += __ldg(Rz + t * nc + c) * u[n + t];
-    ta[c] = a;
-    tb[c] = b;
-  }
-  __syncwarp();
-  for (int q = lane; q < n; q += 32) {
-    double sv = 0.0;
-    for (int c = 0; c < nc; ++c) sv += __ldg(Zd + q * nc + c) * ta[c] + Cy[c * n + q] * tb[c];
-    for (int p = 0; p < n; ++p) sv += Dg[q + n * p] * u[p];
-    out[q] = sv;
-  }
-  for (int t = lane; t < rz; t += 32) {
-    double sv = 0.0;
-    for (int c = 0; c < nc; ++c) sv += __ldg(Rz + t * nc + c) * ta[c];
-    out[n + t] = sv;
-  }
-  __syncwarp();
-}
 
 // p (shared, length r) minus its projections on the first k rows of B
 // (global, row i at B + i r), twice; coefficients 32 at a time, one per lane.
@@ -553,101 +492,111 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   if (e >= A.E) return;                                  // whole warp leaves together
   const KsvdSmem L = ksvd_smem(n, rz);
   double* sm = smk + (size_t)warp * L.total;
-  double *Cx = sm + L.cx, *Cy = sm + L.cy, *Dg = sm + L.dg, *vs = sm + L.vs, *ps = sm + L.ps;
-  double *ta = sm + L.ta, *tb = sm + L.tb, *cf = sm + L.cf, *al = sm + L.al, *be = sm + L.be;
-  double *ee = sm + L.ee, *e2s = sm + L.e2s, *z1 = sm + L.z1, *z2 = sm + L.z2;
+  double* Ms = sm + L.M;
+  const int ld = L.ldm;
+  double *al = sm + L.al, *be = sm + L.be, *ee = sm + L.ee, *e2s = sm + L.e2s;
+  double *z1 = sm + L.z1, *z2 = sm + L.z2, *tl = sm + L.tl, *tr = sm + L.tr;
   double *mu1 = sm + L.mu1, *mv1 = sm + L.mv1, *mu2 = sm + L.mu2, *mv2 = sm + L.mv2;
   double* scal = sm + L.scal;
-  double* U = A.scr + (size_t)e * (2 * (size_t)r * r + 16 * (size_t)r);
-  double* V = U + (size_t)r * r;
-  double* tw = V + (size_t)r * r;
+  double* tw = A.scr + (size_t)e * (2 * (size_t)r * r + 16 * (size_t)r) + 2 * (size_t)r * r;
   int* piv = A.iscr + (size_t)e * 4 * r;
   const int64_t base = e * nn;
+  const double* kc = A.kco + (size_t)e * (2 * nc * n + nn);
+  const double *Cx = kc, *Cy = kc + nc * n, *Dg = kc + 2 * nc * n;
 
-  // ---- coefficients of the rearranged block
-  {
-    const double* src = A.kco + (size_t)e * (2 * nc * n + nn);
-    for (int q = lane; q < 2 * nc * n + nn; q += 32) Cx[q] = src[q];   // Cx, Cy, Dg contiguous
-  }
-  __syncwarp();
-  // scale of M (Frobenius norm of A~) for the breakdown tolerance: ||M||_F
-  // is bounded by the coefficient norms times the basis norms; use the
-  // cheaper bound sqrt(sum Cx^2 + sum Cy^2) * max(||Zd||, ||Rz||) (only the
-  // invariant-subspace test uses it)
-  double cs2 = 0.0, dg2 = 0.0;
-  for (int q = lane; q < 2 * nc * n; q += 32) cs2 += Cx[q] * Cx[q];
-  for (int q = lane; q < nn; q += 32) dg2 += Dg[q] * Dg[q];
-  cs2 = warp_sum(cs2);
-  dg2 = warp_sum(dg2);
-  double zs2 = 0.0;
-  for (int q = lane; q < n * nc; q += 32) zs2 += __ldg(A.Zd + q) * __ldg(A.Zd + q);
-  for (int q = lane; q < rz * nc; q += 32) zs2 += __ldg(A.Rz + q) * __ldg(A.Rz + q);
-  zs2 = warp_sum(zs2);
-  const double tol = 1e-12 * (sqrt(cs2 * zs2) + sqrt(dg2));
-
-  // ---- Golub-Kahan-Lanczos with full reorthogonalisation (Alg. lanczos)
-  for (int t = lane; t < r; t += 32) vs[t] = splitmix_unit(1, t);
-  __syncwarp();
-  {
-    const double nv = 1.0 / sqrt(warp_norm2(vs, r));
-    for (int t = lane; t < r; t += 32) {
-      vs[t] *= nv;
-      V[t] = vs[t];
+  // ---- the core M of the rearranged block, A~ = Q M Q^T (Q = [E | Qo]):
+  // M = [[Cx^T Zd^T + Zd Cy + Dg^T, Cx^T Rz^T], [Rz Cy, 0]]
+  for (int q = lane; q < r * r; q += 32) {
+    const int i = q % r, j = q / r;
+    double v = 0.0;
+    if (i < n && j < n) {
+      for (int c = 0; c < nc; ++c)
+        v += __ldg(Cx + c * n + i) * __ldg(A.Zd + j * nc + c) +
+             __ldg(A.Zd + i * nc + c) * __ldg(Cy + c * n + j);
+      v += __ldg(Dg + j + n * i);
+    } else if (i < n) {
+      const int t = j - n;
+      for (int c = 0; c < nc; ++c) v += __ldg(Cx + c * n + i) * __ldg(A.Rz + t * nc + c);
+    } else if (j < n) {
+      const int t = i - n;
+      for (int c = 0; c < nc; ++c) v += __ldg(A.Rz + t * nc + c) * __ldg(Cy + c * n + j);
     }
-    if (lane == 0) be[0] = 0.0;
+    Ms[i + ld * j] = v;
   }
   __syncwarp();
-  int J = (r < 24) ? r : 24;
-  int jdone = 0;
-  for (int pass = 0; pass < 3; ++pass) {
-    for (int j = jdone; j < J; ++j) {
-      // p = M v_j - beta_j u_{j-1}      (vs holds v_j)
-      warp_mv_M(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, vs, ps, ta, tb);
-      if (j > 0)
-        for (int t = lane; t < r; t += 32) ps[t] -= be[j] * U[(size_t)(j - 1) * r + t];
-      __syncwarp();
-      warp_reorth(ps, U, j, r, cf);
-      double a = sqrt(warp_norm2(ps, r));
-      if (a <= tol) {            // invariant subspace: continue with a fresh direction
-        for (int t = lane; t < r; t += 32) ps[t] = splitmix_unit(1000 + j, t);
-        __syncwarp();
-        warp_reorth(ps, U, j, r, cf);
-        const double nrm = 1.0 / sqrt(warp_norm2(ps, r));
-        for (int t = lane; t < r; t += 32) ps[t] *= nrm;
-        a = 0.0;
-      } else {
-        const double ia = 1.0 / a;
-        for (int t = lane; t < r; t += 32) ps[t] *= ia;
+
+  // ---- Householder bidiagonalisation M = U_h B V_h^T (B upper bidiagonal:
+  // diagonal al[k], superdiagonal be[k + 1]); the reflector vectors stay in
+  // M below the diagonal (left, unit first entry implied) and right of the
+  // superdiagonal (right)
+  for (int k = 0; k < r; ++k) {
+    double* colk = Ms + ld * k;
+    double sg = 0.0;
+    for (int i = k + 1 + lane; i < r; i += 32) sg += colk[i] * colk[i];
+    sg = warp_sum(sg);
+    const double x0 = colk[k];
+    double tau = 0.0, alpha = x0;
+    if (sg > 0.0) {
+      const double nx = sqrt(x0 * x0 + sg);
+      alpha = (x0 > 0.0) ? -nx : nx;
+      tau = (alpha - x0) / alpha;
+      const double iv = 1.0 / (x0 - alpha);
+      for (int i = k + 1 + lane; i < r; i += 32) colk[i] *= iv;
+    }
+    __syncwarp();
+    if (tau != 0.0) {
+      for (int j = k + 1 + lane; j < r; j += 32) {
+        double* cj = Ms + ld * j;
+        double sv = cj[k];
+        for (int i = k + 1; i < r; ++i) sv += colk[i] * cj[i];
+        sv *= tau;
+        cj[k] -= sv;
+        for (int i = k + 1; i < r; ++i) cj[i] -= sv * colk[i];
       }
-      for (int t = lane; t < r; t += 32) U[(size_t)j * r + t] = ps[t];
-      if (lane == 0) al[j] = a;
+    }
+    if (lane == 0) {
+      al[k] = alpha;
+      tl[k] = tau;
+    }
+    __syncwarp();
+    if (k + 1 < r) {
+      double sg2 = 0.0;
+      for (int j = k + 2 + lane; j < r; j += 32) {
+        const double v = Ms[k + ld * j];
+        sg2 += v * v;
+      }
+      sg2 = warp_sum(sg2);
+      const double y0 = Ms[k + ld * (k + 1)];
+      double tau2 = 0.0, beta = y0;
+      if (sg2 > 0.0) {
+        const double ny = sqrt(y0 * y0 + sg2);
+        beta = (y0 > 0.0) ? -ny : ny;
+        tau2 = (beta - y0) / beta;
+        const double iv = 1.0 / (y0 - beta);
+        for (int j = k + 2 + lane; j < r; j += 32) Ms[k + ld * j] *= iv;
+      }
       __syncwarp();
-      if (j + 1 < r) {
-        // q = M^T u_j - alpha_j v_j      (ps holds u_j; result into ta/tb scratch then vs)
-        warp_mv_MT(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, ps, ee, ta, tb);   // ee as scratch (length >= r)
-        for (int t = lane; t < r; t += 32) vs[t] = ee[t] - a * vs[t];
-        __syncwarp();
-        warp_reorth(vs, V, j + 1, r, cf);
-        double b = sqrt(warp_norm2(vs, r));
-        if (b <= tol) {
-          for (int t = lane; t < r; t += 32) vs[t] = splitmix_unit(2000 + j, t);
-          __syncwarp();
-          warp_reorth(vs, V, j + 1, r, cf);
-          const double nrm = 1.0 / sqrt(warp_norm2(vs, r));
-          for (int t = lane; t < r; t += 32) vs[t] *= nrm;
-          b = 0.0;
-        } else {
-          const double ib = 1.0 / b;
-          for (int t = lane; t < r; t += 32) vs[t] *= ib;
+      if (tau2 != 0.0) {
+        for (int i = k + 1 + lane; i < r; i += 32) {
+          double sv = Ms[i + ld * (k + 1)];
+          for (int j = k + 2; j < r; ++j) sv += Ms[i + ld * j] * Ms[k + ld * j];
+          sv *= tau2;
+          Ms[i + ld * (k + 1)] -= sv;
+          for (int j = k + 2; j < r; ++j) Ms[i + ld * j] -= sv * Ms[k + ld * j];
         }
-        for (int t = lane; t < r; t += 32) V[(size_t)(j + 1) * r + t] = vs[t];
-        if (lane == 0) be[j + 1] = b;
-        __syncwarp();
       }
+      if (lane == 0) {
+        be[k + 1] = beta;
+        tr[k] = tau2;
+      }
+      __syncwarp();
     }
-    jdone = J;
+  }
+  const int J = r;
 
-    // ---- top-2 singular values / vectors of the J x J bidiagonal matrix
+  // ---- top-2 singular values / vectors of the bidiagonal B through its
+  // Golub-Kahan tridiagonal (order 2r, zero diagonal)
+  {
     const int m = 2 * J;
     for (int t = lane; t < m - 1; t += 32) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
     __syncwarp();
@@ -693,55 +642,64 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
                         kEps * bnd + 1e-300);
     }
     __syncwarp();
-    if (lane == 0) {
-      if (J >= 2) {                    // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
-        double dt = 0.0;
-        for (int i = 0; i < m; ++i) dt += z1[i] * z2[i];
-        double nr = 0.0;
-        for (int i = 0; i < m; ++i) {
-          z2[i] -= dt * z1[i];
-          nr += z2[i] * z2[i];
-        }
-        nr = 1.0 / sqrt(nr);
-        for (int i = 0; i < m; ++i) z2[i] *= nr;
+    if (lane == 0 && J >= 2) {         // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
+      double dt = 0.0;
+      for (int i = 0; i < m; ++i) dt += z1[i] * z2[i];
+      double nr = 0.0;
+      for (int i = 0; i < m; ++i) {
+        z2[i] -= dt * z1[i];
+        nr += z2[i] * z2[i];
       }
-      // residuals of the Ritz triplets: beta_J |u'_{J-1}| with ||u'|| = 1/sqrt(2)
-      const double bJ = (J < r) ? be[J] : 0.0;
-      const double r1 = bJ * fabs(z1[m - 1]) * 1.4142135623730951;
-      const double r2 = (J >= 2) ? bJ * fabs(z2[m - 1]) * 1.4142135623730951 : 0.0;
-      scal[2] = (r1 <= 1e-14 * scal[0] && r2 <= 1e-14 * scal[0]) ? 1.0 : 0.0;
+      nr = 1.0 / sqrt(nr);
+      for (int i = 0; i < m; ++i) z2[i] *= nr;
     }
     __syncwarp();
-    if (scal[2] != 0.0 || J == r) break;
-    J = (J + 24 < r) ? J + 24 : r;
   }
   const int nsv = (J >= 2) ? 2 : 1;
-  // ---- Ritz vectors in M space (v = V v', u = U u'), gauge trace(A_k) >= 0
+  // ---- singular vectors in M coordinates: u = U_h u', v = V_h v' (u' from the
+  // odd, v' from the even entries of z), reflectors applied last to first;
+  // gauge trace(A_k) >= 0
   for (int k = 0; k < 2; ++k) {
     const double* z = k ? z2 : z1;
     double* mu = k ? mu2 : mu1;
     double* mv = k ? mv2 : mv1;
-    for (int sidx = lane; sidx < r; sidx += 32) {
-      double a = 0.0, b = 0.0;
-      if (k < nsv)
-        for (int t = 0; t < J; ++t) {
-          a += z[2 * t + 1] * U[(size_t)t * r + sidx];
-          b += z[2 * t] * V[(size_t)t * r + sidx];
-        }
-      mu[sidx] = a;
-      mv[sidx] = b;
+    for (int t = lane; t < r; t += 32) {
+      mu[t] = (k < nsv) ? z[2 * t + 1] : 0.0;
+      mv[t] = (k < nsv) ? z[2 * t] : 0.0;
     }
     __syncwarp();
     if (k < nsv) {
+      for (int q = r - 1; q >= 0; --q) {
+        const double* cq = Ms + ld * q;
+        if (tl[q] != 0.0) {
+          double dt = 0.0;
+          for (int i = q + 1 + lane; i < r; i += 32) dt += cq[i] * mu[i];
+          dt = warp_sum(dt) + mu[q];
+          const double f = tl[q] * dt;
+          for (int i = q + 1 + lane; i < r; i += 32) mu[i] -= f * cq[i];
+          __syncwarp();
+          if (lane == 0) mu[q] -= f;
+        }
+        if (q + 1 < r && tr[q] != 0.0) {
+          double dt = 0.0;
+          for (int j = q + 2 + lane; j < r; j += 32) dt += Ms[q + ld * j] * mv[j];
+          dt = warp_sum(dt) + mv[q + 1];
+          const double f = tr[q] * dt;
+          for (int j = q + 2 + lane; j < r; j += 32) mv[j] -= f * Ms[q + ld * j];
+          __syncwarp();
+          if (lane == 0) mv[q + 1] -= f;
+        }
+        __syncwarp();
+      }
       const double pu = warp_norm2(mu, r), pvv = warp_norm2(mv, r);
-      double tr = 0.0;
-      for (int t = lane; t < n; t += 32) tr += mu[t];
-      tr = warp_sum(tr);
-      const double sgn = (tr < 0.0) ? -1.0 : 1.0;
+      double trc = 0.0;
+      for (int t = lane; t < n; t += 32) trc += mu[t];
+      trc = warp_sum(trc);
+      const double sgn = (trc < 0.0) ? -1.0 : 1.0;
       const double fu = sgn / sqrt(pu), fv = sgn / sqrt(pvv);
-      for (int sidx = lane; sidx < r; sidx += 32) {
-        mu[sidx] *= fu;
-        mv[sidx] *= fv;
+      for (int t = lane; t < r; t += 32) {
+        mu[t] *= fu;
+        mv[t] *= fv;
       }
     }
     __syncwarp();

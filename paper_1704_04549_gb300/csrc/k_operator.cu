@@ -314,11 +314,12 @@ __global__ void k_traces(const Tables* T, int n, int64_t E, const double* __rest
   }
 }
 
-cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s) {
+cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
+                          const int32_t* skip) {
   if (c->dim == 2)
-    k_traces<2><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, nullptr);
+    k_traces<2><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
   else
-    k_traces<3><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, nullptr);
+    k_traces<3><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
   count_launch();
   return cudaGetLastError();
 }

@@ -52,6 +52,7 @@ namespace {
 constexpr int kPartialBlocks = 152 * 4;
 constexpr int kPartialStride = 64;
 constexpr int kMaxRestart = 63;
+constexpr int kLookahead = 8;     // Arnoldi steps enqueued between host reads of the state
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -543,13 +544,18 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     res->cycles += 1;
     TPP_TRY_CUDA(vec_scale(V, V, N, nullptr, 1.0 / beta, nullptr, s), "scale v0");
     TPP_TRY_CUDA(gmres_cycle_init(st, g, beta, m, bnorm, opts->rtol, s), "cycle init");
+    // Arnoldi steps are enqueued kLookahead at a time; every kernel of a step
+    // returns at once when the device state says the cycle is done (converged,
+    // breakdown or restart length reached), so the host reads the state only
+    // once per group instead of after every step.
     GmresState hs;
+    const int cycle_start = total;
     for (int j = 0; j < m && total < opts->max_iters; ++j) {
       double* vj = V + (size_t)j * N;
       double* w = V + (size_t)(j + 1) * N;
       double* z = flexible ? Z + (size_t)j * N : t1;
       TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, vj, z, done, s), "precond");
-      TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s), "traces");
+      TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s, done), "traces");
       TPP_TRY_CUDA(launch_dg_apply(c, z, c->p<double>(c->L.traces), w, done, s), "operator");
       TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, h1,
                               &st->tickets[0], s), "dots");
@@ -559,10 +565,13 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
       TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, done, nullptr,
                                 &st->tickets[2], st, H, cs, sn, g, h1, h2, invb, j, s),
                    "norm+givens");
-      TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, nullptr, s), "scale");
+      TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, done, s), "scale");
       ++total;
+      const bool group_end = ((j + 1) % kLookahead) == 0 || j + 1 == m || total >= opts->max_iters;
+      if (!group_end) continue;
       TPP_TRY_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s), "read state");
       TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
+      total = cycle_start + hs.k;          // steps the device actually took
       res->est_rel_res = hs.est;
       if (hs.done) break;
     }

@@ -112,7 +112,8 @@ tpp_status cuda_check(cudaError_t e, const char* what);
 cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s);
-cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s);
+cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
+                          const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s);
