@@ -238,12 +238,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     inner = TPP_FP32 if args.prec == "mixed" else TPP_FP64
 
+    kin = args.inner if inner != TPP_FP64 else 0
+
     def step():
         ctx.tpp_build_factors()
         x.zero_()
         _, res = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters,
                                  pc=TPP_PC_KRON, inner_prec=inner, flexible=(inner != TPP_FP64),
-                                 check=False)
+                                 check=False, inner_iters=kin)
         return res
 
     for _ in range(args.warmup):
@@ -307,7 +309,8 @@ def run_ours(args):
         ctx.tpp_build_factors()
         xd = torch.zeros_like(bd)
         ctx.gmres_solve(bd, xd, restart=30, rtol=1e-8, max_iters=args.max_iters, pc=TPP_PC_KRON,
-                        inner_prec=inner, flexible=(inner != TPP_FP64), check=False)
+                        inner_prec=inner, flexible=(inner != TPP_FP64), check=False,
+                        inner_iters=kin)
         x_pin.copy_(xd, non_blocking=True)
         torch.cuda.synchronize(dev)
         if it > 0:
@@ -330,11 +333,16 @@ def run_ours(args):
                    "n": n, "nel": [64, 64], "h": 1.0, "dt": 0.05, "dofs": N, "rtol": 1e-8,
                    "restart": 30, "preconditioner": "KSVD rank-2 (Alg. 2d-form / 2d-apply)",
                    "inner_prec": args.prec, "apply_form": args.form,
+                   "solver": ("FP64 flexible GMRES(30) around inner FP32 GMRES(%d) solves "
+                              "(FP32 operator + FP32 Kronecker apply)" % kin) if kin > 0 else
+                             ("flexible GMRES(30), FP32 Kronecker apply" if inner != TPP_FP64
+                              else "GMRES(30), FP64"),
                    "l2": "step: inputs larger than L2 (Krylov basis %.0f MB + factors %.0f MB); "
                          "precond_apply: L2 flushed (256 MB write) before each timed launch"
                          % (31 * N * 8 / 1e6, 6 * N * 8 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "gmres": {"iters": res["iters"], "cycles": res["cycles"], "converged": converged,
+        "gmres": {"iters": res["iters"], "inner_iters": res["inner_iters"],
+                  "cycles": res["cycles"], "converged": converged,
                   "true_rel_res": res["true_rel_res"], "build_ms": build_ms,
                   "solve_ms": ms - build_ms},
         "precond_apply": {"fp64_gdofs": apply["fp64"]["gdofs"], "fp64_ms": apply["fp64"]["ms"],
@@ -389,15 +397,15 @@ def run_3d(args):
         op_ms = time_each(lambda: ctx.dg_apply_sumfact(b, z), 10 * args.steps, stream, flush)
     launches = lib.tpp_kernel_launch_count() - l0
     gm = {}
-    for name, prec in (("fp64", TPP_FP64), ("mixed", TPP_FP32)):
+    for name, prec, kin in (("fp64", TPP_FP64, 0), ("mixed", TPP_FP32, args.inner)):
         x = torch.zeros_like(b)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters,
                                pc=TPP_PC_KRON, inner_prec=prec, flexible=(prec != TPP_FP64),
-                               check=False)
-        gm[name] = {"iters": r["iters"], "converged": bool(r["converged"]),
-                    "true_rel_res": r["true_rel_res"],
+                               check=False, inner_iters=kin)
+        gm[name] = {"iters": r["iters"], "inner_iters": r["inner_iters"],
+                    "converged": bool(r["converged"]), "true_rel_res": r["true_rel_res"],
                     "wall_ms": (time.perf_counter() - t0) * 1e3}
     flops = 12.0 * n ** 4 * E         # z transform 2 n^4 + n slice applies of 10 n^3
     achieved = flops / (apply["fp64"]["ms"] * 1e-3) / 1e9
@@ -471,6 +479,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="GMRES iterations the reference arm extrapolates to")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--inner", type=int, default=12,
+                    help="mixed precision: inner FP32 GMRES steps per outer step (0: one FP32 "
+                         "Kronecker apply per outer step)")
     ap.add_argument("--form", choices=["one-sided", "two-sided"], default="one-sided",
                     help="apply form: one-sided (shifted inverses, default) or the paper's "
                          "two-sided Schur / quasi-triangular Sylvester form")

@@ -98,6 +98,14 @@ typedef struct {
   int32_t pc;           /* tpp_pc */
   int32_t inner_prec;   /* tpp_prec of the Kronecker apply; TPP_FP32 needs TPP_FEAT_MIXED */
   int32_t flexible;     /* 1: flexible GMRES (stores Z = P^-1 V); forced to 1 when inner_prec != FP64 */
+  int32_t inner_iters;  /* 0: each preconditioner application is one Kronecker apply.  k > 0
+                           (mixed precision, needs TPP_FEAT_MIXED and TPP_PC_KRON): it is an
+                           inner FP32 GMRES solve S d = v of at most k steps (k <= max_restart),
+                           right-preconditioned by the FP32 Kronecker apply, with the FP32
+                           operator and FP32 basis vectors; the outer solve is flexible GMRES
+                           in FP64 (operator, Arnoldi, Givens, true residual). */
+  int32_t reserved;     /* must be 0 */
+  double inner_rtol;    /* inner solves stop early at this relative residual estimate (0: never) */
 } tpp_gmres_opts;
 
 typedef struct {
@@ -107,6 +115,8 @@ typedef struct {
   int32_t converged;    /* 1 when the true relative residual <= rtol */
   double true_rel_res;  /* ||b - A x|| / ||b|| of the returned x */
   double est_rel_res;   /* last Arnoldi (Givens) estimate */
+  int32_t inner_iters;  /* total inner FP32 steps (inner_iters > 0 in the options) */
+  int32_t reserved;
 } tpp_gmres_result;
 
 typedef struct {
@@ -198,6 +208,18 @@ tpp_status tpp_apply_block_jacobi(const tpp_ctx* ctx, const double* b, double* x
  * not alias.  Asynchronous.
  */
 tpp_status dg_apply_sumfact(const tpp_ctx* ctx, const double* x, double* y, void* stream);
+
+/*
+ * FP32 forms used by the inner solves of the mixed-precision mode (contexts
+ * created with TPP_FEAT_MIXED): the same operator on float vectors with float
+ * copies of the flux Jacobian coefficients (FP32 arithmetic throughout), and
+ * x = P^-1 b with the FP32 factors on float vectors (tpp_apply_inverse_f32
+ * needs tpp_build_factors first).  Vectors: device float32 [num_dofs], must not
+ * alias.  The paper has no FP32 variant; these follow Sec. 3.4 and Alg.
+ * 2d-apply / 3d-apply in single precision.  Asynchronous.
+ */
+tpp_status dg_apply_sumfact_f32(const tpp_ctx* ctx, const float* x, float* y, void* stream);
+tpp_status tpp_apply_inverse_f32(const tpp_ctx* ctx, const float* b, float* x, void* stream);
 
 /*
  * Solve S x = b by restarted right-preconditioned GMRES(m) (Sec. 5 opening;

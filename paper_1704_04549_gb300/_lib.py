@@ -26,13 +26,14 @@ class Problem(C.Structure):
 
 class GmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
-                ("pc", C.c_int32), ("inner_prec", C.c_int32), ("flexible", C.c_int32)]
+                ("pc", C.c_int32), ("inner_prec", C.c_int32), ("flexible", C.c_int32),
+                ("inner_iters", C.c_int32), ("reserved", C.c_int32), ("inner_rtol", C.c_double)]
 
 
 class GmresResult(C.Structure):
     _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("status", C.c_int32),
                 ("converged", C.c_int32), ("true_rel_res", C.c_double),
-                ("est_rel_res", C.c_double)]
+                ("est_rel_res", C.c_double), ("inner_iters", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BuildReport(C.Structure):
@@ -59,6 +60,8 @@ EXPORTS = {
     "tpp_apply_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_apply_sumfact": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_apply_sumfact_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_apply_sumfact_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),

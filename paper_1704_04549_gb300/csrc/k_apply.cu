@@ -94,12 +94,12 @@ __device__ __forceinline__ void small_sylvester(int ni, int nj, const T a[4], co
 // of its row with the contributions of the blocks solved at step s in their
 // columns (T2[i, k] Y[k, j]) and in its own row (Y[i, l] T1[j, l]).  Only
 // warp-level synchronisation is needed.
-template <typename T, int NM>
+template <typename T, int NM, typename VT>
 __global__ void __launch_bounds__(128)
 k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ SB,
              const T* __restrict__ Q1, const T* __restrict__ Q2, const T* __restrict__ T1,
              const T* __restrict__ T2, const uint32_t* __restrict__ masks,
-             const double* b, double* x, const int32_t* skip, int fdiv) {
+             const VT* b, VT* x, const int32_t* skip, int fdiv) {
   if (skip && *skip) return;
   constexpr int EPW = 32 / NM;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -312,7 +312,7 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
 #pragma unroll
     for (int k = 0; k < NM; ++k)
       if (k < n) sacc += row[k] * Wm[k + n * j];
-    if (rok) x[g + i + n * j] = (double)sacc;
+    if (rok) x[g + i + n * j] = (VT)sacc;
   }
 }
 
@@ -330,11 +330,11 @@ k_apply_2d_w(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ S
 // coalesced over the lanes), and updates the remaining columns of its own row
 // in registers.  Every FP64 instruction does useful work for all rows; there is
 // no per-step division and no cross-row dependency inside a column.
-template <typename T, int NM>
+template <typename T, int NM, typename VT>
 __global__ void __launch_bounds__(128)
 k_apply_2d_g(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ LBi,
              const T* __restrict__ Q1, const T* __restrict__ T1, const T* __restrict__ G,
-             const uint32_t* __restrict__ masks, const double* b, double* x,
+             const uint32_t* __restrict__ masks, const VT* b, VT* x,
              const int32_t* skip, int fdiv) {
   if (skip && *skip) return;
   constexpr int EPW = 32 / NM;
@@ -456,31 +456,31 @@ k_apply_2d_g(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ L
 #pragma unroll
     for (int k = 0; k < NM; ++k)
       if (k < n) sacc += row[k] * Fa[j + n * k];
-    if (rok) x[g + i + n * j] = (double)sacc;
+    if (rok) x[g + i + n * j] = (VT)sacc;
   }
 }
 
-template <typename T, int NM>
+template <typename T, int NM, typename VT>
 cudaError_t launch_g(int n, int64_t E, const T* SA, const T* LBi, const T* Q1, const T* T1,
-                     const T* G, const uint32_t* masks, const double* b, double* x,
+                     const T* G, const uint32_t* masks, const VT* b, VT* x,
                      const int32_t* skip, int fdiv, cudaStream_t s) {
   constexpr int EPW = 32 / NM;
   const int warps = 4;
   const int64_t per_block = (int64_t)warps * EPW;
   const int64_t blocks = (E + per_block - 1) / per_block;
   const size_t smem = (size_t)warps * EPW * 2 * NM * NM * sizeof(T);
-  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_g<T, NM>,
+  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_g<T, NM, VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_apply_2d_g<T, NM><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, LBi, Q1, T1, G, masks,
-                                                                  b, x, skip, fdiv);
+  k_apply_2d_g<T, NM, VT><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, LBi, Q1, T1, G,
+                                                                      masks, b, x, skip, fdiv);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T, int NM>
+template <typename T, int NM, typename VT>
 cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, const T* Q2,
-                     const T* T1, const T* T2, const uint32_t* masks, const double* b, double* x,
+                     const T* T1, const T* T2, const uint32_t* masks, const VT* b, VT* x,
                      const int32_t* skip, int fdiv, cudaStream_t s) {
   constexpr int EPW = 32 / NM;
   const int warps = (NM == 32 && sizeof(T) == 8) ? 2 : 4;
@@ -488,60 +488,69 @@ cudaError_t launch_w(int n, int64_t E, const T* SA, const T* SB, const T* Q1, co
   const int64_t blocks = (E + per_block - 1) / per_block;
   const size_t smem = (size_t)warps * EPW * 3 * NM * NM * sizeof(T) +
                       (size_t)warps * EPW * (3 * NM + 4) * sizeof(int);
-  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_w<T, NM>,
+  cudaError_t err = cudaFuncSetAttribute(k_apply_2d_w<T, NM, VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_apply_2d_w<T, NM><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, SB, Q1, Q2, T1, T2,
-                                                                  masks, b, x, skip, fdiv);
+  k_apply_2d_w<T, NM, VT><<<(unsigned)blocks, warps * 32, smem, s>>>(n, E, SA, SB, Q1, Q2, T1,
+                                                                      T2, masks, b, x, skip, fdiv);
   count_launch();
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename VT>
 cudaError_t launch_apply_one(const tpp_ctx* c, const T* SA, const T* LBi, const T* Q1,
-                             const T* T1, const T* G, const double* b, double* x,
+                             const T* T1, const T* G, const VT* b, VT* x,
                              const int32_t* skip, cudaStream_t s) {
   const uint32_t* masks = c->p<uint32_t>(c->L.masks);
   const int fdiv = (c->dim == 3) ? c->n : 1;
   const int64_t nb = c->E * fdiv;
-  if (c->n <= 8) return launch_g<T, 8>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
-  if (c->n <= 16) return launch_g<T, 16>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
-  return launch_g<T, 32>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+  if (c->n <= 8)
+    return launch_g<T, 8, VT>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+  if (c->n <= 16)
+    return launch_g<T, 16, VT>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
+  return launch_g<T, 32, VT>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
 }
 
-template <typename T>
+template <typename T, typename VT>
 cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* Q1, const T* Q2,
-                           const T* T1, const T* T2, const double* b, double* x,
+                           const T* T1, const T* T2, const VT* b, VT* x,
                            const int32_t* skip, cudaStream_t s) {
   const uint32_t* masks = c->p<uint32_t>(c->L.masks);
   const int fdiv = (c->dim == 3) ? c->n : 1;
   const int64_t nb = c->E * fdiv;                  // 2D blocks: elements, or z slices in 3D
   if (c->n <= 8)
-    return launch_w<T, 8>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
+    return launch_w<T, 8, VT>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
   if (c->n <= 16)
-    return launch_w<T, 16>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
-  return launch_w<T, 32>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
+    return launch_w<T, 16, VT>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
+  return launch_w<T, 32, VT>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
 }
 
-cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
-                            const int32_t* skip, cudaStream_t s) {
+template <typename VT>
+cudaError_t launch_apply_2d_t(const tpp_ctx* c, const VT* b, VT* x, int prec,
+                              const int32_t* skip, cudaStream_t s) {
   const bool two = two_sided(c);
   if (prec == TPP_FP64) {
     if (!two)
-      return launch_apply_one<double>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
-                                      c->p<double>(c->L.fQ1), c->p<double>(c->L.fT1),
-                                      c->p<double>(c->L.fG), b, x, skip, s);
-    return launch_apply_t<double>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
-                                  c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
-                                  c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), b, x, skip, s);
+      return launch_apply_one<double, VT>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
+                                          c->p<double>(c->L.fQ1), c->p<double>(c->L.fT1),
+                                          c->p<double>(c->L.fG), b, x, skip, s);
+    return launch_apply_t<double, VT>(c, c->p<double>(c->L.fSA), c->p<double>(c->L.fSB),
+                                      c->p<double>(c->L.fQ1), c->p<double>(c->L.fQ2),
+                                      c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), b, x, skip,
+                                      s);
   }
   const float* f = c->p<float>(c->L.f32);
   const F32Layout F = f32_layout(c->n, c->E, c->dim, two);
   if (!two)
-    return launch_apply_one<float>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.T1, f + F.G, b, x,
-                                   skip, s);
-  return launch_apply_t<float>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.Q2, f + F.T1, f + F.T2, b,
-                               x, skip, s);
+    return launch_apply_one<float, VT>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.T1, f + F.G, b, x,
+                                       skip, s);
+  return launch_apply_t<float, VT>(c, f + F.SA, f + F.SB, f + F.Q1, f + F.Q2, f + F.T1, f + F.T2,
+                                   b, x, skip, s);
+}
+
+cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int prec,
+                            const int32_t* skip, cudaStream_t s) {
+  return launch_apply_2d_t<double>(c, b, x, prec, skip, s);
 }
 
 // float copies of the apply factors, rounded to nearest (up to 8 segments)
@@ -594,10 +603,10 @@ cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
 // x~ = (A1^-1 (x) I) b, one thread per z line (i, j) of an element with the
 // line in registers; then the 2D apply of D1^-1 = (B1 (x) C1 + B2 (x) C2)^-1
 // runs in place on each z slice (n slices per element share its factors).
-template <typename T, int NZ>
+template <typename T, int NZ, typename VT>
 __global__ void __launch_bounds__(128)
-k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const double* __restrict__ b,
-          double* __restrict__ x, const int32_t* skip) {
+k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const VT* __restrict__ b,
+          VT* __restrict__ x, const int32_t* skip) {
   if (skip && *skip) return;
   __shared__ T az[4][NZ * NZ];
   const int nn = n * n, n3 = nn * n;
@@ -607,8 +616,8 @@ k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const double* __restrict_
   const int lane = threadIdx.x & 31;
   for (int q = lane; q < nn; q += 32) az[sub][q] = Azi[e * nn + q];
   __syncwarp();
-  const double* be = b + e * n3;
-  double* xe = x + e * n3;
+  const VT* be = b + e * n3;
+  VT* xe = x + e * n3;
   for (int q = lane; q < nn; q += 32) {
     T line[NZ];
 #pragma unroll
@@ -620,29 +629,42 @@ k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const double* __restrict_
 #pragma unroll
         for (int k2 = 0; k2 < NZ; ++k2)
           if (k2 < n) sv += az[sub][k + n * k2] * line[k2];
-        xe[q + (int64_t)nn * k] = (double)sv;
+        xe[q + (int64_t)nn * k] = (VT)sv;
       }
     }
   }
 }
 
-cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,
-                            const int32_t* skip, cudaStream_t s) {
+template <typename VT>
+cudaError_t launch_apply_3d_t(const tpp_ctx* c, const VT* b, VT* x, int prec,
+                              const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
   const unsigned blocks = (unsigned)((c->E + 3) / 4);
   if (prec == TPP_FP64) {
     const double* azi = c->p<double>(c->L.fAzi);
-    if (n <= 8) k_apply_z<double, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
-    else k_apply_z<double, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    if (n <= 8) k_apply_z<double, 8, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    else k_apply_z<double, 16, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
   } else {
     const float* azi = c->p<float>(c->L.f32) + f32_layout(n, c->E, 3, two_sided(c)).Azi;
-    if (n <= 8) k_apply_z<float, 8><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
-    else k_apply_z<float, 16><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    if (n <= 8) k_apply_z<float, 8, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    else k_apply_z<float, 16, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
   }
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_apply_2d(c, x, x, prec, skip, s);
+  return launch_apply_2d_t<VT>(c, x, x, prec, skip, s);
+}
+
+cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,
+                            const int32_t* skip, cudaStream_t s) {
+  return launch_apply_3d_t<double>(c, b, x, prec, skip, s);
+}
+
+// FP32 factors, float vectors (the inner solves of the mixed-precision mode)
+cudaError_t launch_apply_f32(const tpp_ctx* c, const float* b, float* x, const int32_t* skip,
+                             cudaStream_t s) {
+  if (c->dim == 2) return launch_apply_2d_t<float>(c, b, x, TPP_FP32, skip, s);
+  return launch_apply_3d_t<float>(c, b, x, TPP_FP32, skip, s);
 }
 
 }  // namespace tpp

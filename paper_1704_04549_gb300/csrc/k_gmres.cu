@@ -12,38 +12,49 @@ namespace tpp {
 constexpr int kRedThreads = 256;
 constexpr int kMaxBasis = 64;       // restart + 1 vectors at most
 
-// partials[blk * stride + i] = sum over this block's slice of V_i . w, i < nvec
-__device__ void dot_block(const double* __restrict__ V, int64_t N, int nvec,
-                          const double* __restrict__ w, double* __restrict__ partials,
-                          int stride, double* red) {
-  for (int g0 = 0; g0 < nvec; g0 += 16) {
-    const int gcount = (nvec - g0) < 16 ? (nvec - g0) : 16;
-    double acc[16];
+constexpr int kRegBasis = 32;      // basis sizes kept in register tiles
+constexpr int kWarps = kRedThreads / 32;
+
+// Per-thread accumulators acc[i < cnt] -> partials[blk * stride + g0 + i]
+// (warp sums, then the block's warps in order: deterministic).
+template <typename AT>
+__device__ void store_block_partials(const AT (&acc)[kRegBasis], int cnt, int g0,
+                                     double* partials, int stride, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+  for (int i = 0; i < kRegBasis; ++i) {
+    if (i < cnt) {
+      const double v = warp_sum((double)acc[i]);
+      if (lane == 0) red[i * kWarps + wid] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double t = 0.0;
+    for (int k = 0; k < kWarps; ++k) t += red[threadIdx.x * kWarps + k];
+    partials[blockIdx.x * stride + g0 + threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// partials of V_i . w, i < nvec (groups of kRegBasis vectors)
+template <typename VT>
+__device__ void dot_block(const VT* __restrict__ V, int64_t N, int nvec,
+                          const VT* __restrict__ w, double* __restrict__ partials, int stride,
+                          double* red) {
+  for (int g0 = 0; g0 < nvec; g0 += kRegBasis) {
+    const int cnt = (nvec - g0) < kRegBasis ? (nvec - g0) : kRegBasis;
+    VT acc[kRegBasis];
+#pragma unroll
+    for (int i = 0; i < kRegBasis; ++i) acc[i] = (VT)0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
-      const double wv = w[t];
+      const VT wv = w[t];
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (i < gcount) acc[i] += V[(size_t)(g0 + i) * N + t] * wv;
+      for (int i = 0; i < kRegBasis; ++i)
+        if (i < cnt) acc[i] += V[(size_t)(g0 + i) * N + t] * wv;
     }
-    // per-warp partial sums, then one warp per value folds the 8 warp sums
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (i < gcount) {
-        const double v = warp_sum(acc[i]);
-        if (lane == 0) red[i * 8 + wid] = v;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < gcount) {
-      double t = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x * 8 + k];
-      partials[blockIdx.x * stride + g0 + threadIdx.x] = t;
-    }
-    __syncthreads();
+    store_block_partials(acc, cnt, g0, partials, stride, red);
   }
 }
 
@@ -111,11 +122,12 @@ __device__ void finish_column(const ArnoldiArgs& a, double nrm2) {
 }
 
 // pass 1 of CGS2: h1 = V^T w
+template <typename VT>
 __global__ void __launch_bounds__(kRedThreads)
-k_dots(const double* V, int64_t N, int nvec, const double* w, double* partials, int stride,
+k_dots(const VT* V, int64_t N, int nvec, const VT* w, double* partials, int stride,
        const int32_t* skip, double* h_out, unsigned int* ticket) {
   if (skip && *skip) return;
-  __shared__ double red[16 * (kRedThreads / 32)];
+  __shared__ double red[kRegBasis * kWarps];
   dot_block(V, N, nvec, w, partials, stride, red);
   if (last_block(ticket)) {
     final_reduce(partials, gridDim.x, stride, nvec, h_out);
@@ -123,35 +135,66 @@ k_dots(const double* V, int64_t N, int nvec, const double* w, double* partials, 
   }
 }
 
-// w -= V h_in; mode 0: h_out = V^T w (pass 2 of CGS2);
+// w -= V h_in; mode 0: h_out = V^T w (pass 2 of CGS2, fused: the basis entries
+// of a point stay in registers for both products when nvec <= kRegBasis);
 // mode 1: ||w||^2 and the Givens update of column a.j
+template <typename VT>
 __global__ void __launch_bounds__(kRedThreads)
-k_update(const double* __restrict__ V, int64_t N, int nvec, const double* __restrict__ h_in,
-         double* __restrict__ w, double* partials, int stride, int mode, const int32_t* skip,
+k_update(const VT* __restrict__ V, int64_t N, int nvec, const double* __restrict__ h_in,
+         VT* __restrict__ w, double* partials, int stride, int mode, const int32_t* skip,
          double* h_out, unsigned int* ticket, ArnoldiArgs aa) {
   if (skip && *skip) return;
-  __shared__ double hs[kMaxBasis];
-  __shared__ double red[16 * (kRedThreads / 32)];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = h_in[i];
+  __shared__ VT hs[kMaxBasis];
+  __shared__ double red[kRegBasis * kWarps];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = (VT)h_in[i];
   __syncthreads();
-  double nrm = 0.0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    double v = w[t];
-    for (int i = 0; i < nvec; ++i) v -= hs[i] * V[(size_t)i * N + t];
-    w[t] = v;
-    nrm += v * v;
+  VT nrm = (VT)0;
+  if (nvec <= kRegBasis) {
+    VT acc[kRegBasis];
+#pragma unroll
+    for (int i = 0; i < kRegBasis; ++i) acc[i] = (VT)0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      VT vv[kRegBasis];
+      VT wv = w[t];
+#pragma unroll
+      for (int i = 0; i < kRegBasis; ++i) {
+        if (i < nvec) {
+          vv[i] = V[(size_t)i * N + t];
+          wv -= hs[i] * vv[i];
+        }
+      }
+      w[t] = wv;
+      if (mode == 0) {
+#pragma unroll
+        for (int i = 0; i < kRegBasis; ++i)
+          if (i < nvec) acc[i] += vv[i] * wv;
+      } else {
+        nrm += wv * wv;
+      }
+    }
+    if (mode == 0) store_block_partials(acc, nvec, 0, partials, stride, red);
+  } else {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      VT v = w[t];
+      for (int i = 0; i < nvec; ++i) v -= hs[i] * V[(size_t)i * N + t];
+      w[t] = v;
+      nrm += v * v;
+    }
+    if (mode == 0) {
+      __syncthreads();
+      dot_block(V, N, nvec, w, partials, stride, red);
+    }
   }
   if (mode == 0) {
-    __syncthreads();
-    dot_block(V, N, nvec, w, partials, stride, red);
     if (last_block(ticket)) {
       final_reduce(partials, gridDim.x, stride, nvec, h_out);
       if (threadIdx.x == 0) *ticket = 0;
     }
   } else {
-    const double s = block_sum(nrm, red);
-    if (threadIdx.x == 0) partials[blockIdx.x * stride] = s;
+    const double sblk = block_sum((double)nrm, red);
+    if (threadIdx.x == 0) partials[blockIdx.x * stride] = sblk;
     if (last_block(ticket)) {
       __shared__ double tot;
       final_reduce(partials, gridDim.x, stride, 1, &tot);
@@ -177,28 +220,41 @@ __global__ void k_lsq(const GmresState* st, const double* H, const double* g, do
 }
 
 // out = sum_{i < k} y_i B_i (+ out if accumulate)
-__global__ void k_combine(const double* __restrict__ B, int64_t N, const GmresState* st,
-                          const double* __restrict__ y, double* __restrict__ out, int accumulate) {
-  __shared__ double ys[kMaxBasis];
+template <typename VI, typename VO>
+__global__ void k_combine(const VI* __restrict__ B, int64_t N, const GmresState* st,
+                          const double* __restrict__ y, VO* __restrict__ out, int accumulate,
+                          const int32_t* skip) {
+  if (skip && *skip) return;
+  __shared__ VI ys[kMaxBasis];
   const int k = st->k;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = (VI)y[i];
   __syncthreads();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x) {
-    double s = accumulate ? out[t] : 0.0;
+    VI s = (VI)0;
     for (int i = 0; i < k; ++i) s += ys[i] * B[(size_t)i * N + t];
-    out[t] = s;
+    out[t] = accumulate ? (VO)(out[t] + (VO)s) : (VO)s;
   }
 }
 
-// y = a * x (+ b * y), scalars read from device memory when pointers given
-__global__ void k_scale(double* __restrict__ out, const double* __restrict__ in, int64_t N,
+// out = sc * in, sc read from device memory when sptr is given
+template <typename VT>
+__global__ void k_scale(VT* __restrict__ out, const VT* __restrict__ in, int64_t N,
                         const double* sptr, double sval, const int32_t* skip) {
   if (skip && *skip) return;
-  const double sc = sptr ? *sptr : sval;
+  const VT sc = (VT)(sptr ? *sptr : sval);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x)
     out[t] = sc * in[t];
+}
+
+// float copy of a vector (rounded to nearest)
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t N,
+                           const int32_t* skip) {
+  if (skip && *skip) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = __double2float_rn(in[t]);
 }
 
 __global__ void k_sub(double* __restrict__ out, const double* __restrict__ a,
@@ -220,20 +276,20 @@ k_norm_partials(const double* __restrict__ x, int64_t N, double* partials, int s
 }
 
 __global__ void k_norm_finish(const double* partials, int nblk, int stride, double* out) {
-  if (threadIdx.x != 0) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partials[b * stride];
-  *out = sqrt(s);
+  for (int b = threadIdx.x; b < nblk; b += 32) s += partials[b * stride];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 __global__ void k_cycle_init(GmresState* st, double* g, double beta, int m, double bnorm,
-                             double rtol) {
+                             double rtol, const int32_t* done_src) {
   if (threadIdx.x != 0) return;
   st->bnorm = bnorm;
   st->rtol = rtol;
   st->est = beta / bnorm;
   st->j = 0;
-  st->done = 0;
+  st->done = done_src ? *done_src : 0;
   st->k = 0;
   st->breakdown = 0;
   st->beta = beta;
@@ -243,25 +299,44 @@ __global__ void k_cycle_init(GmresState* st, double* g, double beta, int m, doub
 }
 
 // ---------------------------------------------------------------------------
-// launch helpers used by the host solver
-cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
+// launch helpers used by the host solver (VT = double: the FP64 solver, float:
+// the inner solves of the mixed-precision mode)
+constexpr int kVecBlocks = 152 * 2;     // grid of the register-tiled basis kernels
+
+template <typename VT>
+cudaError_t gmres_dots(const VT* V, int64_t N, int nvec, const VT* w, double* partials,
                        int stride, int nblk, const int32_t* skip, double* h_out,
                        unsigned int* ticket, cudaStream_t s) {
-  k_dots<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
+  const int g = nblk < kVecBlocks ? nblk : kVecBlocks;
+  k_dots<VT><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
   count_launch();
   return cudaGetLastError();
 }
-cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
+template <typename VT>
+cudaError_t gmres_update(const VT* V, int64_t N, int nvec, const double* h, VT* w,
                          double* partials, int stride, int mode, int nblk, const int32_t* skip,
                          double* h_out, unsigned int* ticket, GmresState* st, double* H,
                          double* cs, double* sn, double* g, double* h1, double* h2,
                          double* inv_beta, int j, cudaStream_t s) {
   ArnoldiArgs aa{st, H, cs, sn, g, h1, h2, inv_beta, j};
-  k_update<<<nblk, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip, h_out,
-                                        ticket, aa);
+  const int gr = nblk < kVecBlocks ? nblk : kVecBlocks;
+  k_update<VT><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip, h_out,
+                                          ticket, aa);
   count_launch();
   return cudaGetLastError();
 }
+template cudaError_t gmres_dots<double>(const double*, int64_t, int, const double*, double*, int,
+                                        int, const int32_t*, double*, unsigned int*, cudaStream_t);
+template cudaError_t gmres_dots<float>(const float*, int64_t, int, const float*, double*, int,
+                                       int, const int32_t*, double*, unsigned int*, cudaStream_t);
+template cudaError_t gmres_update<double>(const double*, int64_t, int, const double*, double*,
+                                          double*, int, int, int, const int32_t*, double*,
+                                          unsigned int*, GmresState*, double*, double*, double*,
+                                          double*, double*, double*, double*, int, cudaStream_t);
+template cudaError_t gmres_update<float>(const float*, int64_t, int, const double*, float*,
+                                         double*, int, int, int, const int32_t*, double*,
+                                         unsigned int*, GmresState*, double*, double*, double*,
+                                         double*, double*, double*, double*, int, cudaStream_t);
 cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, double* y,
                       cudaStream_t s) {
   k_lsq<<<1, 32, 0, s>>>(st, H, g, y);
@@ -270,13 +345,31 @@ cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, do
 }
 cudaError_t gmres_combine(const double* B, int64_t N, const GmresState* st, const double* y,
                           double* out, int accumulate, cudaStream_t s) {
-  k_combine<<<152 * 4, 256, 0, s>>>(B, N, st, y, out, accumulate);
+  k_combine<double, double><<<152 * 4, 256, 0, s>>>(B, N, st, y, out, accumulate, nullptr);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t gmres_combine_f32(const float* B, int64_t N, const GmresState* st, const double* y,
+                              double* out, const int32_t* skip, cudaStream_t s) {
+  k_combine<float, double><<<152 * 4, 256, 0, s>>>(B, N, st, y, out, 0, skip);
   count_launch();
   return cudaGetLastError();
 }
 cudaError_t vec_scale(double* out, const double* in, int64_t N, const double* sptr, double sval,
                       const int32_t* skip, cudaStream_t s) {
-  k_scale<<<152 * 4, 256, 0, s>>>(out, in, N, sptr, sval, skip);
+  k_scale<double><<<152 * 4, 256, 0, s>>>(out, in, N, sptr, sval, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_scale_f32(float* out, const float* in, int64_t N, const double* sptr,
+                          double sval, const int32_t* skip, cudaStream_t s) {
+  k_scale<float><<<152 * 4, 256, 0, s>>>(out, in, N, sptr, sval, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t vec_to_float(const double* in, float* out, int64_t N, const int32_t* skip,
+                         cudaStream_t s) {
+  k_to_float<<<152 * 4, 256, 0, s>>>(in, out, N, skip);
   count_launch();
   return cudaGetLastError();
 }
@@ -294,8 +387,8 @@ cudaError_t vec_norm(const double* x, int64_t N, double* partials, int stride, i
   return cudaGetLastError();
 }
 cudaError_t gmres_cycle_init(GmresState* st, double* g, double beta, int m, double bnorm,
-                             double rtol, cudaStream_t s) {
-  k_cycle_init<<<1, 32, 0, s>>>(st, g, beta, m, bnorm, rtol);
+                             double rtol, const int32_t* done_src, cudaStream_t s) {
+  k_cycle_init<<<1, 32, 0, s>>>(st, g, beta, m, bnorm, rtol, done_src);
   count_launch();
   return cudaGetLastError();
 }
@@ -309,6 +402,17 @@ __global__ void k_axpy(double* __restrict__ out, const double* __restrict__ in, 
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
        t += (int64_t)gridDim.x * blockDim.x)
     out[t] += a * in[t];
+}
+
+__global__ void k_accum_inner(GmresState* outer, const GmresState* inner, const int32_t* skip) {
+  if (threadIdx.x == 0 && !(skip && *skip)) outer->inner_total += inner->k;
+}
+
+cudaError_t accumulate_inner(GmresState* outer, const GmresState* inner, const int32_t* skip,
+                             cudaStream_t s) {
+  k_accum_inner<<<1, 32, 0, s>>>(outer, inner, skip);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t vec_axpy(double* out, const double* in, double a, int64_t N, cudaStream_t s) {

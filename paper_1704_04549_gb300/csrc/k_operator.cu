@@ -278,33 +278,33 @@ cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s) {
 // Face traces u(face node) = sum_i l_{0/1}[i] u_i along each direction.
 // tr[e][f][t]: f = 0 (-x, l0), 1 (+x, l1), 2 (-y), 3 (+y) [, 4 (-z), 5 (+z)];
 // t the face node (first tangential fastest).
-template <int DIM>
-__global__ void k_traces(const Tables* T, int n, int64_t E, const double* __restrict__ x,
-                         double* __restrict__ tr, const int32_t* skip) {
+template <int DIM, typename VT>
+__global__ void k_traces(const Tables* T, int n, int64_t E, const VT* __restrict__ x,
+                         VT* __restrict__ tr, const int32_t* skip) {
   if (skip && *skip) return;
   const int nfl = (DIM == 2) ? n : n * n;
   const int nloc = nfl * n;
   const int64_t tot = E * nfl;
-  __shared__ double l0[TPP_MAX_N], l1[TPP_MAX_N];
-  if (threadIdx.x < n) { l0[threadIdx.x] = T->l0[threadIdx.x]; l1[threadIdx.x] = T->l1[threadIdx.x]; }
+  __shared__ VT l0[TPP_MAX_N], l1[TPP_MAX_N];
+  if (threadIdx.x < n) { l0[threadIdx.x] = (VT)T->l0[threadIdx.x]; l1[threadIdx.x] = (VT)T->l1[threadIdx.x]; }
   __syncthreads();
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = g / nfl;
     const int q = (int)(g % nfl);
     const int t0 = q % n, t1 = q / n;
-    const double* xe = x + e * nloc;
-    double* te = tr + e * (2 * DIM) * nfl;
-    double a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
+    const VT* xe = x + e * nloc;
+    VT* te = tr + e * (2 * DIM) * nfl;
+    VT a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0;
     for (int s = 0; s < n; ++s) {
       // x-faces: tangential (y = t0, z = t1), sum over i = s
-      const double vx = (DIM == 2) ? xe[s + n * t0] : xe[s + n * t0 + n * n * t1];
+      const VT vx = (DIM == 2) ? xe[s + n * t0] : xe[s + n * t0 + n * n * t1];
       a0 += l0[s] * vx; a1 += l1[s] * vx;
       // y-faces: tangential (x = t0, z = t1), sum over j = s
-      const double vy = (DIM == 2) ? xe[t0 + n * s] : xe[t0 + n * s + n * n * t1];
+      const VT vy = (DIM == 2) ? xe[t0 + n * s] : xe[t0 + n * s + n * n * t1];
       b0 += l0[s] * vy; b1 += l1[s] * vy;
       if (DIM == 3) {   // z-faces: tangential (x = t0, y = t1), sum over k = s
-        const double vz = xe[t0 + n * t1 + n * n * s];
+        const VT vz = xe[t0 + n * t1 + n * n * s];
         c0 += l0[s] * vz; c1 += l1[s] * vz;
       }
     }
@@ -317,9 +317,19 @@ __global__ void k_traces(const Tables* T, int n, int64_t E, const double* __rest
 cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
                           const int32_t* skip) {
   if (c->dim == 2)
-    k_traces<2><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<2, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
   else
-    k_traces<3><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<3, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
+                              const int32_t* skip) {
+  if (c->dim == 2)
+    k_traces<2, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+  else
+    k_traces<3, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
   count_launch();
   return cudaGetLastError();
 }
@@ -330,19 +340,21 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
 //          + l1_i F^R_j - l0_i F^L_j + l1_j F^T_i - l0_j F^B_i,
 // F^R_j = max(sR_j,0) u^-_R + min(sR_j,0) u^+_R (upwind flux through the +x
 // face, pre-scaled by dt h w_j), etc.
+template <typename VT>
 __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
-                              const double* __restrict__ cx, const double* __restrict__ cy,
-                              const double* __restrict__ sx, const double* __restrict__ sy,
-                              const double* __restrict__ x, const double* __restrict__ tr,
-                              double* __restrict__ y, const int32_t* skip) {
+                              const VT* __restrict__ cx, const VT* __restrict__ cy,
+                              const VT* __restrict__ sx, const VT* __restrict__ sy,
+                              const VT* __restrict__ x, const VT* __restrict__ tr,
+                              VT* __restrict__ y, const int32_t* skip) {
   if (skip && *skip) return;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smo[];
+  VT* sm = reinterpret_cast<VT*>(smo);
   const int nn = n * n;
-  double* Ds = sm;              // n*n, D[a*n + j]
-  double* px = Ds + nn;         // cx * x
-  double* py = px + nn;         // cy * x
-  double* fl = py + nn;         // 4n face fluxes: R, L, T, B
-  double* wl = fl + 4 * n;      // w, l0, l1
+  VT* Ds = sm;                  // n*n, D[a*n + j]
+  VT* px = Ds + nn;             // cx * x
+  VT* py = px + nn;             // cy * x
+  VT* fl = py + nn;             // 4n face fluxes: R, L, T, B
+  VT* wl = fl + 4 * n;          // w, l0, l1
   const int64_t e = blockIdx.x;
   const int ex = (int)(e % nx), ey = (int)(e / nx);
   const int64_t eR = ey * (int64_t)nx + (ex + 1) % nx, eL = ey * (int64_t)nx + (ex + nx - 1) % nx;
@@ -350,39 +362,40 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
   const int tid = threadIdx.x;
   const int64_t base = e * nn;
   for (int q = tid; q < nn; q += blockDim.x) {
-    Ds[q] = T->D[q];
-    const double xv = x[base + q];
+    Ds[q] = (VT)T->D[q];
+    const VT xv = x[base + q];
     px[q] = cx[base + q] * xv;
     py[q] = cy[base + q] * xv;
   }
   if (tid < n) {
-    wl[tid] = T->w[tid];
-    wl[n + tid] = T->l0[tid];
-    wl[2 * n + tid] = T->l1[tid];
-    const double* te = tr + e * 4 * n;
+    wl[tid] = (VT)T->w[tid];
+    wl[n + tid] = (VT)T->l0[tid];
+    wl[2 * n + tid] = (VT)T->l1[tid];
+    const VT* te = tr + e * 4 * n;
     const int t = tid;
+    const VT zero = (VT)0;
     {   // +x face: outward normal +x, flux a_x evaluated on the face owned by eR
-      const double s = sx[eR * n + t];
-      fl[t] = fmax(s, 0.0) * te[1 * n + t] + fmin(s, 0.0) * tr[eR * 4 * n + 0 * n + t];
+      const VT s = sx[eR * n + t];
+      fl[t] = max(s, zero) * te[1 * n + t] + min(s, zero) * tr[eR * 4 * n + 0 * n + t];
     }
     {   // -x face: flux through it in the +x direction, from the left element
-      const double s = sx[e * n + t];
-      fl[n + t] = fmax(s, 0.0) * tr[eL * 4 * n + 1 * n + t] + fmin(s, 0.0) * te[0 * n + t];
+      const VT s = sx[e * n + t];
+      fl[n + t] = max(s, zero) * tr[eL * 4 * n + 1 * n + t] + min(s, zero) * te[0 * n + t];
     }
     {   // +y
-      const double s = sy[eT * n + t];
-      fl[2 * n + t] = fmax(s, 0.0) * te[3 * n + t] + fmin(s, 0.0) * tr[eT * 4 * n + 2 * n + t];
+      const VT s = sy[eT * n + t];
+      fl[2 * n + t] = max(s, zero) * te[3 * n + t] + min(s, zero) * tr[eT * 4 * n + 2 * n + t];
     }
     {   // -y
-      const double s = sy[e * n + t];
-      fl[3 * n + t] = fmax(s, 0.0) * tr[eB * 4 * n + 3 * n + t] + fmin(s, 0.0) * te[2 * n + t];
+      const VT s = sy[e * n + t];
+      fl[3 * n + t] = max(s, zero) * tr[eB * 4 * n + 3 * n + t] + min(s, zero) * te[2 * n + t];
     }
   }
   __syncthreads();
-  const double h2 = h * h;
+  const VT h2 = (VT)(h * h);
   for (int q = tid; q < nn; q += blockDim.x) {
     const int i = q % n, j = q / n;
-    double acc = h2 * wl[i] * wl[j] * x[base + q];
+    VT acc = h2 * wl[i] * wl[j] * x[base + q];
     for (int k = 0; k < n; ++k) acc += Ds[k * n + i] * px[k + n * j];
     for (int l = 0; l < n; ++l) acc += Ds[l * n + j] * py[i + n * l];
     acc += wl[2 * n + i] * fl[j] - wl[n + i] * fl[n + j];
@@ -395,21 +408,23 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
 //   y_ijk = h^3 w_i w_j w_k x + sum_a D_ai cx_ajk x_ajk + sum_b D_bj cy_ibk x_ibk
 //           + sum_c D_ck cz_ijc x_ijc + l1_i F^+x_jk - l0_i F^-x_jk + (same for y, z),
 // face fluxes pre-scaled by dt h^2 and the two tangential weights.
+template <typename VT>
 __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, double h,
-                              const double* __restrict__ cx, const double* __restrict__ cy,
-                              const double* __restrict__ cz, const double* __restrict__ sx,
-                              const double* __restrict__ sy, const double* __restrict__ sz,
-                              const double* __restrict__ x, const double* __restrict__ tr,
-                              double* __restrict__ y, const int32_t* skip) {
+                              const VT* __restrict__ cx, const VT* __restrict__ cy,
+                              const VT* __restrict__ cz, const VT* __restrict__ sx,
+                              const VT* __restrict__ sy, const VT* __restrict__ sz,
+                              const VT* __restrict__ x, const VT* __restrict__ tr,
+                              VT* __restrict__ y, const int32_t* skip) {
   if (skip && *skip) return;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smo[];
+  VT* sm = reinterpret_cast<VT*>(smo);
   const int nn = n * n, n3 = nn * n;
-  double* Ds = sm;              // n*n
-  double* px = Ds + nn;         // n^3 each
-  double* py = px + n3;
-  double* pz = py + n3;
-  double* fl = pz + n3;         // 6 n^2 fluxes: +x, -x, +y, -y, +z, -z
-  double* wl = fl + 6 * nn;     // w, l0, l1
+  VT* Ds = sm;                  // n*n
+  VT* px = Ds + nn;             // n^3 each
+  VT* py = px + n3;
+  VT* pz = py + n3;
+  VT* fl = pz + n3;             // 6 n^2 fluxes: +x, -x, +y, -y, +z, -z
+  VT* wl = fl + 6 * nn;         // w, l0, l1
   const int64_t e = blockIdx.x;
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
   auto eid = [&](int a, int b, int c) -> int64_t {
@@ -420,39 +435,40 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, do
   const int64_t eZp = eid(ex, ey, ez + 1), eZm = eid(ex, ey, ez - 1);
   const int tid = threadIdx.x;
   const int64_t base = e * n3;
-  for (int q = tid; q < nn; q += blockDim.x) Ds[q] = T->D[q];
+  for (int q = tid; q < nn; q += blockDim.x) Ds[q] = (VT)T->D[q];
   for (int q = tid; q < n3; q += blockDim.x) {
-    const double xv = x[base + q];
+    const VT xv = x[base + q];
     px[q] = cx[base + q] * xv;
     py[q] = cy[base + q] * xv;
     pz[q] = cz[base + q] * xv;
   }
   if (tid < n) {
-    wl[tid] = T->w[tid];
-    wl[n + tid] = T->l0[tid];
-    wl[2 * n + tid] = T->l1[tid];
+    wl[tid] = (VT)T->w[tid];
+    wl[n + tid] = (VT)T->l0[tid];
+    wl[2 * n + tid] = (VT)T->l1[tid];
   }
-  const double* te = tr + e * 6 * nn;
+  const VT* te = tr + e * 6 * nn;
+  const VT zero = (VT)0;
   for (int q = tid; q < nn; q += blockDim.x) {
-    double s;
+    VT s;
     s = sx[eXp * nn + q];
-    fl[0 * nn + q] = fmax(s, 0.0) * te[1 * nn + q] + fmin(s, 0.0) * tr[eXp * 6 * nn + 0 * nn + q];
+    fl[0 * nn + q] = max(s, zero) * te[1 * nn + q] + min(s, zero) * tr[eXp * 6 * nn + 0 * nn + q];
     s = sx[e * nn + q];
-    fl[1 * nn + q] = fmax(s, 0.0) * tr[eXm * 6 * nn + 1 * nn + q] + fmin(s, 0.0) * te[0 * nn + q];
+    fl[1 * nn + q] = max(s, zero) * tr[eXm * 6 * nn + 1 * nn + q] + min(s, zero) * te[0 * nn + q];
     s = sy[eYp * nn + q];
-    fl[2 * nn + q] = fmax(s, 0.0) * te[3 * nn + q] + fmin(s, 0.0) * tr[eYp * 6 * nn + 2 * nn + q];
+    fl[2 * nn + q] = max(s, zero) * te[3 * nn + q] + min(s, zero) * tr[eYp * 6 * nn + 2 * nn + q];
     s = sy[e * nn + q];
-    fl[3 * nn + q] = fmax(s, 0.0) * tr[eYm * 6 * nn + 3 * nn + q] + fmin(s, 0.0) * te[2 * nn + q];
+    fl[3 * nn + q] = max(s, zero) * tr[eYm * 6 * nn + 3 * nn + q] + min(s, zero) * te[2 * nn + q];
     s = sz[eZp * nn + q];
-    fl[4 * nn + q] = fmax(s, 0.0) * te[5 * nn + q] + fmin(s, 0.0) * tr[eZp * 6 * nn + 4 * nn + q];
+    fl[4 * nn + q] = max(s, zero) * te[5 * nn + q] + min(s, zero) * tr[eZp * 6 * nn + 4 * nn + q];
     s = sz[e * nn + q];
-    fl[5 * nn + q] = fmax(s, 0.0) * tr[eZm * 6 * nn + 5 * nn + q] + fmin(s, 0.0) * te[4 * nn + q];
+    fl[5 * nn + q] = max(s, zero) * tr[eZm * 6 * nn + 5 * nn + q] + min(s, zero) * te[4 * nn + q];
   }
   __syncthreads();
-  const double h3 = h * h * h;
+  const VT h3 = (VT)(h * h * h);
   for (int q = tid; q < n3; q += blockDim.x) {
     const int i = q % n, j = (q / n) % n, k = q / nn;
-    double acc = h3 * wl[i] * wl[j] * wl[k] * x[base + q];
+    VT acc = h3 * wl[i] * wl[j] * wl[k] * x[base + q];
     for (int a = 0; a < n; ++a) acc += Ds[a * n + i] * px[a + n * j + nn * k];
     for (int b = 0; b < n; ++b) acc += Ds[b * n + j] * py[i + n * b + nn * k];
     for (int c = 0; c < n; ++c) acc += Ds[c * n + k] * pz[i + n * j + nn * c];
@@ -464,29 +480,86 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, do
   }
 }
 
-cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
-                            const int32_t* skip, cudaStream_t s) {
+template <typename VT>
+cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* cz,
+                              const VT* sx, const VT* sy, const VT* sz, const VT* x,
+                              const VT* tr, VT* y, const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
   if (c->dim == 2) {
     const int nn = n * n;
     const int threads = ((nn + 31) / 32) * 32;
-    const size_t smem = (3 * nn + 7 * n) * sizeof(double);
-    k_dg_apply_2d<<<(unsigned)c->E, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.h,
-        c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx),
-        c->p<double>(c->L.sy), x, tr, y, skip);
+    const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
+    k_dg_apply_2d<VT><<<(unsigned)c->E, threads, smem, s>>>(
+        c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.h, cx, cy, sx, sy,
+        x, tr, y, skip);
     count_launch();
     return cudaGetLastError();
   }
   const int nn = n * n, n3 = nn * n;
-  const size_t smem = (size_t)(nn + 3 * n3 + 6 * nn + 3 * n) * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(k_dg_apply_3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  const size_t smem = (size_t)(nn + 3 * n3 + 6 * nn + 3 * n) * sizeof(VT);
+  cudaError_t err = cudaFuncSetAttribute(k_dg_apply_3d<VT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_dg_apply_3d<<<(unsigned)c->E, 256, smem, s>>>(
+  k_dg_apply_3d<VT><<<(unsigned)c->E, 256, smem, s>>>(
       c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.nel[2], c->prob.h,
-      c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.cz), c->p<double>(c->L.sx),
-      c->p<double>(c->L.sy), c->p<double>(c->L.sz), x, tr, y, skip);
+      cx, cy, cz, sx, sy, sz, x, tr, y, skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                            const int32_t* skip, cudaStream_t s) {
+  const bool d3 = c->dim == 3;
+  return launch_dg_apply_t<double>(
+      c, c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
+      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr, x, tr,
+      y, skip, s);
+}
+
+// FP32 operator (the inner solves of the mixed-precision mode) on the float
+// copies of the flux Jacobian coefficients
+cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
+                                const int32_t* skip, cudaStream_t s) {
+  const float* f = c->p<float>(c->L.opf);
+  const OpF32Layout O = op_f32_layout(c->dim, c->N, c->E, c->n);
+  const bool d3 = c->dim == 3;
+  return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, d3 ? f + O.cz : nullptr, f + O.sx,
+                                  f + O.sy, d3 ? f + O.sz : nullptr, x, tr, y, skip, s);
+}
+
+// float copies of the operator coefficients (after k_precompute)
+__global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz,
+                            const double* sx, const double* sy, const double* sz, float* out,
+                            OpF32Layout O, int dim) {
+  const int64_t tv = O.cy - O.cx, tf = O.sy - O.sx;
+  const int64_t total = (int64_t)dim * (tv + tf);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    size_t dst;
+    if (g < dim * tv) {
+      const int which = (int)(g / tv);
+      const int64_t i = g % tv;
+      v = (which == 0 ? cx : which == 1 ? cy : cz)[i];
+      dst = (which == 0 ? O.cx : which == 1 ? O.cy : O.cz) + i;
+    } else {
+      const int64_t h = g - dim * tv;
+      const int which = (int)(h / tf);
+      const int64_t i = h % tf;
+      v = (which == 0 ? sx : which == 1 ? sy : sz)[i];
+      dst = (which == 0 ? O.sx : which == 1 ? O.sy : O.sz) + i;
+    }
+    out[dst] = __double2float_rn(v);
+  }
+}
+
+cudaError_t launch_op_to_f32(const tpp_ctx* c, cudaStream_t s) {
+  const OpF32Layout O = op_f32_layout(c->dim, c->N, c->E, c->n);
+  const bool d3 = c->dim == 3;
+  k_op_to_f32<<<152 * 4, 256, 0, s>>>(
+      c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
+      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr,
+      c->p<float>(c->L.opf), O, c->dim);
   count_launch();
   return cudaGetLastError();
 }

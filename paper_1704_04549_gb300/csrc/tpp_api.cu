@@ -26,10 +26,12 @@ tpp_status cuda_check(cudaError_t e, const char* what) {
 }
 
 // GMRES kernels (k_gmres.cu)
-cudaError_t gmres_dots(const double* V, int64_t N, int nvec, const double* w, double* partials,
+template <typename VT>
+cudaError_t gmres_dots(const VT* V, int64_t N, int nvec, const VT* w, double* partials,
                        int stride, int nblk, const int32_t* skip, double* h_out,
                        unsigned int* ticket, cudaStream_t s);
-cudaError_t gmres_update(const double* V, int64_t N, int nvec, const double* h, double* w,
+template <typename VT>
+cudaError_t gmres_update(const VT* V, int64_t N, int nvec, const double* h, VT* w,
                          double* partials, int stride, int mode, int nblk, const int32_t* skip,
                          double* h_out, unsigned int* ticket, GmresState* st, double* H,
                          double* cs, double* sn, double* g, double* h1, double* h2,
@@ -38,14 +40,22 @@ cudaError_t gmres_lsq(const GmresState* st, const double* H, const double* g, do
                       cudaStream_t s);
 cudaError_t gmres_combine(const double* B, int64_t N, const GmresState* st, const double* y,
                           double* out, int accumulate, cudaStream_t s);
+cudaError_t gmres_combine_f32(const float* B, int64_t N, const GmresState* st, const double* y,
+                              double* out, const int32_t* skip, cudaStream_t s);
 cudaError_t vec_scale(double* out, const double* in, int64_t N, const double* sptr, double sval,
                       const int32_t* skip, cudaStream_t s);
+cudaError_t vec_scale_f32(float* out, const float* in, int64_t N, const double* sptr,
+                          double sval, const int32_t* skip, cudaStream_t s);
+cudaError_t vec_to_float(const double* in, float* out, int64_t N, const int32_t* skip,
+                         cudaStream_t s);
 cudaError_t vec_sub(double* out, const double* a, const double* b, int64_t N, cudaStream_t s);
 cudaError_t vec_norm(const double* x, int64_t N, double* partials, int stride, int nblk,
                      double* out, cudaStream_t s);
 cudaError_t gmres_cycle_init(GmresState* st, double* g, double beta, int m, double bnorm,
-                             double rtol, cudaStream_t s);
+                             double rtol, const int32_t* done_src, cudaStream_t s);
 cudaError_t vec_axpy(double* out, const double* in, double a, int64_t N, cudaStream_t s);
+cudaError_t accumulate_inner(GmresState* outer, const GmresState* inner, const int32_t* skip,
+                             cudaStream_t s);
 
 namespace {
 
@@ -159,6 +169,13 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   }
   L.fG = two ? 0 : take(fsz * 2 * n);
   L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
+  if (features & TPP_FEAT_MIXED) {      // FP32 operator and inner GMRES
+    L.opf = take(op_f32_layout(d, N, E, n).total * 4);
+    L.gstate_in = take(sizeof(GmresState));
+    L.gbuf_in = take(gbuf_layout(m).total * sizeof(double));
+    L.vi = take((size_t)(m + 1) * N * 4);
+    L.tf = take((size_t)N * 4);
+  }
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
   L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
   L.V = take((size_t)(m + 1) * N * 8);
@@ -298,9 +315,16 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
                                          cudaMemcpyHostToDevice, s), "init status")) != TPP_OK) break;
     if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.tables, 0, sizeof(Tables), s), "memset")) != TPP_OK) break;
     if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.gstate, 0, sizeof(GmresState), s), "memset")) != TPP_OK) break;
+    if (L.gstate_in &&
+        (rc = cuda_check(cudaMemsetAsync(c->ws + L.gstate_in, 0, sizeof(GmresState), s),
+                         "memset")) != TPP_OK)
+      break;
     if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
     if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
     if ((rc = cuda_check(launch_precompute(c, s), "k_precompute")) != TPP_OK) break;
+    if ((features & TPP_FEAT_MIXED) &&
+        (rc = cuda_check(launch_op_to_f32(c, s), "k_op_to_f32")) != TPP_OK)
+      break;
     if ((rc = cuda_check(cudaStreamSynchronize(s), "tpp_create sync")) != TPP_OK) break;
   } while (0);
   if (rc != TPP_OK) {
@@ -413,6 +437,38 @@ tpp_status dg_apply_sumfact(const tpp_ctx* c, const double* x, double* y, void* 
   return TPP_OK;
 }
 
+tpp_status dg_apply_sumfact_f32(const tpp_ctx* c, const float* x, float* y, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!x || !y || x == y) {
+    set_error("x and y must be non-NULL and distinct");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (!(c->features & TPP_FEAT_MIXED)) {
+    set_error("dg_apply_sumfact_f32 needs TPP_FEAT_MIXED");
+    return TPP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* trf = c->p<float>(c->L.opf) + op_f32_layout(c->dim, c->N, c->E, c->n).tr;
+  TPP_TRY_CUDA(launch_traces_f32(c, x, trf, s, nullptr), "k_traces<float>");
+  TPP_TRY_CUDA(launch_dg_apply_f32(c, x, trf, y, nullptr, s), "k_dg_apply<float>");
+  return TPP_OK;
+}
+
+tpp_status tpp_apply_inverse_f32(const tpp_ctx* c, const float* b, float* x, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!b || !x || b == x) {
+    set_error("b and x must be non-NULL and distinct");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (!(c->features & TPP_FEAT_MIXED) || !c->factors_built) {
+    set_error("tpp_apply_inverse_f32 needs TPP_FEAT_MIXED and tpp_build_factors");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(launch_apply_f32(c, b, x, nullptr, static_cast<cudaStream_t>(stream)),
+               "tpp_apply_inverse_f32");
+  return TPP_OK;
+}
+
 tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
   if (tpp_status r = check_ctx(c)) return r;
   if (!o) {
@@ -484,7 +540,16 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     set_error("inner_prec TPP_FP32 needs TPP_FEAT_MIXED");
     return TPP_ERR_INVALID_ARG;
   }
-  const bool flexible = opts->flexible || opts->inner_prec != TPP_FP64;
+  const int kin = opts->inner_iters;
+  if (kin < 0 || kin > c->max_restart || opts->reserved != 0 || !(opts->inner_rtol >= 0.0)) {
+    set_error("inner_iters must be in [0, max_restart], reserved 0, inner_rtol >= 0");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (kin > 0 && (!(c->features & TPP_FEAT_MIXED) || opts->pc != TPP_PC_KRON)) {
+    set_error("inner FP32 solves need TPP_FEAT_MIXED and TPP_PC_KRON");
+    return TPP_ERR_INVALID_ARG;
+  }
+  const bool flexible = opts->flexible || opts->inner_prec != TPP_FP64 || kin > 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t N = c->N;
   const int nblk = c->partial_blocks, stride = kPartialStride;
@@ -501,6 +566,53 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
   double *h1 = gbuf + gb.h1, *h2 = gbuf + gb.h2, *y = gbuf + gb.y, *invb = gbuf + gb.invb;
   double* scal = gbuf + gb.scal;
   std::memset(res, 0, sizeof(*res));
+  // counters of this solve; the reduction tickets start at zero (they are
+  // zero after every completed kernel, this also covers an interrupted solve)
+  TPP_TRY_CUDA(cudaMemsetAsync(&st->inner_total, 0, sizeof(int32_t), s), "reset inner count");
+  TPP_TRY_CUDA(cudaMemsetAsync(st->tickets, 0, sizeof(st->tickets), s), "reset tickets");
+  if (c->L.gstate_in) {
+    GmresState* sti0 = c->p<GmresState>(c->L.gstate_in);
+    TPP_TRY_CUDA(cudaMemsetAsync(sti0->tickets, 0, sizeof(sti0->tickets), s), "reset tickets");
+  }
+  // inner FP32 solve z = (approximately) S^-1 v for one outer step (mixed mode):
+  // GMRES(kin) from 0 on float vectors, the FP32 operator and the FP32
+  // Kronecker apply as right preconditioner; every kernel returns at once when
+  // the outer cycle is done, and the inner ones also when the inner solve is.
+  auto inner_solve = [&](const double* v, double* z) -> tpp_status {
+    const GBuf gi = gbuf_layout(c->max_restart);
+    double* gb = c->p<double>(c->L.gbuf_in);
+    double *Hi = gb + gi.H, *csi = gb + gi.cs, *sni = gb + gi.sn, *g0 = gb + gi.g;
+    double *h1i = gb + gi.h1, *h2i = gb + gi.h2, *yi = gb + gi.y, *invbi = gb + gi.invb;
+    GmresState* sti = c->p<GmresState>(c->L.gstate_in);
+    const int32_t* din = &sti->done;
+    float* Vi = c->p<float>(c->L.vi);
+    float* tf = c->p<float>(c->L.tf);
+    float* trf = c->p<float>(c->L.opf) + op_f32_layout(c->dim, N, c->E, c->n).tr;
+    TPP_TRY_CUDA(vec_to_float(v, Vi, N, done, s), "inner v0");
+    TPP_TRY_CUDA(gmres_cycle_init(sti, g0, 1.0, kin, 1.0, opts->inner_rtol, done, s),
+                 "inner init");
+    for (int i = 0; i < kin; ++i) {
+      float* vi = Vi + (size_t)i * N;
+      float* wi = Vi + (size_t)(i + 1) * N;
+      TPP_TRY_CUDA(launch_apply_f32(c, vi, tf, din, s), "inner precond");
+      TPP_TRY_CUDA(launch_traces_f32(c, tf, trf, s, din), "inner traces");
+      TPP_TRY_CUDA(launch_dg_apply_f32(c, tf, trf, wi, din, s), "inner operator");
+      TPP_TRY_CUDA(gmres_dots<float>(Vi, N, i + 1, wi, partials, stride, nblk, din, h1i,
+                                     &sti->tickets[0], s), "inner dots");
+      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h1i, wi, partials, stride, 0, nblk, din, h2i,
+                                       &sti->tickets[1], sti, Hi, csi, sni, g0, h1i, h2i, invbi,
+                                       i, s), "inner update");
+      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h2i, wi, partials, stride, 1, nblk, din,
+                                       nullptr, &sti->tickets[2], sti, Hi, csi, sni, g0, h1i,
+                                       h2i, invbi, i, s), "inner norm+givens");
+      TPP_TRY_CUDA(vec_scale_f32(wi, wi, N, invbi, 0.0, din, s), "inner scale");
+    }
+    TPP_TRY_CUDA(gmres_lsq(sti, Hi, g0, yi, s), "inner lsq");
+    TPP_TRY_CUDA(gmres_combine_f32(Vi, N, sti, yi, t2, done, s), "inner Vy");
+    TPP_TRY_CUDA(accumulate_inner(st, sti, done, s), "inner count");
+    TPP_TRY_CUDA(apply_precond(c, TPP_PC_KRON, TPP_FP32, t2, z, done, s), "inner P^-1");
+    return TPP_OK;
+  };
   auto read_scalar = [&](const double* dptr, double* hv) -> tpp_status {
     TPP_TRY_CUDA(cudaMemcpyAsync(hv, dptr, sizeof(double), cudaMemcpyDeviceToHost, s), "read");
     TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
@@ -543,7 +655,7 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     }
     res->cycles += 1;
     TPP_TRY_CUDA(vec_scale(V, V, N, nullptr, 1.0 / beta, nullptr, s), "scale v0");
-    TPP_TRY_CUDA(gmres_cycle_init(st, g, beta, m, bnorm, opts->rtol, s), "cycle init");
+    TPP_TRY_CUDA(gmres_cycle_init(st, g, beta, m, bnorm, opts->rtol, nullptr, s), "cycle init");
     // Arnoldi steps are enqueued kLookahead at a time; every kernel of a step
     // returns at once when the device state says the cycle is done (converged,
     // breakdown or restart length reached), so the host reads the state only
@@ -554,7 +666,11 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
       double* vj = V + (size_t)j * N;
       double* w = V + (size_t)(j + 1) * N;
       double* z = flexible ? Z + (size_t)j * N : t1;
-      TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, vj, z, done, s), "precond");
+      if (kin > 0) {
+        if (tpp_status r = inner_solve(vj, z)) return r;
+      } else {
+        TPP_TRY_CUDA(apply_precond(c, opts->pc, opts->inner_prec, vj, z, done, s), "precond");
+      }
       TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s, done), "traces");
       TPP_TRY_CUDA(launch_dg_apply(c, z, c->p<double>(c->L.traces), w, done, s), "operator");
       TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, h1,
@@ -567,7 +683,8 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
                    "norm+givens");
       TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, done, s), "scale");
       ++total;
-      const bool group_end = ((j + 1) % kLookahead) == 0 || j + 1 == m || total >= opts->max_iters;
+      const int look = (kin > 0) ? 1 : kLookahead;    // an inner solve is a long step
+      const bool group_end = ((j + 1) % look) == 0 || j + 1 == m || total >= opts->max_iters;
       if (!group_end) continue;
       TPP_TRY_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s), "read state");
       TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
@@ -596,6 +713,13 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     }
   }
   res->iters = total;
+  if (kin > 0) {
+    int32_t nin = 0;
+    TPP_TRY_CUDA(cudaMemcpyAsync(&nin, &st->inner_total, sizeof(nin), cudaMemcpyDeviceToHost, s),
+                 "read inner count");
+    TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
+    res->inner_iters = nin;
+  }
   res->converged = (final_status == TPP_OK);
   res->status = final_status;
   if (final_status == TPP_ERR_NOT_CONVERGED)

@@ -58,7 +58,7 @@ struct GmresState {
   double est;         // |g_{k}| / ||b||
   double rtol;
   int32_t m;          // restart length
-  int32_t pad2;
+  int32_t inner_total;   // inner FP32 steps taken in this solve (mixed mode)
   unsigned int tickets[4];   // last-block-done counters of the reduction kernels
 };
 
@@ -74,6 +74,8 @@ struct Layout {
   size_t bscr, biscr;                  // factor-build scratch (Lanczos bases, tridiagonal work)
   size_t kco;                          // per-block KSVD coefficients (Cx, Cy, Dg)
   size_t fG;                           // one-sided form: shifted inverses, 2 n^3 per element
+  size_t opf;                          // mixed mode: FP32 operator data (OpF32Layout)
+  size_t gstate_in, gbuf_in, vi, tf;   // mixed mode: inner FP32 GMRES state, H, basis, temp
   size_t s1scr, fAz, fAzi, sigz, zflags;   // 3D stage 1: scratch, A1, A1^-1, sigma_1, flags
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
@@ -158,6 +160,13 @@ __host__ __device__ inline int s1_jmax(int n) { return (n * n < 64) ? n * n : 64
 
 cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
+                              const int32_t* skip);
+cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
+                                const int32_t* skip, cudaStream_t s);
+cudaError_t launch_op_to_f32(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_apply_f32(const tpp_ctx* c, const float* b, float* x, const int32_t* skip,
+                             cudaStream_t s);
 // float32 copies of the apply factors (offsets in floats from Layout::f32)
 struct F32Layout {
   size_t SA, SB, Q1, Q2, T1, T2, Azi, G, total;
@@ -173,6 +182,27 @@ inline F32Layout f32_layout(int n, int64_t E, int dim, bool two) {
   if (two) { L.Q2 = o; o += m; L.T2 = o; o += m; }
   if (dim == 3) { L.Azi = o; o += m; }
   if (!two) { L.G = o; o += 2 * m * n; }
+  L.total = o;
+  return L;
+}
+
+// float copies of the operator data for the FP32 inner solves (offsets in
+// floats from Layout::opf): volume coefficients (N each), lower-face
+// coefficients (E n^(d-1) each), face traces (E 2d n^(d-1))
+struct OpF32Layout {
+  size_t cx, cy, cz, sx, sy, sz, tr, total;
+};
+inline OpF32Layout op_f32_layout(int dim, int64_t N, int64_t E, int n) {
+  const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;
+  OpF32Layout L{};
+  size_t o = 0;
+  L.cx = o; o += N;
+  L.cy = o; o += N;
+  L.cz = o; if (dim == 3) o += N;
+  L.sx = o; o += E * nfl;
+  L.sy = o; o += E * nfl;
+  L.sz = o; if (dim == 3) o += E * nfl;
+  L.tr = o; o += E * 2 * dim * nfl;
   L.total = o;
   return L;
 }

@@ -120,6 +120,26 @@ class Context:
                 "dg_apply_sumfact")
         return y
 
+    def _vec32(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous() and t.numel() == self.num_dofs):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {self.num_dofs}")
+        return t
+
+    def dg_apply_sumfact_f32(self, x, y=None, stream=None):
+        x = self._vec32(x, "x")
+        y = torch.empty_like(x) if y is None else self._vec32(y, "y")
+        L.check(self.lib.dg_apply_sumfact_f32(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
+                "dg_apply_sumfact_f32")
+        return y
+
+    def tpp_apply_inverse_f32(self, b, x=None, stream=None):
+        b = self._vec32(b, "b")
+        x = torch.empty_like(b) if x is None else self._vec32(x, "x")
+        L.check(self.lib.tpp_apply_inverse_f32(self._ctx, _ptr(b), _ptr(x), _stream(stream)),
+                "tpp_apply_inverse_f32")
+        return x
+
     def dg_apply_sumfact_static(self, x, y=None, stream=None):
         """dg_apply_sumfact with its trace scratch in libtpp's static device array
         (for callers that cannot allocate device scratch; overlapping calls race)."""
@@ -131,10 +151,12 @@ class Context:
 
     def gmres_solve(self, b, x=None, restart: int = 30, rtol: float = 1e-8,
                     max_iters: int = 3000, pc: int = L.TPP_PC_KRON, inner_prec: int = L.TPP_FP64,
-                    flexible: bool = False, stream=None, check: bool = True):
+                    flexible: bool = False, stream=None, check: bool = True,
+                    inner_iters: int = 0, inner_rtol: float = 0.0):
         b = self._vec(b, "b")
         x = torch.zeros_like(b) if x is None else self._vec(x, "x")
-        o = L.GmresOpts(restart, max_iters, rtol, pc, inner_prec, int(flexible))
+        o = L.GmresOpts(restart, max_iters, rtol, pc, inner_prec, int(flexible), int(inner_iters),
+                        0, float(inner_rtol))
         r = L.GmresResult()
         st = self.lib.gmres_solve(self._ctx, _ptr(b), _ptr(x), C.byref(o), C.byref(r),
                                   _stream(stream))
