@@ -455,8 +455,10 @@ def run_kernels(args):
     if args.workload == "adv2d":           # one solve: the Arnoldi kernels in their share
         from paper_1704_04549_gb300 import TPP_PC_KRON
         x = torch.zeros_like(b)
+        mixed = args.prec == "mixed"
         ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters, pc=TPP_PC_KRON,
-                        check=False)
+                        check=False, inner_prec=TPP_FP32 if mixed else TPP_FP64,
+                        flexible=mixed, inner_iters=args.inner if mixed else 0)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "kernels", "workload": args.workload, "n": w["n"],
                       "dofs": ctx.num_dofs}))

@@ -16,18 +16,37 @@ constexpr int kRegBasis = 32;      // basis sizes kept in register tiles
 constexpr int kWarps = kRedThreads / 32;
 
 // Per-thread accumulators acc[i < cnt] -> partials[blk * stride + g0 + i]
-// (warp sums, then the block's warps in order: deterministic).
-template <typename AT>
-__device__ void store_block_partials(const AT (&acc)[kRegBasis], int cnt, int g0,
-                                     double* partials, int stride, double* red) {
+// (deterministic).  Within a warp the G sums are formed by recursive halving:
+// at each butterfly level a lane keeps half of its values and adds the
+// partner's copy of them, so the warp issues G - 1 + (5 - log2 G) additions in
+// total instead of 5 G for G separate shuffle trees (the additions are FP64
+// instructions for double accumulators, a scarce pipe on this GPU).  Lane l
+// ends with the value whose index is given by its bits 4, 3, ... (high to low);
+// the warps' results are then added in warp order.
+template <typename AT, int G>
+__device__ void store_block_partials(AT (&acc)[G], int cnt, int g0, double* partials,
+                                     int stride, double* red) {
+  static_assert(G == 8 || G == 16 || G == 32, "group size");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int LG = (G == 8) ? 3 : (G == 16) ? 4 : 5;
 #pragma unroll
-  for (int i = 0; i < kRegBasis; ++i) {
-    if (i < cnt) {
-      const double v = warp_sum((double)acc[i]);
-      if (lane == 0) red[i * kWarps + wid] = v;
+  for (int lev = 0; lev < LG; ++lev) {
+    const int sft = 16 >> lev;                 // partner distance
+    const int half = G >> (lev + 1);           // values kept per lane after this level
+    const bool up = (lane & sft) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const AT send = up ? acc[k] : acc[k + half];
+      const AT keep = up ? acc[k + half] : acc[k];
+      acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
     }
   }
+#pragma unroll
+  for (int sft = (16 >> LG); sft > 0; sft >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], sft);
+  int idx = 0;
+#pragma unroll
+  for (int lev = 0; lev < LG; ++lev) idx = 2 * idx + ((lane >> (4 - lev)) & 1);
+  if ((lane & ((1 << (5 - LG)) - 1)) == 0 && idx < cnt) red[idx * kWarps + wid] = (double)acc[0];
   __syncthreads();
   if (threadIdx.x < cnt) {
     double t = 0.0;
@@ -37,24 +56,51 @@ __device__ void store_block_partials(const AT (&acc)[kRegBasis], int cnt, int g0
   __syncthreads();
 }
 
-// partials of V_i . w, i < nvec (groups of kRegBasis vectors)
+// block sum of one value in the accumulator type (float sums stay on the FMA pipe)
+template <typename AT>
+__device__ AT block_sum_t(AT v, AT* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  AT t = (AT)0;
+  for (int k = 0; k < kWarps; ++k) t += red[k];
+  __syncthreads();
+  return t;
+}
+
+// partials of V_i . w for g0 <= i < g0 + cnt, cnt <= G.  The G loads of a point
+// are issued unconditionally (indices past cnt repeat the last vector, a cache
+// hit) so that they are all in flight together.
+template <typename VT, int G>
+__device__ void dot_group(const VT* __restrict__ V, int64_t N, int g0, int cnt,
+                          const VT* __restrict__ w, double* __restrict__ partials, int stride,
+                          double* red) {
+  VT acc[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) acc[i] = (VT)0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const VT wv = w[t];
+    VT vv[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) vv[i] = V[(size_t)(g0 + (i < cnt ? i : cnt - 1)) * N + t];
+#pragma unroll
+    for (int i = 0; i < G; ++i) acc[i] += vv[i] * wv;
+  }
+  store_block_partials<VT, G>(acc, cnt, g0, partials, stride, red);
+}
+
 template <typename VT>
 __device__ void dot_block(const VT* __restrict__ V, int64_t N, int nvec,
                           const VT* __restrict__ w, double* __restrict__ partials, int stride,
                           double* red) {
   for (int g0 = 0; g0 < nvec; g0 += kRegBasis) {
     const int cnt = (nvec - g0) < kRegBasis ? (nvec - g0) : kRegBasis;
-    VT acc[kRegBasis];
-#pragma unroll
-    for (int i = 0; i < kRegBasis; ++i) acc[i] = (VT)0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      const VT wv = w[t];
-#pragma unroll
-      for (int i = 0; i < kRegBasis; ++i)
-        if (i < cnt) acc[i] += V[(size_t)(g0 + i) * N + t] * wv;
-    }
-    store_block_partials(acc, cnt, g0, partials, stride, red);
+    if (cnt <= 8) dot_group<VT, 8>(V, N, g0, cnt, w, partials, stride, red);
+    else if (cnt <= 16) dot_group<VT, 16>(V, N, g0, cnt, w, partials, stride, red);
+    else dot_group<VT, 32>(V, N, g0, cnt, w, partials, stride, red);
   }
 }
 
@@ -122,58 +168,74 @@ __device__ void finish_column(const ArnoldiArgs& a, double nrm2) {
 }
 
 // pass 1 of CGS2: h1 = V^T w
-template <typename VT>
+template <typename VT, int G>
 __global__ void __launch_bounds__(kRedThreads)
 k_dots(const VT* V, int64_t N, int nvec, const VT* w, double* partials, int stride,
        const int32_t* skip, double* h_out, unsigned int* ticket) {
   if (skip && *skip) return;
   __shared__ double red[kRegBasis * kWarps];
-  dot_block(V, N, nvec, w, partials, stride, red);
+  if (G > 0) dot_group<VT, (G > 0 ? G : 8)>(V, N, 0, nvec, w, partials, stride, red);
+  else dot_block(V, N, nvec, w, partials, stride, red);
   if (last_block(ticket)) {
     final_reduce(partials, gridDim.x, stride, nvec, h_out);
     if (threadIdx.x == 0) *ticket = 0;
   }
 }
 
+// w -= V h for one point per thread, nvec <= G vectors (loads unconditional,
+// coefficients of the padded entries are zero); mode 0 also accumulates the
+// products of the same basis entries with the updated w (pass 2 of CGS2 in one
+// read of the basis), mode 1 the squared norm.
+template <typename VT, int G>
+__device__ void update_group(const VT* __restrict__ V, int64_t N, int nvec, const VT* hs,
+                             VT* __restrict__ w, int mode, VT& nrm, double* partials,
+                             int stride, double* red) {
+  VT acc[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) acc[i] = (VT)0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    VT vv[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) vv[i] = V[(size_t)(i < nvec ? i : nvec - 1) * N + t];
+    VT wv = w[t];
+#pragma unroll
+    for (int i = 0; i < G; ++i) wv -= hs[i] * vv[i];
+    w[t] = wv;
+    if (mode == 0) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) acc[i] += vv[i] * wv;
+    } else {
+      nrm += wv * wv;
+    }
+  }
+  if (mode == 0) store_block_partials<VT, G>(acc, nvec, 0, partials, stride, red);
+}
+
 // w -= V h_in; mode 0: h_out = V^T w (pass 2 of CGS2, fused: the basis entries
 // of a point stay in registers for both products when nvec <= kRegBasis);
-// mode 1: ||w||^2 and the Givens update of column a.j
-template <typename VT>
+// mode 1: ||w||^2 and the Givens update of column a.j; mode 2 (first pass of
+// the selectively reorthogonalised Gram-Schmidt): ||w||^2, and if it kept at
+// least half of ||w_before||^2 = h_in[nvec] (the norm did not drop by more than
+// 1/sqrt 2: Daniel-Gragg-Kaufman-Stewart) the column is final, h2 = 0 and the
+// Givens update runs here, st->skip_re = 1; otherwise st->skip_re = 0 and the
+// second pass follows.  A skipped mode-2 launch sets skip_re = 1.
+template <typename VT, int G>
 __global__ void __launch_bounds__(kRedThreads)
 k_update(const VT* __restrict__ V, int64_t N, int nvec, const double* __restrict__ h_in,
          VT* __restrict__ w, double* partials, int stride, int mode, const int32_t* skip,
          double* h_out, unsigned int* ticket, ArnoldiArgs aa) {
-  if (skip && *skip) return;
+  if (skip && *skip) {
+    if (mode == 2 && blockIdx.x == 0 && threadIdx.x == 0) aa.st->skip_re = 1;
+    return;
+  }
   __shared__ VT hs[kMaxBasis];
   __shared__ double red[kRegBasis * kWarps];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = (VT)h_in[i];
+  for (int i = threadIdx.x; i < kMaxBasis; i += blockDim.x) hs[i] = (i < nvec) ? (VT)h_in[i] : (VT)0;
   __syncthreads();
   VT nrm = (VT)0;
-  if (nvec <= kRegBasis) {
-    VT acc[kRegBasis];
-#pragma unroll
-    for (int i = 0; i < kRegBasis; ++i) acc[i] = (VT)0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      VT vv[kRegBasis];
-      VT wv = w[t];
-#pragma unroll
-      for (int i = 0; i < kRegBasis; ++i) {
-        if (i < nvec) {
-          vv[i] = V[(size_t)i * N + t];
-          wv -= hs[i] * vv[i];
-        }
-      }
-      w[t] = wv;
-      if (mode == 0) {
-#pragma unroll
-        for (int i = 0; i < kRegBasis; ++i)
-          if (i < nvec) acc[i] += vv[i] * wv;
-      } else {
-        nrm += wv * wv;
-      }
-    }
-    if (mode == 0) store_block_partials(acc, nvec, 0, partials, stride, red);
+  if (G > 0) {
+    update_group<VT, (G > 0 ? G : 8)>(V, N, nvec, hs, w, mode, nrm, partials, stride, red);
   } else {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -193,14 +255,22 @@ k_update(const VT* __restrict__ V, int64_t N, int nvec, const double* __restrict
       if (threadIdx.x == 0) *ticket = 0;
     }
   } else {
-    const double sblk = block_sum((double)nrm, red);
+    const double sblk = (double)block_sum_t<VT>(nrm, reinterpret_cast<VT*>(red));
     if (threadIdx.x == 0) partials[blockIdx.x * stride] = sblk;
     if (last_block(ticket)) {
       __shared__ double tot;
       final_reduce(partials, gridDim.x, stride, 1, &tot);
       __syncthreads();
       if (threadIdx.x == 0) {
-        finish_column(aa, tot);
+        if (mode == 1) {
+          finish_column(aa, tot);
+        } else if (tot >= 0.5 * h_in[nvec]) {
+          for (int i = 0; i < nvec; ++i) aa.h2[i] = 0.0;
+          finish_column(aa, tot);
+          aa.st->skip_re = 1;
+        } else {
+          aa.st->skip_re = 0;
+        }
         *ticket = 0;
       }
     }
@@ -301,14 +371,21 @@ __global__ void k_cycle_init(GmresState* st, double* g, double beta, int m, doub
 // ---------------------------------------------------------------------------
 // launch helpers used by the host solver (VT = double: the FP64 solver, float:
 // the inner solves of the mixed-precision mode)
-constexpr int kVecBlocks = 152 * 2;     // grid of the register-tiled basis kernels
+constexpr int kVecBlocks = 152 * 4;     // grid of the basis kernels
 
 template <typename VT>
 cudaError_t gmres_dots(const VT* V, int64_t N, int nvec, const VT* w, double* partials,
                        int stride, int nblk, const int32_t* skip, double* h_out,
                        unsigned int* ticket, cudaStream_t s) {
   const int g = nblk < kVecBlocks ? nblk : kVecBlocks;
-  k_dots<VT><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
+  if (nvec <= 8)
+    k_dots<VT, 8><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
+  else if (nvec <= 16)
+    k_dots<VT, 16><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
+  else if (nvec <= kRegBasis)
+    k_dots<VT, 32><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
+  else
+    k_dots<VT, 0><<<g, kRedThreads, 0, s>>>(V, N, nvec, w, partials, stride, skip, h_out, ticket);
   count_launch();
   return cudaGetLastError();
 }
@@ -320,8 +397,18 @@ cudaError_t gmres_update(const VT* V, int64_t N, int nvec, const double* h, VT* 
                          double* inv_beta, int j, cudaStream_t s) {
   ArnoldiArgs aa{st, H, cs, sn, g, h1, h2, inv_beta, j};
   const int gr = nblk < kVecBlocks ? nblk : kVecBlocks;
-  k_update<VT><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip, h_out,
-                                          ticket, aa);
+  if (nvec <= 8)
+    k_update<VT, 8><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip,
+                                               h_out, ticket, aa);
+  else if (nvec <= 16)
+    k_update<VT, 16><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip,
+                                                h_out, ticket, aa);
+  else if (nvec <= kRegBasis)
+    k_update<VT, 32><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip,
+                                                h_out, ticket, aa);
+  else
+    k_update<VT, 0><<<gr, kRedThreads, 0, s>>>(V, N, nvec, h, w, partials, stride, mode, skip,
+                                               h_out, ticket, aa);
   count_launch();
   return cudaGetLastError();
 }

@@ -74,6 +74,13 @@ __global__ void k_tables(Tables* T, int n) {
     T->l0[i] = (lam[i] / (0.0 - T->x[i])) / s0;
     T->l1[i] = (lam[i] / (1.0 - T->x[i])) / s1;
   }
+  __syncthreads();
+  if (i < n) {
+    T->wf[i] = __double2float_rn(T->w[i]);
+    T->l0f[i] = __double2float_rn(T->l0[i]);
+    T->l1f[i] = __double2float_rn(T->l1[i]);
+    for (int j = 0; j < n; ++j) T->Df[i * n + j] = __double2float_rn(T->D[i * n + j]);
+  }
 }
 
 cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s) {
@@ -286,7 +293,10 @@ __global__ void k_traces(const Tables* T, int n, int64_t E, const VT* __restrict
   const int nloc = nfl * n;
   const int64_t tot = E * nfl;
   __shared__ VT l0[TPP_MAX_N], l1[TPP_MAX_N];
-  if (threadIdx.x < n) { l0[threadIdx.x] = (VT)T->l0[threadIdx.x]; l1[threadIdx.x] = (VT)T->l1[threadIdx.x]; }
+  if (threadIdx.x < n) {
+    l0[threadIdx.x] = Tab<VT>::l0(T)[threadIdx.x];
+    l1[threadIdx.x] = Tab<VT>::l1(T)[threadIdx.x];
+  }
   __syncthreads();
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -341,7 +351,7 @@ cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaS
 // F^R_j = max(sR_j,0) u^-_R + min(sR_j,0) u^+_R (upwind flux through the +x
 // face, pre-scaled by dt h w_j), etc.
 template <typename VT>
-__global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
+__global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
                               const VT* __restrict__ cx, const VT* __restrict__ cy,
                               const VT* __restrict__ sx, const VT* __restrict__ sy,
                               const VT* __restrict__ x, const VT* __restrict__ tr,
@@ -362,15 +372,15 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
   const int tid = threadIdx.x;
   const int64_t base = e * nn;
   for (int q = tid; q < nn; q += blockDim.x) {
-    Ds[q] = (VT)T->D[q];
+    Ds[q] = Tab<VT>::D(T)[q];
     const VT xv = x[base + q];
     px[q] = cx[base + q] * xv;
     py[q] = cy[base + q] * xv;
   }
   if (tid < n) {
-    wl[tid] = (VT)T->w[tid];
-    wl[n + tid] = (VT)T->l0[tid];
-    wl[2 * n + tid] = (VT)T->l1[tid];
+    wl[tid] = Tab<VT>::w(T)[tid];
+    wl[n + tid] = Tab<VT>::l0(T)[tid];
+    wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
     const VT* te = tr + e * 4 * n;
     const int t = tid;
     const VT zero = (VT)0;
@@ -392,7 +402,7 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
     }
   }
   __syncthreads();
-  const VT h2 = (VT)(h * h);
+  const VT h2 = hd;                 // h^2
   for (int q = tid; q < nn; q += blockDim.x) {
     const int i = q % n, j = q / n;
     VT acc = h2 * wl[i] * wl[j] * x[base + q];
@@ -409,7 +419,7 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, double h,
 //           + sum_c D_ck cz_ijc x_ijc + l1_i F^+x_jk - l0_i F^-x_jk + (same for y, z),
 // face fluxes pre-scaled by dt h^2 and the two tangential weights.
 template <typename VT>
-__global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, double h,
+__global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT hd,
                               const VT* __restrict__ cx, const VT* __restrict__ cy,
                               const VT* __restrict__ cz, const VT* __restrict__ sx,
                               const VT* __restrict__ sy, const VT* __restrict__ sz,
@@ -435,7 +445,7 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, do
   const int64_t eZp = eid(ex, ey, ez + 1), eZm = eid(ex, ey, ez - 1);
   const int tid = threadIdx.x;
   const int64_t base = e * n3;
-  for (int q = tid; q < nn; q += blockDim.x) Ds[q] = (VT)T->D[q];
+  for (int q = tid; q < nn; q += blockDim.x) Ds[q] = Tab<VT>::D(T)[q];
   for (int q = tid; q < n3; q += blockDim.x) {
     const VT xv = x[base + q];
     px[q] = cx[base + q] * xv;
@@ -443,9 +453,9 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, do
     pz[q] = cz[base + q] * xv;
   }
   if (tid < n) {
-    wl[tid] = (VT)T->w[tid];
-    wl[n + tid] = (VT)T->l0[tid];
-    wl[2 * n + tid] = (VT)T->l1[tid];
+    wl[tid] = Tab<VT>::w(T)[tid];
+    wl[n + tid] = Tab<VT>::l0(T)[tid];
+    wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
   }
   const VT* te = tr + e * 6 * nn;
   const VT zero = (VT)0;
@@ -465,7 +475,7 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, do
     fl[5 * nn + q] = max(s, zero) * tr[eZm * 6 * nn + 5 * nn + q] + min(s, zero) * te[4 * nn + q];
   }
   __syncthreads();
-  const VT h3 = (VT)(h * h * h);
+  const VT h3 = hd;                 // h^3
   for (int q = tid; q < n3; q += blockDim.x) {
     const int i = q % n, j = (q / n) % n, k = q / nn;
     VT acc = h3 * wl[i] * wl[j] * wl[k] * x[base + q];
@@ -489,9 +499,10 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
     const int nn = n * n;
     const int threads = ((nn + 31) / 32) * 32;
     const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
+    const double h = c->prob.h;
     k_dg_apply_2d<VT><<<(unsigned)c->E, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.h, cx, cy, sx, sy,
-        x, tr, y, skip);
+        c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], (VT)(h * h), cx, cy, sx,
+        sy, x, tr, y, skip);
     count_launch();
     return cudaGetLastError();
   }
@@ -500,9 +511,10 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
   cudaError_t err = cudaFuncSetAttribute(k_dg_apply_3d<VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
+  const double h = c->prob.h;
   k_dg_apply_3d<VT><<<(unsigned)c->E, 256, smem, s>>>(
-      c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.nel[2], c->prob.h,
-      cx, cy, cz, sx, sy, sz, x, tr, y, skip);
+      c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.nel[2],
+      (VT)(h * h * h), cx, cy, cz, sx, sy, sz, x, tr, y, skip);
   count_launch();
   return cudaGetLastError();
 }

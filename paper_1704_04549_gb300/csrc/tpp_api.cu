@@ -597,14 +597,19 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
       TPP_TRY_CUDA(launch_apply_f32(c, vi, tf, din, s), "inner precond");
       TPP_TRY_CUDA(launch_traces_f32(c, tf, trf, s, din), "inner traces");
       TPP_TRY_CUDA(launch_dg_apply_f32(c, tf, trf, wi, din, s), "inner operator");
-      TPP_TRY_CUDA(gmres_dots<float>(Vi, N, i + 1, wi, partials, stride, nblk, din, h1i,
+      // Gram-Schmidt with selective reorthogonalisation: dots with the basis
+      // and ||w||^2 (w is basis vector i + 1), update + norm, then the second
+      // pass only when the norm dropped below 1/sqrt 2 of its value
+      TPP_TRY_CUDA(gmres_dots<float>(Vi, N, i + 2, wi, partials, stride, nblk, din, h1i,
                                      &sti->tickets[0], s), "inner dots");
-      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h1i, wi, partials, stride, 0, nblk, din, h2i,
-                                       &sti->tickets[1], sti, Hi, csi, sni, g0, h1i, h2i, invbi,
-                                       i, s), "inner update");
-      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h2i, wi, partials, stride, 1, nblk, din,
-                                       nullptr, &sti->tickets[2], sti, Hi, csi, sni, g0, h1i,
-                                       h2i, invbi, i, s), "inner norm+givens");
+      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h1i, wi, partials, stride, 2, nblk, din,
+                                       nullptr, &sti->tickets[1], sti, Hi, csi, sni, g0, h1i,
+                                       h2i, invbi, i, s), "inner update");
+      TPP_TRY_CUDA(gmres_dots<float>(Vi, N, i + 1, wi, partials, stride, nblk, &sti->skip_re,
+                                     h2i, &sti->tickets[2], s), "inner dots 2");
+      TPP_TRY_CUDA(gmres_update<float>(Vi, N, i + 1, h2i, wi, partials, stride, 1, nblk,
+                                       &sti->skip_re, nullptr, &sti->tickets[3], sti, Hi, csi, sni,
+                                       g0, h1i, h2i, invbi, i, s), "inner norm+givens");
       TPP_TRY_CUDA(vec_scale_f32(wi, wi, N, invbi, 0.0, din, s), "inner scale");
     }
     TPP_TRY_CUDA(gmres_lsq(sti, Hi, g0, yi, s), "inner lsq");
@@ -673,13 +678,17 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
       }
       TPP_TRY_CUDA(launch_traces(c, z, c->p<double>(c->L.traces), s, done), "traces");
       TPP_TRY_CUDA(launch_dg_apply(c, z, c->p<double>(c->L.traces), w, done, s), "operator");
-      TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, done, h1,
+      // Gram-Schmidt with selective reorthogonalisation (see k_update): the
+      // first pass also takes ||w||^2 (w is basis vector j + 1)
+      TPP_TRY_CUDA(gmres_dots(V, N, j + 2, w, partials, stride, nblk, done, h1,
                               &st->tickets[0], s), "dots");
-      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h1, w, partials, stride, 0, nblk, done, h2,
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h1, w, partials, stride, 2, nblk, done, nullptr,
                                 &st->tickets[1], st, H, cs, sn, g, h1, h2, invb, j, s),
                    "update");
-      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, done, nullptr,
-                                &st->tickets[2], st, H, cs, sn, g, h1, h2, invb, j, s),
+      TPP_TRY_CUDA(gmres_dots(V, N, j + 1, w, partials, stride, nblk, &st->skip_re, h2,
+                              &st->tickets[2], s), "dots 2");
+      TPP_TRY_CUDA(gmres_update(V, N, j + 1, h2, w, partials, stride, 1, nblk, &st->skip_re,
+                                nullptr, &st->tickets[3], st, H, cs, sn, g, h1, h2, invb, j, s),
                    "norm+givens");
       TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, done, s), "scale");
       ++total;

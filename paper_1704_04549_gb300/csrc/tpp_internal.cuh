@@ -32,6 +32,26 @@ struct Tables {
   double l0[TPP_MAX_N];
   double l1[TPP_MAX_N];
   double D[TPP_MAX_N * TPP_MAX_N];
+  // float copies (rounded to nearest) for the FP32 kernels, which then issue no
+  // FP64 conversion instructions
+  float wf[TPP_MAX_N];
+  float l0f[TPP_MAX_N];
+  float l1f[TPP_MAX_N];
+  float Df[TPP_MAX_N * TPP_MAX_N];
+};
+
+template <typename VT> struct Tab;
+template <> struct Tab<double> {
+  static __device__ const double* w(const Tables* T) { return T->w; }
+  static __device__ const double* l0(const Tables* T) { return T->l0; }
+  static __device__ const double* l1(const Tables* T) { return T->l1; }
+  static __device__ const double* D(const Tables* T) { return T->D; }
+};
+template <> struct Tab<float> {
+  static __device__ const float* w(const Tables* T) { return T->wf; }
+  static __device__ const float* l0(const Tables* T) { return T->l0f; }
+  static __device__ const float* l1(const Tables* T) { return T->l1f; }
+  static __device__ const float* D(const Tables* T) { return T->Df; }
 };
 
 // Device-side status words written by kernels (never trap).
@@ -60,6 +80,8 @@ struct GmresState {
   int32_t m;          // restart length
   int32_t inner_total;   // inner FP32 steps taken in this solve (mixed mode)
   unsigned int tickets[4];   // last-block-done counters of the reduction kernels
+  int32_t skip_re;    // 1: the current column needs no second Gram-Schmidt pass (or is done)
+  int32_t pad3;
 };
 
 struct Layout {
