@@ -38,9 +38,10 @@ FP64_PEAK_NOTE = ("FP64 peak = 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 125
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
-def workload(n: int):
-    return dict(dim=2, n=n, nel=(64, 64), h=1.0, dt=0.05,
-                velocity=synthetic.fourier_velocity(1705, 2), rhs_seed=1706)
+def workload(n: int, h: float = 1.0, solenoidal: bool = True):
+    return dict(dim=2, n=n, nel=(64, 64), h=h, dt=0.05,
+                velocity=synthetic.fourier_velocity(1705, 2, solenoidal=solenoidal),
+                rhs_seed=1706)
 
 
 def workload_3d(n: int = 11):
@@ -228,7 +229,8 @@ def run_ours(args):
     from paper_1704_04549_gb300 import _lib
 
     lib = _lib.load()
-    w = workload(args.n)
+    w = workload(args.n, 1.0 / 64 if args.h_reading == "domain" else 1.0,
+                 args.field == "solenoidal")
     ctx = Context(2, args.n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
                   features=TPP_FEAT_MIXED | form_bits(args), device=str(dev))
     N, E, n = ctx.num_dofs, ctx.num_elem, args.n
@@ -240,12 +242,12 @@ def run_ours(args):
 
     kin = args.inner if inner != TPP_FP64 else 0
 
-    def step():
+    def step(prec=inner, k_in=kin, rtol=1e-8):
         ctx.tpp_build_factors()
         x.zero_()
-        _, res = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=args.max_iters,
-                                 pc=TPP_PC_KRON, inner_prec=inner, flexible=(inner != TPP_FP64),
-                                 check=False, inner_iters=kin)
+        _, res = ctx.gmres_solve(b, x, restart=30, rtol=rtol, max_iters=args.max_iters,
+                                 pc=TPP_PC_KRON, inner_prec=prec, flexible=(prec != TPP_FP64),
+                                 check=False, inner_iters=k_in)
         return res
 
     for _ in range(args.warmup):
@@ -269,6 +271,25 @@ def run_ours(args):
         ms = float(t.item())
     res = results[-1]
     converged = all(r["converged"] for r in results)
+
+    # the other precision mode on the same workload and clock rules (FP64 <-> mixed)
+    o_prec = TPP_FP64 if inner != TPP_FP64 else TPP_FP32
+    o_kin = args.inner if o_prec != TPP_FP64 else 0
+    for _ in range(args.warmup):
+        step(o_prec, o_kin)
+    torch.cuda.synchronize(dev)
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    o_res = [step(o_prec, o_kin) for _ in range(args.steps)]
+    o1.record(stream)
+    torch.cuda.synchronize(dev)
+    other = {"mode": "fp64" if o_prec == TPP_FP64 else "mixed", "inner_iters_per_outer": o_kin,
+             "ms_per_step": o0.elapsed_time(o1) / args.steps, "iters": o_res[-1]["iters"],
+             "inner_iters": o_res[-1]["inner_iters"],
+             "converged": all(r["converged"] for r in o_res),
+             "true_rel_res": o_res[-1]["true_rel_res"]}
+    # iteration count at the paper's tolerance 1e-5 (shape comparison; untimed)
+    iters_1e5 = step(rtol=1e-5)["iters"]
 
     # split of one step: build vs solve (CUDA events)
     torch.cuda.synchronize(dev)
@@ -327,10 +348,11 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if inner == TPP_FP64 else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": f"adv2d-fourier-64x64-n{n} (p={n - 1}), unit-square quads, "
-                               f"dt=0.05, solenoidal random-Fourier velocity seed 1705, "
+        "config": {"workload": f"adv2d-fourier-64x64-n{n} (p={n - 1}), "
+                               f"{'unit-square quads' if w['h'] == 1.0 else 'h=1/64'}, "
+                               f"dt=0.05, {args.field} random-Fourier velocity seed 1705, "
                                f"b~N(0,1) seed 1706",
-                   "n": n, "nel": [64, 64], "h": 1.0, "dt": 0.05, "dofs": N, "rtol": 1e-8,
+                   "n": n, "nel": [64, 64], "h": w["h"], "dt": 0.05, "dofs": N, "rtol": 1e-8,
                    "restart": 30, "preconditioner": "KSVD rank-2 (Alg. 2d-form / 2d-apply)",
                    "inner_prec": args.prec, "apply_form": args.form,
                    "solver": ("FP64 flexible GMRES(30) around inner FP32 GMRES(%d) solves "
@@ -341,7 +363,8 @@ def run_ours(args):
                          "precond_apply: L2 flushed (256 MB write) before each timed launch"
                          % (31 * N * 8 / 1e6, 6 * N * 8 / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "gmres": {"iters": res["iters"], "inner_iters": res["inner_iters"],
+        "other_mode": other,
+        "gmres": {"iters": res["iters"], "inner_iters": res["inner_iters"], "iters_at_1e-5": iters_1e5,
                   "cycles": res["cycles"], "converged": converged,
                   "true_rel_res": res["true_rel_res"], "build_ms": build_ms,
                   "solve_ms": ms - build_ms},
@@ -481,6 +504,12 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="GMRES iterations the reference arm extrapolates to")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--h-reading", choices=["unit", "domain"], default="unit",
+                    help="unit: unit-square elements (h = 1); domain: the unit square tiled, "
+                         "h = 1/64")
+    ap.add_argument("--field", choices=["solenoidal", "components"], default="solenoidal",
+                    help="random-Fourier velocity: divergence-free modes, or independent "
+                         "modes per component")
     ap.add_argument("--inner", type=int, default=12,
                     help="mixed precision: inner FP32 GMRES steps per outer step (0: one FP32 "
                          "Kronecker apply per outer step)")
