@@ -36,6 +36,9 @@ METRIC = "GMRES time to 1e-8 rel. residual (factor build + solve), 1 GB300"
 FP64_PEAK_NOTE = ("FP64 peak = 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 1258.6 GFLOP/s "
                   "(FP64 pipe unit count and max clock; 1.19 TFLOP/s measured by a DFMA loop)")
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes (read + write) of one FP64 one-sided apply launch at n = 16 on the 64 x 64 mesh,
+# from the ncu capture summarised in profiles/k_apply_2d_g_k_dg_apply_2d_adv2d_64x64_n16.md
+TRAFFIC_APPLY_FP64_N16 = 308.18e6 + 3.45e6
 
 
 def workload(n: int, h: float = 1.0, solenoidal: bool = True):
@@ -314,9 +317,11 @@ def run_ours(args):
     # six n x n factors
     flops = 10.0 * n ** 3 * E
     achieved = flops / (apply["fp64"]["ms"] * 1e-3) / 1e9
-    roofline = {"kernel": "k_apply_2d<double>", "bound": "alu", "achieved": achieved,
+    roofline = {"kernel": "k_apply_2d_g<double,16,double>", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": None, "peak_note": FP64_PEAK_NOTE,
+                "traffic": (TRAFFIC_APPLY_FP64_N16 if (n == 16 and args.form == "one-sided")
+                            else None),
+                "traffic_unit": "bytes per launch", "peak_note": FP64_PEAK_NOTE,
                 "algorithmic": "10 n^3 flop per element (8 n^3 GEMM stages + 2 n^3 Sylvester)"}
 
     # end to end through the public API with host buffers (pinned), copies inside
