@@ -89,6 +89,14 @@ typedef struct {
   const double* amp;    /* [dim * n_modes] */
   const int32_t* kvec;  /* [dim * n_modes * dim] */
   const double* phase;  /* [dim * n_modes] */
+  /* Batch of block-diagonal systems (batch_rhs >= 1): nel[0] isolated elements (nel[1],
+   * nel[2] ignored), element e the cube of width h centred at centres[e * dim + .] in the
+   * unit domain (velocity at the absolute point, xi = x), each system the element's
+   * diagonal block alone (mass, volume and its own upwind face terms; no neighbour
+   * coupling), solved for batch_rhs right-hand sides at once.  Vectors are laid out
+   * [element][rhs][n^dim].  batch_rhs = 0: the periodic mesh described above. */
+  int32_t batch_rhs;
+  const double* centres;  /* host [nel[0] * dim], batch mode only */
 } tpp_problem;
 
 typedef struct {

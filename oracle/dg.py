@@ -278,3 +278,61 @@ class AdvectionDG:
                 ye += self.dt * h ** (d - 1) * (E.T @ (wf * flux)).reshape([n] * d)
             y[e] = ye
         return y.reshape(-1)
+
+
+class IsolatedElements:
+    """Block-diagonal systems of a batch of isolated elements (oracle form).
+
+    Element e is the cube [c_e - h/2, c_e + h/2]^d of the unit domain (centre
+    c_e); its system is the diagonal block S_e = M_e + dt (A_v + A_f)_e of the
+    DG discretisation above with every neighbour coupling dropped: mass,
+    volume, and the own-side upwind face terms dt h^(d-1) E_f^T diag(w_f
+    max(a.n, 0)) E_f on all 2d faces (Eq. jac-entries).  The velocity is the
+    field at the absolute point x (domain length 1).  Per element these are the
+    diagonal blocks of the periodic-mesh operator, which pins this class
+    against AdvectionDG.element_block in tests/test_oracle_dg.py.
+    """
+
+    def __init__(self, n: int, h: float, centres: np.ndarray, dt: float, vel):
+        self.centres = np.asarray(centres, dtype=np.float64)
+        self.dim = self.centres.shape[1]
+        assert vel.dim == self.dim
+        self.n, self.h, self.dt, self.vel = n, float(h), float(dt), vel
+        self.basis = Basis1D(n)
+        self.nloc = n ** self.dim
+        self.num_elem = self.centres.shape[0]
+
+    def _grid(self, lo: np.ndarray) -> np.ndarray:
+        """Points lo + h x at the tensor nodes, index a + n b (+ n^2 c), x fastest."""
+        x = self.basis.x
+        grids = np.meshgrid(*([x] * self.dim), indexing="ij")
+        pts = np.stack([lo[d] + self.h * grids[d] for d in range(self.dim)], axis=-1)
+        pts = np.transpose(pts, tuple(range(self.dim - 1, -1, -1)) + (self.dim,))
+        return pts.reshape(-1, self.dim)
+
+    def block(self, e: int) -> np.ndarray:
+        b, d, h = self.basis, self.dim, self.h
+        lo = self.centres[e] - 0.5 * h
+        a = velocity_eval(self.vel, self._grid(lo))
+        GtW, DtW = b.G.T @ b.W, b.D.T @ b.W
+        G = _kron_all([b.G] * d)
+        S = _kron_all([GtW] * d) @ np.diag(np.full(self.nloc, h ** d)) @ G
+        for comp in range(d):
+            mats = [DtW if t == comp else GtW for t in range(d - 1, -1, -1)]
+            S -= self.dt * _kron_all(mats) @ np.diag(h ** (d - 1) * a[:, comp]) @ G
+        # faces: tangential nodes x fastest, the normal coordinate at the face
+        x = b.x
+        wf = _kron_all([b.w] * (d - 1)) if d > 1 else np.ones(1)
+        for face in range(2 * d):
+            dn, side = divmod(face, 2)
+            tang = [t for t in range(d) if t != dn]
+            grids = np.meshgrid(*([x] * (d - 1)), indexing="ij") if d > 1 else []
+            pts = np.empty((grids[0].shape if d > 1 else ()) + (d,))
+            for t in range(d):
+                pts[..., t] = (lo[t] + side * h) if t == dn else lo[t] + h * grids[tang.index(t)]
+            pts = np.transpose(pts, tuple(range(d - 2, -1, -1)) + (d - 1,)).reshape(-1, d)
+            an = velocity_eval(self.vel, pts)[:, dn] * (1.0 if side == 1 else -1.0)
+            lvec = (b.l1 if side == 1 else b.l0)[None, :]
+            E = _kron_all([lvec if t == dn else b.G for t in range(d - 1, -1, -1)])
+            S += self.dt * h ** (d - 1) * E.T @ np.diag(wf * np.maximum(an, 0.0)) @ E
+        return S

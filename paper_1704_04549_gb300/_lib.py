@@ -21,7 +21,8 @@ class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("nel", C.c_int32 * 3),
                 ("h", C.c_double), ("dt", C.c_double), ("n_modes", C.c_int32),
                 ("a0", C.POINTER(C.c_double)), ("amp", C.POINTER(C.c_double)),
-                ("kvec", C.POINTER(C.c_int32)), ("phase", C.POINTER(C.c_double))]
+                ("kvec", C.POINTER(C.c_int32)), ("phase", C.POINTER(C.c_double)),
+                ("batch_rhs", C.c_int32), ("centres", C.POINTER(C.c_double))]
 
 
 class GmresOpts(C.Structure):

@@ -502,8 +502,9 @@ cudaError_t launch_apply_one(const tpp_ctx* c, const T* SA, const T* LBi, const 
                              const T* T1, const T* G, const VT* b, VT* x,
                              const int32_t* skip, cudaStream_t s) {
   const uint32_t* masks = c->p<uint32_t>(c->L.masks);
-  const int fdiv = (c->dim == 3) ? c->n : 1;
-  const int64_t nb = c->E * fdiv;
+  // 2D blocks: vector blocks (E R), or their z slices in 3D; factors per element
+  const int fdiv = ((c->dim == 3) ? c->n : 1) * c->R;
+  const int64_t nb = c->EB * ((c->dim == 3) ? c->n : 1);
   if (c->n <= 8)
     return launch_g<T, 8, VT>(c->n, nb, SA, LBi, Q1, T1, G, masks, b, x, skip, fdiv, s);
   if (c->n <= 16)
@@ -516,8 +517,8 @@ cudaError_t launch_apply_t(const tpp_ctx* c, const T* SA, const T* SB, const T* 
                            const T* T1, const T* T2, const VT* b, VT* x,
                            const int32_t* skip, cudaStream_t s) {
   const uint32_t* masks = c->p<uint32_t>(c->L.masks);
-  const int fdiv = (c->dim == 3) ? c->n : 1;
-  const int64_t nb = c->E * fdiv;                  // 2D blocks: elements, or z slices in 3D
+  const int fdiv = ((c->dim == 3) ? c->n : 1) * c->R;
+  const int64_t nb = c->EB * ((c->dim == 3) ? c->n : 1);   // 2D blocks (or z slices in 3D)
   if (c->n <= 8)
     return launch_w<T, 8, VT>(c->n, nb, SA, SB, Q1, Q2, T1, T2, masks, b, x, skip, fdiv, s);
   if (c->n <= 16)
@@ -606,7 +607,7 @@ cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
 template <typename T, int NZ, typename VT>
 __global__ void __launch_bounds__(128)
 k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const VT* __restrict__ b,
-          VT* __restrict__ x, const int32_t* skip) {
+          VT* __restrict__ x, const int32_t* skip, int R) {
   if (skip && *skip) return;
   __shared__ T az[4][NZ * NZ];
   const int nn = n * n, n3 = nn * n;
@@ -614,7 +615,7 @@ k_apply_z(int n, int64_t E, const T* __restrict__ Azi, const VT* __restrict__ b,
   const int64_t e = (int64_t)blockIdx.x * 4 + sub;
   if (e >= E) return;
   const int lane = threadIdx.x & 31;
-  for (int q = lane; q < nn; q += 32) az[sub][q] = Azi[e * nn + q];
+  for (int q = lane; q < nn; q += 32) az[sub][q] = Azi[(e / R) * nn + q];   // block e: element e / R
   __syncwarp();
   const VT* be = b + e * n3;
   VT* xe = x + e * n3;
@@ -639,15 +640,15 @@ template <typename VT>
 cudaError_t launch_apply_3d_t(const tpp_ctx* c, const VT* b, VT* x, int prec,
                               const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
-  const unsigned blocks = (unsigned)((c->E + 3) / 4);
+  const unsigned blocks = (unsigned)((c->EB + 3) / 4);
   if (prec == TPP_FP64) {
     const double* azi = c->p<double>(c->L.fAzi);
-    if (n <= 8) k_apply_z<double, 8, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
-    else k_apply_z<double, 16, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    if (n <= 8) k_apply_z<double, 8, VT><<<blocks, 128, 0, s>>>(n, c->EB, azi, b, x, skip, c->R);
+    else k_apply_z<double, 16, VT><<<blocks, 128, 0, s>>>(n, c->EB, azi, b, x, skip, c->R);
   } else {
     const float* azi = c->p<float>(c->L.f32) + f32_layout(n, c->E, 3, two_sided(c)).Azi;
-    if (n <= 8) k_apply_z<float, 8, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
-    else k_apply_z<float, 16, VT><<<blocks, 128, 0, s>>>(n, c->E, azi, b, x, skip);
+    if (n <= 8) k_apply_z<float, 8, VT><<<blocks, 128, 0, s>>>(n, c->EB, azi, b, x, skip, c->R);
+    else k_apply_z<float, 16, VT><<<blocks, 128, 0, s>>>(n, c->EB, azi, b, x, skip, c->R);
   }
   count_launch();
   cudaError_t err = cudaGetLastError();

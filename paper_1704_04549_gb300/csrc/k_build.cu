@@ -1063,8 +1063,10 @@ __global__ void __launch_bounds__(128) k_shift_inv_w(int n, int64_t E, const dou
 // Sec. 3.4.1 in the basis of k_struct_qr): Cx[c][j] = cx[c + n j] (volume,
 // c < n), max(a.n, 0) on the +x and -x faces (c = n, n + 1); Cy likewise for
 // y; Dg[i + n j] = h^2 w_i w_j (mass).
+// (batch mode: sxu / syu hold each isolated element's own upper faces; nx = E, ny = 1)
 __global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, const double* cx,
-                          const double* cy, const double* sx, const double* sy, double* kco) {
+                          const double* cy, const double* sx, const double* sy, double* kco,
+                          const double* sxu, const double* syu) {
   const int nc = n + 2, nn = n * n, per = 2 * nc * n + nn;
   const int64_t E = (int64_t)nx * ny;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E * per;
@@ -1078,11 +1080,13 @@ __global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, cons
       const int c = rem / n, j = rem % n;
       if (which == 0) {          // x-part, j = y index
         if (c < n) v = cx[e * nn + c + n * j];
-        else if (c == n) v = fmax(sx[((int64_t)ey * nx + (ex + 1) % nx) * n + j], 0.0);
+        else if (c == n)
+          v = fmax(sxu ? sxu[e * n + j] : sx[((int64_t)ey * nx + (ex + 1) % nx) * n + j], 0.0);
         else v = fmax(-sx[e * n + j], 0.0);
       } else {                   // y-part, j = x index
         if (c < n) v = cy[e * nn + j + n * c];
-        else if (c == n) v = fmax(sy[((int64_t)((ey + 1) % ny) * nx + ex) * n + j], 0.0);
+        else if (c == n)
+          v = fmax(syu ? syu[e * n + j] : sy[((int64_t)((ey + 1) % ny) * nx + ex) * n + j], 0.0);
         else v = fmax(-sy[e * n + j], 0.0);
       }
     } else {
@@ -1207,10 +1211,11 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s) {
 
 
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
-  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->prob.nel[0],
-                                    c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx),
-                                    c->p<double>(c->L.cy), c->p<double>(c->L.sx),
-                                    c->p<double>(c->L.sy), c->p<double>(c->L.kco));
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(
+      c->p<Tables>(c->L.tables), c->n, c->iso ? (int)c->E : c->prob.nel[0],
+      c->iso ? 1 : c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+      c->p<double>(c->L.sx), c->p<double>(c->L.sy), c->p<double>(c->L.kco),
+      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr);
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
@@ -1239,6 +1244,7 @@ struct Stage1Args {
   int64_t E;
   double h;
   const double *cx, *cy, *cz, *sx, *sy, *sz, *Zd, *Rz;
+  const double *sxu, *syu, *szu;   // batch mode: own upper faces (NULL on a mesh)
   double* scr;
   double* kco;
   double *Az, *Azi, *sigz;
@@ -1345,9 +1351,9 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
       vy = A.cy[e * n3 + a + n * c + nn * b];        // y-line (i = a, k = b)
       vz = A.cz[e * n3 + a + n * b + nn * c];        // z-line (i = a, j = b)
     } else if (c == n) {
-      vx = fmax(A.sx[eXp * nn + t], 0.0);
-      vy = fmax(A.sy[eYp * nn + t], 0.0);
-      vz = fmax(A.sz[eZp * nn + t], 0.0);
+      vx = fmax(A.sxu ? A.sxu[e * nn + t] : A.sx[eXp * nn + t], 0.0);
+      vy = fmax(A.syu ? A.syu[e * nn + t] : A.sy[eYp * nn + t], 0.0);
+      vz = fmax(A.szu ? A.szu[e * nn + t] : A.sz[eZp * nn + t], 0.0);
     } else {
       vx = fmax(-A.sx[e * nn + t], 0.0);
       vy = fmax(-A.sy[e * nn + t], 0.0);
@@ -1595,9 +1601,12 @@ cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s) {
   a.T = c->p<Tables>(c->L.tables);
   a.n = n;
   a.rz = c->rz;
-  a.nx = c->prob.nel[0];
-  a.ny = c->prob.nel[1];
-  a.nz = c->prob.nel[2];
+  a.nx = c->iso ? (int)c->E : c->prob.nel[0];
+  a.ny = c->iso ? 1 : c->prob.nel[1];
+  a.nz = c->iso ? 1 : c->prob.nel[2];
+  a.sxu = c->iso ? c->p<double>(c->L.sxu) : nullptr;
+  a.syu = c->iso ? c->p<double>(c->L.syu) : nullptr;
+  a.szu = c->iso ? c->p<double>(c->L.szu) : nullptr;
   a.Jmax = s1_jmax(n);
   a.E = c->E;
   a.h = c->prob.h;

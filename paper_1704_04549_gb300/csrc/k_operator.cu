@@ -224,10 +224,15 @@ __device__ __forceinline__ double vel_comp(const VelParams* V, int c, const doub
   return a;
 }
 
+// Mesh mode: element (ex, ey, ez) of the periodic mesh, coordinates normalised
+// by the domain length.  Batch mode (centres != NULL): element e is the cube of
+// width h centred at centres[e], coordinates absolute in the unit domain, and
+// the upper faces get their own values (sxu, syu, szu: no neighbour owns them).
 __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n, int nx, int ny,
                              int nz, double h, double dt, double* cx, double* cy, double* cz,
-                             double* sx, double* sy, double* sz) {
-  const int64_t E = (int64_t)nx * ny * nz;
+                             double* sx, double* sy, double* sz, const double* centres,
+                             double* sxu, double* syu, double* szu) {
+  const int64_t E = centres ? (int64_t)nx : (int64_t)nx * ny * nz;
   const int nloc = (dim == 2) ? n * n : n * n * n;
   const int nfl = (dim == 2) ? n : n * n;
   const int64_t tot_v = E * nloc, tot_f = E * nfl;
@@ -238,8 +243,18 @@ __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n
       const int64_t e = g / nloc;
       const int q = (int)(g % nloc);
       const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-      double X[3] = {(ex + T->x[i]) / nx, (ey + T->x[j]) / ny, (ez + T->x[k]) / nz};
+      double X[3];
+      if (centres) {
+        const double* ce = centres + e * dim;
+        X[0] = ce[0] + h * (T->x[i] - 0.5);
+        X[1] = ce[1] + h * (T->x[j] - 0.5);
+        X[2] = (dim == 3) ? ce[2] + h * (T->x[k] - 0.5) : 0.0;
+      } else {
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        X[0] = (ex + T->x[i]) / nx;
+        X[1] = (ey + T->x[j]) / ny;
+        X[2] = (ez + T->x[k]) / nz;
+      }
       double wq = T->w[i] * T->w[j];
       if (dim == 3) wq *= T->w[k];
       const double f = -dt * hf * wq;
@@ -251,9 +266,25 @@ __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n
       const int64_t e = gf / nfl;
       const int q = (int)(gf % nfl);
       const int t0 = q % n, t1 = q / n;   // tangential indices (first tangential fastest)
-      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
       const double wt = (dim == 2) ? T->w[t0] : T->w[t0] * T->w[t1];
       const double f = dt * hf * wt;
+      if (centres) {
+        const double* ce = centres + e * dim;
+        const double lo[3] = {ce[0] - 0.5 * h, ce[1] - 0.5 * h, dim == 3 ? ce[2] - 0.5 * h : 0.0};
+        const double tx = h * T->x[t0], ty = h * T->x[t1];
+        for (int up = 0; up < 2; ++up) {
+          double Xx[3] = {lo[0] + up * h, lo[1] + tx, lo[2] + ty};     // x-face: (y, z)
+          double Xy[3] = {lo[0] + tx, lo[1] + up * h, lo[2] + ty};     // y-face: (x, z)
+          (up ? sxu : sx)[gf] = f * vel_comp(V, 0, Xx, dim);
+          (up ? syu : sy)[gf] = f * vel_comp(V, 1, Xy, dim);
+          if (dim == 3) {
+            double Xz[3] = {lo[0] + tx, lo[1] + ty, lo[2] + up * h};   // z-face: (x, y)
+            (up ? szu : sz)[gf] = f * vel_comp(V, 2, Xz, dim);
+          }
+        }
+        continue;
+      }
+      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
       {   // lower x-face: tangential (y, z)
         double X[3] = {(double)ex / nx, (ey + T->x[t0]) / ny, (ez + T->x[t1]) / nz};
         sx[gf] = f * vel_comp(V, 0, X, dim);
@@ -271,12 +302,16 @@ __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n
 }
 
 cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s) {
-  const int nz = (c->dim == 3) ? c->prob.nel[2] : 1;
+  const int nz = (c->dim == 3 && !c->iso) ? c->prob.nel[2] : 1;
+  const bool d3 = c->dim == 3;
   k_precompute<<<152 * 8, 256, 0, s>>>(
-      c->p<VelParams>(c->L.vel), c->p<Tables>(c->L.tables), c->dim, c->n, c->prob.nel[0],
-      c->prob.nel[1], nz, c->prob.h, c->prob.dt, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-      c->dim == 3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.sx),
-      c->p<double>(c->L.sy), c->dim == 3 ? c->p<double>(c->L.sz) : nullptr);
+      c->p<VelParams>(c->L.vel), c->p<Tables>(c->L.tables), c->dim, c->n,
+      c->iso ? (int)c->E : c->prob.nel[0], c->iso ? 1 : c->prob.nel[1], nz, c->prob.h,
+      c->prob.dt, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+      d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.sx), c->p<double>(c->L.sy),
+      d3 ? c->p<double>(c->L.sz) : nullptr, c->iso ? c->p<double>(c->L.centres) : nullptr,
+      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
+      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -327,9 +362,9 @@ __global__ void k_traces(const Tables* T, int n, int64_t E, const VT* __restrict
 cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
                           const int32_t* skip) {
   if (c->dim == 2)
-    k_traces<2, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<2, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   else
-    k_traces<3, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<3, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   count_launch();
   return cudaGetLastError();
 }
@@ -337,9 +372,9 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
 cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
                               const int32_t* skip) {
   if (c->dim == 2)
-    k_traces<2, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<2, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   else
-    k_traces<3, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, x, tr, skip);
+    k_traces<3, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   count_launch();
   return cudaGetLastError();
 }
@@ -350,12 +385,16 @@ cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaS
 //          + l1_i F^R_j - l0_i F^L_j + l1_j F^T_i - l0_j F^B_i,
 // F^R_j = max(sR_j,0) u^-_R + min(sR_j,0) u^+_R (upwind flux through the +x
 // face, pre-scaled by dt h w_j), etc.
+// Batch mode (R >= 1 right-hand sides per isolated element, sxu / syu given):
+// block b holds rhs b % R of element b / R; only the own-side upwind face terms
+// (outflow through each face) remain.
 template <typename VT>
 __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
                               const VT* __restrict__ cx, const VT* __restrict__ cy,
                               const VT* __restrict__ sx, const VT* __restrict__ sy,
                               const VT* __restrict__ x, const VT* __restrict__ tr,
-                              VT* __restrict__ y, const int32_t* skip) {
+                              VT* __restrict__ y, const int32_t* skip, int R,
+                              const VT* __restrict__ sxu, const VT* __restrict__ syu) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
@@ -365,25 +404,33 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
   VT* py = px + nn;             // cy * x
   VT* fl = py + nn;             // 4n face fluxes: R, L, T, B
   VT* wl = fl + 4 * n;          // w, l0, l1
-  const int64_t e = blockIdx.x;
+  const int64_t blk = blockIdx.x;                 // vector block
+  const bool iso = sxu != nullptr;
+  const int64_t e = iso ? blk / R : blk;           // element (coefficients)
   const int ex = (int)(e % nx), ey = (int)(e / nx);
   const int64_t eR = ey * (int64_t)nx + (ex + 1) % nx, eL = ey * (int64_t)nx + (ex + nx - 1) % nx;
   const int64_t eT = ((ey + 1) % ny) * (int64_t)nx + ex, eB = ((ey + ny - 1) % ny) * (int64_t)nx + ex;
   const int tid = threadIdx.x;
-  const int64_t base = e * nn;
+  const int64_t base = blk * nn, cbase = e * nn;
   for (int q = tid; q < nn; q += blockDim.x) {
     Ds[q] = Tab<VT>::D(T)[q];
     const VT xv = x[base + q];
-    px[q] = cx[base + q] * xv;
-    py[q] = cy[base + q] * xv;
+    px[q] = cx[cbase + q] * xv;
+    py[q] = cy[cbase + q] * xv;
   }
   if (tid < n) {
     wl[tid] = Tab<VT>::w(T)[tid];
     wl[n + tid] = Tab<VT>::l0(T)[tid];
     wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
-    const VT* te = tr + e * 4 * n;
+    const VT* te = tr + blk * 4 * n;
     const int t = tid;
     const VT zero = (VT)0;
+    if (iso) {   // own traces only: outflow through each face
+      fl[t] = max(sxu[e * n + t], zero) * te[1 * n + t];
+      fl[n + t] = min(sx[e * n + t], zero) * te[0 * n + t];
+      fl[2 * n + t] = max(syu[e * n + t], zero) * te[3 * n + t];
+      fl[3 * n + t] = min(sy[e * n + t], zero) * te[2 * n + t];
+    } else {
     {   // +x face: outward normal +x, flux a_x evaluated on the face owned by eR
       const VT s = sx[eR * n + t];
       fl[t] = max(s, zero) * te[1 * n + t] + min(s, zero) * tr[eR * 4 * n + 0 * n + t];
@@ -399,6 +446,7 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
     {   // -y
       const VT s = sy[e * n + t];
       fl[3 * n + t] = max(s, zero) * tr[eB * 4 * n + 3 * n + t] + min(s, zero) * te[2 * n + t];
+    }
     }
   }
   __syncthreads();
@@ -424,7 +472,9 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
                               const VT* __restrict__ cz, const VT* __restrict__ sx,
                               const VT* __restrict__ sy, const VT* __restrict__ sz,
                               const VT* __restrict__ x, const VT* __restrict__ tr,
-                              VT* __restrict__ y, const int32_t* skip) {
+                              VT* __restrict__ y, const int32_t* skip, int R,
+                              const VT* __restrict__ sxu, const VT* __restrict__ syu,
+                              const VT* __restrict__ szu) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
@@ -435,7 +485,9 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
   VT* pz = py + n3;
   VT* fl = pz + n3;             // 6 n^2 fluxes: +x, -x, +y, -y, +z, -z
   VT* wl = fl + 6 * nn;         // w, l0, l1
-  const int64_t e = blockIdx.x;
+  const int64_t blk = blockIdx.x;                 // vector block
+  const bool iso = sxu != nullptr;
+  const int64_t e = iso ? blk / R : blk;           // element (coefficients)
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
   auto eid = [&](int a, int b, int c) -> int64_t {
     return ((int64_t)((c + nz) % nz) * ny + (b + ny) % ny) * nx + (a + nx) % nx;
@@ -444,21 +496,31 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
   const int64_t eYp = eid(ex, ey + 1, ez), eYm = eid(ex, ey - 1, ez);
   const int64_t eZp = eid(ex, ey, ez + 1), eZm = eid(ex, ey, ez - 1);
   const int tid = threadIdx.x;
-  const int64_t base = e * n3;
+  const int64_t base = blk * n3, cbase = e * n3;
   for (int q = tid; q < nn; q += blockDim.x) Ds[q] = Tab<VT>::D(T)[q];
   for (int q = tid; q < n3; q += blockDim.x) {
     const VT xv = x[base + q];
-    px[q] = cx[base + q] * xv;
-    py[q] = cy[base + q] * xv;
-    pz[q] = cz[base + q] * xv;
+    px[q] = cx[cbase + q] * xv;
+    py[q] = cy[cbase + q] * xv;
+    pz[q] = cz[cbase + q] * xv;
   }
   if (tid < n) {
     wl[tid] = Tab<VT>::w(T)[tid];
     wl[n + tid] = Tab<VT>::l0(T)[tid];
     wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
   }
-  const VT* te = tr + e * 6 * nn;
+  const VT* te = tr + blk * 6 * nn;
   const VT zero = (VT)0;
+  if (iso) {   // own traces only: outflow through each face
+    for (int q = tid; q < nn; q += blockDim.x) {
+      fl[0 * nn + q] = max(sxu[e * nn + q], zero) * te[1 * nn + q];
+      fl[1 * nn + q] = min(sx[e * nn + q], zero) * te[0 * nn + q];
+      fl[2 * nn + q] = max(syu[e * nn + q], zero) * te[3 * nn + q];
+      fl[3 * nn + q] = min(sy[e * nn + q], zero) * te[2 * nn + q];
+      fl[4 * nn + q] = max(szu[e * nn + q], zero) * te[5 * nn + q];
+      fl[5 * nn + q] = min(sz[e * nn + q], zero) * te[4 * nn + q];
+    }
+  } else
   for (int q = tid; q < nn; q += blockDim.x) {
     VT s;
     s = sx[eXp * nn + q];
@@ -492,17 +554,19 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
 
 template <typename VT>
 cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* cz,
-                              const VT* sx, const VT* sy, const VT* sz, const VT* x,
-                              const VT* tr, VT* y, const int32_t* skip, cudaStream_t s) {
+                              const VT* sx, const VT* sy, const VT* sz, const VT* sxu,
+                              const VT* syu, const VT* szu, const VT* x, const VT* tr, VT* y,
+                              const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
   if (c->dim == 2) {
     const int nn = n * n;
     const int threads = ((nn + 31) / 32) * 32;
     const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
     const double h = c->prob.h;
-    k_dg_apply_2d<VT><<<(unsigned)c->E, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], (VT)(h * h), cx, cy, sx,
-        sy, x, tr, y, skip);
+    k_dg_apply_2d<VT><<<(unsigned)c->EB, threads, smem, s>>>(
+        c->p<Tables>(c->L.tables), n, c->iso ? (int)c->E : c->prob.nel[0],
+        c->iso ? 1 : c->prob.nel[1], (VT)(h * h), cx, cy, sx, sy, x, tr, y, skip, c->R,
+        c->iso ? sxu : nullptr, c->iso ? syu : nullptr);
     count_launch();
     return cudaGetLastError();
   }
@@ -512,9 +576,11 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const double h = c->prob.h;
-  k_dg_apply_3d<VT><<<(unsigned)c->E, 256, smem, s>>>(
-      c->p<Tables>(c->L.tables), n, c->prob.nel[0], c->prob.nel[1], c->prob.nel[2],
-      (VT)(h * h * h), cx, cy, cz, sx, sy, sz, x, tr, y, skip);
+  k_dg_apply_3d<VT><<<(unsigned)c->EB, 256, smem, s>>>(
+      c->p<Tables>(c->L.tables), n, c->iso ? (int)c->E : c->prob.nel[0],
+      c->iso ? 1 : c->prob.nel[1], c->iso ? 1 : c->prob.nel[2], (VT)(h * h * h), cx, cy, cz, sx,
+      sy, sz, x, tr, y, skip, c->R, c->iso ? sxu : nullptr, c->iso ? syu : nullptr,
+      c->iso ? szu : nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -524,8 +590,9 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(
       c, c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
-      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr, x, tr,
-      y, skip, s);
+      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr,
+      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
+      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr, x, tr, y, skip, s);
 }
 
 // FP32 operator (the inner solves of the mixed-precision mode) on the float
@@ -533,18 +600,21 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
 cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
                                 const int32_t* skip, cudaStream_t s) {
   const float* f = c->p<float>(c->L.opf);
-  const OpF32Layout O = op_f32_layout(c->dim, c->N, c->E, c->n);
+  const OpF32Layout O = op_f32_layout(c);
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, d3 ? f + O.cz : nullptr, f + O.sx,
-                                  f + O.sy, d3 ? f + O.sz : nullptr, x, tr, y, skip, s);
+                                  f + O.sy, d3 ? f + O.sz : nullptr, f + O.sxu, f + O.syu,
+                                  f + O.szu, x, tr, y, skip, s);
 }
 
 // float copies of the operator coefficients (after k_precompute)
 __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz,
-                            const double* sx, const double* sy, const double* sz, float* out,
-                            OpF32Layout O, int dim) {
+                            const double* sx, const double* sy, const double* sz,
+                            const double* sxu, const double* syu, const double* szu, float* out,
+                            OpF32Layout O, int dim, int iso) {
   const int64_t tv = O.cy - O.cx, tf = O.sy - O.sx;
-  const int64_t total = (int64_t)dim * (tv + tf);
+  const int nface = iso ? 2 * dim : dim;
+  const int64_t total = (int64_t)dim * tv + nface * tf;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     double v;
@@ -556,22 +626,28 @@ __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz
       dst = (which == 0 ? O.cx : which == 1 ? O.cy : O.cz) + i;
     } else {
       const int64_t h = g - dim * tv;
-      const int which = (int)(h / tf);
+      const int which = (int)(h / tf);           // sx, sy, (sz,) then sxu, syu, (szu)
       const int64_t i = h % tf;
-      v = (which == 0 ? sx : which == 1 ? sy : sz)[i];
-      dst = (which == 0 ? O.sx : which == 1 ? O.sy : O.sz) + i;
+      const int dir = which % dim, up = which / dim;
+      const double* src = up ? (dir == 0 ? sxu : dir == 1 ? syu : szu)
+                             : (dir == 0 ? sx : dir == 1 ? sy : sz);
+      v = src[i];
+      dst = (up ? (dir == 0 ? O.sxu : dir == 1 ? O.syu : O.szu)
+                : (dir == 0 ? O.sx : dir == 1 ? O.sy : O.sz)) + i;
     }
     out[dst] = __double2float_rn(v);
   }
 }
 
 cudaError_t launch_op_to_f32(const tpp_ctx* c, cudaStream_t s) {
-  const OpF32Layout O = op_f32_layout(c->dim, c->N, c->E, c->n);
+  const OpF32Layout O = op_f32_layout(c);
   const bool d3 = c->dim == 3;
   k_op_to_f32<<<152 * 4, 256, 0, s>>>(
       c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
       c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr,
-      c->p<float>(c->L.opf), O, c->dim);
+      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
+      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr, c->p<float>(c->L.opf), O, c->dim,
+      c->iso ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }

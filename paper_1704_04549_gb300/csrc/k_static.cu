@@ -59,8 +59,8 @@ extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x,
     tpp::set_error("x and y must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
   }
-  if (c->dim != 2) {
-    tpp::set_error("dg_apply_sumfact_static supports 2D contexts only");
+  if (c->dim != 2 || c->iso) {
+    tpp::set_error("dg_apply_sumfact_static supports 2D meshes only");
     return TPP_ERR_UNSUPPORTED;
   }
   const size_t need = (size_t)c->E * 4 * (size_t)c->n;

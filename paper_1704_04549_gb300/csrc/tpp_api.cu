@@ -98,16 +98,34 @@ const char* validate(const tpp_problem* p, int32_t max_restart) {
   if (!p->a0) return "a0 is NULL";
   if (p->n_modes > 0 && (!p->amp || !p->kvec || !p->phase)) return "Fourier arrays are NULL";
   if (max_restart < 1 || max_restart > kMaxRestart) return "max_restart must be in [1, 63]";
+  if (p->batch_rhs < 0) return "batch_rhs must be >= 0";
+  if (p->batch_rhs > 0 && !p->centres) return "centres is NULL (batch mode)";
   return nullptr;
+}
+
+// element count (E), right-hand sides per element (R) and vector blocks (E R)
+void problem_counts(const tpp_problem* p, int64_t* E, int32_t* R) {
+  if (p->batch_rhs > 0) {
+    *E = p->nel[0];
+    *R = p->batch_rhs;
+  } else {
+    *E = (int64_t)p->nel[0] * p->nel[1] * (p->dim == 3 ? p->nel[2] : 1);
+    *R = 1;
+  }
 }
 
 Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t features,
                       int* rz_out) {
   const int n = p->n, d = p->dim;
-  const int64_t E = (int64_t)p->nel[0] * p->nel[1] * (d == 3 ? p->nel[2] : 1);
+  int64_t E = 0;
+  int32_t R = 1;
+  problem_counts(p, &E, &R);
+  const bool iso = p->batch_rhs > 0;
+  const int64_t EB = E * R;
   const int64_t nloc = (d == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t nfl = (d == 2) ? n : (int64_t)n * n;
-  const int64_t N = E * nloc;
+  const int64_t N = EB * nloc;
+  const int64_t Nc = E * nloc;
   const int nc = n + 2, Ro = n * n - n;
   const int rz = Ro < nc ? Ro : nc;
   if (rz_out) *rz_out = rz;
@@ -129,13 +147,17 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.qo = take((size_t)Ro * nc * 8);
   L.qr_work = take((size_t)Ro * nc * 8);
   L.qr_tau = take((size_t)nc * 8);
-  L.cx = take((size_t)N * 8);
-  L.cy = take((size_t)N * 8);
-  L.cz = (d == 3) ? take((size_t)N * 8) : 0;
+  L.cx = take((size_t)Nc * 8);
+  L.cy = take((size_t)Nc * 8);
+  L.cz = (d == 3) ? take((size_t)Nc * 8) : 0;
   L.sx = take((size_t)E * nfl * 8);
   L.sy = take((size_t)E * nfl * 8);
   L.sz = (d == 3) ? take((size_t)E * nfl * 8) : 0;
-  L.traces = take((size_t)E * 2 * d * nfl * 8);
+  L.sxu = iso ? take((size_t)E * nfl * 8) : 0;
+  L.syu = iso ? take((size_t)E * nfl * 8) : 0;
+  L.szu = (iso && d == 3) ? take((size_t)E * nfl * 8) : 0;
+  L.centres = iso ? take((size_t)E * d * 8) : 0;
+  L.traces = take((size_t)EB * 2 * d * nfl * 8);
   const size_t fsz = (size_t)E * n * n * 8;
   L.sigma = take((size_t)E * 2 * 8);
   L.fA1 = take(fsz);
@@ -170,7 +192,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.fG = two ? 0 : take(fsz * 2 * n);
   L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
   if (features & TPP_FEAT_MIXED) {      // FP32 operator and inner GMRES
-    L.opf = take(op_f32_layout(d, N, E, n).total * 4);
+    L.opf = take(op_f32_layout(d, Nc, E, n, EB, iso).total * 4);
     L.gstate_in = take(sizeof(GmresState));
     L.gbuf_in = take(gbuf_layout(m).total * sizeof(double));
     L.vi = take((size_t)(m + 1) * N * 4);
@@ -255,8 +277,8 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     set_error(why);
     return TPP_ERR_INVALID_ARG;
   }
-  if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
-    set_error("exact block Jacobi is implemented for 2D problems only");
+  if ((prob->dim == 3 || prob->batch_rhs > 0) && (features & TPP_FEAT_BLOCK_JACOBI)) {
+    set_error("exact block Jacobi is implemented for 2D meshes only");
     return TPP_ERR_UNSUPPORTED;
   }
   int rz = 0;
@@ -279,11 +301,14 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   c->prob.amp = nullptr;
   c->prob.kvec = nullptr;
   c->prob.phase = nullptr;
+  c->prob.centres = nullptr;
   c->n = prob->n;
   c->dim = prob->dim;
-  c->E = (int64_t)prob->nel[0] * prob->nel[1] * (prob->dim == 3 ? prob->nel[2] : 1);
+  problem_counts(prob, &c->E, &c->R);
+  c->iso = prob->batch_rhs > 0;
+  c->EB = c->E * c->R;
   c->nloc = (prob->dim == 2) ? prob->n * prob->n : prob->n * prob->n * prob->n;
-  c->N = c->E * c->nloc;
+  c->N = c->EB * c->nloc;
   c->max_restart = max_restart;
   c->features = features;
   c->rz = rz;
@@ -318,6 +343,11 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     if (L.gstate_in &&
         (rc = cuda_check(cudaMemsetAsync(c->ws + L.gstate_in, 0, sizeof(GmresState), s),
                          "memset")) != TPP_OK)
+      break;
+    if (c->iso &&
+        (rc = cuda_check(cudaMemcpyAsync(c->ws + L.centres, prob->centres,
+                                         (size_t)c->E * c->dim * sizeof(double),
+                                         cudaMemcpyHostToDevice, s), "copy centres")) != TPP_OK)
       break;
     if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
     if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
@@ -448,7 +478,7 @@ tpp_status dg_apply_sumfact_f32(const tpp_ctx* c, const float* x, float* y, void
     return TPP_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* trf = c->p<float>(c->L.opf) + op_f32_layout(c->dim, c->N, c->E, c->n).tr;
+  float* trf = c->p<float>(c->L.opf) + op_f32_layout(c).tr;
   TPP_TRY_CUDA(launch_traces_f32(c, x, trf, s, nullptr), "k_traces<float>");
   TPP_TRY_CUDA(launch_dg_apply_f32(c, x, trf, y, nullptr, s), "k_dg_apply<float>");
   return TPP_OK;
@@ -587,7 +617,7 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     const int32_t* din = &sti->done;
     float* Vi = c->p<float>(c->L.vi);
     float* tf = c->p<float>(c->L.tf);
-    float* trf = c->p<float>(c->L.opf) + op_f32_layout(c->dim, N, c->E, c->n).tr;
+    float* trf = c->p<float>(c->L.opf) + op_f32_layout(c).tr;
     TPP_TRY_CUDA(vec_to_float(v, Vi, N, done, s), "inner v0");
     TPP_TRY_CUDA(gmres_cycle_init(sti, g0, 1.0, kin, 1.0, opts->inner_rtol, done, s),
                  "inner init");

@@ -89,6 +89,7 @@ struct Layout {
   size_t vel, tables, status, gstate;
   size_t zd, rz, qo, qr_work, qr_tau;   // structure basis of the rearranged block (2D)
   size_t cx, cy, cz, sx, sy, sz;        // flux Jacobians (scaled) at nodes / faces
+  size_t sxu, syu, szu, centres;       // batch mode: upper-face values, element centres
   size_t traces;
   size_t sigma, fA1, fB1, fA2, fB2;
   size_t fSA, fSB, fQ1, fQ2, fT1, fT2, fSC;  // fSC: 3D A1^-1 factor
@@ -111,6 +112,9 @@ struct tpp_ctx {
   tpp_problem prob;        // copy (host pointers cleared)
   int32_t n, dim;
   int64_t E, N;            // elements, DOFs
+  int32_t R;               // right-hand sides per element (1 on a mesh)
+  bool iso;                // batch of isolated elements (block-diagonal systems)
+  int64_t EB;              // vector blocks: E * R
   int32_t nloc;            // n^dim
   int32_t max_restart;
   uint32_t features;
@@ -212,21 +216,28 @@ inline F32Layout f32_layout(int n, int64_t E, int dim, bool two) {
 // floats from Layout::opf): volume coefficients (N each), lower-face
 // coefficients (E n^(d-1) each), face traces (E 2d n^(d-1))
 struct OpF32Layout {
-  size_t cx, cy, cz, sx, sy, sz, tr, total;
+  size_t cx, cy, cz, sx, sy, sz, sxu, syu, szu, tr, total;
 };
-inline OpF32Layout op_f32_layout(int dim, int64_t N, int64_t E, int n) {
+// Nc = E n^dim coefficient values per direction; EB vector blocks (traces)
+inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t EB, bool iso) {
   const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;
   OpF32Layout L{};
   size_t o = 0;
-  L.cx = o; o += N;
-  L.cy = o; o += N;
-  L.cz = o; if (dim == 3) o += N;
+  L.cx = o; o += Nc;
+  L.cy = o; o += Nc;
+  L.cz = o; if (dim == 3) o += Nc;
   L.sx = o; o += E * nfl;
   L.sy = o; o += E * nfl;
   L.sz = o; if (dim == 3) o += E * nfl;
-  L.tr = o; o += E * 2 * dim * nfl;
+  L.sxu = o; if (iso) o += E * nfl;
+  L.syu = o; if (iso) o += E * nfl;
+  L.szu = o; if (iso && dim == 3) o += E * nfl;
+  L.tr = o; o += EB * 2 * dim * nfl;
   L.total = o;
   return L;
+}
+inline OpF32Layout op_f32_layout(const tpp_ctx* c) {
+  return op_f32_layout(c->dim, c->E * c->nloc, c->E, c->n, c->EB, c->iso);
 }
 
 // the paper's two-sided Schur form (both factor products reduced) instead of

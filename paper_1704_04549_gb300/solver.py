@@ -27,16 +27,24 @@ class Context:
 
     velocity: object with attributes dim, a0 [dim], amp [dim, M], kvec [dim, M, dim],
     phase [dim, M] describing a_c(x) = a0_c + sum_m amp cos(2 pi k . x + phase).
+
+    Batch mode (batch_rhs >= 1, centres [E, dim]): E isolated elements of width h
+    with block-diagonal systems, batch_rhs right-hand sides each; nel is ignored
+    and vectors are laid out [element][rhs][n^dim].
     """
 
     def __init__(self, dim: int, n: int, nel, h: float, dt: float, velocity,
                  max_restart: int = 30, features: int = 0, device: str = "cuda:0",
-                 stream=None):
+                 stream=None, batch_rhs: int = 0, centres=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
         self.lib = L.load()
         self.device = torch.device(device)
         self.dim, self.n, self.dt, self.h = dim, n, float(dt), float(h)
+        self.batch_rhs = int(batch_rhs)
+        if self.batch_rhs > 0:
+            self._centres = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, dim)
+            nel = (self._centres.shape[0],)
         nel = tuple(int(v) for v in nel) + (1,) * (3 - len(nel))
         self.nel = nel[:dim]
         self._a0 = np.ascontiguousarray(velocity.a0, dtype=np.float64)
@@ -53,6 +61,9 @@ class Context:
         P.amp = self._amp.ctypes.data_as(C.POINTER(C.c_double))
         P.kvec = self._kvec.ctypes.data_as(C.POINTER(C.c_int32))
         P.phase = self._phase.ctypes.data_as(C.POINTER(C.c_double))
+        P.batch_rhs = self.batch_rhs
+        if self.batch_rhs > 0:
+            P.centres = self._centres.ctypes.data_as(C.POINTER(C.c_double))
         self._prob = P
         nbytes = self.lib.tpp_workspace_bytes(C.byref(P), max_restart, features)
         if nbytes == 0:

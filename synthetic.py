@@ -129,3 +129,33 @@ def advection_3d_fourier(n: int = 11, nel: int = 16, dt: float = 0.05,
     """16^3 periodic unit-cube hexes, n = 11, random-Fourier velocity, dt = 0.05."""
     return Workload(f"adv3d-fourier-{nel}^3-n{n}", 3, n, (nel, nel, nel), dt,
                     fourier_velocity(vel_seed, 3), rhs_seed=rhs_seed)
+
+
+@dataclass
+class DegreeGroup:
+    """Elements of one (dimension, n) group of a mixed-degree batch."""
+    dim: int
+    n: int
+    centres: np.ndarray        # [E_g, dim], uniform in the unit cube
+    ids: np.ndarray            # positions of these elements in the whole batch
+    rhs_seed: int              # b ~ N(0, 1) of shape [E_g][R][n^dim] from this seed
+
+
+def mixed_degree_batch(seed: int = 1709, e2d: int = 20000, e3d: int = 2000,
+                       p2d=(4, 30), p3d=(3, 12)):
+    """Mixed-degree batch of isolated elements: degrees p ~ U{p2d} (2D) and U{p3d}
+    (3D), element centres uniform in [0, 1]^d, grouped by (dim, n = p + 1) in
+    increasing n.  Returns the list of groups (element ids refer to the draw order,
+    2D elements first)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p2 = rng.integers(p2d[0], p2d[1] + 1, size=e2d)
+    c2 = rng.random((e2d, 2))
+    p3 = rng.integers(p3d[0], p3d[1] + 1, size=e3d)
+    c3 = rng.random((e3d, 3))
+    groups = []
+    for dim, ps, cs, off in ((2, p2, c2, 0), (3, p3, c3, e2d)):
+        for p in np.unique(ps):
+            sel = np.nonzero(ps == p)[0]
+            groups.append(DegreeGroup(dim, int(p) + 1, cs[sel], sel + off,
+                                      rhs_seed=seed * 1000 + dim * 100 + int(p)))
+    return groups

@@ -102,3 +102,20 @@ def test_periodic_face_points_agree():
             nb = dg.mesh.neighbor(e, face)
             opp = face ^ 1
             assert np.array_equal(dg.face_points(e, face), dg.face_points(nb, opp))
+
+
+@pytest.mark.parametrize("dim,n,nel", [(2, 3, (4, 4)), (2, 6, (5, 5)), (3, 3, (3, 3, 3))])
+def test_isolated_blocks_are_mesh_diagonal_blocks(dim, n, nel):
+    """Isolated elements at the cell centres of a mesh of the unit cube have the
+    mesh operator's diagonal blocks (neighbour couplings dropped)."""
+    from oracle.dg import IsolatedElements
+    mesh = PeriodicMesh(nel)                       # unit cube, h = 1 / N
+    h = mesh.h
+    vel = synthetic.fourier_velocity(11, dim)
+    dg = AdvectionDG(mesh, n, 0.07, vel)
+    centres = np.array([[(c + 0.5) * h for c in mesh.coords(e)] for e in range(mesh.num_elem)])
+    iso = IsolatedElements(n, h, centres, 0.07, vel)
+    for e in range(mesh.num_elem):
+        B = iso.block(e)
+        ref = dg.element_block(e)
+        assert np.abs(B - ref).max() <= 1e-13 * np.abs(ref).max()
