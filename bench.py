@@ -463,6 +463,59 @@ def run_3d(args):
     return 0
 
 
+def run_batch(args):
+    """The mixed-degree batch (20,000 2D elements, p ~ U{4..30}, and 2,000 3D elements,
+    p ~ U{3..12}; isolated unit elements (h = 1; --h-reading domain: h = 1/64) covering 1/64 of
+    the velocity field's unit domain, centres uniform, random-Fourier velocity, dt = 0.05, 64
+    right-hand sides ~ N(0, 1) per element; each
+    element's block-diagonal system solved to 1e-8).  One context per degree group, groups
+    in sequence; value = the sum over groups of the device time of one step (factor build
+    + solve of all the group's systems)."""
+    import torch
+    from paper_1704_04549_gb300 import batch as B
+    from paper_1704_04549_gb300 import _lib
+    lib = _lib.load()
+    groups = synthetic.mixed_degree_batch(e2d=int(round(20000 * args.batch_scale)),
+                                          e3d=int(round(2000 * args.batch_scale)))
+    vel = {2: synthetic.fourier_velocity(1709, 2), 3: synthetic.fourier_velocity(1709, 3)}
+    h_el = 1.0 / 64 if args.h_reading == "domain" else 1.0   # element width (scales the block)
+    out = {}
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(0) as clk:
+        for mode, kin in (("fp64", 0), ("mixed", args.inner)):
+            rows = [B.solve_group(g, 64, h_el, 0.05, vel[g.dim], span=1.0 / 64,
+                                  inner_iters=kin, max_iters=args.max_iters, steps=args.steps,
+                                  warmup=args.warmup) for g in groups]
+            out[mode] = rows
+    launches = lib.tpp_kernel_launch_count() - l0
+    tot = {m: sum(r["ms_per_step"] for r in rows) for m, rows in out.items()}
+    dofs = sum(r["dofs"] for r in out["fp64"])
+    line = {
+        "metric": "mixed-degree batch: time to solve every block system to 1e-8 "
+                  "(factor build + solve), 1 GB300",
+        "value": tot["fp64"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "mixed-degree batch, %d 2D elements p~U{4..30} + %d 3D elements "
+                               "p~U{3..12}, h=%g, span 1/64, dt=0.05, 64 RHS each, seed 1709"
+                               % (sum(len(g.ids) for g in groups if g.dim == 2),
+                                  sum(len(g.ids) for g in groups if g.dim == 3), h_el),
+                   "groups": len(groups), "dof_rhs": dofs,
+                   "scale": args.batch_scale},
+        "mixed": {"ms": tot["mixed"], "inner_iters_per_outer": args.inner,
+                  "all_converged": all(r["converged"] for r in out["mixed"])},
+        "all_converged": all(r["converged"] for r in out["fp64"]),
+        "dof_rhs_per_s": {m: dofs / (t * 1e-3) for m, t in tot.items()},
+        "groups": {m: [{k: r[k] for k in ("dim", "n", "elements", "ms_per_step", "iters",
+                                          "inner_iters", "converged")} for r in rows]
+                   for m, rows in out.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_kernels(args):
     """Kernel-only pass for profilers: one factor build, then a few launches of
     each hot-path kernel on the same workload (no GMRES loop)."""
@@ -521,7 +574,9 @@ def main():
     ap.add_argument("--form", choices=["one-sided", "two-sided"], default="one-sided",
                     help="apply form: one-sided (shifted inverses, default) or the paper's "
                          "two-sided Schur / quasi-triangular Sylvester form")
-    ap.add_argument("--workload", choices=["adv2d", "adv3d"], default="adv2d",
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="batch workload: fraction of the 20,000 + 2,000 elements")
+    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch"], default="adv2d",
                     help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -530,6 +585,8 @@ def main():
         return run_kernels(args)
     if args.workload == "adv3d":
         return run_3d(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

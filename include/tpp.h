@@ -97,6 +97,9 @@ typedef struct {
    * [element][rhs][n^dim].  batch_rhs = 0: the periodic mesh described above. */
   int32_t batch_rhs;
   const double* centres;  /* host [nel[0] * dim], batch mode only */
+  double batch_span;      /* batch mode: width of each element in the coordinates of the
+                             velocity field (the unit domain); 0 means h.  The element's
+                             integrals scale with its physical width h. */
 } tpp_problem;
 
 typedef struct {

@@ -288,31 +288,35 @@ class IsolatedElements:
     DG discretisation above with every neighbour coupling dropped: mass,
     volume, and the own-side upwind face terms dt h^(d-1) E_f^T diag(w_f
     max(a.n, 0)) E_f on all 2d faces (Eq. jac-entries).  The velocity is the
-    field at the absolute point x (domain length 1).  Per element these are the
-    diagonal blocks of the periodic-mesh operator, which pins this class
-    against AdvectionDG.element_block in tests/test_oracle_dg.py.
+    field at the point c_e + span (xi - 1/2) of the unit domain (span = h unless
+    given): the element's integrals scale with its width h, the field is sampled
+    over span.  Per element these are the diagonal blocks of the periodic-mesh
+    operator (span = 1/N), which pins this class against
+    AdvectionDG.element_block in tests/test_oracle_dg.py.
     """
 
-    def __init__(self, n: int, h: float, centres: np.ndarray, dt: float, vel):
+    def __init__(self, n: int, h: float, centres: np.ndarray, dt: float, vel,
+                 span: float | None = None):
         self.centres = np.asarray(centres, dtype=np.float64)
         self.dim = self.centres.shape[1]
         assert vel.dim == self.dim
         self.n, self.h, self.dt, self.vel = n, float(h), float(dt), vel
+        self.span = float(h if span is None else span)
         self.basis = Basis1D(n)
         self.nloc = n ** self.dim
         self.num_elem = self.centres.shape[0]
 
     def _grid(self, lo: np.ndarray) -> np.ndarray:
-        """Points lo + h x at the tensor nodes, index a + n b (+ n^2 c), x fastest."""
+        """Points lo + span x at the tensor nodes, index a + n b (+ n^2 c), x fastest."""
         x = self.basis.x
         grids = np.meshgrid(*([x] * self.dim), indexing="ij")
-        pts = np.stack([lo[d] + self.h * grids[d] for d in range(self.dim)], axis=-1)
+        pts = np.stack([lo[d] + self.span * grids[d] for d in range(self.dim)], axis=-1)
         pts = np.transpose(pts, tuple(range(self.dim - 1, -1, -1)) + (self.dim,))
         return pts.reshape(-1, self.dim)
 
     def block(self, e: int) -> np.ndarray:
-        b, d, h = self.basis, self.dim, self.h
-        lo = self.centres[e] - 0.5 * h
+        b, d, h, sp = self.basis, self.dim, self.h, self.span
+        lo = self.centres[e] - 0.5 * sp
         a = velocity_eval(self.vel, self._grid(lo))
         GtW, DtW = b.G.T @ b.W, b.D.T @ b.W
         G = _kron_all([b.G] * d)
@@ -329,7 +333,7 @@ class IsolatedElements:
             grids = np.meshgrid(*([x] * (d - 1)), indexing="ij") if d > 1 else []
             pts = np.empty((grids[0].shape if d > 1 else ()) + (d,))
             for t in range(d):
-                pts[..., t] = (lo[t] + side * h) if t == dn else lo[t] + h * grids[tang.index(t)]
+                pts[..., t] = (lo[t] + side * sp) if t == dn else lo[t] + sp * grids[tang.index(t)]
             pts = np.transpose(pts, tuple(range(d - 2, -1, -1)) + (d - 1,)).reshape(-1, d)
             an = velocity_eval(self.vel, pts)[:, dn] * (1.0 if side == 1 else -1.0)
             lvec = (b.l1 if side == 1 else b.l0)[None, :]

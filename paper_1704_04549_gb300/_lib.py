@@ -22,7 +22,8 @@ class Problem(C.Structure):
                 ("h", C.c_double), ("dt", C.c_double), ("n_modes", C.c_int32),
                 ("a0", C.POINTER(C.c_double)), ("amp", C.POINTER(C.c_double)),
                 ("kvec", C.POINTER(C.c_int32)), ("phase", C.POINTER(C.c_double)),
-                ("batch_rhs", C.c_int32), ("centres", C.POINTER(C.c_double))]
+                ("batch_rhs", C.c_int32), ("centres", C.POINTER(C.c_double)),
+                ("batch_span", C.c_double)]
 
 
 class GmresOpts(C.Structure):

@@ -231,7 +231,7 @@ __device__ __forceinline__ double vel_comp(const VelParams* V, int c, const doub
 __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n, int nx, int ny,
                              int nz, double h, double dt, double* cx, double* cy, double* cz,
                              double* sx, double* sy, double* sz, const double* centres,
-                             double* sxu, double* syu, double* szu) {
+                             double* sxu, double* syu, double* szu, double span) {
   const int64_t E = centres ? (int64_t)nx : (int64_t)nx * ny * nz;
   const int nloc = (dim == 2) ? n * n : n * n * n;
   const int nfl = (dim == 2) ? n : n * n;
@@ -246,9 +246,9 @@ __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n
       double X[3];
       if (centres) {
         const double* ce = centres + e * dim;
-        X[0] = ce[0] + h * (T->x[i] - 0.5);
-        X[1] = ce[1] + h * (T->x[j] - 0.5);
-        X[2] = (dim == 3) ? ce[2] + h * (T->x[k] - 0.5) : 0.0;
+        X[0] = ce[0] + span * (T->x[i] - 0.5);
+        X[1] = ce[1] + span * (T->x[j] - 0.5);
+        X[2] = (dim == 3) ? ce[2] + span * (T->x[k] - 0.5) : 0.0;
       } else {
         const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
         X[0] = (ex + T->x[i]) / nx;
@@ -270,15 +270,16 @@ __global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n
       const double f = dt * hf * wt;
       if (centres) {
         const double* ce = centres + e * dim;
-        const double lo[3] = {ce[0] - 0.5 * h, ce[1] - 0.5 * h, dim == 3 ? ce[2] - 0.5 * h : 0.0};
-        const double tx = h * T->x[t0], ty = h * T->x[t1];
+        const double lo[3] = {ce[0] - 0.5 * span, ce[1] - 0.5 * span,
+                              dim == 3 ? ce[2] - 0.5 * span : 0.0};
+        const double tx = span * T->x[t0], ty = span * T->x[t1];
         for (int up = 0; up < 2; ++up) {
-          double Xx[3] = {lo[0] + up * h, lo[1] + tx, lo[2] + ty};     // x-face: (y, z)
-          double Xy[3] = {lo[0] + tx, lo[1] + up * h, lo[2] + ty};     // y-face: (x, z)
+          double Xx[3] = {lo[0] + up * span, lo[1] + tx, lo[2] + ty};  // x-face: (y, z)
+          double Xy[3] = {lo[0] + tx, lo[1] + up * span, lo[2] + ty};  // y-face: (x, z)
           (up ? sxu : sx)[gf] = f * vel_comp(V, 0, Xx, dim);
           (up ? syu : sy)[gf] = f * vel_comp(V, 1, Xy, dim);
           if (dim == 3) {
-            double Xz[3] = {lo[0] + tx, lo[1] + ty, lo[2] + up * h};   // z-face: (x, y)
+            double Xz[3] = {lo[0] + tx, lo[1] + ty, lo[2] + up * span};   // z-face: (x, y)
             (up ? szu : sz)[gf] = f * vel_comp(V, 2, Xz, dim);
           }
         }
@@ -311,7 +312,8 @@ cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s) {
       d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.sx), c->p<double>(c->L.sy),
       d3 ? c->p<double>(c->L.sz) : nullptr, c->iso ? c->p<double>(c->L.centres) : nullptr,
       c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
-      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr);
+      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr,
+      c->prob.batch_span > 0.0 ? c->prob.batch_span : c->prob.h);
   count_launch();
   return cudaGetLastError();
 }

@@ -100,6 +100,7 @@ const char* validate(const tpp_problem* p, int32_t max_restart) {
   if (max_restart < 1 || max_restart > kMaxRestart) return "max_restart must be in [1, 63]";
   if (p->batch_rhs < 0) return "batch_rhs must be >= 0";
   if (p->batch_rhs > 0 && !p->centres) return "centres is NULL (batch mode)";
+  if (!(p->batch_span >= 0.0) || !std::isfinite(p->batch_span)) return "batch_span must be >= 0";
   return nullptr;
 }
 

@@ -35,7 +35,7 @@ class Context:
 
     def __init__(self, dim: int, n: int, nel, h: float, dt: float, velocity,
                  max_restart: int = 30, features: int = 0, device: str = "cuda:0",
-                 stream=None, batch_rhs: int = 0, centres=None):
+                 stream=None, batch_rhs: int = 0, centres=None, batch_span: float = 0.0):
         if not torch.cuda.is_available():
             raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
         self.lib = L.load()
@@ -62,6 +62,7 @@ class Context:
         P.kvec = self._kvec.ctypes.data_as(C.POINTER(C.c_int32))
         P.phase = self._phase.ctypes.data_as(C.POINTER(C.c_double))
         P.batch_rhs = self.batch_rhs
+        P.batch_span = float(batch_span)
         if self.batch_rhs > 0:
             P.centres = self._centres.ctypes.data_as(C.POINTER(C.c_double))
         self._prob = P

@@ -18,22 +18,25 @@ pytestmark = pytest.mark.gpu
 H, DT = 1.0 / 64, 0.05
 
 
-def _batch(dim, n, E, R, seed=5):
+def _batch(dim, n, E, R, seed=5, h=H, span=H):
     from paper_1704_04549_gb300 import Context
     rng = np.random.Generator(np.random.PCG64(seed))
     centres = rng.random((E, dim))
     vel = synthetic.fourier_velocity(1709, dim)
-    ctx = Context(dim, n, (E,), H, DT, vel, features=TPP_FEAT_MIXED, device=DEV,
-                  batch_rhs=R, centres=centres)
-    return ctx, IsolatedElements(n, H, centres, DT, vel)
+    ctx = Context(dim, n, (E,), h, DT, vel, features=TPP_FEAT_MIXED, device=DEV,
+                  batch_rhs=R, centres=centres, batch_span=span)
+    return ctx, IsolatedElements(n, h, centres, DT, vel, span=span)
 
 
-CASES = [(2, 1, 3, 2), (2, 5, 7, 3), (2, 16, 4, 2), (2, 31, 2, 2), (3, 3, 5, 2), (3, 6, 3, 3)]
+# (dim, n, elements, right-hand sides, element width); h = 1: unit elements sampling
+# 1/64 of the field (the batch workload's reading), h = 1/64: elements of the unit domain
+CASES = [(2, 1, 3, 2, H), (2, 5, 7, 3, H), (2, 16, 4, 2, H), (2, 31, 2, 2, H), (3, 3, 5, 2, H),
+         (3, 6, 3, 3, H), (2, 16, 5, 2, 1.0), (3, 11, 2, 2, 1.0)]
 
 
-@pytest.mark.parametrize("dim,n,E,R", CASES)
-def test_batch_operator_matches_isolated_blocks(dim, n, E, R):
-    ctx, iso = _batch(dim, n, E, R)
+@pytest.mark.parametrize("dim,n,E,R,h", CASES)
+def test_batch_operator_matches_isolated_blocks(dim, n, E, R, h):
+    ctx, iso = _batch(dim, n, E, R, h=h)
     nl = iso.nloc
     x = synthetic.rhs(3, E * R * nl)
     y = to_host(ctx.dg_apply_sumfact(to_dev(x))).reshape(E, R, nl)
@@ -44,9 +47,9 @@ def test_batch_operator_matches_isolated_blocks(dim, n, E, R):
             assert rel(y[e, r], S @ X[e, r]) <= 1e-12
 
 
-@pytest.mark.parametrize("dim,n,E,R", CASES)
-def test_batch_factors_and_apply_match_oracle(dim, n, E, R):
-    ctx, iso = _batch(dim, n, E, R)
+@pytest.mark.parametrize("dim,n,E,R,h", CASES)
+def test_batch_factors_and_apply_match_oracle(dim, n, E, R, h):
+    ctx, iso = _batch(dim, n, E, R, h=h)
     rep = ctx.tpp_build_factors()
     assert rep["num_schur_fail"] == 0
     nl = iso.nloc
@@ -70,10 +73,11 @@ def test_batch_factors_and_apply_match_oracle(dim, n, E, R):
             assert rel(x[e, r], apply_dense(P, B[e, r])) <= tol, (e, r, kappa, cpair[e])
 
 
-@pytest.mark.parametrize("dim,n,E,R", [(2, 8, 12, 4), (2, 16, 6, 3), (3, 5, 6, 2)])
-def test_batch_gmres_solves_every_block(dim, n, E, R):
+@pytest.mark.parametrize("dim,n,E,R,h", [(2, 8, 12, 4, H), (2, 16, 6, 3, 1.0), (2, 31, 3, 2, 1.0),
+                                          (3, 5, 6, 2, H), (3, 11, 3, 2, 1.0)])
+def test_batch_gmres_solves_every_block(dim, n, E, R, h):
     """One Krylov solve of the whole block-diagonal system, FP64 and nested mixed."""
-    ctx, iso = _batch(dim, n, E, R)
+    ctx, iso = _batch(dim, n, E, R, h=h)
     ctx.tpp_build_factors()
     nl = iso.nloc
     b = synthetic.rhs(6, E * R * nl)

@@ -119,3 +119,20 @@ def test_isolated_blocks_are_mesh_diagonal_blocks(dim, n, nel):
         B = iso.block(e)
         ref = dg.element_block(e)
         assert np.abs(B - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,n,nel", [(2, 4, (5, 5)), (3, 3, (3, 3, 3))])
+def test_isolated_blocks_unit_elements(dim, n, nel):
+    """Unit elements (h = 1) on an N-wide periodic domain: the isolated element with
+    width 1 sampling the field over span 1/N at the normalised centre is the mesh's
+    diagonal block."""
+    from oracle.dg import IsolatedElements
+    N = nel[0]
+    mesh = PeriodicMesh(nel, 1.0)
+    vel = synthetic.fourier_velocity(12, dim)
+    dg = AdvectionDG(mesh, n, 0.05, vel)
+    centres = np.array([[(c + 0.5) / N for c in mesh.coords(e)] for e in range(mesh.num_elem)])
+    iso = IsolatedElements(n, 1.0, centres, 0.05, vel, span=1.0 / N)
+    for e in range(mesh.num_elem):
+        ref = dg.element_block(e)
+        assert np.abs(iso.block(e) - ref).max() <= 1e-13 * np.abs(ref).max()
