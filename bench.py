@@ -516,6 +516,127 @@ def run_batch(args):
     return 0
 
 
+def run_learned(args):
+    """Learned factors, n = 16 (p = 15).  Training: 50,000 isolated unit elements from
+    10 random-Fourier fields (seeds 1801-1810, span 1/64, dt = 0.05), loss = the
+    gauge-invariant relative rank-2 error on each exact rearranged block, Adam with
+    a cosine learning rate, all in libtpp's kernels.  Held out: 10,000 elements from
+    2 other fields (1811, 1812).  Then the 64 x 64 mesh of the default workload
+    (field 1705, never seen in training): one step = learned build (inputs, network
+    forward, error check, exact KSVD for the elements above 0.05, inverses and
+    Schur forms) + GMRES(30) to 1e-8 with the iteration fallback, against one step
+    of the exact build + the same GMRES."""
+    import torch
+    from paper_1704_04549_gb300 import TPP_FEAT_LEARNED, TPP_FEAT_MIXED, TPP_PC_KRON, Context
+    from paper_1704_04549_gb300 import _lib
+    from paper_1704_04549_gb300 import learned as LN
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    n = 16
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(0) as clk:
+        Xt, Mt, _, basis = LN.element_samples(n, args.train_elems, range(1801, 1811), seed=1800)
+        Xh, Mh, _, _ = LN.element_samples(n, args.eval_elems, (1811, 1812), seed=1799)
+        net = LN.Mlp(n, max_batch=4096, params=LN.default_params(n, 1800))
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        hist = LN.train(net, basis, Xt, Mt, args.epochs, batch=args.mlp_batch, lr=args.lr,
+                        lr_min=args.lr * 1e-2)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        train_s = t0.elapsed_time(t1) * 1e-3
+        err_tr = LN.element_errors(net, basis, Xt[:10000], Mt[:10000]).cpu().numpy()
+        err_ho = LN.element_errors(net, basis, Xh, Mh).cpu().numpy()
+
+        w = workload(n)
+        ctx = Context(2, n, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                      features=TPP_FEAT_LEARNED | TPP_FEAT_MIXED, device=str(dev))
+        b = torch.as_tensor(synthetic.rhs(w["rhs_seed"], ctx.num_dofs), device=dev)
+        x = torch.zeros_like(b)
+        Xm, Mm, _ = ctx.tpp_learned_inputs()
+        err_mesh = LN.element_errors(net, basis, Xm, Mm).cpu().numpy()
+        info = {}
+
+        def exact_step():
+            ctx.tpp_build_factors()
+            x.zero_()
+            _, info["exact"] = ctx.gmres_solve(b, x, restart=30, rtol=1e-8,
+                                               max_iters=args.max_iters, pc=TPP_PC_KRON,
+                                               check=False)
+
+        def learned_step():
+            x.zero_()
+            _, info["learned"] = ctx.tpp_solve_learned(net, b, x, threshold=0.05,
+                                                       iter_limit=args.iter_limit,
+                                                       max_iters=args.max_iters, check=False)
+
+        def exact_build():
+            ctx.tpp_build_factors()
+
+        def learned_build():
+            info["build"] = ctx.tpp_build_factors_learned(net, 0.05)
+
+        def forward():
+            net.forward(Xm)
+
+        for fn in (exact_step, learned_step, exact_build, learned_build, forward):
+            for _ in range(args.warmup):
+                fn()
+        ms = {nm: time_each(fn, args.steps, stream, flush)
+              for nm, fn in (("exact_step", exact_step), ("learned_step", learned_step),
+                             ("exact_build", exact_build), ("learned_build", learned_build),
+                             ("forward", forward))}
+    launches = lib.tpp_kernel_launch_count() - l0
+    E = ctx.num_elem
+    flop_fwd = 2.0 * sum(a * c for a, c in zip(net.widths[:-1], net.widths[1:])) * E
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    lr_, ex = info["learned"], info["exact"]
+
+    def stats(e):
+        return {"accept_frac_0.05": float(np.mean(e <= 0.05)), "median_err": float(np.median(e)),
+                "p90_err": float(np.quantile(e, 0.9)), "max_err": float(np.max(e))}
+
+    line = {
+        "metric": "learned factors, 64x64 mesh n=16: time to 1e-8 rel. residual (learned build "
+                  "with KSVD fallback + GMRES), 1 GB300",
+        "value": ms["learned_step"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms["learned_step"], "higher_is_better": False,
+        "vs_baseline": None, "dtype": "f64 (network: bf16 weights, f32 accumulation)",
+        "data": "synthetic",
+        "config": {"workload": "learned factors n=16: train %d isolated elements (fields "
+                               "1801-1810), hold out %d (fields 1811-1812), evaluate on the "
+                               "adv2d-fourier-64x64-n16 mesh (field 1705)"
+                               % (args.train_elems, args.eval_elems),
+                   "epochs": args.epochs, "mlp_batch": args.mlp_batch, "lr": args.lr,
+                   "threshold": 0.05, "iter_limit": args.iter_limit,
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "exact": {"ms_per_step": ms["exact_step"], "iters": ex["iters"],
+                  "converged": bool(ex["converged"]), "build_ms": ms["exact_build"]},
+        "learned": {"ms_per_step": ms["learned_step"], "iters": lr_["iters"],
+                    "converged": bool(lr_["converged"]), "rebuilt": lr_["rebuilt"],
+                    "true_rel_res": lr_["true_rel_res"], "build_ms": ms["learned_build"],
+                    "fallback_elems": info["build"]["num_fallback"], "elements": E},
+        "errors": {"train_sample": stats(err_tr), "held_out": stats(err_ho),
+                   "mesh": stats(err_mesh)},
+        "training": {"seconds": train_s, "epoch_loss_first": hist[0], "epoch_loss_last": hist[-1],
+                     "elements_per_s": args.epochs * args.train_elems / train_s},
+        "roofline": {"kernel": "k_gemm (network forward, 4 GEMM launches over the mesh's "
+                               "4096 elements)", "bound": "alu",
+                     "achieved": flop_fwd / (ms["forward"] * 1e-3) / 1e12,
+                     "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": flop_fwd / (ms["forward"] * 1e-3) / 1e12 / fp32_peak,
+                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                     "traffic": None},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_kernels(args):
     """Kernel-only pass for profilers: one factor build, then a few launches of
     each hot-path kernel on the same workload (no GMRES loop)."""
@@ -576,7 +697,14 @@ def main():
                          "two-sided Schur / quasi-triangular Sylvester form")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batch workload: fraction of the 20,000 + 2,000 elements")
-    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch"], default="adv2d",
+    ap.add_argument("--train-elems", type=int, default=50000)
+    ap.add_argument("--eval-elems", type=int, default=10000)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--mlp-batch", type=int, default=512)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--iter-limit", type=int, default=50,
+                    help="learned workload: GMRES iterations before the exact rebuild")
+    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned"], default="adv2d",
                     help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -587,6 +715,8 @@ def main():
         return run_3d(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -67,6 +67,7 @@ typedef enum {
 #define TPP_FEAT_MIXED        2u  /* reserve float32 copies of the Kronecker apply factors */
 #define TPP_FEAT_TWO_SIDED    4u  /* apply by the paper's two-sided Schur form (quasi-triangular
                                      Sylvester solve) instead of the default one-sided form */
+#define TPP_FEAT_LEARNED      8u  /* reserve the buffers of tpp_build_factors_learned (2D) */
 
 /*
  * Problem description.  Velocity field (component c) at the normalised point
@@ -141,7 +142,7 @@ typedef struct {
   double max_cond_z;       /* 3D: largest cond_1(A1) of the first-stage z factor (0 in 2D) */
   int32_t num_z_unconverged;  /* 3D: elements whose first-stage Lanczos hit its step cap
                                  (the factor is still the best Ritz pair found) */
-  int32_t reserved;
+  int32_t num_fallback;     /* tpp_build_factors_learned: elements given the exact KSVD */
 } tpp_build_report;
 
 typedef struct tpp_ctx tpp_ctx;
@@ -293,6 +294,65 @@ tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);
 /* Stream-ordered device-to-device copy of `bytes` bytes (for callers that read
  * the views above without a CUDA runtime of their own).  Asynchronous. */
 tpp_status tpp_copy_device(void* dst, const void* src, size_t bytes, void* stream);
+
+/*
+ * Learned Kronecker factors (an extension; the paper has no learned component).
+ * A multilayer perceptron maps an element's velocity samples to its rank-2 factors:
+ * 2 n^2 + 1 inputs (a_x and a_y at the n x n nodes, x fastest, then dt / h), three
+ * hidden layers of width 512 with the exact GELU, 4 n^2 outputs read as vec(A_1),
+ * vec(B_1), vec(A_2), vec(B_2) (column-major) of the rearranged block divided by its
+ * Frobenius norm.  Parameters: FP32 master copies used as BF16 weights, FP32
+ * accumulation everywhere.  Loss of an element: || A~/||A~|| - sum_k vec(A_k)
+ * vec(B_k)^T ||_F^2 (gauge invariant; Sec. 4.1 Eq. NKP), evaluated through the
+ * element's core M (A~ = Q M Q^T); the batch loss is the mean.  Training: Adam
+ * (0.9, 0.999, 1e-8).  The network lives in a caller workspace like a context.
+ */
+typedef struct tpp_mlp tpp_mlp;
+int64_t tpp_mlp_num_params(int32_t n);                      /* -1 for a bad n */
+size_t tpp_mlp_workspace_bytes(int32_t n, int32_t max_batch);
+tpp_status tpp_mlp_create(tpp_mlp** out, int32_t n, int32_t max_batch, void* workspace,
+                          size_t ws_bytes, void* stream);
+void tpp_mlp_destroy(tpp_mlp* net);
+/* host params, FP32: for each layer l = 0..3, W_l [K_l][N_l] row-major, then b_l [N_l];
+ * setting them resets the optimiser state */
+tpp_status tpp_mlp_set_params(tpp_mlp* net, const float* host_params, void* stream);
+tpp_status tpp_mlp_get_params(const tpp_mlp* net, float* host_params, void* stream);
+/* X: device [B][2 n^2 + 1]; out: device [B][4 n^2]; 1 <= B <= max_batch */
+tpp_status tpp_mlp_forward(tpp_mlp* net, const float* X, int32_t B, float* out, void* stream);
+/* Forward, loss and gradients of a batch; with lr > 0 one Adam step.  Mn: device
+ * [B][r*r] normalised cores from tpp_learned_inputs of `basis` (a 2D context of the
+ * same n, whose structure basis defines Q); loss: device float, the batch mean. */
+tpp_status tpp_mlp_train_step(tpp_mlp* net, const tpp_ctx* basis, const float* X,
+                              const double* Mn, int32_t B, float lr, float* loss, void* stream);
+/* device pointer to the gradients of the last train step (parameter layout) */
+const float* tpp_mlp_gradients(const tpp_mlp* net);
+/* Network inputs (X: device [E][2 n^2 + 1], may be NULL), normalised cores (Mn: device
+ * [E][r*r] column-major, r = n + min(n^2 - n, n + 2), may be NULL) and block norms
+ * ||A~||_F (norms: device [E]) of every element of a 2D context.  Asynchronous. */
+tpp_status tpp_learned_inputs(const tpp_ctx* ctx, float* X, double* Mn, double* norms,
+                              void* stream);
+int32_t tpp_core_size(const tpp_ctx* ctx);                 /* r */
+/* tpp_build_factors with the network's factors: every element whose predicted factors
+ * have relative rank-2 error sqrt(L) <= threshold on its own block keeps them; the
+ * others fall back to the exact KSVD.  Then the rest of the build as usual.  Needs a
+ * 2D context with TPP_FEAT_LEARNED and a network of the same n.  report->num_fallback
+ * counts the fallbacks.  Synchronises `stream`. */
+tpp_status tpp_build_factors_learned(tpp_ctx* ctx, tpp_mlp* net, double threshold,
+                                     tpp_build_report* report, void* stream);
+/* Per-element loss L_e (device double [B]) of the network's factors for a batch
+ * (X, Mn as for tpp_mlp_train_step); no gradients.  sqrt(L_e) is the relative
+ * rank-2 error the learned build compares with its threshold.  Asynchronous. */
+tpp_status tpp_mlp_element_loss(tpp_mlp* net, const tpp_ctx* basis, const float* X,
+                                const double* Mn, int32_t B, double* loss, void* stream);
+/* Learned preconditioner with both fallbacks: tpp_build_factors_learned(threshold),
+ * then gmres_solve limited to iter_limit Arnoldi steps; if that solve has not
+ * converged, the exact KSVD build (tpp_build_factors) and gmres_solve again from the
+ * current x with opts->max_iters.  result->iters counts both solves; *rebuilt = 1
+ * when the second build ran.  Same argument rules as the two calls. */
+tpp_status tpp_solve_learned(tpp_ctx* ctx, tpp_mlp* net, double threshold, int32_t iter_limit,
+                             const double* b, double* x, const tpp_gmres_opts* opts,
+                             tpp_gmres_result* result, tpp_build_report* report,
+                             int32_t* rebuilt, void* stream);
 
 /* Number of DOFs and elements of the context's problem. */
 int64_t tpp_num_dofs(const tpp_ctx* ctx);

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "TPP_OK", 1: "TPP_ERR_INVALID_ARG", 2: "TPP_ERR_CUDA",
                 9: "TPP_ERR_WORKSPACE"}
 TPP_FP64, TPP_FP32 = 0, 1
 TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
-TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED = 1, 2, 4
+TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1, 2, 4, 8
 
 
 class Problem(C.Structure):
@@ -42,7 +42,7 @@ class BuildReport(C.Structure):
     _fields_ = [("num_elem", C.c_int32), ("num_shifted", C.c_int32), ("num_rank1", C.c_int32),
                 ("num_schur_fail", C.c_int32), ("max_cond", C.c_double),
                 ("min_sigma_ratio", C.c_double), ("max_cond_z", C.c_double),
-                ("num_z_unconverged", C.c_int32), ("reserved", C.c_int32)]
+                ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32)]
 
 
 class Views(C.Structure):
@@ -72,6 +72,26 @@ EXPORTS = {
     "tpp_num_elem": (C.c_int64, [C.c_void_p]),
     "tpp_last_error": (C.c_char_p, []),
     "tpp_kernel_launch_count": (C.c_int64, []),
+    "tpp_core_size": (C.c_int32, [C.c_void_p]),
+    "tpp_learned_inputs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_build_factors_learned": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double,
+                                            C.POINTER(BuildReport), C.c_void_p]),
+    "tpp_mlp_num_params": (C.c_int64, [C.c_int32]),
+    "tpp_mlp_workspace_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "tpp_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
+                                 C.c_size_t, C.c_void_p]),
+    "tpp_mlp_destroy": (None, [C.c_void_p]),
+    "tpp_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "tpp_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.c_float, C.c_void_p, C.c_void_p]),
+    "tpp_mlp_gradients": (C.c_void_p, [C.c_void_p]),
+    "tpp_mlp_element_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.c_void_p, C.c_void_p]),
+    "tpp_solve_learned": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                    C.c_void_p, C.POINTER(GmresOpts), C.POINTER(GmresResult),
+                                    C.POINTER(BuildReport), C.POINTER(C.c_int32), C.c_void_p]),
 }
 
 _lib = None

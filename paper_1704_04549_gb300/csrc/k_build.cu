@@ -324,6 +324,7 @@ struct KsvdArgs {
   int* iscr;       // per element: 4 r pivot flags
   double *sigma, *A1, *B1, *A2, *B2;
   DevStatus* st;
+  const int32_t* mask;   // optional: only elements with mask[e] != 0 are decomposed
 };
 
 // shared-memory layout of one warp of k_ksvd_w (offsets in doubles): the core
@@ -483,6 +484,31 @@ __device__ __forceinline__ int warp_inverse_rows(double (&a)[M], double (&b)[M],
 
 }  // namespace
 
+// The core M of the rearranged block, A~ = Q M Q^T (Q = [E | Qo]):
+// M = [[Cx^T Zd^T + Zd Cy + Dg^T, Cx^T Rz^T], [Rz Cy, 0]], written column-major
+// (leading dimension ld) by one warp.
+__device__ void form_core(const double* Cx, const double* Cy, const double* Dg, const double* Zd,
+                          const double* Rz, int n, int rz, double* Ms, int ld) {
+  const int nc = n + 2, r = n + rz, lane = threadIdx.x & 31;
+  for (int q = lane; q < r * r; q += 32) {
+    const int i = q % r, j = q / r;
+    double v = 0.0;
+    if (i < n && j < n) {
+      for (int c = 0; c < nc; ++c)
+        v += __ldg(Cx + c * n + i) * __ldg(Zd + j * nc + c) +
+             __ldg(Zd + i * nc + c) * __ldg(Cy + c * n + j);
+      v += __ldg(Dg + j + n * i);
+    } else if (i < n) {
+      const int t = j - n;
+      for (int c = 0; c < nc; ++c) v += __ldg(Cx + c * n + i) * __ldg(Rz + t * nc + c);
+    } else if (j < n) {
+      const int t = i - n;
+      for (int c = 0; c < nc; ++c) v += __ldg(Rz + t * nc + c) * __ldg(Cy + c * n + j);
+    }
+    Ms[i + ld * j] = v;
+  }
+}
+
 // ---- k_ksvd_w ---------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   extern __shared__ double smk[];
@@ -504,25 +530,8 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   const double* kc = A.kco + (size_t)e * (2 * nc * n + nn);
   const double *Cx = kc, *Cy = kc + nc * n, *Dg = kc + 2 * nc * n;
 
-  // ---- the core M of the rearranged block, A~ = Q M Q^T (Q = [E | Qo]):
-  // M = [[Cx^T Zd^T + Zd Cy + Dg^T, Cx^T Rz^T], [Rz Cy, 0]]
-  for (int q = lane; q < r * r; q += 32) {
-    const int i = q % r, j = q / r;
-    double v = 0.0;
-    if (i < n && j < n) {
-      for (int c = 0; c < nc; ++c)
-        v += __ldg(Cx + c * n + i) * __ldg(A.Zd + j * nc + c) +
-             __ldg(A.Zd + i * nc + c) * __ldg(Cy + c * n + j);
-      v += __ldg(Dg + j + n * i);
-    } else if (i < n) {
-      const int t = j - n;
-      for (int c = 0; c < nc; ++c) v += __ldg(Cx + c * n + i) * __ldg(A.Rz + t * nc + c);
-    } else if (j < n) {
-      const int t = i - n;
-      for (int c = 0; c < nc; ++c) v += __ldg(A.Rz + t * nc + c) * __ldg(Cy + c * n + j);
-    }
-    Ms[i + ld * j] = v;
-  }
+  if (A.mask && !A.mask[e]) return;                     // factors given (whole warp)
+  form_core(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, Ms, ld);
   __syncwarp();
 
   // ---- Householder bidiagonalisation M = U_h B V_h^T (B upper bidiagonal:
@@ -1059,6 +1068,125 @@ __global__ void __launch_bounds__(128) k_shift_inv_w(int n, int64_t E, const dou
   }
 }
 
+// ---- learned factors: network inputs, normalised cores, acceptance ------------
+__global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, const double* cx,
+                          const double* cy, const double* sx, const double* sy, double* kco,
+                          const double* sxu, const double* syu);
+
+// Mn = M / ||M||_F (column-major r x r) and ||M||_F (= ||A~||_F) per element
+__global__ void __launch_bounds__(128) k_core(const double* kco, const double* Zd, const double* Rz,
+                                              int n, int rz, int64_t E, double* Mn, double* norms) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;
+  const int nc = n + 2, nn = n * n, r = n + rz;
+  const double* kc = kco + (size_t)e * (2 * nc * n + nn);
+  double* M = Mn + (size_t)e * r * r;
+  form_core(kc, kc + nc * n, kc + 2 * nc * n, Zd, Rz, n, rz, M, r);
+  __syncwarp();
+  double s2 = 0.0;
+  for (int q = lane; q < r * r; q += 32) s2 += M[q] * M[q];
+  const double nr = sqrt(warp_sum(s2));
+  const double inv = (nr > 0.0) ? 1.0 / nr : 0.0;
+  for (int q = lane; q < r * r; q += 32) M[q] *= inv;
+  if (lane == 0) norms[e] = nr;
+}
+
+// network input of an element: a_x, a_y at the n x n nodes (recovered from the
+// scaled flux Jacobians cx = -dt h w_i w_j a_x), then dt / h
+__global__ void k_features(const Tables* T, int n, int64_t E, double h, double dt,
+                           const double* cx, const double* cy, float* X) {
+  const int nn = n * n, K = 2 * nn + 1;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E * K;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / K;
+    const int q = (int)(g % K);
+    float v;
+    if (q == 2 * nn) {
+      v = (float)(dt / h);
+    } else {
+      const int qq = q % nn, i = qq % n, j = qq / n;
+      const double sc = dt * h * T->w[i] * T->w[j];
+      const double c = (q < nn ? cx : cy)[e * nn + qq];
+      v = (sc > 0.0) ? (float)(-c / sc) : 0.0f;
+    }
+    X[g] = v;
+  }
+}
+
+// accept the prediction of element e when sqrt(L_e) <= threshold: factors
+// A_k = sqrt(||A~||) * output (column-major), sigma_k = ||A_k|| ||B_k||;
+// otherwise flag it for the exact KSVD.
+__global__ void __launch_bounds__(128) k_learned_accept(int n, int64_t E, const float* out,
+                                                        const double* norms, const double* lossv,
+                                                        double threshold, double* A1, double* B1,
+                                                        double* A2, double* B2, double* sigma,
+                                                        int32_t* mask, DevStatus* st) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;
+  const int nn = n * n;
+  const double err = sqrt(fmax(lossv[e], 0.0));
+  const bool ok = err <= threshold;
+  if (lane == 0) {
+    mask[e] = ok ? 0 : 1;
+    if (!ok) atomicAdd(&st->learned_fallback, 1);
+  }
+  if (!ok) return;
+  const double f = sqrt(norms[e]);
+  const float* oe = out + (size_t)e * 4 * nn;
+  double nk[4] = {0.0, 0.0, 0.0, 0.0};
+  double* dst[4] = {A1, B1, A2, B2};
+  for (int k = 0; k < 4; ++k) {
+    double s2 = 0.0;
+    for (int q = lane; q < nn; q += 32) {
+      const double v = f * (double)oe[k * nn + q];
+      dst[k][(size_t)e * nn + q] = v;
+      s2 += v * v;
+    }
+    nk[k] = sqrt(warp_sum(s2));
+  }
+  if (lane == 0) {
+    sigma[2 * e] = nk[0] * nk[1];
+    sigma[2 * e + 1] = nk[2] * nk[3];
+  }
+}
+
+cudaError_t launch_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double* norms,
+                                  cudaStream_t s) {
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(
+      c->p<Tables>(c->L.tables), c->n, c->iso ? (int)c->E : c->prob.nel[0],
+      c->iso ? 1 : c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+      c->p<double>(c->L.sx), c->p<double>(c->L.sy), c->p<double>(c->L.kco),
+      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr);
+  count_launch();
+  if (Mn) {
+    k_core<<<(unsigned)((c->E + 3) / 4), 128, 0, s>>>(c->p<double>(c->L.kco),
+                                                      c->p<double>(c->L.zd),
+                                                      c->p<double>(c->L.rz), c->n, c->rz, c->E,
+                                                      Mn, norms);
+    count_launch();
+  }
+  if (X) {
+    k_features<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
+                                        c->prob.dt, c->p<double>(c->L.cx),
+                                        c->p<double>(c->L.cy), X);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const double* norms,
+                                  const double* lossv, double threshold, int32_t* mask,
+                                  cudaStream_t s) {
+  k_learned_accept<<<(unsigned)((c->E + 3) / 4), 128, 0, s>>>(
+      c->n, c->E, out, norms, lossv, threshold, c->p<double>(c->L.fA1), c->p<double>(c->L.fB1),
+      c->p<double>(c->L.fA2), c->p<double>(c->L.fB2), c->p<double>(c->L.sigma), mask,
+      c->p<DevStatus>(c->L.status));
+  count_launch();
+  return cudaGetLastError();
+}
+
 // ---- k_coef_2d: KSVD coefficients of a 2D element block (flux Jacobians of
 // Sec. 3.4.1 in the basis of k_struct_qr): Cx[c][j] = cx[c + n j] (volume,
 // c < n), max(a.n, 0) on the +x and -x faces (c = n, n + 1); Cy likewise for
@@ -1099,7 +1227,7 @@ __global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, cons
 
 // KSVD of the 2D-structured blocks in kco (2D elements, or the second stage
 // of the 3D nested form), inverses, Schur forms, S_A and S_B.
-cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s) {
+cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t* mask) {
   const int n = c->n, rz = c->rz, nn = n * n;
   const int64_t E = c->E;
   DevStatus* st = c->p<DevStatus>(c->L.status);
@@ -1120,6 +1248,7 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s) {
   ka.A2 = c->p<double>(c->L.fA2);
   ka.B2 = c->p<double>(c->L.fB2);
   ka.st = st;
+  ka.mask = mask;
   {
     const int warps = 4;
     const size_t smem = (size_t)warps * ksvd_smem(n, rz).total * sizeof(double);
@@ -1219,7 +1348,7 @@ cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_ksvd_pipeline(c, s);
+  return launch_ksvd_pipeline(c, s, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1631,7 +1760,7 @@ cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s) {
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_ksvd_pipeline(c, s);
+  return launch_ksvd_pipeline(c, s, nullptr);
 }
 
 }  // namespace tpp

@@ -191,6 +191,15 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
     L.zflags = take((size_t)E * 4);
   }
   L.fG = two ? 0 : take(fsz * 2 * n);
+  if (features & TPP_FEAT_LEARNED) {
+    const size_t r = (size_t)n + rz;
+    L.lx = take((size_t)E * (2 * n * n + 1) * 4);
+    L.lout = take((size_t)E * 4 * n * n * 4);
+    L.lmn = take((size_t)E * r * r * 8);
+    L.lnorm = take((size_t)E * 8);
+    L.lloss = take((size_t)E * 8);
+    L.lmask = take((size_t)E * 4);
+  }
   L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
   if (features & TPP_FEAT_MIXED) {      // FP32 operator and inner GMRES
     L.opf = take(op_f32_layout(d, Nc, E, n, EB, iso).total * 4);
@@ -277,6 +286,10 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   if (const char* why = validate(prob, max_restart)) {
     set_error(why);
     return TPP_ERR_INVALID_ARG;
+  }
+  if (prob->dim == 3 && (features & TPP_FEAT_LEARNED)) {
+    set_error("learned factors are implemented for 2D problems only");
+    return TPP_ERR_UNSUPPORTED;
   }
   if ((prob->dim == 3 || prob->batch_rhs > 0) && (features & TPP_FEAT_BLOCK_JACOBI)) {
     set_error("exact block Jacobi is implemented for 2D meshes only");
@@ -371,13 +384,9 @@ void tpp_destroy(tpp_ctx* ctx) { delete ctx; }
 int64_t tpp_num_dofs(const tpp_ctx* ctx) { return ctx ? ctx->N : -1; }
 int64_t tpp_num_elem(const tpp_ctx* ctx) { return ctx ? ctx->E : -1; }
 
-tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream) {
-  if (tpp_status r = check_ctx(c)) return r;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const DevStatus st0 = fresh_status();
-  TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
-               "reset status");
-  TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
+namespace {
+// status of the build just enqueued -> report and return code
+tpp_status finish_build(tpp_ctx* c, tpp_build_report* report, cudaStream_t s) {
   if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_to_f32(c, s), "k_to_f32");
   DevStatus st;
   TPP_TRY_CUDA(cudaMemcpyAsync(&st, c->ws + c->L.status, sizeof(st), cudaMemcpyDeviceToHost, s),
@@ -392,7 +401,7 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
     report->min_sigma_ratio = st.min_sigma_ratio;
     report->max_cond_z = st.max_cond_z;
     report->num_z_unconverged = st.z_unconverged;
-    report->reserved = 0;
+    report->num_fallback = st.learned_fallback;
   }
   c->factors_built = true;
   if (st.build_schur_fail) {
@@ -405,6 +414,63 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
     return TPP_ERR_SINGULAR_FACTOR;
   }
   return TPP_OK;
+}
+}  // namespace
+
+tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevStatus st0 = fresh_status();
+  TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
+               "reset status");
+  TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
+  return finish_build(c, report, s);
+}
+
+int32_t tpp_core_size(const tpp_ctx* c) { return c ? c->r : -1; }
+
+tpp_status tpp_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double* norms,
+                              void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (c->dim != 2 || (Mn && !norms) || (!X && !Mn)) {
+    set_error("tpp_learned_inputs: 2D context; Mn needs norms; X or Mn required");
+    return TPP_ERR_INVALID_ARG;
+  }
+  TPP_TRY_CUDA(launch_learned_inputs(c, X, Mn, norms, static_cast<cudaStream_t>(stream)),
+               "tpp_learned_inputs");
+  return TPP_OK;
+}
+
+tpp_status tpp_build_factors_learned(tpp_ctx* c, tpp_mlp* net, double threshold,
+                                     tpp_build_report* report, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!net || c->dim != 2 || !(c->features & TPP_FEAT_LEARNED) || mlp_n(net) != c->n ||
+      !(threshold >= 0.0)) {
+    set_error("tpp_build_factors_learned: 2D context with TPP_FEAT_LEARNED, network of the "
+              "same n, threshold >= 0");
+    return TPP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevStatus st0 = fresh_status();
+  TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
+               "reset status");
+  float* X = c->p<float>(c->L.lx);
+  float* out = c->p<float>(c->L.lout);
+  double* Mn = c->p<double>(c->L.lmn);
+  double* norms = c->p<double>(c->L.lnorm);
+  double* lossv = c->p<double>(c->L.lloss);
+  TPP_TRY_CUDA(launch_learned_inputs(c, X, Mn, norms, s), "learned inputs");
+  const int n = c->n, K = 2 * n * n + 1, O = 4 * n * n, r = c->r, mb = mlp_max_batch(net);
+  for (int64_t e0 = 0; e0 < c->E; e0 += mb) {
+    const int B = (int)((c->E - e0) < mb ? (c->E - e0) : mb);
+    mlp_forward(net, X + e0 * K, B, out + e0 * O, s);
+    TPP_TRY_CUDA(mlp_factor_loss(out + e0 * O, Mn + e0 * r * r, c->p<double>(c->L.qo), n, c->rz,
+                                 B, 1.0f, nullptr, lossv + e0, s), "learned loss");
+  }
+  TPP_TRY_CUDA(launch_learned_accept(c, out, norms, lossv, threshold, c->p<int32_t>(c->L.lmask), s),
+               "learned accept");
+  TPP_TRY_CUDA(launch_ksvd_pipeline(c, s, c->p<int32_t>(c->L.lmask)), "k_build (fallback)");
+  return finish_build(c, report, s);
 }
 
 tpp_status tpp_build_block_jacobi(tpp_ctx* c, void* stream) {
@@ -766,6 +832,36 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     set_error("GMRES did not reach rtol within max_iters");
   if (final_status == TPP_ERR_NAN) set_error("NaN or Inf in the GMRES residual");
   return final_status;
+}
+
+tpp_status tpp_solve_learned(tpp_ctx* c, tpp_mlp* net, double threshold, int32_t iter_limit,
+                             const double* b, double* x, const tpp_gmres_opts* opts,
+                             tpp_gmres_result* res, tpp_build_report* report, int32_t* rebuilt,
+                             void* stream) {
+  if (!opts || !res || !rebuilt || iter_limit < 1) {
+    set_error("tpp_solve_learned: opts, result, rebuilt non-NULL and iter_limit >= 1");
+    return TPP_ERR_INVALID_ARG;
+  }
+  *rebuilt = 0;
+  if (tpp_status r = tpp_build_factors_learned(c, net, threshold, report, stream)) return r;
+  tpp_gmres_opts o = *opts;
+  o.max_iters = iter_limit < opts->max_iters ? iter_limit : opts->max_iters;
+  tpp_status r = gmres_solve(c, b, x, &o, res, stream);
+  if (r != TPP_ERR_NOT_CONVERGED || res->converged) return r;
+  // iteration threshold exceeded: exact KSVD for every element, continue from x
+  const int32_t first = res->iters, first_inner = res->inner_iters, first_cycles = res->cycles;
+  *rebuilt = 1;
+  tpp_build_report rep2;
+  if (tpp_status r2 = tpp_build_factors(c, &rep2, stream)) return r2;
+  if (report) {
+    report->num_fallback = report->num_elem;
+    report->max_cond = rep2.max_cond;
+  }
+  r = gmres_solve(c, b, x, opts, res, stream);
+  res->iters += first;
+  res->inner_iters += first_inner;
+  res->cycles += first_cycles;
+  return r;
 }
 
 }  // extern "C"

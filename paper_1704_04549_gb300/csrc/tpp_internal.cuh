@@ -64,6 +64,8 @@ struct DevStatus {
   double min_sigma_ratio;
   int32_t nan_seen;
   int32_t z_unconverged;    // 3D stage 1: elements whose Lanczos hit its step cap
+  int32_t learned_fallback; // learned build: elements handed to the exact KSVD
+  int32_t pad_st;
   double max_cond_z;        // 3D stage 1: largest cond_1(A1)
 };
 
@@ -97,6 +99,7 @@ struct Layout {
   size_t bscr, biscr;                  // factor-build scratch (Lanczos bases, tridiagonal work)
   size_t kco;                          // per-block KSVD coefficients (Cx, Cy, Dg)
   size_t fG;                           // one-sided form: shifted inverses, 2 n^3 per element
+  size_t lx, lout, lmn, lnorm, lloss, lmask;   // learned build: inputs, outputs, cores, flags
   size_t opf;                          // mixed mode: FP32 operator data (OpF32Layout)
   size_t gstate_in, gbuf_in, vi, tf;   // mixed mode: inner FP32 GMRES state, H, basis, temp
   size_t s1scr, fAz, fAzi, sigz, zflags;   // 3D stage 1: scratch, A1, A1^-1, sigma_1, flags
@@ -185,7 +188,17 @@ __host__ __device__ inline S1Layout s1_layout(int n, int rz, int Jmax) {
 __host__ __device__ inline int s1_jmax(int n) { return (n * n < 64) ? n * n : 64; }
 
 cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s);
-cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t* mask);
+cudaError_t launch_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double* norms,
+                                  cudaStream_t s);
+cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const double* norms,
+                                  const double* lossv, double threshold, int32_t* mask,
+                                  cudaStream_t s);
+void mlp_forward(tpp_mlp* net, const float* X, int B, float* out, cudaStream_t s);
+int mlp_n(const tpp_mlp* net);
+int mlp_max_batch(const tpp_mlp* net);
+cudaError_t mlp_factor_loss(const float* out, const double* Mn, const double* Qo, int n, int rz,
+                            int B, float inv_batch, float* dout, double* lossv, cudaStream_t s);
 cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
                               const int32_t* skip);
 cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,

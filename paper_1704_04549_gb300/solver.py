@@ -107,6 +107,54 @@ class Context:
             raise L.TppError(st, "tpp_build_factors")
         return out
 
+    def tpp_core_size(self) -> int:
+        return int(self.lib.tpp_core_size(self._ctx))
+
+    def tpp_learned_inputs(self, features: bool = True, cores: bool = True, stream=None):
+        """(X [E, 2n^2+1] float32 or None, Mn [E, r*r] float64 or None, norms [E] or None)."""
+        E, n, r = self.num_elem, self.n, self.tpp_core_size()
+        X = torch.empty((E, 2 * n * n + 1), dtype=torch.float32, device=self.device) \
+            if features else None
+        Mn = torch.empty((E, r * r), dtype=torch.float64, device=self.device) if cores else None
+        nr = torch.empty(E, dtype=torch.float64, device=self.device) if cores else None
+        nul = C.c_void_p(0)
+        L.check(self.lib.tpp_learned_inputs(self._ctx, _ptr(X) if X is not None else nul,
+                                            _ptr(Mn) if Mn is not None else nul,
+                                            _ptr(nr) if nr is not None else nul,
+                                            _stream(stream)), "tpp_learned_inputs")
+        return X, Mn, nr
+
+    def tpp_build_factors_learned(self, net, threshold: float = 0.05, stream=None) -> dict:
+        rep = L.BuildReport()
+        st = self.lib.tpp_build_factors_learned(self._ctx, net._net, float(threshold),
+                                                C.byref(rep), _stream(stream))
+        out = {k: getattr(rep, k) for k, _ in L.BuildReport._fields_}
+        out["status"] = st
+        if st not in (L.TPP_OK,):
+            raise L.TppError(st, "tpp_build_factors_learned")
+        return out
+
+    def tpp_solve_learned(self, net, b, x=None, threshold: float = 0.05, iter_limit: int = 60,
+                          restart: int = 30, rtol: float = 1e-8, max_iters: int = 3000,
+                          inner_iters: int = 0, stream=None, check: bool = True):
+        """Learned build + GMRES with both fallbacks (factor error above threshold per
+        element; more than iter_limit iterations: exact rebuild and continue)."""
+        b = self._vec(b, "b")
+        x = torch.zeros_like(b) if x is None else self._vec(x, "x")
+        mixed = inner_iters > 0
+        o = L.GmresOpts(restart, max_iters, rtol, L.TPP_PC_KRON,
+                        L.TPP_FP32 if mixed else L.TPP_FP64, int(mixed), int(inner_iters), 0, 0.0)
+        r, rep, rebuilt = L.GmresResult(), L.BuildReport(), C.c_int32(0)
+        st = self.lib.tpp_solve_learned(self._ctx, net._net, float(threshold), int(iter_limit),
+                                        _ptr(b), _ptr(x), C.byref(o), C.byref(r), C.byref(rep),
+                                        C.byref(rebuilt), _stream(stream))
+        res = {k: getattr(r, k) for k, _ in L.GmresResult._fields_}
+        res["build"] = {k: getattr(rep, k) for k, _ in L.BuildReport._fields_}
+        res["rebuilt"] = int(rebuilt.value)
+        if check and st != L.TPP_OK:
+            raise L.TppError(st, "tpp_solve_learned")
+        return x, res
+
     def tpp_build_block_jacobi(self, stream=None):
         L.check(self.lib.tpp_build_block_jacobi(self._ctx, _stream(stream)),
                 "tpp_build_block_jacobi")
