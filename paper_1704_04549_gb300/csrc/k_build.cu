@@ -441,16 +441,21 @@ __device__ bool warp_gauss_jordan(double* a, int n, double* fac) {
 // of [A | I] reads [d_r e_{k_r} | d_r (row k_r of A^-1)].  On return b[] of lane
 // r holds row k_r of A^-1 and the function returns k_r (-1 for lanes >= m).
 // `sing` is set when a pivot is zero (its row of the inverse is then left 0).
+// In-place Gauss-Jordan inverse of the m x m matrix whose row l sits in lane l's
+// registers (m <= M <= 32), partial pivoting without row exchanges: at step k the
+// pivot row p scales to (row_p / a_pk, with 1 / a_pk in column k) and every other
+// row r takes row_r - f row_p (f = a_rk / a_pk, -f in column k).  On return lane r
+// holds, in slot c, entry (kr, piv[c]) of the inverse, kr the step at which row r
+// was the pivot (-1 for lanes >= m).  M FMAs per lane and step (the augmented
+// [A | I] form needs up to 2M).  Pivot search on the magnitude bits (integer pipe).
 template <int M>
-__device__ __forceinline__ int warp_inverse_rows(double (&a)[M], double (&b)[M], int m, bool& sing) {
+__device__ __forceinline__ int warp_gj_inplace(double (&a)[M], int (&piv)[M], int m, bool& sing) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int c = 0; c < M; ++c) b[c] = (c == lane) ? 1.0 : 0.0;
   bool used = lane >= m;
   int kr = -1;
-  double d = 0.0;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
+    piv[k] = 0;
     if (k < m) {
       const int key = used ? -1 : (__double2hiint(a[k]) & 0x7fffffff);
       const int mx = __reduce_max_sync(0xffffffffu, key);
@@ -462,23 +467,76 @@ __device__ __forceinline__ int warp_inverse_rows(double (&a)[M], double (&b)[M],
       const int p = __ffs(bal) - 1;
       const double pv = __shfl_sync(0xffffffffu, a[k], p);
       const double ip = (pv != 0.0) ? 1.0 / pv : 0.0;
-      const double f = (lane == p) ? 0.0 : a[k] * ip;
-      if (lane == p) {
+      const bool isp = (lane == p);
+      const double f = a[k] * ip;
+      const double s1 = isp ? ip : -f;
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        if (c == k || c >= m) continue;
+        const double v = __shfl_sync(0xffffffffu, a[c], p);
+        a[c] = fma(s1, v, isp ? 0.0 : a[c]);
+      }
+      a[k] = s1;
+      if (isp) {
         used = true;
         kr = k;
-        d = pv;
       }
-#pragma unroll
-      for (int c = k + 1; c < M; ++c)
-        if (c < m) a[c] -= f * __shfl_sync(0xffffffffu, a[c], p);
-#pragma unroll
-      for (int c = 0; c < M; ++c)
-        if (c < m) b[c] -= f * __shfl_sync(0xffffffffu, b[c], p);
+      piv[k] = p;
     }
   }
-  const double id = (d != 0.0) ? 1.0 / d : 0.0;
+  return kr;
+}
+
+// Complex version for n <= 16: the n x n complex matrix Y0 = C_2 + mu I with row l's
+// real part in lane l and imaginary part in lane l + 16; same in-place scheme.
+__device__ __forceinline__ int warp_gj_inplace_c(double (&a)[16], uint64_t& piv, int n,
+                                                 bool& sing) {
+  const int lane = threadIdx.x & 31, row = lane & 15;
+  const bool im = lane >= 16;
+  bool used = row >= n;
+  int kr = -1;
+  piv = 0;                      // pivot row of step k in bits 4k..4k+3
 #pragma unroll
-  for (int c = 0; c < M; ++c) b[c] *= id;
+  for (int k = 0; k < 16; ++k) {
+    if (k < n) {
+      const double ak = a[k];
+      const double ao = __shfl_xor_sync(0xffffffffu, ak, 16);
+      const int key = used ? -1 : max(__double2hiint(ak) & 0x7fffffff,
+                                      __double2hiint(ao) & 0x7fffffff);
+      const int mx = __reduce_max_sync(0xffffffffu, key);
+      unsigned bal = __ballot_sync(0xffffffffu, !used && !im && key == mx);
+      if (mx <= 0) {
+        sing = true;
+        bal = __ballot_sync(0xffffffffu, !used && !im);
+      }
+      const int p = __ffs(bal) - 1;
+      const double pr = __shfl_sync(0xffffffffu, ak, p);
+      const double pi = __shfl_sync(0xffffffffu, ak, p + 16);
+      const double den = pr * pr + pi * pi;
+      const double iden = (den != 0.0) ? 1.0 / den : 0.0;
+      const double ipr = pr * iden, ipi = -pi * iden;
+      const double akr = im ? ao : ak, aki = im ? ak : ao;
+      const double fr = akr * ipr - aki * ipi, fi = akr * ipi + aki * ipr;
+      const bool isp = (row == p);
+      // lane value of row_r - f row_p (re: b - fr vr + fi vi, im: b - fr vi - fi vr);
+      // pivot row: ip row_p (re: ipr vr - ipi vi, im: ipr vi + ipi vr)
+      const double s1 = isp ? ipr : -fr;
+      const double s2 = isp ? (im ? ipi : -ipi) : (im ? -fi : fi);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        if (c == k || c >= n) continue;
+        const double vr = __shfl_sync(0xffffffffu, a[c], p);
+        const double vi = __shfl_sync(0xffffffffu, a[c], p + 16);
+        a[c] = fma(s1, im ? vi : vr, fma(s2, im ? vr : vi, isp ? 0.0 : a[c]));
+      }
+      a[k] = isp ? (im ? ipi : ipr) : (im ? -fi : -fr);
+      if (isp) {
+        used = true;
+        kr = k;
+      }
+      piv |= (uint64_t)p << (4 * k);
+    }
+  }
   return kr;
 }
 
@@ -857,6 +915,180 @@ __global__ void __launch_bounds__(64) k_invert_w(InvArgs A) {
   }
 }
 
+// ---- k_invert_r (n <= 16): the same gauge search with both inversions of a
+// candidate in one warp: lanes 0-15 hold the rows of A_2 + alpha A_1, lanes 16-31
+// those of B_1 - alpha B_2, and one in-place Gauss-Jordan pass inverts both.  The
+// candidates are ranked in FP32 (their condition numbers only choose alpha); the
+// chosen pair is then inverted in FP64.
+__device__ __forceinline__ int mag_key(float v) { return __float_as_int(v) & 0x7fffffff; }
+__device__ __forceinline__ int mag_key(double v) { return __double2hiint(v) & 0x7fffffff; }
+
+// dual in-place Gauss-Jordan (see warp_gj_inplace) of two m x m matrices, m <= 16,
+// one per half-warp; pivot rows of step k in bits 4k..4k+3 of piv; returns kr.
+template <typename T>
+__device__ __forceinline__ int warp_gj_dual(T (&a)[16], uint64_t& piv, int m, bool& sing) {
+  const int lane = threadIdx.x & 31, row = lane & 15, hb = lane & 16;
+  bool used = row >= m;
+  int kr = -1;
+  piv = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k < m) {
+      const int key = used ? -1 : mag_key(a[k]);
+      int mx = key;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const unsigned b1 = __ballot_sync(0xffffffffu, !used && key == mx);
+      const unsigned b2 = __ballot_sync(0xffffffffu, !used);
+      if (mx <= 0) sing = true;
+      const unsigned bits = ((mx > 0 ? b1 : b2) >> hb) & 0xffffu;
+      const int p = __ffs(bits) - 1;
+      const int src = hb + p;
+      const T pv = __shfl_sync(0xffffffffu, a[k], src);
+      const T ip = (pv != T(0)) ? T(1) / pv : T(0);
+      const bool isp = (row == p);
+      const T f = a[k] * ip;
+      const T s1 = isp ? ip : -f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        if (c == k || c >= m) continue;
+        const T v = __shfl_sync(0xffffffffu, a[c], src);
+        a[c] = fma(s1, v, isp ? T(0) : a[c]);
+      }
+      a[k] = s1;
+      if (isp) {
+        used = true;
+        kr = k;
+      }
+      piv |= (uint64_t)p << (4 * k);
+    }
+  }
+  return kr;
+}
+
+// 1-norms (max column sums of |.|) of the half-warp's matrix and of its inverse slots
+template <typename T>
+__device__ __forceinline__ float half_norm1(const T (&a)[16], int m) {
+  float best = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    if (c >= m) continue;
+    float v = fabsf((float)a[c]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    best = fmaxf(best, v);
+  }
+  return best;
+}
+
+template <typename T>
+__device__ __forceinline__ void invert_rows_load(const InvArgs& A, int64_t base, bool rank1,
+                                                 double al, T (&a)[16]) {
+  const int lane = threadIdx.x & 31, row = lane & 15, n = A.n;
+  const bool bside = lane >= 16;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    double v = 0.0;
+    if (row < n && c < n) {
+      const int64_t idx = base + row + n * c;
+      if (!bside) v = rank1 ? A.A1[idx] : A.A2[idx] + al * A.A1[idx];
+      else v = rank1 ? A.B1[idx] : A.B1[idx] - al * A.B2[idx];
+    }
+    a[c] = (T)v;
+  }
+}
+
+// cond_1 product of a candidate from the two halves' norms (double: no overflow)
+__device__ __forceinline__ double pair_cond(float nm, float ninv, bool sing) {
+  const int lane = threadIdx.x & 31;
+  const double mine = (double)nm * (double)ninv;
+  const double other = __shfl_xor_sync(0xffffffffu, mine, 16);
+  const bool anys = __any_sync(0xffffffffu, sing);
+  const double cp = mine * other;
+  (void)lane;
+  return (anys || !(cp < 1e300)) ? INFINITY : cp;
+}
+
+__global__ void __launch_bounds__(128, 4) k_invert_r(InvArgs A) {
+  const int n = A.n, nn = n * n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = lane & 15;
+  const bool bside = lane >= 16;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= A.E) return;
+  const int64_t base = e * nn;
+  const double s1 = A.sigma[2 * e], s2 = A.sigma[2 * e + 1];
+  const bool rank1 = !(s2 > 1e-14 * s1);
+  double nA1 = 0.0, nA2 = 0.0;
+  for (int q = lane; q < nn; q += 32) {
+    nA1 += A.A1[base + q] * A.A1[base + q];
+    nA2 += A.A2[base + q] * A.A2[base + q];
+  }
+  nA1 = warp_sum(nA1);
+  nA2 = warp_sum(nA2);
+  const double ascale = (nA1 > 0.0) ? sqrt(nA2 / nA1) : 0.0;
+  double best = INFINITY, alpha = 0.0;
+  const int ncand = rank1 ? 1 : 7;
+  for (int ci = 0; ci < ncand; ++ci) {
+    // t = 0, 0.25, -0.25, 1, -1, 4, -4 (the list of k_invert_w)
+    const double t = (ci == 0) ? 0.0 : ((ci & 1) ? 1.0 : -1.0) * ldexp(0.25, 2 * ((ci - 1) >> 1));
+    const double al = rank1 ? 0.0 : t * ascale;
+    float af[16];
+    invert_rows_load<float>(A, base, rank1, al, af);
+    const float nm = half_norm1(af, n);
+    uint64_t pv;
+    bool sg = false;
+    warp_gj_dual<float>(af, pv, n, sg);
+    const double cp = pair_cond(nm, half_norm1(af, n), sg);
+    if (cp < best) {
+      best = cp;
+      alpha = al;
+    }
+    if (best <= 1e3) break;
+  }
+  // the chosen pair in FP64
+  double ad[16];
+  invert_rows_load<double>(A, base, rank1, alpha, ad);
+  const float nm = half_norm1(ad, n);
+  uint64_t piv;
+  bool sg = false;
+  const int kr = warp_gj_dual<double>(ad, piv, n, sg);
+  const double cond = pair_cond(nm, half_norm1(ad, n), sg);
+  const int sing = !(cond <= 1e14);
+  const bool shifted = (alpha != 0.0);
+  // lane (row r, side): row kr of L_A^-1 (side 0) or L_B^-1 (side 1) in slots piv[c]
+  double* Li = bside ? A.LBi : A.LAi;
+  double* Cout = bside ? A.C2 : A.C1;
+  const double* R = bside ? A.B2 : A.A1;       // C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2
+  if (kr >= 0) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < n) Li[base + kr + n * (int)((piv >> (4 * c)) & 15u)] = ad[c];
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+      double v = 0.0;
+      if (!rank1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c < n) v = fma(ad[c], __ldg(R + base + (int)((piv >> (4 * c)) & 15u) + n * j), v);
+      }
+      Cout[base + kr + n * j] = v;
+    }
+  }
+  (void)row;
+  if (lane == 0) {
+    int fl = 0;
+    if (shifted) fl |= 1;
+    if (rank1) fl |= 2;
+    if (sing) fl |= 8;
+    A.flags[e] = fl;
+    A.cond[e] = cond;
+    if (shifted) atomicAdd(&A.st->build_shifted, 1);
+    if (rank1) atomicAdd(&A.st->build_rank1, 1);
+    if (sing) atomicAdd(&A.st->build_singular, 1);
+    if (cond < 1e300) atomic_max_double(&A.st->max_cond, cond);
+  }
+}
+
 // ---- k_schur_w: real Schur form of C (staged in T1 / T2), one warp per matrix
 // (mpe = 2: C_1 and C_2 of every element; mpe = 1: C_1 only)
 __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, double* T1,
@@ -970,24 +1202,101 @@ __device__ __noinline__ bool shift_inv_block(const double* Tg, const double* Cg,
                                              int j, int m, double* Ge) {
   const int lane = threadIdx.x & 31;
   bool sing = false;
-  double a[M], b[M];
+  double a[M];
+  int piv[M];
 #pragma unroll
   for (int c = 0; c < M; ++c)
     a[c] = (lane < m && c < m) ? shifted_entry(Tg, Cg, rank1, n, j, lane, c) : 0.0;
-  const int kr = warp_inverse_rows<M>(a, b, m, sing);
+  const int kr = warp_gj_inplace<M>(a, piv, m, sing);
   if (kr >= 0) {
 #pragma unroll
     for (int c = 0; c < M; ++c)
-      if (c < m) Ge[g_index(n, j, kr, c)] = b[c];
+      if (c < m) Ge[g_index(n, j, kr, piv[c])] = a[c];
   }
   return sing;
 }
 
-// n <= M / 2: one warp per element, register Gauss-Jordan (lanes own rows)
+// 2x2 block {j, j+1} of T_1 with complex eigenvalues (n <= 16).  Balanced by
+// D = diag(1, d) (|t01 d| = |t10 / d|), T' = D^-1 T D = W diag(mu, conj mu) W^-1 with
+// w = (t01', mu - t00) the eigenvector of mu, the 2n x 2n system
+// K = I (x) C_2 + T (x) I has K^-1 = (DW (x) I) diag(Y, conj Y) ((DW)^-1 (x) I),
+// Y = (C_2 + mu I)^-1, so block (a, b) of K^-1 is 2 Re(c_ab Y) with
+// c_ab = D_a w_a [W^-1]_{0b} / D_b: one complex n x n inverse instead of a real
+// 2n x 2n one.  Returns 0 without writing when the block is not a well-separated
+// complex pair (|Im mu| < 0.1 |t01'|: W near singular); bit 0 = done, bit 1 = singular.
+__device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg, int n, int j,
+                                             double* Ge) {
+  double t00 = Tg[j + n * j], t01 = Tg[j + n * (j + 1)];
+  double t10 = Tg[(j + 1) + n * j], t11 = Tg[(j + 1) + n * (j + 1)];
+  if (!(t01 * t10 < 0.0)) return 0;
+  double d = sqrt(-t10 / t01);                 // D = diag(1, d)
+  double b01 = t01 * d;                        // balanced t01' (|t01'| = |t10'|)
+  double hd = 0.5 * (t00 - t11);
+  double y2 = -(hd * hd + t01 * t10);
+  if (!(y2 > 0.01 * b01 * b01)) return 0;
+  const double x = 0.5 * (t00 + t11), y = sqrt(y2);
+
+  const int lane = threadIdx.x & 31, row = lane & 15;
+  const bool im = lane >= 16;
+  double a[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    double v = 0.0;
+    if (row < n && c < n) v = im ? ((c == row) ? y : 0.0) : Cg[row + n * c] + ((c == row) ? x : 0.0);
+    a[c] = v;
+  }
+  bool sing = false;
+  uint64_t piv;
+  const int kr = warp_gj_inplace_c(a, piv, n, sing);
+  // coefficients (recomputed here to keep them out of the elimination's registers):
+  // w = (b01, -hd + i y); 1 / det W = i idet, idet = 1 / (2 y b01);
+  // u = [W^-1]_{0.} = ((y - i hd) idet, -i b01 idet); c_ab = D_a w_a u_b / D_b
+  t00 = Tg[j + n * j];
+  t01 = Tg[j + n * (j + 1)];
+  t10 = Tg[(j + 1) + n * j];
+  t11 = Tg[(j + 1) + n * (j + 1)];
+  d = sqrt(-t10 / t01);
+  b01 = t01 * d;
+  hd = 0.5 * (t00 - t11);
+  const double idet = 1.0 / (2.0 * y * b01);
+  const double u0r = y * idet, u0i = -hd * idet, u1i = -b01 * idet;
+  // re lanes: blocks (0, 0), (0, 1); im lanes: (1, 0), (1, 1)
+  double car0, cai0, car1, cai1;
+  if (!im) {
+    car0 = b01 * u0r;
+    cai0 = b01 * u0i;
+    car1 = 0.0;
+    cai1 = b01 * u1i / d;
+  } else {
+    car0 = (-hd * u0r - y * u0i) * d;
+    cai0 = (-hd * u0i + y * u0r) * d;
+    car1 = -y * u1i;
+    cai1 = -hd * u1i;
+  }
+  const int ab = im ? 1 : 0;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const double own = a[c];
+    const double oth = __shfl_xor_sync(0xffffffffu, own, 16);
+    if (c < n && kr >= 0) {
+      const double yr = im ? oth : own, yi = im ? own : oth;
+      const int kc = (int)((piv >> (4 * c)) & 15u);
+      Ge[g_index(n, j, ab * n + kr, kc)] = 2.0 * (car0 * yr - cai0 * yi);
+      Ge[g_index(n, j, ab * n + kr, n + kc)] = 2.0 * (car1 * yr - cai1 * yi);
+    }
+  }
+  return 1 | (sing ? 2 : 0);
+}
+
+// n <= M / 2: one warp per element.  1x1 blocks: register Gauss-Jordan (lanes
+// own rows); 2x2 blocks: the complex form above, else (nearly defective
+// blocks) a bit in fb[e] for k_shift_inv_fb, which inverts the real 2n x 2n
+// system.
 template <int M>
 __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const double* T1,
                                                      const double* C2, const uint32_t* masks,
-                                                     int32_t* flags, double* G, DevStatus* st) {
+                                                     int32_t* flags, double* G, uint32_t* fb,
+                                                     DevStatus* st) {
   const int nn = n * n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1010,14 +1319,48 @@ __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const dou
     if (sblk == 1 && !pairj) Ge[q] = 0.0;
   }
   bool sing = false;
+  uint32_t fbits = 0;
   int j = 0;
   while (j < n) {
     const bool pair = ((m1 >> j) & 1u) && j + 1 < n;
-    sing |= pair ? shift_inv_block<M>(Tg, Cg, rank1, n, j, 2 * n, Ge)
-                 : shift_inv_block<M / 2>(Tg, Cg, rank1, n, j, n, Ge);
+    if (pair) {
+      const int pc = rank1 ? 0 : shift_inv_pair_c(Tg, Cg, n, j, Ge);
+      if (pc) sing |= (pc & 2) != 0;
+      else fbits |= 1u << j;
+    } else {
+      sing |= shift_inv_block<M / 2>(Tg, Cg, rank1, n, j, n, Ge);
+    }
     j += pair ? 2 : 1;
   }
-  if (lane == 0 && sing) {
+  if (lane == 0) {
+    fb[e] = fbits;
+    if (sing) {
+      atomicOr(reinterpret_cast<int*>(flags + e), 8);
+      atomicAdd(&st->build_singular, 1);
+    }
+  }
+}
+
+// the real 2n x 2n inverses of the 2x2 blocks k_shift_inv_r left (bits of fb[e])
+template <int M>
+__global__ void __launch_bounds__(128) k_shift_inv_fb(int n, int64_t E, const double* T1,
+                                                      const double* C2, int32_t* flags, double* G,
+                                                      const uint32_t* fb, DevStatus* st) {
+  const int nn = n * n;
+  const int warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;
+  uint32_t bits = fb[e];
+  if (!bits) return;
+  const bool rank1 = (flags[e] & 2) != 0;
+  bool sing = false;
+  while (bits) {
+    const int j = __ffs(bits) - 1;
+    bits &= bits - 1;
+    sing |= shift_inv_block<M>(T1 + e * nn, C2 + e * nn, rank1, n, j, 2 * n,
+                               G + (size_t)e * 2 * n * nn);
+  }
+  if ((threadIdx.x & 31) == 0 && sing) {
     atomicOr(reinterpret_cast<int*>(flags + e), 8);
     atomicAdd(&st->build_singular, 1);
   }
@@ -1275,7 +1618,12 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
   ia.cond = c->p<double>(c->L.fSC);
   ia.flags = c->p<int32_t>(c->L.flags);
   ia.st = st;
-  {
+  if (n <= 16) {
+    k_invert_r<<<(unsigned)((E + 3) / 4), 128, 0, s>>>(ia);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  } else {
     const int warps = 2;
     const size_t smem = (size_t)warps * (4 * nn + 2 * n + 8) * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_invert_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1309,10 +1657,16 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
     int32_t* fl = c->p<int32_t>(c->L.flags);
     double* Gp = c->p<double>(c->L.fG);
     cudaError_t err;
+    uint32_t* fb = reinterpret_cast<uint32_t*>(c->p<int>(c->L.biscr));   // free after the KSVD
+    const unsigned gw = (unsigned)((E + 3) / 4);
     if (n <= 8) {
-      k_shift_inv_r<16><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, st);
+      k_shift_inv_r<16><<<gw, 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, fb, st);
+      count_launch();
+      k_shift_inv_fb<16><<<gw, 128, 0, s>>>(n, E, T1p, C2p, fl, Gp, fb, st);
     } else if (n <= 16) {
-      k_shift_inv_r<32><<<(unsigned)((E + 3) / 4), 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, st);
+      k_shift_inv_r<32><<<gw, 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, fb, st);
+      count_launch();
+      k_shift_inv_fb<32><<<gw, 128, 0, s>>>(n, E, T1p, C2p, fl, Gp, fb, st);
     } else {
       const size_t smem = (size_t)(8 * nn + 2 * n + 8) * sizeof(double);
       err = cudaFuncSetAttribute(k_shift_inv_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
