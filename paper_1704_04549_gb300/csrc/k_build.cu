@@ -197,30 +197,10 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
 }
 
 // ---- Golub-Kahan tridiagonal T (zero diagonal, off-diagonal e, size m) ------
-// Number of eigenvalues of T below x by the sign changes of the leading
-// principal minors of T - x I (Sturm sequence): D_0 = 1, D_1 = -x,
-// D_k = -x D_{k-1} - e_{k-2}^2 D_{k-2}.  e2 holds e^2 of the tridiagonal
-// scaled to spectral radius <= 1, so no division is needed; an occasional
-// rescale keeps D in range.
-__device__ int sturm_count_df(const double* e2, int m, double x) {
-  double d0 = 1.0, d1 = -x;
-  int cnt = (d1 < 0.0) ? 1 : 0;
-  bool neg_prev = d1 < 0.0;
-  for (int k = 2; k <= m; ++k) {
-    double d2 = fma(-x, d1, -e2[k - 2] * d0);
-    bool neg = d2 < 0.0;
-    if (d2 == 0.0) neg = !neg_prev;              // a zero minor counts as a sign change
-    cnt += (neg != neg_prev) ? 1 : 0;
-    neg_prev = neg;
-    d0 = d1;
-    d1 = d2;
-    if ((k & 31) == 0 && fabs(d1) < 1e-200 && fabs(d0) < 1e-200) {
-      d0 *= 1e200;
-      d1 *= 1e200;
-    }
-  }
-  return cnt;
-}
+// Sturm counts: sturm_count_gk (k_ksvd_tri) counts the eigenvalues of T below x
+// by the sign changes of the leading principal minors of T - x I: D_0 = 1,
+// D_1 = -x, D_k = -x D_{k-1} - e_{k-2}^2 D_{k-2}, with e scaled to spectral
+// radius <= 1 (no division) and an occasional rescale to keep D in range.
 
 // Inverse iteration on T - lam I (Gaussian elimination with partial pivoting,
 // pivots inverted once); z in/out, work arrays of length m each.
@@ -567,7 +547,21 @@ __device__ void form_core(const double* Cx, const double* Cy, const double* Dg, 
   }
 }
 
-// ---- k_ksvd_w ---------------------------------------------------------------
+// ---- KSVD in three stages (one-thread scalar work is split out: on GB300 an
+// FP64 warp instruction costs the pipe the same with 1 or 32 active lanes):
+//  k_ksvd_w    warp per element: core M, Householder bidiagonalisation; the
+//              warp's shared-memory image goes to the element's scratch,
+//  k_ksvd_tri  thread per (element, k), k = 0, 1: k-th largest eigenvalue of
+//              the Golub-Kahan tridiagonal (bisection on Sturm counts) and its
+//              eigenvector (inverse iteration),
+//  k_ksvd_vec  warp per element: singular vectors back in M coordinates
+//              (reflectors last to first) and the factors A_k, B_k.
+// Scratch per element (doubles): the image (ksvd_smem total) then 16 r of
+// tridiagonal work; ksvd_scr_stride() of them.
+__host__ __device__ inline size_t ksvd_scr_stride(int n, int rz) {
+  return (size_t)ksvd_smem(n, rz).total + 16 * (size_t)(n + rz);
+}
+
 __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   extern __shared__ double smk[];
   const int n = A.n, rz = A.rz, nc = n + 2, r = n + rz, nn = n * n, Ro = nn - n;
@@ -578,13 +572,8 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   double* sm = smk + (size_t)warp * L.total;
   double* Ms = sm + L.M;
   const int ld = L.ldm;
-  double *al = sm + L.al, *be = sm + L.be, *ee = sm + L.ee, *e2s = sm + L.e2s;
-  double *z1 = sm + L.z1, *z2 = sm + L.z2, *tl = sm + L.tl, *tr = sm + L.tr;
-  double *mu1 = sm + L.mu1, *mv1 = sm + L.mv1, *mu2 = sm + L.mu2, *mv2 = sm + L.mv2;
-  double* scal = sm + L.scal;
-  double* tw = A.scr + (size_t)e * (2 * (size_t)r * r + 16 * (size_t)r) + 2 * (size_t)r * r;
-  int* piv = A.iscr + (size_t)e * 4 * r;
-  const int64_t base = e * nn;
+  double *al = sm + L.al, *be = sm + L.be, *tl = sm + L.tl, *tr = sm + L.tr;
+  double* Sg = A.scr + (size_t)e * ksvd_scr_stride(n, rz);
   const double* kc = A.kco + (size_t)e * (2 * nc * n + nn);
   const double *Cx = kc, *Cy = kc + nc * n, *Dg = kc + 2 * nc * n;
 
@@ -659,67 +648,118 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
       __syncwarp();
     }
   }
-  const int J = r;
+  __syncwarp();
+  for (int q = lane; q < L.total; q += 32) Sg[q] = sm[q];
+  (void)Ro;
+}
 
-  // ---- top-2 singular values / vectors of the bidiagonal B through its
-  // Golub-Kahan tridiagonal (order 2r, zero diagonal)
-  {
-    const int m = 2 * J;
-    for (int t = lane; t < m - 1; t += 32) ee[t] = (t & 1) ? be[(t + 1) >> 1] : al[t >> 1];
-    __syncwarp();
-    double bnd = 0.0;
+// Sturm count of the scaled Golub-Kahan tridiagonal with off-diagonal
+// ee(t) = (t odd ? be[(t + 1) / 2] : al[t / 2]) * ib (one thread)
+__device__ int sturm_count_gk(const double* al, const double* be, double ib, int m, double x) {
+  double d0 = 1.0, d1 = -x;
+  int cnt = (d1 < 0.0) ? 1 : 0;
+  bool neg_prev = d1 < 0.0;
+  for (int k = 2; k <= m; ++k) {
+    const int t = k - 2;
+    const double es = ((t & 1) ? be[(t + 1) >> 1] : al[t >> 1]) * ib;
+    double d2 = fma(-x, d1, -(es * es) * d0);
+    bool neg = d2 < 0.0;
+    if (d2 == 0.0) neg = !neg_prev;              // a zero minor counts as a sign change
+    cnt += (neg != neg_prev) ? 1 : 0;
+    neg_prev = neg;
+    d0 = d1;
+    d1 = d2;
+    if ((k & 31) == 0 && fabs(d1) < 1e-200 && fabs(d0) < 1e-200) {
+      d0 *= 1e200;
+      d1 *= 1e200;
+    }
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(128) k_ksvd_tri(KsvdArgs A) {
+  const int n = A.n, rz = A.rz, r = n + rz;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = t >> 1;
+  const int k = (int)(t & 1);
+  if (e >= A.E) return;
+  if (A.mask && !A.mask[e]) return;
+  const KsvdSmem L = ksvd_smem(n, rz);
+  double* S = A.scr + (size_t)e * ksvd_scr_stride(n, rz);
+  const double *al = S + L.al, *be = S + L.be;
+  const int J = r, m = 2 * J;
+  if (k >= J) {
+    S[L.scal + k] = 0.0;
+    return;
+  }
+  double bnd = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double a = (i > 0) ? fabs(((i - 1) & 1) ? be[i >> 1] : al[(i - 1) >> 1]) : 0.0;
+    const double b = (i < m - 1) ? fabs((i & 1) ? be[(i + 1) >> 1] : al[i >> 1]) : 0.0;
+    bnd = fmax(bnd, a + b);
+  }
+  if (bnd == 0.0) bnd = 1.0;
+  const double ib = 1.0 / bnd;
+  // bisection for the (m - k)-th smallest eigenvalue of the scaled tridiagonal in [0, 1]
+  // (to 2^-30 of the bound: the shift of the inverse iteration below; the value
+  // itself is the Rayleigh quotient of the converged vector, accurate to the
+  // square of the vector's error)
+  const int idx = m - k;
+  double lo = 0.0, hi = 1.0 + 1e-12;
+  for (int it = 0; it < 30; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count_gk(al, be, ib, m, mid) >= idx) hi = mid;
+    else lo = mid;
+  }
+  const double lam = 0.5 * (lo + hi) * bnd;
+  // eigenvector by inverse iteration on the unscaled tridiagonal, in this thread's
+  // 4m of work (d, du, du2, dl; dl starts as the off-diagonal, which the
+  // factorisation reads entry by entry before overwriting it)
+  double* w0 = S + L.total + (size_t)k * 4 * m;
+  int* piv = A.iscr + (size_t)e * 4 * r + (size_t)k * m;
+  double* z = S + (k ? L.z2 : L.z1);
+  double* dl = w0 + 3 * m;
+  for (int i = 0; i < m - 1; ++i) dl[i] = (i & 1) ? be[(i + 1) >> 1] : al[i >> 1];
+  for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + k, i);
+  inverse_iteration(dl, m, lam, z, w0, w0 + m, w0 + 2 * m, dl, piv, kEps * bnd + 1e-300);
+  // Rayleigh quotient z^T T z = 2 sum_i ee_i z_i z_{i+1} (|z| = 1; zero diagonal)
+  double rq = 0.0;
+  for (int i = 0; i < m - 1; ++i) rq = fma((i & 1) ? be[(i + 1) >> 1] : al[i >> 1], z[i] * z[i + 1], rq);
+  S[L.scal + k] = 2.0 * rq;
+}
+
+__global__ void __launch_bounds__(128) k_ksvd_vec(KsvdArgs A) {
+  extern __shared__ double smk[];
+  const int n = A.n, rz = A.rz, r = n + rz, nn = n * n, Ro = nn - n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= A.E) return;
+  if (A.mask && !A.mask[e]) return;
+  const KsvdSmem L = ksvd_smem(n, rz);
+  double* sm = smk + (size_t)warp * L.total;
+  const double* Sg = A.scr + (size_t)e * ksvd_scr_stride(n, rz);
+  for (int q = lane; q < L.total; q += 32) sm[q] = Sg[q];
+  __syncwarp();
+  double* Ms = sm + L.M;
+  const int ld = L.ldm;
+  double *z1 = sm + L.z1, *z2 = sm + L.z2, *tl = sm + L.tl, *tr = sm + L.tr;
+  double *mu1 = sm + L.mu1, *mv1 = sm + L.mv1, *mu2 = sm + L.mu2, *mv2 = sm + L.mv2;
+  double* scal = sm + L.scal;
+  const int64_t base = e * nn;
+  const int J = r, m = 2 * J;
+  if (J >= 2) {         // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
+    double dt = 0.0;
+    for (int i = lane; i < m; i += 32) dt += z1[i] * z2[i];
+    dt = warp_sum(dt);
+    double nr = 0.0;
     for (int i = lane; i < m; i += 32) {
-      const double sv = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < m - 1 ? fabs(ee[i]) : 0.0);
-      bnd = fmax(bnd, sv);
+      const double v = z2[i] - dt * z1[i];
+      z2[i] = v;
+      nr += v * v;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
-    if (bnd == 0.0) bnd = 1.0;
-    const double ib = 1.0 / bnd;
-    for (int i = lane; i < m - 1; i += 32) {
-      const double es = ee[i] * ib;
-      e2s[i] = es * es;
-    }
-    __syncwarp();
-    {
-      // multisection: lanes 0-15 bracket the largest eigenvalue, 16-31 the second
-      const int grp = lane >> 4, gl = lane & 15;
-      const int idx = m - grp;
-      double lo = 0.0, hi = 1.0 + 1e-12;
-      for (int it = 0; it < 14; ++it) {
-        const double x = lo + (hi - lo) * (double)(gl + 1) * (1.0 / 17.0);
-        const int cnt = sturm_count_df(e2s, m, x);
-        const unsigned ge = __ballot_sync(0xffffffffu, cnt >= idx);
-        const unsigned mine = (ge >> (grp * 16)) & 0xffffu;
-        const int f = mine ? (__ffs(mine) - 1) : 16;
-        const double w = hi - lo;
-        const double nlo = (f == 0) ? lo : lo + w * (double)f * (1.0 / 17.0);
-        const double nhi = (f == 16) ? hi : lo + w * (double)(f + 1) * (1.0 / 17.0);
-        lo = nlo;
-        hi = nhi;
-      }
-      if (gl == 0) scal[grp] = (grp < J) ? 0.5 * (lo + hi) * bnd : 0.0;
-    }
-    __syncwarp();
-    if (lane < 2 && lane < J) {        // inverse iteration, lanes 0 and 1 in lockstep
-      double* z = lane ? z2 : z1;
-      for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + lane, i);
-      double* w0 = tw + lane * 4 * m;
-      inverse_iteration(ee, m, scal[lane], z, w0, w0 + m, w0 + 2 * m, w0 + 3 * m, piv + lane * m,
-                        kEps * bnd + 1e-300);
-    }
-    __syncwarp();
-    if (lane == 0 && J >= 2) {         // z2 orthogonal to z1 (matters if sigma_1 ~ sigma_2)
-      double dt = 0.0;
-      for (int i = 0; i < m; ++i) dt += z1[i] * z2[i];
-      double nr = 0.0;
-      for (int i = 0; i < m; ++i) {
-        z2[i] -= dt * z1[i];
-        nr += z2[i] * z2[i];
-      }
-      nr = 1.0 / sqrt(nr);
-      for (int i = 0; i < m; ++i) z2[i] *= nr;
-    }
+    nr = warp_sum(nr);
+    const double inr = 1.0 / sqrt(nr);
+    for (int i = lane; i < m; i += 32) z2[i] *= inr;
     __syncwarp();
   }
   const int nsv = (J >= 2) ? 2 : 1;
@@ -1495,6 +1535,8 @@ __global__ void __launch_bounds__(128) k_learned_accept(int n, int64_t E, const 
   }
 }
 
+size_t ksvd_scr_doubles(int n, int rz) { return ksvd_scr_stride(n, rz); }
+
 cudaError_t launch_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double* norms,
                                   cudaStream_t s) {
   k_coef_2d<<<152 * 4, 256, 0, s>>>(
@@ -1599,6 +1641,14 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
                                            (int)smem);
     if (err != cudaSuccess) return err;
     k_ksvd_w<<<(unsigned)((E + warps - 1) / warps), warps * 32, smem, s>>>(ka);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    k_ksvd_tri<<<(unsigned)((2 * E + 127) / 128), 128, 0, s>>>(ka);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_ksvd_vec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_ksvd_vec<<<(unsigned)((E + warps - 1) / warps), warps * 32, smem, s>>>(ka);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }

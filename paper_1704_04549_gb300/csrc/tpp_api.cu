@@ -177,7 +177,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.masks = take((size_t)E * 2 * 4);
   {
     const size_t r = (size_t)n + rz;
-    L.bscr = take((size_t)E * (2 * r * r + 16 * r) * 8);
+    L.bscr = take((size_t)E * ksvd_scr_doubles(n, rz) * 8);
     L.biscr = take((size_t)E * 4 * r * 4);
     // coefficients of the 2D-structured block fed to the KSVD (2D: the element
     // block; 3D: the second-stage block D1): Cx, Cy ((n+2) x n each), Dg (n x n)

@@ -195,6 +195,7 @@ cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const doub
                                   const double* lossv, double threshold, int32_t* mask,
                                   cudaStream_t s);
 void mlp_forward(tpp_mlp* net, const float* X, int B, float* out, cudaStream_t s);
+size_t ksvd_scr_doubles(int n, int rz);   // KSVD scratch per element (doubles)
 int mlp_n(const tpp_mlp* net);
 int mlp_max_batch(const tpp_mlp* net);
 cudaError_t mlp_factor_loss(const float* out, const double* Mn, const double* Qo, int n, int rz,
