@@ -196,6 +196,188 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
   return true;
 }
 
+// ---- two real Schur forms per warp (n <= 16), one per half-warp -----------
+// The algorithm of warp_real_schur (Householder Hessenberg reduction, Francis
+// double-shift sweeps with deflation from the bottom) run by each half-warp on
+// its own matrix in lockstep: the bulge-chasing loop runs to the longer of the
+// two active windows and a half whose matrix has converged idles.  Every FP64
+// instruction then serves two matrices (on GB300 a warp FP64 instruction costs
+// the pipe the same with 16 or 32 active lanes).  Deflation: the negligible
+// subdiagonal entries of a half are found in parallel (one lane per position,
+// a ballot) and the window update is integer work.
+__device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, bool empty) {
+  const int lane = threadIdx.x & 31, hl = lane & 15, hb = lane & 16;
+  for (int c = 0; c < n; ++c)
+    if (hl < n) Q[hl + ld * c] = (hl == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k = 0; k + 2 < n; ++k) {                 // Hessenberg reduction (uniform)
+    const int L = n - k - 1;
+    const double xh = (1 + hl < L) ? H[(k + 1 + 1 + hl) + ld * k] : 0.0;
+    double tail = xh * xh;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+    const double alpha = H[(k + 1) + ld * k];
+    const double nrm = sqrt(alpha * alpha + tail);
+    const double v0 = alpha + copysign(nrm, alpha);
+    const double den = v0 * v0 + tail;
+    const double inv = (tail != 0.0) ? 1.0 / sqrt(den) : 0.0;   // tail = 0: identity
+    if (hl < L) vb[hb + hl] = (hl == 0 ? v0 : H[(k + 1 + hl) + ld * k]) * inv;
+    __syncwarp();
+    const double* v = vb + hb;
+    if (k + hl < n) {                               // left: rows k+1.., column k + hl
+      const int c = k + hl;
+      double d = 0.0;
+      for (int i = 0; i < L; ++i) d += v[i] * H[(k + 1 + i) + ld * c];
+      d *= 2.0;
+      for (int i = 0; i < L; ++i) H[(k + 1 + i) + ld * c] -= d * v[i];
+    }
+    __syncwarp();
+    if (hl < n) {                                   // right: columns k+1.., row hl
+      const int r = hl;
+      double d = 0.0, dq = 0.0;
+      for (int i = 0; i < L; ++i) {
+        d += H[r + ld * (k + 1 + i)] * v[i];
+        dq += Q[r + ld * (k + 1 + i)] * v[i];
+      }
+      d *= 2.0;
+      dq *= 2.0;
+      for (int i = 0; i < L; ++i) {
+        H[r + ld * (k + 1 + i)] -= d * v[i];
+        Q[r + ld * (k + 1 + i)] -= dq * v[i];
+      }
+    }
+    __syncwarp();
+    if (inv != 0.0 && 2 + hl < L + 1) H[(k + 2 + hl) + ld * k] = 0.0;
+    __syncwarp();
+  }
+  double amax = 0.0;
+  for (int c = 0; c < n; ++c)
+    if (hl < n) amax = fmax(amax, fabs(H[hl + ld * c]));
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  int hi = (empty || amax == 0.0) ? 0 : n - 1, its = 0, total = 0;
+  bool fail = false;
+  const int maxit = 40 * (n > 8 ? n : 8);
+  while (true) {
+    // negligible subdiagonal entries (position i = hl + 1: H[i][i-1])
+    bool small = false;
+    {
+      const int i = hl + 1;
+      if (i < n && hi > 0) {
+        double sc = fabs(H[(i - 1) + ld * (i - 1)]) + fabs(H[i + ld * i]);
+        if (sc == 0.0) sc = amax;
+        small = fabs(H[i + ld * (i - 1)]) <= kEps * sc;
+      }
+    }
+    const unsigned mine = (__ballot_sync(0xffffffffu, small) >> hb) & 0xffffu;
+    __syncwarp();
+    if (small && hl + 1 <= hi) H[(hl + 1) + ld * hl] = 0.0;
+    int l = 0;
+    while (hi > 0) {                                // deflation: integer work
+      const unsigned mm = mine & ((hi >= 16) ? 0xffffu : ((1u << hi) - 1u));
+      l = mm ? (32 - __clz(mm)) : 0;
+      if (l == hi) { --hi; its = 0; continue; }
+      if (l == hi - 1) { hi -= 2; its = 0; continue; }
+      break;
+    }
+    bool go = hi > 0 && !fail;
+    if (go) {
+      ++its;
+      if (++total > maxit) {
+        fail = true;
+        go = false;
+      }
+    }
+    if (!__any_sync(0xffffffffu, go)) break;
+    __syncwarp();
+    // shifts (indices clamped for an idle half; its values are not used)
+    const int h2 = go ? hi : 2, l2 = go ? l : 0;
+    double sh, t;
+    if (its % 10 == 0) {
+      const double mu = H[h2 + ld * h2] +
+                        0.75 * (fabs(H[h2 + ld * (h2 - 1)]) + fabs(H[(h2 - 1) + ld * (h2 - 2)]));
+      sh = 2.0 * mu;
+      t = mu * mu;
+    } else {
+      const double a = H[(h2 - 1) + ld * (h2 - 1)], b = H[(h2 - 1) + ld * h2];
+      const double c = H[h2 + ld * (h2 - 1)], d = H[h2 + ld * h2];
+      sh = a + d;
+      t = a * d - b * c;
+    }
+    const double h00 = H[l2 + ld * l2], h01 = H[l2 + ld * (l2 + 1)];
+    const double h10 = H[(l2 + 1) + ld * l2], h11 = H[(l2 + 1) + ld * (l2 + 1)];
+    const double h21 = H[(l2 + 2) + ld * (l2 + 1)];
+    double xv[3] = {h00 * h00 + h01 * h10 - sh * h00 + t, h10 * (h00 + h11 - sh), h10 * h21};
+    double v[3];
+    const int nst = go ? hi - 1 - l : 0;            // bulge steps k = l .. hi - 2
+    const int nmax = max(nst, __shfl_xor_sync(0xffffffffu, nst, 16));
+    for (int kk = 0; kk < nmax; ++kk) {
+      const int k = l2 + kk;
+      const bool a = kk < nst;
+      house_vec(xv, 3, v);
+      const int q = (k - 1 > l2) ? k - 1 : l2;
+      if (a && q + hl < n) {
+        double* col = H + ld * (q + hl);
+        const double d = 2.0 * (v[0] * col[k] + v[1] * col[k + 1] + v[2] * col[k + 2]);
+        col[k] -= d * v[0];
+        col[k + 1] -= d * v[1];
+        col[k + 2] -= d * v[2];
+      }
+      __syncwarp();
+      if (a && hl < n) {
+        const int r = hl;
+        const int rmax = (k + 3 < hi) ? k + 3 : hi;
+        if (r <= rmax) {
+          const double d = 2.0 * (H[r + ld * k] * v[0] + H[r + ld * (k + 1)] * v[1] +
+                                  H[r + ld * (k + 2)] * v[2]);
+          H[r + ld * k] -= d * v[0];
+          H[r + ld * (k + 1)] -= d * v[1];
+          H[r + ld * (k + 2)] -= d * v[2];
+        }
+        const double dq = 2.0 * (Q[r + ld * k] * v[0] + Q[r + ld * (k + 1)] * v[1] +
+                                 Q[r + ld * (k + 2)] * v[2]);
+        Q[r + ld * k] -= dq * v[0];
+        Q[r + ld * (k + 1)] -= dq * v[1];
+        Q[r + ld * (k + 2)] -= dq * v[2];
+      }
+      __syncwarp();
+      if (a && k > l2 && hl == 0) {
+        H[(k + 1) + ld * (k - 1)] = 0.0;
+        H[(k + 2) + ld * (k - 1)] = 0.0;
+      }
+      __syncwarp();
+      if (a) {                                      // a finished half keeps its last bulge
+        xv[0] = H[(k + 1) + ld * k];
+        xv[1] = H[(k + 2) + ld * k];
+        xv[2] = (k < hi - 2) ? H[(k + 3) + ld * k] : 0.0;
+      }
+    }
+    house_vec(xv, 2, v);
+    if (go && (h2 - 2) + hl < n) {
+      double* col = H + ld * ((h2 - 2) + hl);
+      const double d = 2.0 * (v[0] * col[h2 - 1] + v[1] * col[h2]);
+      col[h2 - 1] -= d * v[0];
+      col[h2] -= d * v[1];
+    }
+    __syncwarp();
+    if (go && hl < n) {
+      const int r = hl;
+      if (r <= h2) {
+        const double d = 2.0 * (H[r + ld * (h2 - 1)] * v[0] + H[r + ld * h2] * v[1]);
+        H[r + ld * (h2 - 1)] -= d * v[0];
+        H[r + ld * h2] -= d * v[1];
+      }
+      const double dq = 2.0 * (Q[r + ld * (h2 - 1)] * v[0] + Q[r + ld * h2] * v[1]);
+      Q[r + ld * (h2 - 1)] -= dq * v[0];
+      Q[r + ld * h2] -= dq * v[1];
+    }
+    __syncwarp();
+    if (go && hl == 0) H[h2 + ld * (h2 - 2)] = 0.0;
+    __syncwarp();
+  }
+  return !fail;
+}
+
 // ---- Golub-Kahan tridiagonal T (zero diagonal, off-diagonal e, size m) ------
 // Sturm counts: sturm_count_gk (k_ksvd_tri) counts the eigenvalues of T below x
 // by the sign changes of the leading principal minors of T - x I: D_0 = 1,
@@ -1180,6 +1362,49 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, doub
   }
 }
 
+// ---- k_schur_w2: k_schur_w with two matrices per warp (n <= 16)
+__global__ void __launch_bounds__(128) k_schur_w2(int n, int64_t E, int mpe, double* T1,
+                                                  double* T2, double* Q1, double* Q2,
+                                                  uint32_t* masks, int32_t* flags, DevStatus* st) {
+  extern __shared__ double sms[];
+  const int nn = n * n, ld = ld_of(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hl = lane & 15, h = lane >> 4;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (2 * gw >= mpe * E) return;                     // whole warp
+  const int64_t mtx = 2 * gw + h;
+  const bool empty = mtx >= mpe * E;
+  const int64_t e = empty ? 0 : mtx / mpe;
+  const int which = empty ? 0 : (int)(mtx % mpe);
+  double* H = sms + (size_t)(2 * warp + h) * (2 * n * ld + 16);
+  double* Q = H + n * ld;
+  double* vb = sms + (size_t)8 * (2 * n * ld + 16) + (size_t)warp * 32;
+  double* Tg = (which ? T2 : T1) + e * nn;
+  double* Qg = (which ? Q2 : Q1) + e * nn;
+  const bool rank1 = empty || (flags[e] & 2) != 0;
+  for (int c = 0; c < n; ++c)
+    if (hl < n) H[hl + ld * c] = rank1 ? ((which && hl == c && !empty) ? 1.0 : 0.0) : Tg[hl + n * c];
+  __syncwarp();
+  const bool ok = hw_real_schur(H, Q, n, ld, vb, rank1);
+  if (!empty) {
+    for (int c = 0; c < n; ++c)
+      if (hl < n) {
+        Tg[hl + n * c] = H[hl + ld * c];
+        Qg[hl + n * c] = Q[hl + ld * c];
+      }
+    if (hl == 0) {
+      uint32_t m = 0;
+      for (int i = 0; i + 1 < n; ++i)
+        if (H[(i + 1) + ld * i] != 0.0) m |= 1u << i;
+      masks[2 * e + which] = m;
+      if (mpe == 1) masks[2 * e + 1] = 0u;
+      if (!ok && !rank1) {
+        atomicOr(reinterpret_cast<int*>(flags + e), 4);
+        atomicAdd(&st->build_schur_fail, 1);
+      }
+    }
+  }
+}
+
 // ---- k_final_w: S_A = Q1^T L_A^-1, S_B = Q2^T L_B^-1 (in place over the staged inverses)
 // (mpe = 2: both; mpe = 1: S_A only)
 __global__ void __launch_bounds__(128) k_final_w(int n, int64_t E, int mpe, double* SA,
@@ -1686,7 +1911,20 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
   // 3. real Schur forms: C_1 and C_2 (two-sided form), or C_1 only
   const bool two = two_sided(c);
   const int mpe = two ? 2 : 1;
-  {
+  if (n <= 16) {
+    const int ld = ld_of(n);
+    const size_t smem = ((size_t)8 * (2 * n * ld + 16) + 4 * 32) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_schur_w2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    const int64_t warps_needed = (mpe * E + 1) / 2;
+    k_schur_w2<<<(unsigned)((warps_needed + 3) / 4), 128, smem, s>>>(
+        n, E, mpe, c->p<double>(c->L.fT1), c->p<double>(c->L.fT2), c->p<double>(c->L.fQ1),
+        two ? c->p<double>(c->L.fQ2) : nullptr, c->p<uint32_t>(c->L.masks),
+        c->p<int32_t>(c->L.flags), st);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  } else   {
     const int warps = 4, ld = ld_of(n);
     const size_t smem = (size_t)warps * (2 * n * ld + 32) * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_schur_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
