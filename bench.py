@@ -641,6 +641,22 @@ def run_kernels(args):
     """Kernel-only pass for profilers: one factor build, then a few launches of
     each hot-path kernel on the same workload (no GMRES loop)."""
     import torch
+    if args.workload == "learned":         # network forward (4096 elements), loss, one train
+        from paper_1704_04549_gb300 import TPP_FEAT_LEARNED, Context   # step, learned build
+        from paper_1704_04549_gb300 import learned as LN
+        w = workload(16)
+        ctx = Context(2, 16, w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                      features=TPP_FEAT_LEARNED)
+        net = LN.Mlp(16, max_batch=4096, params=LN.default_params(16, 1800))
+        X, Mn, _ = ctx.tpp_learned_inputs()
+        net.forward(X)
+        net.element_loss(ctx, X, Mn)
+        net.train_step(ctx, X[:512], Mn[:512], 1e-3)
+        ctx.tpp_build_factors_learned(net, 0.05)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernels", "workload": "learned", "n": 16,
+                          "elements": ctx.num_elem}))
+        return 0
     from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, Context
     w = workload_3d(args.n if args.n != 16 else 11) if args.workload == "adv3d" else workload(args.n)
     ctx = Context(w["dim"], w["n"], w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,

@@ -405,8 +405,20 @@ k_apply_2d_g(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ L
       Fa[q] = inblk ? (T)0 : T1[gf + q];
     }
   __syncwarp(gmask);
-  // ---- column sweep, last column first
+  // ---- column sweep, last column first.  FP32: the rows of the next column's
+  // inverses are loaded one column ahead (their addresses do not depend on the
+  // sweep), so the global-load latency overlaps the current column's work.
+  constexpr bool PF = sizeof(T) == 4 && NM <= 16;
   T rsave = (T)0;
+  T cs[PF ? NM : 1], cp[PF ? NM : 1];
+  if constexpr (PF) {
+    const T* gs0 = Ge + (size_t)(2 * (n - 1)) * nn + (rok ? i : 0);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      cs[k] = (k < n) ? gs0[(size_t)k * n] : (T)0;
+      cp[k] = (k < n) ? gs0[nn + (size_t)k * n] : (T)0;
+    }
+  }
 #pragma unroll
   for (int jj = NM - 1; jj >= 0; --jj) {
     if (jj < n) {
@@ -421,19 +433,39 @@ k_apply_2d_g(int n, int64_t E, const T* __restrict__ SA, const T* __restrict__ L
         Wm[NM + i] = rp;
       }
       __syncwarp(gmask);
-      const T* gs = Ge + (size_t)(2 * jj) * nn + (rok ? i : 0);   // idle lanes read row 0
       T z0 = (T)0, z1 = (T)0;
+      if constexpr (PF) {
+        T ns[NM], np[NM];
+        const T* gn = Ge + (size_t)(2 * (jj > 0 ? jj - 1 : 0)) * nn + (rok ? i : 0);
 #pragma unroll
-      for (int k = 0; k < NM; k += 2) {
-        if (k < n) z0 += gs[(size_t)k * n] * Wm[k];
-        if (k + 1 < n) z1 += gs[(size_t)(k + 1) * n] * Wm[k + 1];
-      }
-      if (__any_sync(0xffffffffu, eok && (lo || up))) {
-        const T* gp = gs + nn;
+        for (int k = 0; k < NM; ++k) {
+          ns[k] = (jj > 0 && k < n) ? gn[(size_t)k * n] : (T)0;
+          np[k] = (jj > 0 && k < n) ? gn[nn + (size_t)k * n] : (T)0;
+        }
 #pragma unroll
         for (int k = 0; k < NM; k += 2) {
-          if (k < n) z0 += gp[(size_t)k * n] * Wm[NM + k];
-          if (k + 1 < n) z1 += gp[(size_t)(k + 1) * n] * Wm[NM + k + 1];
+          if (k < n) z0 += cs[k] * Wm[k] + cp[k] * Wm[NM + k];
+          if (k + 1 < n) z1 += cs[k + 1] * Wm[k + 1] + cp[k + 1] * Wm[NM + k + 1];
+        }
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          cs[k] = ns[k];
+          cp[k] = np[k];
+        }
+      } else {
+        const T* gs = Ge + (size_t)(2 * jj) * nn + (rok ? i : 0);   // idle lanes read row 0
+#pragma unroll
+        for (int k = 0; k < NM; k += 2) {
+          if (k < n) z0 += gs[(size_t)k * n] * Wm[k];
+          if (k + 1 < n) z1 += gs[(size_t)(k + 1) * n] * Wm[k + 1];
+        }
+        if (__any_sync(0xffffffffu, eok && (lo || up))) {
+          const T* gp = gs + nn;
+#pragma unroll
+          for (int k = 0; k < NM; k += 2) {
+            if (k < n) z0 += gp[(size_t)k * n] * Wm[NM + k];
+            if (k + 1 < n) z1 += gp[(size_t)(k + 1) * n] * Wm[NM + k + 1];
+          }
         }
       }
       const T z = z0 + z1;
