@@ -835,25 +835,30 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   (void)Ro;
 }
 
-// Sturm count of the scaled Golub-Kahan tridiagonal with off-diagonal
-// ee(t) = (t odd ? be[(t + 1) / 2] : al[t / 2]) * ib (one thread)
-__device__ int sturm_count_gk(const double* al, const double* be, double ib, int m, double x) {
+// Sturm count of the scaled Golub-Kahan tridiagonal (squared scaled off-diagonal
+// e2[0..m-2]), one thread: two FP64 operations per step (the sign tests read the
+// sign and exponent bits on the integer pipe).
+__device__ int sturm_count_gk(const double* e2, int m, double x) {
   double d0 = 1.0, d1 = -x;
-  int cnt = (d1 < 0.0) ? 1 : 0;
-  bool neg_prev = d1 < 0.0;
+  bool neg_prev = __double_as_longlong(d1) < 0 && d1 != 0.0;
+  int cnt = neg_prev ? 1 : 0;
   for (int k = 2; k <= m; ++k) {
-    const int t = k - 2;
-    const double es = ((t & 1) ? be[(t + 1) >> 1] : al[t >> 1]) * ib;
-    double d2 = fma(-x, d1, -(es * es) * d0);
-    bool neg = d2 < 0.0;
-    if (d2 == 0.0) neg = !neg_prev;              // a zero minor counts as a sign change
+    const double d2 = fma(-x, d1, -e2[k - 2] * d0);
+    const long long bits = __double_as_longlong(d2);
+    // a zero minor counts as a sign change
+    const bool neg = ((bits << 1) == 0) ? !neg_prev : (bits < 0);
     cnt += (neg != neg_prev) ? 1 : 0;
     neg_prev = neg;
     d0 = d1;
     d1 = d2;
-    if ((k & 31) == 0 && fabs(d1) < 1e-200 && fabs(d0) < 1e-200) {
-      d0 *= 1e200;
-      d1 *= 1e200;
+    if ((k & 31) == 0) {
+      // rescale when both minors are tiny (exponent field below that of 1e-200)
+      const int ex1 = (int)((__double_as_longlong(d1) >> 52) & 0x7ff);
+      const int ex0 = (int)((__double_as_longlong(d0) >> 52) & 0x7ff);
+      if (ex1 < 358 && ex0 < 358) {
+        d0 *= 1e200;
+        d1 *= 1e200;
+      }
     }
   }
   return cnt;
@@ -887,17 +892,22 @@ __global__ void __launch_bounds__(128) k_ksvd_tri(KsvdArgs A) {
   // itself is the Rayleigh quotient of the converged vector, accurate to the
   // square of the vector's error)
   const int idx = m - k;
+  double* w0 = S + L.total + (size_t)k * 4 * m;
+  double* e2 = w0 + 2 * m;                     // squared scaled off-diagonal (du2 slot)
+  for (int i = 0; i < m - 1; ++i) {
+    const double es = ((i & 1) ? be[(i + 1) >> 1] : al[i >> 1]) * ib;
+    e2[i] = es * es;
+  }
   double lo = 0.0, hi = 1.0 + 1e-12;
   for (int it = 0; it < 30; ++it) {
     const double mid = 0.5 * (lo + hi);
-    if (sturm_count_gk(al, be, ib, m, mid) >= idx) hi = mid;
+    if (sturm_count_gk(e2, m, mid) >= idx) hi = mid;
     else lo = mid;
   }
   const double lam = 0.5 * (lo + hi) * bnd;
   // eigenvector by inverse iteration on the unscaled tridiagonal, in this thread's
   // 4m of work (d, du, du2, dl; dl starts as the off-diagonal, which the
   // factorisation reads entry by entry before overwriting it)
-  double* w0 = S + L.total + (size_t)k * 4 * m;
   int* piv = A.iscr + (size_t)e * 4 * r + (size_t)k * m;
   double* z = S + (k ? L.z2 : L.z1);
   double* dl = w0 + 3 * m;
