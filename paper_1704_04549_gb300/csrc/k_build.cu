@@ -36,9 +36,7 @@ __device__ void house_vec(const double* x, int len, double* v) {
   }
   const double nrm = sqrt(nrm2);
   v[0] += copysign(nrm, x[0]);
-  double vn2 = 0.0;
-  for (int i = 0; i < len; ++i) vn2 += v[i] * v[i];
-  const double inv = 1.0 / sqrt(vn2);
+  const double inv = rsqrt(2.0 * nrm * (nrm + fabs(x[0])));   // ||v||^2 = 2 nrm (nrm + |x0|)
   for (int i = 0; i < len; ++i) v[i] *= inv;
 }
 
@@ -219,8 +217,7 @@ __device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, b
     const double alpha = H[(k + 1) + ld * k];
     const double nrm = sqrt(alpha * alpha + tail);
     const double v0 = alpha + copysign(nrm, alpha);
-    const double den = v0 * v0 + tail;
-    const double inv = (tail != 0.0) ? 1.0 / sqrt(den) : 0.0;   // tail = 0: identity
+    const double inv = (tail != 0.0) ? rsqrt(v0 * v0 + tail) : 0.0;   // tail = 0: identity
     if (hl < L) vb[hb + hl] = (hl == 0 ? v0 : H[(k + 1 + hl) + ld * k]) * inv;
     __syncwarp();
     const double* v = vb + hb;
