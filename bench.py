@@ -250,7 +250,7 @@ def run_ours(args):
         x.zero_()
         _, res = ctx.gmres_solve(b, x, restart=30, rtol=rtol, max_iters=args.max_iters,
                                  pc=TPP_PC_KRON, inner_prec=prec, flexible=(prec != TPP_FP64),
-                                 check=False, inner_iters=k_in)
+                                 check=False, inner_iters=k_in, use_graph=args.graph)
         return res
 
     for _ in range(args.warmup):
@@ -336,7 +336,7 @@ def run_ours(args):
         xd = torch.zeros_like(bd)
         ctx.gmres_solve(bd, xd, restart=30, rtol=1e-8, max_iters=args.max_iters, pc=TPP_PC_KRON,
                         inner_prec=inner, flexible=(inner != TPP_FP64), check=False,
-                        inner_iters=kin)
+                        inner_iters=kin, use_graph=args.graph)
         x_pin.copy_(xd, non_blocking=True)
         torch.cuda.synchronize(dev)
         if it > 0:
@@ -360,6 +360,7 @@ def run_ours(args):
                    "n": n, "nel": [64, 64], "h": w["h"], "dt": 0.05, "dofs": N, "rtol": 1e-8,
                    "restart": 30, "preconditioner": "KSVD rank-2 (Alg. 2d-form / 2d-apply)",
                    "inner_prec": args.prec, "apply_form": args.form,
+                   "cuda_graphs": bool(args.graph),
                    "solver": ("FP64 flexible GMRES(30) around inner FP32 GMRES(%d) solves "
                               "(FP32 operator + FP32 Kronecker apply)" % kin) if kin > 0 else
                              ("flexible GMRES(30), FP32 Kronecker apply" if inner != TPP_FP64
@@ -485,7 +486,7 @@ def run_batch(args):
         for mode, kin in (("fp64", 0), ("mixed", args.inner)):
             rows = [B.solve_group(g, 64, h_el, 0.05, vel[g.dim], span=1.0 / 64,
                                   inner_iters=kin, max_iters=args.max_iters, steps=args.steps,
-                                  warmup=args.warmup) for g in groups]
+                                  warmup=args.warmup, use_graph=args.graph) for g in groups]
             out[mode] = rows
     launches = lib.tpp_kernel_launch_count() - l0
     tot = {m: sum(r["ms_per_step"] for r in rows) for m, rows in out.items()}
@@ -713,6 +714,9 @@ def main():
                          "two-sided Schur / quasi-triangular Sylvester form")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batch workload: fraction of the 20,000 + 2,000 elements")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="plain kernel launches instead of one captured CUDA graph per group "
+                         "of Arnoldi steps (the default)")
     ap.add_argument("--train-elems", type=int, default=50000)
     ap.add_argument("--eval-elems", type=int, default=10000)
     ap.add_argument("--epochs", type=int, default=60)

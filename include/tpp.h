@@ -116,7 +116,13 @@ typedef struct {
                            right-preconditioned by the FP32 Kronecker apply, with the FP32
                            operator and FP32 basis vectors; the outer solve is flexible GMRES
                            in FP64 (operator, Arnoldi, Givens, true residual). */
-  int32_t reserved;     /* must be 0 */
+  int32_t use_graph;    /* 1: every group of Arnoldi steps between two host reads of the solver
+                           state (8 steps; 1 outer step when inner_iters > 0) runs as one CUDA
+                           graph, captured at its first use and kept in the context for later
+                           cycles and solves with the same restart, pc, inner_prec, flexible,
+                           inner_iters and inner_rtol (another combination recaptures); a group
+                           cut short by max_iters runs as plain launches.  Same kernels in the
+                           same order as 0, so the same iterates.  0 or 1. */
   double inner_rtol;    /* inner solves stop early at this relative residual estimate (0: never) */
 } tpp_gmres_opts;
 

@@ -29,7 +29,7 @@ class Problem(C.Structure):
 class GmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
                 ("pc", C.c_int32), ("inner_prec", C.c_int32), ("flexible", C.c_int32),
-                ("inner_iters", C.c_int32), ("reserved", C.c_int32), ("inner_rtol", C.c_double)]
+                ("inner_iters", C.c_int32), ("use_graph", C.c_int32), ("inner_rtol", C.c_double)]
 
 
 class GmresResult(C.Structure):

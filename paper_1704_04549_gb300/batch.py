@@ -19,7 +19,8 @@ from . import _lib as L
 
 def solve_group(group, rhs: int, h: float, dt: float, velocity, *, span: float = 0.0,
                 inner_iters: int = 0, rtol: float = 1e-8, max_iters: int = 3000,
-                restart: int = 30, device: str = "cuda:0", steps: int = 1, warmup: int = 0):
+                restart: int = 30, device: str = "cuda:0", steps: int = 1, warmup: int = 0,
+                use_graph: bool = False):
     """Build the factors of one degree group and solve its systems; returns a dict
     with the device times (CUDA events) of the timed steps and the solve report."""
     from .solver import Context
@@ -28,7 +29,8 @@ def solve_group(group, rhs: int, h: float, dt: float, velocity, *, span: float =
                   batch_rhs=rhs, centres=group.centres, batch_span=span)
     b = torch.as_tensor(synthetic.rhs(group.rhs_seed, ctx.num_dofs), device=device)
     x = torch.zeros_like(b)
-    kw = dict(restart=restart, rtol=rtol, max_iters=max_iters, pc=L.TPP_PC_KRON, check=False)
+    kw = dict(restart=restart, rtol=rtol, max_iters=max_iters, pc=L.TPP_PC_KRON, check=False,
+              use_graph=use_graph)
     if inner_iters > 0:
         kw.update(inner_prec=L.TPP_FP32, flexible=True, inner_iters=inner_iters)
 

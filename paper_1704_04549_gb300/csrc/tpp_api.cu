@@ -379,7 +379,13 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   return TPP_OK;
 }
 
-void tpp_destroy(tpp_ctx* ctx) { delete ctx; }
+void tpp_destroy(tpp_ctx* ctx) {
+  if (ctx)
+    for (int q = 0; q < kMaxRestart; ++q)
+      if (ctx->gexec[q]) cudaGraphExecDestroy(ctx->gexec[q]);
+  if (ctx && ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  delete ctx;
+}
 
 int64_t tpp_num_dofs(const tpp_ctx* ctx) { return ctx ? ctx->N : -1; }
 int64_t tpp_num_elem(const tpp_ctx* ctx) { return ctx ? ctx->E : -1; }
@@ -638,8 +644,9 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     return TPP_ERR_INVALID_ARG;
   }
   const int kin = opts->inner_iters;
-  if (kin < 0 || kin > c->max_restart || opts->reserved != 0 || !(opts->inner_rtol >= 0.0)) {
-    set_error("inner_iters must be in [0, max_restart], reserved 0, inner_rtol >= 0");
+  if (kin < 0 || kin > c->max_restart || (opts->use_graph != 0 && opts->use_graph != 1) ||
+      !(opts->inner_rtol >= 0.0)) {
+    set_error("inner_iters must be in [0, max_restart], use_graph 0 or 1, inner_rtol >= 0");
     return TPP_ERR_INVALID_ARG;
   }
   if (kin > 0 && (!(c->features & TPP_FEAT_MIXED) || opts->pc != TPP_PC_KRON)) {
@@ -647,7 +654,7 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     return TPP_ERR_INVALID_ARG;
   }
   const bool flexible = opts->flexible || opts->inner_prec != TPP_FP64 || kin > 0;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);   // the capture below swaps it briefly
   const int64_t N = c->N;
   const int nblk = c->partial_blocks, stride = kPartialStride;
   double* V = c->p<double>(c->L.V);
@@ -764,7 +771,8 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     // once per group instead of after every step.
     GmresState hs;
     const int cycle_start = total;
-    for (int j = 0; j < m && total < opts->max_iters; ++j) {
+    // one Arnoldi step j (every kernel returns at once when the cycle is done)
+    auto step = [&](int j) -> tpp_status {
       double* vj = V + (size_t)j * N;
       double* w = V + (size_t)(j + 1) * N;
       double* z = flexible ? Z + (size_t)j * N : t1;
@@ -788,13 +796,66 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
                                 nullptr, &st->tickets[3], st, H, cs, sn, g, h1, h2, invb, j, s),
                    "norm+givens");
       TPP_TRY_CUDA(vec_scale(w, w, N, invb, 0.0, done, s), "scale");
-      ++total;
-      const int look = (kin > 0) ? 1 : kLookahead;    // an inner solve is a long step
-      const bool group_end = ((j + 1) % look) == 0 || j + 1 == m || total >= opts->max_iters;
-      if (!group_end) continue;
+      return TPP_OK;
+    };
+    // Arnoldi steps are enqueued in groups of `look`; the host reads the device state
+    // once per group.  With use_graph every full group runs as one CUDA graph,
+    // captured once per group start and kept in the context (its kernels read only
+    // context buffers), so later cycles and solves with the same options replay it.
+    const int look = (kin > 0) ? 1 : kLookahead;    // an inner solve is a long step
+    if (opts->use_graph) {
+      const double key[6] = {(double)m, (double)opts->pc, (double)opts->inner_prec,
+                             (double)flexible, (double)kin, opts->inner_rtol};
+      if (std::memcmp(key, c->gkey, sizeof(key)) != 0) {
+        for (int q = 0; q < kMaxRestart; ++q)
+          if (c->gexec[q]) {
+            cudaGraphExecDestroy(c->gexec[q]);
+            c->gexec[q] = nullptr;
+          }
+        std::memcpy(c->gkey, key, sizeof(key));
+      }
+    }
+    for (int j0 = 0; j0 < m && total < opts->max_iters; j0 += look) {
+      const int j1 = (j0 + look < m) ? j0 + look : m;
+      if (opts->use_graph && total + (j1 - j0) <= opts->max_iters) {
+        if (!c->gexec[j0]) {
+          // captured on the context's own stream (the legacy default stream cannot
+          // be captured); capturing runs nothing, the graph is then launched on s
+          if (!c->gstream)
+            TPP_TRY_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking),
+                         "capture stream");
+          const cudaStream_t user = s;
+          s = c->gstream;
+          TPP_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed), "begin capture");
+          const int64_t k0 = tpp_kernel_launch_count();
+          tpp_status rs = TPP_OK;
+          for (int j = j0; j < j1 && rs == TPP_OK; ++j) rs = step(j);
+          cudaGraph_t graph = nullptr;
+          const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+          s = user;
+          c->gkernels[j0] = (int32_t)(tpp_kernel_launch_count() - k0);
+          count_launch(-c->gkernels[j0]);       // counted per replay instead
+          if (rs != TPP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rs;
+          }
+          TPP_TRY_CUDA(ec, "end capture");
+          const cudaError_t ei = cudaGraphInstantiate(&c->gexec[j0], graph, 0);
+          cudaGraphDestroy(graph);
+          TPP_TRY_CUDA(ei, "instantiate graph");
+        }
+        TPP_TRY_CUDA(cudaGraphLaunch(c->gexec[j0], s), "graph launch");
+        count_launch(c->gkernels[j0]);
+        total += j1 - j0;
+      } else {
+        for (int j = j0; j < j1 && total < opts->max_iters; ++j) {
+          if (tpp_status r = step(j)) return r;
+          ++total;
+        }
+      }
       TPP_TRY_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s), "read state");
       TPP_TRY_CUDA(cudaStreamSynchronize(s), "sync");
-      total = cycle_start + hs.k;          // steps the device actually took
+      total = cycle_start + hs.k;            // steps the device actually took
       res->est_rel_res = hs.est;
       if (hs.done) break;
     }

@@ -129,6 +129,10 @@ struct tpp_ctx {
   bool factors_built;
   bool bj_built;
   int32_t partial_blocks;  // number of CTAs of the reduction kernels
+  cudaGraphExec_t gexec[64];   // use_graph: captured Arnoldi step groups, by first step
+  int32_t gkernels[64];        // kernels in each (added to the launch count per replay)
+  double gkey[6];              // GMRES options they were captured for
+  cudaStream_t gstream;        // stream they are captured on (created at the first capture)
   template <typename T> T* p(size_t off) const { return reinterpret_cast<T*>(ws + off); }
 };
 

@@ -212,11 +212,11 @@ class Context:
     def gmres_solve(self, b, x=None, restart: int = 30, rtol: float = 1e-8,
                     max_iters: int = 3000, pc: int = L.TPP_PC_KRON, inner_prec: int = L.TPP_FP64,
                     flexible: bool = False, stream=None, check: bool = True,
-                    inner_iters: int = 0, inner_rtol: float = 0.0):
+                    inner_iters: int = 0, inner_rtol: float = 0.0, use_graph: bool = False):
         b = self._vec(b, "b")
         x = torch.zeros_like(b) if x is None else self._vec(x, "x")
         o = L.GmresOpts(restart, max_iters, rtol, pc, inner_prec, int(flexible), int(inner_iters),
-                        0, float(inner_rtol))
+                        int(use_graph), float(inner_rtol))
         r = L.GmresResult()
         st = self.lib.gmres_solve(self._ctx, _ptr(b), _ptr(x), C.byref(o), C.byref(r),
                                   _stream(stream))

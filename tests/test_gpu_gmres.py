@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
+import torch
 
 import synthetic
 from oracle.gmres import gmres
@@ -107,3 +108,27 @@ def test_mixed_precision_2d(n):
                              flexible=True)
     assert r32["converged"] and r32["true_rel_res"] <= 1e-8
     assert r32["iters"] <= r64["iters"] + 3
+
+
+@pytest.mark.parametrize("n,nel,kin", [(8, (8, 8), 0), (8, (8, 8), 8), (5, (3, 3, 3), 0),
+                                       (16, (6, 6), 12)])
+def test_graph_cycles_match_plain_launches(n, nel, kin):
+    """use_graph runs each group of Arnoldi steps as one captured CUDA graph: the
+    same kernels in the same order, so the same iterates bit for bit; a second
+    solve replays the cached graphs and a new restart length recaptures."""
+    from paper_1704_04549_gb300 import TPP_FEAT_MIXED
+    vel = synthetic.fourier_velocity(1705, len(nel))
+    ctx, dg = make_pair(n, nel, 0.05, vel, features=TPP_FEAT_MIXED, h=1.0)
+    ctx.tpp_build_factors()
+    b = to_dev(synthetic.rhs(1707, dg.ndof))
+    for restart in (10, 30, 10):
+        kw = dict(pc=TPP_PC_KRON, rtol=1e-9, restart=restart, inner_iters=kin, max_iters=300,
+                  check=False)
+        x0, r0 = ctx.gmres_solve(b, **kw)
+        x1, r1 = ctx.gmres_solve(b, use_graph=True, **kw)
+        assert r1["converged"] == r0["converged"] and r1["status"] == r0["status"]
+        assert r1["iters"] == r0["iters"] and r1["cycles"] == r0["cycles"]
+        assert r1["inner_iters"] == r0["inner_iters"]
+        assert torch.equal(x0, x1)
+        if restart == 30 and kin == 0:
+            assert r1["converged"]
