@@ -544,13 +544,6 @@ __device__ void warp_reorth(double* p, const double* B, int k, int r, double* cf
   }
 }
 
-__device__ __forceinline__ double warp_norm2(const double* v, int len) {
-  const int lane = threadIdx.x & 31;
-  double sv = 0.0;
-  for (int t = lane; t < len; t += 32) sv += v[t] * v[t];
-  return warp_sum(sv);
-}
-
 // Gauss-Jordan inverse of the n x n left half of a (n x 2n, column-major, ld n)
 // with partial pivoting, by one warp (lanes over columns).  Returns true if a
 // zero pivot was met.  fac: n scratch.
@@ -954,50 +947,51 @@ __global__ void __launch_bounds__(128) k_ksvd_vec(KsvdArgs A) {
   const int nsv = (J >= 2) ? 2 : 1;
   // ---- singular vectors in M coordinates: u = U_h u', v = V_h v' (u' from the
   // odd, v' from the even entries of z), reflectors applied last to first;
-  // gauge trace(A_k) >= 0
-  for (int k = 0; k < 2; ++k) {
+  // gauge trace(A_k) >= 0.  The four back-transformations are independent: one
+  // per group of 8 lanes (g = 0: u_1, 1: u_2 by the left reflectors; 2: v_1,
+  // 3: v_2 by the right ones).
+  {
+    const int g = lane >> 3, gl = lane & 7, k = g & 1;
+    const bool left = g < 2;
     const double* z = k ? z2 : z1;
-    double* mu = k ? mu2 : mu1;
-    double* mv = k ? mv2 : mv1;
-    for (int t = lane; t < r; t += 32) {
-      mu[t] = (k < nsv) ? z[2 * t + 1] : 0.0;
-      mv[t] = (k < nsv) ? z[2 * t] : 0.0;
-    }
+    double* vec = left ? (k ? mu2 : mu1) : (k ? mv2 : mv1);
+    const bool act = k < nsv;
+    for (int t = gl; t < r; t += 8) vec[t] = act ? z[2 * t + (left ? 1 : 0)] : 0.0;
     __syncwarp();
-    if (k < nsv) {
-      for (int q = r - 1; q >= 0; --q) {
-        const double* cq = Ms + ld * q;
-        if (tl[q] != 0.0) {
-          double dt = 0.0;
-          for (int i = q + 1 + lane; i < r; i += 32) dt += cq[i] * mu[i];
-          dt = warp_sum(dt) + mu[q];
-          const double f = tl[q] * dt;
-          for (int i = q + 1 + lane; i < r; i += 32) mu[i] -= f * cq[i];
-          __syncwarp();
-          if (lane == 0) mu[q] -= f;
-        }
-        if (q + 1 < r && tr[q] != 0.0) {
-          double dt = 0.0;
-          for (int j = q + 2 + lane; j < r; j += 32) dt += Ms[q + ld * j] * mv[j];
-          dt = warp_sum(dt) + mv[q + 1];
-          const double f = tr[q] * dt;
-          for (int j = q + 2 + lane; j < r; j += 32) mv[j] -= f * Ms[q + ld * j];
-          __syncwarp();
-          if (lane == 0) mv[q + 1] -= f;
-        }
-        __syncwarp();
+    for (int q = r - 1; q >= 0; --q) {
+      const double tau = left ? tl[q] : ((q + 1 < r) ? tr[q] : 0.0);
+      const bool on = act && tau != 0.0;
+      const int st0 = left ? q + 1 : q + 2, h = left ? q : q + 1;
+      double dt = 0.0;
+      if (on)
+        for (int i = st0 + gl; i < r; i += 8)
+          dt += (left ? Ms[i + ld * q] : Ms[q + ld * i]) * vec[i];
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+      if (on) {
+        const double f = tau * (dt + vec[h]);
+        for (int i = st0 + gl; i < r; i += 8)
+          vec[i] -= f * (left ? Ms[i + ld * q] : Ms[q + ld * i]);
+        __syncwarp(0xffu << (8 * g));
+        if (gl == 0) vec[h] -= f;
       }
-      const double pu = warp_norm2(mu, r), pvv = warp_norm2(mv, r);
-      double trc = 0.0;
-      for (int t = lane; t < n; t += 32) trc += mu[t];
-      trc = warp_sum(trc);
-      const double sgn = (trc < 0.0) ? -1.0 : 1.0;
-      const double fu = sgn / sqrt(pu), fv = sgn / sqrt(pvv);
-      for (int t = lane; t < r; t += 32) {
-        mu[t] *= fu;
-        mv[t] *= fv;
-      }
+      __syncwarp();
     }
+    double p2 = 0.0, trc = 0.0;
+    for (int t = gl; t < r; t += 8) {
+      p2 += vec[t] * vec[t];
+      if (t < n) trc += vec[t];
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+      trc += __shfl_xor_sync(0xffffffffu, trc, o);
+    }
+    // the sign of u_k's trace also flips v_k: group g + 2 takes it from group g
+    const double trk = __shfl_sync(0xffffffffu, trc, (left ? g : g - 2) * 8);
+    const double sgn = (trk < 0.0) ? -1.0 : 1.0;
+    const double fsc = act ? sgn * rsqrt(p2) : 0.0;
+    for (int t = gl; t < r; t += 8) vec[t] *= fsc;
     __syncwarp();
   }
   const double s1 = scal[0], s2 = (nsv == 2) ? scal[1] : 0.0;
@@ -1495,7 +1489,7 @@ __device__ __noinline__ bool shift_inv_block(const double* Tg, const double* Cg,
 // Y = (C_2 + mu I)^-1, so block (a, b) of K^-1 is 2 Re(c_ab Y) with
 // c_ab = D_a w_a [W^-1]_{0b} / D_b: one complex n x n inverse instead of a real
 // 2n x 2n one.  Returns 0 without writing when the block is not a well-separated
-// complex pair (|Im mu| < 0.1 |t01'|: W near singular); bit 0 = done, bit 1 = singular.
+// complex pair (|Im mu| < 0.0316 |t01'|: W near singular); bit 0 = done, bit 1 = singular.
 __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg, int n, int j,
                                              double* Ge) {
   double t00 = Tg[j + n * j], t01 = Tg[j + n * (j + 1)];
@@ -1505,7 +1499,7 @@ __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg,
   double b01 = t01 * d;                        // balanced t01' (|t01'| = |t10'|)
   double hd = 0.5 * (t00 - t11);
   double y2 = -(hd * hd + t01 * t10);
-  if (!(y2 > 0.01 * b01 * b01)) return 0;
+  if (!(y2 > 1e-3 * b01 * b01)) return 0;
   const double x = 0.5 * (t00 + t11), y = sqrt(y2);
 
   const int lane = threadIdx.x & 31, row = lane & 15;
