@@ -73,6 +73,18 @@ def form_bits(args) -> int:
     return TPP_FEAT_TWO_SIDED if args.form == "two-sided" else 0
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over the ranks of the default process group (the slowest
+    replica's time); the value itself when the run is not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,11 +279,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     launches = lib.tpp_kernel_launch_count() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     res = results[-1]
     converged = all(r["converged"] for r in results)
 
