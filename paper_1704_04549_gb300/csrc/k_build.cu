@@ -1386,6 +1386,63 @@ __global__ void __launch_bounds__(128) k_schur_w2(int n, int64_t E, int mpe, dou
     if (hl < n) H[hl + ld * c] = rank1 ? ((which && hl == c && !empty) ? 1.0 : 0.0) : Tg[hl + n * c];
   __syncwarp();
   const bool ok = hw_real_schur(H, Q, n, ld, vb, rank1);
+  // 2x2 diagonal blocks with real eigenvalues are rotated to upper triangular form
+  // (Givens rotation whose first column is an eigenvector), so that only complex
+  // pairs stay 2x2; kept when the rotated block does not come out triangular to
+  // rounding (nearly equal eigenvalues)
+  for (int j = 0; j + 1 < n; ++j) {
+    const double t00 = H[j + ld * j], t01 = H[j + ld * (j + 1)];
+    const double t10 = H[(j + 1) + ld * j], t11 = H[(j + 1) + ld * (j + 1)];
+    const bool start = t10 != 0.0 && (j == 0 || H[j + ld * (j - 1)] == 0.0);
+    const double hd = 0.5 * (t00 - t11), disc = hd * hd + t01 * t10;
+    bool rot = start && ok && !rank1 && disc > 0.0;
+    double cr = 1.0, sr = 0.0;
+    if (rot) {
+      const double lam = 0.5 * (t00 + t11) + copysign(sqrt(disc), hd);
+      // eigenvector of lam: (t01, lam - t00) or (lam - t11, t10), the longer one
+      double v0 = t01, v1 = lam - t00;
+      const double w0 = lam - t11, w1 = t10;
+      if (w0 * w0 + w1 * w1 > v0 * v0 + v1 * v1) {
+        v0 = w0;
+        v1 = w1;
+      }
+      const double iv = rsqrt(v0 * v0 + v1 * v1);
+      cr = v0 * iv;
+      sr = v1 * iv;
+      // rotated block G^T B G, G = [[c, -s], [s, c]] (first column the eigenvector):
+      // its (1, 0) entry g2^T B g1 must vanish to rounding
+      const double r10 = -sr * (cr * t00 + sr * t01) + cr * (cr * t10 + sr * t11);
+      const double r00 = cr * (cr * t00 + sr * t01) + sr * (cr * t10 + sr * t11);
+      const double r11 = -sr * (-sr * t00 + cr * t01) + cr * (-sr * t10 + cr * t11);
+      rot = fabs(r10) <= 1e-14 * (fabs(r00) + fabs(r11) + fabs(t01) + fabs(t10));
+    }
+    __syncwarp();
+    if (rot) {
+      if (j + hl < n) {                       // rows j, j+1 of columns j..n-1
+        const int c = j + hl;
+        const double a = H[j + ld * c], bb = H[(j + 1) + ld * c];
+        H[j + ld * c] = cr * a + sr * bb;
+        H[(j + 1) + ld * c] = -sr * a + cr * bb;
+      }
+    }
+    __syncwarp();
+    if (rot) {
+      if (hl < n) {                           // columns j, j+1 of rows 0..j+1, and of Q
+        const int r = hl;
+        if (r <= j + 1) {
+          const double a = H[r + ld * j], bb = H[r + ld * (j + 1)];
+          H[r + ld * j] = cr * a + sr * bb;
+          H[r + ld * (j + 1)] = -sr * a + cr * bb;
+        }
+        const double qa = Q[r + ld * j], qb = Q[r + ld * (j + 1)];
+        Q[r + ld * j] = cr * qa + sr * qb;
+        Q[r + ld * (j + 1)] = -sr * qa + cr * qb;
+      }
+    }
+    __syncwarp();
+    if (rot && hl == 0) H[(j + 1) + ld * j] = 0.0;
+    __syncwarp();
+  }
   if (!empty) {
     for (int c = 0; c < n; ++c)
       if (hl < n) {
