@@ -1,18 +1,18 @@
-// Per-element formation of the Kronecker preconditioner (Alg. 2d-form).
-//
-// One CTA per element:
+// Per-element formation of the Kronecker preconditioner (Alg. 2d-form):
 //  1. coefficients of the rearranged block A~ = Q M Q^T (see k_struct_qr),
-//  2. Golub-Kahan-Lanczos bidiagonalisation of M with full
-//     reorthogonalisation (Alg. lanczos; Sec. 4.1.1 "full orthogonalization"),
+//  2. dense Householder bidiagonalisation of the small core M (the paper runs
+//     Lanczos on A~, Sec. 4.1.1; the triplets are the same),
 //  3. top-2 singular triplets of the bidiagonal matrix: bisection on the
-//     Golub-Kahan tridiagonal [[0, B], [B^T, 0]] (eigenvalues +-sigma) and
-//     inverse iteration for the vectors; Ritz vectors back in A~ space,
+//     Golub-Kahan tridiagonal [[0, B], [B^T, 0]] (eigenvalues +-sigma),
+//     inverse iteration for the vectors, reflectors applied back,
 //  4. A_k = sqrt(s_k) mat(u_k), B_k = sqrt(s_k) mat(v_k)  (column-major vec),
-//  5. LU (Gauss-Jordan, partial pivoting) inverses of A_2 and B_1,
-//     C_1 = A_2^-1 A_1, C_2 = B_1^-1 B_2 (Sec. 4.2),
+//  5. Gauss-Jordan inverses of the gauge-shifted pair A_2 + alpha A_1 and
+//     B_1 - alpha B_2 (the paper's A_2, B_1 for alpha = 0), C_1 = L_A^-1 A_1,
+//     C_2 = L_B^-1 B_2 (Sec. 4.2),
 //  6. real Schur forms C_i = Q_i T_i Q_i^T by Householder Hessenberg reduction
-//     and Francis double-shift QR (one warp per matrix), Eq. quad-triang,
-//  7. S_A = Q_1^T A_2^-1, S_B = Q_2^T B_1^-1 stored with Q_1, Q_2, T_1, T_2.
+//     and Francis double-shift QR, Eq. quad-triang (C_1 only in the one-sided
+//     form, whose shifted systems C_2 + T_1[J, J] are then inverted),
+//  7. S_A = Q_1^T L_A^-1 (and S_B = Q_2^T L_B^-1) stored with Q_1, T_1 (Q_2, T_2).
 #include "tpp_internal.cuh"
 
 namespace tpp {
@@ -461,17 +461,23 @@ __device__ void atomic_min_double(double* addr, double v) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Build pipeline (2D), one warp per element or per matrix so that every FP64
-// instruction is issued by a full warp and many elements are in flight per SM:
-//   k_ksvd_w       the core M of the rearranged block (r = n + rz), dense
-//                  Householder bidiagonalisation, top-2 singular triplets
-//                  of the bidiagonal (multisection + inverse iteration on
-//                  its Golub-Kahan tridiagonal), factors A_k, B_k    (a3, a4)
-//   k_invert_w     choice of the inverted pair, Gauss-Jordan inverses,
-//                  C_1 = L_A^-1 A_1, C_2 = L_B^-1 B_2                (a5)
-//   k_schur_w      real Schur form of C_1 (and of C_2 in the two-sided form)
-//   k_shift_inv_w  one-sided form: inverses of the shifted diagonal systems
-//                  (C_2 + T_1[J, J]) of every column block of T_1
+// Build pipeline (2D).  A warp-wide FP64 instruction costs the FP64 pipe the
+// same (16 SM cycles) whatever its active lanes, so the work is laid out for
+// full warps:
+//   k_ksvd_w       warp per element: core M of the rearranged block
+//                  (r = n + rz), dense Householder bidiagonalisation
+//   k_ksvd_tri     thread per (element, k): sigma_k by bisection, its vector
+//                  by inverse iteration on the Golub-Kahan tridiagonal
+//   k_ksvd_vec     warp per element: reflectors back (four vectors in lane
+//                  groups), factors A_k, B_k                           (a3, a4)
+//   k_invert_r     n <= 16: gauge candidates ranked in FP32, the chosen pair
+//                  inverted in FP64, both matrices in one warp (k_invert_w:
+//                  n > 16, shared-memory Gauss-Jordan); C_1, C_2        (a5)
+//   k_schur_w2     n <= 16: two real Schur forms per warp (k_schur_w: n > 16)
+//   k_shift_inv_r  one-sided form, n <= 16: inverses of the shifted diagonal
+//                  systems of every column block of T_1 (complex n x n for the
+//                  2x2 blocks; k_shift_inv_fb the nearly defective ones;
+//                  k_shift_inv_w: n > 16)
 //   k_final_w      S_A = Q_1^T L_A^-1 (two-sided: also S_B = Q_2^T L_B^-1)
 
 struct KsvdArgs {
@@ -479,7 +485,7 @@ struct KsvdArgs {
   int64_t E;
   const double* kco;   // per block: Cx ((n+2) x n), Cy ((n+2) x n), Dg (n x n)
   const double *Zd, *Rz, *Qo;
-  double* scr;     // per element: U (r*r), V (r*r), tridiagonal work (16 r)
+  double* scr;     // per element: the k_ksvd_w shared-memory image, tridiagonal work (16 r)
   int* iscr;       // per element: 4 r pivot flags
   double *sigma, *A1, *B1, *A2, *B2;
   DevStatus* st;
