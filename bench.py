@@ -38,7 +38,7 @@ FP64_PEAK_NOTE = ("FP64 peak = 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 125
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) of one FP64 one-sided apply launch at n = 16 on the 64 x 64 mesh,
 # from the ncu capture summarised in profiles/k_apply_2d_g_k_dg_apply_2d_adv2d_64x64_n16.md
-TRAFFIC_APPLY_FP64_N16 = 308.18e6 + 3.45e6
+TRAFFIC_APPLY_FP64_N16 = 305.2e6 + 3.39e6
 
 
 def workload(n: int, h: float = 1.0, solenoidal: bool = True):
