@@ -1819,8 +1819,11 @@ __global__ void __launch_bounds__(128) k_learned_accept(int n, int64_t E, const 
     nk[k] = sqrt(warp_sum(s2));
   }
   if (lane == 0) {
-    sigma[2 * e] = nk[0] * nk[1];
-    sigma[2 * e + 1] = nk[2] * nk[3];
+    const double s1 = nk[0] * nk[1], s2 = nk[2] * nk[3];
+    sigma[2 * e] = s1;
+    sigma[2 * e + 1] = s2;
+    const double hi = fmax(s1, s2);
+    atomic_min_double(&st->min_sigma_ratio, (hi > 0.0) ? fmin(s1, s2) / hi : 0.0);
   }
 }
 
