@@ -96,3 +96,32 @@ def test_3d_constant_velocity_first_stage_not_rank_one():
     dg = AdvectionDG(PeriodicMesh((2, 2, 2)), 3, 0.1, synthetic.constant_velocity([1.0, 0.5, 0.25]))
     s, _, _ = ksvd(dg.element_block(0), 3, 3, 9, 9, 1)
     assert s[1] / s[0] > 1e-6 and s[2] / s[0] < 1e-14
+
+
+@pytest.mark.parametrize("n", [3, 4])
+def test_3d_nested_stages_on_advection_blocks(n):
+    """The nested construction (Sec. 4.3) on real 3D advection blocks, where neither
+    stage is exact: each stage's error is the Eckart-Young tail of its rearrangement,
+    a perturbed stage-1 factor is worse, and the two errors add in quadrature,
+    ||S - P||^2 = ||S - A1 (x) D1||^2 + ||A1||^2 ||D1 - D1_2||^2, because the stage-1
+    residual is orthogonal to every A1 (x) X (it fails when P is assembled from a
+    different A1 than the one stage 2 was scaled against).  Which operator the
+    stages approximate is pinned by the exact-recovery test above."""
+    dg = AdvectionDG(PeriodicMesh((2, 2, 2)), n, 0.1, synthetic.fourier_velocity(11, 3))
+    rng = np.random.default_rng(n)
+    for e in [0, 5]:
+        S = dg.element_block(e)
+        out = ksvd_3d_nested(S, n)
+        A1, D1, s1, s2 = out["A1"], out["D1"], out["s1"], out["s2"]
+        R1 = S - np.kron(A1, D1)
+        assert abs(np.linalg.norm(R1) - np.sqrt(np.sum(s1[1:] ** 2))) <= 1e-12 * np.linalg.norm(S)
+        assert s1[1] / s1[0] > 1e-8                     # stage 1 is not exact
+        for _ in range(3):
+            dA = A1 + 1e-3 * rng.standard_normal(A1.shape)
+            assert np.linalg.norm(S - np.kron(dA, D1)) > np.linalg.norm(R1)
+        D12 = np.kron(out["B1"], out["C1"]) + np.kron(out["B2"], out["C2"])
+        R2 = D1 - D12
+        assert abs(np.linalg.norm(R2) - np.sqrt(np.sum(s2[2:] ** 2))) <= 1e-12 * np.linalg.norm(D1)
+        lhs = np.linalg.norm(S - out["P"]) ** 2
+        rhs = np.linalg.norm(R1) ** 2 + np.linalg.norm(A1) ** 2 * np.linalg.norm(R2) ** 2
+        assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(S) ** 2
