@@ -261,7 +261,9 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
  * num_elem * 4 * n <= 524288 only; larger ones return TPP_ERR_INVALID_ARG.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU race.  Asynchronous.
+ * All calls share the array: calls that overlap on the GPU race.  The current device
+ * must be the one the context was created on (TPP_ERR_INVALID_ARG otherwise), since
+ * the array's address is that of the current device.  Asynchronous.
  */
 tpp_status dg_apply_sumfact_static(const tpp_ctx* ctx, const double* x, double* y, void* stream);
 
@@ -353,8 +355,10 @@ tpp_status tpp_mlp_element_loss(tpp_mlp* net, const tpp_ctx* basis, const float*
 /* Learned preconditioner with both fallbacks: tpp_build_factors_learned(threshold),
  * then gmres_solve limited to iter_limit Arnoldi steps; if that solve has not
  * converged, the exact KSVD build (tpp_build_factors) and gmres_solve again from the
- * current x with opts->max_iters.  result->iters counts both solves; *rebuilt = 1
- * when the second build ran.  Same argument rules as the two calls. */
+ * current x with the Arnoldi steps left of opts->max_iters (both solves together take
+ * at most opts->max_iters).  result->iters counts both solves; *rebuilt = 1 when the
+ * second build ran (report->num_fallback then equals num_elem).  Same argument rules
+ * as the two calls. */
 tpp_status tpp_solve_learned(tpp_ctx* ctx, tpp_mlp* net, double threshold, int32_t iter_limit,
                              const double* b, double* x, const tpp_gmres_opts* opts,
                              tpp_gmres_result* result, tpp_build_report* report,

@@ -19,8 +19,13 @@ two terms, and whose minimum over the factors is sum_{k > 2} sigma_k^2 /
 the mean over elements.  Backward: dL/da_k = -2 R b_k, dL/db_k = -2 R^T a_k with
 R the residual matrix, then the chain rule through the layers.
 
+Training uses Adam (``adam_step``, Kingma and Ba 2015, Algorithm 1).
+
 Pinned by central finite differences of the loss with respect to every
-parameter of a small network and by the Eckart-Young minimum.
+parameter of a small network, by the Eckart-Young minimum, by values of the
+GELU and its derivative at points where the normal CDF is tabulated, and by
+Adam's closed forms (first step, constant gradient) and its convergence on a
+quadratic.
 """
 from __future__ import annotations
 
@@ -80,6 +85,22 @@ def backward(params, pre, dout: np.ndarray):
         grads[l] = (h.T @ g, g.sum(axis=0))
         g = g @ W.T
     return grads
+
+
+def adam_step(p, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) of parameters p with
+    gradient g, first and second moment estimates m, v and step number t >= 1.
+
+    m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+    p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+    Returns (p, m, v) as float64 arrays."""
+    p, g = np.asarray(p, dtype=np.float64), np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
 
 
 def unpack(out: np.ndarray, n: int):

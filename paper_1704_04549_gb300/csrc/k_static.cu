@@ -70,6 +70,16 @@ extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x,
                    std::to_string(kStaticTraceDoubles) + " doubles");
     return TPP_ERR_INVALID_ARG;
   }
+  int dev = -1;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return tpp::cuda_check(ed, "cudaGetDevice");
+  if (dev != c->device) {
+    // the scratch address below belongs to the current device, the workspace and the
+    // vectors to the context's: refuse rather than mix two GPUs' memory
+    tpp::set_error("dg_apply_sumfact_static: current device " + std::to_string(dev) +
+                   " is not the context's device " + std::to_string(c->device));
+    return TPP_ERR_INVALID_ARG;
+  }
   double* tr = nullptr;
   if (tpp_status st = scratch_address(&tr)) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -318,6 +318,7 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   c->prob.centres = nullptr;
   c->n = prob->n;
   c->dim = prob->dim;
+  c->device = dev;
   problem_counts(prob, &c->E, &c->R);
   c->iso = prob->batch_rhs > 0;
   c->EB = c->E * c->R;
@@ -918,7 +919,15 @@ tpp_status tpp_solve_learned(tpp_ctx* c, tpp_mlp* net, double threshold, int32_t
     report->num_fallback = report->num_elem;
     report->max_cond = rep2.max_cond;
   }
-  r = gmres_solve(c, b, x, opts, res, stream);
+  // the caller's max_iters bounds both solves together
+  tpp_gmres_opts o2 = *opts;
+  o2.max_iters = opts->max_iters - first;
+  if (o2.max_iters < 1) {
+    res->status = TPP_ERR_NOT_CONVERGED;
+    set_error("GMRES did not reach rtol within max_iters");
+    return TPP_ERR_NOT_CONVERGED;
+  }
+  r = gmres_solve(c, b, x, &o2, res, stream);
   res->iters += first;
   res->inner_iters += first_inner;
   res->cycles += first_cycles;

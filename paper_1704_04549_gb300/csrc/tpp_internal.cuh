@@ -114,6 +114,7 @@ struct Layout {
 struct tpp_ctx {
   tpp_problem prob;        // copy (host pointers cleared)
   int32_t n, dim;
+  int32_t device;          // CUDA device the context (and its workspace) was created on
   int64_t E, N;            // elements, DOFs
   int32_t R;               // right-hand sides per element (1 on a mesh)
   bool iso;                // batch of isolated elements (block-diagonal systems)

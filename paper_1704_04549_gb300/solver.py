@@ -134,7 +134,7 @@ class Context:
             raise L.TppError(st, "tpp_build_factors_learned")
         return out
 
-    def tpp_solve_learned(self, net, b, x=None, threshold: float = 0.05, iter_limit: int = 60,
+    def tpp_solve_learned(self, net, b, x=None, threshold: float = 0.05, iter_limit: int = 50,
                           restart: int = 30, rtol: float = 1e-8, max_iters: int = 3000,
                           inner_iters: int = 0, stream=None, check: bool = True):
         """Learned build + GMRES with both fallbacks (factor error above threshold per
@@ -205,8 +205,9 @@ class Context:
         (for callers that cannot allocate device scratch; overlapping calls race)."""
         x = self._vec(x, "x")
         y = torch.empty_like(x) if y is None else self._vec(y, "y")
-        L.check(self.lib.dg_apply_sumfact_static(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
-                "dg_apply_sumfact_static")
+        with torch.cuda.device(self.device):
+            L.check(self.lib.dg_apply_sumfact_static(self._ctx, _ptr(x), _ptr(y),
+                                                     _stream(stream)), "dg_apply_sumfact_static")
         return y
 
     def gmres_solve(self, b, x=None, restart: int = 30, rtol: float = 1e-8,

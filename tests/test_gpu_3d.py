@@ -8,7 +8,7 @@ from oracle.gmres import gmres
 from oracle.ksvd import ksvd_3d_nested
 from oracle.precond import apply_dense, kron_dense
 from paper_1704_04549_gb300 import TPP_FP32, TPP_FEAT_MIXED, TPP_PC_KRON
-from tests.gpu_util import make_pair, rel, to_dev, to_host
+from tests.gpu_util import make_pair, rel, solve_tol, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,7 @@ def _check_3d(ctx, dg, elems):
     n, nl = dg.n, dg.nloc
     b = synthetic.rhs(99, dg.ndof)
     x = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    worst = 0.0
     for e in elems:
         ref = ksvd_3d_nested(dg.element_block(e), n)
         s1_ref = np.atleast_1d(ref["s1"])[0]
@@ -73,11 +74,12 @@ def _check_3d(ctx, dg, elems):
         assert np.abs(Azi[e] @ Az[e] - np.eye(n)).max() <= 1e-12 * np.linalg.cond(Az[e], 1)
         be = b[e * nl:(e + 1) * nl]
         x_ref = apply_dense(ref["P"], be)
+        err = rel(x[e * nl:(e + 1) * nl], x_ref)
+        worst = max(worst, err)
         kappa = np.linalg.cond(ref["P"])
-        cz = np.linalg.cond(Az[e], 1)
-        tol = max(1e-12, 1e-14 * kappa * cpair[e] * cz)
-        assert rel(x[e * nl:(e + 1) * nl], x_ref) <= tol, (e, kappa, cpair[e], cz)
+        assert err <= solve_tol(kappa), (e, err, kappa, cpair[e])
         assert zflags[e] & 2 == 0 and flags[e] & 12 == 0
+    print(f"3D FP64 apply vs oracle, n={n}: max element relative error {worst:.2e}")
 
 
 @pytest.mark.parametrize("n,nel,field", [(2, (2, 2, 2), "fourier"), (3, (2, 2, 2), "fourier"),

@@ -147,20 +147,26 @@ def test_loss_is_gauge_invariant():
     assert abs(l1 - l3) <= 1e-6 * max(1.0, l1)
 
 
-def test_adam_step():
-    """First Adam step: p <- p - lr g / (|g| + 1e-8) (bias-corrected moments)."""
+def test_adam_steps_match_oracle():
+    """Three Adam steps against the oracle's update (Kingma and Ba, Algorithm 1) fed
+    with the GPU's gradients of each step: FP32 moments and parameters, so the
+    parameters agree to FP32 rounding of updates of size lr."""
     from paper_1704_04549_gb300 import Mlp
     n = 4
     ctx, _ = _mesh(n, (3, 3))
     X, Mn, _ = ctx.tpp_learned_inputs()
     ps = _params(n, 41, out_scale=0.2)
-    p0 = _flat(ps)
-    net = Mlp(n, max_batch=16, params=p0)
-    net.train_step(ctx, X, Mn, lr=1e-3)
-    g = to_host(net.gradients()).astype(np.float64)
-    p1 = net.get_params().astype(np.float64)
-    ref = p0 - 1e-3 * g / (np.abs(g) + 1e-8)
-    assert np.max(np.abs(p1 - ref)) <= 1e-6
+    p = _flat(ps).astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    net = Mlp(n, max_batch=16, params=_flat(ps))
+    for t in range(1, 4):
+        net.train_step(ctx, X, Mn, lr=1e-3)
+        g = to_host(net.gradients()).astype(np.float64)
+        p, m, v = mlp.adam_step(p, g, m, v, t, 1e-3)
+        p1 = net.get_params().astype(np.float64)
+        assert np.max(np.abs(p1 - p)) <= 2e-6, t
+        p = p1                 # continue from the GPU's parameters (FP32 state)
 
 
 def test_training_reduces_loss():
@@ -247,3 +253,36 @@ def test_learned_factors_in_gmres():
     assert r["iters"] <= 2 * r_exact["iters"] + 2, (r["iters"], r_exact["iters"], rep)
     Ax = to_host(ctx.dg_apply_sumfact(x))
     assert np.linalg.norm(Ax - b) <= 1.0001e-8 * np.linalg.norm(b)
+
+
+def test_solve_learned_iteration_fallback():
+    """tpp_solve_learned's second fallback: with every element on an untrained
+    network's factors (threshold infinity) the first GMRES solve exceeds its
+    iteration limit, every element is rebuilt by the exact KSVD and GMRES continues
+    from the current iterate to the 1e-8 true residual (checked with the oracle's
+    S); both solves together stay within max_iters."""
+    from paper_1704_04549_gb300 import Mlp
+    n = 4
+    ctx, dg = _mesh(n, (6, 6))
+    net = Mlp(n, max_batch=64, params=_flat(_params(n, 81, out_scale=0.1)))
+    b = synthetic.rhs(1714, dg.ndof)
+    S = dg.global_matrix()
+    ctx.tpp_build_factors()
+    _, r_exact = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    limit = 3
+    x, r = ctx.tpp_solve_learned(net, to_dev(b), threshold=np.inf, iter_limit=limit, rtol=1e-8)
+    assert r["rebuilt"] == 1 and r["build"]["num_fallback"] == dg.mesh.num_elem
+    assert r["converged"] and r["true_rel_res"] <= 1e-8
+    assert limit < r["iters"] <= limit + r_exact["iters"] + 2
+    xh = to_host(x)
+    assert np.linalg.norm(b - S @ xh) <= 1.0001e-8 * np.linalg.norm(b)
+    # the caller's max_iters bounds both solves: 3 + 2 steps are not enough
+    x, r = ctx.tpp_solve_learned(net, to_dev(b), threshold=np.inf, iter_limit=limit,
+                                 rtol=1e-8, max_iters=limit + 2, check=False)
+    assert r["rebuilt"] == 1 and not r["converged"] and r["iters"] == limit + 2
+    assert r["status"] == 4
+    # threshold 0: every element takes the exact KSVD, the first solve converges
+    # within its limit and nothing is rebuilt
+    x, r = ctx.tpp_solve_learned(net, to_dev(b), threshold=0.0, iter_limit=r_exact["iters"] + 1,
+                                 rtol=1e-8)
+    assert r["rebuilt"] == 0 and r["converged"] and r["iters"] == r_exact["iters"]

@@ -1,11 +1,16 @@
 """GPU: the FP32 forms of the operator and the Kronecker apply (stated error
-bounds against the FP64 oracle / FP64 path), and the mixed-precision solver
-(FP64 flexible GMRES around inner FP32 GMRES solves)."""
+bounds against the FP64 oracle), and the mixed-precision solver (FP64 flexible
+GMRES around inner FP32 GMRES solves) against the oracle's operator and a
+sparse direct solve."""
 import numpy as np
 import pytest
 import torch
 
 import synthetic
+import scipy.sparse.linalg as spla
+
+from oracle.ksvd import ksvd_2d, ksvd_3d_nested, kron_sum
+from oracle.precond import apply_dense
 from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_PC_KRON
 from tests.gpu_util import make_pair, rel, to_dev, to_host
 
@@ -32,19 +37,41 @@ def test_operator_f32_within_rounding_bound(n, nel):
     assert np.all(np.abs(y32 - y) <= bound + 1e-300)
 
 
-@pytest.mark.parametrize("n,nel", [(8, (4, 4)), (16, (4, 4)), (6, (2, 2, 2))])
-def test_apply_f32_vs_fp64(n, nel):
+def _oracle_P(dg, e):
+    """The oracle's Kronecker approximation of element e (2D: rank 2; 3D: nested)."""
+    if dg.dim == 2:
+        _, As, Bs = ksvd_2d(dg.element_block(e), dg.n)
+        return kron_sum(As, Bs)
+    return ksvd_3d_nested(dg.element_block(e), dg.n)["P"]
+
+
+# Largest element-wise relative error of the FP32 apply against the oracle's
+# dense LU solve measured on the GB300 over these cases: 1.07e-6 (2D, n = 16);
+# the asserted bound is the stated FP32 target, about 10x the measurement.
+F32_APPLY_BOUND = 1e-5
+
+
+@pytest.mark.parametrize("n,nel", [(8, (4, 4)), (16, (4, 4)), (31, (2, 2)), (6, (2, 2, 2)),
+                                   (11, (2, 2, 2))])
+def test_apply_f32_vs_oracle(n, nel):
+    """FP32 Kronecker apply (float factors, float arithmetic) against the oracle's
+    dense LU solve with P = sum A_k (x) B_k, element by element."""
     ctx, dg = make_pair(n, nel, 0.05, _vel(len(nel)), features=TPP_FEAT_MIXED)
     ctx.tpp_build_factors()
     b = synthetic.rhs(99, dg.ndof)
-    x64 = to_host(ctx.tpp_apply_inverse(to_dev(b)))
-    x32 = to_host(ctx.tpp_apply_inverse_f32(torch.as_tensor(b.astype(np.float32), device="cuda:0")))
+    x32 = to_host(ctx.tpp_apply_inverse_f32(torch.as_tensor(b.astype(np.float32),
+                                                           device="cuda:0")))
     xd = to_host(ctx.tpp_apply_inverse(to_dev(b), prec=TPP_FP32))
-    cp = to_host(ctx.views()["cond"]).max()
-    # FP32 contractions and sweep: error ~ n u32 times the factor conditioning
-    assert rel(x32, x64) <= 1e-6 * n * max(1.0, np.sqrt(cp))
-    # float or double vectors around the same FP32 factors agree to input rounding
-    assert rel(x32, xd) <= 1e-6 * n * max(1.0, np.sqrt(cp))
+    nl, worst = dg.nloc, 0.0
+    for e in range(dg.mesh.num_elem):
+        be = b[e * nl:(e + 1) * nl]
+        x_ref = apply_dense(_oracle_P(dg, e), be)
+        err = rel(xd[e * nl:(e + 1) * nl], x_ref)
+        worst = max(worst, err)
+        assert err <= F32_APPLY_BOUND, (e, err)
+        # float input vectors: the same FP32 factors, b rounded to float first
+        assert rel(x32[e * nl:(e + 1) * nl], x_ref) <= F32_APPLY_BOUND, e
+    print(f"FP32 apply vs oracle, n={n} {nel}: max element relative error {worst:.2e}")
 
 
 @pytest.mark.parametrize("n,nel,kmax,kin", [(8, (4, 4), 1, 8), (16, (4, 4), 1, 12),
@@ -62,3 +89,10 @@ def test_nested_mixed_gmres_reaches_fp64_residual(n, nel, kmax, kin):
     assert r["inner_iters"] <= r["iters"] * kin and r["iters"] <= max(4, r64["iters"] // 4)
     Ax = to_host(ctx.dg_apply_sumfact(x))
     assert np.linalg.norm(Ax - b) <= 1.0001e-8 * np.linalg.norm(b)
+    if dg.ndof <= 70000:
+        # against the oracle: true residual with the assembled S, and the solution
+        # against a sparse direct solve (GMRES to 1e-8: within 1e-6, as in FP64)
+        S = dg.global_matrix()
+        xh = to_host(x)
+        assert np.linalg.norm(b - S @ xh) <= 1.0001e-8 * np.linalg.norm(b)
+        assert rel(xh, spla.spsolve(S.tocsc(), b)) <= 1e-6

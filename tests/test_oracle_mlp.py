@@ -101,3 +101,51 @@ def test_network_gradient_finite_differences():
         fd = (loss64(P64[:l] + [(W, bp)] + P64[l + 1:]) - loss64(P64[:l] + [(W, bm)] + P64[l + 1:])) / (2 * eps)
         assert abs(fd - grads[l][1][0]) <= 1e-6 * max(1.0, abs(fd))
     assert abs(loss_of(params) - loss64(P64)) <= 1e-12
+
+
+def test_gelu_known_values():
+    """GELU(x) = x Phi(x) with the standard normal CDF: Phi(1) = 0.8413447460685429,
+    phi(1) = exp(-1/2) / sqrt(2 pi) = 0.24197072451914337 (tabulated values).
+    The tanh approximation misses GELU(1) by 2e-4, so it would fail here."""
+    x = np.array([0.0, 1.0, -1.0, 2.0, -3.0])
+    g = mlp.gelu(x)
+    assert g[0] == 0.0
+    assert abs(g[1] - 0.8413447460685429) <= 1e-15
+    assert abs(g[2] + 0.15865525393145707) <= 1e-15
+    assert abs(g[3] - 2.0 * 0.9772498680518208) <= 1e-15       # Phi(2)
+    assert abs(g[4] + 3.0 * 0.0013498980316300946) <= 1e-15    # Phi(-3)
+    # GELU(x) - GELU(-x) = x (Phi(x) + Phi(-x) = 1)
+    xs = np.linspace(-5.0, 5.0, 41)
+    assert np.max(np.abs(mlp.gelu(xs) - mlp.gelu(-xs) - xs)) <= 1e-14
+    # derivative: Phi(x) + x phi(x)
+    d = mlp.gelu_grad(np.array([0.0, 1.0, -1.0]))
+    assert d[0] == 0.5
+    assert abs(d[1] - (0.8413447460685429 + 0.24197072451914337)) <= 1e-15
+    assert abs(d[2] - (0.15865525393145707 - 0.24197072451914337)) <= 1e-15
+
+
+def test_adam_closed_forms():
+    """Step 1: the bias corrections make m_hat = g and v_hat = g^2, so the move is
+    lr g / (|g| + eps).  A constant gradient keeps m_hat = g, v_hat = g^2 at every
+    step (the purpose of the bias correction)."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    g = rng.standard_normal(50) * np.logspace(-6, 2, 50)
+    p0 = rng.standard_normal(50)
+    z = np.zeros(50)
+    p1, m, v = mlp.adam_step(p0, g, z, z, 1, 1e-3)
+    assert np.max(np.abs(p1 - (p0 - 1e-3 * g / (np.abs(g) + 1e-8)))) <= 1e-15
+    p, m, v = p0, z, z
+    for t in range(1, 41):
+        p_prev = p
+        p, m, v = mlp.adam_step(p, g, m, v, t, 1e-2)
+        step = p_prev - p
+        assert np.max(np.abs(step - 1e-2 * g / (np.abs(g) + 1e-8)) / 1e-2) <= 1e-12
+
+
+def test_adam_minimises_a_quadratic():
+    """f(p) = sum (p - c)^2 from p = 0: Adam with lr 0.05 ends within 1e-2 of c."""
+    c = np.array([3.0, -1.0, 0.25, 10.0])
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 3001):
+        p, m, v = mlp.adam_step(p, 2.0 * (p - c), m, v, t, 0.05 if t < 2000 else 0.005)
+    assert np.max(np.abs(p - c)) <= 1e-2
