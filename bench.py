@@ -37,8 +37,19 @@ FP64_PEAK_NOTE = ("FP64 peak = 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 125
                   "(FP64 pipe unit count and max clock; 1.19 TFLOP/s measured by a DFMA loop)")
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) of one FP64 one-sided apply launch at n = 16 on the 64 x 64 mesh,
-# from the ncu capture summarised in profiles/k_apply_2d_g_k_dg_apply_2d_adv2d_64x64_n16.md
+# from one ncu capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_APPLY_FP64_N16 = 305.2e6 + 3.39e6
+
+
+def bf16_peak_tflops():
+    """Dense BF16 tensor peak for a kernel timed alone: the measured burst figure of
+    MEASURED_PEAKS.json when present, else the machine's fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json, burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s (no MEASURED_PEAKS.json)"
 
 
 def workload(n: int, h: float = 1.0, solenoidal: bool = True):
@@ -49,7 +60,7 @@ def workload(n: int, h: float = 1.0, solenoidal: bool = True):
 
 def workload_3d(n: int = 11):
     return dict(dim=3, n=n, nel=(16, 16, 16), h=1.0, dt=0.05,
-                velocity=synthetic.fourier_velocity(1705, 3), rhs_seed=1706)
+                velocity=synthetic.fourier_velocity(1707, 3), rhs_seed=1708)
 
 
 def time_each(fn, reps, stream, flush):
@@ -452,7 +463,7 @@ def run_3d(args):
         "warmup": args.warmup, "higher_is_better": True, "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"adv3d-fourier-16x16x16-n{n} (p={n - 1}), unit hexes, dt=0.05, "
-                               f"solenoidal random-Fourier velocity seed 1705, b~N(0,1) seed 1706",
+                               f"solenoidal random-Fourier velocity seed 1707, b~N(0,1) seed 1708",
                    "n": n, "nel": [16, 16, 16], "h": 1.0, "dt": 0.05, "dofs": N,
                    "apply_form": args.form,
                    "l2": "L2 flushed (256 MB write) before each timed launch"},
@@ -461,7 +472,9 @@ def run_3d(args):
                           "fp32_gdofs": apply["fp32"]["gdofs"], "fp32_ms": apply["fp32"]["ms"]},
         "operator": {"ms": op_ms, "gdofs": N / (op_ms * 1e-3) / 1e9},
         "gmres": gm,
-        "roofline": {"kernel": "3D apply (k_apply_z + k_apply_2d_w<double> on z slices)",
+        "roofline": {"kernel": "3D apply (k_apply_z + %s on z slices)"
+                               % ("k_apply_2d_w<double>" if args.form == "two-sided"
+                                  else "k_apply_2d_g<double>"),
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                      "peak_note": FP64_PEAK_NOTE, "algorithmic": "12 n^4 flop per element"},
@@ -548,7 +561,7 @@ def run_learned(args):
     with ClockSampler(0) as clk:
         Xt, Mt, _, basis = LN.element_samples(n, args.train_elems, range(1801, 1811), seed=1800)
         Xh, Mh, _, _ = LN.element_samples(n, args.eval_elems, (1811, 1812), seed=1799)
-        net = LN.Mlp(n, max_batch=4096, params=LN.default_params(n, 1800))
+        net = LN.Mlp(n, max_batch=16384, params=LN.default_params(n, 1800))
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -588,8 +601,10 @@ def run_learned(args):
         def learned_build():
             info["build"] = ctx.tpp_build_factors_learned(net, 0.05)
 
+        X16 = Xm.repeat(4, 1).contiguous()       # 16,384 rows: the roofline batch
+
         def forward():
-            net.forward(Xm)
+            net.forward(X16)
 
         for fn in (exact_step, learned_step, exact_build, learned_build, forward):
             for _ in range(args.warmup):
@@ -600,8 +615,8 @@ def run_learned(args):
                              ("forward", forward))}
     launches = lib.tpp_kernel_launch_count() - l0
     E = ctx.num_elem
-    flop_fwd = 2.0 * sum(a * c for a, c in zip(net.widths[:-1], net.widths[1:])) * E
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    flop_fwd = 2.0 * sum(a * c for a, c in zip(net.widths[:-1], net.widths[1:])) * X16.shape[0]
+    bf16_peak, peak_src = bf16_peak_tflops()
     lr_, ex = info["learned"], info["exact"]
 
     def stats(e):
@@ -632,12 +647,13 @@ def run_learned(args):
                    "mesh": stats(err_mesh)},
         "training": {"seconds": train_s, "epoch_loss_first": hist[0], "epoch_loss_last": hist[-1],
                      "elements_per_s": args.epochs * args.train_elems / train_s},
-        "roofline": {"kernel": "k_gemm (network forward, 4 GEMM launches over the mesh's "
-                               "4096 elements)", "bound": "alu",
+        "roofline": {"kernel": "k_gemm_tc (tcgen05 BF16, network forward: pair split + 4 "
+                               "GEMM launches over 16,384 rows)", "bound": "tensor",
                      "achieved": flop_fwd / (ms["forward"] * 1e-3) / 1e12,
-                     "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": flop_fwd / (ms["forward"] * 1e-3) / 1e12 / fp32_peak,
-                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                     "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": flop_fwd / (ms["forward"] * 1e-3) / 1e12 / bf16_peak,
+                     "peak_note": peak_src + "; algorithmic flops 2 B sum_l K_l N_l (the BF16 "
+                                  "pairs execute 2x that on the tensor pipe)",
                      "traffic": None},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

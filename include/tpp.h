@@ -51,7 +51,8 @@ typedef enum {
   TPP_ERR_SCHUR = 6,           /* Francis QR did not converge within its iteration cap */
   TPP_ERR_NAN = 7,             /* NaN or Inf met in a residual */
   TPP_ERR_UNSUPPORTED = 8,     /* valid request this build does not implement */
-  TPP_ERR_WORKSPACE = 9        /* workspace too small or misaligned */
+  TPP_ERR_WORKSPACE = 9,       /* workspace too small or misaligned */
+  TPP_ERR_TIMEOUT = 10         /* a device-side pipeline wait gave up (status word set; no trap) */
 } tpp_status;
 
 typedef enum { TPP_FP64 = 0, TPP_FP32 = 1 } tpp_prec;

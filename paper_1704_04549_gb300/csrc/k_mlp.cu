@@ -11,6 +11,14 @@
 // evaluated through the structure A~ = Q M Q^T (Q = [E | Qo] orthonormal, M the
 // r x r core) as L = 1 - 2 sum_k (Q^T a_k)^T Mn (Q^T b_k) + sum_kl (a_k.a_l)(b_k.b_l)
 // with Mn = M / ||M||_F.
+//
+// Every layer product runs on the tensor cores (k_tc_gemm.cu): BF16 weights times
+// activations and gradients carried as BF16 pairs hi + lo (FP32 to 2^-17), FP32
+// accumulation.  Per layer l (W_l [K_l][N_l], batch B):
+//   forward   Z_l = H_l W_l + b_l            A = (H_l hi, lo) [B][K_l],  B = W_l^T
+//             H_{l+1} = GELU(Z_l)            (fused epilogue, pair written for layer l + 1)
+//   backward  dW_l = H_l^T G_l               A = H_l^T pair [K_l][B], B = G_l^T pair [N_l][B]
+//             G_{l-1} = (G_l W_l^T) GELU'(Z_{l-1})   A = (G_l hi, lo), B = W_l [K_l][N_l]
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -18,16 +26,26 @@
 #include <string>
 
 #include "tpp_internal.cuh"
+#include "tpp_tc.cuh"
 
 struct tpp_mlp {
   int32_t n, max_batch;
   int32_t widths[5];
-  int64_t woff[4], boff[4], nparams;   // offsets (floats) of W_l [K][N] row-major and b_l
-  int64_t wbf_off[4];                   // offsets (bf16) of the BF16 weights
+  int32_t kp[4], np[4];                 // layer input / output widths padded to 64
+  int32_t bp;                           // max_batch padded to 64 (transposed buffers)
+  int64_t woff[4], boff[4], nparams;    // offsets (floats) of W_l [K][N] row-major and b_l
   char* ws;
   size_t ws_bytes;
-  size_t p32, pbf, grad, am, av, act, pre, g0, g1, lossv, scal;   // byte offsets
+  size_t p32, grad, am, av, pre, g[2], err, lossv, scal;   // byte offsets
+  size_t wt[4], wk[4];                  // BF16 weights: W_l^T [N][kp], W_l [K][np]
+  size_t hhi[4], hlo[4];                // layer inputs as pairs [max_batch][kp]
+  size_t thi[4], tlo[4];                // transposed layer inputs [K_l][bp]
+  size_t ghi[2], glo[2];                // gradients of the pre-activations as pairs
+  size_t gthi, gtlo;                    // transposed gradient pair [N_l][bp]
+  int64_t poff[4];                      // offsets (floats) of Z_l in pre
   int64_t step;
+  // tensor maps of every operand (buffers fixed at creation, sized for max_batch)
+  CUtensorMap fa[4][2], fb[4], da[4][2], db[4], wa[4][2], wb[4][2];
 };
 
 namespace tpp {
@@ -39,8 +57,11 @@ constexpr int kHidden = 512;
 inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct MlpLayout {
-  int64_t woff[4], boff[4], nparams, wbf_off[4], nwbf;
-  size_t p32, pbf, grad, am, av, act, pre, g0, g1, lossv, scal, total;
+  int64_t woff[4], boff[4], nparams, poff[4];
+  int32_t kp[4], np[4], bp;
+  size_t p32, grad, am, av, pre, g[2], err, lossv, scal;
+  size_t wt[4], wk[4], hhi[4], hlo[4], thi[4], tlo[4], ghi[2], glo[2], gthi, gtlo;
+  size_t total;
 };
 
 MlpLayout mlp_layout(int n, int max_batch, int32_t* widths) {
@@ -48,129 +69,95 @@ MlpLayout mlp_layout(int n, int max_batch, int32_t* widths) {
   widths[1] = widths[2] = widths[3] = kHidden;
   widths[4] = 4 * n * n;
   MlpLayout L{};
-  int64_t o = 0, ob = 0;
+  int64_t o = 0;
   for (int l = 0; l < 4; ++l) {
     L.woff[l] = o;
     o += (int64_t)widths[l] * widths[l + 1];
     L.boff[l] = o;
     o += widths[l + 1];
-    L.wbf_off[l] = ob;
-    ob += (int64_t)widths[l] * widths[l + 1];
+    L.kp[l] = tc::round_up(widths[l], 64);
+    L.np[l] = tc::round_up(widths[l + 1], 64);
   }
   L.nparams = o;
-  L.nwbf = ob;
-  int64_t actsz = 0;                // inputs of every layer and pre-activations
-  for (int l = 0; l < 4; ++l) actsz += (int64_t)max_batch * widths[l];
+  L.bp = tc::round_up(max_batch, 64);
   int64_t presz = 0;
-  for (int l = 0; l < 4; ++l) presz += (int64_t)max_batch * widths[l + 1];
+  for (int l = 0; l < 4; ++l) {
+    L.poff[l] = presz;
+    presz += (int64_t)max_batch * widths[l + 1];
+  }
+  int wmax = 0, npmax = 0;
+  for (int l = 0; l < 5; ++l) wmax = widths[l] > wmax ? widths[l] : wmax;
+  for (int l = 0; l < 4; ++l) npmax = L.np[l] > npmax ? L.np[l] : npmax;
   size_t off = 0;
   auto take = [&](size_t b) {
     const size_t r = off;
     off = al256(off + (b ? b : 8));
     return r;
   };
+  const size_t B = (size_t)max_batch;
   L.p32 = take(o * 4);
-  L.pbf = take(ob * 2);
   L.grad = take(o * 4);
   L.am = take(o * 4);
   L.av = take(o * 4);
-  L.act = take(actsz * 4);
   L.pre = take(presz * 4);
-  L.g0 = take((size_t)max_batch * 4 * n * n > (size_t)max_batch * kHidden
-                  ? (size_t)max_batch * 4 * n * n * 4 : (size_t)max_batch * kHidden * 4);
-  L.g1 = take((size_t)max_batch * 4 * n * n > (size_t)max_batch * kHidden
-                  ? (size_t)max_batch * 4 * n * n * 4 : (size_t)max_batch * kHidden * 4);
-  L.lossv = take((size_t)max_batch * 8);
+  L.g[0] = take(B * wmax * 4);
+  L.g[1] = take(B * wmax * 4);
+  for (int l = 0; l < 4; ++l) {
+    L.wt[l] = take((size_t)widths[l + 1] * L.kp[l] * 2);
+    L.wk[l] = take((size_t)widths[l] * L.np[l] * 2);
+    L.hhi[l] = take(B * L.kp[l] * 2);
+    L.hlo[l] = take(B * L.kp[l] * 2);
+    L.thi[l] = take((size_t)widths[l] * L.bp * 2);
+    L.tlo[l] = take((size_t)widths[l] * L.bp * 2);
+  }
+  for (int q = 0; q < 2; ++q) {
+    L.ghi[q] = take(B * npmax * 2);
+    L.glo[q] = take(B * npmax * 2);
+  }
+  L.gthi = take((size_t)wmax * L.bp * 2);
+  L.gtlo = take((size_t)wmax * L.bp * 2);
+  L.err = take(64);
+  L.lossv = take(B * 8);
   L.scal = take(64);
   L.total = off;
   return L;
 }
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-__device__ __forceinline__ float gelu_f(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
-         x * expf(-0.5f * x * x) * 0.39894228040143268f;
+template <typename T> T* at(const tpp_mlp* m, size_t off) {
+  return reinterpret_cast<T*>(m->ws + off);
 }
 
-// C[M x N] = op(A) op(B) (+ bias[j]) (+ C if accumulate), FP32 accumulation;
-// A(i, k) = A[i sai + k sak], B(k, j) = B[k sbk + j sbj].  With Cact, also
-// Cact = GELU(C).  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread.
-template <typename TB>
-__global__ void __launch_bounds__(256)
-k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sai, int64_t sak,
-       const TB* __restrict__ B, int64_t sbk, int64_t sbj, float* __restrict__ C, int ldc,
-       const float* __restrict__ bias, float* __restrict__ Cact, int accumulate) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  float acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
-  const bool akfast = (sak == 1), bjfast = (sbj == 1);
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int t = threadIdx.x; t < 64 * 16; t += 256) {
-      const int ii = akfast ? t / 16 : t % 64, kk = akfast ? t % 16 : t / 64;
-      const int gi = i0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < M && gk < K) ? A[gi * sai + gk * sak] : 0.0f;
-    }
-    for (int t = threadIdx.x; t < 16 * 64; t += 256) {
-      const int jj = bjfast ? t % 64 : t / 16, kk = bjfast ? t / 64 : t % 16;
-      const int gj = j0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < K) ? to_f(B[gk * sbk + gj * sbj]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-    __syncthreads();
+// tensor maps of every operand buffer of the network
+cudaError_t make_maps(tpp_mlp* m) {
+  const int* w = m->widths;
+  const int B = m->max_batch, bp = m->bp;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    const int kp = m->kp[l], np = m->np[l];
+    const int q = (3 - l) & 1;                       // pair buffer holding G_l
+    e = tc::make_map(&m->fa[l][0], m->ws + m->hhi[l], kp, B, kp);
+    if (e == cudaSuccess) e = tc::make_map(&m->fa[l][1], m->ws + m->hlo[l], kp, B, kp);
+    if (e == cudaSuccess) e = tc::make_map(&m->fb[l], m->ws + m->wt[l], kp, w[l + 1], kp);
+    if (e == cudaSuccess) e = tc::make_map(&m->da[l][0], m->ws + m->ghi[q], np, B, np);
+    if (e == cudaSuccess) e = tc::make_map(&m->da[l][1], m->ws + m->glo[q], np, B, np);
+    if (e == cudaSuccess) e = tc::make_map(&m->db[l], m->ws + m->wk[l], np, w[l], np);
+    if (e == cudaSuccess) e = tc::make_map(&m->wa[l][0], m->ws + m->thi[l], bp, w[l], bp);
+    if (e == cudaSuccess) e = tc::make_map(&m->wa[l][1], m->ws + m->tlo[l], bp, w[l], bp);
+    if (e == cudaSuccess) e = tc::make_map(&m->wb[l][0], m->ws + m->gthi, bp, w[l + 1], bp);
+    if (e == cudaSuccess) e = tc::make_map(&m->wb[l][1], m->ws + m->gtlo, bp, w[l + 1], bp);
   }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = i0 + ty * 4 + r;
-    if (i >= M) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = j0 + tx * 4 + c;
-      if (j >= N) continue;
-      float v = acc[r][c] + (bias ? bias[j] : 0.0f);
-      if (accumulate) v += C[(int64_t)i * ldc + j];
-      C[(int64_t)i * ldc + j] = v;
-      if (Cact) Cact[(int64_t)i * ldc + j] = gelu_f(v);
-    }
+  return e;
+}
+
+cudaError_t refresh_weights(tpp_mlp* m, cudaStream_t s) {
+  const float* p32 = at<float>(m, m->p32);
+  for (int l = 0; l < 4; ++l) {
+    cudaError_t e = tc::weights_bf16(p32 + m->woff[l], m->widths[l], m->widths[l + 1],
+                                     at<__nv_bfloat16>(m, m->wt[l]), m->kp[l],
+                                     at<__nv_bfloat16>(m, m->wk[l]), m->np[l], s);
+    if (e != cudaSuccess) return e;
   }
-}
-
-template <typename TB>
-void gemm(int M, int N, int K, const float* A, int64_t sai, int64_t sak, const TB* B,
-          int64_t sbk, int64_t sbj, float* C, int ldc, const float* bias, float* Cact,
-          int accumulate, cudaStream_t s) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_gemm<TB><<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, bias, Cact,
-                                  accumulate);
-  count_launch();
-}
-
-__global__ void k_gelu_back(float* __restrict__ G, const float* __restrict__ Z, int64_t count) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
-       t += (int64_t)gridDim.x * blockDim.x)
-    G[t] *= gelu_grad_f(Z[t]);
+  return cudaSuccess;
 }
 
 // db[j] = sum_i G[i, j] (rows in order: deterministic)
@@ -180,13 +167,6 @@ __global__ void k_colsum(const float* __restrict__ G, int rows, int cols, float*
   float sv = 0.0f;
   for (int i = 0; i < rows; ++i) sv += G[(int64_t)i * cols + j];
   db[j] = sv;
-}
-
-__global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
-                          int64_t count) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
-       t += (int64_t)gridDim.x * blockDim.x)
-    out[t] = __float2bfloat16_rn(in[t]);
 }
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master weights
@@ -315,6 +295,56 @@ __global__ void k_mean(const double* __restrict__ v, int count, float* __restric
   if (threadIdx.x == 0) *out = (float)(sv / count);
 }
 
+
+// Forward pass of B rows.  train: keep the transposed input pairs of every layer
+// (for the weight gradients) and write the outputs to Z_3; otherwise to out.
+cudaError_t forward_tc(tpp_mlp* m, const float* X, int B, float* out, bool train,
+                       cudaStream_t s) {
+  const int* w = m->widths;
+  const int Mt = tc::round_up(B, 64);
+  float* pre = at<float>(m, m->pre);
+  const float* p32 = at<float>(m, m->p32);
+  int* err = at<int>(m, m->err);
+  cudaError_t e = tc::split(X, B, w[0], w[0], at<__nv_bfloat16>(m, m->hhi[0]),
+                            at<__nv_bfloat16>(m, m->hlo[0]), m->kp[0],
+                            train ? at<__nv_bfloat16>(m, m->thi[0]) : nullptr,
+                            train ? at<__nv_bfloat16>(m, m->tlo[0]) : nullptr, m->bp, Mt, s);
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+    tc::Operands op;
+    op.a[0] = m->fa[l][0];
+    op.a[1] = m->fa[l][1];
+    op.b[0] = m->fb[l];
+    op.b[1] = m->fb[l];
+    op.ktiles[0] = op.ktiles[1] = m->kp[l] / 64;
+    op.nseg = 2;
+    tc::Epilogue ep{};
+    ep.M = B;
+    ep.N = w[l + 1];
+    ep.Mt = Mt;
+    ep.bias = p32 + m->boff[l];
+    ep.err = err;
+    if (l < 3) {
+      ep.kind = tc::kEpiHidden;
+      ep.outf = pre + m->poff[l];
+      ep.ldo = w[l + 1];
+      ep.hi = at<__nv_bfloat16>(m, m->hhi[l + 1]);
+      ep.lo = at<__nv_bfloat16>(m, m->hlo[l + 1]);
+      ep.ldh = m->kp[l + 1];
+      if (train) {
+        ep.thi = at<__nv_bfloat16>(m, m->thi[l + 1]);
+        ep.tlo = at<__nv_bfloat16>(m, m->tlo[l + 1]);
+        ep.ldt = m->bp;
+      }
+    } else {
+      ep.kind = tc::kEpiF32;
+      ep.outf = train ? pre + m->poff[3] : out;
+      ep.ldo = w[4];
+    }
+    e = tc::gemm(op, ep, B, w[l + 1], s);
+  }
+  return e;
+}
+
 }  // namespace
 
 // ---- helpers used by the context-side learned build (k_build.cu) -------------
@@ -322,26 +352,16 @@ int mlp_n(const tpp_mlp* net) { return net->n; }
 int mlp_max_batch(const tpp_mlp* net) { return net->max_batch; }
 
 void mlp_forward(tpp_mlp* net, const float* X, int B, float* out, cudaStream_t s) {
-  const float* p32 = reinterpret_cast<const float*>(net->ws + net->p32);
-  const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(net->ws + net->pbf);
-  float* act = reinterpret_cast<float*>(net->ws + net->act);
-  float* pre = reinterpret_cast<float*>(net->ws + net->pre);
-  const int* w = net->widths;
-  // layer l input H_l (act), pre-activation Z_l (pre); H_0 = X (copied)
-  int64_t ao = 0, po = 0;
-  cudaMemcpyAsync(act, X, (size_t)B * w[0] * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  for (int l = 0; l < 4; ++l) {
-    const float* H = act + ao;
-    float* Z = pre + po;
-    const bool last = (l == 3);
-    float* Hn = last ? nullptr : act + ao + (int64_t)B * w[l];
-    gemm<__nv_bfloat16>(B, w[l + 1], w[l], H, w[l], 1, wb + net->wbf_off[l], w[l + 1], 1, Z,
-                        w[l + 1], p32 + net->boff[l], Hn, 0, s);
-    ao += (int64_t)B * w[l];
-    po += (int64_t)B * w[l + 1];
-  }
-  cudaMemcpyAsync(out, pre + po - (int64_t)B * w[4], (size_t)B * w[4] * sizeof(float),
-                  cudaMemcpyDeviceToDevice, s);
+  forward_tc(net, X, B, out, false, s);
+}
+
+int mlp_read_error(const tpp_mlp* net, cudaStream_t s) {
+  int v = 0;
+  if (cudaMemcpyAsync(&v, net->ws + net->err, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return v;
 }
 
 cudaError_t mlp_factor_loss(const float* out, const double* Mn, const double* Qo, int n, int rz,
@@ -397,25 +417,43 @@ tpp_status tpp_mlp_create(tpp_mlp** out, int32_t n, int32_t max_batch, void* wor
   for (int l = 0; l < 4; ++l) {
     m->woff[l] = L.woff[l];
     m->boff[l] = L.boff[l];
-    m->wbf_off[l] = L.wbf_off[l];
+    m->poff[l] = L.poff[l];
+    m->kp[l] = L.kp[l];
+    m->np[l] = L.np[l];
+    m->wt[l] = L.wt[l];
+    m->wk[l] = L.wk[l];
+    m->hhi[l] = L.hhi[l];
+    m->hlo[l] = L.hlo[l];
+    m->thi[l] = L.thi[l];
+    m->tlo[l] = L.tlo[l];
   }
+  m->bp = L.bp;
   m->nparams = L.nparams;
   m->ws = static_cast<char*>(workspace);
   m->ws_bytes = ws_bytes;
   m->p32 = L.p32;
-  m->pbf = L.pbf;
   m->grad = L.grad;
   m->am = L.am;
   m->av = L.av;
-  m->act = L.act;
   m->pre = L.pre;
-  m->g0 = L.g0;
-  m->g1 = L.g1;
+  for (int q = 0; q < 2; ++q) {
+    m->g[q] = L.g[q];
+    m->ghi[q] = L.ghi[q];
+    m->glo[q] = L.glo[q];
+  }
+  m->gthi = L.gthi;
+  m->gtlo = L.gtlo;
+  m->err = L.err;
   m->lossv = L.lossv;
   m->scal = L.scal;
   m->step = 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(m->ws, 0, L.total, s);
+  cudaError_t e = make_maps(m);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_check(e, "tpp_mlp_create: tensor maps");
+  }
+  e = cudaMemsetAsync(m->ws, 0, L.total, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     delete m;
@@ -434,20 +472,14 @@ tpp_status tpp_mlp_set_params(tpp_mlp* m, const float* host, void* stream) {
     return TPP_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* p32 = reinterpret_cast<float*>(m->ws + m->p32);
+  float* p32 = at<float>(m, m->p32);
   cudaError_t e = cudaMemcpyAsync(p32, host, (size_t)m->nparams * 4, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_check(e, "tpp_mlp_set_params");
-  __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(m->ws + m->pbf);
-  for (int l = 0; l < 4; ++l) {
-    k_to_bf16<<<152, 256, 0, s>>>(p32 + m->woff[l], wb + m->wbf_off[l],
-                                   (int64_t)m->widths[l] * m->widths[l + 1]);
-    count_launch();
-  }
+  if (e == cudaSuccess) e = refresh_weights(m, s);
   // fresh optimiser state
-  cudaMemsetAsync(m->ws + m->am, 0, (size_t)m->nparams * 4, s);
-  cudaMemsetAsync(m->ws + m->av, 0, (size_t)m->nparams * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->ws + m->am, 0, (size_t)m->nparams * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->ws + m->av, 0, (size_t)m->nparams * 4, s);
   m->step = 0;
-  return cuda_check(cudaGetLastError(), "tpp_mlp_set_params");
+  return cuda_check(e, "tpp_mlp_set_params");
 }
 
 tpp_status tpp_mlp_get_params(const tpp_mlp* m, float* host, void* stream) {
@@ -459,7 +491,12 @@ tpp_status tpp_mlp_get_params(const tpp_mlp* m, float* host, void* stream) {
   cudaError_t e = cudaMemcpyAsync(host, m->ws + m->p32, (size_t)m->nparams * 4,
                                   cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return cuda_check(e, "tpp_mlp_get_params");
+  if (e != cudaSuccess) return cuda_check(e, "tpp_mlp_get_params");
+  if (mlp_read_error(m, s) != 0) {
+    set_error("a tensor-core GEMM of the network gave up waiting on its pipeline");
+    return TPP_ERR_TIMEOUT;
+  }
+  return TPP_OK;
 }
 
 tpp_status tpp_mlp_forward(tpp_mlp* m, const float* X, int32_t B, float* out, void* stream) {
@@ -468,8 +505,7 @@ tpp_status tpp_mlp_forward(tpp_mlp* m, const float* X, int32_t B, float* out, vo
     return TPP_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  mlp_forward(m, X, B, out, s);
-  return cuda_check(cudaGetLastError(), "tpp_mlp_forward");
+  return cuda_check(forward_tc(m, X, B, out, false, s), "tpp_mlp_forward");
 }
 
 // forward, loss and gradients (into the net's gradient buffer); with lr > 0 also
@@ -484,66 +520,85 @@ tpp_status tpp_mlp_train_step(tpp_mlp* m, const tpp_ctx* basis, const float* X, 
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int* w = m->widths;
-  float* p32 = reinterpret_cast<float*>(m->ws + m->p32);
-  __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(m->ws + m->pbf);
-  float* grad = reinterpret_cast<float*>(m->ws + m->grad);
-  float* act = reinterpret_cast<float*>(m->ws + m->act);
-  float* pre = reinterpret_cast<float*>(m->ws + m->pre);
-  float* G0 = reinterpret_cast<float*>(m->ws + m->g0);
-  float* G1 = reinterpret_cast<float*>(m->ws + m->g1);
-  double* lossv = reinterpret_cast<double*>(m->ws + m->lossv);
-  // forward (activations kept)
-  int64_t aoff[4], poff[4], ao = 0, po = 0;
-  cudaMemcpyAsync(act, X, (size_t)B * w[0] * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  for (int l = 0; l < 4; ++l) {
-    aoff[l] = ao;
-    poff[l] = po;
-    const bool last = (l == 3);
-    gemm<__nv_bfloat16>(B, w[l + 1], w[l], act + ao, w[l], 1, wb + m->wbf_off[l], w[l + 1], 1,
-                        pre + po, w[l + 1], p32 + m->boff[l],
-                        last ? nullptr : act + ao + (int64_t)B * w[l], 0, s);
-    ao += (int64_t)B * w[l];
-    po += (int64_t)B * w[l + 1];
-  }
-  // loss and dL/d(outputs) into G0
-  cudaError_t e = mlp_factor_loss(pre + poff[3], Mn, basis->p<double>(basis->L.qo), m->n,
-                                  basis->rz, B, 1.0f / B, G0, lossv, s);
+  const int Mt = tc::round_up(B, 64);
+  float* p32 = at<float>(m, m->p32);
+  float* grad = at<float>(m, m->grad);
+  float* pre = at<float>(m, m->pre);
+  double* lossv = at<double>(m, m->lossv);
+  int* err = at<int>(m, m->err);
+  cudaError_t e = forward_tc(m, X, B, nullptr, true, s);
+  if (e != cudaSuccess) return cuda_check(e, "network forward");
+  // loss and dL/d(outputs) = G_3 (FP32) into g[0], then its BF16 pair
+  e = mlp_factor_loss(pre + m->poff[3], Mn, basis->p<double>(basis->L.qo), m->n, basis->rz, B,
+                      1.0f / B, at<float>(m, m->g[0]), lossv, s);
   if (e != cudaSuccess) return cuda_check(e, "k_factor_loss");
   k_mean<<<1, 32, 0, s>>>(lossv, B, loss);
   count_launch();
-  // backward
-  float* Gc = G0;
-  float* Gn = G1;
-  for (int l = 3; l >= 0; --l) {
-    const int K = w[l], N = w[l + 1];
-    if (l < 3) {
-      k_gelu_back<<<152 * 4, 256, 0, s>>>(Gc, pre + poff[l], (int64_t)B * N);
-      count_launch();
-    }
-    // dW = H^T G  (K x N), db = column sums of G
-    gemm<float>(K, N, B, act + aoff[l], 1, K, Gc, N, 1, grad + m->woff[l], N, nullptr, nullptr, 0,
-                s);
-    k_colsum<<<(N + 255) / 256, 256, 0, s>>>(Gc, B, N, grad + m->boff[l]);
+  e = tc::split(at<float>(m, m->g[0]), B, w[4], w[4], at<__nv_bfloat16>(m, m->ghi[0]),
+                at<__nv_bfloat16>(m, m->glo[0]), m->np[3], at<__nv_bfloat16>(m, m->gthi),
+                at<__nv_bfloat16>(m, m->gtlo), m->bp, Mt, s);
+  for (int l = 3; l >= 0 && e == cudaSuccess; --l) {
+    const int q = (3 - l) & 1;
+    // dW_l = H_l^T G_l: pairs (hi hi + hi lo + lo hi) over the batch
+    tc::Operands op;
+    op.a[0] = m->wa[l][0];
+    op.a[1] = m->wa[l][0];
+    op.a[2] = m->wa[l][1];
+    op.b[0] = m->wb[l][0];
+    op.b[1] = m->wb[l][1];
+    op.b[2] = m->wb[l][0];
+    op.ktiles[0] = op.ktiles[1] = op.ktiles[2] = Mt / 64;
+    op.nseg = 3;
+    tc::Epilogue ep{};
+    ep.kind = tc::kEpiF32;
+    ep.M = w[l];
+    ep.N = w[l + 1];
+    ep.outf = grad + m->woff[l];
+    ep.ldo = w[l + 1];
+    ep.err = err;
+    e = tc::gemm(op, ep, w[l], w[l + 1], s);
+    if (e != cudaSuccess) break;
+    // db_l = column sums of G_l
+    k_colsum<<<(w[l + 1] + 255) / 256, 256, 0, s>>>(at<float>(m, m->g[q]), B, w[l + 1],
+                                                     grad + m->boff[l]);
     count_launch();
-    if (l > 0) {   // dH = G W^T  (B x K)
-      gemm<__nv_bfloat16>(B, K, N, Gc, N, 1, wb + m->wbf_off[l], 1, N, Gn, K, nullptr, nullptr,
-                          0, s);
-      float* t = Gc;
-      Gc = Gn;
-      Gn = t;
-    }
+    if (l == 0) break;
+    // G_{l-1} = (G_l W_l^T) GELU'(Z_{l-1})
+    tc::Operands od;
+    od.a[0] = m->da[l][0];
+    od.a[1] = m->da[l][1];
+    od.b[0] = m->db[l];
+    od.b[1] = m->db[l];
+    od.ktiles[0] = od.ktiles[1] = m->np[l] / 64;
+    od.nseg = 2;
+    tc::Epilogue eg{};
+    eg.kind = tc::kEpiGeluBack;
+    eg.M = B;
+    eg.N = w[l];
+    eg.Mt = Mt;
+    eg.zprev = pre + m->poff[l - 1];
+    eg.ldz = w[l];
+    eg.outf = at<float>(m, m->g[1 - q]);
+    eg.ldo = w[l];
+    eg.hi = at<__nv_bfloat16>(m, m->ghi[1 - q]);
+    eg.lo = at<__nv_bfloat16>(m, m->glo[1 - q]);
+    eg.ldh = m->np[l - 1];
+    eg.thi = at<__nv_bfloat16>(m, m->gthi);
+    eg.tlo = at<__nv_bfloat16>(m, m->gtlo);
+    eg.ldt = m->bp;
+    eg.err = err;
+    e = tc::gemm(od, eg, B, w[l], s);
   }
+  if (e != cudaSuccess) return cuda_check(e, "network backward");
   if (lr > 0.0f) {
     m->step += 1;
     const double t = (double)m->step;
     const float c1 = (float)(1.0 / (1.0 - pow(0.9, t))), c2 = (float)(1.0 / (1.0 - pow(0.999, t)));
-    k_adam<<<152 * 4, 256, 0, s>>>(p32, grad, reinterpret_cast<float*>(m->ws + m->am),
-                                   reinterpret_cast<float*>(m->ws + m->av), m->nparams, lr, c1, c2);
+    k_adam<<<152 * 4, 256, 0, s>>>(p32, grad, at<float>(m, m->am), at<float>(m, m->av),
+                                   m->nparams, lr, c1, c2);
     count_launch();
-    for (int l = 0; l < 4; ++l) {
-      k_to_bf16<<<152, 256, 0, s>>>(p32 + m->woff[l], wb + m->wbf_off[l], (int64_t)w[l] * w[l + 1]);
-      count_launch();
-    }
+    e = refresh_weights(m, s);
+    if (e != cudaSuccess) return cuda_check(e, "BF16 weights");
   }
   return cuda_check(cudaGetLastError(), "tpp_mlp_train_step");
 }
@@ -556,10 +611,11 @@ tpp_status tpp_mlp_element_loss(tpp_mlp* m, const tpp_ctx* basis, const float* X
     return TPP_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* out = reinterpret_cast<float*>(m->ws + m->g0);
-  mlp_forward(m, X, B, out, s);
-  cudaError_t e = mlp_factor_loss(out, Mn, basis->p<double>(basis->L.qo), m->n, basis->rz, B,
-                                  1.0f, nullptr, loss, s);
+  float* out = at<float>(m, m->g[0]);
+  cudaError_t e = forward_tc(m, X, B, out, false, s);
+  if (e != cudaSuccess) return cuda_check(e, "network forward");
+  e = mlp_factor_loss(out, Mn, basis->p<double>(basis->L.qo), m->n, basis->rz, B, 1.0f, nullptr,
+                      loss, s);
   if (e != cudaSuccess) return cuda_check(e, "k_factor_loss");
   return cuda_check(cudaGetLastError(), "tpp_mlp_element_loss");
 }

@@ -477,7 +477,12 @@ tpp_status tpp_build_factors_learned(tpp_ctx* c, tpp_mlp* net, double threshold,
   TPP_TRY_CUDA(launch_learned_accept(c, out, norms, lossv, threshold, c->p<int32_t>(c->L.lmask), s),
                "learned accept");
   TPP_TRY_CUDA(launch_ksvd_pipeline(c, s, c->p<int32_t>(c->L.lmask)), "k_build (fallback)");
-  return finish_build(c, report, s);
+  const tpp_status st = finish_build(c, report, s);
+  if (mlp_read_error(net, s) != 0) {
+    set_error("a tensor-core GEMM of the network gave up waiting on its pipeline");
+    return TPP_ERR_TIMEOUT;
+  }
+  return st;
 }
 
 tpp_status tpp_build_block_jacobi(tpp_ctx* c, void* stream) {

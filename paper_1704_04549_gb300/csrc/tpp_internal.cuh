@@ -200,6 +200,8 @@ cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const doub
                                   const double* lossv, double threshold, int32_t* mask,
                                   cudaStream_t s);
 void mlp_forward(tpp_mlp* net, const float* X, int B, float* out, cudaStream_t s);
+// error word of the network's tensor-core GEMMs (synchronises s): 0 = no pipeline wait gave up
+int mlp_read_error(const tpp_mlp* net, cudaStream_t s);
 size_t ksvd_scr_doubles(int n, int rz);   // KSVD scratch per element (doubles)
 int mlp_n(const tpp_mlp* net);
 int mlp_max_batch(const tpp_mlp* net);

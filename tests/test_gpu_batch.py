@@ -70,7 +70,7 @@ def test_batch_factors_and_apply_match_oracle(dim, n, E, R, h):
         kappa = np.linalg.cond(P)
         for r in range(R):
             err = rel(x[e, r], apply_dense(P, B[e, r]))
-            assert err <= solve_tol(kappa), (e, r, err, kappa, cpair[e], cz)
+            assert err <= solve_tol(kappa, cpair[e] * cz), (e, r, err, kappa, cpair[e], cz)
 
 
 @pytest.mark.parametrize("dim,n,E,R,h", [(2, 8, 12, 4, H), (2, 16, 6, 3, 1.0), (2, 31, 3, 2, 1.0),

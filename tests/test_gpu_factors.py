@@ -35,7 +35,7 @@ def _check_elements(ctx, dg, elems, tol_sigma=FP64_TOL, tol_P=FP64_TOL, tol_x=FP
         err = rel(x[e * nl:(e + 1) * nl], x_ref)
         kappa = np.linalg.cond(P_ref)
         worst = max(worst, err)
-        assert err <= max(tol_x, solve_tol(kappa)), (e, err, kappa, cpair[e])
+        assert err <= max(tol_x, solve_tol(kappa, cpair[e])), (e, err, kappa, cpair[e])
         assert cpair[e] <= 1e8, (e, cpair[e])
         assert flags[e] & 12 == 0          # no Schur failure, no singular factor
     print(f"FP64 apply vs oracle, n={n}: max element relative error {worst:.2e} "

@@ -286,3 +286,73 @@ def test_solve_learned_iteration_fallback():
     x, r = ctx.tpp_solve_learned(net, to_dev(b), threshold=0.0, iter_limit=r_exact["iters"] + 1,
                                  rtol=1e-8)
     assert r["rebuilt"] == 0 and r["converged"] and r["iters"] == r_exact["iters"]
+
+
+def _build_ms(fn, reps=5):
+    """Median device time (ms) of fn() on the current stream."""
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def test_trained_network_gain_on_the_mesh():
+    """What the trained network gains over the exact construction on the 64 x 64 mesh
+    (n = 16, unit quads, dt = 0.05, field 1705, which training never sees): trained
+    on 20,000 isolated elements of ten other fields (30 epochs), it keeps its own
+    factors on most elements at the 5% error threshold, GMRES with the learned
+    preconditioner reaches the 1e-8 true residual (checked with the oracle's
+    sum-factorised matvec) in at most the exact preconditioner's iterations + 2, and
+    the learned build (network, error check, exact KSVD of the fallback elements,
+    inverses and Schur forms) takes less time than the exact build."""
+    from paper_1704_04549_gb300 import learned as LN
+    n = 16
+    Xt, Mt, _, basis = LN.element_samples(n, 20000, range(1801, 1811), seed=1800)
+    net = LN.Mlp(n, max_batch=4096, params=LN.default_params(n, 1800))
+    hist = LN.train(net, basis, Xt, Mt, 30, batch=512, lr=1e-3, lr_min=1e-5)
+    ctx, dg = make_pair(n, (64, 64), 0.05, synthetic.fourier_velocity(1705, 2),
+                        features=TPP_FEAT_LEARNED, h=1.0)
+    b = synthetic.rhs(1706, dg.ndof)
+    E = dg.mesh.num_elem
+    ctx.tpp_build_factors()
+    t_exact = _build_ms(ctx.tpp_build_factors)
+    _, r_exact = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    t_learned = _build_ms(lambda: ctx.tpp_build_factors_learned(net, 0.05))
+    rep = ctx.tpp_build_factors_learned(net, 0.05)
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    print(f"learned gain, 64x64 n=16: training loss {hist[0]:.3e} -> {hist[-1]:.3e}; "
+          f"{E - rep['num_fallback']} of {E} elements keep the network's factors; "
+          f"build {t_exact:.2f} ms exact -> {t_learned:.2f} ms learned; GMRES "
+          f"{r_exact['iters']} -> {r['iters']} iterations")
+    assert hist[-1] < 0.2 * hist[0]
+    assert rep["num_fallback"] <= E // 2
+    assert r["converged"] and r["iters"] <= r_exact["iters"] + 2
+    Ax = dg.apply_sumfact(to_host(x))
+    assert np.linalg.norm(Ax - b) <= 1.0001e-8 * np.linalg.norm(b)
+    assert t_learned < t_exact
+
+
+@pytest.mark.parametrize("n,B", [(16, 300)])
+def test_large_batch_gradients_match_oracle(n, B):
+    """A batch of three 128-row tiles with a ragged tail at n = 16 (output width 1024,
+    input width 513): loss and every layer's gradients against the oracle."""
+    from paper_1704_04549_gb300 import Mlp
+    ctx, dg = _mesh(n, (10, 30))
+    X, Mn, _ = ctx.tpp_learned_inputs()
+    assert X.shape[0] == B
+    ps = _params(n, 23, out_scale=0.2)
+    net = Mlp(n, max_batch=512, params=_flat(ps))
+    loss = float(to_host(net.train_step(ctx, X, Mn, lr=0.0))[0])
+    g = to_host(net.gradients())
+    out, pre = mlp.forward(ps, to_host(X).astype(np.float64))
+    At = [rearrange(dg.element_block(e), n, n, n, n) for e in range(B)]
+    ref_loss, dout = mlp.factor_loss(At, out, n)
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
+    for l, ((dW, db), (gW, gb)) in enumerate(zip(mlp.backward(ps, pre, dout), _unflat(g, n))):
+        assert rel(gW, dW) <= 1e-3, (l, rel(gW, dW))
+        assert rel(gb, db) <= 1e-3, (l, rel(gb, db))
