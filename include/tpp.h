@@ -71,37 +71,40 @@ typedef enum {
 #define TPP_FEAT_LEARNED      8u  /* reserve the buffers of tpp_build_factors_learned (2D) */
 
 /*
- * Problem description.  Velocity field (component c) at the normalised point
- * xi = x / L of the periodic domain [0, L_1] x ... (L_d = nel[d] h):
- *   a_c(x) = a0[c] + sum_m amp[c*n_modes + m] * cos(2 pi kvec[(c*n_modes + m)*dim + .] . xi
- *                                                  + phase[c*n_modes + m])
- * All pointers are host pointers, read during tpp_create only.
- * Mesh: element (ex, ey[, ez]) covers [ex h, (ex+1) h] x ...; periodic wrap in
- * every direction.  Limits: dim in {2, 3}; 1 <= n <= 32 (2D), 1 <= n <= 16 (3D); nel[d] >= 1;
- * h > 0; dt >= 0; 0 <= n_modes <= 64.
+ * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
+ * one implicit step of u_t + div(a u) = 0, discretised on num_elem elements of width h
+ * (squares / cubes of side h, affine), n = p + 1 Gauss-Legendre nodes per direction,
+ * quadrature collocated with the nodes, upwind flux.  The library needs the flux
+ * Jacobians of Alg. matrix-free-matvec (steps 1-2): dF_c/du = a_c at the volume nodes and
+ * a . n_outward at the face nodes, given here as arrays, and the element connectivity.
+ *
+ *  vel_nodes        device [dim][num_elem * n^dim]: a_c at the volume nodes, element-major,
+ *                   node index i + n j (+ n^2 k), x fastest.
+ *  vel_face_normal  device [num_elem][2 dim][n^(dim-1)]: a . n_outward at the face nodes,
+ *                   faces ordered -x, +x, -y, +y (, -z, +z), face nodes by their tangential
+ *                   indices in (x, y, z) order, the first fastest.  Both sides of an interior
+ *                   face should carry opposite values (the caller's data is used as given).
+ *  nbr              device [num_elem][2 dim]: the element across each face, which meets it
+ *                   with its opposite face (-x against +x, ...) and the same tangential node
+ *                   order; -1 for no coupling (the face keeps only its own outflow term, so a
+ *                   problem with every entry -1 is a batch of block-diagonal systems).
+ * The three arrays are read by tpp_create (and tpp_set_velocity) only; the library keeps
+ * its own copies.  nrhs right-hand sides per element are stored together in every vector:
+ * layout [num_elem][nrhs][n^dim] (float64 unless stated).
+ * Limits: dim in {2, 3}; 1 <= n <= 32 (2D), 1 <= n <= 16 (3D); num_elem >= 1; nrhs >= 1;
+ * h > 0; dt >= 0; every nbr entry in [-1, num_elem).
  */
 typedef struct {
   int32_t dim;
   int32_t n;
-  int32_t nel[3];
+  int64_t num_elem;
+  int32_t nrhs;
+  int32_t reserved;
   double h;
   double dt;
-  int32_t n_modes;
-  const double* a0;     /* [dim] */
-  const double* amp;    /* [dim * n_modes] */
-  const int32_t* kvec;  /* [dim * n_modes * dim] */
-  const double* phase;  /* [dim * n_modes] */
-  /* Batch of block-diagonal systems (batch_rhs >= 1): nel[0] isolated elements (nel[1],
-   * nel[2] ignored), element e the cube of width h centred at centres[e * dim + .] in the
-   * unit domain (velocity at the absolute point, xi = x), each system the element's
-   * diagonal block alone (mass, volume and its own upwind face terms; no neighbour
-   * coupling), solved for batch_rhs right-hand sides at once.  Vectors are laid out
-   * [element][rhs][n^dim].  batch_rhs = 0: the periodic mesh described above. */
-  int32_t batch_rhs;
-  const double* centres;  /* host [nel[0] * dim], batch mode only */
-  double batch_span;      /* batch mode: width of each element in the coordinates of the
-                             velocity field (the unit domain); 0 means h.  The element's
-                             integrals scale with its physical width h. */
+  const double* vel_nodes;
+  const double* vel_face_normal;
+  const int32_t* nbr;
 } tpp_problem;
 
 typedef struct {
@@ -164,9 +167,11 @@ size_t tpp_workspace_bytes(const tpp_problem* prob, int32_t max_restart, uint32_
 /*
  * Create a context on the caller's workspace and run the precomputation step of
  * Alg. matrix-free-matvec (steps 1-2): 1D Gauss-Legendre tables, the flux
- * Jacobians dF/du = a at volume nodes and dF^/du^- = max(a.n, 0) at face nodes
- * (Sec. 3.4.1), and the element-independent basis of the rearranged block used
- * by the factor build.  Synchronises `stream` before returning.
+ * Jacobians dF/du = a at volume nodes and a.n at face nodes scaled by the
+ * quadrature weights (Sec. 3.4.1), the connectivity, and the element-independent
+ * basis of the rearranged block used by the factor build.  vel_nodes and
+ * vel_face_normal may be NULL (a zero field, to be set by tpp_set_velocity before
+ * the first build); nbr may not.  Synchronises `stream` before returning.
  * workspace: device, ws_bytes >= tpp_workspace_bytes(prob, max_restart, features).
  */
 tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restart,
@@ -174,6 +179,20 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
 
 /* Release the host-side context (the workspace stays the caller's). */
 void tpp_destroy(tpp_ctx* ctx);
+
+/*
+ * Replace the linearisation data of a context (Alg. matrix-free-matvec steps 1-2 again):
+ * the velocity at the nodes and faces (layouts as in tpp_problem; device, read before
+ * the call returns) and the step dt >= 0.  The factors and block-Jacobi LU of the old
+ * operator become stale: call tpp_build_factors (and tpp_build_block_jacobi) again.
+ * Synchronises `stream`.
+ */
+tpp_status tpp_set_velocity(tpp_ctx* ctx, const double* vel_nodes, const double* vel_face_normal,
+                            double dt, void* stream);
+
+/* Nodes and weights of the Gauss-Legendre rule on [0, 1] (host arrays of n doubles), for
+ * callers that evaluate their field at the nodes.  Synchronises the legacy stream. */
+tpp_status tpp_gauss_legendre(const tpp_ctx* ctx, double* nodes, double* weights);
 
 /*
  * Form the Kronecker preconditioner of every element (Alg. 2d-form in 2D,
@@ -211,41 +230,51 @@ tpp_status tpp_build_block_jacobi(tpp_ctx* ctx, void* stream);
  * form (default): R = L_B^-1 B S_A^T, then C2 Z + Z T1^T = R column block by
  * column block from the last with the stored shifted inverses, x = Z Q1^T.
  * 3D applies the A1^-1 factor along z first, then the 2D form on each z slice.
- * b, x: device float64 [num_dofs], must not alias.  prec selects the arithmetic
- * and factor precision (TPP_FP32 needs TPP_FEAT_MIXED).  Asynchronous.
+ * b, x: device float64 [num_elem][nrhs][n^dim], 1 <= nrhs <= the problem's nrhs, must not
+ * alias.  prec selects the arithmetic and factor precision (TPP_FP32 needs
+ * TPP_FEAT_MIXED).  Asynchronous.
  */
-tpp_status tpp_apply_inverse(const tpp_ctx* ctx, const double* b, double* x, int32_t prec,
-                             void* stream);
+tpp_status tpp_apply_inverse(const tpp_ctx* ctx, const double* b, double* x, int32_t nrhs,
+                             int32_t prec, void* stream);
 
-/* x = (block-Jacobi)^-1 b with the exact block LU factors.  Asynchronous. */
-tpp_status tpp_apply_block_jacobi(const tpp_ctx* ctx, const double* b, double* x, void* stream);
+/* x = (block-Jacobi)^-1 b with the exact block LU factors (layout and nrhs as in
+ * tpp_apply_inverse).  Asynchronous. */
+tpp_status tpp_apply_block_jacobi(const tpp_ctx* ctx, const double* b, double* x, int32_t nrhs,
+                                  void* stream);
 
 /*
  * y = (M + dt A) x by sum factorisation (Alg. matrix-free-matvec step 3): mass
  * h^d w(x)w, volume -dt h^(d-1) sum_c (D^T along c) of w a_c x, upwind face
- * fluxes lifted by the endpoint values.  x, y: device float64 [num_dofs], must
- * not alias.  Asynchronous.
+ * fluxes lifted by the endpoint values; across a face with neighbour e' the
+ * inflow reads the same right-hand side r of e'.  x, y: device float64
+ * [num_elem][nrhs][n^dim], 1 <= nrhs <= the problem's nrhs, must not alias.
+ * Asynchronous.
  */
-tpp_status dg_apply_sumfact(const tpp_ctx* ctx, const double* x, double* y, void* stream);
+tpp_status dg_apply_sumfact(const tpp_ctx* ctx, const double* x, double* y, int32_t nrhs,
+                            void* stream);
 
 /*
  * FP32 forms used by the inner solves of the mixed-precision mode (contexts
  * created with TPP_FEAT_MIXED): the same operator on float vectors with float
  * copies of the flux Jacobian coefficients (FP32 arithmetic throughout), and
  * x = P^-1 b with the FP32 factors on float vectors (tpp_apply_inverse_f32
- * needs tpp_build_factors first).  Vectors: device float32 [num_dofs], must not
- * alias.  The paper has no FP32 variant; these follow Sec. 3.4 and Alg.
+ * needs tpp_build_factors first).  Vectors: device float32 [num_elem][nrhs][n^dim],
+ * must not alias.  The paper has no FP32 variant; these follow Sec. 3.4 and Alg.
  * 2d-apply / 3d-apply in single precision.  Asynchronous.
  */
-tpp_status dg_apply_sumfact_f32(const tpp_ctx* ctx, const float* x, float* y, void* stream);
-tpp_status tpp_apply_inverse_f32(const tpp_ctx* ctx, const float* b, float* x, void* stream);
+tpp_status dg_apply_sumfact_f32(const tpp_ctx* ctx, const float* x, float* y, int32_t nrhs,
+                                void* stream);
+tpp_status tpp_apply_inverse_f32(const tpp_ctx* ctx, const float* b, float* x, int32_t nrhs,
+                                 void* stream);
 
 /*
  * Solve S x = b by restarted right-preconditioned GMRES(m) (Sec. 5 opening;
  * classical Gram-Schmidt with one reorthogonalisation, Givens rotations on
  * the device).  b: device float64 [num_dofs]; x: device float64 [num_dofs],
- * on entry the initial guess, on exit the solution.  Synchronises `stream`
- * and fills `result` (host, required).
+ * on entry the initial guess, on exit the solution.  The problem's nrhs
+ * right-hand sides form one block-diagonal system (one Krylov space, residual
+ * norms over all of them).  Synchronises `stream` and fills `result` (host,
+ * required).
  */
 tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres_opts* opts,
                        tpp_gmres_result* result, void* stream);
@@ -258,15 +287,16 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
  * lives in a static 4 MiB device array inside libtpp (held by every GPU that
  * loads the library until exit) instead of the context workspace; no device
  * memory is allocated.  The paper has no counterpart to this entry point.
- * x, y: device float64 [num_dofs], must not alias.  2D contexts with
- * num_elem * 4 * n <= 524288 only; larger ones return TPP_ERR_INVALID_ARG.
+ * x, y: device float64 [num_elem][nrhs][n^2], must not alias.  2D contexts with
+ * num_elem * nrhs * 4 * n <= 524288 only; larger ones return TPP_ERR_INVALID_ARG.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU race.  The current device
  * must be the one the context was created on (TPP_ERR_INVALID_ARG otherwise), since
  * the array's address is that of the current device.  Asynchronous.
  */
-tpp_status dg_apply_sumfact_static(const tpp_ctx* ctx, const double* x, double* y, void* stream);
+tpp_status dg_apply_sumfact_static(const tpp_ctx* ctx, const double* x, double* y, int32_t nrhs,
+                                   void* stream);
 
 /* Device pointers into the workspace for inspection (tests); NULL if absent. */
 typedef struct {

@@ -18,12 +18,10 @@ TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1,
 
 
 class Problem(C.Structure):
-    _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("nel", C.c_int32 * 3),
-                ("h", C.c_double), ("dt", C.c_double), ("n_modes", C.c_int32),
-                ("a0", C.POINTER(C.c_double)), ("amp", C.POINTER(C.c_double)),
-                ("kvec", C.POINTER(C.c_int32)), ("phase", C.POINTER(C.c_double)),
-                ("batch_rhs", C.c_int32), ("centres", C.POINTER(C.c_double)),
-                ("batch_span", C.c_double)]
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("num_elem", C.c_int64),
+                ("nrhs", C.c_int32), ("reserved", C.c_int32), ("h", C.c_double),
+                ("dt", C.c_double), ("vel_nodes", C.c_void_p), ("vel_face_normal", C.c_void_p),
+                ("nbr", C.c_void_p)]
 
 
 class GmresOpts(C.Structure):
@@ -58,12 +56,19 @@ EXPORTS = {
     "tpp_destroy": (None, [C.c_void_p]),
     "tpp_build_factors": (C.c_int, [C.c_void_p, C.POINTER(BuildReport), C.c_void_p]),
     "tpp_build_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p]),
-    "tpp_apply_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
-    "tpp_apply_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "dg_apply_sumfact": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "dg_apply_sumfact_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "dg_apply_sumfact_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_set_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "tpp_gauss_legendre": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tpp_apply_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.c_void_p]),
+    "tpp_apply_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                         C.c_void_p]),
+    "dg_apply_sumfact": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "dg_apply_sumfact_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.c_void_p]),
+    "dg_apply_sumfact_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.c_void_p]),
+    "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                        C.c_void_p]),
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),

@@ -3,22 +3,21 @@
 // Each diagonal block S_e (n^2 x n^2 in 2D) is assembled entry by entry from
 // the precomputed flux Jacobians (Eq. jac-entries with collocated quadrature):
 //   S[(i,j),(k,l)] = h^2 w_i w_j d_ik d_jl
-//     + d_lj (D_ki cx_kj + l1_i l1_k max(sR_j, 0) + l0_i l0_k max(-sL_j, 0))
-//     + d_ki (D_lj cy_il + l1_j l1_l max(sT_i, 0) + l0_j l0_l max(-sB_i, 0)),
+//     + d_lj (D_ki cx_kj + l1_i l1_k max(an_+x,j, 0) + l0_i l0_k max(an_-x,j, 0))
+//     + d_ki (D_lj cy_il + l1_j l1_l max(an_+y,i, 0) + l0_j l0_l max(an_-y,i, 0)),
+// an the scaled outward normal velocity of each face (only its outflow part enters the
+// diagonal block),
 // then LU-factored with partial pivoting (one CTA per element, in place in the
 // workspace).  The apply is a forward / backward substitution per element.
 #include "tpp_internal.cuh"
 
 namespace tpp {
 
-__global__ void k_bj_assemble_2d(const Tables* T, int n, int nx, int ny, double h,
-                                 const double* cx, const double* cy, const double* sx,
-                                 const double* sy, double* LU) {
+__global__ void k_bj_assemble_2d(const Tables* T, int n, double h, const double* cx,
+                                 const double* cy, const double* fa, double* LU) {
   const int nn = n * n;
   const int64_t e = blockIdx.x;
-  const int ex = (int)(e % nx), ey = (int)(e / nx);
-  const int64_t eR = ey * (int64_t)nx + (ex + 1) % nx;
-  const int64_t eT = ((ey + 1) % ny) * (int64_t)nx + ex;
+  const double* fe = fa + e * 4 * n;          // outward normal velocities, faces -x, +x, -y, +y
   double* A = LU + e * (int64_t)nn * nn;      // row-major nn x nn
   for (int q = threadIdx.x; q < nn * nn; q += blockDim.x) {
     const int row = q / nn, col = q % nn;
@@ -27,13 +26,13 @@ __global__ void k_bj_assemble_2d(const Tables* T, int n, int nx, int ny, double 
     if (i == k && j == l) v += h * h * T->w[i] * T->w[j];
     if (l == j) {
       v += T->D[k * n + i] * cx[e * nn + k + n * j];
-      v += T->l1[i] * T->l1[k] * fmax(sx[eR * n + j], 0.0);
-      v += T->l0[i] * T->l0[k] * fmax(-sx[e * n + j], 0.0);
+      v += T->l1[i] * T->l1[k] * fmax(fe[1 * n + j], 0.0);
+      v += T->l0[i] * T->l0[k] * fmax(fe[0 * n + j], 0.0);
     }
     if (k == i) {
       v += T->D[l * n + j] * cy[e * nn + i + n * l];
-      v += T->l1[j] * T->l1[l] * fmax(sy[eT * n + i], 0.0);
-      v += T->l0[j] * T->l0[l] * fmax(-sy[e * n + i], 0.0);
+      v += T->l1[j] * T->l1[l] * fmax(fe[3 * n + i], 0.0);
+      v += T->l0[j] * T->l0[l] * fmax(fe[2 * n + i], 0.0);
     }
     A[q] = v;
   }
@@ -93,14 +92,14 @@ __global__ void k_bj_lu(int nb, double* LU, int32_t* piv) {
 }
 
 __global__ void k_bj_solve(int nb, const double* LU, const int32_t* piv, const double* b,
-                           double* x, const int32_t* skip) {
+                           double* x, const int32_t* skip, int R) {
   if (skip && *skip) return;
   extern __shared__ double ys[];
-  const int64_t e = blockIdx.x;
+  const int64_t blk = blockIdx.x, e = blk / R;   // vector block: right-hand side blk % R
   const double* A = LU + e * (int64_t)nb * nb;
   const int32_t* P = piv + e * (int64_t)nb;
   const int tid = threadIdx.x;
-  for (int i = tid; i < nb; i += blockDim.x) ys[i] = b[e * nb + i];
+  for (int i = tid; i < nb; i += blockDim.x) ys[i] = b[blk * nb + i];
   __syncthreads();
   if (tid == 0)
     for (int k = 0; k < nb; ++k)
@@ -118,15 +117,14 @@ __global__ void k_bj_solve(int nb, const double* LU, const int32_t* piv, const d
     for (int i = tid; i < k; i += blockDim.x) ys[i] -= A[(int64_t)i * nb + k] * xk;
     __syncthreads();
   }
-  for (int i = tid; i < nb; i += blockDim.x) x[e * nb + i] = ys[i];
+  for (int i = tid; i < nb; i += blockDim.x) x[blk * nb + i] = ys[i];
 }
 
 cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s) {
   if (c->dim != 2) return cudaErrorNotSupported;
   k_bj_assemble_2d<<<(unsigned)c->E, 256, 0, s>>>(
-      c->p<Tables>(c->L.tables), c->n, c->prob.nel[0], c->prob.nel[1], c->prob.h,
-      c->p<double>(c->L.cx), c->p<double>(c->L.cy), c->p<double>(c->L.sx), c->p<double>(c->L.sy),
-      c->p<double>(c->L.bj_lu));
+      c->p<Tables>(c->L.tables), c->n, c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+      c->p<double>(c->L.fa), c->p<double>(c->L.bj_lu));
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -138,8 +136,8 @@ cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s) {
 
 cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
                             cudaStream_t s) {
-  k_bj_solve<<<(unsigned)c->E, 256, c->nloc * sizeof(double), s>>>(
-      c->nloc, c->p<double>(c->L.bj_lu), c->p<int32_t>(c->L.bj_piv), b, x, skip);
+  k_bj_solve<<<(unsigned)c->EB, 256, c->nloc * sizeof(double), s>>>(
+      c->nloc, c->p<double>(c->L.bj_lu), c->p<int32_t>(c->L.bj_piv), b, x, skip, c->R);
   count_launch();
   return cudaGetLastError();
 }

@@ -1741,9 +1741,8 @@ __global__ void __launch_bounds__(128) k_shift_inv_w(int n, int64_t E, const dou
 }
 
 // ---- learned factors: network inputs, normalised cores, acceptance ------------
-__global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, const double* cx,
-                          const double* cy, const double* sx, const double* sy, double* kco,
-                          const double* sxu, const double* syu);
+__global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const double* cx,
+                          const double* cy, const double* fa, double* kco);
 
 // Mn = M / ||M||_F (column-major r x r) and ||M||_F (= ||A~||_F) per element
 __global__ void __launch_bounds__(128) k_core(const double* kco, const double* Zd, const double* Rz,
@@ -1831,11 +1830,9 @@ size_t ksvd_scr_doubles(int n, int rz) { return ksvd_scr_stride(n, rz); }
 
 cudaError_t launch_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double* norms,
                                   cudaStream_t s) {
-  k_coef_2d<<<152 * 4, 256, 0, s>>>(
-      c->p<Tables>(c->L.tables), c->n, c->iso ? (int)c->E : c->prob.nel[0],
-      c->iso ? 1 : c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-      c->p<double>(c->L.sx), c->p<double>(c->L.sy), c->p<double>(c->L.kco),
-      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr);
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
+                                    c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco));
   count_launch();
   if (Mn) {
     k_core<<<(unsigned)((c->E + 3) / 4), 128, 0, s>>>(c->p<double>(c->L.kco),
@@ -1868,31 +1865,26 @@ cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const doub
 // Sec. 3.4.1 in the basis of k_struct_qr): Cx[c][j] = cx[c + n j] (volume,
 // c < n), max(a.n, 0) on the +x and -x faces (c = n, n + 1); Cy likewise for
 // y; Dg[i + n j] = h^2 w_i w_j (mass).
-// (batch mode: sxu / syu hold each isolated element's own upper faces; nx = E, ny = 1)
-__global__ void k_coef_2d(const Tables* T, int n, int nx, int ny, double h, const double* cx,
-                          const double* cy, const double* sx, const double* sy, double* kco,
-                          const double* sxu, const double* syu) {
+__global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const double* cx,
+                          const double* cy, const double* fa, double* kco) {
   const int nc = n + 2, nn = n * n, per = 2 * nc * n + nn;
-  const int64_t E = (int64_t)nx * ny;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E * per;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = g / per;
     const int q = (int)(g % per);
-    const int ex = (int)(e % nx), ey = (int)(e / nx);
+    const double* fe = fa + e * 4 * n;      // outward normal velocities, faces -x, +x, -y, +y
     double v;
     if (q < 2 * nc * n) {
       const int which = q / (nc * n), rem = q % (nc * n);
       const int c = rem / n, j = rem % n;
       if (which == 0) {          // x-part, j = y index
         if (c < n) v = cx[e * nn + c + n * j];
-        else if (c == n)
-          v = fmax(sxu ? sxu[e * n + j] : sx[((int64_t)ey * nx + (ex + 1) % nx) * n + j], 0.0);
-        else v = fmax(-sx[e * n + j], 0.0);
+        else if (c == n) v = fmax(fe[1 * n + j], 0.0);       // outflow through +x
+        else v = fmax(fe[0 * n + j], 0.0);                   // outflow through -x
       } else {                   // y-part, j = x index
         if (c < n) v = cy[e * nn + j + n * c];
-        else if (c == n)
-          v = fmax(syu ? syu[e * n + j] : sy[((int64_t)((ey + 1) % ny) * nx + ex) * n + j], 0.0);
-        else v = fmax(-sy[e * n + j], 0.0);
+        else if (c == n) v = fmax(fe[3 * n + j], 0.0);
+        else v = fmax(fe[2 * n + j], 0.0);
       }
     } else {
       const int d = q - 2 * nc * n, i = d % n, j = d / n;
@@ -2049,11 +2041,9 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
 
 
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
-  k_coef_2d<<<152 * 4, 256, 0, s>>>(
-      c->p<Tables>(c->L.tables), c->n, c->iso ? (int)c->E : c->prob.nel[0],
-      c->iso ? 1 : c->prob.nel[1], c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-      c->p<double>(c->L.sx), c->p<double>(c->L.sy), c->p<double>(c->L.kco),
-      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr);
+  k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
+                                    c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco));
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
@@ -2078,11 +2068,10 @@ cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
 
 struct Stage1Args {
   const Tables* T;
-  int n, rz, nx, ny, nz, Jmax;
+  int n, rz, Jmax;
   int64_t E;
   double h;
-  const double *cx, *cy, *cz, *sx, *sy, *sz, *Zd, *Rz;
-  const double *sxu, *syu, *szu;   // batch mode: own upper faces (NULL on a mesh)
+  const double *cx, *cy, *cz, *fa, *Zd, *Rz;   // fa: [E][6][n^2] outward normal velocities
   double* scr;
   double* kco;
   double *Az, *Azi, *sigz;
@@ -2172,12 +2161,7 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
   double* aug = sm1 + (size_t)warp * (2 * nn + n + 40);
   double* fac = aug + 2 * nn;
   double* cfs = fac + n + 8;   // 32 reorthogonalisation coefficients
-  const int nx = A.nx, ny = A.ny, nz = A.nz;
-  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-  auto eid = [&](int a, int b, int c) -> int64_t {
-    return ((int64_t)((c + nz) % nz) * ny + (b + ny) % ny) * nx + (a + nx) % nx;
-  };
-  const int64_t eXp = eid(ex + 1, ey, ez), eYp = eid(ex, ey + 1, ez), eZp = eid(ex, ey, ez + 1);
+  const double* fe = A.fa + e * 6 * nn;      // faces -x, +x, -y, +y, -z, +z
   const double h3 = A.h * A.h * A.h;
   const Tables* T = A.T;
   // ---- 1. line coefficients in the Z basis (flux Jacobians of Sec. 3.4.1)
@@ -2188,14 +2172,14 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
       vx = A.cx[e * n3 + c + n * a + nn * b];        // x-line (j = a, k = b)
       vy = A.cy[e * n3 + a + n * c + nn * b];        // y-line (i = a, k = b)
       vz = A.cz[e * n3 + a + n * b + nn * c];        // z-line (i = a, j = b)
-    } else if (c == n) {
-      vx = fmax(A.sxu ? A.sxu[e * nn + t] : A.sx[eXp * nn + t], 0.0);
-      vy = fmax(A.syu ? A.syu[e * nn + t] : A.sy[eYp * nn + t], 0.0);
-      vz = fmax(A.szu ? A.szu[e * nn + t] : A.sz[eZp * nn + t], 0.0);
-    } else {
-      vx = fmax(-A.sx[e * nn + t], 0.0);
-      vy = fmax(-A.sy[e * nn + t], 0.0);
-      vz = fmax(-A.sz[e * nn + t], 0.0);
+    } else if (c == n) {        // outflow through the upper faces
+      vx = fmax(fe[1 * nn + t], 0.0);
+      vy = fmax(fe[3 * nn + t], 0.0);
+      vz = fmax(fe[5 * nn + t], 0.0);
+    } else {                    // outflow through the lower faces
+      vx = fmax(fe[0 * nn + t], 0.0);
+      vy = fmax(fe[2 * nn + t], 0.0);
+      vz = fmax(fe[4 * nn + t], 0.0);
     }
     Cx3[q] = vx;
     Cy3[q] = vy;
@@ -2439,21 +2423,13 @@ cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s) {
   a.T = c->p<Tables>(c->L.tables);
   a.n = n;
   a.rz = c->rz;
-  a.nx = c->iso ? (int)c->E : c->prob.nel[0];
-  a.ny = c->iso ? 1 : c->prob.nel[1];
-  a.nz = c->iso ? 1 : c->prob.nel[2];
-  a.sxu = c->iso ? c->p<double>(c->L.sxu) : nullptr;
-  a.syu = c->iso ? c->p<double>(c->L.syu) : nullptr;
-  a.szu = c->iso ? c->p<double>(c->L.szu) : nullptr;
   a.Jmax = s1_jmax(n);
   a.E = c->E;
   a.h = c->prob.h;
   a.cx = c->p<double>(c->L.cx);
   a.cy = c->p<double>(c->L.cy);
   a.cz = c->p<double>(c->L.cz);
-  a.sx = c->p<double>(c->L.sx);
-  a.sy = c->p<double>(c->L.sy);
-  a.sz = c->p<double>(c->L.sz);
+  a.fa = c->p<double>(c->L.fa);
   a.Zd = c->p<double>(c->L.zd);
   a.Rz = c->p<double>(c->L.rz);
   a.scr = c->p<double>(c->L.s1scr);

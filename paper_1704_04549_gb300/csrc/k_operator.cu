@@ -204,116 +204,46 @@ cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Flux Jacobians (Alg. matrix-free-matvec step 2).  For advection
-// dF_c/du = a_c, and for the upwind flux dF^/du^- = max(a.n, 0).  Stored
-// pre-multiplied by the quadrature weights and metric factors:
-//   cX[e][i + n j (+ n^2 k)] = -dt h^(d-1) w_i w_j (w_k) a_X(node)   (X = x, y, z)
-//   sX[e][face node] = dt h^(d-1) (tangential weights) a_X(lower X-face node)
-// The lower X-face of element e is owned by e; its upper X-face is the lower
-// face of the +X neighbour, so both sides of a face read the same value.
-// The field is a function of the normalised point x / L, L_d = nel_d h the
-// domain length, so it is periodic on the mesh for any h.
-__device__ __forceinline__ double vel_comp(const VelParams* V, int c, const double* X, int dim) {
-  double a = V->a0[c];
-  const int M = V->n_modes;
-  for (int m = 0; m < M; ++m) {
-    const double* k = V->kvec + (c * M + m) * dim;
-    double kx = X[0] * k[0] + X[1] * k[1];
-    if (dim == 3) kx += X[2] * k[2];
-    a += V->amp[c * M + m] * cos(2.0 * M_PI * kx + V->phase[c * M + m]);
-  }
-  return a;
-}
-
-// Mesh mode: element (ex, ey, ez) of the periodic mesh, coordinates normalised
-// by the domain length.  Batch mode (centres != NULL): element e is the cube of
-// width h centred at centres[e], coordinates absolute in the unit domain, and
-// the upper faces get their own values (sxu, syu, szu: no neighbour owns them).
-__global__ void k_precompute(const VelParams* V, const Tables* T, int dim, int n, int nx, int ny,
-                             int nz, double h, double dt, double* cx, double* cy, double* cz,
-                             double* sx, double* sy, double* sz, const double* centres,
-                             double* sxu, double* syu, double* szu, double span) {
-  const int64_t E = centres ? (int64_t)nx : (int64_t)nx * ny * nz;
+// dF_c/du = a_c, and the upwind flux through a face depends on a.n_outward.
+// Stored pre-multiplied by the quadrature weights and metric factors:
+//   cX[e][i + n j (+ n^2 k)] = -dt h^(d-1) w_i w_j (w_k) a_X(node)     (X = x, y, z)
+//   fa[e][f][t]              = dt h^(d-1) (tangential weights) (a.n_outward)(face node)
+// from the caller's arrays (NULL: a zero field).
+__global__ void k_precompute(const Tables* T, int dim, int n, int64_t E, double h, double dt,
+                             const double* __restrict__ vel, const double* __restrict__ vfn,
+                             double* cx, double* cy, double* cz, double* fa) {
   const int nloc = (dim == 2) ? n * n : n * n * n;
   const int nfl = (dim == 2) ? n : n * n;
-  const int64_t tot_v = E * nloc, tot_f = E * nfl;
+  const int64_t tot_v = E * nloc, tot_f = E * 2 * dim * nfl;
   const double hf = (dim == 2) ? h : h * h;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot_v + tot_f;
        g += (int64_t)gridDim.x * blockDim.x) {
     if (g < tot_v) {
-      const int64_t e = g / nloc;
       const int q = (int)(g % nloc);
       const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      double X[3];
-      if (centres) {
-        const double* ce = centres + e * dim;
-        X[0] = ce[0] + span * (T->x[i] - 0.5);
-        X[1] = ce[1] + span * (T->x[j] - 0.5);
-        X[2] = (dim == 3) ? ce[2] + span * (T->x[k] - 0.5) : 0.0;
-      } else {
-        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-        X[0] = (ex + T->x[i]) / nx;
-        X[1] = (ey + T->x[j]) / ny;
-        X[2] = (ez + T->x[k]) / nz;
-      }
       double wq = T->w[i] * T->w[j];
       if (dim == 3) wq *= T->w[k];
       const double f = -dt * hf * wq;
-      cx[g] = f * vel_comp(V, 0, X, dim);
-      cy[g] = f * vel_comp(V, 1, X, dim);
-      if (dim == 3) cz[g] = f * vel_comp(V, 2, X, dim);
+      cx[g] = vel ? f * vel[g] : 0.0;
+      cy[g] = vel ? f * vel[tot_v + g] : 0.0;
+      if (dim == 3) cz[g] = vel ? f * vel[2 * tot_v + g] : 0.0;
     } else {
       const int64_t gf = g - tot_v;
-      const int64_t e = gf / nfl;
       const int q = (int)(gf % nfl);
       const int t0 = q % n, t1 = q / n;   // tangential indices (first tangential fastest)
       const double wt = (dim == 2) ? T->w[t0] : T->w[t0] * T->w[t1];
-      const double f = dt * hf * wt;
-      if (centres) {
-        const double* ce = centres + e * dim;
-        const double lo[3] = {ce[0] - 0.5 * span, ce[1] - 0.5 * span,
-                              dim == 3 ? ce[2] - 0.5 * span : 0.0};
-        const double tx = span * T->x[t0], ty = span * T->x[t1];
-        for (int up = 0; up < 2; ++up) {
-          double Xx[3] = {lo[0] + up * span, lo[1] + tx, lo[2] + ty};  // x-face: (y, z)
-          double Xy[3] = {lo[0] + tx, lo[1] + up * span, lo[2] + ty};  // y-face: (x, z)
-          (up ? sxu : sx)[gf] = f * vel_comp(V, 0, Xx, dim);
-          (up ? syu : sy)[gf] = f * vel_comp(V, 1, Xy, dim);
-          if (dim == 3) {
-            double Xz[3] = {lo[0] + tx, lo[1] + ty, lo[2] + up * span};   // z-face: (x, y)
-            (up ? szu : sz)[gf] = f * vel_comp(V, 2, Xz, dim);
-          }
-        }
-        continue;
-      }
-      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-      {   // lower x-face: tangential (y, z)
-        double X[3] = {(double)ex / nx, (ey + T->x[t0]) / ny, (ez + T->x[t1]) / nz};
-        sx[gf] = f * vel_comp(V, 0, X, dim);
-      }
-      {   // lower y-face: tangential (x, z)
-        double X[3] = {(ex + T->x[t0]) / nx, (double)ey / ny, (ez + T->x[t1]) / nz};
-        sy[gf] = f * vel_comp(V, 1, X, dim);
-      }
-      if (dim == 3) {   // lower z-face: tangential (x, y)
-        double X[3] = {(ex + T->x[t0]) / nx, (ey + T->x[t1]) / ny, (double)ez / nz};
-        sz[gf] = f * vel_comp(V, 2, X, dim);
-      }
+      fa[gf] = vfn ? dt * hf * wt * vfn[gf] : 0.0;
     }
   }
 }
 
-cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s) {
-  const int nz = (c->dim == 3 && !c->iso) ? c->prob.nel[2] : 1;
+cudaError_t launch_precompute(const tpp_ctx* c, const double* vel_nodes,
+                              const double* vel_face_normal, cudaStream_t s) {
   const bool d3 = c->dim == 3;
   k_precompute<<<152 * 8, 256, 0, s>>>(
-      c->p<VelParams>(c->L.vel), c->p<Tables>(c->L.tables), c->dim, c->n,
-      c->iso ? (int)c->E : c->prob.nel[0], c->iso ? 1 : c->prob.nel[1], nz, c->prob.h,
-      c->prob.dt, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-      d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.sx), c->p<double>(c->L.sy),
-      d3 ? c->p<double>(c->L.sz) : nullptr, c->iso ? c->p<double>(c->L.centres) : nullptr,
-      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
-      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr,
-      c->prob.batch_span > 0.0 ? c->prob.batch_span : c->prob.h);
+      c->p<Tables>(c->L.tables), c->dim, c->n, c->E, c->prob.h, c->prob.dt, vel_nodes,
+      vel_face_normal, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+      d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa));
   count_launch();
   return cudaGetLastError();
 }
@@ -382,21 +312,19 @@ cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaS
 }
 
 // ---------------------------------------------------------------------------
-// y = (M + dt A) x for one element per CTA (2D), Alg. matrix-free-matvec step 3:
+// y = (M + dt A) x for one vector block per CTA (2D), Alg. matrix-free-matvec step 3:
 //   y_ij = h^2 w_i w_j x_ij + sum_k D_ki cx_kj x_kj + sum_l D_lj cy_il x_il
-//          + l1_i F^R_j - l0_i F^L_j + l1_j F^T_i - l0_j F^B_i,
-// F^R_j = max(sR_j,0) u^-_R + min(sR_j,0) u^+_R (upwind flux through the +x
-// face, pre-scaled by dt h w_j), etc.
-// Batch mode (R >= 1 right-hand sides per isolated element, sxu / syu given):
-// block b holds rhs b % R of element b / R; only the own-side upwind face terms
-// (outflow through each face) remain.
+//          + l0_i F_-x,j + l1_i F_+x,j + l0_j F_-y,i + l1_j F_+y,i,
+// F_f = max(fa_f, 0) u^own_f + min(fa_f, 0) u^nbr_f the upwind flux out through face f
+// (fa pre-scaled by dt h w); u^nbr_f is the trace of the neighbour's opposite face for
+// the same right-hand side, and the inflow term is dropped where there is no
+// neighbour.  Block b holds right-hand side b % R of element b / R.
 template <typename VT>
-__global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
-                              const VT* __restrict__ cx, const VT* __restrict__ cy,
-                              const VT* __restrict__ sx, const VT* __restrict__ sy,
-                              const VT* __restrict__ x, const VT* __restrict__ tr,
-                              VT* __restrict__ y, const int32_t* skip, int R,
-                              const VT* __restrict__ sxu, const VT* __restrict__ syu) {
+__global__ void k_dg_apply_2d(const Tables* T, int n, VT hd, const VT* __restrict__ cx,
+                              const VT* __restrict__ cy, const VT* __restrict__ fa,
+                              const int32_t* __restrict__ nbr, const VT* __restrict__ x,
+                              const VT* __restrict__ tr, VT* __restrict__ y, const int32_t* skip,
+                              int R) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
@@ -404,14 +332,11 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
   VT* Ds = sm;                  // n*n, D[a*n + j]
   VT* px = Ds + nn;             // cx * x
   VT* py = px + nn;             // cy * x
-  VT* fl = py + nn;             // 4n face fluxes: R, L, T, B
+  VT* fl = py + nn;             // 4n outward face fluxes, faces -x, +x, -y, +y
   VT* wl = fl + 4 * n;          // w, l0, l1
   const int64_t blk = blockIdx.x;                 // vector block
-  const bool iso = sxu != nullptr;
-  const int64_t e = iso ? blk / R : blk;           // element (coefficients)
-  const int ex = (int)(e % nx), ey = (int)(e / nx);
-  const int64_t eR = ey * (int64_t)nx + (ex + 1) % nx, eL = ey * (int64_t)nx + (ex + nx - 1) % nx;
-  const int64_t eT = ((ey + 1) % ny) * (int64_t)nx + ex, eB = ((ey + ny - 1) % ny) * (int64_t)nx + ex;
+  const int64_t e = blk / R;                      // element (coefficients)
+  const int r = (int)(blk % R);
   const int tid = threadIdx.x;
   const int64_t base = blk * nn, cbase = e * nn;
   for (int q = tid; q < nn; q += blockDim.x) {
@@ -420,36 +345,19 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
     px[q] = cx[cbase + q] * xv;
     py[q] = cy[cbase + q] * xv;
   }
+  if (tid < 4 * n) {
+    const int f = tid / n, t = tid % n;
+    const VT zero = (VT)0;
+    const VT a = fa[(e * 4 + f) * n + t];
+    const int64_t nb = nbr[e * 4 + f];
+    VT F = max(a, zero) * tr[blk * 4 * n + f * n + t];
+    if (nb >= 0) F += min(a, zero) * tr[((nb * R + r) * 4 + (f ^ 1)) * n + t];
+    fl[f * n + t] = F;
+  }
   if (tid < n) {
     wl[tid] = Tab<VT>::w(T)[tid];
     wl[n + tid] = Tab<VT>::l0(T)[tid];
     wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
-    const VT* te = tr + blk * 4 * n;
-    const int t = tid;
-    const VT zero = (VT)0;
-    if (iso) {   // own traces only: outflow through each face
-      fl[t] = max(sxu[e * n + t], zero) * te[1 * n + t];
-      fl[n + t] = min(sx[e * n + t], zero) * te[0 * n + t];
-      fl[2 * n + t] = max(syu[e * n + t], zero) * te[3 * n + t];
-      fl[3 * n + t] = min(sy[e * n + t], zero) * te[2 * n + t];
-    } else {
-    {   // +x face: outward normal +x, flux a_x evaluated on the face owned by eR
-      const VT s = sx[eR * n + t];
-      fl[t] = max(s, zero) * te[1 * n + t] + min(s, zero) * tr[eR * 4 * n + 0 * n + t];
-    }
-    {   // -x face: flux through it in the +x direction, from the left element
-      const VT s = sx[e * n + t];
-      fl[n + t] = max(s, zero) * tr[eL * 4 * n + 1 * n + t] + min(s, zero) * te[0 * n + t];
-    }
-    {   // +y
-      const VT s = sy[eT * n + t];
-      fl[2 * n + t] = max(s, zero) * te[3 * n + t] + min(s, zero) * tr[eT * 4 * n + 2 * n + t];
-    }
-    {   // -y
-      const VT s = sy[e * n + t];
-      fl[3 * n + t] = max(s, zero) * tr[eB * 4 * n + 3 * n + t] + min(s, zero) * te[2 * n + t];
-    }
-    }
   }
   __syncthreads();
   const VT h2 = hd;                 // h^2
@@ -458,25 +366,22 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, int nx, int ny, VT hd,
     VT acc = h2 * wl[i] * wl[j] * x[base + q];
     for (int k = 0; k < n; ++k) acc += Ds[k * n + i] * px[k + n * j];
     for (int l = 0; l < n; ++l) acc += Ds[l * n + j] * py[i + n * l];
-    acc += wl[2 * n + i] * fl[j] - wl[n + i] * fl[n + j];
-    acc += wl[2 * n + j] * fl[2 * n + i] - wl[n + j] * fl[3 * n + i];
+    acc += wl[n + i] * fl[j] + wl[2 * n + i] * fl[n + j];
+    acc += wl[n + j] * fl[2 * n + i] + wl[2 * n + j] * fl[3 * n + i];
     y[base + q] = acc;
   }
 }
 
-// y = (M + dt A) x for one element per CTA (3D):
+// y = (M + dt A) x for one vector block per CTA (3D):
 //   y_ijk = h^3 w_i w_j w_k x + sum_a D_ai cx_ajk x_ajk + sum_b D_bj cy_ibk x_ibk
-//           + sum_c D_ck cz_ijc x_ijc + l1_i F^+x_jk - l0_i F^-x_jk + (same for y, z),
-// face fluxes pre-scaled by dt h^2 and the two tangential weights.
+//           + sum_c D_ck cz_ijc x_ijc + l0_i F_-x,jk + l1_i F_+x,jk + (same for y, z),
+// outward face fluxes as in 2D, pre-scaled by dt h^2 and the two tangential weights.
 template <typename VT>
-__global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT hd,
-                              const VT* __restrict__ cx, const VT* __restrict__ cy,
-                              const VT* __restrict__ cz, const VT* __restrict__ sx,
-                              const VT* __restrict__ sy, const VT* __restrict__ sz,
+__global__ void k_dg_apply_3d(const Tables* T, int n, VT hd, const VT* __restrict__ cx,
+                              const VT* __restrict__ cy, const VT* __restrict__ cz,
+                              const VT* __restrict__ fa, const int32_t* __restrict__ nbr,
                               const VT* __restrict__ x, const VT* __restrict__ tr,
-                              VT* __restrict__ y, const int32_t* skip, int R,
-                              const VT* __restrict__ sxu, const VT* __restrict__ syu,
-                              const VT* __restrict__ szu) {
+                              VT* __restrict__ y, const int32_t* skip, int R) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
@@ -485,18 +390,11 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
   VT* px = Ds + nn;             // n^3 each
   VT* py = px + n3;
   VT* pz = py + n3;
-  VT* fl = pz + n3;             // 6 n^2 fluxes: +x, -x, +y, -y, +z, -z
+  VT* fl = pz + n3;             // 6 n^2 outward fluxes: -x, +x, -y, +y, -z, +z
   VT* wl = fl + 6 * nn;         // w, l0, l1
   const int64_t blk = blockIdx.x;                 // vector block
-  const bool iso = sxu != nullptr;
-  const int64_t e = iso ? blk / R : blk;           // element (coefficients)
-  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-  auto eid = [&](int a, int b, int c) -> int64_t {
-    return ((int64_t)((c + nz) % nz) * ny + (b + ny) % ny) * nx + (a + nx) % nx;
-  };
-  const int64_t eXp = eid(ex + 1, ey, ez), eXm = eid(ex - 1, ey, ez);
-  const int64_t eYp = eid(ex, ey + 1, ez), eYm = eid(ex, ey - 1, ez);
-  const int64_t eZp = eid(ex, ey, ez + 1), eZm = eid(ex, ey, ez - 1);
+  const int64_t e = blk / R;                      // element (coefficients)
+  const int r = (int)(blk % R);
   const int tid = threadIdx.x;
   const int64_t base = blk * n3, cbase = e * n3;
   for (int q = tid; q < nn; q += blockDim.x) Ds[q] = Tab<VT>::D(T)[q];
@@ -511,32 +409,14 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
     wl[n + tid] = Tab<VT>::l0(T)[tid];
     wl[2 * n + tid] = Tab<VT>::l1(T)[tid];
   }
-  const VT* te = tr + blk * 6 * nn;
   const VT zero = (VT)0;
-  if (iso) {   // own traces only: outflow through each face
-    for (int q = tid; q < nn; q += blockDim.x) {
-      fl[0 * nn + q] = max(sxu[e * nn + q], zero) * te[1 * nn + q];
-      fl[1 * nn + q] = min(sx[e * nn + q], zero) * te[0 * nn + q];
-      fl[2 * nn + q] = max(syu[e * nn + q], zero) * te[3 * nn + q];
-      fl[3 * nn + q] = min(sy[e * nn + q], zero) * te[2 * nn + q];
-      fl[4 * nn + q] = max(szu[e * nn + q], zero) * te[5 * nn + q];
-      fl[5 * nn + q] = min(sz[e * nn + q], zero) * te[4 * nn + q];
-    }
-  } else
-  for (int q = tid; q < nn; q += blockDim.x) {
-    VT s;
-    s = sx[eXp * nn + q];
-    fl[0 * nn + q] = max(s, zero) * te[1 * nn + q] + min(s, zero) * tr[eXp * 6 * nn + 0 * nn + q];
-    s = sx[e * nn + q];
-    fl[1 * nn + q] = max(s, zero) * tr[eXm * 6 * nn + 1 * nn + q] + min(s, zero) * te[0 * nn + q];
-    s = sy[eYp * nn + q];
-    fl[2 * nn + q] = max(s, zero) * te[3 * nn + q] + min(s, zero) * tr[eYp * 6 * nn + 2 * nn + q];
-    s = sy[e * nn + q];
-    fl[3 * nn + q] = max(s, zero) * tr[eYm * 6 * nn + 3 * nn + q] + min(s, zero) * te[2 * nn + q];
-    s = sz[eZp * nn + q];
-    fl[4 * nn + q] = max(s, zero) * te[5 * nn + q] + min(s, zero) * tr[eZp * 6 * nn + 4 * nn + q];
-    s = sz[e * nn + q];
-    fl[5 * nn + q] = max(s, zero) * tr[eZm * 6 * nn + 5 * nn + q] + min(s, zero) * te[4 * nn + q];
+  for (int g = tid; g < 6 * nn; g += blockDim.x) {
+    const int f = g / nn, q = g % nn;
+    const VT a = fa[(e * 6 + f) * nn + q];
+    const int64_t nb = nbr[e * 6 + f];
+    VT F = max(a, zero) * tr[blk * 6 * nn + f * nn + q];
+    if (nb >= 0) F += min(a, zero) * tr[((nb * R + r) * 6 + (f ^ 1)) * nn + q];
+    fl[g] = F;
   }
   __syncthreads();
   const VT h3 = hd;                 // h^3
@@ -547,28 +427,27 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, int nx, int ny, int nz, VT
     for (int b = 0; b < n; ++b) acc += Ds[b * n + j] * py[i + n * b + nn * k];
     for (int c = 0; c < n; ++c) acc += Ds[c * n + k] * pz[i + n * j + nn * c];
     const int qx = j + n * k, qy = i + n * k, qz = i + n * j;
-    acc += wl[2 * n + i] * fl[0 * nn + qx] - wl[n + i] * fl[1 * nn + qx];
-    acc += wl[2 * n + j] * fl[2 * nn + qy] - wl[n + j] * fl[3 * nn + qy];
-    acc += wl[2 * n + k] * fl[4 * nn + qz] - wl[n + k] * fl[5 * nn + qz];
+    acc += wl[n + i] * fl[0 * nn + qx] + wl[2 * n + i] * fl[1 * nn + qx];
+    acc += wl[n + j] * fl[2 * nn + qy] + wl[2 * n + j] * fl[3 * nn + qy];
+    acc += wl[n + k] * fl[4 * nn + qz] + wl[2 * n + k] * fl[5 * nn + qz];
     y[base + q] = acc;
   }
 }
 
 template <typename VT>
 cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* cz,
-                              const VT* sx, const VT* sy, const VT* sz, const VT* sxu,
-                              const VT* syu, const VT* szu, const VT* x, const VT* tr, VT* y,
+                              const VT* fa, const VT* x, const VT* tr, VT* y,
                               const int32_t* skip, cudaStream_t s) {
   const int n = c->n;
+  const int32_t* nbr = c->p<int32_t>(c->L.nbr);
+  const double h = c->prob.h;
   if (c->dim == 2) {
     const int nn = n * n;
-    const int threads = ((nn + 31) / 32) * 32;
+    int threads = ((nn + 31) / 32) * 32;
+    if (threads < 4 * n) threads = ((4 * n + 31) / 32) * 32;
     const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
-    const double h = c->prob.h;
     k_dg_apply_2d<VT><<<(unsigned)c->EB, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, c->iso ? (int)c->E : c->prob.nel[0],
-        c->iso ? 1 : c->prob.nel[1], (VT)(h * h), cx, cy, sx, sy, x, tr, y, skip, c->R,
-        c->iso ? sxu : nullptr, c->iso ? syu : nullptr);
+        c->p<Tables>(c->L.tables), n, (VT)(h * h), cx, cy, fa, nbr, x, tr, y, skip, c->R);
     count_launch();
     return cudaGetLastError();
   }
@@ -577,12 +456,8 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
   cudaError_t err = cudaFuncSetAttribute(k_dg_apply_3d<VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const double h = c->prob.h;
   k_dg_apply_3d<VT><<<(unsigned)c->EB, 256, smem, s>>>(
-      c->p<Tables>(c->L.tables), n, c->iso ? (int)c->E : c->prob.nel[0],
-      c->iso ? 1 : c->prob.nel[1], c->iso ? 1 : c->prob.nel[2], (VT)(h * h * h), cx, cy, cz, sx,
-      sy, sz, x, tr, y, skip, c->R, c->iso ? sxu : nullptr, c->iso ? syu : nullptr,
-      c->iso ? szu : nullptr);
+      c->p<Tables>(c->L.tables), n, (VT)(h * h * h), cx, cy, cz, fa, nbr, x, tr, y, skip, c->R);
   count_launch();
   return cudaGetLastError();
 }
@@ -590,11 +465,9 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s) {
   const bool d3 = c->dim == 3;
-  return launch_dg_apply_t<double>(
-      c, c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
-      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr,
-      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
-      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr, x, tr, y, skip, s);
+  return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                   d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
+                                   x, tr, y, skip, s);
 }
 
 // FP32 operator (the inner solves of the mixed-precision mode) on the float
@@ -603,20 +476,15 @@ cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* t
                                 const int32_t* skip, cudaStream_t s) {
   const float* f = c->p<float>(c->L.opf);
   const OpF32Layout O = op_f32_layout(c);
-  const bool d3 = c->dim == 3;
-  return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, d3 ? f + O.cz : nullptr, f + O.sx,
-                                  f + O.sy, d3 ? f + O.sz : nullptr, f + O.sxu, f + O.syu,
-                                  f + O.szu, x, tr, y, skip, s);
+  return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, c->dim == 3 ? f + O.cz : nullptr,
+                                  f + O.fa, x, tr, y, skip, s);
 }
 
 // float copies of the operator coefficients (after k_precompute)
 __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz,
-                            const double* sx, const double* sy, const double* sz,
-                            const double* sxu, const double* syu, const double* szu, float* out,
-                            OpF32Layout O, int dim, int iso) {
-  const int64_t tv = O.cy - O.cx, tf = O.sy - O.sx;
-  const int nface = iso ? 2 * dim : dim;
-  const int64_t total = (int64_t)dim * tv + nface * tf;
+                            const double* fa, float* out, OpF32Layout O, int dim) {
+  const int64_t tv = O.cy - O.cx, tf = O.tr - O.fa;
+  const int64_t total = (int64_t)dim * tv + tf;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     double v;
@@ -627,15 +495,9 @@ __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz
       v = (which == 0 ? cx : which == 1 ? cy : cz)[i];
       dst = (which == 0 ? O.cx : which == 1 ? O.cy : O.cz) + i;
     } else {
-      const int64_t h = g - dim * tv;
-      const int which = (int)(h / tf);           // sx, sy, (sz,) then sxu, syu, (szu)
-      const int64_t i = h % tf;
-      const int dir = which % dim, up = which / dim;
-      const double* src = up ? (dir == 0 ? sxu : dir == 1 ? syu : szu)
-                             : (dir == 0 ? sx : dir == 1 ? sy : sz);
-      v = src[i];
-      dst = (up ? (dir == 0 ? O.sxu : dir == 1 ? O.syu : O.szu)
-                : (dir == 0 ? O.sx : dir == 1 ? O.sy : O.sz)) + i;
+      const int64_t i = g - dim * tv;
+      v = fa[i];
+      dst = O.fa + i;
     }
     out[dst] = __double2float_rn(v);
   }
@@ -644,12 +506,9 @@ __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz
 cudaError_t launch_op_to_f32(const tpp_ctx* c, cudaStream_t s) {
   const OpF32Layout O = op_f32_layout(c);
   const bool d3 = c->dim == 3;
-  k_op_to_f32<<<152 * 4, 256, 0, s>>>(
-      c->p<double>(c->L.cx), c->p<double>(c->L.cy), d3 ? c->p<double>(c->L.cz) : nullptr,
-      c->p<double>(c->L.sx), c->p<double>(c->L.sy), d3 ? c->p<double>(c->L.sz) : nullptr,
-      c->iso ? c->p<double>(c->L.sxu) : nullptr, c->iso ? c->p<double>(c->L.syu) : nullptr,
-      (c->iso && d3) ? c->p<double>(c->L.szu) : nullptr, c->p<float>(c->L.opf), O, c->dim,
-      c->iso ? 1 : 0);
+  k_op_to_f32<<<152 * 4, 256, 0, s>>>(c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                      d3 ? c->p<double>(c->L.cz) : nullptr,
+                                      c->p<double>(c->L.fa), c->p<float>(c->L.opf), O, c->dim);
   count_launch();
   return cudaGetLastError();
 }

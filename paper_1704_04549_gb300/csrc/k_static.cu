@@ -12,8 +12,8 @@
 
 #include "tpp_internal.cuh"
 
-// 4 MiB of doubles: 2D problems with num_elem * 4 * n <= 524288 face-trace
-// values (e.g. 64 x 64 elements up to n = 32).  Every GPU that loads libtpp
+// 4 MiB of doubles: 2D problems with num_elem * nrhs * 4 * n <= 524288 face-trace
+// values (e.g. 64 x 64 elements up to n = 32 with one right-hand side).  Every GPU that loads libtpp
 // holds this array until the process exits.  All calls share it and it keeps
 // the last call's contents; calls that overlap on the GPU race on it.
 constexpr size_t kStaticTraceDoubles = size_t(1) << 19;
@@ -50,7 +50,7 @@ tpp_status scratch_address(double** out) {
 }  // namespace
 
 extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x, double* y,
-                                              void* stream) {
+                                              int32_t nrhs, void* stream) {
   if (!c) {
     tpp::set_error("context is NULL");
     return TPP_ERR_INVALID_ARG;
@@ -59,13 +59,17 @@ extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x,
     tpp::set_error("x and y must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
   }
-  if (c->dim != 2 || c->iso) {
-    tpp::set_error("dg_apply_sumfact_static supports 2D meshes only");
+  if (c->dim != 2) {
+    tpp::set_error("dg_apply_sumfact_static supports 2D problems only");
     return TPP_ERR_UNSUPPORTED;
   }
-  const size_t need = (size_t)c->E * 4 * (size_t)c->n;
+  if (nrhs < 1 || nrhs > c->R) {
+    tpp::set_error("nrhs must be in [1, the problem's nrhs]");
+    return TPP_ERR_INVALID_ARG;
+  }
+  const size_t need = (size_t)c->E * nrhs * 4 * (size_t)c->n;
   if (need > kStaticTraceDoubles) {
-    tpp::set_error("dg_apply_sumfact_static: num_elem * 4 * n = " + std::to_string(need) +
+    tpp::set_error("dg_apply_sumfact_static: num_elem * nrhs * 4 * n = " + std::to_string(need) +
                    " face-trace values exceed the static scratch of " +
                    std::to_string(kStaticTraceDoubles) + " doubles");
     return TPP_ERR_INVALID_ARG;
@@ -83,9 +87,10 @@ extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x,
   double* tr = nullptr;
   if (tpp_status st = scratch_address(&tr)) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = tpp::launch_traces(c, x, tr, s);
+  const tpp_ctx v = tpp::call_view(c, nrhs);
+  cudaError_t e = tpp::launch_traces(&v, x, tr, s);
   if (e != cudaSuccess) return tpp::cuda_check(e, "k_traces");
-  e = tpp::launch_dg_apply(c, x, tr, y, nullptr, s);
+  e = tpp::launch_dg_apply(&v, x, tr, y, nullptr, s);
   if (e != cudaSuccess) return tpp::cuda_check(e, "k_dg_apply_2d");
   return TPP_OK;
 }

@@ -90,38 +90,23 @@ const char* validate(const tpp_problem* p, int32_t max_restart) {
   if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
   if (p->n < 1 || p->n > TPP_MAX_N) return "n must be in [1, 32]";
   if (p->dim == 3 && p->n > TPP_MAX_N_3D) return "n must be in [1, 16] in 3D";
-  for (int d = 0; d < p->dim; ++d)
-    if (p->nel[d] < 1) return "nel[d] must be >= 1";
+  if (p->num_elem < 1 || p->num_elem > (int64_t)INT32_MAX) return "num_elem must be in [1, 2^31)";
+  if (p->nrhs < 1) return "nrhs must be >= 1";
+  if ((int64_t)p->num_elem * p->nrhs > (int64_t)INT32_MAX)
+    return "num_elem * nrhs must be below 2^31";
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return "h must be positive and finite";
   if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return "dt must be >= 0 and finite";
-  if (p->n_modes < 0 || p->n_modes > TPP_MAX_MODES) return "n_modes must be in [0, 64]";
-  if (!p->a0) return "a0 is NULL";
-  if (p->n_modes > 0 && (!p->amp || !p->kvec || !p->phase)) return "Fourier arrays are NULL";
   if (max_restart < 1 || max_restart > kMaxRestart) return "max_restart must be in [1, 63]";
-  if (p->batch_rhs < 0) return "batch_rhs must be >= 0";
-  if (p->batch_rhs > 0 && !p->centres) return "centres is NULL (batch mode)";
-  if (!(p->batch_span >= 0.0) || !std::isfinite(p->batch_span)) return "batch_span must be >= 0";
+  if ((p->vel_nodes == nullptr) != (p->vel_face_normal == nullptr))
+    return "vel_nodes and vel_face_normal must both be given or both be NULL";
   return nullptr;
-}
-
-// element count (E), right-hand sides per element (R) and vector blocks (E R)
-void problem_counts(const tpp_problem* p, int64_t* E, int32_t* R) {
-  if (p->batch_rhs > 0) {
-    *E = p->nel[0];
-    *R = p->batch_rhs;
-  } else {
-    *E = (int64_t)p->nel[0] * p->nel[1] * (p->dim == 3 ? p->nel[2] : 1);
-    *R = 1;
-  }
 }
 
 Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t features,
                       int* rz_out) {
   const int n = p->n, d = p->dim;
-  int64_t E = 0;
-  int32_t R = 1;
-  problem_counts(p, &E, &R);
-  const bool iso = p->batch_rhs > 0;
+  const int64_t E = p->num_elem;
+  const int32_t R = p->nrhs;
   const int64_t EB = E * R;
   const int64_t nloc = (d == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t nfl = (d == 2) ? n : (int64_t)n * n;
@@ -138,7 +123,6 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
     off = align256(off + (bytes ? bytes : 8));
     return o;
   };
-  L.vel = take(sizeof(VelParams));
   L.tables = take(sizeof(Tables));
   L.status = take(sizeof(DevStatus));
   L.gstate = take(sizeof(GmresState));
@@ -151,13 +135,8 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.cx = take((size_t)Nc * 8);
   L.cy = take((size_t)Nc * 8);
   L.cz = (d == 3) ? take((size_t)Nc * 8) : 0;
-  L.sx = take((size_t)E * nfl * 8);
-  L.sy = take((size_t)E * nfl * 8);
-  L.sz = (d == 3) ? take((size_t)E * nfl * 8) : 0;
-  L.sxu = iso ? take((size_t)E * nfl * 8) : 0;
-  L.syu = iso ? take((size_t)E * nfl * 8) : 0;
-  L.szu = (iso && d == 3) ? take((size_t)E * nfl * 8) : 0;
-  L.centres = iso ? take((size_t)E * d * 8) : 0;
+  L.fa = take((size_t)E * 2 * d * nfl * 8);
+  L.nbr = take((size_t)E * 2 * d * 4);
   L.traces = take((size_t)EB * 2 * d * nfl * 8);
   const size_t fsz = (size_t)E * n * n * 8;
   L.sigma = take((size_t)E * 2 * 8);
@@ -202,7 +181,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   }
   L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
   if (features & TPP_FEAT_MIXED) {      // FP32 operator and inner GMRES
-    L.opf = take(op_f32_layout(d, Nc, E, n, EB, iso).total * 4);
+    L.opf = take(op_f32_layout(d, Nc, E, n, EB).total * 4);
     L.gstate_in = take(sizeof(GmresState));
     L.gbuf_in = take(gbuf_layout(m).total * sizeof(double));
     L.vi = take((size_t)(m + 1) * N * 4);
@@ -291,9 +270,13 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     set_error("learned factors are implemented for 2D problems only");
     return TPP_ERR_UNSUPPORTED;
   }
-  if ((prob->dim == 3 || prob->batch_rhs > 0) && (features & TPP_FEAT_BLOCK_JACOBI)) {
-    set_error("exact block Jacobi is implemented for 2D meshes only");
+  if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
+    set_error("exact block Jacobi is implemented for 2D problems only");
     return TPP_ERR_UNSUPPORTED;
+  }
+  if (!prob->nbr) {
+    set_error("nbr is NULL");
+    return TPP_ERR_INVALID_ARG;
   }
   int rz = 0;
   const Layout L = compute_layout(prob, max_restart, features, &rz);
@@ -309,18 +292,27 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     set_error("workspace is not device memory");
     return TPP_ERR_INVALID_ARG;
   }
+  // connectivity: checked on the host, then kept in the workspace
+  const int nface = 2 * prob->dim;
+  std::vector<int32_t> nb((size_t)prob->num_elem * nface);
+  TPP_TRY_CUDA(cudaMemcpy(nb.data(), prob->nbr, nb.size() * sizeof(int32_t), cudaMemcpyDefault),
+               "read nbr");
+  for (size_t i = 0; i < nb.size(); ++i)
+    if (nb[i] < -1 || nb[i] >= prob->num_elem) {
+      set_error("nbr entry " + std::to_string(i) + " = " + std::to_string(nb[i]) +
+                " is outside [-1, num_elem)");
+      return TPP_ERR_INVALID_ARG;
+    }
   tpp_ctx* c = new tpp_ctx();
   c->prob = *prob;
-  c->prob.a0 = nullptr;
-  c->prob.amp = nullptr;
-  c->prob.kvec = nullptr;
-  c->prob.phase = nullptr;
-  c->prob.centres = nullptr;
+  c->prob.vel_nodes = nullptr;
+  c->prob.vel_face_normal = nullptr;
+  c->prob.nbr = nullptr;
   c->n = prob->n;
   c->dim = prob->dim;
   c->device = dev;
-  problem_counts(prob, &c->E, &c->R);
-  c->iso = prob->batch_rhs > 0;
+  c->E = prob->num_elem;
+  c->R = prob->nrhs;
   c->EB = c->E * c->R;
   c->nloc = (prob->dim == 2) ? prob->n * prob->n : prob->n * prob->n * prob->n;
   c->N = c->EB * c->nloc;
@@ -335,22 +327,12 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   c->bj_built = false;
   c->partial_blocks = kPartialBlocks;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // velocity parameters
-  VelParams vp;
-  std::memset(&vp, 0, sizeof(vp));
-  vp.dim = prob->dim;
-  vp.n_modes = prob->n_modes;
-  for (int cc = 0; cc < prob->dim; ++cc) vp.a0[cc] = prob->a0[cc];
-  for (int i = 0; i < prob->dim * prob->n_modes; ++i) {
-    vp.amp[i] = prob->amp[i];
-    vp.phase[i] = prob->phase[i];
-  }
-  for (int i = 0; i < prob->dim * prob->n_modes * prob->dim; ++i) vp.kvec[i] = prob->kvec[i];
   const DevStatus st0 = fresh_status();
   tpp_status rc = TPP_OK;
   do {
-    if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.vel, &vp, sizeof(vp), cudaMemcpyHostToDevice, s),
-                         "copy velocity parameters")) != TPP_OK) break;
+    if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.nbr, nb.data(), nb.size() * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, s), "copy nbr")) != TPP_OK)
+      break;
     if ((rc = cuda_check(cudaMemcpyAsync(c->ws + L.status, &st0, sizeof(st0),
                                          cudaMemcpyHostToDevice, s), "init status")) != TPP_OK) break;
     if ((rc = cuda_check(cudaMemsetAsync(c->ws + L.tables, 0, sizeof(Tables), s), "memset")) != TPP_OK) break;
@@ -359,14 +341,11 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
         (rc = cuda_check(cudaMemsetAsync(c->ws + L.gstate_in, 0, sizeof(GmresState), s),
                          "memset")) != TPP_OK)
       break;
-    if (c->iso &&
-        (rc = cuda_check(cudaMemcpyAsync(c->ws + L.centres, prob->centres,
-                                         (size_t)c->E * c->dim * sizeof(double),
-                                         cudaMemcpyHostToDevice, s), "copy centres")) != TPP_OK)
-      break;
     if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
     if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
-    if ((rc = cuda_check(launch_precompute(c, s), "k_precompute")) != TPP_OK) break;
+    if ((rc = cuda_check(launch_precompute(c, prob->vel_nodes, prob->vel_face_normal, s),
+                         "k_precompute")) != TPP_OK)
+      break;
     if ((features & TPP_FEAT_MIXED) &&
         (rc = cuda_check(launch_op_to_f32(c, s), "k_op_to_f32")) != TPP_OK)
       break;
@@ -377,6 +356,37 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     return rc;
   }
   *out = c;
+  return TPP_OK;
+}
+
+tpp_status tpp_set_velocity(tpp_ctx* c, const double* vel_nodes, const double* vel_face_normal,
+                            double dt, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!vel_nodes || !vel_face_normal || !(dt >= 0.0) || !std::isfinite(dt)) {
+    set_error("tpp_set_velocity: vel_nodes and vel_face_normal non-NULL, dt >= 0 and finite");
+    return TPP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->prob.dt = dt;
+  c->factors_built = false;
+  c->bj_built = false;
+  TPP_TRY_CUDA(launch_precompute(c, vel_nodes, vel_face_normal, s), "k_precompute");
+  if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_op_to_f32(c, s), "k_op_to_f32");
+  TPP_TRY_CUDA(cudaStreamSynchronize(s), "tpp_set_velocity sync");
+  return TPP_OK;
+}
+
+tpp_status tpp_gauss_legendre(const tpp_ctx* c, double* nodes, double* weights) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (!nodes || !weights) {
+    set_error("nodes and weights must be non-NULL");
+    return TPP_ERR_INVALID_ARG;
+  }
+  const Tables* T = c->p<Tables>(c->L.tables);
+  TPP_TRY_CUDA(cudaMemcpy(nodes, T->x, c->n * sizeof(double), cudaMemcpyDeviceToHost),
+               "read nodes");
+  TPP_TRY_CUDA(cudaMemcpy(weights, T->w, c->n * sizeof(double), cudaMemcpyDeviceToHost),
+               "read weights");
   return TPP_OK;
 }
 
@@ -496,9 +506,20 @@ tpp_status tpp_build_block_jacobi(tpp_ctx* c, void* stream) {
   return TPP_OK;
 }
 
-tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32_t prec,
-                             void* stream) {
+namespace {
+tpp_status check_nrhs(const tpp_ctx* c, int32_t nrhs) {
+  if (nrhs < 1 || nrhs > c->R) {
+    set_error("nrhs must be in [1, the problem's nrhs = " + std::to_string(c->R) + "]");
+    return TPP_ERR_INVALID_ARG;
+  }
+  return TPP_OK;
+}
+}  // namespace
+
+tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32_t nrhs,
+                             int32_t prec, void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (tpp_status r = check_nrhs(c, nrhs)) return r;
   if (!b || !x || b == x) {
     set_error("b and x must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
@@ -515,13 +536,16 @@ tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32
     set_error("tpp_build_factors has not been called");
     return TPP_ERR_INVALID_ARG;
   }
-  TPP_TRY_CUDA(apply_precond(c, TPP_PC_KRON, prec, b, x, nullptr,
+  const tpp_ctx v = call_view(c, nrhs);
+  TPP_TRY_CUDA(apply_precond(&v, TPP_PC_KRON, prec, b, x, nullptr,
                              static_cast<cudaStream_t>(stream)), "tpp_apply_inverse");
   return TPP_OK;
 }
 
-tpp_status tpp_apply_block_jacobi(const tpp_ctx* c, const double* b, double* x, void* stream) {
+tpp_status tpp_apply_block_jacobi(const tpp_ctx* c, const double* b, double* x, int32_t nrhs,
+                                  void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (tpp_status r = check_nrhs(c, nrhs)) return r;
   if (!b || !x || b == x) {
     set_error("b and x must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
@@ -530,24 +554,30 @@ tpp_status tpp_apply_block_jacobi(const tpp_ctx* c, const double* b, double* x, 
     set_error("tpp_build_block_jacobi has not been called");
     return TPP_ERR_INVALID_ARG;
   }
-  TPP_TRY_CUDA(launch_bj_apply(c, b, x, nullptr, static_cast<cudaStream_t>(stream)),
+  const tpp_ctx v = call_view(c, nrhs);
+  TPP_TRY_CUDA(launch_bj_apply(&v, b, x, nullptr, static_cast<cudaStream_t>(stream)),
                "tpp_apply_block_jacobi");
   return TPP_OK;
 }
 
-tpp_status dg_apply_sumfact(const tpp_ctx* c, const double* x, double* y, void* stream) {
+tpp_status dg_apply_sumfact(const tpp_ctx* c, const double* x, double* y, int32_t nrhs,
+                            void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (tpp_status r = check_nrhs(c, nrhs)) return r;
   if (!x || !y || x == y) {
     set_error("x and y must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
   }
-  TPP_TRY_CUDA(apply_operator(c, x, y, nullptr, static_cast<cudaStream_t>(stream)),
+  const tpp_ctx v = call_view(c, nrhs);
+  TPP_TRY_CUDA(apply_operator(&v, x, y, nullptr, static_cast<cudaStream_t>(stream)),
                "dg_apply_sumfact");
   return TPP_OK;
 }
 
-tpp_status dg_apply_sumfact_f32(const tpp_ctx* c, const float* x, float* y, void* stream) {
+tpp_status dg_apply_sumfact_f32(const tpp_ctx* c, const float* x, float* y, int32_t nrhs,
+                                void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (tpp_status r = check_nrhs(c, nrhs)) return r;
   if (!x || !y || x == y) {
     set_error("x and y must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
@@ -557,14 +587,17 @@ tpp_status dg_apply_sumfact_f32(const tpp_ctx* c, const float* x, float* y, void
     return TPP_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const tpp_ctx v = call_view(c, nrhs);
   float* trf = c->p<float>(c->L.opf) + op_f32_layout(c).tr;
-  TPP_TRY_CUDA(launch_traces_f32(c, x, trf, s, nullptr), "k_traces<float>");
-  TPP_TRY_CUDA(launch_dg_apply_f32(c, x, trf, y, nullptr, s), "k_dg_apply<float>");
+  TPP_TRY_CUDA(launch_traces_f32(&v, x, trf, s, nullptr), "k_traces<float>");
+  TPP_TRY_CUDA(launch_dg_apply_f32(&v, x, trf, y, nullptr, s), "k_dg_apply<float>");
   return TPP_OK;
 }
 
-tpp_status tpp_apply_inverse_f32(const tpp_ctx* c, const float* b, float* x, void* stream) {
+tpp_status tpp_apply_inverse_f32(const tpp_ctx* c, const float* b, float* x, int32_t nrhs,
+                                 void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (tpp_status r = check_nrhs(c, nrhs)) return r;
   if (!b || !x || b == x) {
     set_error("b and x must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
@@ -573,7 +606,8 @@ tpp_status tpp_apply_inverse_f32(const tpp_ctx* c, const float* b, float* x, voi
     set_error("tpp_apply_inverse_f32 needs TPP_FEAT_MIXED and tpp_build_factors");
     return TPP_ERR_INVALID_ARG;
   }
-  TPP_TRY_CUDA(launch_apply_f32(c, b, x, nullptr, static_cast<cudaStream_t>(stream)),
+  const tpp_ctx v = call_view(c, nrhs);
+  TPP_TRY_CUDA(launch_apply_f32(&v, b, x, nullptr, static_cast<cudaStream_t>(stream)),
                "tpp_apply_inverse_f32");
   return TPP_OK;
 }

@@ -10,19 +10,8 @@
 
 #define TPP_MAX_N 32
 #define TPP_MAX_N_3D 16
-#define TPP_MAX_MODES 64
 
 namespace tpp {
-
-// Velocity-field parameters as stored in the workspace (see tpp_problem).
-struct VelParams {
-  int dim;
-  int n_modes;
-  double a0[3];
-  double amp[3 * TPP_MAX_MODES];
-  double kvec[3 * TPP_MAX_MODES * 3];
-  double phase[3 * TPP_MAX_MODES];
-};
 
 // 1D tables of the nodal basis (Sec. 3.2): Gauss-Legendre nodes x and weights
 // w on [0, 1], D[a*n + j] = phi_j'(x_a), l0[j] = phi_j(0), l1[j] = phi_j(1).
@@ -88,10 +77,11 @@ struct GmresState {
 
 struct Layout {
   // offsets in bytes from workspace start
-  size_t vel, tables, status, gstate;
+  size_t tables, status, gstate;
   size_t zd, rz, qo, qr_work, qr_tau;   // structure basis of the rearranged block (2D)
-  size_t cx, cy, cz, sx, sy, sz;        // flux Jacobians (scaled) at nodes / faces
-  size_t sxu, syu, szu, centres;       // batch mode: upper-face values, element centres
+  size_t cx, cy, cz;                    // flux Jacobians at the volume nodes (scaled)
+  size_t fa;                            // a.n_outward at the face nodes (scaled), [E][2d][nfl]
+  size_t nbr;                           // neighbour across each face, [E][2d] (-1: none)
   size_t traces;
   size_t sigma, fA1, fB1, fA2, fB2;
   size_t fSA, fSB, fQ1, fQ2, fT1, fT2, fSC;  // fSC: 3D A1^-1 factor
@@ -112,12 +102,11 @@ struct Layout {
 }  // namespace tpp
 
 struct tpp_ctx {
-  tpp_problem prob;        // copy (host pointers cleared)
+  tpp_problem prob;        // copy (array pointers cleared: the workspace holds the data)
   int32_t n, dim;
   int32_t device;          // CUDA device the context (and its workspace) was created on
   int64_t E, N;            // elements, DOFs
-  int32_t R;               // right-hand sides per element (1 on a mesh)
-  bool iso;                // batch of isolated elements (block-diagonal systems)
+  int32_t R;               // right-hand sides per element ([E][R][n^d] vectors)
   int64_t EB;              // vector blocks: E * R
   int32_t nloc;            // n^dim
   int32_t max_restart;
@@ -147,7 +136,9 @@ tpp_status cuda_check(cudaError_t e, const char* what);
 // kernels launchers (defined in the .cu files)
 cudaError_t launch_tables(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s);
-cudaError_t launch_precompute(const tpp_ctx* c, cudaStream_t s);
+// flux Jacobians from the caller's velocity arrays (NULL: a zero field)
+cudaError_t launch_precompute(const tpp_ctx* c, const double* vel_nodes,
+                              const double* vel_face_normal, cudaStream_t s);
 cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
                           const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
@@ -234,31 +225,35 @@ inline F32Layout f32_layout(int n, int64_t E, int dim, bool two) {
 }
 
 // float copies of the operator data for the FP32 inner solves (offsets in
-// floats from Layout::opf): volume coefficients (N each), lower-face
-// coefficients (E n^(d-1) each), face traces (E 2d n^(d-1))
+// floats from Layout::opf): volume coefficients (E n^d each), face coefficients
+// (E 2d n^(d-1)), face traces (EB 2d n^(d-1))
 struct OpF32Layout {
-  size_t cx, cy, cz, sx, sy, sz, sxu, syu, szu, tr, total;
+  size_t cx, cy, cz, fa, tr, total;
 };
-// Nc = E n^dim coefficient values per direction; EB vector blocks (traces)
-inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t EB, bool iso) {
+inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t EB) {
   const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;
   OpF32Layout L{};
   size_t o = 0;
   L.cx = o; o += Nc;
   L.cy = o; o += Nc;
   L.cz = o; if (dim == 3) o += Nc;
-  L.sx = o; o += E * nfl;
-  L.sy = o; o += E * nfl;
-  L.sz = o; if (dim == 3) o += E * nfl;
-  L.sxu = o; if (iso) o += E * nfl;
-  L.syu = o; if (iso) o += E * nfl;
-  L.szu = o; if (iso && dim == 3) o += E * nfl;
+  L.fa = o; o += E * 2 * dim * nfl;
   L.tr = o; o += EB * 2 * dim * nfl;
   L.total = o;
   return L;
 }
 inline OpF32Layout op_f32_layout(const tpp_ctx* c) {
-  return op_f32_layout(c->dim, c->E * c->nloc, c->E, c->n, c->EB, c->iso);
+  return op_f32_layout(c->dim, c->E * c->nloc, c->E, c->n, c->EB);
+}
+
+// A view of the context for a call on nrhs <= R right-hand sides per element
+// (vectors [E][nrhs][n^d]): the same workspace with R, EB and N of the call.
+inline tpp_ctx call_view(const tpp_ctx* c, int nrhs) {
+  tpp_ctx v = *c;
+  v.R = nrhs;
+  v.EB = c->E * nrhs;
+  v.N = v.EB * c->nloc;
+  return v;
 }
 
 // the paper's two-sided Schur form (both factor products reduced) instead of

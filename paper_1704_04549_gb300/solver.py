@@ -25,47 +25,64 @@ def _stream(stream) -> C.c_void_p:
 class Context:
     """One DG advection problem on one GPU (a tpp_ctx and its workspace).
 
-    velocity: object with attributes dim, a0 [dim], amp [dim, M], kvec [dim, M, dim],
-    phase [dim, M] describing a_c(x) = a0_c + sum_m amp cos(2 pi k . x + phase).
+    velocity: a synthetic.Velocity (a_c(x) = a0_c + sum_m amp cos(2 pi k . x + phase));
+    its values at the nodes and faces are evaluated on the host (mesh.py) and handed
+    to the library as the arrays of tpp_problem.
 
+    Mesh mode (batch_rhs = 0): the periodic Cartesian mesh of nel elements of width h.
     Batch mode (batch_rhs >= 1, centres [E, dim]): E isolated elements of width h
-    with block-diagonal systems, batch_rhs right-hand sides each; nel is ignored
-    and vectors are laid out [element][rhs][n^dim].
+    with block-diagonal systems, batch_rhs right-hand sides each (nel is ignored);
+    the field is sampled over batch_span (0: h) around each centre.  Vectors are laid
+    out [element][rhs][n^dim].  ``Context.from_arrays`` takes the tpp_problem arrays
+    directly.
     """
 
     def __init__(self, dim: int, n: int, nel, h: float, dt: float, velocity,
                  max_restart: int = 30, features: int = 0, device: str = "cuda:0",
                  stream=None, batch_rhs: int = 0, centres=None, batch_span: float = 0.0):
+        from . import mesh
+        self.batch_rhs = int(batch_rhs)
+        if self.batch_rhs > 0:
+            cen = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, dim)
+            self.nel = (cen.shape[0],)
+            nbr, nrhs = mesh.isolated_nbr(cen.shape[0], dim), self.batch_rhs
+        else:
+            self.nel = tuple(int(v) for v in nel)[:dim]
+            nbr, nrhs = mesh.periodic_nbr(self.nel), 1
+        # geometry first (zero field): the field is evaluated at the library's nodes
+        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream)
+        x = self.gauss_legendre()[0]
+        if self.batch_rhs > 0:
+            vn, fn = mesh.isolated_field(cen, x, velocity, batch_span if batch_span > 0 else h)
+        else:
+            vn, fn = mesh.periodic_field(self.nel, x, velocity)
+        self.tpp_set_velocity(vn, fn, dt, stream)
+
+    @classmethod
+    def from_arrays(cls, dim: int, n: int, h: float, dt: float, nbr, vel_nodes,
+                    vel_face_normal, nrhs: int = 1, max_restart: int = 30, features: int = 0,
+                    device: str = "cuda:0", stream=None):
+        """A context from the arrays of tpp_problem (layouts as in tpp.h)."""
+        self = cls.__new__(cls)
+        self.batch_rhs = 0
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1, 2 * dim)
+        self.nel = (nbr.shape[0],)
+        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream)
+        self.tpp_set_velocity(vel_nodes, vel_face_normal, dt, stream)
+        return self
+
+    def _create(self, dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream):
         if not torch.cuda.is_available():
             raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
         self.lib = L.load()
         self.device = torch.device(device)
         self.dim, self.n, self.dt, self.h = dim, n, float(dt), float(h)
-        self.batch_rhs = int(batch_rhs)
-        if self.batch_rhs > 0:
-            self._centres = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, dim)
-            nel = (self._centres.shape[0],)
-        nel = tuple(int(v) for v in nel) + (1,) * (3 - len(nel))
-        self.nel = nel[:dim]
-        self._a0 = np.ascontiguousarray(velocity.a0, dtype=np.float64)
-        self._amp = np.ascontiguousarray(velocity.amp, dtype=np.float64).reshape(-1)
-        self._kvec = np.ascontiguousarray(velocity.kvec, dtype=np.int32).reshape(-1)
-        self._phase = np.ascontiguousarray(velocity.phase, dtype=np.float64).reshape(-1)
-        M = int(np.asarray(velocity.amp).shape[1]) if np.asarray(velocity.amp).ndim == 2 else 0
+        self.nrhs = int(nrhs)
+        nb = torch.as_tensor(np.ascontiguousarray(nbr, dtype=np.int32), device=self.device)
         P = L.Problem()
-        P.dim, P.n = dim, n
-        for d in range(3):
-            P.nel[d] = nel[d]
-        P.h, P.dt, P.n_modes = self.h, self.dt, M
-        P.a0 = self._a0.ctypes.data_as(C.POINTER(C.c_double))
-        P.amp = self._amp.ctypes.data_as(C.POINTER(C.c_double))
-        P.kvec = self._kvec.ctypes.data_as(C.POINTER(C.c_int32))
-        P.phase = self._phase.ctypes.data_as(C.POINTER(C.c_double))
-        P.batch_rhs = self.batch_rhs
-        P.batch_span = float(batch_span)
-        if self.batch_rhs > 0:
-            P.centres = self._centres.ctypes.data_as(C.POINTER(C.c_double))
-        self._prob = P
+        P.dim, P.n, P.num_elem, P.nrhs = dim, n, int(nb.shape[0]), self.nrhs
+        P.h, P.dt = self.h, self.dt
+        P.nbr = _ptr(nb)
         nbytes = self.lib.tpp_workspace_bytes(C.byref(P), max_restart, features)
         if nbytes == 0:
             raise L.TppError(1, "tpp_workspace_bytes")
@@ -85,6 +102,26 @@ class Context:
         self.num_dofs = int(self.lib.tpp_num_dofs(ctx))
         self.num_elem = int(self.lib.tpp_num_elem(ctx))
 
+    def gauss_legendre(self):
+        """(nodes, weights) of the context's Gauss-Legendre rule on [0, 1] (host)."""
+        x, w = np.empty(self.n), np.empty(self.n)
+        L.check(self.lib.tpp_gauss_legendre(self._ctx, x.ctypes.data_as(C.c_void_p),
+                                            w.ctypes.data_as(C.c_void_p)), "tpp_gauss_legendre")
+        return x, w
+
+    def tpp_set_velocity(self, vel_nodes, vel_face_normal, dt: float, stream=None):
+        """New field and step (arrays as in tpp_problem); the factors must be rebuilt."""
+        vn = torch.as_tensor(np.ascontiguousarray(vel_nodes, dtype=np.float64).reshape(-1),
+                             device=self.device) if not isinstance(vel_nodes, torch.Tensor) \
+            else vel_nodes.contiguous()
+        fn = torch.as_tensor(np.ascontiguousarray(vel_face_normal, dtype=np.float64).reshape(-1),
+                             device=self.device) if not isinstance(vel_face_normal, torch.Tensor) \
+            else vel_face_normal.contiguous()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.tpp_set_velocity(self._ctx, _ptr(vn), _ptr(fn), float(dt),
+                                              _stream(stream)), "tpp_set_velocity")
+        self.dt = float(dt)
+
     def __del__(self):
         ctx = getattr(self, "_ctx", None)
         if ctx is not None and ctx.value:
@@ -92,10 +129,11 @@ class Context:
             self._ctx = None
 
     # -- C ABI calls ---------------------------------------------------------
-    def _vec(self, t, name):
+    def _vec(self, t, name, size=None):
+        size = self.num_dofs if size is None else size
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-                and t.is_contiguous() and t.numel() == self.num_dofs):
-            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {self.num_dofs}")
+                and t.is_contiguous() and t.numel() == size):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {size}")
         return t
 
     def tpp_build_factors(self, stream=None) -> dict:
@@ -159,54 +197,65 @@ class Context:
         L.check(self.lib.tpp_build_block_jacobi(self._ctx, _stream(stream)),
                 "tpp_build_block_jacobi")
 
-    def tpp_apply_inverse(self, b, x=None, prec: int = L.TPP_FP64, stream=None):
-        b = self._vec(b, "b")
-        x = torch.empty_like(b) if x is None else self._vec(x, "x")
-        L.check(self.lib.tpp_apply_inverse(self._ctx, _ptr(b), _ptr(x), prec, _stream(stream)),
-                "tpp_apply_inverse")
+    def _nrhs(self, nrhs):
+        k = self.nrhs if nrhs is None else int(nrhs)
+        return k, self.num_elem * k * self.n ** self.dim
+
+    def tpp_apply_inverse(self, b, x=None, prec: int = L.TPP_FP64, stream=None, nrhs=None):
+        k, size = self._nrhs(nrhs)
+        b = self._vec(b, "b", size)
+        x = torch.empty_like(b) if x is None else self._vec(x, "x", size)
+        L.check(self.lib.tpp_apply_inverse(self._ctx, _ptr(b), _ptr(x), k, prec,
+                                           _stream(stream)), "tpp_apply_inverse")
         return x
 
-    def tpp_apply_block_jacobi(self, b, x=None, stream=None):
-        b = self._vec(b, "b")
-        x = torch.empty_like(b) if x is None else self._vec(x, "x")
-        L.check(self.lib.tpp_apply_block_jacobi(self._ctx, _ptr(b), _ptr(x), _stream(stream)),
+    def tpp_apply_block_jacobi(self, b, x=None, stream=None, nrhs=None):
+        k, size = self._nrhs(nrhs)
+        b = self._vec(b, "b", size)
+        x = torch.empty_like(b) if x is None else self._vec(x, "x", size)
+        L.check(self.lib.tpp_apply_block_jacobi(self._ctx, _ptr(b), _ptr(x), k, _stream(stream)),
                 "tpp_apply_block_jacobi")
         return x
 
-    def dg_apply_sumfact(self, x, y=None, stream=None):
-        x = self._vec(x, "x")
-        y = torch.empty_like(x) if y is None else self._vec(y, "y")
-        L.check(self.lib.dg_apply_sumfact(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
+    def dg_apply_sumfact(self, x, y=None, stream=None, nrhs=None):
+        k, size = self._nrhs(nrhs)
+        x = self._vec(x, "x", size)
+        y = torch.empty_like(x) if y is None else self._vec(y, "y", size)
+        L.check(self.lib.dg_apply_sumfact(self._ctx, _ptr(x), _ptr(y), k, _stream(stream)),
                 "dg_apply_sumfact")
         return y
 
-    def _vec32(self, t, name):
+    def _vec32(self, t, name, size=None):
+        size = self.num_dofs if size is None else size
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
-                and t.is_contiguous() and t.numel() == self.num_dofs):
-            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {self.num_dofs}")
+                and t.is_contiguous() and t.numel() == size):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {size}")
         return t
 
-    def dg_apply_sumfact_f32(self, x, y=None, stream=None):
-        x = self._vec32(x, "x")
-        y = torch.empty_like(x) if y is None else self._vec32(y, "y")
-        L.check(self.lib.dg_apply_sumfact_f32(self._ctx, _ptr(x), _ptr(y), _stream(stream)),
+    def dg_apply_sumfact_f32(self, x, y=None, stream=None, nrhs=None):
+        k, size = self._nrhs(nrhs)
+        x = self._vec32(x, "x", size)
+        y = torch.empty_like(x) if y is None else self._vec32(y, "y", size)
+        L.check(self.lib.dg_apply_sumfact_f32(self._ctx, _ptr(x), _ptr(y), k, _stream(stream)),
                 "dg_apply_sumfact_f32")
         return y
 
-    def tpp_apply_inverse_f32(self, b, x=None, stream=None):
-        b = self._vec32(b, "b")
-        x = torch.empty_like(b) if x is None else self._vec32(x, "x")
-        L.check(self.lib.tpp_apply_inverse_f32(self._ctx, _ptr(b), _ptr(x), _stream(stream)),
+    def tpp_apply_inverse_f32(self, b, x=None, stream=None, nrhs=None):
+        k, size = self._nrhs(nrhs)
+        b = self._vec32(b, "b", size)
+        x = torch.empty_like(b) if x is None else self._vec32(x, "x", size)
+        L.check(self.lib.tpp_apply_inverse_f32(self._ctx, _ptr(b), _ptr(x), k, _stream(stream)),
                 "tpp_apply_inverse_f32")
         return x
 
-    def dg_apply_sumfact_static(self, x, y=None, stream=None):
+    def dg_apply_sumfact_static(self, x, y=None, stream=None, nrhs=None):
         """dg_apply_sumfact with its trace scratch in libtpp's static device array
         (for callers that cannot allocate device scratch; overlapping calls race)."""
-        x = self._vec(x, "x")
-        y = torch.empty_like(x) if y is None else self._vec(y, "y")
+        k, size = self._nrhs(nrhs)
+        x = self._vec(x, "x", size)
+        y = torch.empty_like(x) if y is None else self._vec(y, "y", size)
         with torch.cuda.device(self.device):
-            L.check(self.lib.dg_apply_sumfact_static(self._ctx, _ptr(x), _ptr(y),
+            L.check(self.lib.dg_apply_sumfact_static(self._ctx, _ptr(x), _ptr(y), k,
                                                      _stream(stream)), "dg_apply_sumfact_static")
         return y
 

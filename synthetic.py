@@ -1,8 +1,10 @@
 """Seeded synthetic inputs shared by the oracle and the CUDA path.
 
-This module only draws random numbers and fixes workload sizes; it holds none
-of the method's arithmetic (no basis, quadrature, operator, factorisation or
-solver).  Both sides receive the same parameters and evaluate them on their own.
+This module only draws random numbers, fixes workload sizes and evaluates the
+drawn velocity fields at given points; it holds none of the method's arithmetic
+(no basis, quadrature, operator, factorisation or solver).  The oracle evaluates
+the field parameters with its own code; the CUDA path receives field values at
+its nodes from ``velocity_values``.
 
 Velocity fields are described by parameters, not values: component ``c`` is
 
@@ -80,6 +82,20 @@ def fourier_velocity(seed: int, dim: int, n_modes: int = 8, kmax: int = 4,
     kvec = np.broadcast_to(k[None], (dim, n_modes, dim)).astype(np.int32).copy()
     phase = np.broadcast_to(phi[None], (dim, n_modes)).copy()
     return Velocity(dim, a0, amp, kvec, phase)
+
+
+def velocity_values(vel: Velocity, X: np.ndarray) -> np.ndarray:
+    """Values of the field at points X[..., dim] of the unit cube (the series above);
+    returns [..., dim] float64."""
+    X = np.asarray(X, dtype=np.float64)
+    out = np.empty(X.shape[:-1] + (vel.dim,))
+    for c in range(vel.dim):
+        val = np.full(X.shape[:-1], float(vel.a0[c]))
+        for m in range(vel.n_modes):
+            k = vel.kvec[c, m].astype(np.float64)
+            val += vel.amp[c, m] * np.cos(2.0 * np.pi * (X @ k) + vel.phase[c, m])
+        out[..., c] = val
+    return out
 
 
 def rhs(seed: int, ndof: int) -> np.ndarray:

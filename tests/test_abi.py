@@ -48,12 +48,8 @@ def test_python_binding_declares_the_same_names(lib):
 def test_workspace_query_validates_without_gpu(lib):
     from paper_1704_04549_gb300 import _lib
     L = _lib.load()
-    import numpy as np
-    a0 = np.array([1.0, 0.5])
     P = _lib.Problem()
-    P.dim, P.n, P.h, P.dt, P.n_modes = 2, 8, 1 / 8, 0.1, 0
-    P.nel[0], P.nel[1], P.nel[2] = 8, 8, 1
-    P.a0 = a0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    P.dim, P.n, P.num_elem, P.nrhs, P.h, P.dt = 2, 8, 64, 1, 1 / 8, 0.1
     nb = L.tpp_workspace_bytes(ctypes.byref(P), 30, 0)
     assert nb > 31 * 4096 * 8
     P.n = 33
@@ -69,12 +65,11 @@ def test_create_fails_loudly_without_device(lib):
         pytest.skip("a GPU is present")
     from paper_1704_04549_gb300 import _lib
     L = _lib.load()
-    import numpy as np
-    a0 = np.array([1.0, 0.5])
+    from paper_1704_04549_gb300 import mesh
+    nbr = mesh.periodic_nbr((4, 4))
     P = _lib.Problem()
-    P.dim, P.n, P.h, P.dt, P.n_modes = 2, 4, 1 / 4, 0.1, 0
-    P.nel[0], P.nel[1], P.nel[2] = 4, 4, 1
-    P.a0 = a0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    P.dim, P.n, P.num_elem, P.nrhs, P.h, P.dt = 2, 4, 16, 1, 1 / 4, 0.1
+    P.nbr = nbr.ctypes.data_as(ctypes.c_void_p)
     ctx = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(1 << 16)
     st = L.tpp_create(ctypes.byref(ctx), ctypes.byref(P), 30, 0, ctypes.cast(buf, ctypes.c_void_p),

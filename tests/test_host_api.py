@@ -17,25 +17,17 @@ def L():
     return _lib
 
 
-def _problem(L, dim=2, n=8, nel=(4, 4), h=1.0, dt=0.05, batch_rhs=0, centres=None):
-    vel = synthetic.fourier_velocity(1705, dim if dim in (2, 3) else 2)
-    keep = dict(a0=np.ascontiguousarray(vel.a0, dtype=np.float64),
-                amp=np.ascontiguousarray(vel.amp, dtype=np.float64).reshape(-1),
-                kvec=np.ascontiguousarray(vel.kvec, dtype=np.int32).reshape(-1),
-                phase=np.ascontiguousarray(vel.phase, dtype=np.float64).reshape(-1))
+def _problem(L, dim=2, n=8, nel=(4, 4), h=1.0, dt=0.05, nrhs=1, isolated=False):
+    """A tpp_problem on host arrays (the sizing and validation calls read no array)."""
+    from paper_1704_04549_gb300 import mesh
+    E = int(np.prod(nel)) if len(nel) else 0
+    nbr = (mesh.isolated_nbr(E, dim) if isolated or dim not in (2, 3) or min(nel, default=0) < 1
+           else mesh.periodic_nbr(nel))
+    keep = dict(nbr=np.ascontiguousarray(nbr, dtype=np.int32))
     P = L.Problem()
-    P.dim, P.n = dim, n
-    for d in range(3):
-        P.nel[d] = nel[d] if d < len(nel) else 1
-    P.h, P.dt, P.n_modes = h, dt, np.asarray(vel.amp).shape[1]
-    P.a0 = keep["a0"].ctypes.data_as(C.POINTER(C.c_double))
-    P.amp = keep["amp"].ctypes.data_as(C.POINTER(C.c_double))
-    P.kvec = keep["kvec"].ctypes.data_as(C.POINTER(C.c_int32))
-    P.phase = keep["phase"].ctypes.data_as(C.POINTER(C.c_double))
-    P.batch_rhs = batch_rhs
-    if centres is not None:
-        keep["centres"] = np.ascontiguousarray(centres, dtype=np.float64)
-        P.centres = keep["centres"].ctypes.data_as(C.POINTER(C.c_double))
+    P.dim, P.n, P.num_elem, P.nrhs = dim, n, E, nrhs
+    P.h, P.dt = h, dt
+    P.nbr = keep["nbr"].ctypes.data_as(C.c_void_p)
     return P, keep
 
 
@@ -63,13 +55,19 @@ def test_workspace_sizing_and_validation(L):
     P2, keep2 = _problem(L, nel=(8, 8))
     assert lib.tpp_workspace_bytes(C.byref(P2), 30, 0) > base      # more elements
     for bad in (dict(n=0), dict(n=33), dict(dim=4), dict(nel=(0, 4)), dict(h=0.0),
-                dict(dt=-1.0), dict(dim=3, n=17, nel=(2, 2, 2)), dict(batch_rhs=2)):
+                dict(dt=-1.0), dict(dim=3, n=17, nel=(2, 2, 2)), dict(nrhs=0)):
         Pb, kb = _problem(L, **bad)
         assert lib.tpp_workspace_bytes(C.byref(Pb), 30, 0) == 0, bad
     assert lib.tpp_workspace_bytes(C.byref(P), 0, 0) == 0
     assert lib.tpp_workspace_bytes(C.byref(P), 64, 0) == 0
-    Pc, kc = _problem(L, nel=(5,), batch_rhs=3, centres=np.full((5, 2), 0.5))
-    assert lib.tpp_workspace_bytes(C.byref(Pc), 30, 0) > 0
+    # right-hand sides per element scale the vectors, not the factors
+    Pc, kc = _problem(L, nel=(5, 1), nrhs=3, isolated=True)
+    P1, k1 = _problem(L, nel=(5, 1), nrhs=1, isolated=True)
+    assert lib.tpp_workspace_bytes(C.byref(Pc), 30, 0) > lib.tpp_workspace_bytes(C.byref(P1), 30, 0)
+    # one of the velocity arrays without the other
+    v = np.zeros(2 * 16 * 64)
+    P.vel_nodes = v.ctypes.data_as(C.c_void_p)
+    assert lib.tpp_workspace_bytes(C.byref(P), 30, 0) == 0
 
 
 def test_invalid_arguments_are_reported_without_a_device(L):
@@ -84,3 +82,60 @@ def test_invalid_arguments_are_reported_without_a_device(L):
     net = C.c_void_p()
     assert lib.tpp_mlp_create(C.byref(net), 1, 8, None, 0, None) == 1
     assert not net.value
+
+
+def test_invalid_neighbour_table_is_rejected_before_any_device_work(L):
+    """A NULL neighbour table is refused by tpp_create (the workspace check and the
+    table's range check come before any kernel)."""
+    lib = L.load()
+    P, keep = _problem(L)
+    P.nbr = None
+    ctx = C.c_void_p()
+    assert lib.tpp_create(C.byref(ctx), C.byref(P), 30, 0, None, 0, None) == 1
+    assert b"nbr" in lib.tpp_last_error() and not ctx.value
+
+
+@pytest.mark.parametrize("nel", [(4, 3), (3, 2, 5)])
+def test_periodic_mesh_arrays(nel):
+    """Neighbour table: the element across face f sees e across its opposite face; face
+    values: both sides of every face carry opposite a.n; volume values are the field at
+    the normalised node positions (x fastest)."""
+    from paper_1704_04549_gb300 import mesh
+    dim = len(nel)
+    nbr = mesh.periodic_nbr(nel)
+    E = int(np.prod(nel))
+    assert nbr.shape == (E, 2 * dim) and nbr.min() >= 0 and nbr.max() < E
+    for f in range(2 * dim):
+        assert np.array_equal(nbr[nbr[:, f], f ^ 1], np.arange(E))
+    x = np.array([0.2, 0.7, 0.9])
+    vel = synthetic.fourier_velocity(1705, dim)
+    vn, fn = mesh.periodic_field(nel, x, vel)
+    n = len(x)
+    assert vn.shape == (dim, E * n ** dim) and fn.shape == (E, 2 * dim, n ** (dim - 1))
+    for f in range(2 * dim):
+        assert np.array_equal(fn[nbr[:, f], f ^ 1], -fn[:, f])
+    # node (i, j[, k]) of element (ex, ey[, ez]) sits at ((ex + x_i) / N_x, ...)
+    e = E - 1
+    c = np.unravel_index(e, tuple(reversed(nel)))[::-1]
+    q = 1 + n * 2 if dim == 2 else 1 + n * 2 + n * n * 0
+    ijk = (1, 2) if dim == 2 else (1, 2, 0)
+    X = np.array([(c[d] + x[ijk[d]]) / nel[d] for d in range(dim)])
+    assert np.allclose(vn[:, e * n ** dim + q], synthetic.velocity_values(vel, X), rtol=0,
+                       atol=1e-14)
+
+
+def test_isolated_element_arrays():
+    """Isolated elements: no neighbours; the lower and upper face values are the field
+    at the faces of the element's sampled span, with the outward sign."""
+    from paper_1704_04549_gb300 import mesh
+    cen = np.array([[0.3, 0.6], [0.9, 0.1]])
+    x = np.array([0.25, 0.75])
+    vel = synthetic.fourier_velocity(7, 2)
+    nbr = mesh.isolated_nbr(2, 2)
+    assert (nbr == -1).all()
+    vn, fn = mesh.isolated_field(cen, x, vel, span=0.1)
+    # +x face of element 1, tangential node 0: (0.9 + 0.05, 0.1 + 0.1 (0.25 - 0.5))
+    a = synthetic.velocity_values(vel, np.array([0.95, 0.1 - 0.025]))
+    assert abs(fn[1, 1, 0] - a[0]) <= 1e-15
+    a = synthetic.velocity_values(vel, np.array([0.3 + 0.1 * (0.75 - 0.5), 0.55]))
+    assert abs(fn[0, 2, 1] + a[1]) <= 1e-15        # -y face: outward normal -e_y
