@@ -69,6 +69,7 @@ typedef enum {
 #define TPP_FEAT_TWO_SIDED    4u  /* apply by the paper's two-sided Schur form (quasi-triangular
                                      Sylvester solve) instead of the default one-sided form */
 #define TPP_FEAT_LEARNED      8u  /* reserve the buffers of tpp_build_factors_learned (2D) */
+#define TPP_FEAT_TIME        16u  /* reserve 6 solution-sized vectors for tpp_time_integrate */
 
 /*
  * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
@@ -297,6 +298,40 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
  */
 tpp_status dg_apply_sumfact_static(const tpp_ctx* ctx, const double* x, double* y, int32_t nrhs,
                                    void* stream);
+
+/*
+ * Time integration of the semi-discrete system M u' = J u (Sec. 3.3, Eq. mass-u-r, with
+ * the linear flux of Sec. 5.1; the context's operator is S = M - dt_ctx J, dt_ctx its
+ * problem's dt).  Schemes:
+ *  TPP_TS_BACKWARD_EULER  (M - dt J) u^{n+1} = M u^n  (the single implicit steps of Sec. 5.3-5.6);
+ *  TPP_TS_DIRK3           the three-stage, third-order, L-stable DIRK method of Alexander used in
+ *                         Sec. 5.2: stage values solve (M - gamma dt J) U_i = M (u^n + dt
+ *                         sum_{j<i} a_ij k_j), k_i = M^-1 J U_i, u^{n+1} = U_3 (stiffly accurate);
+ *  TPP_TS_RK4             the classical explicit fourth-order Runge-Kutta method (the explicit
+ *                         comparison of Sec. 5.2); M is diagonal (collocated quadrature).
+ * Implicit schemes first rescale the context's operator to dt_ctx = a_ii dt (dt for backward
+ * Euler, gamma dt for DIRK3) when it differs (needs dt_ctx > 0; the context keeps the new dt),
+ * build the Kronecker factors once, or before every step when rebuild_each_step (the paper's
+ * setting, where the Jacobian changes every step), and solve every stage with gmres_solve and
+ * `opts` (initial guess: the stage's explicit part).  RK4 applies J as -(S - M) / dt_ctx
+ * through the operator without its mass term (needs dt_ctx > 0).
+ * u: device float64 [num_dofs]: on entry u^0, on exit u after `steps` steps of size dt > 0.
+ * Needs TPP_FEAT_TIME.  Synchronises `stream`; report (host, may be NULL) counts GMRES
+ * iterations, factor builds and the largest true relative residual of any stage solve.
+ * Returns the first failing solve's status (the integration stops there).
+ */
+typedef enum { TPP_TS_BACKWARD_EULER = 0, TPP_TS_DIRK3 = 1, TPP_TS_RK4 = 2 } tpp_time_scheme;
+typedef struct {
+  int32_t steps;            /* steps completed */
+  int32_t gmres_iters;      /* Arnoldi steps over every stage solve */
+  int32_t builds;           /* factor builds */
+  int32_t solves;           /* stage solves */
+  double max_true_rel_res;  /* largest ||b - S U|| / ||b|| of the stage solves */
+} tpp_time_report;
+
+tpp_status tpp_time_integrate(tpp_ctx* ctx, double* u, int32_t scheme, double dt, int32_t steps,
+                              int32_t rebuild_each_step, const tpp_gmres_opts* opts,
+                              tpp_time_report* report, void* stream);
 
 /* Device pointers into the workspace for inspection (tests); NULL if absent. */
 typedef struct {

@@ -15,6 +15,8 @@ STATUS_NAMES = {0: "TPP_OK", 1: "TPP_ERR_INVALID_ARG", 2: "TPP_ERR_CUDA",
 TPP_FP64, TPP_FP32 = 0, 1
 TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
 TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1, 2, 4, 8
+TPP_FEAT_TIME = 16
+TPP_TS_BACKWARD_EULER, TPP_TS_DIRK3, TPP_TS_RK4 = 0, 1, 2
 
 
 class Problem(C.Structure):
@@ -41,6 +43,11 @@ class BuildReport(C.Structure):
                 ("num_schur_fail", C.c_int32), ("max_cond", C.c_double),
                 ("min_sigma_ratio", C.c_double), ("max_cond_z", C.c_double),
                 ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32)]
+
+
+class TimeReport(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("gmres_iters", C.c_int32), ("builds", C.c_int32),
+                ("solves", C.c_int32), ("max_true_rel_res", C.c_double)]
 
 
 class Views(C.Structure):
@@ -72,6 +79,9 @@ EXPORTS = {
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),
+    "tpp_time_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                     C.c_int32, C.POINTER(GmresOpts), C.POINTER(TimeReport),
+                                     C.c_void_p]),
     "tpp_copy_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "tpp_num_dofs": (C.c_int64, [C.c_void_p]),
     "tpp_num_elem": (C.c_int64, [C.c_void_p]),

@@ -437,7 +437,7 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, VT hd, const VT* __restric
 template <typename VT>
 cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* cz,
                               const VT* fa, const VT* x, const VT* tr, VT* y,
-                              const int32_t* skip, cudaStream_t s) {
+                              const int32_t* skip, cudaStream_t s, double mass = 1.0) {
   const int n = c->n;
   const int32_t* nbr = c->p<int32_t>(c->L.nbr);
   const double h = c->prob.h;
@@ -447,7 +447,7 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
     if (threads < 4 * n) threads = ((4 * n + 31) / 32) * 32;
     const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
     k_dg_apply_2d<VT><<<(unsigned)c->EB, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, (VT)(h * h), cx, cy, fa, nbr, x, tr, y, skip, c->R);
+        c->p<Tables>(c->L.tables), n, (VT)(mass * h * h), cx, cy, fa, nbr, x, tr, y, skip, c->R);
     count_launch();
     return cudaGetLastError();
   }
@@ -457,7 +457,8 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_dg_apply_3d<VT><<<(unsigned)c->EB, 256, smem, s>>>(
-      c->p<Tables>(c->L.tables), n, (VT)(h * h * h), cx, cy, cz, fa, nbr, x, tr, y, skip, c->R);
+      c->p<Tables>(c->L.tables), n, (VT)(mass * h * h * h), cx, cy, cz, fa, nbr, x, tr, y, skip,
+      c->R);
   count_launch();
   return cudaGetLastError();
 }
@@ -468,6 +469,15 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                    d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
                                    x, tr, y, skip, s);
+}
+
+// y = dt A x = -dt J x: the operator without its mass term (traces tr of x given)
+cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                                 cudaStream_t s) {
+  const bool d3 = c->dim == 3;
+  return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                   d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
+                                   x, tr, y, nullptr, s, 0.0);
 }
 
 // FP32 operator (the inner solves of the mixed-precision mode) on the float

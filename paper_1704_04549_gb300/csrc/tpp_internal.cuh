@@ -95,6 +95,7 @@ struct Layout {
   size_t s1scr, fAz, fAzi, sigz, zflags;   // 3D stage 1: scratch, A1, A1^-1, sigma_1, flags
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
+  size_t tvec;                         // time integration: 6 solution-sized vectors
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
   size_t total;
 };
@@ -143,6 +144,9 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
                           const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
+// y = dt A x without the mass term (explicit time stepping: J x = -y / dt)
+cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                                 cudaStream_t s);
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s);
 // per-element scratch of the 3D stage-1 kernel (doubles)
 struct S1Layout {

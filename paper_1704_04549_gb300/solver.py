@@ -275,6 +275,28 @@ class Context:
             raise L.TppError(st, "gmres_solve")
         return x, res
 
+    def tpp_time_integrate(self, u, scheme: int, dt: float, steps: int,
+                           rebuild_each_step: bool = False, restart: int = 30, rtol: float = 1e-10,
+                           max_iters: int = 3000, pc: int = L.TPP_PC_KRON, use_graph: bool = False,
+                           inner_iters: int = 0, stream=None, check: bool = True) -> dict:
+        """Advance u (float64 CUDA tensor, in place) by `steps` steps of `scheme`
+        (TPP_TS_*); implicit stages by GMRES with these options.  Implicit schemes leave
+        the context's operator at dt_ctx = a_ii dt.  Returns the report."""
+        u = self._vec(u, "u")
+        mixed = inner_iters > 0
+        o = L.GmresOpts(restart, max_iters, rtol, pc, L.TPP_FP32 if mixed else L.TPP_FP64,
+                        int(mixed), int(inner_iters), int(use_graph), 0.0)
+        rep = L.TimeReport()
+        with torch.cuda.device(self.device):
+            st = self.lib.tpp_time_integrate(self._ctx, _ptr(u), int(scheme), float(dt), int(steps),
+                                             int(bool(rebuild_each_step)), C.byref(o),
+                                             C.byref(rep), _stream(stream))
+        out = {k: getattr(rep, k) for k, _ in L.TimeReport._fields_}
+        out["status"] = st
+        if check and st != L.TPP_OK:
+            raise L.TppError(st, "tpp_time_integrate")
+        return out
+
     def views(self) -> dict:
         """Copies of the factor arrays (torch tensors) for inspection."""
         v = L.Views()
