@@ -333,6 +333,28 @@ tpp_status tpp_time_integrate(tpp_ctx* ctx, double* u, int32_t scheme, double dt
                               int32_t rebuild_each_step, const tpp_gmres_opts* opts,
                               tpp_time_report* report, void* stream);
 
+/*
+ * Element-wise inversion of the exact mass matrix (Sec. 3.3, Eq. mass-kron):
+ *   M_K = (G^T W (x) ... (x) G^T W) J_T (G (x) ... (x) G)
+ * with the mu-point Gauss-Legendre rule per direction (n <= mu <= 64; G the mu x n
+ * evaluation matrix of the nodal basis at its points, W its weights) and J_T the
+ * |Jacobian determinant| of each element's map at those points (curved or non-affine
+ * elements), solved element by element by preconditioned conjugate gradients from x = 0
+ * with the under-integrated (n-point, collocated) mass matrix as preconditioner: diagonal,
+ * w (x) ... (x) w times J_T at the nodes (Sec. 3.3).  Stops at ||r|| <= rtol ||b|| per block.
+ *  jac_q  device [num_elem][mu^dim]: |J_T| at the quadrature points (x fastest), including
+ *         the element size (h^dim for an affine cube of side h);
+ *  jac_n  device [num_elem][n^dim]: |J_T| at the nodes;
+ *  r, x   device [num_elem][nrhs][n^dim] (must not alias);
+ *  iters  device [num_elem * nrhs] iterations per block, or NULL.
+ * Shared memory of one element block must fit 200 KB (2D: n <= 32, mu <= 64; 3D: e.g.
+ * n <= 11 with mu <= 16), else TPP_ERR_UNSUPPORTED.  Synchronises `stream`; returns
+ * TPP_ERR_NOT_CONVERGED when a block reached max_iters (x still written).
+ */
+tpp_status tpp_mass_solve(const tpp_ctx* ctx, int32_t mu, const double* jac_q,
+                          const double* jac_n, const double* r, double* x, int32_t nrhs,
+                          double rtol, int32_t max_iters, int32_t* iters, void* stream);
+
 /* Device pointers into the workspace for inspection (tests); NULL if absent. */
 typedef struct {
   const double* sigma;   /* [E][2] top singular values of the rearranged block (2D) */

@@ -79,6 +79,9 @@ EXPORTS = {
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),
+    "tpp_mass_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p,
+                                 C.c_void_p]),
     "tpp_time_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
                                      C.c_int32, C.POINTER(GmresOpts), C.POINTER(TimeReport),
                                      C.c_void_p]),

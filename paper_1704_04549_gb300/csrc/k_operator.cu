@@ -16,38 +16,7 @@ namespace tpp {
 __global__ void k_tables(Tables* T, int n) {
   __shared__ double lam[TPP_MAX_N];
   const int i = threadIdx.x;
-  if (i < n) {
-    const int k = n - 1 - i;                  // ascending order on [0, 1]
-    double x = cos(M_PI * (k + 0.75) / (n + 0.5));
-    double dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = x;
-      for (int m = 2; m <= n; ++m) {
-        const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
-        p0 = p1;
-        p1 = p2;
-      }
-      const double pn = (n == 1) ? x : p1;
-      const double pm = (n == 1) ? 1.0 : p0;
-      dp = n * (x * pn - pm) / (x * x - 1.0);
-      const double dx = pn / dp;
-      x -= dx;
-      if (fabs(dx) <= 1e-16 * fmax(1.0, fabs(x))) break;
-    }
-    {   // weight from the converged node
-      double p0 = 1.0, p1 = x;
-      for (int m = 2; m <= n; ++m) {
-        const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
-        p0 = p1;
-        p1 = p2;
-      }
-      const double pn = (n == 1) ? x : p1;
-      const double pm = (n == 1) ? 1.0 : p0;
-      dp = n * (x * pn - pm) / (x * x - 1.0);
-    }
-    T->x[i] = 0.5 * (x + 1.0);
-    T->w[i] = 1.0 / ((1.0 - x * x) * dp * dp);   // 2/(...) mapped by 1/2
-  }
+  if (i < n) gauss_legendre_node(n, i, &T->x[i], &T->w[i]);
   __syncthreads();
   if (i < n) {
     double prod = 1.0;

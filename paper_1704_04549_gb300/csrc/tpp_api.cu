@@ -190,6 +190,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.bj_lu = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * nloc * 8) : 0;
   L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
   L.tvec = (features & TPP_FEAT_TIME) ? take((size_t)6 * N * 8) : 0;
+  L.mtab = take((size_t)(2 * TPP_MAX_MU + TPP_MAX_MU * TPP_MAX_N) * 8);
   L.V = take((size_t)(m + 1) * N * 8);
   L.Z = take((size_t)m * N * 8);
   L.vtmp = take((size_t)N * 8);

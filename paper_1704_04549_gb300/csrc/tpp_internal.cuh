@@ -10,6 +10,7 @@
 
 #define TPP_MAX_N 32
 #define TPP_MAX_N_3D 16
+#define TPP_MAX_MU 64
 
 namespace tpp {
 
@@ -54,7 +55,7 @@ struct DevStatus {
   int32_t nan_seen;
   int32_t z_unconverged;    // 3D stage 1: elements whose Lanczos hit its step cap
   int32_t learned_fallback; // learned build: elements handed to the exact KSVD
-  int32_t pad_st;
+  int32_t mass_unconverged; // element mass solves that hit their iteration limit
   double max_cond_z;        // 3D stage 1: largest cond_1(A1)
 };
 
@@ -96,6 +97,7 @@ struct Layout {
   size_t f32;                          // float copies of SA,SB,Q1,Q2,T1,T2 (mixed)
   size_t bj_lu, bj_piv;
   size_t tvec;                         // time integration: 6 solution-sized vectors
+  size_t mtab;                         // mass solve: mu-point rule and interpolation matrix
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
   size_t total;
 };
@@ -294,6 +296,40 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   double t = 0.0;
   for (int i = 0; i < nw; ++i) t += red[i];   // same order in every thread: deterministic
   return t;
+}
+
+// k-th (ascending) Gauss-Legendre node and weight of the n-point rule on [0, 1]:
+// Newton's method on the three-term Legendre recurrence from cos(pi (j + 3/4) /
+// (n + 1/2)), j = n - 1 - k; weight 1 / ((1 - t^2) P_n'(t)^2) on [0, 1].
+__device__ inline void gauss_legendre_node(int n, int k, double* node, double* weight) {
+  const int jj = n - 1 - k;
+  double x = cos(M_PI * (jj + 0.75) / (n + 0.5));
+  double dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double p0 = 1.0, p1 = x;
+    for (int m = 2; m <= n; ++m) {
+      const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double pn = (n == 1) ? x : p1;
+    const double pm = (n == 1) ? 1.0 : p0;
+    dp = n * (x * pn - pm) / (x * x - 1.0);
+    const double dx = pn / dp;
+    x -= dx;
+    if (fabs(dx) <= 1e-16 * fmax(1.0, fabs(x))) break;
+  }
+  double p0 = 1.0, p1 = x;
+  for (int m = 2; m <= n; ++m) {
+    const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+    p0 = p1;
+    p1 = p2;
+  }
+  const double pn = (n == 1) ? x : p1;
+  const double pm = (n == 1) ? 1.0 : p0;
+  dp = n * (x * pn - pm) / (x * x - 1.0);
+  *node = 0.5 * (x + 1.0);
+  *weight = 1.0 / ((1.0 - x * x) * dp * dp);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) mapped to [-1, 1): deterministic

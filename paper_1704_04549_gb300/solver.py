@@ -297,6 +297,29 @@ class Context:
             raise L.TppError(st, "tpp_time_integrate")
         return out
 
+    def tpp_mass_solve(self, mu: int, jac_q, jac_n, r, x=None, rtol: float = 1e-12,
+                       max_iters: int = 100, nrhs=None, stream=None, check: bool = True):
+        """Element-wise PCG solve of M_K x = r with the mu-point exact mass matrix
+        (jac_q [E, mu^dim], jac_n [E, n^dim]: |J_T| at the quadrature points and nodes).
+        Returns (x, iterations per block [E * nrhs] int32 tensor, status)."""
+        k, size = self._nrhs(nrhs)
+        r = self._vec(r, "r", size)
+        x = torch.empty_like(r) if x is None else self._vec(x, "x", size)
+        jq = torch.as_tensor(np.ascontiguousarray(jac_q, dtype=np.float64).reshape(-1),
+                             device=self.device)
+        jn = torch.as_tensor(np.ascontiguousarray(jac_n, dtype=np.float64).reshape(-1),
+                             device=self.device)
+        if jq.numel() != self.num_elem * mu ** self.dim or jn.numel() != self.num_elem * self.n ** self.dim:
+            raise ValueError("jac_q must hold E mu^dim values and jac_n E n^dim")
+        its = torch.zeros(self.num_elem * k, dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            st = self.lib.tpp_mass_solve(self._ctx, int(mu), _ptr(jq), _ptr(jn), _ptr(r), _ptr(x),
+                                         k, float(rtol), int(max_iters), _ptr(its),
+                                         _stream(stream))
+        if check and st != L.TPP_OK:
+            raise L.TppError(st, "tpp_mass_solve")
+        return x, its, st
+
     def views(self) -> dict:
         """Copies of the factor arrays (torch tensors) for inspection."""
         v = L.Views()

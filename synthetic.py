@@ -98,6 +98,63 @@ def velocity_values(vel: Velocity, X: np.ndarray) -> np.ndarray:
     return out
 
 
+@dataclass
+class ElementMaps:
+    """Geometry of E elements of width h for the mass-matrix workloads: element e maps
+    the reference cube [0, 1]^dim by
+      bilinear:  the multilinear interpolation of its corners, each corner of the
+                 reference cube moved by h * eps * (a U(-1, 1) vector);
+      curved:    x = h (xi + eps sum_d s_d sin(2 pi xi_{d+1} + phi_{e,d}) e_d), a smooth
+                 non-polynomial map (indices cyclic);
+      affine:    x = h xi.
+    ``jacobian(e, X)`` is |det dx/dxi| at reference points X[..., dim]."""
+    kind: str
+    dim: int
+    h: float
+    eps: float
+    corners: np.ndarray      # [E, 2^dim, dim] corner displacements (bilinear)
+    phase: np.ndarray        # [E, dim] (curved)
+
+    @property
+    def num_elem(self) -> int:
+        return int(self.phase.shape[0])
+
+    def jacobian(self, e: int, X: np.ndarray) -> np.ndarray:
+        X = np.asarray(X, dtype=np.float64)
+        d = self.dim
+        Jm = np.zeros(X.shape[:-1] + (d, d))
+        if self.kind == "affine":
+            Jm[...] = np.eye(d)
+        elif self.kind == "curved":
+            Jm[...] = np.eye(d)
+            for c in range(d):
+                nxt = (c + 1) % d
+                Jm[..., c, nxt] += self.eps * 2 * np.pi * np.cos(
+                    2 * np.pi * X[..., nxt] + self.phase[e, c])
+        else:
+            # x(xi) = sum_corners N_k(xi) (corner_k + h eps delta_k) / h-scaled below
+            for k in range(2 ** d):
+                bits = [(k >> c) & 1 for c in range(d)]
+                corner = np.array(bits, dtype=np.float64) + self.eps * self.corners[e, k]
+                for c in range(d):         # derivative of N_k along c
+                    dN = np.ones(X.shape[:-1])
+                    for q in range(d):
+                        f = X[..., q] if bits[q] else 1.0 - X[..., q]
+                        if q == c:
+                            f = np.ones(X.shape[:-1]) if bits[q] else -np.ones(X.shape[:-1])
+                        dN = dN * f
+                    Jm[..., :, c] += dN[..., None] * corner
+        return np.abs(np.linalg.det(Jm)) * self.h ** d
+
+
+def element_maps(seed: int, num_elem: int, dim: int, kind: str, h: float = 1.0,
+                 eps: float = 0.1) -> ElementMaps:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    corners = rng.uniform(-1.0, 1.0, size=(num_elem, 2 ** dim, dim))
+    phase = rng.uniform(0.0, 2 * np.pi, size=(num_elem, dim))
+    return ElementMaps(kind, dim, h, eps, corners, phase)
+
+
 def rhs(seed: int, ndof: int) -> np.ndarray:
     """Right-hand side b ~ N(0, 1), float64."""
     rng = np.random.Generator(np.random.PCG64(seed))
