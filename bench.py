@@ -731,6 +731,67 @@ def run_timestep(args):
     return 0
 
 
+def run_mrhs(args):
+    """Preconditioner apply with 64 right-hand sides per element (the dense case of the
+    batch workload): 4096 isolated unit elements of the random-Fourier field 1705 sampled
+    over 1/64 of the unit domain at centres uniform (seed 1709), n = 16, dt = 0.05,
+    b ~ N(0, 1) (seed 1711).  FP64, FP32 (SIMT) and BF16 (tensor cores, FP32 accumulation)
+    applies on the same float64 vectors, L2 flushed before each launch.
+    value = BF16 apply GDOF/s."""
+    import torch
+    from paper_1704_04549_gb300 import (TPP_BF16, TPP_FEAT_BF16, TPP_FEAT_MIXED, TPP_FP32,
+                                        TPP_FP64, Context)
+    from paper_1704_04549_gb300 import _lib
+    lib = _lib.load()
+    dev = torch.device("cuda", 0)
+    n, E, R = 16, 4096, 64
+    rng = np.random.Generator(np.random.PCG64(1709))
+    ctx = Context(2, n, (E,), 1.0, 0.05, synthetic.fourier_velocity(1705, 2), max_restart=1,
+                  features=TPP_FEAT_MIXED | TPP_FEAT_BF16, device=str(dev), batch_rhs=R,
+                  centres=rng.random((E, 2)), batch_span=1.0 / 64)
+    ctx.tpp_build_factors()
+    N = ctx.num_dofs
+    b = torch.as_tensor(synthetic.rhs(1711, N), device=dev)
+    z = torch.empty_like(b)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(0) as clk:
+        for name, prec in (("fp64", TPP_FP64), ("fp32", TPP_FP32), ("bf16", TPP_BF16)):
+            for _ in range(args.warmup):
+                ctx.tpp_apply_inverse(b, z, prec=prec)
+            t_ms = time_each(lambda: ctx.tpp_apply_inverse(b, z, prec=prec), 10 * args.steps,
+                             stream, flush)
+            out[name] = {"ms": t_ms, "gdofs": N / (t_ms * 1e-3) / 1e9}
+    launches = lib.tpp_kernel_launch_count() - l0
+    # algorithmic bytes of the BF16 apply: b and x in float64 plus the element's BF16 factors
+    # (S_A, L_B^-1, Q1: 3 n^2; shifted inverses 2 n^3) and T1 in float (n^2)
+    fbytes = E * (3 * n * n * 2 + n * n * 4 + 2 * n ** 3 * 2)
+    vbytes = 2 * 8 * N
+    achieved = (fbytes + vbytes) / (out["bf16"]["ms"] * 1e-3) / 1e9
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "preconditioner apply GDOF/s with 64 right-hand sides per element, "
+                      "BF16 tensor cores vs FP32 / FP64, 1 GB300",
+            "value": out["bf16"]["gdofs"], "unit": "GDOF/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "vs_baseline": None,
+            "dtype": "bf16 operands, f32 accumulation (vectors f64)", "data": "synthetic",
+            "config": {"workload": "4096 isolated elements n=16, 64 rhs each, field 1705 span "
+                                   "1/64, centres seed 1709, b seed 1711",
+                       "l2": "flushed (256 MB write) before each timed launch"},
+            "apply": out,
+            "roofline": {"kernel": "k_apply_2d_tc<double> (mma.sync BF16)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "algorithmic": "2 x 8 B per DOF (b, x) + per element 3 n^2 BF16 "
+                                        "factors, n^2 float T1, 2 n^3 BF16 shifted inverses"},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_kernels(args):
     """Kernel-only pass for profilers: one factor build, then a few launches of
     each hot-path kernel on the same workload (no GMRES loop)."""
@@ -817,7 +878,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--iter-limit", type=int, default=50,
                     help="learned workload: GMRES iterations before the exact rebuild")
-    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned", "timestep"],
+    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned", "timestep",
+                                           "mrhs"],
                     default="adv2d",
                     help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
     args = ap.parse_args()
@@ -833,6 +895,8 @@ def main():
         return run_learned(args)
     if args.workload == "timestep":
         return run_timestep(args)
+    if args.workload == "mrhs":
+        return run_mrhs(args)
     return run_ours(args)
 
 

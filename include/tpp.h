@@ -55,7 +55,10 @@ typedef enum {
   TPP_ERR_TIMEOUT = 10         /* a device-side pipeline wait gave up (status word set; no trap) */
 } tpp_status;
 
-typedef enum { TPP_FP64 = 0, TPP_FP32 = 1 } tpp_prec;
+/* Arithmetic of the Kronecker apply: FP64; FP32 (float factors and arithmetic); BF16
+ * (BF16 factors and stage inputs, FP32 accumulation, on the tensor cores; 2D, n <= 16,
+ * contexts with TPP_FEAT_BF16). */
+typedef enum { TPP_FP64 = 0, TPP_FP32 = 1, TPP_BF16 = 2 } tpp_prec;
 
 typedef enum {
   TPP_PC_NONE = 0,         /* unpreconditioned */
@@ -70,6 +73,8 @@ typedef enum {
                                      Sylvester solve) instead of the default one-sided form */
 #define TPP_FEAT_LEARNED      8u  /* reserve the buffers of tpp_build_factors_learned (2D) */
 #define TPP_FEAT_TIME        16u  /* reserve 6 solution-sized vectors for tpp_time_integrate */
+#define TPP_FEAT_BF16        32u  /* reserve BF16 copies of the apply factors for TPP_BF16
+                                     (2D, n <= 16, one-sided form) */
 
 /*
  * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
@@ -113,7 +118,8 @@ typedef struct {
   int32_t max_iters;    /* total Arnoldi steps over all cycles, >= 1 */
   double rtol;          /* stop when ||b - A x|| <= rtol ||b||, rtol > 0 */
   int32_t pc;           /* tpp_pc */
-  int32_t inner_prec;   /* tpp_prec of the Kronecker apply; TPP_FP32 needs TPP_FEAT_MIXED */
+  int32_t inner_prec;   /* tpp_prec of the Kronecker apply; TPP_FP32 needs TPP_FEAT_MIXED,
+                           TPP_BF16 TPP_FEAT_BF16 (and TPP_FEAT_MIXED for inner solves) */
   int32_t flexible;     /* 1: flexible GMRES (stores Z = P^-1 V); forced to 1 when inner_prec != FP64 */
   int32_t inner_iters;  /* 0: each preconditioner application is one Kronecker apply.  k > 0
                            (mixed precision, needs TPP_FEAT_MIXED and TPP_PC_KRON): it is an
@@ -233,7 +239,9 @@ tpp_status tpp_build_block_jacobi(tpp_ctx* ctx, void* stream);
  * 3D applies the A1^-1 factor along z first, then the 2D form on each z slice.
  * b, x: device float64 [num_elem][nrhs][n^dim], 1 <= nrhs <= the problem's nrhs, must not
  * alias.  prec selects the arithmetic and factor precision (TPP_FP32 needs
- * TPP_FEAT_MIXED).  Asynchronous.
+ * TPP_FEAT_MIXED; TPP_BF16 needs TPP_FEAT_BF16: one CTA per element, the three dense
+ * stages and the column sweep as BF16 tensor-core products with FP32 accumulation, eight
+ * right-hand sides per warp).  Asynchronous.
  */
 tpp_status tpp_apply_inverse(const tpp_ctx* ctx, const double* b, double* x, int32_t nrhs,
                              int32_t prec, void* stream);

@@ -12,10 +12,11 @@ STATUS_NAMES = {0: "TPP_OK", 1: "TPP_ERR_INVALID_ARG", 2: "TPP_ERR_CUDA",
                 3: "TPP_ERR_SINGULAR_FACTOR", 4: "TPP_ERR_NOT_CONVERGED", 5: "TPP_ERR_BREAKDOWN",
                 6: "TPP_ERR_SCHUR", 7: "TPP_ERR_NAN", 8: "TPP_ERR_UNSUPPORTED",
                 9: "TPP_ERR_WORKSPACE", 10: "TPP_ERR_TIMEOUT"}
-TPP_FP64, TPP_FP32 = 0, 1
+TPP_FP64, TPP_FP32, TPP_BF16 = 0, 1, 2
 TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
 TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1, 2, 4, 8
 TPP_FEAT_TIME = 16
+TPP_FEAT_BF16 = 32
 TPP_TS_BACKWARD_EULER, TPP_TS_DIRK3, TPP_TS_RK4 = 0, 1, 2
 
 

@@ -191,6 +191,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.bj_piv = (features & TPP_FEAT_BLOCK_JACOBI) ? take((size_t)E * nloc * 4) : 0;
   L.tvec = (features & TPP_FEAT_TIME) ? take((size_t)6 * N * 8) : 0;
   L.mtab = take((size_t)(2 * TPP_MAX_MU + TPP_MAX_MU * TPP_MAX_N) * 8);
+  L.bf16 = (features & TPP_FEAT_BF16) ? take(bf16_factor_bytes(n, E)) : 0;
   L.V = take((size_t)(m + 1) * N * 8);
   L.Z = take((size_t)m * N * 8);
   L.vtmp = take((size_t)N * 8);
@@ -237,6 +238,7 @@ cudaError_t apply_precond(const tpp_ctx* c, int pc, int prec, const double* b, d
     return cudaMemcpyAsync(x, b, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
   if (pc == TPP_PC_BLOCK_JACOBI) return launch_bj_apply(c, b, x, skip, s);
+  if (prec == TPP_BF16) return launch_apply_bf16(c, b, x, skip, s);
   if (c->dim == 2) return launch_apply_2d(c, b, x, prec, skip, s);
   return launch_apply_3d(c, b, x, prec, skip, s);
 }
@@ -270,6 +272,11 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   }
   if (prob->dim == 3 && (features & TPP_FEAT_LEARNED)) {
     set_error("learned factors are implemented for 2D problems only");
+    return TPP_ERR_UNSUPPORTED;
+  }
+  if ((features & TPP_FEAT_BF16) &&
+      (prob->dim != 2 || prob->n > 16 || (features & TPP_FEAT_TWO_SIDED))) {
+    set_error("the BF16 tensor-core apply is implemented for 2D, n <= 16, one-sided form");
     return TPP_ERR_UNSUPPORTED;
   }
   if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
@@ -407,6 +414,7 @@ namespace {
 // status of the build just enqueued -> report and return code
 tpp_status finish_build(tpp_ctx* c, tpp_build_report* report, cudaStream_t s) {
   if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_to_f32(c, s), "k_to_f32");
+  if (c->features & TPP_FEAT_BF16) TPP_TRY_CUDA(launch_to_bf16(c, s), "k_bf16_factors");
   DevStatus st;
   TPP_TRY_CUDA(cudaMemcpyAsync(&st, c->ws + c->L.status, sizeof(st), cudaMemcpyDeviceToHost, s),
                "read status");
@@ -526,12 +534,16 @@ tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32
     set_error("b and x must be non-NULL and distinct");
     return TPP_ERR_INVALID_ARG;
   }
-  if (prec != TPP_FP64 && prec != TPP_FP32) {
-    set_error("prec must be TPP_FP64 or TPP_FP32");
+  if (prec != TPP_FP64 && prec != TPP_FP32 && prec != TPP_BF16) {
+    set_error("prec must be TPP_FP64, TPP_FP32 or TPP_BF16");
     return TPP_ERR_INVALID_ARG;
   }
   if (prec == TPP_FP32 && !(c->features & TPP_FEAT_MIXED)) {
     set_error("TPP_FP32 apply needs a context created with TPP_FEAT_MIXED");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (prec == TPP_BF16 && !(c->features & TPP_FEAT_BF16)) {
+    set_error("TPP_BF16 apply needs a context created with TPP_FEAT_BF16");
     return TPP_ERR_INVALID_ARG;
   }
   if (!c->factors_built) {
@@ -669,7 +681,8 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
   const int m = opts->restart;
   if (m < 1 || m > c->max_restart || opts->max_iters < 1 || !(opts->rtol > 0.0) ||
       opts->pc < TPP_PC_NONE || opts->pc > TPP_PC_BLOCK_JACOBI ||
-      (opts->inner_prec != TPP_FP64 && opts->inner_prec != TPP_FP32)) {
+      (opts->inner_prec != TPP_FP64 && opts->inner_prec != TPP_FP32 &&
+       opts->inner_prec != TPP_BF16)) {
     set_error("invalid GMRES options (restart, max_iters, rtol, pc or inner_prec)");
     return TPP_ERR_INVALID_ARG;
   }
@@ -679,6 +692,10 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
   }
   if (opts->pc == TPP_PC_BLOCK_JACOBI && !c->bj_built) {
     set_error("TPP_PC_BLOCK_JACOBI needs tpp_build_block_jacobi first");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (opts->inner_prec == TPP_BF16 && !(c->features & TPP_FEAT_BF16)) {
+    set_error("inner_prec TPP_BF16 needs TPP_FEAT_BF16");
     return TPP_ERR_INVALID_ARG;
   }
   if (opts->inner_prec == TPP_FP32 && !(c->features & TPP_FEAT_MIXED)) {
@@ -740,7 +757,9 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     for (int i = 0; i < kin; ++i) {
       float* vi = Vi + (size_t)i * N;
       float* wi = Vi + (size_t)(i + 1) * N;
-      TPP_TRY_CUDA(launch_apply_f32(c, vi, tf, din, s), "inner precond");
+      TPP_TRY_CUDA(opts->inner_prec == TPP_BF16 ? launch_apply_bf16_f32(c, vi, tf, din, s)
+                                                : launch_apply_f32(c, vi, tf, din, s),
+                   "inner precond");
       TPP_TRY_CUDA(launch_traces_f32(c, tf, trf, s, din), "inner traces");
       TPP_TRY_CUDA(launch_dg_apply_f32(c, tf, trf, wi, din, s), "inner operator");
       // Gram-Schmidt with selective reorthogonalisation: dots with the basis
@@ -761,7 +780,8 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
     TPP_TRY_CUDA(gmres_lsq(sti, Hi, g0, yi, s), "inner lsq");
     TPP_TRY_CUDA(gmres_combine_f32(Vi, N, sti, yi, t2, done, s), "inner Vy");
     TPP_TRY_CUDA(accumulate_inner(st, sti, done, s), "inner count");
-    TPP_TRY_CUDA(apply_precond(c, TPP_PC_KRON, TPP_FP32, t2, z, done, s), "inner P^-1");
+    TPP_TRY_CUDA(apply_precond(c, TPP_PC_KRON, opts->inner_prec == TPP_BF16 ? TPP_BF16 : TPP_FP32,
+                               t2, z, done, s), "inner P^-1");
     return TPP_OK;
   };
   auto read_scalar = [&](const double* dptr, double* hv) -> tpp_status {

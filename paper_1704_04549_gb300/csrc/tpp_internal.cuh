@@ -98,6 +98,7 @@ struct Layout {
   size_t bj_lu, bj_piv;
   size_t tvec;                         // time integration: 6 solution-sized vectors
   size_t mtab;                         // mass solve: mu-point rule and interpolation matrix
+  size_t bf16;                         // BF16 copies of the one-sided apply factors
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
   size_t total;
 };
@@ -270,6 +271,13 @@ cudaError_t launch_apply_2d(const tpp_ctx* c, const double* b, double* x, int pr
 cudaError_t launch_apply_3d(const tpp_ctx* c, const double* b, double* x, int prec,
                             const int32_t* skip, cudaStream_t s);
 cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s);
+// BF16 tensor-core apply (2D, n <= 16, one-sided form; k_apply_tc.cu)
+size_t bf16_factor_bytes(int n, int64_t E);
+cudaError_t launch_to_bf16(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_apply_bf16(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
+                              cudaStream_t s);
+cudaError_t launch_apply_bf16_f32(const tpp_ctx* c, const float* b, float* x,
+                                  const int32_t* skip, cudaStream_t s);
 cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
                             cudaStream_t s);
