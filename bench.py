@@ -16,6 +16,7 @@ divergence-free random-Fourier velocity (seed 1705), dt = 0.05, b ~ N(0, 1)
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -362,6 +363,16 @@ def run_ours(args):
             t_e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = statistics.median(t_e2e)
 
+    # arithmetic peaks measured live by the DFMA / FFMA chain probe
+    probe = {}
+    for name, prec, iters in (("fp64", TPP_FP64, 12000), ("fp32", TPP_FP32, 400000)):
+        rate = ctypes.c_double(0.0)
+        if lib.tpp_probe_fma_rate(prec, iters, ctypes.byref(rate),
+                                  ctypes.c_void_p(stream.cuda_stream)) == 0:
+            probe[name] = rate.value / 1e9
+    roofline["peak_probe_gflops"] = probe
+    extra = {} if args.no_extra else other_configs(args, dev)
+
     if rank != 0:
         return 0
     cpu = None
@@ -401,11 +412,54 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "other_configs": extra,
     }
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def other_configs(args, dev):
+    """Compact untimed-region records of the other configurations (each measured with
+    CUDA events, L2 flushed before apply launches): the 64 x 64 mesh at n = 31 and the
+    16^3 hex mesh at n = 11.  Apply GDOF/s in FP64 and FP32, the factor build, and the
+    mixed solver (FP64 FGMRES(30) around FP32 GMRES(12)) to 1e-8 within a step cap."""
+    import torch
+    from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, TPP_PC_KRON, Context
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+    for key, w, cap in (("adv2d_64x64_n31", workload(31), 300), ("adv3d_16cubed_n11", workload_3d(11), 400)):
+        ctx = Context(w["dim"], w["n"], w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
+                      features=TPP_FEAT_MIXED, device=str(dev))
+        N = ctx.num_dofs
+        b = torch.as_tensor(synthetic.rhs(w["rhs_seed"], N), device=dev)
+        z = torch.empty_like(b)
+        ctx.tpp_build_factors()
+        build_ms = time_each(lambda: ctx.tpp_build_factors(), 3, stream, flush)
+        rec = {"dofs": N, "build_ms": build_ms}
+        for name, prec in (("fp64", TPP_FP64), ("fp32", TPP_FP32)):
+            for _ in range(3):
+                ctx.tpp_apply_inverse(b, z, prec=prec)
+            t = time_each(lambda: ctx.tpp_apply_inverse(b, z, prec=prec), 10, stream, flush)
+            rec[f"apply_{name}_gdofs"] = N / (t * 1e-3) / 1e9
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=cap, pc=TPP_PC_KRON,
+                               inner_prec=TPP_FP32, flexible=True, inner_iters=args.inner,
+                               check=False, use_graph=args.graph)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rec["mixed"] = {"solve_ms": e0.elapsed_time(e1), "outer_iters": r["iters"],
+                        "inner_iters": r["inner_iters"], "converged": bool(r["converged"]),
+                        "true_rel_res": r["true_rel_res"], "outer_cap": cap}
+        out[key] = rec
+        del ctx
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_3d(args):
@@ -851,6 +905,8 @@ def main():
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the n = 31 and 3D sub-records of the default line")
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="GMRES iterations the reference arm extrapolates to")
     ap.add_argument("--ref-budget", type=float, default=15.0)

@@ -464,6 +464,12 @@ tpp_status tpp_solve_learned(tpp_ctx* ctx, tpp_mlp* net, double threshold, int32
 int64_t tpp_num_dofs(const tpp_ctx* ctx);
 int64_t tpp_num_elem(const tpp_ctx* ctx);
 
+/* Arithmetic peak probe (instrumentation for rooflines): the rate in flop/s of 8
+ * independent FMA chains per thread on 8 CTAs of 256 threads per SM, `iters` FMAs per
+ * chain, prec TPP_FP64 (DFMA) or TPP_FP32 (FFMA), timed with CUDA events on `stream`
+ * (synchronised).  The paper has no counterpart. */
+tpp_status tpp_probe_fma_rate(int32_t prec, int32_t iters, double* flops, void* stream);
+
 /* Number of CUDA kernels libtpp has launched since it was loaded (all contexts
  * and threads; instrumentation for benchmarks). */
 int64_t tpp_kernel_launch_count(void);

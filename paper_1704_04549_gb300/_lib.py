@@ -91,6 +91,7 @@ EXPORTS = {
     "tpp_num_elem": (C.c_int64, [C.c_void_p]),
     "tpp_last_error": (C.c_char_p, []),
     "tpp_kernel_launch_count": (C.c_int64, []),
+    "tpp_probe_fma_rate": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
     "tpp_core_size": (C.c_int32, [C.c_void_p]),
     "tpp_learned_inputs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tpp_build_factors_learned": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double,
