@@ -99,13 +99,24 @@ typedef enum {
  * layout [num_elem][nrhs][n^dim] (float64 unless stated).
  * Limits: dim in {2, 3}; 1 <= n <= 32 (2D), 1 <= n <= 16 (3D); num_elem >= 1; nrhs >= 1;
  * h > 0; dt >= 0; every nbr entry in [-1, num_elem).
+ *
+ * Over-integration (mu > n, Sec. 3.2 with the mu-point Gauss-Legendre rule, 2D): the
+ * integrals of the operator are evaluated at mu points per direction (the evaluation and
+ * derivative matrices G and D of the nodal basis at the quadrature points, Table
+ * tab:dg-ops), so vel_nodes holds a at the mu^2 quadrature points of every element and
+ * vel_face_normal a.n at the mu face quadrature points of every face (same orderings, mu in
+ * place of n; tpp_gauss_legendre returns the rule).  The rearranged block then has rank up
+ * to 2 mu + 2 instead of 2 n + 2 (the structure of Sec. 4.2.1 changes) and the factor
+ * build works on the explicit core described at tpp_build_factors.  Not with
+ * TPP_FEAT_BLOCK_JACOBI or TPP_FEAT_LEARNED.
  */
 typedef struct {
   int32_t dim;
   int32_t n;
   int64_t num_elem;
   int32_t nrhs;
-  int32_t reserved;
+  int32_t mu;          /* quadrature points per direction: 0 or n = collocated with the nodes;
+                          n < mu <= 32 = over-integration (2D), see below */
   double h;
   double dt;
   const double* vel_nodes;
@@ -197,8 +208,10 @@ void tpp_destroy(tpp_ctx* ctx);
 tpp_status tpp_set_velocity(tpp_ctx* ctx, const double* vel_nodes, const double* vel_face_normal,
                             double dt, void* stream);
 
-/* Nodes and weights of the Gauss-Legendre rule on [0, 1] (host arrays of n doubles), for
- * callers that evaluate their field at the nodes.  Synchronises the legacy stream. */
+/* Points and weights of the context's quadrature rule on [0, 1] (host arrays of mu
+ * doubles: the n Gauss-Legendre nodes when collocated, the mu-point rule when
+ * over-integrated), for callers that evaluate their field at the quadrature points.
+ * Synchronises the legacy stream. */
 tpp_status tpp_gauss_legendre(const tpp_ctx* ctx, double* nodes, double* weights);
 
 /*
@@ -219,6 +232,12 @@ tpp_status tpp_gauss_legendre(const tpp_ctx* ctx, double* nodes, double* weights
  * be NULL) is filled after a stream synchronisation.
  * Returns TPP_ERR_SINGULAR_FACTOR / TPP_ERR_SCHUR when an element could not be
  * factored (the report counts them).
+ * Over-integrated problems (mu > n): with the element-independent basis B = [vec(g_b g_b^T) |
+ * vec(d_b g_b^T) | vec(l1 l1^T) | vec(l0 l0^T)] (g_b, d_b the rows of G and D at quadrature
+ * point b, l0 / l1 the endpoint values) the rearranged block is A~ = B K B^T with K built
+ * from the element's weights and flux Jacobians at the quadrature points; one Householder
+ * QR B = Q R per context gives A~ = Q (R K R^T) Q^T, and the top-2 triplets come from the
+ * dense SVD of the small core R K R^T (size min(n^2, 2 mu + 2)), O(mu^3) per element.
  */
 tpp_status tpp_build_factors(tpp_ctx* ctx, tpp_build_report* report, void* stream);
 
@@ -391,6 +410,12 @@ typedef struct {
   const int32_t* zflags; /* [E] bit0 Lanczos not converged, bit1 A1 singular or cond_1 >= 1e14 */
   const double* G;       /* one-sided form: [E][n][2][n*n] shifted inverses Gs_j, Gp_j
                             (column-major n x n), NULL in the two-sided form */
+  /* Over-integrated 2D contexts only (mu > n; NULL otherwise), r = tpp_core_size:
+   * the rearranged block is A~ = Qb core Qb^T with B = Qb Rb (see tpp_build_factors) */
+  const double* core;    /* [E][r*r] explicit cores R K R^T, column-major */
+  const double* Qb;      /* [n^2 * r] orthonormal basis, column-major */
+  const double* Rb;      /* [r][2 mu + 2] triangular factor of the basis B, row-major */
+  const double* qtr;     /* [r] trace of mat(Qb[:, t]) */
 } tpp_views;
 
 tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);

@@ -22,7 +22,7 @@ TPP_TS_BACKWARD_EULER, TPP_TS_DIRK3, TPP_TS_RK4 = 0, 1, 2
 
 class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("num_elem", C.c_int64),
-                ("nrhs", C.c_int32), ("reserved", C.c_int32), ("h", C.c_double),
+                ("nrhs", C.c_int32), ("mu", C.c_int32), ("h", C.c_double),
                 ("dt", C.c_double), ("vel_nodes", C.c_void_p), ("vel_face_normal", C.c_void_p),
                 ("nbr", C.c_void_p)]
 
@@ -54,7 +54,8 @@ class TimeReport(C.Structure):
 class Views(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in
                 ("sigma", "A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2", "flags",
-                 "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags", "G")]
+                 "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags", "G", "core", "Qb",
+                 "Rb", "qtr")]
 
 
 EXPORTS = {

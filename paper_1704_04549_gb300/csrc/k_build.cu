@@ -481,10 +481,14 @@ __device__ void atomic_min_double(double* addr, double v) {
 //   k_final_w      S_A = Q_1^T L_A^-1 (two-sided: also S_B = Q_2^T L_B^-1)
 
 struct KsvdArgs {
-  int n, rz;
+  int n, rz;           // core size r = n + rz
   int64_t E;
   const double* kco;   // per block: Cx ((n+2) x n), Cy ((n+2) x n), Dg (n x n)
   const double *Zd, *Rz, *Qo;
+  // over-integrated blocks (mu > n): the core of every element given explicitly
+  // (Mcore [E][r x r] column-major), A~ = Qb M Qb^T with the dense orthonormal basis
+  // Qb (column-major n^2 x r) and qtr[t] = trace of mat(Qb[:, t]); NULL otherwise
+  const double *Mcore, *Qb, *qtr;
   double* scr;     // per element: the k_ksvd_w shared-memory image, tridiagonal work (16 r)
   int* iscr;       // per element: 4 r pivot flags
   double *sigma, *A1, *B1, *A2, *B2;
@@ -756,7 +760,12 @@ __global__ void __launch_bounds__(128) k_ksvd_w(KsvdArgs A) {
   const double *Cx = kc, *Cy = kc + nc * n, *Dg = kc + 2 * nc * n;
 
   if (A.mask && !A.mask[e]) return;                     // factors given (whole warp)
-  form_core(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, Ms, ld);
+  if (A.Mcore) {
+    const double* Mg = A.Mcore + (size_t)e * r * r;
+    for (int q = lane; q < r * r; q += 32) Ms[(q % r) + ld * (q / r)] = Mg[q];
+  } else {
+    form_core(Cx, Cy, Dg, A.Zd, A.Rz, n, rz, Ms, ld);
+  }
   __syncwarp();
 
   // ---- Householder bidiagonalisation M = U_h B V_h^T (B upper bidiagonal:
@@ -986,7 +995,8 @@ __global__ void __launch_bounds__(128) k_ksvd_vec(KsvdArgs A) {
     double p2 = 0.0, trc = 0.0;
     for (int t = gl; t < r; t += 8) {
       p2 += vec[t] * vec[t];
-      if (t < n) trc += vec[t];
+      if (A.qtr) trc += vec[t] * __ldg(A.qtr + t);
+      else if (t < n) trc += vec[t];
     }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
@@ -1009,7 +1019,11 @@ __global__ void __launch_bounds__(128) k_ksvd_vec(KsvdArgs A) {
       const int a = idx % n, b = idx / n;
       const double* mvec = (which == 0) ? mu1 : (which == 1) ? mv1 : (which == 2) ? mu2 : mv2;
       double val;
-      if (a == b) {
+      if (A.Qb) {
+        double sv = 0.0;
+        for (int t = 0; t < r; ++t) sv += __ldg(A.Qb + (size_t)t * nn + idx) * mvec[t];
+        val = sv;
+      } else if (a == b) {
         val = mvec[a];
       } else {
         const int o = b * (n - 1) + (a > b ? a - 1 : a);
@@ -1897,13 +1911,13 @@ __global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const dou
 // KSVD of the 2D-structured blocks in kco (2D elements, or the second stage
 // of the 3D nested form), inverses, Schur forms, S_A and S_B.
 cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t* mask) {
-  const int n = c->n, rz = c->rz, nn = n * n;
+  const int n = c->n, nn = n * n;
   const int64_t E = c->E;
   DevStatus* st = c->p<DevStatus>(c->L.status);
   // 1. KSVD
   KsvdArgs ka;
   ka.n = n;
-  ka.rz = rz;
+  ka.rz = c->rz;
   ka.E = E;
   ka.kco = c->p<double>(c->L.kco);
   ka.Zd = c->p<double>(c->L.zd);
@@ -1918,9 +1932,16 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
   ka.B2 = c->p<double>(c->L.fB2);
   ka.st = st;
   ka.mask = mask;
+  ka.Mcore = ka.Qb = ka.qtr = nullptr;
+  if (c->mu > c->n) {     // over-integration: explicit cores from k_core_mu
+    ka.rz = c->r - n;
+    ka.Mcore = c->p<double>(c->L.kco);
+    ka.Qb = c->p<double>(c->L.qb);
+    ka.qtr = c->p<double>(c->L.qtr);
+  }
   {
     const int warps = 4;
-    const size_t smem = (size_t)warps * ksvd_smem(n, rz).total * sizeof(double);
+    const size_t smem = (size_t)warps * ksvd_smem(n, ka.rz).total * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_ksvd_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
@@ -2041,6 +2062,11 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
 
 
 cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
+  if (c->mu > c->n) {           // over-integrated blocks: explicit cores (k_overint.cu)
+    cudaError_t err = launch_core_mu(c, s);
+    if (err != cudaSuccess) return err;
+    return launch_ksvd_pipeline(c, s, nullptr);
+  }
   k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
                                     c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                     c->p<double>(c->L.fa), c->p<double>(c->L.kco));

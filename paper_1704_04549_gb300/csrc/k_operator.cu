@@ -178,9 +178,11 @@ cudaError_t launch_struct_qr(const tpp_ctx* c, cudaStream_t s) {
 //   cX[e][i + n j (+ n^2 k)] = -dt h^(d-1) w_i w_j (w_k) a_X(node)     (X = x, y, z)
 //   fa[e][f][t]              = dt h^(d-1) (tangential weights) (a.n_outward)(face node)
 // from the caller's arrays (NULL: a zero field).
-__global__ void k_precompute(const Tables* T, int dim, int n, int64_t E, double h, double dt,
-                             const double* __restrict__ vel, const double* __restrict__ vfn,
-                             double* cx, double* cy, double* cz, double* fa) {
+__global__ void k_precompute(const double* __restrict__ wq, int dim, int n, int64_t E, double h,
+                             double dt, const double* __restrict__ vel,
+                             const double* __restrict__ vfn, double* cx, double* cy, double* cz,
+                             double* fa) {
+  // n: quadrature points per direction (the nodes, or the mu-point rule), weights wq
   const int nloc = (dim == 2) ? n * n : n * n * n;
   const int nfl = (dim == 2) ? n : n * n;
   const int64_t tot_v = E * nloc, tot_f = E * 2 * dim * nfl;
@@ -190,9 +192,9 @@ __global__ void k_precompute(const Tables* T, int dim, int n, int64_t E, double 
     if (g < tot_v) {
       const int q = (int)(g % nloc);
       const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      double wq = T->w[i] * T->w[j];
-      if (dim == 3) wq *= T->w[k];
-      const double f = -dt * hf * wq;
+      double wv = wq[i] * wq[j];
+      if (dim == 3) wv *= wq[k];
+      const double f = -dt * hf * wv;
       cx[g] = vel ? f * vel[g] : 0.0;
       cy[g] = vel ? f * vel[tot_v + g] : 0.0;
       if (dim == 3) cz[g] = vel ? f * vel[2 * tot_v + g] : 0.0;
@@ -200,7 +202,7 @@ __global__ void k_precompute(const Tables* T, int dim, int n, int64_t E, double 
       const int64_t gf = g - tot_v;
       const int q = (int)(gf % nfl);
       const int t0 = q % n, t1 = q / n;   // tangential indices (first tangential fastest)
-      const double wt = (dim == 2) ? T->w[t0] : T->w[t0] * T->w[t1];
+      const double wt = (dim == 2) ? wq[t0] : wq[t0] * wq[t1];
       fa[gf] = vfn ? dt * hf * wt * vfn[gf] : 0.0;
     }
   }
@@ -209,8 +211,9 @@ __global__ void k_precompute(const Tables* T, int dim, int n, int64_t E, double 
 cudaError_t launch_precompute(const tpp_ctx* c, const double* vel_nodes,
                               const double* vel_face_normal, cudaStream_t s) {
   const bool d3 = c->dim == 3;
+  const double* wq = (c->mu > c->n) ? c->p<MuTables>(c->L.mutab)->w : c->p<Tables>(c->L.tables)->w;
   k_precompute<<<152 * 8, 256, 0, s>>>(
-      c->p<Tables>(c->L.tables), c->dim, c->n, c->E, c->prob.h, c->prob.dt, vel_nodes,
+      wq, c->dim, c->mu, c->E, c->prob.h, c->prob.dt, vel_nodes,
       vel_face_normal, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
       d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa));
   count_launch();
@@ -262,6 +265,7 @@ __global__ void k_traces(const Tables* T, int n, int64_t E, const VT* __restrict
 
 cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
                           const int32_t* skip) {
+  if (c->mu > c->n) return launch_traces_mu(c, x, tr, s, skip);
   if (c->dim == 2)
     k_traces<2, double><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   else
@@ -272,6 +276,7 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
 
 cudaError_t launch_traces_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
                               const int32_t* skip) {
+  if (c->mu > c->n) return launch_traces_mu_f32(c, x, tr, s, skip);
   if (c->dim == 2)
     k_traces<2, float><<<152 * 8, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->EB, x, tr, skip);
   else
@@ -434,6 +439,7 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
 
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s) {
+  if (c->mu > c->n) return launch_dg_apply_mu(c, x, tr, y, skip, s, 1.0);
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                    d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
@@ -443,6 +449,7 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
 // y = dt A x = -dt J x: the operator without its mass term (traces tr of x given)
 cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double* tr, double* y,
                                  cudaStream_t s) {
+  if (c->mu > c->n) return launch_dg_apply_mu(c, x, tr, y, nullptr, s, 0.0);
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                    d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
@@ -453,6 +460,7 @@ cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double
 // copies of the flux Jacobian coefficients
 cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
                                 const int32_t* skip, cudaStream_t s) {
+  if (c->mu > c->n) return launch_dg_apply_mu_f32(c, x, tr, y, skip, s);
   const float* f = c->p<float>(c->L.opf);
   const OpF32Layout O = op_f32_layout(c);
   return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, c->dim == 3 ? f + O.cz : nullptr,

@@ -67,9 +67,9 @@ extern "C" tpp_status dg_apply_sumfact_static(const tpp_ctx* c, const double* x,
     tpp::set_error("nrhs must be in [1, the problem's nrhs]");
     return TPP_ERR_INVALID_ARG;
   }
-  const size_t need = (size_t)c->E * nrhs * 4 * (size_t)c->n;
+  const size_t need = (size_t)c->E * nrhs * 4 * (size_t)c->nfq;
   if (need > kStaticTraceDoubles) {
-    tpp::set_error("dg_apply_sumfact_static: num_elem * nrhs * 4 * n = " + std::to_string(need) +
+    tpp::set_error("dg_apply_sumfact_static: num_elem * nrhs * 4 * mu = " + std::to_string(need) +
                    " face-trace values exceed the static scratch of " +
                    std::to_string(kStaticTraceDoubles) + " doubles");
     return TPP_ERR_INVALID_ARG;

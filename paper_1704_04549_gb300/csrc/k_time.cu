@@ -69,8 +69,8 @@ cudaError_t lincomb(const tpp_ctx* c, double* out, double a0, const double* x0, 
 // dt to dt_new; the FP32 copies follow
 cudaError_t rescale_dt(tpp_ctx* c, double dt_new, cudaStream_t st) {
   const double f = dt_new / c->prob.dt;
-  const int64_t nv = c->E * c->nloc;
-  const int64_t nf = c->E * 2 * c->dim * (c->dim == 2 ? c->n : c->n * c->n);
+  const int64_t nv = c->E * c->nq;                  // coefficients at the quadrature points
+  const int64_t nf = c->E * 2 * c->dim * c->nfq;
   const size_t offs[3] = {c->L.cx, c->L.cy, c->L.cz};
   for (int d = 0; d < c->dim; ++d) {
     k_scale<<<152 * 4, 256, 0, st>>>(c->p<double>(offs[d]), nv, f);

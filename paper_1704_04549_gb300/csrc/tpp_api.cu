@@ -97,6 +97,10 @@ const char* validate(const tpp_problem* p, int32_t max_restart) {
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return "h must be positive and finite";
   if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return "dt must be >= 0 and finite";
   if (max_restart < 1 || max_restart > kMaxRestart) return "max_restart must be in [1, 63]";
+  if (p->mu != 0 && (p->mu < p->n || p->mu > TPP_MAX_MU)) return "mu must be 0 or in [n, 64]";
+  if (p->mu > p->n && p->dim != 2) return "over-integration (mu > n) is implemented in 2D";
+  if (p->mu > p->n && p->mu > 32)
+    return "over-integration needs mu <= 32 (KSVD core of size up to 2 mu + 2 <= 66)";
   if ((p->vel_nodes == nullptr) != (p->vel_face_normal == nullptr))
     return "vel_nodes and vel_face_normal must both be given or both be NULL";
   return nullptr;
@@ -109,9 +113,10 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   const int32_t R = p->nrhs;
   const int64_t EB = E * R;
   const int64_t nloc = (d == 2) ? (int64_t)n * n : (int64_t)n * n * n;
-  const int64_t nfl = (d == 2) ? n : (int64_t)n * n;
+  const int mu = (p->mu > n) ? p->mu : n;            // quadrature points per direction
+  const int64_t nfl = (d == 2) ? mu : (int64_t)mu * mu;
   const int64_t N = EB * nloc;
-  const int64_t Nc = E * nloc;
+  const int64_t Nc = E * ((d == 2) ? (int64_t)mu * mu : (int64_t)mu * mu * mu);
   const int nc = n + 2, Ro = n * n - n;
   const int rz = Ro < nc ? Ro : nc;
   if (rz_out) *rz_out = rz;
@@ -155,12 +160,24 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.flags = take((size_t)E * 4);
   L.masks = take((size_t)E * 2 * 4);
   {
-    const size_t r = (size_t)n + rz;
-    L.bscr = take((size_t)E * ksvd_scr_doubles(n, rz) * 8);
+    // KSVD core size: n + rz collocated; min(n^2, 2 mu + 2) over-integrated
+    const int rc = (mu > n) ? core_size_mu(n, mu) : n + rz;
+    const size_t r = (size_t)rc;
+    L.bscr = take((size_t)E * ksvd_scr_doubles(n, rc - n) * 8);
     L.biscr = take((size_t)E * 4 * r * 4);
     // coefficients of the 2D-structured block fed to the KSVD (2D: the element
-    // block; 3D: the second-stage block D1): Cx, Cy ((n+2) x n each), Dg (n x n)
-    L.kco = take((size_t)E * (2 * (size_t)nc * n + (size_t)n * n) * 8);
+    // block; 3D: the second-stage block D1): Cx, Cy ((n+2) x n each), Dg (n x n);
+    // over-integrated: the explicit cores (r x r)
+    const size_t per = (mu > n) ? r * r : (2 * (size_t)nc * n + (size_t)n * n);
+    L.kco = take((size_t)E * per * 8);
+  }
+  if (mu > n) {
+    const int m = 2 * mu + 2, rc = core_size_mu(n, mu);
+    L.mutab = take(sizeof(MuTables));
+    L.qb = take((size_t)n * n * rc * 8);
+    L.rb = take((size_t)rc * m * 8);
+    L.qtr = take((size_t)rc * 8);
+    L.bwork = take((size_t)n * n * m * 8 + (size_t)m * 8);
   }
   if (d == 3) {
     L.s1scr = take((size_t)E * s1_layout(n, rz, s1_jmax(n)).total * 8);
@@ -181,7 +198,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   }
   L.f32 = (features & TPP_FEAT_MIXED) ? take(f32_layout(n, E, d, two).total * 4) : 0;
   if (features & TPP_FEAT_MIXED) {      // FP32 operator and inner GMRES
-    L.opf = take(op_f32_layout(d, Nc, E, n, EB).total * 4);
+    L.opf = take(op_f32_layout(d, Nc, E, mu, EB).total * 4);
     L.gstate_in = take(sizeof(GmresState));
     L.gbuf_in = take(gbuf_layout(m).total * sizeof(double));
     L.vi = take((size_t)(m + 1) * N * 4);
@@ -279,6 +296,12 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
     set_error("the BF16 tensor-core apply is implemented for 2D, n <= 16, one-sided form");
     return TPP_ERR_UNSUPPORTED;
   }
+  if (prob->mu > prob->n &&
+      (features & (TPP_FEAT_BLOCK_JACOBI | TPP_FEAT_LEARNED | TPP_FEAT_TIME | TPP_FEAT_BF16))) {
+    set_error("over-integration (mu > n) does not support block Jacobi, learned factors, time "
+              "integration (its mass matrix is not diagonal) or the BF16 apply");
+    return TPP_ERR_UNSUPPORTED;
+  }
   if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
     set_error("exact block Jacobi is implemented for 2D problems only");
     return TPP_ERR_UNSUPPORTED;
@@ -325,10 +348,13 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
   c->EB = c->E * c->R;
   c->nloc = (prob->dim == 2) ? prob->n * prob->n : prob->n * prob->n * prob->n;
   c->N = c->EB * c->nloc;
+  c->mu = (prob->mu > prob->n) ? prob->mu : prob->n;
+  c->nq = (prob->dim == 2) ? c->mu * c->mu : c->mu * c->mu * c->mu;
+  c->nfq = (prob->dim == 2) ? c->mu : c->mu * c->mu;
   c->max_restart = max_restart;
   c->features = features;
   c->rz = rz;
-  c->r = prob->n + rz;
+  c->r = (c->mu > c->n) ? core_size_mu(c->n, c->mu) : prob->n + rz;
   c->ws = static_cast<char*>(workspace);
   c->ws_bytes = ws_bytes;
   c->L = L;
@@ -352,6 +378,8 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
       break;
     if ((rc = cuda_check(launch_tables(c, s), "k_tables")) != TPP_OK) break;
     if ((rc = cuda_check(launch_struct_qr(c, s), "k_struct_qr")) != TPP_OK) break;
+    if (c->mu > c->n && (rc = cuda_check(launch_mu_setup(c, s), "over-integration setup")) != TPP_OK)
+      break;
     if ((rc = cuda_check(launch_precompute(c, prob->vel_nodes, prob->vel_face_normal, s),
                          "k_precompute")) != TPP_OK)
       break;
@@ -391,10 +419,15 @@ tpp_status tpp_gauss_legendre(const tpp_ctx* c, double* nodes, double* weights) 
     set_error("nodes and weights must be non-NULL");
     return TPP_ERR_INVALID_ARG;
   }
-  const Tables* T = c->p<Tables>(c->L.tables);
-  TPP_TRY_CUDA(cudaMemcpy(nodes, T->x, c->n * sizeof(double), cudaMemcpyDeviceToHost),
+  const double* xs = c->p<Tables>(c->L.tables)->x;
+  const double* ws = c->p<Tables>(c->L.tables)->w;
+  if (c->mu > c->n) {
+    xs = c->p<MuTables>(c->L.mutab)->x;
+    ws = c->p<MuTables>(c->L.mutab)->w;
+  }
+  TPP_TRY_CUDA(cudaMemcpy(nodes, xs, c->mu * sizeof(double), cudaMemcpyDeviceToHost),
                "read nodes");
-  TPP_TRY_CUDA(cudaMemcpy(weights, T->w, c->n * sizeof(double), cudaMemcpyDeviceToHost),
+  TPP_TRY_CUDA(cudaMemcpy(weights, ws, c->mu * sizeof(double), cudaMemcpyDeviceToHost),
                "read weights");
   return TPP_OK;
 }
@@ -652,6 +685,12 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
     o->Azi = c->p<double>(c->L.fAzi);
     o->sigz = c->p<double>(c->L.sigz);
     o->zflags = c->p<int32_t>(c->L.zflags);
+  }
+  if (c->mu > c->n) {
+    o->core = c->p<double>(c->L.kco);
+    o->Qb = c->p<double>(c->L.qb);
+    o->Rb = c->p<double>(c->L.rb);
+    o->qtr = c->p<double>(c->L.qtr);
   }
   const Tables* T = c->p<Tables>(c->L.tables);
   o->gl_x = T->x;

@@ -99,6 +99,7 @@ struct Layout {
   size_t tvec;                         // time integration: 6 solution-sized vectors
   size_t mtab;                         // mass solve: mu-point rule and interpolation matrix
   size_t bf16;                         // BF16 copies of the one-sided apply factors
+  size_t mutab, qb, rb, qtr, bwork;    // over-integration: rule, core basis Q, R, traces, QR work
   size_t V, Z, vtmp, vtmp2, partials, hbuf, gbuf;
   size_t total;
 };
@@ -113,6 +114,9 @@ struct tpp_ctx {
   int32_t R;               // right-hand sides per element ([E][R][n^d] vectors)
   int64_t EB;              // vector blocks: E * R
   int32_t nloc;            // n^dim
+  int32_t mu;              // quadrature points per direction (n: collocated; > n: over-integrated)
+  int32_t nq;              // mu^dim quadrature points per element
+  int32_t nfq;             // mu^(dim-1) quadrature points per face
   int32_t max_restart;
   uint32_t features;
   int32_t rz;              // rank of the off-diagonal structure block
@@ -147,6 +151,27 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
                           const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
+// over-integration (mu > n, 2D; k_overint.cu)
+struct MuTables {        // the mu-point rule and the nodal basis at its points
+  double x[TPP_MAX_MU], w[TPP_MAX_MU];
+  double G[TPP_MAX_MU * TPP_MAX_N];      // G[a * n + j] = phi_j(x_a)
+  double D[TPP_MAX_MU * TPP_MAX_N];      // D[a * n + j] = phi_j'(x_a)
+  float Gf[TPP_MAX_MU * TPP_MAX_N], Df[TPP_MAX_MU * TPP_MAX_N], wf[TPP_MAX_N];
+};
+inline int core_size_mu(int n, int mu) {
+  const int m = 2 * mu + 2;
+  return (n * n < m) ? n * n : m;
+}
+cudaError_t launch_mu_setup(const tpp_ctx* c, cudaStream_t s);   // rule, basis QR
+cudaError_t launch_core_mu(const tpp_ctx* c, cudaStream_t s);    // explicit cores R K R^T
+cudaError_t launch_traces_mu(const tpp_ctx* c, const double* x, double* tr, cudaStream_t s,
+                             const int32_t* skip);
+cudaError_t launch_dg_apply_mu(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                               const int32_t* skip, cudaStream_t s, double mass);
+cudaError_t launch_traces_mu_f32(const tpp_ctx* c, const float* x, float* tr, cudaStream_t s,
+                                 const int32_t* skip);
+cudaError_t launch_dg_apply_mu_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
+                                   const int32_t* skip, cudaStream_t s);
 // y = dt A x without the mass term (explicit time stepping: J x = -y / dt)
 cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double* tr, double* y,
                                  cudaStream_t s);
@@ -238,7 +263,7 @@ struct OpF32Layout {
   size_t cx, cy, cz, fa, tr, total;
 };
 inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t EB) {
-  const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;
+  const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;   // n: points per direction
   OpF32Layout L{};
   size_t o = 0;
   L.cx = o; o += Nc;
@@ -250,7 +275,7 @@ inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t 
   return L;
 }
 inline OpF32Layout op_f32_layout(const tpp_ctx* c) {
-  return op_f32_layout(c->dim, c->E * c->nloc, c->E, c->n, c->EB);
+  return op_f32_layout(c->dim, c->E * c->nq, c->E, c->mu, c->EB);
 }
 
 // A view of the context for a call on nrhs <= R right-hand sides per element

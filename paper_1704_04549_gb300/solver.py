@@ -39,7 +39,8 @@ class Context:
 
     def __init__(self, dim: int, n: int, nel, h: float, dt: float, velocity,
                  max_restart: int = 30, features: int = 0, device: str = "cuda:0",
-                 stream=None, batch_rhs: int = 0, centres=None, batch_span: float = 0.0):
+                 stream=None, batch_rhs: int = 0, centres=None, batch_span: float = 0.0,
+                 mu: int = 0):
         from . import mesh
         self.batch_rhs = int(batch_rhs)
         if self.batch_rhs > 0:
@@ -49,8 +50,9 @@ class Context:
         else:
             self.nel = tuple(int(v) for v in nel)[:dim]
             nbr, nrhs = mesh.periodic_nbr(self.nel), 1
-        # geometry first (zero field): the field is evaluated at the library's nodes
-        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream)
+        # geometry first (zero field): the field is evaluated at the library's
+        # quadrature points (the nodes, or the mu-point rule when over-integrated)
+        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream, mu)
         x = self.gauss_legendre()[0]
         if self.batch_rhs > 0:
             vn, fn = mesh.isolated_field(cen, x, velocity, batch_span if batch_span > 0 else h)
@@ -61,17 +63,17 @@ class Context:
     @classmethod
     def from_arrays(cls, dim: int, n: int, h: float, dt: float, nbr, vel_nodes,
                     vel_face_normal, nrhs: int = 1, max_restart: int = 30, features: int = 0,
-                    device: str = "cuda:0", stream=None):
+                    device: str = "cuda:0", stream=None, mu: int = 0):
         """A context from the arrays of tpp_problem (layouts as in tpp.h)."""
         self = cls.__new__(cls)
         self.batch_rhs = 0
         nbr = np.ascontiguousarray(nbr, dtype=np.int32).reshape(-1, 2 * dim)
         self.nel = (nbr.shape[0],)
-        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream)
+        self._create(dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream, mu)
         self.tpp_set_velocity(vel_nodes, vel_face_normal, dt, stream)
         return self
 
-    def _create(self, dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream):
+    def _create(self, dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream, mu=0):
         if not torch.cuda.is_available():
             raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
         self.lib = L.load()
@@ -80,7 +82,8 @@ class Context:
         self.nrhs = int(nrhs)
         nb = torch.as_tensor(np.ascontiguousarray(nbr, dtype=np.int32), device=self.device)
         P = L.Problem()
-        P.dim, P.n, P.num_elem, P.nrhs = dim, n, int(nb.shape[0]), self.nrhs
+        P.dim, P.n, P.num_elem, P.nrhs, P.mu = dim, n, int(nb.shape[0]), self.nrhs, int(mu)
+        self.mu = max(int(mu), n)
         P.h, P.dt = self.h, self.dt
         P.nbr = _ptr(nb)
         nbytes = self.lib.tpp_workspace_bytes(C.byref(P), max_restart, features)
@@ -103,8 +106,9 @@ class Context:
         self.num_elem = int(self.lib.tpp_num_elem(ctx))
 
     def gauss_legendre(self):
-        """(nodes, weights) of the context's Gauss-Legendre rule on [0, 1] (host)."""
-        x, w = np.empty(self.n), np.empty(self.n)
+        """(points, weights) of the context's quadrature rule on [0, 1] (host): the n
+        Gauss-Legendre nodes, or the mu-point rule when over-integrated."""
+        x, w = np.empty(self.mu), np.empty(self.mu)
         L.check(self.lib.tpp_gauss_legendre(self._ctx, x.ctypes.data_as(C.c_void_p),
                                             w.ctypes.data_as(C.c_void_p)), "tpp_gauss_legendre")
         return x, w
@@ -346,6 +350,12 @@ class Context:
         res["gl_x"] = grab(v.gl_x, n, torch.float64)
         res["gl_w"] = grab(v.gl_w, n, torch.float64)
         res["D"] = grab(v.D, n * n, torch.float64).view(n, n)
+        if self.mu > self.n:
+            r, m = self.tpp_core_size(), 2 * self.mu + 2
+            res["core"] = grab(v.core, E * r * r, torch.float64).view(E, r, r).transpose(1, 2)
+            res["Qb"] = grab(v.Qb, n * n * r, torch.float64).view(r, n * n).t()
+            res["Rb"] = grab(v.Rb, r * m, torch.float64).view(r, m)
+            res["qtr"] = grab(v.qtr, r, torch.float64)
         if self.dim == 3:
             res["Az"] = grab(v.Az, E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
             res["Azi"] = grab(v.Azi, E * n * n, torch.float64).view(E, n, n).transpose(1, 2)

@@ -8,13 +8,13 @@ from oracle.dg import AdvectionDG, PeriodicMesh
 DEV = "cuda:0"
 
 
-def make_pair(n, nel, dt, vel, max_restart=30, features=0, h=None):
-    """(CUDA Context, oracle AdvectionDG) for the same problem."""
+def make_pair(n, nel, dt, vel, max_restart=30, features=0, h=None, mu=None):
+    """(CUDA Context, oracle AdvectionDG) for the same problem; mu > n over-integrates."""
     from paper_1704_04549_gb300 import Context
     mesh = PeriodicMesh(nel, h)
     ctx = Context(len(nel), n, nel, mesh.h, dt, vel, max_restart=max_restart,
-                  features=features, device=DEV)
-    return ctx, AdvectionDG(mesh, n, dt, vel)
+                  features=features, device=DEV, mu=mu or 0)
+    return ctx, AdvectionDG(mesh, n, dt, vel, mu)
 
 
 def to_dev(a):

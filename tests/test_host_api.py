@@ -17,7 +17,7 @@ def L():
     return _lib
 
 
-def _problem(L, dim=2, n=8, nel=(4, 4), h=1.0, dt=0.05, nrhs=1, isolated=False):
+def _problem(L, dim=2, n=8, nel=(4, 4), h=1.0, dt=0.05, nrhs=1, isolated=False, mu=0):
     """A tpp_problem on host arrays (the sizing and validation calls read no array)."""
     from paper_1704_04549_gb300 import mesh
     E = int(np.prod(nel)) if len(nel) else 0
@@ -25,7 +25,7 @@ def _problem(L, dim=2, n=8, nel=(4, 4), h=1.0, dt=0.05, nrhs=1, isolated=False):
            else mesh.periodic_nbr(nel))
     keep = dict(nbr=np.ascontiguousarray(nbr, dtype=np.int32))
     P = L.Problem()
-    P.dim, P.n, P.num_elem, P.nrhs = dim, n, E, nrhs
+    P.dim, P.n, P.num_elem, P.nrhs, P.mu = dim, n, E, nrhs, mu
     P.h, P.dt = h, dt
     P.nbr = keep["nbr"].ctypes.data_as(C.c_void_p)
     return P, keep
@@ -68,6 +68,19 @@ def test_workspace_sizing_and_validation(L):
     v = np.zeros(2 * 16 * 64)
     P.vel_nodes = v.ctypes.data_as(C.c_void_p)
     assert lib.tpp_workspace_bytes(C.byref(P), 30, 0) == 0
+
+
+def test_over_integration_sizing_and_validation(L):
+    """mu = 0 and mu = n are the collocated rule; n < mu <= 32 over-integrates in 2D
+    (explicit cores of size min(n^2, 2 mu + 2), operator coefficients at mu^2 points)."""
+    lib = L.load()
+    base = lib.tpp_workspace_bytes(C.byref(_problem(L)[0]), 30, 0)
+    assert lib.tpp_workspace_bytes(C.byref(_problem(L, mu=8)[0]), 30, 0) == base
+    P12, k12 = _problem(L, mu=12)
+    assert lib.tpp_workspace_bytes(C.byref(P12), 30, 0) > base
+    for bad in (dict(mu=5), dict(mu=33), dict(mu=-1), dict(dim=3, n=4, nel=(2, 2, 2), mu=6)):
+        Pb, kb = _problem(L, **bad)
+        assert lib.tpp_workspace_bytes(C.byref(Pb), 30, 0) == 0, bad
 
 
 def test_invalid_arguments_are_reported_without_a_device(L):
