@@ -308,6 +308,72 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
                        tpp_gmres_result* result, void* stream);
 
 /*
+ * Per-system batched GMRES over batches of isolated elements (an extension for
+ * mixed-degree batches; each system is one element's diagonal block of Sec. 3.4,
+ * S_e x = b with mass, volume and outflow face terms, solved by the
+ * right-preconditioned restarted GMRES of Sec. 5 with the Kronecker preconditioner
+ * of Alg. 2d-apply / 3d-apply).  Unlike gmres_solve, every (element, right-hand
+ * side) system runs its own Arnoldi process with its own Givens rotations,
+ * restarts and convergence test: ||b - S_e x|| <= rtol ||b|| per system.
+ *
+ * The contexts (one per degree group: dim, n) must be isolated (every nbr entry
+ * -1), collocated (mu <= n), created with TPP_FEAT_TWO_SIDED (the two-sided factors
+ * are staged in shared memory), with n <= 32 (2D) / n <= 16 (3D), factors built,
+ * all on the current device; prec = TPP_FP32 also needs TPP_FEAT_MIXED.  The
+ * systems run in persistent launches grouped by n (8, 16 or 32 lanes per system,
+ * lane i owning row i of the n x n matrix of a vector or of its z slices); CTAs
+ * take elements from one queue per launch, most expensive degree first, stage an
+ * element's factors and flux coefficients in shared memory and solve its nrhs
+ * systems warp by warp.
+ *
+ * prec TPP_FP64: GMRES(restart) in FP64.  prec TPP_FP32: FP64 iterative refinement
+ * (true residual with the FP64 operator, up to max_outer steps) around FP32
+ * GMRES(restart) solves of the correction to the relative residual inner_rtol
+ * (FP32 operator, factors and Arnoldi vectors; Hessenberg and Givens in FP64).
+ * max_iters bounds the Arnoldi steps of a system (summed over the inner solves).
+ */
+typedef struct {
+  int32_t restart;          /* m, 1..31 */
+  int32_t max_iters;        /* >= 1 */
+  double rtol;              /* > 0 */
+  int32_t prec;             /* TPP_FP64 or TPP_FP32 (mixed) */
+  int32_t max_outer;        /* mixed: refinement steps (>= 1) */
+  double inner_rtol;        /* mixed: relative tolerance of each FP32 solve, in (0, 1) */
+  int32_t warps[3];         /* warps per CTA of the 8-, 16- and 32-lane launches, 1..8; 0: 8 */
+  int32_t ctas_per_sm[3];   /* CTAs per SM of those launches; 0: as many as fit */
+  int32_t* const* iters;    /* optional (NULL): per context a device int32 [E * nrhs] of
+                               Arnoldi steps per system */
+  double* const* relres;    /* optional (NULL): per context a device float64 [E * nrhs] of
+                               final true relative residuals */
+} tpp_batch_opts;
+
+typedef struct {
+  int64_t systems;          /* (element, right-hand side) systems solved */
+  int64_t total_iters;      /* Arnoldi steps summed over the systems */
+  int32_t max_iters;        /* largest per system */
+  int32_t unconverged;      /* systems above rtol at exit */
+  int32_t max_outer;        /* mixed: largest number of refinement steps */
+  int32_t launches;         /* persistent launches made (one per lane-group width used) */
+  double max_relres;        /* largest final true relative residual */
+} tpp_batch_report;
+
+/* Workspace for tpp_batch_gmres with these contexts and options (0 if invalid;
+ * tpp_last_error says why).  Queries the current device. */
+size_t tpp_batch_workspace_bytes(tpp_ctx* const* ctxs, int32_t nctx, const tpp_batch_opts* opts);
+
+/* ctxs: host array of nctx contexts; b, x: host arrays of nctx device float64
+ * pointers [E][nrhs][n^d] (x overwritten, zero initial guess); workspace: device,
+ * 256-byte aligned, ws_bytes >= tpp_batch_workspace_bytes, owned by the caller.
+ * Synchronises `stream` and fills `report` (host, required).  Returns
+ * TPP_ERR_INVALID_ARG for a context or option outside the limits above,
+ * TPP_ERR_WORKSPACE for a small or misaligned workspace, TPP_ERR_NOT_CONVERGED if a
+ * system ends above rtol (x still holds every system's last iterate). */
+tpp_status tpp_batch_gmres(tpp_ctx* const* ctxs, int32_t nctx, const double* const* b,
+                           double* const* x, const tpp_batch_opts* opts,
+                           tpp_batch_report* report, void* workspace, size_t ws_bytes,
+                           void* stream);
+
+/*
  * dg_apply_sumfact_static: the same y = (M + dt A) x as dg_apply_sumfact, for
  * callers that cannot allocate device memory themselves (their device memory is
  * handed out by an allocator they do not control, or fixed once at start-up) and

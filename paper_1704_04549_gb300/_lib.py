@@ -46,6 +46,19 @@ class BuildReport(C.Structure):
                 ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
+                ("prec", C.c_int32), ("max_outer", C.c_int32), ("inner_rtol", C.c_double),
+                ("warps", C.c_int32 * 3), ("ctas_per_sm", C.c_int32 * 3),
+                ("iters", C.c_void_p), ("relres", C.c_void_p)]
+
+
+class BatchReport(C.Structure):
+    _fields_ = [("systems", C.c_int64), ("total_iters", C.c_int64), ("max_iters", C.c_int32),
+                ("unconverged", C.c_int32), ("max_outer", C.c_int32), ("launches", C.c_int32),
+                ("max_relres", C.c_double)]
+
+
 class TimeReport(C.Structure):
     _fields_ = [("steps", C.c_int32), ("gmres_iters", C.c_int32), ("builds", C.c_int32),
                 ("solves", C.c_int32), ("max_true_rel_res", C.c_double)]
@@ -78,6 +91,10 @@ EXPORTS = {
                                        C.c_void_p]),
     "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                         C.c_void_p]),
+    "tpp_batch_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int32, C.POINTER(BatchOpts)]),
+    "tpp_batch_gmres": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.POINTER(BatchOpts), C.POINTER(BatchReport), C.c_void_p,
+                                  C.c_size_t, C.c_void_p]),
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(GmresOpts),
                               C.POINTER(GmresResult), C.c_void_p]),
     "tpp_get_views": (C.c_int, [C.c_void_p, C.POINTER(Views)]),

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/tpp.h: validation, workspace
 // layout, launch sequencing and the restarted GMRES driver.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -336,6 +337,7 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
       return TPP_ERR_INVALID_ARG;
     }
   tpp_ctx* c = new tpp_ctx();
+  c->isolated = std::all_of(nb.begin(), nb.end(), [](int32_t v) { return v == -1; });
   c->prob = *prob;
   c->prob.vel_nodes = nullptr;
   c->prob.vel_face_normal = nullptr;

@@ -126,6 +126,7 @@ struct tpp_ctx {
   tpp::Layout L;
   bool factors_built;
   bool bj_built;
+  bool isolated;           // no neighbour coupling (every nbr entry -1): block-diagonal
   int32_t partial_blocks;  // number of CTAs of the reduction kernels
   cudaGraphExec_t gexec[64];   // use_graph: captured Arnoldi step groups, by first step
   int32_t gkernels[64];        // kernels in each (added to the launch count per replay)

@@ -16,6 +16,9 @@ STRUCTS = {
     "tpp_gmres_result": "GmresResult",
     "tpp_build_report": "BuildReport",
     "tpp_views": "Views",
+    "tpp_batch_opts": "BatchOpts",
+    "tpp_batch_report": "BatchReport",
+    "tpp_time_report": "TimeReport",
 }
 
 
