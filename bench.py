@@ -541,12 +541,122 @@ def run_3d(args):
 
 def run_batch(args):
     """The mixed-degree batch (20,000 2D elements, p ~ U{4..30}, and 2,000 3D elements,
+    p ~ U{3..12}; isolated unit elements (h = 1; --h-reading domain: h = 1/64) covering 1/64
+    of the velocity field's unit domain, centres uniform, random-Fourier velocity, dt = 0.05,
+    64 right-hand sides ~ N(0, 1) per element), every (element, right-hand side) system
+    solved to 1e-8 by its own GMRES (tpp_batch_gmres: persistent launches grouped by n).
+    One context per degree group holds the factors; a step = the factor build of every
+    group + the batched solve; value = device time of one FP64 step, the mixed-precision
+    step as a sub-record.  Inputs (3.9 + 0.8 GB per vector set) exceed L2."""
+    if args.batch_solver == "group":
+        return run_batch_groups(args)
+    import torch
+    from paper_1704_04549_gb300 import Context
+    from paper_1704_04549_gb300 import _lib
+    from paper_1704_04549_gb300.batch import BatchGmres
+    lib = _lib.load()
+    dev = torch.device("cuda:0")
+    groups = synthetic.mixed_degree_batch(e2d=int(round(20000 * args.batch_scale)),
+                                          e3d=int(round(2000 * args.batch_scale)))
+    vel = {2: synthetic.fourier_velocity(1709, 2), 3: synthetic.fourier_velocity(1709, 3)}
+    h_el = 1.0 / 64 if args.h_reading == "domain" else 1.0
+    R = 64
+    feats = _lib.TPP_FEAT_TWO_SIDED | _lib.TPP_FEAT_MIXED
+
+    def make(grps):
+        cs, b_, x_ = [], [], []
+        for g in grps:
+            c = Context(g.dim, g.n, (len(g.ids),), h_el, 0.05, vel[g.dim], max_restart=1,
+                        features=feats, device=str(dev), batch_rhs=R, centres=g.centres,
+                        batch_span=1.0 / 64)
+            c.tpp_build_factors()
+            cs.append(c)
+            b_.append(torch.as_tensor(synthetic.rhs(g.rhs_seed, c.num_dofs), device=dev))
+            x_.append(torch.zeros(c.num_dofs, dtype=torch.float64, device=dev))
+        return cs, b_, x_
+
+    # launch shapes per lane-group width from the autotuner, on a 5 % sample of the batch
+    # (same degree groups; JSON cache keyed by GPU, precision, restart and groups)
+    from paper_1704_04549_gb300.autotune import tune_batch_gmres
+    sample = synthetic.mixed_degree_batch(e2d=max(1, int(round(1000 * args.batch_scale))),
+                                          e3d=max(1, int(round(100 * args.batch_scale))))
+    sc, sb, sx = make(sample)
+    common = dict(restart=args.batch_restart, rtol=1e-8, max_iters=args.max_iters,
+                  inner_rtol=args.batch_inner_rtol, max_outer=8)
+    tuned = {m: tune_batch_gmres(sc, sb, sx, mixed=(m == "mixed"), **common)
+             for m in ("fp64", "mixed")}
+    del sc, sb, sx
+    ctxs, bs, xs = make(groups)
+    dofs = sum(c.num_dofs for c in ctxs)
+    solvers = {m: BatchGmres(ctxs, mixed=(m == "mixed"), warps=tuned[m]["warps"],
+                             ctas_per_sm=tuned[m]["ctas_per_sm"],
+                             reg_budget=tuned[m]["reg_budget"], per_system=True, **common)
+               for m in ("fp64", "mixed")}
+    stream = torch.cuda.current_stream(dev)
+
+    def build():
+        for c in ctxs:
+            c.tpp_build_factors()
+
+    def timed(fn, steps):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = [fn() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, out[-1]
+
+    res = {}
+    l0 = lib.tpp_kernel_launch_count()
+    with ClockSampler(0) as clk:
+        for mode, sv in solvers.items():
+            for _ in range(args.warmup):
+                build()
+                sv.solve(bs, xs)
+            ms, rep = timed(lambda: (build(), sv.solve(bs, xs))[1], args.steps)
+            ms_solve, _ = timed(lambda: sv.solve(bs, xs), args.steps)
+            its = torch.cat([t.double() for t in sv.iters])
+            res[mode] = {"ms": ms, "solve_ms": ms_solve, "build_ms": ms - ms_solve,
+                         "launch_ms": rep["launch_ms"],
+                         "unconverged": rep["unconverged"], "max_relres": rep["max_relres"],
+                         "iters_mean": float(its.mean()), "iters_max": rep["max_iters"],
+                         "iters_total": rep["total_iters"], "max_outer": rep["max_outer"],
+                         "launches_per_solve": rep["launches"]}
+    launches = lib.tpp_kernel_launch_count() - l0
+    e2d = sum(len(g.ids) for g in groups if g.dim == 2)
+    e3d = sum(len(g.ids) for g in groups if g.dim == 3)
+    line = {
+        "metric": "mixed-degree batch: time to solve every (element, rhs) system to 1e-8 "
+                  "(factor build + per-system batched GMRES), 1 GB300",
+        "value": res["fp64"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "mixed-degree batch, %d 2D elements p~U{4..30} + %d 3D elements "
+                               "p~U{3..12}, h=%g, span 1/64, dt=0.05, 64 RHS each, seed 1709, "
+                               "GMRES(%d) per system" % (e2d, e3d, h_el, args.batch_restart),
+                   "groups": len(groups), "dof_rhs": dofs, "scale": args.batch_scale,
+                   "l2": "inputs larger than L2"},
+        "fp64": res["fp64"], "mixed": res["mixed"],
+        "autotune": {m: {k: t[k] for k in ("warps", "ctas_per_sm", "reg_budget", "cached",
+                                            "table")} for m, t in tuned.items()},
+        "all_converged": all(r["unconverged"] == 0 for r in res.values()),
+        "dof_rhs_per_s": {m: dofs / (r["ms"] * 1e-3) for m, r in res.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_batch_groups(args):
+    """The mixed-degree batch (20,000 2D elements, p ~ U{4..30}, and 2,000 3D elements,
     p ~ U{3..12}; isolated unit elements (h = 1; --h-reading domain: h = 1/64) covering 1/64 of
     the velocity field's unit domain, centres uniform, random-Fourier velocity, dt = 0.05, 64
     right-hand sides ~ N(0, 1) per element; each
     element's block-diagonal system solved to 1e-8).  One context per degree group, groups
-    in sequence; value = the sum over groups of the device time of one step (factor build
-    + solve of all the group's systems)."""
+    in sequence, each group's systems as one Krylov solve (gmres_solve); value = the sum
+    over groups of the device time of one step (factor build + solve)."""
     import torch
     from paper_1704_04549_gb300 import batch as B
     from paper_1704_04549_gb300 import _lib
@@ -922,6 +1032,11 @@ def main():
     ap.add_argument("--form", choices=["one-sided", "two-sided"], default="one-sided",
                     help="apply form: one-sided (shifted inverses, default) or the paper's "
                          "two-sided Schur / quasi-triangular Sylvester form")
+    ap.add_argument("--batch-solver", choices=["system", "group"], default="system",
+                    help="batch workload: per-system batched GMRES or one Krylov solve per "
+                         "degree group")
+    ap.add_argument("--batch-restart", type=int, default=20)
+    ap.add_argument("--batch-inner-rtol", type=float, default=1e-4)
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="batch workload: fraction of the 20,000 + 2,000 elements")
     ap.add_argument("--no-graph", dest="graph", action="store_false",

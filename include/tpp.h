@@ -341,6 +341,9 @@ typedef struct {
   double inner_rtol;        /* mixed: relative tolerance of each FP32 solve, in (0, 1) */
   int32_t warps[3];         /* warps per CTA of the 8-, 16- and 32-lane launches, 1..8; 0: 8 */
   int32_t ctas_per_sm[3];   /* CTAs per SM of those launches; 0: as many as fit */
+  int32_t reg_budget[3];    /* kernel variant of those launches: 1 = up to 255 registers per
+                               thread, 2 = up to 128 (two 256-thread CTAs per SM); 0: 2 for
+                               the 8- and 16-lane launches, 1 for the 32-lane one */
   int32_t* const* iters;    /* optional (NULL): per context a device int32 [E * nrhs] of
                                Arnoldi steps per system */
   double* const* relres;    /* optional (NULL): per context a device float64 [E * nrhs] of
@@ -355,6 +358,7 @@ typedef struct {
   int32_t max_outer;        /* mixed: largest number of refinement steps */
   int32_t launches;         /* persistent launches made (one per lane-group width used) */
   double max_relres;        /* largest final true relative residual */
+  double launch_ms[3];      /* device time of the 8-, 16- and 32-lane launches (0: none) */
 } tpp_batch_report;
 
 /* Workspace for tpp_batch_gmres with these contexts and options (0 if invalid;

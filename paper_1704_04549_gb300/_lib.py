@@ -50,13 +50,13 @@ class BatchOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
                 ("prec", C.c_int32), ("max_outer", C.c_int32), ("inner_rtol", C.c_double),
                 ("warps", C.c_int32 * 3), ("ctas_per_sm", C.c_int32 * 3),
-                ("iters", C.c_void_p), ("relres", C.c_void_p)]
+                ("reg_budget", C.c_int32 * 3), ("iters", C.c_void_p), ("relres", C.c_void_p)]
 
 
 class BatchReport(C.Structure):
     _fields_ = [("systems", C.c_int64), ("total_iters", C.c_int64), ("max_iters", C.c_int32),
                 ("unconverged", C.c_int32), ("max_outer", C.c_int32), ("launches", C.c_int32),
-                ("max_relres", C.c_double)]
+                ("max_relres", C.c_double), ("launch_ms", C.c_double * 3)]
 
 
 class TimeReport(C.Structure):

@@ -70,7 +70,7 @@ class BatchGmres:
     def __init__(self, contexts, *, restart: int = 20, rtol: float = 1e-8,
                  max_iters: int = 300, mixed: bool = False, inner_rtol: float = 1e-4,
                  max_outer: int = 8, warps=(0, 0, 0), ctas_per_sm=(0, 0, 0),
-                 per_system: bool = False):
+                 reg_budget=(0, 0, 0), per_system: bool = False):
         import ctypes as C
         self.C = C
         self.lib = L.load()
@@ -85,6 +85,7 @@ class BatchGmres:
         o.max_outer, o.inner_rtol = int(max_outer), float(inner_rtol)
         for i in range(3):
             o.warps[i], o.ctas_per_sm[i] = int(warps[i]), int(ctas_per_sm[i])
+            o.reg_budget[i] = int(reg_budget[i])
         if per_system:
             sizes = [c.num_dofs // c.n ** c.dim for c in self.contexts]
             self.iters = [torch.zeros(m, dtype=torch.int32, device=self.device) for m in sizes]
@@ -117,6 +118,7 @@ class BatchGmres:
                                           C.byref(rep), C.c_void_p(self.ws.data_ptr()),
                                           self.ws.numel(), C.c_void_p(s.cuda_stream))
         out = {f: getattr(rep, f) for f, _ in L.BatchReport._fields_}
+        out["launch_ms"] = list(rep.launch_ms)
         out["status"] = st
         if check and st != L.TPP_OK:
             raise L.TppError(st, "tpp_batch_gmres")

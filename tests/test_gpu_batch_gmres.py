@@ -129,3 +129,23 @@ def test_invalid_contexts_and_options_are_rejected():
         BatchGmres([good], restart=40)
     with pytest.raises(TppError, match="TPP_FEAT_MIXED"):
         BatchGmres([good], mixed=True)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_launch_shapes_give_identical_results(mixed):
+    """Warps per CTA, CTAs per SM and the register budget (the autotuner's choices) change
+    only the schedule: every system's iterate is bit-identical across shapes."""
+    from paper_1704_04549_gb300.batch import BatchGmres
+    groups = [(2, 4, 3), (2, 13, 2), (2, 25, 2), (3, 6, 2)]
+    ctxs, isos, bs, xs = _batch(mixed, groups)
+    ref = None
+    for w, c, rb in [(8, 0, 1), (2, 1, 2), (4, 0, 2), (8, 1, 1)]:
+        solver = BatchGmres(ctxs, restart=RESTART, rtol=1e-8, mixed=mixed, warps=(w,) * 3,
+                            ctas_per_sm=(c,) * 3, reg_budget=(rb,) * 3)
+        rep = solver.solve(bs, xs)
+        assert rep["unconverged"] == 0 and all(t > 0 for t in rep["launch_ms"])
+        got = [to_host(x).copy() for x in xs]
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(ref, got)), (w, c, rb)
