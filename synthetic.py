@@ -232,3 +232,30 @@ def mixed_degree_batch(seed: int = 1709, e2d: int = 20000, e3d: int = 2000,
             groups.append(DegreeGroup(dim, int(p) + 1, cs[sel], sel + off,
                                       rhs_seed=seed * 1000 + dim * 100 + int(p)))
     return groups
+
+
+# ---------------------------------------------------------------------------
+# Linearisation state of the 2D Euler workload (Sec. 5.3, the moving isentropic vortex at
+# t = 0): conserved variables (rho, rho u, rho v, rho E) at points X [..., 2].
+VORTEX = dict(gamma=1.4, mach=0.5, u_inf=1.0, theta=float(np.arctan(0.5)), eps=0.3, rc=1.5,
+              x0=5.0, y0=5.0, rho_inf=1.0)
+
+
+def euler_vortex_state(X: np.ndarray, params: dict = VORTEX) -> np.ndarray:
+    """The vortex of Sec. 5.3 with the paper's parameters (M = 0.5, u_inf = 1, theta =
+    atan(1/2), eps = 0.3, r_c = 1.5, centre (5, 5)); p_inf = rho_inf u_inf^2 / (gamma M^2)
+    (free-stream Mach number M).  Returns [..., 4] conserved variables."""
+    P = params
+    g = P["gamma"]
+    X = np.asarray(X, dtype=np.float64)
+    dx, dy = X[..., 0] - P["x0"], X[..., 1] - P["y0"]
+    f = (1.0 - dx * dx - dy * dy) / P["rc"] ** 2
+    s = P["eps"] / (2.0 * np.pi * P["rc"]) * np.exp(0.5 * f)
+    u = P["u_inf"] * (np.cos(P["theta"]) - s * dy)
+    v = P["u_inf"] * (np.sin(P["theta"]) + s * dx)
+    base = 1.0 - P["eps"] ** 2 * (g - 1.0) * P["mach"] ** 2 / (8.0 * np.pi ** 2) * np.exp(f)
+    rho = P["rho_inf"] * base ** (1.0 / (g - 1.0))
+    p_inf = P["rho_inf"] * P["u_inf"] ** 2 / (g * P["mach"] ** 2)
+    p = p_inf * base ** (g / (g - 1.0))
+    E = p / ((g - 1.0) * rho) + 0.5 * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, rho * E], axis=-1)
