@@ -308,6 +308,51 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
                        tpp_gmres_result* result, void* stream);
 
 /*
+ * Coupled systems of conservation laws (Sec. 5.3, Sec. 5.6: the 2D Euler equations,
+ * n_c = 4 components rho, rho u, rho v, rho E with the flux of Eq. euler-flux),
+ * linearised around a DG state u0 given at the nodes.  The operator is the Jacobian
+ * system S = M - dt J of the DG discretisation with the local Lax-Friedrichs flux
+ * F^(u-, u+).n = 1/2 (F(u-) + F(u+)).n + 1/2 lam (u- - u+), lam = max(|v-.n| + c-,
+ * |v+.n| + c+) frozen at u0: volume coefficients A_x(u0), A_y(u0) (n_c x n_c per node),
+ * face coefficients 1/2 (A_n(u0-) + lam I) on the own trace and 1/2 (A_n(u0+) - lam I)
+ * on the neighbour's.  The preconditioners are the paper's "small" ones: the n_c
+ * diagonal n^2 x n^2 sub-blocks of every element block (no coupling between
+ * components), approximated by the rank-2 Kronecker sum (K_small) or inverted exactly
+ * (block Jacobi, J_small).  The coupled "full" Kronecker blocks (A_k of size
+ * n_c n) are not built.
+ *
+ * tpp_create_system returns an ordinary context whose elements are the (element,
+ * component) pairs e * n_c + c: vectors are [E][n_c][n^2], tpp_num_elem() is
+ * E * n_c, dg_apply_sumfact / dg_apply_sumfact_static apply the coupled S, gmres_solve
+ * solves with it, and tpp_build_factors / tpp_apply_inverse / tpp_build_block_jacobi
+ * / tpp_apply_block_jacobi act on the small blocks.  Features: TPP_FEAT_TWO_SIDED,
+ * TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16 (others: TPP_ERR_INVALID_ARG).  tpp_set_velocity
+ * must not be called on a system context (it would replace the small blocks only).
+ */
+#define TPP_FLUX_EULER 1
+typedef struct {
+  int32_t dim;              /* 2 */
+  int32_t n;                /* nodes per direction, 1..32 */
+  int64_t num_elem;         /* physical elements E */
+  int32_t nc;               /* components: 4 for TPP_FLUX_EULER */
+  int32_t flux;             /* TPP_FLUX_EULER */
+  double gamma;             /* ratio of specific heats, > 1 (1.4 in the paper) */
+  double h, dt;             /* element width (square elements), time step */
+  const double* state;      /* device [E][nc][n^2]: u0 in conserved variables at the nodes
+                               (read during tpp_create_system only) */
+  const int32_t* nbr;       /* [E][4] neighbour across faces -x, +x, -y, +y (-1: none), as in
+                               tpp_problem (read during tpp_create_system only) */
+} tpp_sys_problem;
+
+/* Workspace for a system context (0 if invalid).  max_restart >= 5. */
+size_t tpp_sys_workspace_bytes(const tpp_sys_problem* prob, int32_t max_restart,
+                               uint32_t features);
+/* As tpp_create; computes the linearisation coefficients from the state (synchronises
+ * `stream`).  The workspace must hold tpp_sys_workspace_bytes. */
+tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* prob, int32_t max_restart,
+                             uint32_t features, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Per-system batched GMRES over batches of isolated elements (an extension for
  * mixed-degree batches; each system is one element's diagonal block of Sec. 3.4,
  * S_e x = b with mass, volume and outflow face terms, solved by the

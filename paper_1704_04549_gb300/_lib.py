@@ -46,6 +46,16 @@ class BuildReport(C.Structure):
                 ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32)]
 
 
+TPP_FLUX_EULER = 1
+
+
+class SysProblem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("num_elem", C.c_int64),
+                ("nc", C.c_int32), ("flux", C.c_int32), ("gamma", C.c_double),
+                ("h", C.c_double), ("dt", C.c_double), ("state", C.c_void_p),
+                ("nbr", C.c_void_p)]
+
+
 class BatchOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
                 ("prec", C.c_int32), ("max_outer", C.c_int32), ("inner_rtol", C.c_double),
@@ -91,6 +101,9 @@ EXPORTS = {
                                        C.c_void_p]),
     "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                         C.c_void_p]),
+    "tpp_sys_workspace_bytes": (C.c_size_t, [C.POINTER(SysProblem), C.c_int32, C.c_uint32]),
+    "tpp_create_system": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(SysProblem), C.c_int32,
+                                    C.c_uint32, C.c_void_p, C.c_size_t, C.c_void_p]),
     "tpp_batch_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int32, C.POINTER(BatchOpts)]),
     "tpp_batch_gmres": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                   C.POINTER(BatchOpts), C.POINTER(BatchReport), C.c_void_p,

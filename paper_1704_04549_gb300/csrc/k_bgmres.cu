@@ -79,7 +79,8 @@ std::string plan_batch(tpp_ctx* const* ctxs, int32_t nctx, const double* const* 
     const tpp_ctx* c = ctxs[g];
     const std::string who = "context " + std::to_string(g) + ": ";
     if (!c) return who + "NULL";
-    if (!c->isolated) return who + "not isolated (every nbr entry must be -1)";
+    if (!c->isolated || c->sys_nc > 0)
+      return who + "not isolated (every nbr entry must be -1; no coupled system)";
     if (c->mu > c->n) return who + "over-integrated contexts are not supported";
     if (!two_sided(c)) return who + "needs TPP_FEAT_TWO_SIDED";
     if (c->dim == 2 ? c->n > 32 : c->n > 16) return who + "n above the limit (32 in 2D, 16 in 3D)";

@@ -439,6 +439,7 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
 
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s) {
+  if (c->sys_nc > 0) return launch_sys_apply(c, x, tr, y, skip, s, 1.0);
   if (c->mu > c->n) return launch_dg_apply_mu(c, x, tr, y, skip, s, 1.0);
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
@@ -449,6 +450,7 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
 // y = dt A x = -dt J x: the operator without its mass term (traces tr of x given)
 cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double* tr, double* y,
                                  cudaStream_t s) {
+  if (c->sys_nc > 0) return launch_sys_apply(c, x, tr, y, nullptr, s, 0.0);
   if (c->mu > c->n) return launch_dg_apply_mu(c, x, tr, y, nullptr, s, 0.0);
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),

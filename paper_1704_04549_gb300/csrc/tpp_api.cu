@@ -401,6 +401,10 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
 tpp_status tpp_set_velocity(tpp_ctx* c, const double* vel_nodes, const double* vel_face_normal,
                             double dt, void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
+  if (c->sys_nc > 0) {
+    set_error("tpp_set_velocity: a system context's coefficients come from tpp_create_system");
+    return TPP_ERR_INVALID_ARG;
+  }
   if (!vel_nodes || !vel_face_normal || !(dt >= 0.0) || !std::isfinite(dt)) {
     set_error("tpp_set_velocity: vel_nodes and vel_face_normal non-NULL, dt >= 0 and finite");
     return TPP_ERR_INVALID_ARG;

@@ -127,6 +127,11 @@ struct tpp_ctx {
   bool factors_built;
   bool bj_built;
   bool isolated;           // no neighbour coupling (every nbr entry -1): block-diagonal
+  // coupled system (k_system.cu): sys_nc components per physical element, the context's
+  // elements are the (element, component) pairs; 0 for a scalar problem
+  int32_t sys_nc = 0;
+  int64_t sys_E = 0;
+  size_t sys_cx = 0, sys_cy = 0, sys_fo = 0, sys_fn = 0, sys_nbr = 0;
   int32_t partial_blocks;  // number of CTAs of the reduction kernels
   cudaGraphExec_t gexec[64];   // use_graph: captured Arnoldi step groups, by first step
   int32_t gkernels[64];        // kernels in each (added to the launch count per replay)
@@ -152,6 +157,9 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
                           const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
+// coupled-system operator (k_system.cu); traces tr of x per (element, component) block
+cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
+                             const int32_t* skip, cudaStream_t s, double mass);
 // over-integration (mu > n, 2D; k_overint.cu)
 struct MuTables {        // the mu-point rule and the nodal basis at its points
   double x[TPP_MAX_MU], w[TPP_MAX_MU];

@@ -73,6 +73,49 @@ class Context:
         self.tpp_set_velocity(vel_nodes, vel_face_normal, dt, stream)
         return self
 
+    @classmethod
+    def euler_system(cls, n: int, nel, h: float, dt: float, state, gamma: float = 1.4,
+                     max_restart: int = 30, features: int = 0, device: str = "cuda:0",
+                     stream=None):
+        """The 2D Euler equations linearised around `state` (conserved variables at the
+        nodes, [E][4][n^2], E = nel[0] nel[1] on the periodic mesh of mesh.periodic_nbr):
+        the coupled operator with the small-block preconditioners (tpp_create_system).
+        Vectors are [E][4][n^2]; num_elem counts (element, component) pairs."""
+        from . import mesh
+        self = cls.__new__(cls)
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        self.batch_rhs = 0
+        self.nel = tuple(int(v) for v in nel)
+        self.dim, self.n, self.dt, self.h, self.nrhs, self.mu = 2, n, float(dt), float(h), 1, n
+        nb = torch.as_tensor(np.ascontiguousarray(mesh.periodic_nbr(self.nel), dtype=np.int32),
+                             device=self.device)
+        st = torch.as_tensor(np.ascontiguousarray(state, dtype=np.float64).reshape(-1),
+                             device=self.device) if not isinstance(state, torch.Tensor) \
+            else state.contiguous()
+        P = L.SysProblem()
+        P.dim, P.n, P.num_elem, P.nc, P.flux = 2, n, int(nb.shape[0]), 4, L.TPP_FLUX_EULER
+        P.gamma, P.h, P.dt = float(gamma), self.h, self.dt
+        P.state, P.nbr = _ptr(st), _ptr(nb)
+        nbytes = self.lib.tpp_sys_workspace_bytes(C.byref(P), max_restart, features)
+        if nbytes == 0:
+            raise L.TppError(1, "tpp_sys_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self._ws_ptr = (self.workspace.data_ptr() + 255) & ~255
+        self.ws_bytes, self.max_restart, self.features = nbytes, max_restart, features
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.tpp_create_system(C.byref(ctx), C.byref(P), max_restart, features,
+                                               C.c_void_p(self._ws_ptr), nbytes,
+                                               _stream(stream)), "tpp_create_system")
+        self._ctx = ctx
+        self.num_dofs = int(self.lib.tpp_num_dofs(ctx))
+        self.num_elem = int(self.lib.tpp_num_elem(ctx))
+        return self
+
     def _create(self, dim, n, nbr, nrhs, h, dt, max_restart, features, device, stream, mu=0):
         if not torch.cuda.is_available():
             raise RuntimeError("libtpp needs a CUDA device; there is no CPU path")

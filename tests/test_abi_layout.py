@@ -17,6 +17,7 @@ STRUCTS = {
     "tpp_build_report": "BuildReport",
     "tpp_views": "Views",
     "tpp_batch_opts": "BatchOpts",
+    "tpp_sys_problem": "SysProblem",
     "tpp_batch_report": "BatchReport",
     "tpp_time_report": "TimeReport",
 }

@@ -1,0 +1,130 @@
+"""GPU parity: the coupled 2D Euler system linearised around the vortex of Sec. 5.3
+(tpp_create_system) against the oracle's assembled system (oracle/systems.py): the
+coupled operator, the small-block Kronecker factors and their apply, exact small-block
+Jacobi, and GMRES with both small-block preconditioners."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import synthetic
+from oracle.gmres import gmres
+from oracle.ksvd import kron_sum, ksvd_2d
+from oracle.precond import apply_dense
+from oracle.systems import vortex_system
+from paper_1704_04549_gb300 import (TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_TWO_SIDED,
+                                    TPP_PC_BLOCK_JACOBI, TPP_PC_KRON)
+from tests.gpu_util import DEV, FP64_TOL, rel, solve_tol, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(n, nel, h):
+    """Vortex state at the Gauss-Legendre nodes, [E][4][n^2] (x fastest, element index
+    x fastest), from the input generator."""
+    xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    E = nel[0] * nel[1]
+    out = np.empty((E, 4, n * n))
+    for e in range(E):
+        cx, cy = e % nel[0], e // nel[0]
+        X = np.stack(np.meshgrid((cx + xg) * h, (cy + xg) * h, indexing="xy"), -1).reshape(-1, 2)
+        out[e] = synthetic.euler_vortex_state(X).T
+    return out
+
+
+def _pair(n, nel, h, dt, features=0):
+    from paper_1704_04549_gb300 import Context
+    U0 = _state(n, nel, h)
+    ora = vortex_system(nel, h, n, dt, synthetic.euler_vortex_state)
+    ora.U0 = U0
+    ctx = Context.euler_system(n, nel, h, dt, U0, features=features, device=DEV)
+    return ctx, ora
+
+
+CASES = [(2, (3, 2), 5.0), (4, (4, 3), 2.5), (8, (4, 4), 2.5), (16, (2, 2), 5.0),
+         (31, (2, 1), 5.0)]
+
+
+@pytest.mark.parametrize("n,nel,h", CASES)
+def test_coupled_operator_matches_oracle(n, nel, h):
+    ctx, ora = _pair(n, nel, h, 0.1)
+    S = ora.global_matrix()
+    x = synthetic.rhs(7, ora.ndof)
+    y = to_host(ctx.dg_apply_sumfact(to_dev(x)))
+    assert rel(y, S @ x) <= FP64_TOL, rel(y, S @ x)
+    if n <= 16:
+        ys = to_host(ctx.dg_apply_sumfact_static(to_dev(x)))
+        assert rel(ys, S @ x) <= FP64_TOL
+
+
+@pytest.mark.parametrize("n,nel,h", CASES[:4])
+@pytest.mark.parametrize("form", ["one-sided", "two-sided"])
+def test_small_block_factors_apply_and_jacobi(n, nel, h, form):
+    feats = TPP_FEAT_BLOCK_JACOBI | (TPP_FEAT_TWO_SIDED if form == "two-sided" else 0)
+    ctx, ora = _pair(n, nel, h, 0.1, features=feats)
+    rep = ctx.tpp_build_factors()
+    assert rep["num_schur_fail"] == 0
+    ctx.tpp_build_block_jacobi()
+    v = ctx.views()
+    sig = to_host(v["sigma"])
+    A1, B1, A2, B2 = (to_host(v[k]) for k in ("A1", "B1", "A2", "B2"))
+    cpair = to_host(v["cond"])
+    b = synthetic.rhs(9, ora.ndof)
+    xk = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    xj = to_host(ctx.tpp_apply_block_jacobi(to_dev(b)))
+    nl = ora.nloc
+    for e in range(ora.mesh.num_elem):
+        for c in range(4):
+            k = e * 4 + c
+            Ssm = ora.small_block(e, c)
+            s_ref, As, Bs = ksvd_2d(Ssm, n)
+            P_ref = kron_sum(As, Bs)
+            assert abs(sig[k, 0] - s_ref[0]) <= FP64_TOL * s_ref[0]
+            P = np.kron(A1[k], B1[k]) + np.kron(A2[k], B2[k])
+            assert rel(P, P_ref) <= FP64_TOL, (e, c, rel(P, P_ref))
+            blk = slice(k * nl, (k + 1) * nl)
+            err = rel(xk[blk], apply_dense(P_ref, b[blk]))
+            assert err <= solve_tol(np.linalg.cond(P_ref), cpair[k]), (e, c, err)
+            assert rel(xj[blk], np.linalg.solve(Ssm, b[blk])) <= FP64_TOL * np.linalg.cond(Ssm)
+
+
+def _oracle_precond(ora, kind):
+    nl, inv = ora.nloc, []
+    for e in range(ora.mesh.num_elem):
+        for c in range(4):
+            Ssm = ora.small_block(e, c)
+            if kind == "K":
+                _, As, Bs = ksvd_2d(Ssm, ora.n)
+                inv.append(np.linalg.inv(kron_sum(As, Bs)))
+            else:
+                inv.append(np.linalg.inv(Ssm))
+
+    def apply(v):
+        out = np.empty_like(v)
+        for k, Pi in enumerate(inv):
+            out[k * nl:(k + 1) * nl] = Pi @ v[k * nl:(k + 1) * nl]
+        return out
+    return apply
+
+
+@pytest.mark.parametrize("n,nel,h,dt", [(4, (4, 3), 2.5, 0.1), (8, (4, 4), 2.5, 0.1),
+                                         (8, (4, 4), 2.5, 0.01), (12, (3, 3), 2.5, 0.1)])
+def test_gmres_with_small_block_preconditioners(n, nel, h, dt):
+    ctx, ora = _pair(n, nel, h, dt, features=TPP_FEAT_BLOCK_JACOBI)
+    ctx.tpp_build_factors()
+    ctx.tpp_build_block_jacobi()
+    S = ora.global_matrix()
+    b = synthetic.rhs(11, ora.ndof)
+    xs = spla.spsolve(S.tocsc(), b)
+    its = {}
+    for kind, pc in (("K", TPP_PC_KRON), ("J", TPP_PC_BLOCK_JACOBI)):
+        x_ref, o = gmres(lambda v: S @ v, b, M=_oracle_precond(ora, kind), rtol=1e-8)
+        assert o["converged"]
+        x, r = ctx.gmres_solve(to_dev(b), pc=pc, rtol=1e-8)
+        assert r["converged"] and r["true_rel_res"] <= 1e-8
+        xh = to_host(x)
+        assert np.linalg.norm(b - S @ xh) <= 1.0001e-8 * np.linalg.norm(b)
+        assert abs(r["iters"] - o["iters"]) <= 1, (kind, r["iters"], o["iters"])
+        assert rel(xh, xs) <= 1e-6
+        its[kind] = (r["iters"], o["iters"])
+    print(f"Euler vortex n={n} dt={dt}: GMRES(30) iterations (GPU, oracle) K_small {its['K']}, "
+          f"J_small {its['J']}")
