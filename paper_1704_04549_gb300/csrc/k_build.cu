@@ -869,7 +869,7 @@ __device__ int sturm_count_gk(const double* e2, int m, double x) {
   return cnt;
 }
 
-__global__ void __launch_bounds__(128) k_ksvd_tri(KsvdArgs A) {
+__global__ void __launch_bounds__(32) k_ksvd_tri(KsvdArgs A) {
   const int n = A.n, rz = A.rz, r = n + rz;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t e = t >> 1;
@@ -1948,7 +1948,9 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
     k_ksvd_w<<<(unsigned)((E + warps - 1) / warps), warps * 32, smem, s>>>(ka);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    k_ksvd_tri<<<(unsigned)((2 * E + 127) / 128), 128, 0, s>>>(ka);
+    // one thread per (element, k): 32-thread CTAs spread the 2 E sequential problems over
+    // every SM (the FP64 pipe of an SM, not its warp count, bounds this kernel)
+    k_ksvd_tri<<<(unsigned)((2 * E + 31) / 32), 32, 0, s>>>(ka);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_ksvd_vec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
