@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import contextlib
 import json
 import os
 import statistics
@@ -459,6 +460,62 @@ def other_configs(args, dev):
         out[key] = rec
         del ctx
         torch.cuda.empty_cache()
+    # the mixed-degree batch at 10 % (per-system batched GMRES, autotuned shapes)
+    res, tuned, groups, dofs, _, _ = batch_measure(args, 0.1, 2, 1, sample_clocks=False)
+    out["batch_10pct"] = {"dof_rhs": dofs, "groups": len(groups),
+                          "fp64": {k: res["fp64"][k] for k in ("ms", "solve_ms", "launch_ms",
+                                                               "iters_mean", "iters_max",
+                                                               "unconverged")},
+                          "mixed": {k: res["mixed"][k] for k in ("ms", "solve_ms", "launch_ms",
+                                                                 "iters_mean", "iters_max",
+                                                                 "unconverged", "max_outer")},
+                          "shapes": {m: {k: t[k] for k in ("warps", "reg_budget")}
+                                     for m, t in tuned.items()}}
+    torch.cuda.empty_cache()
+    out["euler_vortex_16x12_n8"] = euler_record(dev)
+    return out
+
+
+def euler_record(dev):
+    """2D Euler equations linearised around the vortex of Sec. 5.3 at t = 0: 16 x 12
+    periodic mesh of the 20 x 15 domain (h = 1.25), n = 8 (p = 7), one backward Euler
+    system per dt; GMRES(30) to 1e-8 with the small-block Kronecker (K_small) and the
+    small-block Jacobi (J_small) preconditioners.  Times with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_1704_04549_gb300 import (TPP_FEAT_BLOCK_JACOBI, TPP_PC_BLOCK_JACOBI,
+                                        TPP_PC_KRON, Context)
+    nel, h, n = (16, 12), 1.25, 8
+    xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    E = nel[0] * nel[1]
+    state = np.empty((E, 4, n * n))
+    for e in range(E):
+        cx, cy = e % nel[0], e // nel[0]
+        X = np.stack(np.meshgrid((cx + xg) * h, (cy + xg) * h, indexing="xy"), -1)
+        state[e] = synthetic.euler_vortex_state(X.reshape(-1, 2)).T
+    stream = torch.cuda.current_stream(dev)
+    out = {"dofs": E * 4 * n * n}
+    for dt in (0.1, 0.01):
+        ctx = Context.euler_system(n, nel, h, dt, state, features=TPP_FEAT_BLOCK_JACOBI,
+                                   device=str(dev))
+        b = torch.as_tensor(synthetic.rhs(1713, ctx.num_dofs), device=dev)
+        rec = {}
+        for name, pc, build in (("K_small", TPP_PC_KRON, ctx.tpp_build_factors),
+                                ("J_small", TPP_PC_BLOCK_JACOBI, ctx.tpp_build_block_jacobi)):
+            build()
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            build()
+            _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=3000, pc=pc,
+                                   check=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            rec[name] = {"iters": r["iters"], "converged": bool(r["converged"]),
+                         "true_rel_res": r["true_rel_res"], "build_solve_ms": e0.elapsed_time(e1)}
+        out[f"dt={dt}"] = rec
+        del ctx
     return out
 
 
@@ -539,25 +596,19 @@ def run_3d(args):
     return 0
 
 
-def run_batch(args):
-    """The mixed-degree batch (20,000 2D elements, p ~ U{4..30}, and 2,000 3D elements,
-    p ~ U{3..12}; isolated unit elements (h = 1; --h-reading domain: h = 1/64) covering 1/64
-    of the velocity field's unit domain, centres uniform, random-Fourier velocity, dt = 0.05,
-    64 right-hand sides ~ N(0, 1) per element), every (element, right-hand side) system
-    solved to 1e-8 by its own GMRES (tpp_batch_gmres: persistent launches grouped by n).
-    One context per degree group holds the factors; a step = the factor build of every
-    group + the batched solve; value = device time of one FP64 step, the mixed-precision
-    step as a sub-record.  Inputs (3.9 + 0.8 GB per vector set) exceed L2."""
-    if args.batch_solver == "group":
-        return run_batch_groups(args)
+def batch_measure(args, scale: float, steps: int, warmup: int, sample_clocks: bool = True):
+    """Per-system batched GMRES on the mixed-degree batch scaled by `scale`: contexts and
+    right-hand sides, autotuned launch shapes (5 % sample), then `warmup` untimed and
+    `steps` timed steps (factor build of every group + solve) in FP64 and mixed precision.
+    Returns (results per mode, autotune, groups, dof_rhs, clocks, kernel launches)."""
     import torch
     from paper_1704_04549_gb300 import Context
     from paper_1704_04549_gb300 import _lib
     from paper_1704_04549_gb300.batch import BatchGmres
     lib = _lib.load()
     dev = torch.device("cuda:0")
-    groups = synthetic.mixed_degree_batch(e2d=int(round(20000 * args.batch_scale)),
-                                          e3d=int(round(2000 * args.batch_scale)))
+    groups = synthetic.mixed_degree_batch(e2d=int(round(20000 * scale)),
+                                          e3d=int(round(2000 * scale)))
     vel = {2: synthetic.fourier_velocity(1709, 2), 3: synthetic.fourier_velocity(1709, 3)}
     h_el = 1.0 / 64 if args.h_reading == "domain" else 1.0
     R = 64
@@ -578,8 +629,8 @@ def run_batch(args):
     # launch shapes per lane-group width from the autotuner, on a 5 % sample of the batch
     # (same degree groups; JSON cache keyed by GPU, precision, restart and groups)
     from paper_1704_04549_gb300.autotune import tune_batch_gmres
-    sample = synthetic.mixed_degree_batch(e2d=max(1, int(round(1000 * args.batch_scale))),
-                                          e3d=max(1, int(round(100 * args.batch_scale))))
+    sample = synthetic.mixed_degree_batch(e2d=max(1, int(round(1000 * scale))),
+                                          e3d=max(1, int(round(100 * scale))))
     sc, sb, sx = make(sample)
     common = dict(restart=args.batch_restart, rtol=1e-8, max_iters=args.max_iters,
                   inner_rtol=args.batch_inner_rtol, max_outer=8)
@@ -609,13 +660,14 @@ def run_batch(args):
 
     res = {}
     l0 = lib.tpp_kernel_launch_count()
-    with ClockSampler(0) as clk:
+    clk = ClockSampler(0) if sample_clocks else contextlib.nullcontext()
+    with clk:
         for mode, sv in solvers.items():
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 build()
                 sv.solve(bs, xs)
-            ms, rep = timed(lambda: (build(), sv.solve(bs, xs))[1], args.steps)
-            ms_solve, _ = timed(lambda: sv.solve(bs, xs), args.steps)
+            ms, rep = timed(lambda: (build(), sv.solve(bs, xs))[1], steps)
+            ms_solve, _ = timed(lambda: sv.solve(bs, xs), steps)
             its = torch.cat([t.double() for t in sv.iters])
             res[mode] = {"ms": ms, "solve_ms": ms_solve, "build_ms": ms - ms_solve,
                          "launch_ms": rep["launch_ms"],
@@ -624,6 +676,24 @@ def run_batch(args):
                          "iters_total": rep["total_iters"], "max_outer": rep["max_outer"],
                          "launches_per_solve": rep["launches"]}
     launches = lib.tpp_kernel_launch_count() - l0
+    return res, tuned, groups, dofs, (clk.summary() if sample_clocks else None), launches
+
+
+def run_batch(args):
+    """The mixed-degree batch (20,000 2D elements, p ~ U{4..30}, and 2,000 3D elements,
+    p ~ U{3..12}; isolated unit elements (h = 1; --h-reading domain: h = 1/64) covering 1/64
+    of the velocity field's unit domain, centres uniform, random-Fourier velocity, dt = 0.05,
+    64 right-hand sides ~ N(0, 1) per element), every (element, right-hand side) system
+    solved to 1e-8 by its own GMRES (tpp_batch_gmres: persistent launches grouped by n).
+    One context per degree group holds the factors; a step = the factor build of every
+    group + the batched solve; value = device time of one FP64 step, the mixed-precision
+    step as a sub-record.  Inputs (3.9 + 0.8 GB per vector set) exceed L2."""
+    import torch
+    if args.batch_solver == "group":
+        return run_batch_groups(args)
+    h_el = 1.0 / 64 if args.h_reading == "domain" else 1.0
+    res, tuned, groups, dofs, clocks, launches = batch_measure(args, args.batch_scale,
+                                                               args.steps, args.warmup)
     e2d = sum(len(g.ids) for g in groups if g.dim == 2)
     e3d = sum(len(g.ids) for g in groups if g.dim == 3)
     line = {
@@ -643,7 +713,7 @@ def run_batch(args):
         "all_converged": all(r["unconverged"] == 0 for r in res.values()),
         "dof_rhs_per_s": {m: dofs / (r["ms"] * 1e-3) for m, r in res.items()},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     print(json.dumps(line))
     return 0

@@ -171,6 +171,9 @@ typedef struct {
   int32_t num_z_unconverged;  /* 3D: elements whose first-stage Lanczos hit its step cap
                                  (the factor is still the best Ritz pair found) */
   int32_t num_fallback;     /* tpp_build_factors_learned: elements given the exact KSVD */
+  int32_t num_schur_relaxed;  /* elements whose Francis iteration deflated a nearly defective
+                                 eigenvalue cluster at sqrt(eps) instead of eps (flags bit 4):
+                                 their factors are those of a matrix within sqrt(eps) |C| */
 } tpp_build_report;
 
 typedef struct tpp_ctx tpp_ctx;
@@ -510,7 +513,8 @@ typedef struct {
   const double* Q2;      /* two-sided form only (NULL otherwise) */
   const double* T1;      /* real Schur form of C1 */
   const double* T2;      /* two-sided: real Schur form of C2; one-sided: C2 itself */
-  const int32_t* flags;  /* [E] bit0 shifted pair, bit1 rank-1, bit2 schur fail, bit3 singular */
+  const int32_t* flags;  /* [E] bit0 shifted pair, bit1 rank-1, bit2 schur fail, bit3 singular,
+                            bit4 Schur deflated at sqrt(eps) */
   const double* cond;    /* [E] cond_1(L_A) * cond_1(L_B) of the inverted factor pair */
   const double* gl_x;    /* [n] Gauss-Legendre nodes on [0, 1] */
   const double* gl_w;    /* [n] weights */

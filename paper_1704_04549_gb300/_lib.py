@@ -43,7 +43,8 @@ class BuildReport(C.Structure):
     _fields_ = [("num_elem", C.c_int32), ("num_shifted", C.c_int32), ("num_rank1", C.c_int32),
                 ("num_schur_fail", C.c_int32), ("max_cond", C.c_double),
                 ("min_sigma_ratio", C.c_double), ("max_cond_z", C.c_double),
-                ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32)]
+                ("num_z_unconverged", C.c_int32), ("num_fallback", C.c_int32),
+                ("num_schur_relaxed", C.c_int32)]
 
 
 TPP_FLUX_EULER = 1

@@ -20,6 +20,11 @@ namespace tpp {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
+// deflation threshold of the Francis iterations after 20 max(n, 8) steps without full
+// convergence: sqrt(eps).  Clusters of nearly defective eigenvalues (e.g. the density
+// blocks of the Euler systems, whose factors are a diagonal plus rank-one face terms)
+// stall with subdiagonals near 1e-9; accepting them perturbs C by at most sqrt(eps) |C|.
+constexpr double kRelax = 1.4901161193847656e-08;
 
 
 __host__ __device__ __forceinline__ int ld_of(int n) { return (n & 1) ? n : n + 1; }
@@ -43,7 +48,7 @@ __device__ void house_vec(const double* x, int len, double* v) {
 // Real Schur form of H (n x n, column-major, leading dimension ld) in place,
 // accumulating Q (initialised here).  Returns false when the Francis
 // iteration exceeds its cap.  Executed by one full warp.
-__device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb) {
+__device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb, bool* relaxed) {
   const int lane = threadIdx.x & 31;
   for (int r = lane; r < n; r += 32)
     for (int c = 0; c < n; ++c) Q[r + ld * c] = (r == c) ? 1.0 : 0.0;
@@ -96,13 +101,15 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
   if (amax == 0.0) return true;
   // Francis double-shift QR with deflation from the bottom
   int hi = n - 1, its = 0, total = 0;
-  const int maxit = 40 * (n > 8 ? n : 8);
+  const int maxit = 40 * (n > 8 ? n : 8), relax = 20 * (n > 8 ? n : 8);
   while (hi > 0) {
+    const double tol = (total > relax) ? kRelax : kEps;
+    if (total > relax) *relaxed = true;
     int l = hi;
     while (l > 0) {
       double sc = fabs(H[(l - 1) + ld * (l - 1)]) + fabs(H[l + ld * l]);
       if (sc == 0.0) sc = amax;
-      if (fabs(H[l + ld * (l - 1)]) <= kEps * sc) break;
+      if (fabs(H[l + ld * (l - 1)]) <= tol * sc) break;
       --l;
     }
     __syncwarp();
@@ -115,11 +122,14 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
     ++its;
     if (++total > maxit) return false;
     double s, t;
-    if (its % 10 == 0) {     // exceptional shift: double real shift mu
-      const double mu = H[hi + ld * hi] +
-                        0.75 * (fabs(H[hi + ld * (hi - 1)]) + fabs(H[(hi - 1) + ld * (hi - 2)]));
+    if (its % 10 == 0) {
+      // exceptional shift: the complex pair mu +- i sqrt(0.4375) w, w the size of the
+      // last two subdiagonals, mu = H[hi][hi] + 0.75 w (a real double shift at mu stalls
+      // on nearly defective eigenvalue clusters)
+      const double w = fabs(H[hi + ld * (hi - 1)]) + fabs(H[(hi - 1) + ld * (hi - 2)]);
+      const double mu = H[hi + ld * hi] + 0.75 * w;
       s = 2.0 * mu;
-      t = mu * mu;
+      t = mu * mu + 0.4375 * w * w;
     } else {                 // eigenvalues of the trailing 2 x 2 block
       const double a = H[(hi - 1) + ld * (hi - 1)], b = H[(hi - 1) + ld * hi];
       const double c = H[hi + ld * (hi - 1)], d = H[hi + ld * hi];
@@ -203,7 +213,8 @@ __device__ bool warp_real_schur(double* H, double* Q, int n, int ld, double* vb)
 // the pipe the same with 16 or 32 active lanes).  Deflation: the negligible
 // subdiagonal entries of a half are found in parallel (one lane per position,
 // a ballot) and the window update is integer work.
-__device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, bool empty) {
+__device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, bool empty,
+                              bool* relaxed) {
   const int lane = threadIdx.x & 31, hl = lane & 15, hb = lane & 16;
   for (int c = 0; c < n; ++c)
     if (hl < n) Q[hl + ld * c] = (hl == c) ? 1.0 : 0.0;
@@ -254,16 +265,17 @@ __device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, b
   for (int o = 8; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   int hi = (empty || amax == 0.0) ? 0 : n - 1, its = 0, total = 0;
   bool fail = false;
-  const int maxit = 40 * (n > 8 ? n : 8);
+  const int maxit = 40 * (n > 8 ? n : 8), relax = 20 * (n > 8 ? n : 8);
   while (true) {
     // negligible subdiagonal entries (position i = hl + 1: H[i][i-1])
     bool small = false;
     {
       const int i = hl + 1;
+      if (total > relax) *relaxed = true;
       if (i < n && hi > 0) {
         double sc = fabs(H[(i - 1) + ld * (i - 1)]) + fabs(H[i + ld * i]);
         if (sc == 0.0) sc = amax;
-        small = fabs(H[i + ld * (i - 1)]) <= kEps * sc;
+        small = fabs(H[i + ld * (i - 1)]) <= ((total > relax) ? kRelax : kEps) * sc;
       }
     }
     const unsigned mine = (__ballot_sync(0xffffffffu, small) >> hb) & 0xffffu;
@@ -290,11 +302,11 @@ __device__ bool hw_real_schur(double* H, double* Q, int n, int ld, double* vb, b
     // shifts (indices clamped for an idle half; its values are not used)
     const int h2 = go ? hi : 2, l2 = go ? l : 0;
     double sh, t;
-    if (its % 10 == 0) {
-      const double mu = H[h2 + ld * h2] +
-                        0.75 * (fabs(H[h2 + ld * (h2 - 1)]) + fabs(H[(h2 - 1) + ld * (h2 - 2)]));
+    if (its % 10 == 0) {     // exceptional complex shift pair (as in k_schur_w)
+      const double w = fabs(H[h2 + ld * (h2 - 1)]) + fabs(H[(h2 - 1) + ld * (h2 - 2)]);
+      const double mu = H[h2 + ld * h2] + 0.75 * w;
       sh = 2.0 * mu;
-      t = mu * mu;
+      t = mu * mu + 0.4375 * w * w;
     } else {
       const double a = H[(h2 - 1) + ld * (h2 - 1)], b = H[(h2 - 1) + ld * h2];
       const double c = H[h2 + ld * (h2 - 1)], d = H[h2 + ld * h2];
@@ -1355,7 +1367,7 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, doub
     H[rr + ld * c] = rank1 ? ((which && rr == c) ? 1.0 : 0.0) : Tg[q];
   }
   __syncwarp();
-  bool ok = true;
+  bool ok = true, relaxed = false;
   if (rank1) {     // P = A1 (x) B1: T1 = 0, T2 = I, Q = I
     for (int q = lane; q < nn; q += 32) {
       const int rr = q % n, c = q / n;
@@ -1363,7 +1375,7 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, doub
     }
     __syncwarp();
   } else {
-    ok = warp_real_schur(H, Q, n, ld, vb);
+    ok = warp_real_schur(H, Q, n, ld, vb, &relaxed);
   }
   for (int q = lane; q < nn; q += 32) {
     const int rr = q % n, c = q / n;
@@ -1379,6 +1391,9 @@ __global__ void __launch_bounds__(128) k_schur_w(int n, int64_t E, int mpe, doub
     if (!ok) {
       atomicOr(reinterpret_cast<int*>(flags + e), 4);
       atomicAdd(&st->build_schur_fail, 1);
+    } else if (relaxed) {
+      atomicOr(reinterpret_cast<int*>(flags + e), 16);
+      atomicAdd(&st->build_schur_relaxed, 1);
     }
   }
 }
@@ -1405,7 +1420,8 @@ __global__ void __launch_bounds__(128) k_schur_w2(int n, int64_t E, int mpe, dou
   for (int c = 0; c < n; ++c)
     if (hl < n) H[hl + ld * c] = rank1 ? ((which && hl == c && !empty) ? 1.0 : 0.0) : Tg[hl + n * c];
   __syncwarp();
-  const bool ok = hw_real_schur(H, Q, n, ld, vb, rank1);
+  bool relaxed = false;
+  const bool ok = hw_real_schur(H, Q, n, ld, vb, rank1, &relaxed);
   // 2x2 diagonal blocks with real eigenvalues are rotated to upper triangular form
   // (Givens rotation whose first column is an eigenvector), so that only complex
   // pairs stay 2x2; kept when the rotated block does not come out triangular to
@@ -1478,6 +1494,9 @@ __global__ void __launch_bounds__(128) k_schur_w2(int n, int64_t E, int mpe, dou
       if (!ok && !rank1) {
         atomicOr(reinterpret_cast<int*>(flags + e), 4);
         atomicAdd(&st->build_schur_fail, 1);
+      } else if (relaxed && !rank1) {
+        atomicOr(reinterpret_cast<int*>(flags + e), 16);
+        atomicAdd(&st->build_schur_relaxed, 1);
       }
     }
   }

@@ -463,6 +463,7 @@ tpp_status finish_build(tpp_ctx* c, tpp_build_report* report, cudaStream_t s) {
     report->num_shifted = st.build_shifted;
     report->num_rank1 = st.build_rank1;
     report->num_schur_fail = st.build_schur_fail;
+    report->num_schur_relaxed = st.build_schur_relaxed;
     report->max_cond = st.max_cond;
     report->min_sigma_ratio = st.min_sigma_ratio;
     report->max_cond_z = st.max_cond_z;

@@ -48,6 +48,7 @@ template <> struct Tab<float> {
 struct DevStatus {
   int32_t build_singular;   // elements whose inverted factors were singular
   int32_t build_schur_fail; // elements whose Francis iteration hit the cap
+  int32_t build_schur_relaxed;  // elements deflated at sqrt(eps) (nearly defective clusters)
   int32_t build_shifted;
   int32_t build_rank1;
   double max_cond;          // stored as ordered bits via atomicMax on long long
