@@ -259,3 +259,26 @@ def euler_vortex_state(X: np.ndarray, params: dict = VORTEX) -> np.ndarray:
     p = p_inf * base ** (g / (g - 1.0))
     E = p / ((g - 1.0) * rho) + 0.5 * (u * u + v * v)
     return np.stack([rho, rho * u, rho * v, rho * E], axis=-1)
+
+
+# ---------------------------------------------------------------------------
+# Curved (non-affine) elements: a smooth periodic warp of the periodic square of side L,
+#   Phi(X) = X + alpha L sin(2 pi X / L) sin(2 pi Y / L) (1, 1),
+# a bijection of the torus onto itself for 2 pi alpha < 1 (det grad Phi =
+# 1 + 2 pi alpha sin(2 pi (X + Y) / L) > 0).  Elements are the images of the
+# Cartesian cells: x = Phi((c + xi) h).
+def periodic_warp(X: np.ndarray, L: float, alpha: float = 0.05):
+    """(x = Phi(X) [..., 2], grad Phi [..., 2, 2] with [..., i, j] = d x_i / d X_j)."""
+    X = np.asarray(X, dtype=np.float64)
+    k = 2.0 * np.pi / L
+    sx, sy = np.sin(k * X[..., 0]), np.sin(k * X[..., 1])
+    cx, cy = np.cos(k * X[..., 0]), np.cos(k * X[..., 1])
+    p = alpha * L * sx * sy
+    x = np.stack([X[..., 0] + p, X[..., 1] + p], axis=-1)
+    dpx, dpy = alpha * L * k * cx * sy, alpha * L * k * sx * cy
+    G = np.empty(X.shape[:-1] + (2, 2))
+    G[..., 0, 0] = 1.0 + dpx
+    G[..., 0, 1] = dpy
+    G[..., 1, 0] = dpx
+    G[..., 1, 1] = 1.0 + dpy
+    return x, G
