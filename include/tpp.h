@@ -311,6 +311,27 @@ tpp_status gmres_solve(tpp_ctx* ctx, const double* b, double* x, const tpp_gmres
                        tpp_gmres_result* result, void* stream);
 
 /*
+ * Curved (non-affine) 2D elements: the general-geometry form of Sec. 3.2 (Eq. mass-kron,
+ * adv-kron with a full element Jacobian J_T = dx/dxi at every quadrature point; the
+ * paper's unstructured and curved meshes of Sec. 5.1).  The caller gives, at the
+ * quadrature points of the context's rule (the n nodes, or the mu-point rule when
+ * over-integrated; tpp_gauss_legendre), the metric terms folded with the velocity:
+ *   jdet      device [E][q^2]      |J_T|                       (point a + q b, x fastest)
+ *   flux      device [2][E][q^2]   F~ = |J_T| J_T^-1 a          (contravariant velocity)
+ *   flux_face device [E][4][q]     a . (|J_T| J_T^-T N^)         (own side of faces -x, +x,
+ *                                  -y, +y; N^ the reference outward normal)
+ * For an affine element of width h these are h^2, h a and h a . n.  The mass becomes
+ * w |J_T| point by point (applied through the mu-point rule when over-integrated), and
+ * the factor build, block Jacobi and time integration use it.  Replaces the
+ * coefficients of tpp_set_velocity (which returns the context to affine elements);
+ * the factors must be rebuilt.  2D scalar contexts without TPP_FEAT_LEARNED
+ * (TPP_ERR_UNSUPPORTED otherwise); not accepted by tpp_batch_gmres.  Synchronises
+ * `stream`.
+ */
+tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* flux,
+                                const double* flux_face, double dt, void* stream);
+
+/*
  * Coupled systems of conservation laws (Sec. 5.3, Sec. 5.6: the 2D Euler equations,
  * n_c = 4 components rho, rho u, rho v, rho E with the flux of Eq. euler-flux),
  * linearised around a DG state u0 given at the nodes.  The operator is the Jacobian

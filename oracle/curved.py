@@ -19,11 +19,13 @@ a face point is computed from the element that owns the face as its lower face, 
 the two sides of a face see s and -s exactly.  The velocity is a(x / L) with the
 field of oracle/dg.py (periodic on the square).
 
-Pinned in tests/test_oracle_curved.py: the identity map reproduces oracle/dg.py,
-discrete conservation 1^T (S - M) = 0 for the warped map, the mass of the whole
-domain equals the area L^2 (the warp preserves area) to quadrature accuracy, and the
-operator applied to the nodal interpolant of a smooth function u converges to the
-exact M u + dt [div(a u)] weak form as n grows.
+Pinned in tests/test_oracle_curved.py: the identity map reproduces oracle/dg.py
+(collocated and over-integrated), the warp's gradient against finite differences,
+discrete conservation 1^T (S - M) = 0 for the warped map, opposite scaled normal
+velocities on the two sides of every face, the mass of the whole domain equal to the
+area L^2 and a single element's area converging spectrally, and the free-stream
+identity (constant velocity, u = 1: volume and face terms cancel by the divergence
+theorem) reached as the quadrature is refined.
 """
 from __future__ import annotations
 
@@ -42,6 +44,7 @@ class CurvedAdvectionDG:
     def __init__(self, mesh: PeriodicMesh, n: int, dt: float, vel, warp, mu: int | None = None):
         assert mesh.dim == 2
         self.mesh, self.n, self.dt, self.vel, self.warp = mesh, n, float(dt), vel, warp
+        self.dim = 2
         self.basis = Basis1D(n, mu)
         self.mu = self.basis.mu
         self.L = mesh.nel[0] * mesh.h

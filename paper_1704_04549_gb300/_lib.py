@@ -102,6 +102,8 @@ EXPORTS = {
                                        C.c_void_p]),
     "tpp_apply_inverse_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                         C.c_void_p]),
+    "tpp_set_metric_terms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_double, C.c_void_p]),
     "tpp_sys_workspace_bytes": (C.c_size_t, [C.POINTER(SysProblem), C.c_int32, C.c_uint32]),
     "tpp_create_system": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(SysProblem), C.c_int32,
                                     C.c_uint32, C.c_void_p, C.c_size_t, C.c_void_p]),

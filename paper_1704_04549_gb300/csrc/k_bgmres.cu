@@ -81,7 +81,8 @@ std::string plan_batch(tpp_ctx* const* ctxs, int32_t nctx, const double* const* 
     if (!c) return who + "NULL";
     if (!c->isolated || c->sys_nc > 0)
       return who + "not isolated (every nbr entry must be -1; no coupled system)";
-    if (c->mu > c->n) return who + "over-integrated contexts are not supported";
+    if (c->mu > c->n || c->curved)
+      return who + "over-integrated and curved contexts are not supported";
     if (!two_sided(c)) return who + "needs TPP_FEAT_TWO_SIDED";
     if (c->dim == 2 ? c->n > 32 : c->n > 16) return who + "n above the limit (32 in 2D, 16 in 3D)";
     if (mixed && !(c->features & TPP_FEAT_MIXED)) return who + "mixed precision needs TPP_FEAT_MIXED";

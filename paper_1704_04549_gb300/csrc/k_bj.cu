@@ -14,7 +14,8 @@
 namespace tpp {
 
 __global__ void k_bj_assemble_2d(const Tables* T, int n, double h, const double* cx,
-                                 const double* cy, const double* fa, double* LU) {
+                                 const double* cy, const double* fa, double* LU,
+                                 const double* mq) {
   const int nn = n * n;
   const int64_t e = blockIdx.x;
   const double* fe = fa + e * 4 * n;          // outward normal velocities, faces -x, +x, -y, +y
@@ -23,7 +24,7 @@ __global__ void k_bj_assemble_2d(const Tables* T, int n, double h, const double*
     const int row = q / nn, col = q % nn;
     const int i = row % n, j = row / n, k = col % n, l = col / n;
     double v = 0.0;
-    if (i == k && j == l) v += h * h * T->w[i] * T->w[j];
+    if (i == k && j == l) v += mq ? mq[e * nn + row] : h * h * T->w[i] * T->w[j];
     if (l == j) {
       v += T->D[k * n + i] * cx[e * nn + k + n * j];
       v += T->l1[i] * T->l1[k] * fmax(fe[1 * n + j], 0.0);
@@ -124,7 +125,8 @@ cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s) {
   if (c->dim != 2) return cudaErrorNotSupported;
   k_bj_assemble_2d<<<(unsigned)c->E, 256, 0, s>>>(
       c->p<Tables>(c->L.tables), c->n, c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-      c->p<double>(c->L.fa), c->p<double>(c->L.bj_lu));
+      c->p<double>(c->L.fa), c->p<double>(c->L.bj_lu),
+      c->curved ? c->p<double>(c->L.mq) : nullptr);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -1775,7 +1775,7 @@ __global__ void __launch_bounds__(128) k_shift_inv_w(int n, int64_t E, const dou
 
 // ---- learned factors: network inputs, normalised cores, acceptance ------------
 __global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const double* cx,
-                          const double* cy, const double* fa, double* kco);
+                          const double* cy, const double* fa, double* kco, const double* mq);
 
 // Mn = M / ||M||_F (column-major r x r) and ||M||_F (= ||A~||_F) per element
 __global__ void __launch_bounds__(128) k_core(const double* kco, const double* Zd, const double* Rz,
@@ -1865,7 +1865,8 @@ cudaError_t launch_learned_inputs(const tpp_ctx* c, float* X, double* Mn, double
                                   cudaStream_t s) {
   k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
                                     c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco));
+                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco),
+                                    c->curved ? c->p<double>(c->L.mq) : nullptr);
   count_launch();
   if (Mn) {
     k_core<<<(unsigned)((c->E + 3) / 4), 128, 0, s>>>(c->p<double>(c->L.kco),
@@ -1899,7 +1900,7 @@ cudaError_t launch_learned_accept(const tpp_ctx* c, const float* out, const doub
 // c < n), max(a.n, 0) on the +x and -x faces (c = n, n + 1); Cy likewise for
 // y; Dg[i + n j] = h^2 w_i w_j (mass).
 __global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const double* cx,
-                          const double* cy, const double* fa, double* kco) {
+                          const double* cy, const double* fa, double* kco, const double* mq) {
   const int nc = n + 2, nn = n * n, per = 2 * nc * n + nn;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < E * per;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -1921,7 +1922,7 @@ __global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const dou
       }
     } else {
       const int d = q - 2 * nc * n, i = d % n, j = d / n;
-      v = h * h * T->w[i] * T->w[j];
+      v = mq ? mq[e * nn + d] : h * h * T->w[i] * T->w[j];     // mass (curved: w |J_T|)
     }
     kco[g] = v;
   }
@@ -2090,7 +2091,8 @@ cudaError_t launch_build_2d(const tpp_ctx* c, cudaStream_t s) {
   }
   k_coef_2d<<<152 * 4, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->E, c->prob.h,
                                     c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco));
+                                    c->p<double>(c->L.fa), c->p<double>(c->L.kco),
+                                    c->curved ? c->p<double>(c->L.mq) : nullptr);
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;

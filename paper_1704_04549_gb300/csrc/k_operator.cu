@@ -208,6 +208,40 @@ __global__ void k_precompute(const double* __restrict__ wq, int dim, int n, int6
   }
 }
 
+// Curved elements (2D): the caller's metric terms at the quadrature points of the rule
+// (n nodes or mu points per direction, weights wq): mq = w |J_T|, cx = -dt w F~_x,
+// cy = -dt w F~_y with F~ = |J_T| J_T^-1 a, and fa = dt w_t a . (|J_T| J_T^-T N^).
+__global__ void k_metric_2d(const double* __restrict__ wq, int m, int64_t E, double dt,
+                            const double* __restrict__ jdet, const double* __restrict__ flux,
+                            const double* __restrict__ ff, double* mq, double* cx, double* cy,
+                            double* fa) {
+  const int mm = m * m;
+  const int64_t tot_v = E * mm, tot_f = E * 4 * m;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot_v + tot_f;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (g < tot_v) {
+      const int q = (int)(g % mm);
+      const double w = wq[q % m] * wq[q / m];
+      mq[g] = w * jdet[g];
+      cx[g] = -dt * w * flux[g];
+      cy[g] = -dt * w * flux[tot_v + g];
+    } else {
+      const int64_t gf = g - tot_v;
+      fa[gf] = dt * wq[(int)(gf % m)] * ff[gf];
+    }
+  }
+}
+
+cudaError_t launch_metric_2d(const tpp_ctx* c, const double* jdet, const double* flux,
+                             const double* ff, double dt, cudaStream_t s) {
+  const double* wq = (c->mu > c->n) ? c->p<MuTables>(c->L.mutab)->w : c->p<Tables>(c->L.tables)->w;
+  k_metric_2d<<<152 * 8, 256, 0, s>>>(wq, c->mu, c->E, dt, jdet, flux, ff, c->p<double>(c->L.mq),
+                                      c->p<double>(c->L.cx), c->p<double>(c->L.cy),
+                                      c->p<double>(c->L.fa));
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_precompute(const tpp_ctx* c, const double* vel_nodes,
                               const double* vel_face_normal, cudaStream_t s) {
   const bool d3 = c->dim == 3;
@@ -298,7 +332,7 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, VT hd, const VT* __restric
                               const VT* __restrict__ cy, const VT* __restrict__ fa,
                               const int32_t* __restrict__ nbr, const VT* __restrict__ x,
                               const VT* __restrict__ tr, VT* __restrict__ y, const int32_t* skip,
-                              int R) {
+                              int R, const VT* __restrict__ mq) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
@@ -337,7 +371,9 @@ __global__ void k_dg_apply_2d(const Tables* T, int n, VT hd, const VT* __restric
   const VT h2 = hd;                 // h^2
   for (int q = tid; q < nn; q += blockDim.x) {
     const int i = q % n, j = q / n;
-    VT acc = h2 * wl[i] * wl[j] * x[base + q];
+    // mass: h^2 w_i w_j, or w |J_T| of a curved element (mq; hd = 0 drops it)
+    const VT m = mq ? ((h2 != (VT)0) ? mq[cbase + q] : (VT)0) : h2 * wl[i] * wl[j];
+    VT acc = m * x[base + q];
     for (int k = 0; k < n; ++k) acc += Ds[k * n + i] * px[k + n * j];
     for (int l = 0; l < n; ++l) acc += Ds[l * n + j] * py[i + n * l];
     acc += wl[n + i] * fl[j] + wl[2 * n + i] * fl[n + j];
@@ -411,7 +447,8 @@ __global__ void k_dg_apply_3d(const Tables* T, int n, VT hd, const VT* __restric
 template <typename VT>
 cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* cz,
                               const VT* fa, const VT* x, const VT* tr, VT* y,
-                              const int32_t* skip, cudaStream_t s, double mass = 1.0) {
+                              const int32_t* skip, cudaStream_t s, double mass = 1.0,
+                              const VT* mq = nullptr) {
   const int n = c->n;
   const int32_t* nbr = c->p<int32_t>(c->L.nbr);
   const double h = c->prob.h;
@@ -421,7 +458,8 @@ cudaError_t launch_dg_apply_t(const tpp_ctx* c, const VT* cx, const VT* cy, cons
     if (threads < 4 * n) threads = ((4 * n + 31) / 32) * 32;
     const size_t smem = (3 * nn + 7 * n) * sizeof(VT);
     k_dg_apply_2d<VT><<<(unsigned)c->EB, threads, smem, s>>>(
-        c->p<Tables>(c->L.tables), n, (VT)(mass * h * h), cx, cy, fa, nbr, x, tr, y, skip, c->R);
+        c->p<Tables>(c->L.tables), n, (VT)(mass * h * h), cx, cy, fa, nbr, x, tr, y, skip, c->R,
+        mq);
     count_launch();
     return cudaGetLastError();
   }
@@ -444,7 +482,8 @@ cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr,
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                    d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
-                                   x, tr, y, skip, s);
+                                   x, tr, y, skip, s, 1.0,
+                                   c->curved ? c->p<double>(c->L.mq) : nullptr);
 }
 
 // y = dt A x = -dt J x: the operator without its mass term (traces tr of x given)
@@ -455,7 +494,8 @@ cudaError_t launch_dg_apply_flux(const tpp_ctx* c, const double* x, const double
   const bool d3 = c->dim == 3;
   return launch_dg_apply_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                    d3 ? c->p<double>(c->L.cz) : nullptr, c->p<double>(c->L.fa),
-                                   x, tr, y, nullptr, s, 0.0);
+                                   x, tr, y, nullptr, s, 0.0,
+                                   c->curved ? c->p<double>(c->L.mq) : nullptr);
 }
 
 // FP32 operator (the inner solves of the mixed-precision mode) on the float
@@ -466,14 +506,16 @@ cudaError_t launch_dg_apply_f32(const tpp_ctx* c, const float* x, const float* t
   const float* f = c->p<float>(c->L.opf);
   const OpF32Layout O = op_f32_layout(c);
   return launch_dg_apply_t<float>(c, f + O.cx, f + O.cy, c->dim == 3 ? f + O.cz : nullptr,
-                                  f + O.fa, x, tr, y, skip, s);
+                                  f + O.fa, x, tr, y, skip, s, 1.0,
+                                  c->curved ? f + O.mq : nullptr);
 }
 
 // float copies of the operator coefficients (after k_precompute)
 __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz,
-                            const double* fa, float* out, OpF32Layout O, int dim) {
+                            const double* fa, const double* mq, float* out, OpF32Layout O,
+                            int dim) {
   const int64_t tv = O.cy - O.cx, tf = O.tr - O.fa;
-  const int64_t total = (int64_t)dim * tv + tf;
+  const int64_t total = (int64_t)dim * tv + tf + (mq ? tv : 0);
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     double v;
@@ -483,10 +525,14 @@ __global__ void k_op_to_f32(const double* cx, const double* cy, const double* cz
       const int64_t i = g % tv;
       v = (which == 0 ? cx : which == 1 ? cy : cz)[i];
       dst = (which == 0 ? O.cx : which == 1 ? O.cy : O.cz) + i;
-    } else {
+    } else if (g < dim * tv + tf) {
       const int64_t i = g - dim * tv;
       v = fa[i];
       dst = O.fa + i;
+    } else {                              // curved elements: the per-point mass
+      const int64_t i = g - dim * tv - tf;
+      v = mq[i];
+      dst = O.mq + i;
     }
     out[dst] = __double2float_rn(v);
   }
@@ -497,7 +543,9 @@ cudaError_t launch_op_to_f32(const tpp_ctx* c, cudaStream_t s) {
   const bool d3 = c->dim == 3;
   k_op_to_f32<<<152 * 4, 256, 0, s>>>(c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                       d3 ? c->p<double>(c->L.cz) : nullptr,
-                                      c->p<double>(c->L.fa), c->p<float>(c->L.opf), O, c->dim);
+                                      c->p<double>(c->L.fa),
+                                      c->curved ? c->p<double>(c->L.mq) : nullptr,
+                                      c->p<float>(c->L.opf), O, c->dim);
   count_launch();
   return cudaGetLastError();
 }

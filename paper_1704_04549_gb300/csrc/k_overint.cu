@@ -157,7 +157,8 @@ __global__ void k_mu_basis(const Tables* T, const MuTables* M, int n, int mu, do
 __global__ void __launch_bounds__(128)
 k_core_mu(int n, int mu, int64_t E, double h, const MuTables* M, const double* __restrict__ cx,
           const double* __restrict__ cy, const double* __restrict__ fa,
-          const double* __restrict__ Rb, double* __restrict__ cores) {
+          const double* __restrict__ Rb, double* __restrict__ cores,
+          const double* __restrict__ mq) {
   extern __shared__ double smc[];
   const int nn = n * n, m = 2 * mu + 2, p = (nn < m) ? nn : m;
   const int64_t e = blockIdx.x;
@@ -172,7 +173,8 @@ k_core_mu(int n, int mu, int64_t E, double h, const MuTables* M, const double* _
     double v = 0.0;
     if (row < mu) {
       const int b = row;
-      if (col < mu) v = h * h * M->w[col] * M->w[b];                 // mass
+      if (col < mu)                                                  // mass (curved: w |J_T|)
+        v = mq ? mq[e * mu * mu + col + mu * b] : h * h * M->w[col] * M->w[b];
       else if (col < 2 * mu) v = cxe[(col - mu) + mu * b];           // x-volume
       else if (col == 2 * mu) v = fmax(fe[1 * mu + b], 0.0);         // +x face
       else v = fmax(fe[0 * mu + b], 0.0);                            // -x face
@@ -237,8 +239,11 @@ __global__ void __launch_bounds__(256)
 k_dg_apply_mu(const Tables* T, const MuTables* M, int n, int mu, double mass_h2,
               const VT* __restrict__ cx, const VT* __restrict__ cy, const VT* __restrict__ fa,
               const int32_t* __restrict__ nbr, const VT* __restrict__ x,
-              const VT* __restrict__ tr, VT* __restrict__ y, const int32_t* skip, int R) {
+              const VT* __restrict__ tr, VT* __restrict__ y, const int32_t* skip, int R,
+              const VT* __restrict__ mq) {
   if (skip && *skip) return;
+  // curved elements: the mass goes through the mu-point rule, w |J_T| u at the points
+  const bool qmass = mq && mass_h2 != 0.0;
   extern __shared__ __align__(16) unsigned char smo[];
   VT* sm = reinterpret_cast<VT*>(smo);
   const int nn = n * n, qq = mu * mu;
@@ -250,6 +255,7 @@ k_dg_apply_mu(const Tables* T, const MuTables* M, int n, int mu, double mass_h2,
   VT* px = t2 + n * mu;       // mu^2
   VT* py = px + qq;           // mu^2
   VT* fl = py + qq;           // 4 mu outward fluxes
+  VT* pm = fl + 4 * mu;       // mu^2 (curved mass)
   const int64_t blk = blockIdx.x, e = blk / R;
   const int r = (int)(blk % R);
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -282,6 +288,7 @@ k_dg_apply_mu(const Tables* T, const MuTables* M, int n, int mu, double mass_h2,
     for (int i = 0; i < n; ++i) s += G[a * n + i] * t1[i + n * b];
     px[q] = cx[e * qq + q] * s;
     py[q] = cy[e * qq + q] * s;
+    if (qmass) pm[q] = mq[e * qq + q] * s;
   }
   __syncthreads();
   // t1[i + n b] = sum_a D[a][i] px[a + mu b];  t2[i + n b] = sum_a G[a][i] py[a + mu b]
@@ -292,13 +299,15 @@ k_dg_apply_mu(const Tables* T, const MuTables* M, int n, int mu, double mass_h2,
       s1 += D[a * n + i] * px[a + mu * b];
       s2 += G[a * n + i] * py[a + mu * b];
     }
+    if (qmass)
+      for (int a = 0; a < mu; ++a) s1 += G[a * n + i] * pm[a + mu * b];
     t1[q] = s1;
     t2[q] = s2;
   }
   __syncthreads();
   for (int q = tid; q < nn; q += nt) {
     const int i = q % n, j = q / n;
-    VT acc = (VT)(mass_h2 * T->w[i] * T->w[j]) * xs[q];
+    VT acc = qmass ? (VT)0 : (VT)(mass_h2 * T->w[i] * T->w[j]) * xs[q];
     VT fx0 = 0, fx1 = 0, fy0 = 0, fy1 = 0;
     for (int b = 0; b < mu; ++b) {
       acc += G[b * n + j] * t1[i + n * b] + D[b * n + j] * t2[i + n * b];
@@ -315,15 +324,17 @@ k_dg_apply_mu(const Tables* T, const MuTables* M, int n, int mu, double mass_h2,
 template <typename VT>
 cudaError_t dg_apply_mu_t(const tpp_ctx* c, const VT* cx, const VT* cy, const VT* fa,
                           const VT* x, const VT* tr, VT* y, const int32_t* skip, cudaStream_t s,
-                          double mass) {
+                          double mass, const VT* mq) {
   const int n = c->n, mu = c->mu;
-  const size_t smem = (size_t)(2 * mu * n + n * n + 2 * n * mu + 2 * mu * mu + 4 * mu) * sizeof(VT);
+  const size_t smem =
+      (size_t)(2 * mu * n + n * n + 2 * n * mu + 3 * mu * mu + 4 * mu) * sizeof(VT);
   cudaError_t e = cudaFuncSetAttribute(k_dg_apply_mu<VT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_dg_apply_mu<VT><<<(unsigned)c->EB, 256, smem, s>>>(
       c->p<Tables>(c->L.tables), c->p<MuTables>(c->L.mutab), n, mu,
-      mass * c->prob.h * c->prob.h, cx, cy, fa, c->p<int32_t>(c->L.nbr), x, tr, y, skip, c->R);
+      mass * c->prob.h * c->prob.h, cx, cy, fa, c->p<int32_t>(c->L.nbr), x, tr, y, skip, c->R,
+      mq);
   count_launch();
   return cudaGetLastError();
 }
@@ -354,7 +365,8 @@ cudaError_t launch_core_mu(const tpp_ctx* c, cudaStream_t s) {
   k_core_mu<<<(unsigned)c->E, 128, smem, s>>>(n, mu, c->E, c->prob.h, c->p<MuTables>(c->L.mutab),
                                               c->p<double>(c->L.cx), c->p<double>(c->L.cy),
                                               c->p<double>(c->L.fa), c->p<double>(c->L.rb),
-                                              c->p<double>(c->L.kco));
+                                              c->p<double>(c->L.kco),
+                                              c->curved ? c->p<double>(c->L.mq) : nullptr);
   count_launch();
   return cudaGetLastError();
 }
@@ -378,14 +390,16 @@ cudaError_t launch_traces_mu_f32(const tpp_ctx* c, const float* x, float* tr, cu
 cudaError_t launch_dg_apply_mu(const tpp_ctx* c, const double* x, const double* tr, double* y,
                                const int32_t* skip, cudaStream_t s, double mass) {
   return dg_apply_mu_t<double>(c, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
-                               c->p<double>(c->L.fa), x, tr, y, skip, s, mass);
+                               c->p<double>(c->L.fa), x, tr, y, skip, s, mass,
+                               c->curved ? c->p<double>(c->L.mq) : nullptr);
 }
 
 cudaError_t launch_dg_apply_mu_f32(const tpp_ctx* c, const float* x, const float* tr, float* y,
                                    const int32_t* skip, cudaStream_t s) {
   const float* f = c->p<float>(c->L.opf);
   const OpF32Layout O = op_f32_layout(c);
-  return dg_apply_mu_t<float>(c, f + O.cx, f + O.cy, f + O.fa, x, tr, y, skip, s, 1.0);
+  return dg_apply_mu_t<float>(c, f + O.cx, f + O.cy, f + O.fa, x, tr, y, skip, s, 1.0,
+                              c->curved ? f + O.mq : nullptr);
 }
 
 }  // namespace tpp

@@ -16,7 +16,8 @@ namespace {
 
 // y = s M x (mode 0) or y = s M^-1 x (mode 1), M = h^d w (x) w (x) w, per vector block
 __global__ void k_mass(const Tables* T, int n, int dim, double hd, int64_t N,
-                       const double* __restrict__ x, double* __restrict__ y, double s, int mode) {
+                       const double* __restrict__ x, double* __restrict__ y, double s, int mode,
+                       const double* __restrict__ mq, int R) {
   const int nloc = (dim == 2) ? n * n : n * n * n;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -24,6 +25,7 @@ __global__ void k_mass(const Tables* T, int n, int dim, double hd, int64_t N,
     const int i = q % n, j = (q / n) % n, k = q / (n * n);
     double m = hd * T->w[i] * T->w[j];
     if (dim == 3) m *= T->w[k];
+    if (mq) m = mq[(g / nloc / R) * nloc + q];      // curved elements: w |J_T| (collocated)
     y[g] = mode == 0 ? s * m * x[g] : s * x[g] / m;
   }
 }
@@ -52,7 +54,7 @@ cudaError_t mass(const tpp_ctx* c, const double* x, double* y, double s, int mod
                  cudaStream_t st) {
   const double hd = (c->dim == 2) ? c->prob.h * c->prob.h : c->prob.h * c->prob.h * c->prob.h;
   k_mass<<<152 * 4, 256, 0, st>>>(c->p<Tables>(c->L.tables), c->n, c->dim, hd, c->N, x, y, s,
-                                  mode);
+                                  mode, c->curved ? c->p<double>(c->L.mq) : nullptr, c->R);
   count_launch();
   return cudaGetLastError();
 }

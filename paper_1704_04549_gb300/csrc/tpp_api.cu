@@ -142,6 +142,7 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
   L.cy = take((size_t)Nc * 8);
   L.cz = (d == 3) ? take((size_t)Nc * 8) : 0;
   L.fa = take((size_t)E * 2 * d * nfl * 8);
+  L.mq = take((size_t)Nc * 8);
   L.nbr = take((size_t)E * 2 * d * 4);
   L.traces = take((size_t)EB * 2 * d * nfl * 8);
   const size_t fsz = (size_t)E * n * n * 8;
@@ -413,9 +414,32 @@ tpp_status tpp_set_velocity(tpp_ctx* c, const double* vel_nodes, const double* v
   c->prob.dt = dt;
   c->factors_built = false;
   c->bj_built = false;
+  c->curved = false;
   TPP_TRY_CUDA(launch_precompute(c, vel_nodes, vel_face_normal, s), "k_precompute");
   if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_op_to_f32(c, s), "k_op_to_f32");
   TPP_TRY_CUDA(cudaStreamSynchronize(s), "tpp_set_velocity sync");
+  return TPP_OK;
+}
+
+tpp_status tpp_set_metric_terms(tpp_ctx* c, const double* jdet, const double* flux,
+                                const double* flux_face, double dt, void* stream) {
+  if (tpp_status r = check_ctx(c)) return r;
+  if (c->dim != 2 || c->sys_nc > 0 || (c->features & TPP_FEAT_LEARNED)) {
+    set_error("tpp_set_metric_terms: 2D scalar contexts without TPP_FEAT_LEARNED only");
+    return TPP_ERR_UNSUPPORTED;
+  }
+  if (!jdet || !flux || !flux_face || !(dt >= 0.0) || !std::isfinite(dt)) {
+    set_error("tpp_set_metric_terms: jdet, flux and flux_face non-NULL, dt >= 0 and finite");
+    return TPP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->prob.dt = dt;
+  c->factors_built = false;
+  c->bj_built = false;
+  c->curved = true;
+  TPP_TRY_CUDA(launch_metric_2d(c, jdet, flux, flux_face, dt, s), "k_metric_2d");
+  if (c->features & TPP_FEAT_MIXED) TPP_TRY_CUDA(launch_op_to_f32(c, s), "k_op_to_f32");
+  TPP_TRY_CUDA(cudaStreamSynchronize(s), "tpp_set_metric_terms sync");
   return TPP_OK;
 }
 

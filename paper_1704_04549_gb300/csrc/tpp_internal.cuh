@@ -82,6 +82,7 @@ struct Layout {
   size_t tables, status, gstate;
   size_t zd, rz, qo, qr_work, qr_tau;   // structure basis of the rearranged block (2D)
   size_t cx, cy, cz;                    // flux Jacobians at the volume nodes (scaled)
+  size_t mq;                            // curved elements: w |J_T| at the quadrature points
   size_t fa;                            // a.n_outward at the face nodes (scaled), [E][2d][nfl]
   size_t nbr;                           // neighbour across each face, [E][2d] (-1: none)
   size_t traces;
@@ -128,6 +129,7 @@ struct tpp_ctx {
   bool factors_built;
   bool bj_built;
   bool isolated;           // no neighbour coupling (every nbr entry -1): block-diagonal
+  bool curved = false;     // tpp_set_metric_terms: per-point mass L.mq (general geometry)
   // coupled system (k_system.cu): sys_nc components per physical element, the context's
   // elements are the (element, component) pairs; 0 for a scalar problem
   int32_t sys_nc = 0;
@@ -158,6 +160,9 @@ cudaError_t launch_traces(const tpp_ctx* c, const double* x, double* tr, cudaStr
                           const int32_t* skip = nullptr);
 cudaError_t launch_dg_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                             const int32_t* skip, cudaStream_t s);
+// curved elements: mass and flux coefficients from the caller's metric terms (2D)
+cudaError_t launch_metric_2d(const tpp_ctx* c, const double* jdet, const double* flux,
+                             const double* ff, double dt, cudaStream_t s);
 // coupled-system operator (k_system.cu); traces tr of x per (element, component) block
 cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                              const int32_t* skip, cudaStream_t s, double mass);
@@ -270,7 +275,7 @@ inline F32Layout f32_layout(int n, int64_t E, int dim, bool two) {
 // floats from Layout::opf): volume coefficients (E n^d each), face coefficients
 // (E 2d n^(d-1)), face traces (EB 2d n^(d-1))
 struct OpF32Layout {
-  size_t cx, cy, cz, fa, tr, total;
+  size_t cx, cy, cz, fa, tr, mq, total;
 };
 inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t EB) {
   const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;   // n: points per direction
@@ -281,6 +286,7 @@ inline OpF32Layout op_f32_layout(int dim, int64_t Nc, int64_t E, int n, int64_t 
   L.cz = o; if (dim == 3) o += Nc;
   L.fa = o; o += E * 2 * dim * nfl;
   L.tr = o; o += EB * 2 * dim * nfl;
+  L.mq = o; o += Nc;
   L.total = o;
   return L;
 }

@@ -123,3 +123,49 @@ def isolated_field(centres: np.ndarray, x: np.ndarray, velocity, span: float):
             a = synthetic.velocity_values(velocity, P)[..., d]
             fn[:, 2 * d + up, :] = a if up else -a
     return vel_nodes, np.ascontiguousarray(fn)
+
+
+def warped_metric_terms(nel, h: float, x: np.ndarray, velocity, warp):
+    """Metric terms of tpp_set_metric_terms for the 2D periodic mesh of nel = (N, N)
+    square cells of width h mapped by `warp` (X -> (Phi(X), grad Phi(X)), a bijection of
+    the periodic square of side L = N h, e.g. synthetic.periodic_warp): element e is
+    x = Phi((c + xi) h) and J_T = h grad Phi.  x: the context's quadrature points on
+    [0, 1] (tpp_gauss_legendre).  Returns (jdet [E][q^2], flux [2][E][q^2],
+    flux_face [E][4][q]); the velocity is evaluated at the physical point divided by L.
+    A face's geometry is computed from the element that owns it as its lower face, so
+    the two sides get opposite scaled normal velocities."""
+    nel = tuple(int(v) for v in nel)
+    assert len(nel) == 2 and nel[0] == nel[1]
+    L = nel[0] * h
+    q = len(x)
+    E, (cx, cy) = _coords(nel)
+    # volume points, a + q b with x fastest
+    xi_x = np.tile(x, q)
+    xi_y = np.repeat(x, q)
+    X = np.stack([(cx[:, None] + xi_x[None, :]) * h, (cy[:, None] + xi_y[None, :]) * h], -1)
+    phys, G = warp(X)
+    J = h * G
+    det = J[..., 0, 0] * J[..., 1, 1] - J[..., 0, 1] * J[..., 1, 0]
+    a = synthetic.velocity_values(velocity, phys / L)
+    # |J| J^-1 a = adj(J) a
+    fx = J[..., 1, 1] * a[..., 0] - J[..., 0, 1] * a[..., 1]
+    fy = -J[..., 1, 0] * a[..., 0] + J[..., 0, 0] * a[..., 1]
+    flux = np.stack([fx, fy], 0)
+    ff = np.empty((E, 4, q))
+    normals = ((-1.0, 0.0), (1.0, 0.0), (0.0, -1.0), (0.0, 1.0))
+    for f in range(4):
+        d, side = divmod(f, 2)
+        XF = np.empty((E, q, 2))
+        own = (cx if d == 0 else cy) + side
+        tang = cy if d == 0 else cx
+        XF[..., d] = own[:, None] * h
+        XF[..., 1 - d] = (tang[:, None] + x[None, :]) * h
+        pf, GF = warp(XF)
+        JF = h * GF
+        # |J| J^-T N = adj(J)^T N
+        nx, ny = normals[f]
+        sx = JF[..., 1, 1] * nx - JF[..., 1, 0] * ny
+        sy = -JF[..., 0, 1] * nx + JF[..., 0, 0] * ny
+        af = synthetic.velocity_values(velocity, pf / L)
+        ff[:, f, :] = af[..., 0] * sx + af[..., 1] * sy
+    return det, flux, ff

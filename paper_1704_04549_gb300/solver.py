@@ -169,6 +169,19 @@ class Context:
                                               _stream(stream)), "tpp_set_velocity")
         self.dt = float(dt)
 
+    def tpp_set_metric_terms(self, jdet, flux, flux_face, dt: float, stream=None):
+        """Curved elements: |J_T|, |J_T| J_T^-1 a and a . |J_T| J_T^-T N^ at the quadrature
+        points (layouts as in tpp.h); the factors must be rebuilt."""
+        def dev(a):
+            return a.contiguous() if isinstance(a, torch.Tensor) else torch.as_tensor(
+                np.ascontiguousarray(a, dtype=np.float64).reshape(-1), device=self.device)
+        jd, fl, ff = dev(jdet), dev(flux), dev(flux_face)
+        with torch.cuda.device(self.device):
+            L.check(self.lib.tpp_set_metric_terms(self._ctx, _ptr(jd), _ptr(fl), _ptr(ff),
+                                                  float(dt), _stream(stream)),
+                    "tpp_set_metric_terms")
+        self.dt = float(dt)
+
     def __del__(self):
         ctx = getattr(self, "_ctx", None)
         if ctx is not None and ctx.value:
