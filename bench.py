@@ -476,6 +476,25 @@ def other_configs(args, dev):
     return out
 
 
+def run_euler(args):
+    """The Euler vortex systems (euler_record) as their own JSON line: value = factor build +
+    GMRES solve of the dt = 0.1 system with the small-block Kronecker preconditioner."""
+    import torch
+    dev = torch.device("cuda:0")
+    with ClockSampler(0) as clk:
+        rec = euler_record(dev)
+    line = {"metric": "2D Euler vortex, linearised LLF system: build + GMRES(30) to 1e-8 with "
+                      "the small-block Kronecker preconditioner, 1 GB300",
+            "value": rec["dt=0.1"]["K_small"]["build_solve_ms"], "unit": "ms", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "16 x 12 periodic mesh of the 20 x 15 domain, n = 8, vortex "
+                                   "of Sec. 5.3 at t = 0, dt = 0.1 and 0.01"},
+            "records": rec, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def euler_record(dev):
     """2D Euler equations linearised around the vortex of Sec. 5.3 at t = 0: 16 x 12
     periodic mesh of the 20 x 15 domain (h = 1.25), n = 8 (p = 7), one backward Euler
@@ -1046,6 +1065,40 @@ def run_kernels(args):
         print(json.dumps({"mode": "kernels", "workload": "learned", "n": 16,
                           "elements": ctx.num_elem}))
         return 0
+    if args.workload == "batch":           # per-system batched GMRES, one width class:
+        import numpy as np                  # 2D n = 31, 152 isolated elements x 64 rhs
+        from paper_1704_04549_gb300 import TPP_FEAT_TWO_SIDED, Context
+        from paper_1704_04549_gb300.batch import BatchGmres
+        rng = np.random.Generator(np.random.PCG64(7))
+        c = Context(2, 31, (152,), 1.0, 0.05, synthetic.fourier_velocity(1709, 2), max_restart=1,
+                    features=TPP_FEAT_TWO_SIDED, device="cuda:0", batch_rhs=64,
+                    centres=rng.random((152, 2)), batch_span=1.0 / 64)
+        c.tpp_build_factors()
+        b = torch.as_tensor(synthetic.rhs(3, c.num_dofs), device="cuda:0")
+        x = torch.zeros_like(b)
+        sv = BatchGmres([c], restart=20, rtol=1e-8)
+        sv.solve([b], [x])
+        rep = sv.solve([b], [x])
+        print(json.dumps({"mode": "kernels", "workload": "batch", "n": 31, "systems": rep["systems"],
+                          "launch_ms": rep["launch_ms"], "total_iters": rep["total_iters"]}))
+        return 0
+    if args.workload == "euler":           # coupled Euler operator, 64 x 64 elements, n = 16
+        import numpy as np
+        from paper_1704_04549_gb300 import Context
+        n, N, h = 16, 64, 20.0 / 64
+        xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+        cx, cy = np.arange(N * N) % N, np.arange(N * N) // N
+        X = np.stack(np.meshgrid(xg, xg, indexing="xy"), -1).reshape(-1, 2)
+        pts = np.stack([(cx[:, None] + X[None, :, 0]) * h, (cy[:, None] + X[None, :, 1]) * h], -1)
+        state = synthetic.euler_vortex_state(pts).transpose(0, 2, 1)
+        ctx = Context.euler_system(n, (N, N), h, 0.05, state, device="cuda:0")
+        v = torch.as_tensor(synthetic.rhs(5, ctx.num_dofs), device="cuda:0")
+        y = torch.empty_like(v)
+        for _ in range(4):
+            ctx.dg_apply_sumfact(v, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernels", "workload": "euler", "n": n, "dofs": ctx.num_dofs}))
+        return 0
     from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, Context
     w = workload_3d(args.n if args.n != 16 else 11) if args.workload == "adv3d" else workload(args.n)
     ctx = Context(w["dim"], w["n"], w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
@@ -1119,7 +1172,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--iter-limit", type=int, default=50,
                     help="learned workload: GMRES iterations before the exact rebuild")
-    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned", "timestep",
+    ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned", "timestep", "euler",
                                            "mrhs"],
                     default="adv2d",
                     help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
@@ -1138,6 +1191,8 @@ def main():
         return run_timestep(args)
     if args.workload == "mrhs":
         return run_mrhs(args)
+    if args.workload == "euler":
+        return run_euler(args)
     return run_ours(args)
 
 
