@@ -473,7 +473,49 @@ def other_configs(args, dev):
                                      for m, t in tuned.items()}}
     torch.cuda.empty_cache()
     out["euler_vortex_16x12_n8"] = euler_record(dev)
+    out["curved_64x64_n16"] = curved_record(dev, flush)
     return out
+
+
+def curved_record(dev, flush):
+    """Curved elements: the 64 x 64 mesh of the 2D configuration mapped by the periodic
+    warp Phi(X) = X + 0.05 L sin(2 pi X / L) sin(2 pi Y / L) (1, 1) (L = 64, h = 1), n = 16,
+    field 1705, dt = 0.05: operator and FP64 apply throughput, factor build, and the FP64
+    GMRES(30) solve to 1e-8 (metric terms from mesh.warped_metric_terms)."""
+    import torch
+    from paper_1704_04549_gb300 import TPP_FP64, TPP_PC_KRON, Context, mesh
+    n, N, h = 16, 64, 1.0
+    vel = synthetic.fourier_velocity(1705, 2)
+    ctx = Context(2, n, (N, N), h, 0.05, vel, max_restart=30, device=str(dev))
+    warp = lambda X: synthetic.periodic_warp(X, N * h, 0.05)
+    jd, fl, ff = mesh.warped_metric_terms((N, N), h, ctx.gauss_legendre()[0], vel, warp)
+    ctx.tpp_set_metric_terms(jd, fl, ff, 0.05)
+    stream = torch.cuda.current_stream(dev)
+    Nd = ctx.num_dofs
+    b = torch.as_tensor(synthetic.rhs(1706, Nd), device=dev)
+    z = torch.empty_like(b)
+    ctx.tpp_build_factors()
+    rec = {"dofs": Nd, "build_ms": time_each(lambda: ctx.tpp_build_factors(), 3, stream, flush)}
+    for _ in range(3):
+        ctx.dg_apply_sumfact(b, z)
+        ctx.tpp_apply_inverse(b, z, prec=TPP_FP64)
+    rec["operator_gdofs"] = Nd / (time_each(lambda: ctx.dg_apply_sumfact(b, z), 10, stream,
+                                            flush) * 1e-3) / 1e9
+    rec["apply_fp64_gdofs"] = Nd / (time_each(lambda: ctx.tpp_apply_inverse(b, z, prec=TPP_FP64),
+                                              10, stream, flush) * 1e-3) / 1e9
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=1000, pc=TPP_PC_KRON,
+                           check=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rec["gmres"] = {"solve_ms": e0.elapsed_time(e1), "iters": r["iters"],
+                    "converged": bool(r["converged"]), "true_rel_res": r["true_rel_res"]}
+    del ctx
+    torch.cuda.empty_cache()
+    return rec
 
 
 def run_euler(args):

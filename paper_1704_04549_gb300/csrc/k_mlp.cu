@@ -325,7 +325,7 @@ cudaError_t forward_tc(tpp_mlp* m, const float* X, int B, float* out, bool train
     ep.err = err;
     if (l < 3) {
       ep.kind = tc::kEpiHidden;
-      ep.outf = pre + m->poff[l];
+      ep.outf = train ? pre + m->poff[l] : nullptr;   // pre-activations: back-propagation only
       ep.ldo = w[l + 1];
       ep.hi = at<__nv_bfloat16>(m, m->hhi[l + 1]);
       ep.lo = at<__nv_bfloat16>(m, m->hlo[l + 1]);

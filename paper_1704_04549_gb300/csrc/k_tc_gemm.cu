@@ -33,7 +33,7 @@ namespace tc {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 6;
 constexpr int kABytes = kBM * kBK * 2;       // 16 KB per A tile
 constexpr int kBBytes = kBN * kBK * 2;       // 16 KB per B tile
 constexpr int kStageBytes = kABytes + kBBytes;
@@ -153,59 +153,102 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 }
 
 // Epilogue of one 32 x 32 block of the tile (rows mb.., columns nb..), run by one
-// warp: acc[j] is row mb + lane, column nb + j.  The block goes through a padded
-// shared buffer so that row-major stores are coalesced (lane = column) and the
-// transposed BF16 pair is written with lane = row.
-__device__ __forceinline__ void epilogue_block(const Epilogue& ep, int mb, int nb,
-                                               const float* acc, float (*st)[33]) {
+// warp straight from the tensor-memory load: lane = row mb + lane, acc[j] = column
+// nb + j.  Row-major outputs leave as 16-byte vector stores of the lane's row (no
+// shared-memory staging, which leaves the shared memory to the operand pipeline);
+// the transposed BF16 pair (training) is written column by column with lane = row,
+// coalesced over the warp.
+__device__ __forceinline__ void epilogue_block(const Epilogue& ep, int mb, int nb, float* acc) {
   const int lane = threadIdx.x & 31;
+  const int m = mb + lane;
+  const bool row_ok = m < ep.M;
+  const bool full = nb + 32 <= ep.N;                  // warp-uniform
+  if (ep.kind == kEpiF32) {
+    if (!row_ok) return;
+    float* o = ep.outf + (int64_t)m * ep.ldo + nb;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) st[lane][j] = acc[j];
-  __syncwarp();
-  const int n = nb + lane;
-  const bool col_ok = n < ep.N;
-  const float bias = (ep.bias && col_ok) ? ep.bias[n] : 0.0f;
-  for (int r = 0; r < 32; ++r) {
-    const int m = mb + r;
-    const bool ok = col_ok && m < ep.M;
-    const float a = st[r][lane];
-    if (ep.kind == kEpiF32) {
-      if (ok) ep.outf[(int64_t)m * ep.ldo + n] = a + bias;
-      continue;
-    }
-    float v = 0.0f;
-    if (ok) {
-      if (ep.kind == kEpiHidden) {
-        const float z = a + bias;
-        ep.outf[(int64_t)m * ep.ldo + n] = z;
-        v = gelu_f(z);
+    for (int g = 0; g < 32; g += 4) {
+      float v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int n = nb + g + t;
+        v[t] = acc[g + t] + ((ep.bias && n < ep.N) ? ep.bias[n] : 0.0f);
+      }
+      if (full) {
+        *reinterpret_cast<float4*>(o + g) = make_float4(v[0], v[1], v[2], v[3]);
       } else {
-        v = a * gelu_grad_f(ep.zprev[(int64_t)m * ep.ldz + n]);
-        ep.outf[(int64_t)m * ep.ldo + n] = v;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (nb + g + t < ep.N) o[g + t] = v[t];
       }
     }
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    if (ok) {
-      ep.hi[(int64_t)m * ep.ldh + n] = hi;
-      ep.lo[(int64_t)m * ep.ldh + n] = lo;
-    }
-    st[r][lane] = __uint_as_float((uint32_t)__bfloat16_as_ushort(hi) |
-                                  ((uint32_t)__bfloat16_as_ushort(lo) << 16));
+    return;
   }
-  if (ep.kind != kEpiF32 && ep.thi) {
-    __syncwarp();
-    const int m = mb + lane;
-    if (m < ep.Mt) {
-      for (int j = 0; j < 32; ++j) {
-        if (nb + j >= ep.N) break;
-        const uint32_t pk = __float_as_uint(st[lane][j]);
-        ep.thi[(int64_t)(nb + j) * ep.ldt + m] = __ushort_as_bfloat16((unsigned short)(pk & 0xFFFFu));
-        ep.tlo[(int64_t)(nb + j) * ep.ldt + m] = __ushort_as_bfloat16((unsigned short)(pk >> 16));
+  uint32_t hl[32];                                    // packed (hi, lo) of every column
+#pragma unroll
+  for (int g = 0; g < 32; g += 4) {
+    float z[4], v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int n = nb + g + t;
+      const bool ok = row_ok && n < ep.N;
+      if (ep.kind == kEpiHidden) {
+        z[t] = acc[g + t] + ((ep.bias && n < ep.N) ? ep.bias[n] : 0.0f);
+        v[t] = ok ? gelu_f(z[t]) : 0.0f;
+      } else {
+        v[t] = ok ? acc[g + t] * gelu_grad_f(ep.zprev[(int64_t)m * ep.ldz + n]) : 0.0f;
+        z[t] = v[t];
+      }
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v[t]);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v[t] - __bfloat162float(hi));
+      hl[g + t] = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+    }
+    if (ep.outf && row_ok) {                          // pre-activation / gradient, FP32
+      float* o = ep.outf + (int64_t)m * ep.ldo + nb + g;
+      if (full) {
+        *reinterpret_cast<float4*>(o) = make_float4(z[0], z[1], z[2], z[3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (nb + g + t < ep.N) o[t] = z[t];
       }
     }
   }
-  __syncwarp();
+  if (row_ok) {                                       // the BF16 pair, row-major
+    __nv_bfloat16* ph = ep.hi + (int64_t)m * ep.ldh + nb;
+    __nv_bfloat16* pl = ep.lo + (int64_t)m * ep.ldh + nb;
+    if (full) {
+#pragma unroll
+      for (int g = 0; g < 32; g += 8) {
+        uint4 h4, l4;
+        h4.x = (hl[g] & 0xFFFFu) | (hl[g + 1] << 16);
+        h4.y = (hl[g + 2] & 0xFFFFu) | (hl[g + 3] << 16);
+        h4.z = (hl[g + 4] & 0xFFFFu) | (hl[g + 5] << 16);
+        h4.w = (hl[g + 6] & 0xFFFFu) | (hl[g + 7] << 16);
+        l4.x = (hl[g] >> 16) | (hl[g + 1] & 0xFFFF0000u);
+        l4.y = (hl[g + 2] >> 16) | (hl[g + 3] & 0xFFFF0000u);
+        l4.z = (hl[g + 4] >> 16) | (hl[g + 5] & 0xFFFF0000u);
+        l4.w = (hl[g + 6] >> 16) | (hl[g + 7] & 0xFFFF0000u);
+        *reinterpret_cast<uint4*>(ph + g) = h4;
+        *reinterpret_cast<uint4*>(pl + g) = l4;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (nb + j < ep.N) {
+          ph[j] = __ushort_as_bfloat16((unsigned short)(hl[j] & 0xFFFFu));
+          pl[j] = __ushort_as_bfloat16((unsigned short)(hl[j] >> 16));
+        }
+    }
+  }
+  if (ep.thi && m < ep.Mt) {                          // transposed pair (zero for m >= M)
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (nb + j < ep.N) {
+        ep.thi[(int64_t)(nb + j) * ep.ldt + m] = __ushort_as_bfloat16((unsigned short)(hl[j] & 0xFFFFu));
+        ep.tlo[(int64_t)(nb + j) * ep.ldt + m] = __ushort_as_bfloat16((unsigned short)(hl[j] >> 16));
+      }
+  }
 }
 
 // Persistent kernel: CTA c takes output tiles c, c + gridDim.x, ... (tile t is row
@@ -217,7 +260,6 @@ __device__ __forceinline__ void epilogue_block(const Epilogue& ep, int mb, int n
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTmemCols = 2 * kBN;
-constexpr int kStageSmem = kEpiWarps * 32 * 33 * 4;
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tc(const __grid_constant__ Operands op, const Epilogue ep) {
@@ -229,7 +271,6 @@ k_gemm_tc(const __grid_constant__ Operands op, const Epilogue ep) {
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const uint32_t sbase = smem_u32(smem);
-  float(*stage_buf)[32][33] = reinterpret_cast<float(*)[32][33]>(smem + kStages * kStageBytes);
   const int ntn = (ep.N + kBN - 1) / kBN, ntm = (ep.M + kBM - 1) / kBM;
   const int ntiles = ntn * ntm;
   if (threadIdx.x == 0) {
@@ -316,7 +357,6 @@ k_gemm_tc(const __grid_constant__ Operands op, const Epilogue ep) {
   } else {
     // epilogue warps
     const int e = warp - 2, q = warp & 3, h = e >> 2;
-    float(*st)[33] = stage_buf[e];
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1;
@@ -328,7 +368,7 @@ k_gemm_tc(const __grid_constant__ Operands op, const Epilogue ep) {
       if (n0 + col < ep.N) {              // warp-uniform
         float acc[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN + col), acc);
-        epilogue_block(ep, m0 + q * 32, n0 + col, acc, st);
+        epilogue_block(ep, m0 + q * 32, n0 + col, acc);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -383,7 +423,7 @@ cudaError_t make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_
 }
 
 cudaError_t gemm(const Operands& op, const Epilogue& ep, int M, int N, cudaStream_t s) {
-  constexpr int kSmemBytes = kStages * kStageBytes + kStageSmem + 1024;   // + alignment slack
+  constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   static int num_sms = 0;

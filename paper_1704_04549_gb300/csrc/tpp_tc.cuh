@@ -24,7 +24,7 @@ enum { kEpiF32 = 0, kEpiHidden = 1, kEpiGeluBack = 2 };
 
 // Epilogue of one output tile (rows m < M and columns n < N are written):
 //  kEpiF32:      outf[m][n] = acc (+ bias[n])
-//  kEpiHidden:   z = acc + bias[n]; outf[m][n] = z; v = GELU(z)
+//  kEpiHidden:   z = acc + bias[n]; outf[m][n] = z (if outf != NULL); v = GELU(z)
 //  kEpiGeluBack: v = acc * GELU'(zprev[m][n]); outf[m][n] = v
 // and for the last two the BF16 pair of v: hi/lo[m][n] (row stride ldh) and, when
 // thi != NULL, transposed thi/tlo[n][m] (stride ldt) for every m < Mt, zero for
