@@ -152,3 +152,53 @@ def test_isolated_element_arrays():
     assert abs(fn[1, 1, 0] - a[0]) <= 1e-15
     a = synthetic.velocity_values(vel, np.array([0.3 + 0.1 * (0.75 - 0.5), 0.55]))
     assert abs(fn[0, 2, 1] + a[1]) <= 1e-15        # -y face: outward normal -e_y
+
+
+def test_system_problem_validation(L):
+    """tpp_sys_workspace_bytes rejects what tpp_create_system would (no kernel runs)."""
+    lib = L.load()
+    from paper_1704_04549_gb300 import mesh
+    nbr = np.ascontiguousarray(mesh.periodic_nbr((3, 3)), dtype=np.int32)
+    state = np.ones(9 * 4 * 16)
+
+    def problem(**kw):
+        P = L.SysProblem()
+        P.dim, P.n, P.num_elem, P.nc, P.flux = 2, 4, 9, 4, L.TPP_FLUX_EULER
+        P.gamma, P.h, P.dt = 1.4, 1.0, 0.1
+        P.state = state.ctypes.data_as(C.c_void_p)
+        P.nbr = nbr.ctypes.data_as(C.c_void_p)
+        for k, v in kw.items():
+            setattr(P, k, v)
+        return P
+    good = lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, 0)
+    assert good > 0
+    scalar, _ = _problem(L, n=4, nel=(36,), isolated=True)
+    assert good > lib.tpp_workspace_bytes(C.byref(scalar), 30, 0)   # + the coupling arrays
+    for bad in (dict(dim=3), dict(nc=5), dict(flux=0), dict(gamma=1.0), dict(n=0), dict(h=0.0),
+                dict(state=None)):
+        assert lib.tpp_sys_workspace_bytes(C.byref(problem(**bad)), 30, 0) == 0, bad
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 4, 0) == 0        # max_restart >= 5
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, L.TPP_FEAT_MIXED) == 0
+    assert b"TPP_FEAT" in lib.tpp_last_error()
+
+
+def test_batch_and_metric_argument_checks(L):
+    """The batched GMRES checks its options before touching a context, and the metric
+    terms entry point rejects NULL arguments; neither needs a device."""
+    lib = L.load()
+    o = L.BatchOpts()
+    o.restart, o.max_iters, o.rtol, o.prec = 20, 100, 1e-8, L.TPP_FP64
+    dummy = (C.c_void_p * 1)(None)
+    assert lib.tpp_batch_workspace_bytes(dummy, 1, C.byref(o)) == 0          # NULL context
+    assert b"NULL" in lib.tpp_last_error()
+    for field, val in (("restart", 0), ("restart", 32), ("max_iters", 0), ("rtol", 0.0),
+                       ("prec", 7)):
+        ob = L.BatchOpts()
+        C.pointer(ob)[0] = o
+        setattr(ob, field, val)
+        assert lib.tpp_batch_workspace_bytes(dummy, 1, C.byref(ob)) == 0, field
+    om = L.BatchOpts()
+    C.pointer(om)[0] = o
+    om.prec, om.max_outer, om.inner_rtol = L.TPP_FP32, 0, 1e-4
+    assert lib.tpp_batch_workspace_bytes(dummy, 1, C.byref(om)) == 0
+    assert lib.tpp_set_metric_terms(None, None, None, None, 0.1, None) == 1  # NULL context
