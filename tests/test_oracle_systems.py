@@ -104,3 +104,67 @@ def test_vortex_state_is_isentropic_and_faces_are_outflow_dominated():
         for f in range(4):
             own, _, _ = sysdg.face_data(e, f)
             assert np.diagonal(own, axis1=1, axis2=2).min() >= 0.0
+
+
+# ---- 3D (five components) ----------------------------------------------------------
+def _states3d(seed, m):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rho = rng.uniform(0.5, 2.0, m)
+    V = rng.uniform(-1, 1, (m, 3))
+    p = rng.uniform(0.5, 3.0, m)
+    E = p / ((GAMMA - 1) * rho) + 0.5 * np.sum(V * V, -1)
+    return np.concatenate([rho[:, None], rho[:, None] * V, (rho * E)[:, None]], -1)
+
+
+def test_euler3d_jacobians_and_speeds():
+    from oracle.systems import euler3d_flux, euler3d_jacobians
+    U = _states3d(6, 15)
+    A = euler3d_jacobians(U, GAMMA)
+    eps = 1e-6
+    for k in range(5):
+        d = np.zeros(5)
+        d[k] = eps
+        Fp, Fm = euler3d_flux(U + d, GAMMA), euler3d_flux(U - d, GAMMA)
+        for dd in range(3):
+            fd = (Fp[dd] - Fm[dd]) / (2 * eps)
+            assert np.abs(fd - A[dd][:, :, k]).max() <= 1e-7 * max(1, np.abs(A[dd]).max())
+    rho = U[:, 0]
+    V = U[:, 1:4] / rho[:, None]
+    p = (GAMMA - 1) * (U[:, 4] - 0.5 * rho * np.sum(V * V, -1))
+    c = np.sqrt(GAMMA * p / rho)
+    nv = np.array([0.48, 0.6, 0.64])
+    for q in range(U.shape[0]):
+        An = sum(nv[d] * A[d][q] for d in range(3))
+        vn = V[q] @ nv
+        ev = np.sort(np.linalg.eigvals(An).real)
+        ref = np.sort([vn - c[q], vn, vn, vn, vn + c[q]])
+        assert np.abs(ev - ref).max() <= 1e-9 * (abs(vn) + c[q])
+
+
+def test_one_component_system_is_upwind_advection_3d():
+    mesh = PeriodicMesh((2, 3, 2), 0.5)
+    a = (1.0, -0.5, 0.3)
+    n = 3
+    sysdg = LinearizedSystemDG(mesh, n, 0.1, LinearAdvectionFlux(a),
+                               np.zeros((mesh.num_elem, 1, n ** 3)))
+    ref = AdvectionDG(mesh, n, 0.1, synthetic.constant_velocity(list(a))).global_matrix()
+    assert abs(sysdg.global_matrix() - ref).max() <= 1e-13 * abs(ref).max()
+
+
+def test_3d_conservation_and_residual():
+    L = 2.0
+    sysdg = vortex_system((2, 2, 2), L / 2, 3, 0.05,
+                          lambda X: synthetic.euler3d_wave_state(X, L))
+    D = sysdg.global_matrix() - sysdg.mass_matrix()
+    Dd = D.toarray()
+    for c in range(5):
+        one = np.zeros(sysdg.ndof)
+        for e in range(sysdg.mesh.num_elem):
+            one[e * sysdg.bs + c * sysdg.nloc:e * sysdg.bs + (c + 1) * sysdg.nloc] = 1.0
+        assert np.abs(one @ Dd).max() <= 1e-12 * np.abs(Dd).max()
+    lam = [[sysdg.face_data(e, f)[2] for f in range(6)] for e in range(sysdg.mesh.num_elem)]
+    x = synthetic.rhs(8, sysdg.ndof) * 0.01
+    eps = 1e-4
+    U0 = sysdg.U0.reshape(-1)
+    fd = (sysdg.residual(U0 + eps * x, lam) - sysdg.residual(U0 - eps * x, lam)) / (2 * eps)
+    assert np.linalg.norm(fd - D @ x) <= 1e-6 * np.linalg.norm(D @ x)
