@@ -332,8 +332,8 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
                                 const double* flux_face, double dt, void* stream);
 
 /*
- * Coupled systems of conservation laws (Sec. 5.3, Sec. 5.6: the 2D Euler equations,
- * n_c = 4 components rho, rho u, rho v, rho E with the flux of Eq. euler-flux),
+ * Coupled systems of conservation laws (Sec. 5.3, Sec. 5.6: the Euler equations,
+ * n_c = dim + 2 components rho, the momenta, rho E with the flux of Eq. euler-flux),
  * linearised around a DG state u0 given at the nodes.  The operator is the Jacobian
  * system S = M - dt J of the DG discretisation with the local Lax-Friedrichs flux
  * F^(u-, u+).n = 1/2 (F(u-) + F(u+)).n + 1/2 lam (u- - u+), lam = max(|v-.n| + c-,
@@ -346,7 +346,7 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * n_c n) are not built.
  *
  * tpp_create_system returns an ordinary context whose elements are the (element,
- * component) pairs e * n_c + c: vectors are [E][n_c][n^2], tpp_num_elem() is
+ * component) pairs e * n_c + c: vectors are [E][n_c][n^dim], tpp_num_elem() is
  * E * n_c, dg_apply_sumfact / dg_apply_sumfact_static apply the coupled S, gmres_solve
  * solves with it, and tpp_build_factors / tpp_apply_inverse / tpp_build_block_jacobi
  * / tpp_apply_block_jacobi act on the small blocks.  Features: TPP_FEAT_TWO_SIDED,
@@ -355,20 +355,21 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  */
 #define TPP_FLUX_EULER 1
 typedef struct {
-  int32_t dim;              /* 2 */
-  int32_t n;                /* nodes per direction, 1..32 */
+  int32_t dim;              /* 2 or 3 */
+  int32_t n;                /* nodes per direction, 1..32 (2D), 1..12 (3D) */
   int64_t num_elem;         /* physical elements E */
-  int32_t nc;               /* components: 4 for TPP_FLUX_EULER */
+  int32_t nc;               /* components: dim + 2 for TPP_FLUX_EULER */
   int32_t flux;             /* TPP_FLUX_EULER */
   double gamma;             /* ratio of specific heats, > 1 (1.4 in the paper) */
   double h, dt;             /* element width (square elements), time step */
-  const double* state;      /* device [E][nc][n^2]: u0 in conserved variables at the nodes
-                               (read during tpp_create_system only) */
-  const int32_t* nbr;       /* [E][4] neighbour across faces -x, +x, -y, +y (-1: none), as in
-                               tpp_problem (read during tpp_create_system only) */
+  const double* state;      /* device [E][nc][n^dim]: u0 in conserved variables (rho, the
+                               momenta, rho E) at the nodes (read during tpp_create_system) */
+  const int32_t* nbr;       /* [E][2 dim] neighbour across faces -x, +x, -y, +y (, -z, +z)
+                               (-1: none), as in tpp_problem (read during tpp_create_system) */
 } tpp_sys_problem;
 
-/* Workspace for a system context (0 if invalid).  max_restart >= 5. */
+/* Workspace for a system context (0 if invalid).  max_restart >= 5 and
+ * (max_restart + 1) n >= dim (n + 2). */
 size_t tpp_sys_workspace_bytes(const tpp_sys_problem* prob, int32_t max_restart,
                                uint32_t features);
 /* As tpp_create; computes the linearisation coefficients from the state (synchronises

@@ -1,17 +1,17 @@
 // Coupled systems of conservation laws (Sec. 5.3 and Sec. 5.6: the Euler equations,
-// n_c = 4 components in 2D, flux of Eq. euler-flux), linearised around a DG state.
+// n_c = dim + 2 components, flux of Eq. euler-flux), linearised around a DG state.
 //
 // A system context is an ordinary context over E * n_c pseudo-elements (element e,
-// component c at e * n_c + c, vectors [E][n_c][n^2]), isolated from one another,
+// component c at e * n_c + c, vectors [E][n_c][n^dim]), isolated from one another,
 // whose own coefficients are the "small" diagonal blocks of the Jacobian: component
 // c's volume coefficients A_d[c][c] and own-face coefficients 1/2 (A_n[c][c] + lam).
 // Factor build, Kronecker apply and block Jacobi act on those small blocks
 // unchanged.  The operator (dg_apply_sumfact, gmres_solve) is the coupled one:
-//   y_c = M x_c + sum_c' [ sum_k D_ki cx[c][c'] x_c' + sum_l D_lj cy[c][c'] x_c' ]
+//   y_c = M x_c + sum_d sum_c' D_d^T cd[c][c'] x_c'
 //         + lifted face fluxes F_c = sum_c' fo[c][c'] u_c'^own + fn[c][c'] u_c'^nbr,
 // with the local Lax-Friedrichs flux linearised around the state (lam frozen):
-//   fo = dt h w_t 1/2 (A_n(u0-) + lam I),  fn = dt h w_t 1/2 (A_n(u0+) - lam I),
-//   lam = max(|v- . n| + c-, |v+ . n| + c+),  cx = -dt h w_i w_j A_x(u0), cy likewise.
+//   fo = dt h^(dim-1) w_t 1/2 (A_n(u0-) + lam I),  fn = dt h^(dim-1) w_t 1/2 (A_n(u0+) - lam I),
+//   lam = max(|v- . n| + c-, |v+ . n| + c+),  cd = -dt h^(dim-1) w_q A_d(u0).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -24,104 +24,132 @@ namespace tpp {
 
 namespace {
 
-constexpr int kNc = 4;
-
-// A_x, A_y = dF/du of Eq. euler-flux in conserved variables, |v.n| + c for normal nv
-__device__ void euler_jacobians(const double U[kNc], double g, double Ax[kNc][kNc],
-                                double Ay[kNc][kNc]) {
-  const double rho = U[0], u = U[1] / rho, v = U[2] / rho;
+// A_d = dF_d/du of the Euler flux in conserved variables (NC = DIM + 2 components:
+// rho, the DIM momenta, rho E), A[d][c][c'] for d < DIM
+template <int DIM>
+__device__ void euler_jacobians(const double* U, double g, double (*A)[DIM + 2][DIM + 2]) {
+  constexpr int NC = DIM + 2, E_ = DIM + 1;
+  const double rho = U[0];
+  double V[DIM], q2 = 0.0;
+  for (int i = 0; i < DIM; ++i) {
+    V[i] = U[1 + i] / rho;
+    q2 += V[i] * V[i];
+  }
   const double g1 = g - 1.0;
-  const double p = g1 * (U[3] - 0.5 * rho * (u * u + v * v));
-  const double H = (U[3] + p) / rho;
-  const double phi = 0.5 * g1 * (u * u + v * v);
-  Ax[0][0] = 0.0;            Ax[0][1] = 1.0;                Ax[0][2] = 0.0;              Ax[0][3] = 0.0;
-  Ax[1][0] = phi - u * u;    Ax[1][1] = (3.0 - g) * u;      Ax[1][2] = -g1 * v;          Ax[1][3] = g1;
-  Ax[2][0] = -u * v;         Ax[2][1] = v;                  Ax[2][2] = u;                Ax[2][3] = 0.0;
-  Ax[3][0] = u * (phi - H);  Ax[3][1] = H - g1 * u * u;     Ax[3][2] = -g1 * u * v;      Ax[3][3] = g * u;
-  Ay[0][0] = 0.0;            Ay[0][1] = 0.0;                Ay[0][2] = 1.0;              Ay[0][3] = 0.0;
-  Ay[1][0] = -u * v;         Ay[1][1] = v;                  Ay[1][2] = u;                Ay[1][3] = 0.0;
-  Ay[2][0] = phi - v * v;    Ay[2][1] = -g1 * u;            Ay[2][2] = (3.0 - g) * v;    Ay[2][3] = g1;
-  Ay[3][0] = v * (phi - H);  Ay[3][1] = -g1 * u * v;        Ay[3][2] = H - g1 * v * v;   Ay[3][3] = g * v;
-}
-
-__device__ double euler_speed(const double U[kNc], double g, double nx, double ny) {
-  const double rho = U[0], u = U[1] / rho, v = U[2] / rho;
-  const double p = (g - 1.0) * (U[3] - 0.5 * rho * (u * u + v * v));
-  return fabs(u * nx + v * ny) + sqrt(g * p / rho);
-}
-
-// volume coefficients at the nodes; the diagonal entries go to vel (the small blocks'
-// "velocity" for the scalar precompute: vel[g] = A_x[c][c], vel[Ep n^2 + g] = A_y[c][c])
-__global__ void k_sys_volume(const Tables* T, int n, int64_t E, double g, double h, double dt,
-                             const double* __restrict__ state, double* __restrict__ scx,
-                             double* __restrict__ scy, double* __restrict__ vel) {
-  const int nn = n * n;
-  const int64_t tot = E * nn, totp = E * kNc * nn;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = q / nn;
-    const int node = (int)(q % nn), i = node % n, j = node / n;
-    double U[kNc], Ax[kNc][kNc], Ay[kNc][kNc];
-    for (int c = 0; c < kNc; ++c) U[c] = state[(e * kNc + c) * nn + node];
-    euler_jacobians(U, g, Ax, Ay);
-    const double f = -dt * h * T->w[i] * T->w[j];
-    for (int c = 0; c < kNc; ++c) {
-      for (int c2 = 0; c2 < kNc; ++c2) {
-        const int64_t o = ((e * kNc + c) * kNc + c2) * nn + node;
-        scx[o] = f * Ax[c][c2];
-        scy[o] = f * Ay[c][c2];
-      }
-      vel[(e * kNc + c) * nn + node] = Ax[c][c];
-      vel[totp + (e * kNc + c) * nn + node] = Ay[c][c];
+  const double p = g1 * (U[E_] - 0.5 * rho * q2);
+  const double H = (U[E_] + p) / rho;
+  const double phi = 0.5 * g1 * q2;
+  for (int d = 0; d < DIM; ++d) {
+    const double vd = V[d];
+    for (int r = 0; r < NC; ++r)
+      for (int c = 0; c < NC; ++c) A[d][r][c] = 0.0;
+    A[d][0][1 + d] = 1.0;
+    for (int i = 0; i < DIM; ++i) {
+      A[d][1 + i][0] = -V[i] * vd + ((i == d) ? phi : 0.0);
+      for (int j = 0; j < DIM; ++j)
+        A[d][1 + i][1 + j] = ((i == j) ? vd : 0.0) + ((j == d) ? V[i] : 0.0) -
+                             ((i == d) ? g1 * V[j] : 0.0);
+      A[d][1 + i][E_] = (i == d) ? g1 : 0.0;
     }
+    A[d][E_][0] = vd * (phi - H);
+    for (int j = 0; j < DIM; ++j) A[d][E_][1 + j] = ((j == d) ? H : 0.0) - g1 * V[j] * vd;
+    A[d][E_][E_] = g * vd;
   }
 }
 
-// face coefficients from the state traces tr ([E n_c][4][n], k_traces layout) and the
-// element neighbours; vfn: the small blocks' own-face coefficient 1/2 (A_n[c][c] + lam)
+// |v . n| + c for the unit normal along axis `ax` (the Cartesian faces)
+template <int DIM>
+__device__ double euler_speed(const double* U, double g, int ax) {
+  const double rho = U[0];
+  double q2 = 0.0;
+  for (int i = 0; i < DIM; ++i) q2 += (U[1 + i] / rho) * (U[1 + i] / rho);
+  const double p = (g - 1.0) * (U[DIM + 1] - 0.5 * rho * q2);
+  return fabs(U[1 + ax] / rho) + sqrt(g * p / rho);
+}
+
+// volume coefficients at the nodes: sc[d][((e NC + c) NC + c') n^DIM + q] =
+// -dt h^(DIM-1) w_q A_d[c][c']; the diagonal entries go to vel (the small blocks'
+// "velocity" for the scalar precompute: vel[d][(e NC + c) n^DIM + q] = A_d[c][c])
+template <int DIM>
+__global__ void k_sys_volume(const Tables* T, int n, int64_t E, double g, double h, double dt,
+                             const double* __restrict__ state, double* __restrict__ scx,
+                             double* __restrict__ scy, double* __restrict__ scz,
+                             double* __restrict__ vel) {
+  constexpr int NC = DIM + 2;
+  const int nl = (DIM == 2) ? n * n : n * n * n;
+  const int64_t tot = E * nl, totp = E * NC * nl;
+  const double hf = (DIM == 2) ? h : h * h;
+  double* sc[3] = {scx, scy, scz};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / nl;
+    const int node = (int)(q % nl), i = node % n, j = (node / n) % n, k = node / (n * n);
+    double U[NC], A[DIM][NC][NC];
+    for (int c = 0; c < NC; ++c) U[c] = state[(e * NC + c) * nl + node];
+    euler_jacobians<DIM>(U, g, A);
+    double w = T->w[i] * T->w[j];
+    if (DIM == 3) w *= T->w[k];
+    const double f = -dt * hf * w;
+    for (int d = 0; d < DIM; ++d)
+      for (int c = 0; c < NC; ++c) {
+        for (int c2 = 0; c2 < NC; ++c2) sc[d][((e * NC + c) * NC + c2) * nl + node] = f * A[d][c][c2];
+        vel[d * totp + (e * NC + c) * nl + node] = A[d][c][c];
+      }
+  }
+}
+
+// face coefficients from the state traces tr ([E NC][2 DIM][n^(DIM-1)], k_traces layout)
+// and the element neighbours; vfn: the small blocks' own-face coefficient
+// 1/2 (A_n[c][c] + lam)
+template <int DIM>
 __global__ void k_sys_faces(const Tables* T, int n, int64_t E, double g, double h, double dt,
                             const double* __restrict__ tr, const int32_t* __restrict__ nbr,
                             double* __restrict__ sfo, double* __restrict__ sfn,
                             double* __restrict__ vfn) {
-  const int64_t tot = E * 4 * n;
+  constexpr int NC = DIM + 2, NF = 2 * DIM;
+  const int nfl = (DIM == 2) ? n : n * n;
+  const int64_t tot = E * NF * nfl;
+  const double hf = (DIM == 2) ? h : h * h;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = q / (4 * n);
-    const int f = (int)((q / n) % 4), t = (int)(q % n);
-    const double nx = (f == 0) ? -1.0 : (f == 1) ? 1.0 : 0.0;
-    const double ny = (f == 2) ? -1.0 : (f == 3) ? 1.0 : 0.0;
-    const int nb = nbr[e * 4 + f];
-    double um[kNc], up[kNc];
-    for (int c = 0; c < kNc; ++c) {
-      um[c] = tr[((e * kNc + c) * 4 + f) * n + t];
-      up[c] = (nb >= 0) ? tr[(((int64_t)nb * kNc + c) * 4 + (f ^ 1)) * n + t] : um[c];
+    const int64_t e = q / (NF * nfl);
+    const int f = (int)((q / nfl) % NF), t = (int)(q % nfl);
+    const int ax = f / 2;
+    const double sgn = (f & 1) ? 1.0 : -1.0;           // outward normal sgn e_ax
+    const int nb = nbr[e * NF + f];
+    double um[NC], up[NC];
+    for (int c = 0; c < NC; ++c) {
+      um[c] = tr[((e * NC + c) * NF + f) * nfl + t];
+      up[c] = (nb >= 0) ? tr[(((int64_t)nb * NC + c) * NF + (f ^ 1)) * nfl + t] : um[c];
     }
-    double lam = euler_speed(um, g, nx, ny);
-    if (nb >= 0) lam = fmax(lam, euler_speed(up, g, nx, ny));
-    double Ax[kNc][kNc], Ay[kNc][kNc], Bx[kNc][kNc], By[kNc][kNc];
-    euler_jacobians(um, g, Ax, Ay);
-    euler_jacobians(up, g, Bx, By);
-    const double sc = dt * h * T->w[t];
-    for (int c = 0; c < kNc; ++c) {
-      for (int c2 = 0; c2 < kNc; ++c2) {
+    double lam = euler_speed<DIM>(um, g, ax);
+    if (nb >= 0) lam = fmax(lam, euler_speed<DIM>(up, g, ax));
+    double Am[DIM][NC][NC], Ap[DIM][NC][NC];
+    euler_jacobians<DIM>(um, g, Am);
+    euler_jacobians<DIM>(up, g, Ap);
+    double wt = T->w[t % n];
+    if (DIM == 3) wt *= T->w[t / n];
+    const double sc = dt * hf * wt;
+    for (int c = 0; c < NC; ++c) {
+      for (int c2 = 0; c2 < NC; ++c2) {
         const double d = (c == c2) ? lam : 0.0;
-        const double jm = nx * Ax[c][c2] + ny * Ay[c][c2];
-        const double jp = nx * Bx[c][c2] + ny * By[c][c2];
-        const int64_t o = (((e * 4 + f) * kNc + c) * kNc + c2) * n + t;
+        const double jm = sgn * Am[ax][c][c2], jp = sgn * Ap[ax][c][c2];
+        const int64_t o = (((e * NF + f) * NC + c) * NC + c2) * nfl + t;
         sfo[o] = sc * 0.5 * (jm + d);
         sfn[o] = (nb >= 0) ? sc * 0.5 * (jp - d) : 0.0;
-        if (c == c2) vfn[((e * kNc + c) * 4 + f) * n + t] = 0.5 * (jm + lam);
+        if (c == c2) vfn[((e * NC + c) * NF + f) * nfl + t] = 0.5 * (jm + lam);
       }
     }
   }
 }
 
-// y = (mass M + dt A) x for the coupled system, one physical element per CTA
+// y = (mass M + dt A) x for the coupled 2D system, one physical element per CTA
 __global__ void k_sys_apply_2d(const Tables* T, int n, double hd, const double* __restrict__ scx,
                                const double* __restrict__ scy, const double* __restrict__ sfo,
                                const double* __restrict__ sfn, const int32_t* __restrict__ nbr,
                                const double* __restrict__ x, const double* __restrict__ tr,
                                double* __restrict__ y, const int32_t* skip) {
+  constexpr int kNc = 4;
   if (skip && *skip) return;
   extern __shared__ __align__(16) double sms[];
   const int nn = n * n, tid = threadIdx.x, nt = blockDim.x;
@@ -178,33 +206,112 @@ __global__ void k_sys_apply_2d(const Tables* T, int n, double hd, const double* 
   }
 }
 
+// the same for the coupled 3D system (5 components), as k_dg_apply_3d per component
+__global__ void k_sys_apply_3d(const Tables* T, int n, double hd, const double* __restrict__ scx,
+                               const double* __restrict__ scy, const double* __restrict__ scz,
+                               const double* __restrict__ sfo, const double* __restrict__ sfn,
+                               const int32_t* __restrict__ nbr, const double* __restrict__ x,
+                               const double* __restrict__ tr, double* __restrict__ y,
+                               const int32_t* skip) {
+  constexpr int kNc = 5;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) double sms[];
+  const int nn = n * n, n3 = nn * n, tid = threadIdx.x, nt = blockDim.x;
+  double* Ds = sms;                 // n^2
+  double* wl = Ds + nn;             // w, l0, l1
+  double* xs = wl + 3 * n;          // kNc n^3
+  double* px = xs + kNc * n3;       // n^3 each
+  double* py = px + n3;
+  double* pz = py + n3;
+  double* fl = pz + n3;             // 6 n^2
+  const int64_t e = blockIdx.x;
+  for (int q = tid; q < nn; q += nt) Ds[q] = T->D[q];
+  for (int q = tid; q < n; q += nt) {
+    wl[q] = T->w[q];
+    wl[n + q] = T->l0[q];
+    wl[2 * n + q] = T->l1[q];
+  }
+  for (int q = tid; q < kNc * n3; q += nt) xs[q] = x[e * kNc * n3 + q];
+  int nbf[6];
+  for (int f = 0; f < 6; ++f) nbf[f] = nbr[e * 6 + f];
+  __syncthreads();
+  for (int c = 0; c < kNc; ++c) {
+    for (int q = tid; q < n3; q += nt) {
+      double a = 0.0, b = 0.0, d = 0.0;
+      for (int c2 = 0; c2 < kNc; ++c2) {
+        const int64_t o = ((e * kNc + c) * kNc + c2) * n3 + q;
+        const double xv = xs[c2 * n3 + q];
+        a += scx[o] * xv;
+        b += scy[o] * xv;
+        d += scz[o] * xv;
+      }
+      px[q] = a;
+      py[q] = b;
+      pz[q] = d;
+    }
+    for (int q = tid; q < 6 * nn; q += nt) {
+      const int f = q / nn, t = q % nn;
+      const int nb = nbf[f];
+      double F = 0.0;
+      for (int c2 = 0; c2 < kNc; ++c2) {
+        const int64_t o = (((e * 6 + f) * kNc + c) * kNc + c2) * nn + t;
+        F += sfo[o] * tr[((e * kNc + c2) * 6 + f) * nn + t];
+        if (nb >= 0) F += sfn[o] * tr[(((int64_t)nb * kNc + c2) * 6 + (f ^ 1)) * nn + t];
+      }
+      fl[q] = F;
+    }
+    __syncthreads();
+    for (int q = tid; q < n3; q += nt) {
+      const int i = q % n, j = (q / n) % n, k = q / nn;
+      double acc = hd * wl[i] * wl[j] * wl[k] * xs[c * n3 + q];
+      for (int a = 0; a < n; ++a) acc += Ds[a * n + i] * px[a + n * j + nn * k];
+      for (int b = 0; b < n; ++b) acc += Ds[b * n + j] * py[i + n * b + nn * k];
+      for (int cc = 0; cc < n; ++cc) acc += Ds[cc * n + k] * pz[i + n * j + nn * cc];
+      const int qx = j + n * k, qy = i + n * k, qz = i + n * j;
+      acc += wl[n + i] * fl[0 * nn + qx] + wl[2 * n + i] * fl[1 * nn + qx];
+      acc += wl[n + j] * fl[2 * nn + qy] + wl[2 * n + j] * fl[3 * nn + qy];
+      acc += wl[n + k] * fl[4 * nn + qz] + wl[2 * n + k] * fl[5 * nn + qz];
+      y[(e * kNc + c) * n3 + q] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 struct SysLayout {
-  size_t cx, cy, fo, fn, nbr, total;
+  size_t cx, cy, cz, fo, fn, nbr, total;
 };
 
-SysLayout sys_layout(size_t base, int n, int64_t E) {
+// NC = dim + 2 components; coupling arrays of the coupled operator after the scalar layout
+SysLayout sys_layout(size_t base, int dim, int n, int64_t E) {
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t vol = (size_t)E * kNc * kNc * n * n * 8, fac = (size_t)E * 4 * kNc * kNc * n * 8;
+  const size_t nc = (size_t)dim + 2, nl = (dim == 2) ? (size_t)n * n : (size_t)n * n * n;
+  const size_t nfl = (dim == 2) ? (size_t)n : (size_t)n * n;
+  const size_t vol = (size_t)E * nc * nc * nl * 8, fac = (size_t)E * 2 * dim * nc * nc * nfl * 8;
   SysLayout L;
   size_t o = al(base);
   L.cx = o; o += al(vol);
   L.cy = o; o += al(vol);
+  L.cz = o; o += (dim == 3) ? al(vol) : 0;
   L.fo = o; o += al(fac);
   L.fn = o; o += al(fac);
-  L.nbr = o; o += al((size_t)E * 4 * 4);
+  L.nbr = o; o += al((size_t)E * 2 * dim * 4);
   L.total = o;
   return L;
 }
 
 const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t features) {
   if (!p) return "tpp_sys_problem is NULL";
-  if (p->dim != 2) return "systems are implemented in 2D";
-  if (p->flux != TPP_FLUX_EULER || p->nc != kNc) return "flux TPP_FLUX_EULER needs nc = 4";
-  if (p->n < 1 || p->n > TPP_MAX_N) return "n must be in 1..32";
+  if (p->dim != 2 && p->dim != 3) return "dim must be 2 or 3";
+  if (p->flux != TPP_FLUX_EULER || p->nc != p->dim + 2)
+    return "flux TPP_FLUX_EULER needs nc = dim + 2 (4 in 2D, 5 in 3D)";
+  if (p->n < 1 || p->n > (p->dim == 2 ? TPP_MAX_N : 12))
+    return "n must be in 1..32 (2D) or 1..12 (3D)";
   if (p->num_elem < 1 || p->num_elem > (int64_t)1 << 28) return "num_elem out of range";
   if (!(p->gamma > 1.0) || !(p->h > 0.0) || !(p->dt >= 0.0)) return "gamma > 1, h > 0, dt >= 0";
   if (!p->state || !p->nbr) return "state and nbr must be non-NULL";
-  if (max_restart < 5) return "system contexts need max_restart >= 5";
+  // the diagonal 'velocity' scratch (dim + 2 dim / n solution sizes) lives in the Krylov basis
+  if ((int64_t)(max_restart + 1) * p->n < (int64_t)p->dim * p->n + 2 * p->dim || max_restart < 5)
+    return "system contexts need max_restart >= 5 (and (max_restart + 1) n >= dim (n + 2))";
   if (features & (TPP_FEAT_MIXED | TPP_FEAT_TIME | TPP_FEAT_LEARNED))
     return "system contexts support TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI and TPP_FEAT_BF16";
   return nullptr;
@@ -213,9 +320,9 @@ const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t
 tpp_problem small_problem(const tpp_sys_problem* p, const int32_t* iso_nbr) {
   tpp_problem q;
   std::memset(&q, 0, sizeof(q));
-  q.dim = 2;
+  q.dim = p->dim;
   q.n = p->n;
-  q.num_elem = p->num_elem * kNc;
+  q.num_elem = p->num_elem * p->nc;
   q.nrhs = 1;
   q.mu = 0;
   q.h = p->h;
@@ -228,16 +335,29 @@ tpp_problem small_problem(const tpp_sys_problem* p, const int32_t* iso_nbr) {
 
 cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                              const int32_t* skip, cudaStream_t s, double mass) {
-  const int n = c->n;
-  const size_t smem = (size_t)(n * n + 3 * n + kNc * n * n + 2 * n * n + 4 * n) * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_sys_apply_2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const int threads = std::max(64, ((n * n + 31) / 32) * 32);
-  k_sys_apply_2d<<<(unsigned)c->sys_E, std::min(threads, 1024), smem, s>>>(
-      c->p<Tables>(c->L.tables), n, mass * c->prob.h * c->prob.h, c->p<double>(c->sys_cx),
-      c->p<double>(c->sys_cy), c->p<double>(c->sys_fo), c->p<double>(c->sys_fn),
-      c->p<int32_t>(c->sys_nbr), x, tr, y, skip);
+  const int n = c->n, nn = n * n;
+  if (c->dim == 2) {
+    const size_t smem = (size_t)(nn + 3 * n + 4 * nn + 2 * nn + 4 * n) * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sys_apply_2d,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = std::max(64, ((nn + 31) / 32) * 32);
+    k_sys_apply_2d<<<(unsigned)c->sys_E, std::min(threads, 1024), smem, s>>>(
+        c->p<Tables>(c->L.tables), n, mass * c->prob.h * c->prob.h, c->p<double>(c->sys_cx),
+        c->p<double>(c->sys_cy), c->p<double>(c->sys_fo), c->p<double>(c->sys_fn),
+        c->p<int32_t>(c->sys_nbr), x, tr, y, skip);
+  } else {
+    const int n3 = nn * n;
+    const size_t smem = (size_t)(nn + 3 * n + 5 * n3 + 3 * n3 + 6 * nn) * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sys_apply_3d,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sys_apply_3d<<<(unsigned)c->sys_E, 256, smem, s>>>(
+        c->p<Tables>(c->L.tables), n, mass * c->prob.h * c->prob.h * c->prob.h,
+        c->p<double>(c->sys_cx), c->p<double>(c->sys_cy), c->p<double>(c->sys_cz),
+        c->p<double>(c->sys_fo), c->p<double>(c->sys_fn), c->p<int32_t>(c->sys_nbr), x, tr, y,
+        skip);
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -252,11 +372,11 @@ extern "C" size_t tpp_sys_workspace_bytes(const tpp_sys_problem* p, int32_t max_
     set_error(why);
     return 0;
   }
-  std::vector<int32_t> iso((size_t)p->num_elem * kNc * 4, -1);
+  std::vector<int32_t> iso((size_t)p->num_elem * p->nc * 2 * p->dim, -1);
   const tpp_problem q = small_problem(p, iso.data());
   const size_t base = tpp_workspace_bytes(&q, max_restart, features);
   if (base == 0) return 0;
-  return sys_layout(base, p->n, p->num_elem).total;
+  return sys_layout(base, p->dim, p->n, p->num_elem).total;
 }
 
 extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
@@ -271,8 +391,9 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
     set_error(why);
     return TPP_ERR_INVALID_ARG;
   }
+  const int dim = p->dim, nf = 2 * dim, NC = p->nc;
   const int64_t E = p->num_elem;
-  std::vector<int32_t> nb((size_t)E * 4);
+  std::vector<int32_t> nb((size_t)E * nf);
   {
     cudaError_t e = cudaMemcpy(nb.data(), p->nbr, nb.size() * 4, cudaMemcpyDefault);
     if (e != cudaSuccess) return cuda_check(e, "read nbr");
@@ -282,10 +403,10 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
       set_error("nbr entry " + std::to_string(i) + " is outside [-1, num_elem)");
       return TPP_ERR_INVALID_ARG;
     }
-  std::vector<int32_t> iso((size_t)E * kNc * 4, -1);
+  std::vector<int32_t> iso((size_t)E * NC * nf, -1);
   const tpp_problem q = small_problem(p, iso.data());
   const size_t base = tpp_workspace_bytes(&q, max_restart, features);
-  const SysLayout SL = sys_layout(base, p->n, E);
+  const SysLayout SL = sys_layout(base, dim, p->n, E);
   if (base == 0 || ws_bytes < SL.total) {
     set_error("workspace smaller than tpp_sys_workspace_bytes");
     return TPP_ERR_WORKSPACE;
@@ -295,9 +416,9 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
     return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = p->n;
-  const int64_t Ep = E * kNc, N = Ep * n * n;
-  double* vel = c->p<double>(c->L.V);                    // scratch: Krylov basis, unused yet
-  double* vfn = vel + 2 * N;
+  const int64_t N = c->N;                               // E NC n^dim
+  double* vel = c->p<double>(c->L.V);                   // scratch: Krylov basis, unused yet
+  double* vfn = vel + (size_t)dim * N;
   auto fail = [&](cudaError_t e, const char* what) {
     const tpp_status st = cuda_check(e, what);
     tpp_destroy(c);
@@ -309,22 +430,31 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
   double* tr = c->p<double>(c->L.traces);
   if ((e = launch_traces(c, p->state, tr, s)) != cudaSuccess) return fail(e, "state traces");
   const Tables* T = c->p<Tables>(c->L.tables);
-  k_sys_volume<<<152 * 8, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, p->state,
-                                       c->p<double>(SL.cx), c->p<double>(SL.cy), vel);
-  count_launch();
-  k_sys_faces<<<152 * 4, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, tr,
-                                      c->p<int32_t>(SL.nbr), c->p<double>(SL.fo),
-                                      c->p<double>(SL.fn), vfn);
-  count_launch();
+  if (dim == 2) {
+    k_sys_volume<2><<<152 * 8, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, p->state,
+                                            c->p<double>(SL.cx), c->p<double>(SL.cy), nullptr, vel);
+    k_sys_faces<2><<<152 * 4, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, tr,
+                                           c->p<int32_t>(SL.nbr), c->p<double>(SL.fo),
+                                           c->p<double>(SL.fn), vfn);
+  } else {
+    k_sys_volume<3><<<152 * 8, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, p->state,
+                                            c->p<double>(SL.cx), c->p<double>(SL.cy),
+                                            c->p<double>(SL.cz), vel);
+    k_sys_faces<3><<<152 * 4, 256, 0, s>>>(T, n, E, p->gamma, p->h, p->dt, tr,
+                                           c->p<int32_t>(SL.nbr), c->p<double>(SL.fo),
+                                           c->p<double>(SL.fn), vfn);
+  }
+  count_launch(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "system coefficients");
   if (tpp_status st = tpp_set_velocity(c, vel, vfn, p->dt, stream)) {   // the small blocks
     tpp_destroy(c);
     return st;
   }
-  c->sys_nc = kNc;
+  c->sys_nc = NC;
   c->sys_E = E;
   c->sys_cx = SL.cx;
   c->sys_cy = SL.cy;
+  c->sys_cz = SL.cz;
   c->sys_fo = SL.fo;
   c->sys_fn = SL.fn;
   c->sys_nbr = SL.nbr;

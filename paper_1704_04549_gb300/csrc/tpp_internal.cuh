@@ -134,7 +134,7 @@ struct tpp_ctx {
   // elements are the (element, component) pairs; 0 for a scalar problem
   int32_t sys_nc = 0;
   int64_t sys_E = 0;
-  size_t sys_cx = 0, sys_cy = 0, sys_fo = 0, sys_fn = 0, sys_nbr = 0;
+  size_t sys_cx = 0, sys_cy = 0, sys_cz = 0, sys_fo = 0, sys_fn = 0, sys_nbr = 0;
   int32_t partial_blocks;  // number of CTAs of the reduction kernels
   cudaGraphExec_t gexec[64];   // use_graph: captured Arnoldi step groups, by first step
   int32_t gkernels[64];        // kernels in each (added to the launch count per replay)

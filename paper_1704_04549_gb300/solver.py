@@ -77,10 +77,11 @@ class Context:
     def euler_system(cls, n: int, nel, h: float, dt: float, state, gamma: float = 1.4,
                      max_restart: int = 30, features: int = 0, device: str = "cuda:0",
                      stream=None):
-        """The 2D Euler equations linearised around `state` (conserved variables at the
-        nodes, [E][4][n^2], E = nel[0] nel[1] on the periodic mesh of mesh.periodic_nbr):
-        the coupled operator with the small-block preconditioners (tpp_create_system).
-        Vectors are [E][4][n^2]; num_elem counts (element, component) pairs."""
+        """The Euler equations linearised around `state` (conserved variables at the nodes,
+        [E][dim + 2][n^dim], E = prod(nel) on the periodic mesh of mesh.periodic_nbr, dim =
+        len(nel)): the coupled operator with the small-block preconditioners
+        (tpp_create_system).  Vectors are [E][dim + 2][n^dim]; num_elem counts (element,
+        component) pairs."""
         from . import mesh
         self = cls.__new__(cls)
         if not torch.cuda.is_available():
@@ -89,14 +90,15 @@ class Context:
         self.device = torch.device(device)
         self.batch_rhs = 0
         self.nel = tuple(int(v) for v in nel)
-        self.dim, self.n, self.dt, self.h, self.nrhs, self.mu = 2, n, float(dt), float(h), 1, n
+        dim = len(self.nel)
+        self.dim, self.n, self.dt, self.h, self.nrhs, self.mu = dim, n, float(dt), float(h), 1, n
         nb = torch.as_tensor(np.ascontiguousarray(mesh.periodic_nbr(self.nel), dtype=np.int32),
                              device=self.device)
         st = torch.as_tensor(np.ascontiguousarray(state, dtype=np.float64).reshape(-1),
                              device=self.device) if not isinstance(state, torch.Tensor) \
             else state.contiguous()
         P = L.SysProblem()
-        P.dim, P.n, P.num_elem, P.nc, P.flux = 2, n, int(nb.shape[0]), 4, L.TPP_FLUX_EULER
+        P.dim, P.n, P.num_elem, P.nc, P.flux = dim, n, int(nb.shape[0]), dim + 2, L.TPP_FLUX_EULER
         P.gamma, P.h, P.dt = float(gamma), self.h, self.dt
         P.state, P.nbr = _ptr(st), _ptr(nb)
         nbytes = self.lib.tpp_sys_workspace_bytes(C.byref(P), max_restart, features)

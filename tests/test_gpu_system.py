@@ -161,3 +161,79 @@ def test_nearly_defective_density_blocks():
     assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
     print(f"relaxed Schur deflation on {len(relaxed)} density blocks; worst apply error "
           f"{worst:.1e}; GMRES {r['iters']} (oracle {o['iters']})")
+
+
+# ---- 3D: five components (Sec. 5.6's periodic Euler case) -----------------------------
+def _state3d(n, nel, h, L):
+    xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    E = nel[0] * nel[1] * nel[2]
+    out = np.empty((E, 5, n ** 3))
+    gz, gy, gx = np.meshgrid(xg, xg, xg, indexing="ij")          # x fastest when flattened
+    for e in range(E):
+        cx, cy, cz = e % nel[0], (e // nel[0]) % nel[1], e // (nel[0] * nel[1])
+        X = np.stack([(cx + gx) * h, (cy + gy) * h, (cz + gz) * h], -1).reshape(-1, 3)
+        out[e] = synthetic.euler3d_wave_state(X, L).T
+    return out
+
+
+def _pair3d(n, nel, dt, features=0):
+    from paper_1704_04549_gb300 import Context
+    L = 2.0
+    h = L / nel[0]
+    U0 = _state3d(n, nel, h, L)
+    ora = vortex_system(nel, h, n, dt, lambda X: synthetic.euler3d_wave_state(X, L))
+    ora.U0 = U0
+    ctx = Context.euler_system(n, nel, h, dt, U0, features=features, device=DEV)
+    return ctx, ora
+
+
+@pytest.mark.parametrize("n,nel", [(2, (2, 2, 2)), (3, (2, 2, 2)), (5, (2, 2, 2)), (8, (2, 2, 1)),
+                                   (12, (2, 1, 1))])
+def test_coupled_3d_operator_matches_oracle(n, nel):
+    ctx, ora = _pair3d(n, nel, 0.05)
+    S = ora.global_matrix()
+    x = synthetic.rhs(7, ora.ndof)
+    y = to_host(ctx.dg_apply_sumfact(to_dev(x)))
+    assert rel(y, S @ x) <= FP64_TOL, rel(y, S @ x)
+
+
+@pytest.mark.parametrize("n,nel", [(3, (2, 2, 2)), (5, (2, 2, 2))])
+def test_3d_small_block_factors_and_gmres(n, nel):
+    """The nested 3D KSVD (Sec. 4.3) of every small block against the oracle's, and GMRES
+    on the coupled system with the small-block preconditioner (iteration parity)."""
+    from oracle.ksvd import ksvd_3d_nested
+    ctx, ora = _pair3d(n, nel, 0.05)
+    rep = ctx.tpp_build_factors()
+    assert rep["num_schur_fail"] == 0
+    v = ctx.views()
+    Az = to_host(v["Az"])
+    A1, B1, A2, B2 = (to_host(v[k]) for k in ("A1", "B1", "A2", "B2"))
+    sigz, cpair = to_host(v["sigz"]), to_host(v["cond"])
+    b = synthetic.rhs(9, ora.ndof)
+    x = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    nl = ora.nloc
+    Ps = []
+    for e in range(ora.mesh.num_elem):
+        for c in range(5):
+            k = e * 5 + c
+            ref = ksvd_3d_nested(ora.small_block(e, c), n)
+            s1 = np.atleast_1d(ref["s1"])[0]
+            assert abs(sigz[k] - s1) <= 1e-12 * s1, (e, c, sigz[k], s1)
+            P = np.kron(Az[k], np.kron(A1[k], B1[k]) + np.kron(A2[k], B2[k]))
+            assert rel(P, ref["P"]) <= 1e-12, (e, c, rel(P, ref["P"]))
+            Ps.append(ref["P"])
+            xr = np.linalg.solve(ref["P"], b[k * nl:(k + 1) * nl])
+            err = rel(x[k * nl:(k + 1) * nl], xr)
+            assert err <= solve_tol(np.linalg.cond(ref["P"]), cpair[k] * np.linalg.cond(Az[k], 1)), (e, c, err)
+
+    def M(vec):
+        out = np.empty_like(vec)
+        for k, P in enumerate(Ps):
+            out[k * nl:(k + 1) * nl] = np.linalg.solve(P, vec[k * nl:(k + 1) * nl])
+        return out
+    S = ora.global_matrix()
+    _, o = gmres(lambda vec: S @ vec, b, M=M, rtol=1e-8)
+    xg, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    assert o["converged"] and r["converged"] and abs(r["iters"] - o["iters"]) <= 1
+    assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
+    print(f"3D Euler n={n}: GMRES K_small {r['iters']} (oracle {o['iters']})")

@@ -180,6 +180,17 @@ def test_system_problem_validation(L):
     assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 4, 0) == 0        # max_restart >= 5
     assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, L.TPP_FEAT_MIXED) == 0
     assert b"TPP_FEAT" in lib.tpp_last_error()
+    # 3D: five components, n <= 12, and a Krylov basis large enough for the diagonal
+    # coefficient scratch, (max_restart + 1) n >= dim (n + 2)
+    nbr3 = np.ascontiguousarray(mesh.periodic_nbr((2, 2, 2)), dtype=np.int32)
+    p3 = dict(dim=3, nc=5, num_elem=8, nbr=nbr3.ctypes.data_as(C.c_void_p))
+    g3 = lib.tpp_sys_workspace_bytes(C.byref(problem(**p3)), 30, 0)
+    assert g3 > 0
+    for bad in (dict(nc=4), dict(n=13)):
+        assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, **bad})), 30, 0) == 0, bad
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 1})), 7, 0) == 0   # 8 < 9
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 1})), 8, 0) > 0
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 12})), 30, 0) > g3
 
 
 def test_batch_and_metric_argument_checks(L):
