@@ -75,6 +75,10 @@ typedef enum {
 #define TPP_FEAT_TIME        16u  /* reserve 6 solution-sized vectors for tpp_time_integrate */
 #define TPP_FEAT_BF16        32u  /* reserve BF16 copies of the apply factors for TPP_BF16
                                      (2D, n <= 16, one-sided form) */
+#define TPP_FEAT_FULL_BLOCKS 64u  /* system contexts (tpp_create_system, 2D, n <= 16): Kronecker
+                                     factors (and, with TPP_FEAT_BLOCK_JACOBI, exact LU) of the
+                                     whole n_c n^2 x n_c n^2 element blocks instead of the
+                                     n_c small ones (Sec. 5.3, Sec. 5.6) */
 
 /*
  * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
@@ -339,18 +343,21 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * F^(u-, u+).n = 1/2 (F(u-) + F(u+)).n + 1/2 lam (u- - u+), lam = max(|v-.n| + c-,
  * |v+.n| + c+) frozen at u0: volume coefficients A_x(u0), A_y(u0) (n_c x n_c per node),
  * face coefficients 1/2 (A_n(u0-) + lam I) on the own trace and 1/2 (A_n(u0+) - lam I)
- * on the neighbour's.  The preconditioners are the paper's "small" ones: the n_c
- * diagonal n^2 x n^2 sub-blocks of every element block (no coupling between
- * components), approximated by the rank-2 Kronecker sum (K_small) or inverted exactly
- * (block Jacobi, J_small).  The coupled "full" Kronecker blocks (A_k of size
- * n_c n) are not built.
+ * on the neighbour's.  By default the preconditioners are the paper's "small" ones:
+ * the n_c diagonal n^d x n^d sub-blocks of every element block (no coupling between
+ * components), approximated by the rank-2 Kronecker sum (K_small, nested in 3D) or
+ * inverted exactly (block Jacobi, J_small, 2D).  With TPP_FEAT_FULL_BLOCKS (2D, n <= 16)
+ * they are the "full" ones: the whole n_c n^2 block approximated by A_1 (x) B_1 +
+ * A_2 (x) B_2 with A_k of size n_c n on the (component, y) index and B_k of size n on
+ * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI).
  *
  * tpp_create_system returns an ordinary context whose elements are the (element,
  * component) pairs e * n_c + c: vectors are [E][n_c][n^dim], tpp_num_elem() is
  * E * n_c, dg_apply_sumfact / dg_apply_sumfact_static apply the coupled S, gmres_solve
  * solves with it, and tpp_build_factors / tpp_apply_inverse / tpp_build_block_jacobi
- * / tpp_apply_block_jacobi act on the small blocks.  Features: TPP_FEAT_TWO_SIDED,
- * TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16 (others: TPP_ERR_INVALID_ARG).  tpp_set_velocity
+ * / tpp_apply_block_jacobi act on the small (or full) blocks.  Features:
+ * TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI (2D), TPP_FEAT_BF16, TPP_FEAT_FULL_BLOCKS
+ * (alone or with TPP_FEAT_BLOCK_JACOBI; others: TPP_ERR_INVALID_ARG).  tpp_set_velocity
  * must not be called on a system context (it would replace the small blocks only).
  */
 #define TPP_FLUX_EULER 1
@@ -557,6 +564,12 @@ typedef struct {
   const double* Qb;      /* [n^2 * r] orthonormal basis, column-major */
   const double* Rb;      /* [r][2 mu + 2] triangular factor of the basis B, row-major */
   const double* qtr;     /* [r] trace of mat(Qb[:, t]) */
+  /* System contexts with TPP_FEAT_FULL_BLOCKS only (NULL otherwise), m = n_c n: the
+   * factors of the whole element blocks, A_k on (component, y), B_k on x, row-major */
+  const double* fA;      /* [E_phys][2][m][m] */
+  const double* fB;      /* [E_phys][2][n][n] */
+  const double* fsig;    /* [E_phys][2] sigma_1, sigma_2 of the rearranged block */
+  const int32_t* fflags; /* [E_phys] bit1 rank-1, bit2 Schur fail, bit3 singular, bit4 relaxed */
 } tpp_views;
 
 tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);

@@ -29,7 +29,9 @@ Pinned in tests/test_oracle_systems.py: the analytic Euler Jacobians against
 finite differences of the flux, the eigenvalues of A_n (v.n - c, v.n, v.n,
 v.n + c), the reduction of a one-component linear "system" (flux a u, lam =
 |a.n|) to the upwind advection operator of oracle/dg.py, discrete conservation of
-every component, and J x against a finite difference of the nonlinear DG residual.
+every component, and J x against a finite difference of the nonlinear DG residual;
+the full-block KSVD against the scalar KSVD for one component and against an exact
+Kronecker block (dt = 0: the mass alone).
 """
 from __future__ import annotations
 
@@ -291,6 +293,17 @@ class LinearizedSystemDG:
         """The component-c diagonal sub-block of S_e (the 'small' block)."""
         S = self.element_block(e)
         return S[c * self.nloc:(c + 1) * self.nloc, c * self.nloc:(c + 1) * self.nloc]
+
+    def full_block_ksvd(self, e: int):
+        """Rank-2 Kronecker approximation of the full block S_e (2D; Sec. 5.3: A_k of
+        size n_c (p+1), B_k of size p+1).  Reading: with the DOF order (component, y, x)
+        the A factor acts on the (component, y) index c n + j and B on x, so the
+        rearrangement is the one of ksvd with m1 = n1 = n_c n, m2 = n2 = n.  Returns
+        (sigma_all, [A_1, A_2], [B_1, B_2])."""
+        assert self.dim == 2
+        from .ksvd import ksvd
+        m = self.nc * self.n
+        return ksvd(self.element_block(e), m, m, self.n, self.n, 2)
 
     def global_matrix(self) -> sp.csr_matrix:
         bs = self.bs

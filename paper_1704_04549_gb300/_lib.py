@@ -17,6 +17,7 @@ TPP_PC_NONE, TPP_PC_KRON, TPP_PC_BLOCK_JACOBI = 0, 1, 2
 TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1, 2, 4, 8
 TPP_FEAT_TIME = 16
 TPP_FEAT_BF16 = 32
+TPP_FEAT_FULL_BLOCKS = 64
 TPP_TS_BACKWARD_EULER, TPP_TS_DIRK3, TPP_TS_RK4 = 0, 1, 2
 
 
@@ -79,7 +80,7 @@ class Views(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in
                 ("sigma", "A1", "B1", "A2", "B2", "SA", "SB", "Q1", "Q2", "T1", "T2", "flags",
                  "cond", "gl_x", "gl_w", "D", "Az", "Azi", "sigz", "zflags", "G", "core", "Qb",
-                 "Rb", "qtr")]
+                 "Rb", "qtr", "fA", "fB", "fsig", "fflags")]
 
 
 EXPORTS = {

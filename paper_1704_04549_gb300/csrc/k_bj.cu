@@ -144,4 +144,17 @@ cudaError_t launch_bj_apply(const tpp_ctx* c, const double* b, double* x, const 
   return cudaGetLastError();
 }
 
+cudaError_t launch_bj_lu(int nb, int64_t nblk, double* LU, int32_t* piv, cudaStream_t s) {
+  k_bj_lu<<<(unsigned)nblk, 256, 0, s>>>(nb, LU, piv);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bj_solve(int nb, int64_t nblk, int R, const double* LU, const int32_t* piv,
+                            const double* b, double* x, const int32_t* skip, cudaStream_t s) {
+  k_bj_solve<<<(unsigned)(nblk * R), 256, nb * sizeof(double), s>>>(nb, LU, piv, b, x, skip, R);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace tpp

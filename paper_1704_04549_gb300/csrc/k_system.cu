@@ -313,8 +313,20 @@ const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t
   if ((int64_t)(max_restart + 1) * p->n < (int64_t)p->dim * p->n + 2 * p->dim || max_restart < 5)
     return "system contexts need max_restart >= 5 (and (max_restart + 1) n >= dim (n + 2))";
   if (features & (TPP_FEAT_MIXED | TPP_FEAT_TIME | TPP_FEAT_LEARNED))
-    return "system contexts support TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI and TPP_FEAT_BF16";
+    return "system contexts support TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16 "
+           "and TPP_FEAT_FULL_BLOCKS";
+  if ((features & TPP_FEAT_BLOCK_JACOBI) && p->dim != 2) return "block Jacobi is 2D only";
+  if ((features & TPP_FEAT_FULL_BLOCKS) &&
+      (p->dim != 2 || p->n > 16 || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16))))
+    return "TPP_FEAT_FULL_BLOCKS: 2D, n <= 16, without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16";
   return nullptr;
+}
+
+// features of the small-block context: the full-block factors and their exact LU live
+// after the coupling arrays instead
+uint32_t small_features(uint32_t f) {
+  if (f & TPP_FEAT_FULL_BLOCKS) f &= ~(TPP_FEAT_FULL_BLOCKS | TPP_FEAT_BLOCK_JACOBI);
+  return f;
 }
 
 tpp_problem small_problem(const tpp_sys_problem* p, const int32_t* iso_nbr) {
@@ -374,9 +386,11 @@ extern "C" size_t tpp_sys_workspace_bytes(const tpp_sys_problem* p, int32_t max_
   }
   std::vector<int32_t> iso((size_t)p->num_elem * p->nc * 2 * p->dim, -1);
   const tpp_problem q = small_problem(p, iso.data());
-  const size_t base = tpp_workspace_bytes(&q, max_restart, features);
+  const size_t base = tpp_workspace_bytes(&q, max_restart, small_features(features));
   if (base == 0) return 0;
-  return sys_layout(base, p->dim, p->n, p->num_elem).total;
+  const size_t tot = sys_layout(base, p->dim, p->n, p->num_elem).total;
+  if (!(features & TPP_FEAT_FULL_BLOCKS)) return tot;
+  return full_layout(tot, p->n, p->num_elem, (features & TPP_FEAT_BLOCK_JACOBI) != 0, nullptr);
 }
 
 extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
@@ -405,14 +419,19 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
     }
   std::vector<int32_t> iso((size_t)E * NC * nf, -1);
   const tpp_problem q = small_problem(p, iso.data());
-  const size_t base = tpp_workspace_bytes(&q, max_restart, features);
+  const uint32_t sf = small_features(features);
+  const bool full = (features & TPP_FEAT_FULL_BLOCKS) != 0;
+  const size_t base = tpp_workspace_bytes(&q, max_restart, sf);
   const SysLayout SL = sys_layout(base, dim, p->n, E);
-  if (base == 0 || ws_bytes < SL.total) {
+  FullOffsets FO;
+  const size_t need =
+      full ? full_layout(SL.total, p->n, E, (features & TPP_FEAT_BLOCK_JACOBI) != 0, &FO) : SL.total;
+  if (base == 0 || ws_bytes < need) {
     set_error("workspace smaller than tpp_sys_workspace_bytes");
     return TPP_ERR_WORKSPACE;
   }
   tpp_ctx* c = nullptr;
-  if (tpp_status st = tpp_create(&c, &q, max_restart, features, workspace, ws_bytes, stream))
+  if (tpp_status st = tpp_create(&c, &q, max_restart, sf, workspace, ws_bytes, stream))
     return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = p->n;
@@ -458,6 +477,12 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
   c->sys_fo = SL.fo;
   c->sys_fn = SL.fn;
   c->sys_nbr = SL.nbr;
+  if (full) {
+    c->sys_full = true;
+    c->sys_full_bj = (features & TPP_FEAT_BLOCK_JACOBI) != 0;
+    c->fb = FO;
+    if ((e = launch_full_basis(c, s)) != cudaSuccess) return fail(e, "full-block basis");
+  }
   *out = c;
   return TPP_OK;
 }

@@ -256,6 +256,10 @@ cudaError_t apply_precond(const tpp_ctx* c, int pc, int prec, const double* b, d
   if (pc == TPP_PC_NONE) {
     return cudaMemcpyAsync(x, b, (size_t)c->N * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
+  if (c->sys_full) {
+    if (pc == TPP_PC_BLOCK_JACOBI) return launch_full_bj_apply(c, b, x, skip, s);
+    return launch_full_apply(c, b, x, skip, s);
+  }
   if (pc == TPP_PC_BLOCK_JACOBI) return launch_bj_apply(c, b, x, skip, s);
   if (prec == TPP_BF16) return launch_apply_bf16(c, b, x, skip, s);
   if (c->dim == 2) return launch_apply_2d(c, b, x, prec, skip, s);
@@ -514,7 +518,10 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
   const DevStatus st0 = fresh_status();
   TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
                "reset status");
-  TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
+  if (c->sys_full)
+    TPP_TRY_CUDA(launch_full_build(c, s), "k_full (full-block factors)");
+  else
+    TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
   return finish_build(c, report, s);
 }
 
@@ -571,11 +578,13 @@ tpp_status tpp_build_factors_learned(tpp_ctx* c, tpp_mlp* net, double threshold,
 
 tpp_status tpp_build_block_jacobi(tpp_ctx* c, void* stream) {
   if (tpp_status r = check_ctx(c)) return r;
-  if (!(c->features & TPP_FEAT_BLOCK_JACOBI)) {
+  if (!(c->features & TPP_FEAT_BLOCK_JACOBI) && !c->sys_full_bj) {
     set_error("context was created without TPP_FEAT_BLOCK_JACOBI");
     return TPP_ERR_INVALID_ARG;
   }
-  TPP_TRY_CUDA(launch_bj_build(c, static_cast<cudaStream_t>(stream)), "block Jacobi build");
+  TPP_TRY_CUDA(c->sys_full_bj ? launch_full_bj_build(c, static_cast<cudaStream_t>(stream))
+                              : launch_bj_build(c, static_cast<cudaStream_t>(stream)),
+               "block Jacobi build");
   c->bj_built = true;
   return TPP_OK;
 }
@@ -633,7 +642,9 @@ tpp_status tpp_apply_block_jacobi(const tpp_ctx* c, const double* b, double* x, 
     return TPP_ERR_INVALID_ARG;
   }
   const tpp_ctx v = call_view(c, nrhs);
-  TPP_TRY_CUDA(launch_bj_apply(&v, b, x, nullptr, static_cast<cudaStream_t>(stream)),
+  TPP_TRY_CUDA(v.sys_full_bj
+                   ? launch_full_bj_apply(&v, b, x, nullptr, static_cast<cudaStream_t>(stream))
+                   : launch_bj_apply(&v, b, x, nullptr, static_cast<cudaStream_t>(stream)),
                "tpp_apply_block_jacobi");
   return TPP_OK;
 }
@@ -722,6 +733,12 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
     o->Qb = c->p<double>(c->L.qb);
     o->Rb = c->p<double>(c->L.rb);
     o->qtr = c->p<double>(c->L.qtr);
+  }
+  if (c->sys_full) {
+    o->fA = c->p<double>(c->fb.A);
+    o->fB = c->p<double>(c->fb.B);
+    o->fsig = c->p<double>(c->fb.sig);
+    o->fflags = c->p<int32_t>(c->fb.flags);
   }
   const Tables* T = c->p<Tables>(c->L.tables);
   o->gl_x = T->x;

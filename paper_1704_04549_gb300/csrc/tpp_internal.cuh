@@ -106,6 +106,12 @@ struct Layout {
   size_t total;
 };
 
+// full multi-component blocks of a 2D system context (k_full.cu): workspace offsets
+struct FullOffsets {
+  size_t QB = 0, RB = 0, rk = 0, A = 0, B = 0, sig = 0, T = 0, Q = 0, Mb = 0, inv = 0,
+         flags = 0, lu = 0, piv = 0, total = 0;
+};
+
 }  // namespace tpp
 
 struct tpp_ctx {
@@ -135,6 +141,10 @@ struct tpp_ctx {
   int32_t sys_nc = 0;
   int64_t sys_E = 0;
   size_t sys_cx = 0, sys_cy = 0, sys_cz = 0, sys_fo = 0, sys_fn = 0, sys_nbr = 0;
+  // TPP_FEAT_FULL_BLOCKS: factors of the whole n_c n^2 blocks (and their exact LU with
+  // TPP_FEAT_BLOCK_JACOBI) replace the small-block ones
+  bool sys_full = false, sys_full_bj = false;
+  tpp::FullOffsets fb;
   int32_t partial_blocks;  // number of CTAs of the reduction kernels
   cudaGraphExec_t gexec[64];   // use_graph: captured Arnoldi step groups, by first step
   int32_t gkernels[64];        // kernels in each (added to the launch count per replay)
@@ -166,6 +176,19 @@ cudaError_t launch_metric_2d(const tpp_ctx* c, const double* jdet, const double*
 // coupled-system operator (k_system.cu); traces tr of x per (element, component) block
 cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                              const int32_t* skip, cudaStream_t s, double mass);
+// full multi-component blocks (k_full.cu); the layout returns its end offset
+size_t full_layout(size_t base, int n, int64_t E, bool bj, FullOffsets* out);
+cudaError_t launch_full_basis(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_full_build(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_full_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
+                              cudaStream_t s);
+cudaError_t launch_full_bj_build(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_full_bj_apply(const tpp_ctx* c, const double* b, double* x,
+                                 const int32_t* skip, cudaStream_t s);
+// dense LU with partial pivoting of nblk row-major nb x nb blocks, and the solves
+cudaError_t launch_bj_lu(int nb, int64_t nblk, double* LU, int32_t* piv, cudaStream_t s);
+cudaError_t launch_bj_solve(int nb, int64_t nblk, int R, const double* LU, const int32_t* piv,
+                            const double* b, double* x, const int32_t* skip, cudaStream_t s);
 // over-integration (mu > n, 2D; k_overint.cu)
 struct MuTables {        // the mu-point rule and the nodal basis at its points
   double x[TPP_MAX_MU], w[TPP_MAX_MU];

@@ -419,6 +419,12 @@ class Context:
             res["Azi"] = grab(v.Azi, E * n * n, torch.float64).view(E, n, n).transpose(1, 2)
             res["sigz"] = grab(v.sigz, E, torch.float64)
             res["zflags"] = grab(v.zflags, E, torch.int32)
+        if v.fA:                       # full multi-component blocks (row-major factors)
+            Ep, m = self.num_elem // (self.dim + 2), (self.dim + 2) * n
+            res["fA"] = grab(v.fA, Ep * 2 * m * m, torch.float64).view(Ep, 2, m, m)
+            res["fB"] = grab(v.fB, Ep * 2 * n * n, torch.float64).view(Ep, 2, n, n)
+            res["fsig"] = grab(v.fsig, Ep * 2, torch.float64).view(Ep, 2)
+            res["fflags"] = grab(v.fflags, Ep, torch.int32)
         torch.cuda.synchronize(self.device)
         return res
 

@@ -163,6 +163,83 @@ def test_nearly_defective_density_blocks():
           f"{worst:.1e}; GMRES {r['iters']} (oracle {o['iters']})")
 
 
+# ---- full blocks (Sec. 5.3: A_k of size n_c (p+1), B_k of size p+1) ------------------
+FULL_CASES = [(2, (3, 2), 5.0), (3, (3, 3), 2.5), (4, (4, 3), 2.5), (8, (4, 4), 2.5),
+              (16, (2, 2), 5.0)]
+
+
+@pytest.mark.parametrize("n,nel,h", FULL_CASES)
+def test_full_block_factors_apply_and_jacobi(n, nel, h):
+    """K_full and J_full: the factors of every element's whole n_c n^2 block against the
+    oracle's rank-2 KSVD with the (component, y) x (x) split, their inverse, and the exact
+    full-block LU."""
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS
+    ctx, ora = _pair(n, nel, h, 0.1, features=TPP_FEAT_FULL_BLOCKS | TPP_FEAT_BLOCK_JACOBI)
+    rep = ctx.tpp_build_factors()
+    assert rep["num_schur_fail"] == 0
+    ctx.tpp_build_block_jacobi()
+    v = ctx.views()
+    fA, fB, fsig = to_host(v["fA"]), to_host(v["fB"]), to_host(v["fsig"])
+    fflags = to_host(v["fflags"])
+    b = synthetic.rhs(19, ora.ndof)
+    xk = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    xj = to_host(ctx.tpp_apply_block_jacobi(to_dev(b)))
+    bs = ora.bs
+    worst_P, worst_x = 0.0, 0.0
+    for e in range(ora.mesh.num_elem):
+        s_ref, As, Bs = ora.full_block_ksvd(e)
+        assert abs(fsig[e, 0] - s_ref[0]) <= 1e-12 * s_ref[0], (e, fsig[e], s_ref[:2])
+        assert abs(fsig[e, 1] - s_ref[1]) <= 1e-12 * s_ref[0], (e, fsig[e], s_ref[:2])
+        P_ref = kron_sum(As, Bs)
+        P = np.kron(fA[e, 0], fB[e, 0]) + np.kron(fA[e, 1], fB[e, 1])
+        worst_P = max(worst_P, rel(P, P_ref))
+        assert rel(P, P_ref) <= 1e-13, (e, rel(P, P_ref))     # measured <= 1.1e-14
+        blk = slice(e * bs, (e + 1) * bs)
+        err = rel(xk[blk], np.linalg.solve(P_ref, b[blk]))
+        worst_x = max(worst_x, err)
+        assert err <= solve_tol(np.linalg.cond(P_ref)), (e, err)
+        Se = ora.element_block(e)
+        assert rel(xj[blk], np.linalg.solve(Se, b[blk])) <= FP64_TOL * np.linalg.cond(Se)
+        assert fflags[e] & 12 == 0
+    print(f"full blocks n={n}: max relative error of P {worst_P:.1e}, of P^-1 b {worst_x:.1e}")
+
+
+@pytest.mark.parametrize("n,nel,h,dt", [(4, (4, 3), 2.5, 0.1), (8, (4, 4), 2.5, 0.1),
+                                         (8, (4, 4), 2.5, 0.01), (12, (3, 3), 2.5, 0.1)])
+def test_gmres_with_full_block_preconditioners(n, nel, h, dt):
+    """GMRES iteration counts with K_full and J_full equal to the oracle's (+-1)."""
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS
+    ctx, ora = _pair(n, nel, h, dt, features=TPP_FEAT_FULL_BLOCKS | TPP_FEAT_BLOCK_JACOBI)
+    ctx.tpp_build_factors()
+    ctx.tpp_build_block_jacobi()
+    S = ora.global_matrix()
+    b = synthetic.rhs(11, ora.ndof)
+    bs = ora.bs
+    its = {}
+    for kind, pc in (("K", TPP_PC_KRON), ("J", TPP_PC_BLOCK_JACOBI)):
+        inv = []
+        for e in range(ora.mesh.num_elem):
+            if kind == "K":
+                _, As, Bs = ora.full_block_ksvd(e)
+                inv.append(np.linalg.inv(kron_sum(As, Bs)))
+            else:
+                inv.append(np.linalg.inv(ora.element_block(e)))
+
+        def M(vec, inv=inv):
+            out = np.empty_like(vec)
+            for k, Pi in enumerate(inv):
+                out[k * bs:(k + 1) * bs] = Pi @ vec[k * bs:(k + 1) * bs]
+            return out
+        _, o = gmres(lambda vec: S @ vec, b, M=M, rtol=1e-8)
+        x, r = ctx.gmres_solve(to_dev(b), pc=pc, rtol=1e-8)
+        assert o["converged"] and r["converged"]
+        assert np.linalg.norm(b - S @ to_host(x)) <= 1.0001e-8 * np.linalg.norm(b)
+        assert abs(r["iters"] - o["iters"]) <= 1, (kind, r["iters"], o["iters"])
+        its[kind] = (r["iters"], o["iters"])
+    print(f"Euler vortex n={n} dt={dt}: GMRES(30) iterations (GPU, oracle) K_full {its['K']}, "
+          f"J_full {its['J']}")
+
+
 # ---- 3D: five components (Sec. 5.6's periodic Euler case) -----------------------------
 def _state3d(n, nel, h, L):
     xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)

@@ -168,3 +168,34 @@ def test_3d_conservation_and_residual():
     U0 = sysdg.U0.reshape(-1)
     fd = (sysdg.residual(U0 + eps * x, lam) - sysdg.residual(U0 - eps * x, lam)) / (2 * eps)
     assert np.linalg.norm(fd - D @ x) <= 1e-6 * np.linalg.norm(D @ x)
+
+
+# ---- full-block KSVD (Sec. 5.3: A_k of size n_c (p+1)) ---------------------------
+def test_full_block_ksvd_reduces_to_the_scalar_ksvd():
+    """One component: the full block is the scalar block and its KSVD the scalar one."""
+    from oracle.ksvd import kron_sum, ksvd_2d
+    mesh = PeriodicMesh((3, 2), 0.5)
+    n = 4
+    sysdg = LinearizedSystemDG(mesh, n, 0.1, LinearAdvectionFlux((1.0, -0.4)),
+                               np.zeros((mesh.num_elem, 1, n * n)))
+    for e in (0, 4):
+        s, As, Bs = sysdg.full_block_ksvd(e)
+        s_ref, Ar, Br = ksvd_2d(sysdg.element_block(e), n)
+        assert np.abs(s[:2] - s_ref[:2]).max() <= 1e-13 * s_ref[0]
+        P, Pr = kron_sum(As, Bs), kron_sum(Ar, Br)
+        assert np.abs(P - Pr).max() <= 1e-12 * np.abs(Pr).max()
+
+
+def test_full_block_ksvd_exact_for_the_mass():
+    """dt = 0: S_e = I_(n_c) (x) h^2 diag(w) (x) diag(w) = (I (x) h^2 diag(w)) (x) diag(w),
+    rank 1 in the (component, y) x (x) split: the approximation is exact and
+    sigma_1 = h^2 ||w||^2 sqrt(n_c)."""
+    from oracle.ksvd import kron_sum
+    n, h = 5, 2.5
+    sysdg = vortex_system((3, 3), h, n, 0.0, synthetic.euler_vortex_state)
+    s, As, Bs = sysdg.full_block_ksvd(4)
+    S = sysdg.element_block(4)
+    assert np.abs(kron_sum(As, Bs) - S).max() <= 1e-13 * np.abs(S).max()
+    w = 0.5 * np.polynomial.legendre.leggauss(n)[1]
+    assert abs(s[0] - h * h * np.sum(w * w) * 2.0) <= 1e-13 * s[0]
+    assert s[1] <= 1e-13 * s[0]
