@@ -540,12 +540,13 @@ def run_euler(args):
 def euler_record(dev):
     """2D Euler equations linearised around the vortex of Sec. 5.3 at t = 0: 16 x 12
     periodic mesh of the 20 x 15 domain (h = 1.25), n = 8 (p = 7), one backward Euler
-    system per dt; GMRES(30) to 1e-8 with the small-block Kronecker (K_small) and the
-    small-block Jacobi (J_small) preconditioners.  Times with CUDA events."""
+    system per dt; GMRES(30) to 1e-8 with the Kronecker (K) and exact block Jacobi (J)
+    preconditioners on the small (per-component) blocks and on the full n_c n^2 blocks.
+    Times with CUDA events."""
     import numpy as np
     import torch
-    from paper_1704_04549_gb300 import (TPP_FEAT_BLOCK_JACOBI, TPP_PC_BLOCK_JACOBI,
-                                        TPP_PC_KRON, Context)
+    from paper_1704_04549_gb300 import (TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_FULL_BLOCKS,
+                                        TPP_PC_BLOCK_JACOBI, TPP_PC_KRON, Context)
     nel, h, n = (16, 12), 1.25, 8
     xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
     E = nel[0] * nel[1]
@@ -557,26 +558,29 @@ def euler_record(dev):
     stream = torch.cuda.current_stream(dev)
     out = {"dofs": E * 4 * n * n}
     for dt in (0.1, 0.01):
-        ctx = Context.euler_system(n, nel, h, dt, state, features=TPP_FEAT_BLOCK_JACOBI,
-                                   device=str(dev))
-        b = torch.as_tensor(synthetic.rhs(1713, ctx.num_dofs), device=dev)
         rec = {}
-        for name, pc, build in (("K_small", TPP_PC_KRON, ctx.tpp_build_factors),
-                                ("J_small", TPP_PC_BLOCK_JACOBI, ctx.tpp_build_block_jacobi)):
-            build()
-            x = torch.zeros_like(b)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            build()
-            _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=3000, pc=pc,
-                                   check=False)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            rec[name] = {"iters": r["iters"], "converged": bool(r["converged"]),
-                         "true_rel_res": r["true_rel_res"], "build_solve_ms": e0.elapsed_time(e1)}
+        for blocks, extra in (("small", 0), ("full", TPP_FEAT_FULL_BLOCKS)):
+            ctx = Context.euler_system(n, nel, h, dt, state,
+                                       features=TPP_FEAT_BLOCK_JACOBI | extra, device=str(dev))
+            b = torch.as_tensor(synthetic.rhs(1713, ctx.num_dofs), device=dev)
+            for kind, pc, build in (("K", TPP_PC_KRON, ctx.tpp_build_factors),
+                                    ("J", TPP_PC_BLOCK_JACOBI, ctx.tpp_build_block_jacobi)):
+                build()
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                build()
+                _, r = ctx.gmres_solve(b, x, restart=30, rtol=1e-8, max_iters=3000, pc=pc,
+                                       check=False)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                rec[f"{kind}_{blocks}"] = {"iters": r["iters"], "converged": bool(r["converged"]),
+                                           "true_rel_res": r["true_rel_res"],
+                                           "build_solve_ms": e0.elapsed_time(e1)}
+            del ctx
         out[f"dt={dt}"] = rec
-        del ctx
     return out
 
 

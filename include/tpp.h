@@ -67,7 +67,7 @@ typedef enum {
 } tpp_pc;
 
 /* Feature bits for tpp_workspace_bytes / tpp_create. */
-#define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^4 doubles per element for exact block Jacobi (2D only) */
+#define TPP_FEAT_BLOCK_JACOBI 1u  /* reserve n^(2d) doubles per element for exact block Jacobi */
 #define TPP_FEAT_MIXED        2u  /* reserve float32 copies of the Kronecker apply factors */
 #define TPP_FEAT_TWO_SIDED    4u  /* apply by the paper's two-sided Schur form (quasi-triangular
                                      Sylvester solve) instead of the default one-sided form */
@@ -346,7 +346,7 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * on the neighbour's.  By default the preconditioners are the paper's "small" ones:
  * the n_c diagonal n^d x n^d sub-blocks of every element block (no coupling between
  * components), approximated by the rank-2 Kronecker sum (K_small, nested in 3D) or
- * inverted exactly (block Jacobi, J_small, 2D).  With TPP_FEAT_FULL_BLOCKS (2D, n <= 16)
+ * inverted exactly (block Jacobi, J_small).  With TPP_FEAT_FULL_BLOCKS (2D, n <= 16)
  * they are the "full" ones: the whole n_c n^2 block approximated by A_1 (x) B_1 +
  * A_2 (x) B_2 with A_k of size n_c n on the (component, y) index and B_k of size n on
  * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI).
@@ -356,7 +356,7 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * E * n_c, dg_apply_sumfact / dg_apply_sumfact_static apply the coupled S, gmres_solve
  * solves with it, and tpp_build_factors / tpp_apply_inverse / tpp_build_block_jacobi
  * / tpp_apply_block_jacobi act on the small (or full) blocks.  Features:
- * TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI (2D), TPP_FEAT_BF16, TPP_FEAT_FULL_BLOCKS
+ * TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16, TPP_FEAT_FULL_BLOCKS
  * (alone or with TPP_FEAT_BLOCK_JACOBI; others: TPP_ERR_INVALID_ARG).  tpp_set_velocity
  * must not be called on a system context (it would replace the small blocks only).
  */

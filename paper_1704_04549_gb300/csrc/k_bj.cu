@@ -1,6 +1,6 @@
 // Exact block-Jacobi comparator (Sec. 5: "exact block Jacobi" preconditioner).
 //
-// Each diagonal block S_e (n^2 x n^2 in 2D) is assembled entry by entry from
+// Each diagonal block S_e (n^2 x n^2 in 2D, n^3 x n^3 in 3D) is assembled entry by entry from
 // the precomputed flux Jacobians (Eq. jac-entries with collocated quadrature):
 //   S[(i,j),(k,l)] = h^2 w_i w_j d_ik d_jl
 //     + d_lj (D_ki cx_kj + l1_i l1_k max(an_+x,j, 0) + l0_i l0_k max(an_-x,j, 0))
@@ -34,6 +34,43 @@ __global__ void k_bj_assemble_2d(const Tables* T, int n, double h, const double*
       v += T->D[l * n + j] * cy[e * nn + i + n * l];
       v += T->l1[j] * T->l1[l] * fmax(fe[3 * n + i], 0.0);
       v += T->l0[j] * T->l0[l] * fmax(fe[2 * n + i], 0.0);
+    }
+    A[q] = v;
+  }
+}
+
+// The 3D block (n^3 x n^3, node i + n j + n^2 k), the same terms in three directions:
+//   S[(i,j,k),(i',j',k')] = h^3 w_i w_j w_k d_ii' d_jj' d_kk'
+//     + d_jj' d_kk' (D_i'i cx_i'jk + l1_i l1_i' max(an_+x,jk, 0) + l0_i l0_i' max(an_-x,jk, 0))
+//     + d_ii' d_kk' (D_j'j cy_ij'k + l1_j l1_j' max(an_+y,ik, 0) + l0_j l0_j' max(an_-y,ik, 0))
+//     + d_ii' d_jj' (D_k'k cz_ijk' + l1_k l1_k' max(an_+z,ij, 0) + l0_k l0_k' max(an_-z,ij, 0)).
+__global__ void k_bj_assemble_3d(const Tables* T, int n, double h, const double* cx,
+                                 const double* cy, const double* cz, const double* fa,
+                                 double* LU) {
+  const int nn = n * n, n3 = nn * n;
+  const int64_t e = blockIdx.x;
+  const double* fe = fa + e * 6 * nn;
+  const double* ce[3] = {cx + e * n3, cy + e * n3, cz + e * n3};
+  double* A = LU + e * (int64_t)n3 * n3;
+  const double h3 = h * h * h;
+  for (int64_t q = threadIdx.x; q < (int64_t)n3 * n3; q += blockDim.x) {
+    const int row = (int)(q / n3), col = (int)(q % n3);
+    const int r3[3] = {row % n, (row / n) % n, row / nn};
+    const int c3[3] = {col % n, (col / n) % n, col / nn};
+    double v = 0.0;
+    if (row == col) v += h3 * T->w[r3[0]] * T->w[r3[1]] * T->w[r3[2]];
+    for (int d = 0; d < 3; ++d) {
+      const int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+      if (r3[o1] != c3[o1] || r3[o2] != c3[o2]) continue;
+      const int a = r3[d], ap = c3[d];
+      int node[3] = {r3[0], r3[1], r3[2]};
+      node[d] = ap;                                   // the coefficient sits at the column node
+      v += T->D[ap * n + a] * ce[d][node[0] + n * node[1] + nn * node[2]];
+      // tangential index of the face points: the two other directions, lower first
+      const int lo = (d == 0) ? 1 : 0, hi = (d == 2) ? 1 : 2;
+      const int t = r3[lo] + n * r3[hi];
+      v += T->l0[a] * T->l0[ap] * fmax(fe[(2 * d) * nn + t], 0.0);
+      v += T->l1[a] * T->l1[ap] * fmax(fe[(2 * d + 1) * nn + t], 0.0);
     }
     A[q] = v;
   }
@@ -122,7 +159,19 @@ __global__ void k_bj_solve(int nb, const double* LU, const int32_t* piv, const d
 }
 
 cudaError_t launch_bj_build(const tpp_ctx* c, cudaStream_t s) {
-  if (c->dim != 2) return cudaErrorNotSupported;
+  if (c->dim == 3) {
+    k_bj_assemble_3d<<<(unsigned)c->E, 256, 0, s>>>(
+        c->p<Tables>(c->L.tables), c->n, c->prob.h, c->p<double>(c->L.cx),
+        c->p<double>(c->L.cy), c->p<double>(c->L.cz), c->p<double>(c->L.fa),
+        c->p<double>(c->L.bj_lu));
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bj_lu<<<(unsigned)c->E, 256, 0, s>>>(c->nloc, c->p<double>(c->L.bj_lu),
+                                           c->p<int32_t>(c->L.bj_piv));
+    count_launch();
+    return cudaGetLastError();
+  }
   k_bj_assemble_2d<<<(unsigned)c->E, 256, 0, s>>>(
       c->p<Tables>(c->L.tables), c->n, c->prob.h, c->p<double>(c->L.cx), c->p<double>(c->L.cy),
       c->p<double>(c->L.fa), c->p<double>(c->L.bj_lu),

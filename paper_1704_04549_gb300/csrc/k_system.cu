@@ -315,7 +315,6 @@ const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t
   if (features & (TPP_FEAT_MIXED | TPP_FEAT_TIME | TPP_FEAT_LEARNED))
     return "system contexts support TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16 "
            "and TPP_FEAT_FULL_BLOCKS";
-  if ((features & TPP_FEAT_BLOCK_JACOBI) && p->dim != 2) return "block Jacobi is 2D only";
   if ((features & TPP_FEAT_FULL_BLOCKS) &&
       (p->dim != 2 || p->n > 16 || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16))))
     return "TPP_FEAT_FULL_BLOCKS: 2D, n <= 16, without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16";

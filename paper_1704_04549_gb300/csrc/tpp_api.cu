@@ -308,10 +308,6 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
               "integration (its mass matrix is not diagonal) or the BF16 apply");
     return TPP_ERR_UNSUPPORTED;
   }
-  if (prob->dim == 3 && (features & TPP_FEAT_BLOCK_JACOBI)) {
-    set_error("exact block Jacobi is implemented for 2D problems only");
-    return TPP_ERR_UNSUPPORTED;
-  }
   if (!prob->nbr) {
     set_error("nbr is NULL");
     return TPP_ERR_INVALID_ARG;

@@ -279,9 +279,11 @@ def test_3d_small_block_factors_and_gmres(n, nel):
     """The nested 3D KSVD (Sec. 4.3) of every small block against the oracle's, and GMRES
     on the coupled system with the small-block preconditioner (iteration parity)."""
     from oracle.ksvd import ksvd_3d_nested
-    ctx, ora = _pair3d(n, nel, 0.05)
+    ctx, ora = _pair3d(n, nel, 0.05, features=TPP_FEAT_BLOCK_JACOBI)
     rep = ctx.tpp_build_factors()
     assert rep["num_schur_fail"] == 0
+    ctx.tpp_build_block_jacobi()
+    xj = to_host(ctx.tpp_apply_block_jacobi(to_dev(synthetic.rhs(9, ora.ndof))))
     v = ctx.views()
     Az = to_host(v["Az"])
     A1, B1, A2, B2 = (to_host(v[k]) for k in ("A1", "B1", "A2", "B2"))
@@ -302,6 +304,9 @@ def test_3d_small_block_factors_and_gmres(n, nel):
             xr = np.linalg.solve(ref["P"], b[k * nl:(k + 1) * nl])
             err = rel(x[k * nl:(k + 1) * nl], xr)
             assert err <= solve_tol(np.linalg.cond(ref["P"]), cpair[k] * np.linalg.cond(Az[k], 1)), (e, c, err)
+            Ssm = ora.small_block(e, c)                       # J_small in 3D
+            assert rel(xj[k * nl:(k + 1) * nl], np.linalg.solve(Ssm, b[k * nl:(k + 1) * nl])) <= \
+                FP64_TOL * np.linalg.cond(Ssm)
 
     def M(vec):
         out = np.empty_like(vec)
