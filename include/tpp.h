@@ -75,10 +75,10 @@ typedef enum {
 #define TPP_FEAT_TIME        16u  /* reserve 6 solution-sized vectors for tpp_time_integrate */
 #define TPP_FEAT_BF16        32u  /* reserve BF16 copies of the apply factors for TPP_BF16
                                      (2D, n <= 16, one-sided form) */
-#define TPP_FEAT_FULL_BLOCKS 64u  /* system contexts (tpp_create_system, 2D, n <= 16): Kronecker
-                                     factors (and, with TPP_FEAT_BLOCK_JACOBI, exact LU) of the
-                                     whole n_c n^2 x n_c n^2 element blocks instead of the
-                                     n_c small ones (Sec. 5.3, Sec. 5.6) */
+#define TPP_FEAT_FULL_BLOCKS 64u  /* system contexts (tpp_create_system): Kronecker factors
+                                     (2D, n <= 16) and, with TPP_FEAT_BLOCK_JACOBI, exact LU
+                                     (2D, n <= 16; 3D, n <= 6) of the whole n_c n^d element
+                                     blocks instead of the n_c small ones (Sec. 5.3, 5.6) */
 
 /*
  * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
@@ -346,10 +346,12 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * on the neighbour's.  By default the preconditioners are the paper's "small" ones:
  * the n_c diagonal n^d x n^d sub-blocks of every element block (no coupling between
  * components), approximated by the rank-2 Kronecker sum (K_small, nested in 3D) or
- * inverted exactly (block Jacobi, J_small).  With TPP_FEAT_FULL_BLOCKS (2D, n <= 16)
- * they are the "full" ones: the whole n_c n^2 block approximated by A_1 (x) B_1 +
+ * inverted exactly (block Jacobi, J_small).  With TPP_FEAT_FULL_BLOCKS they are the
+ * "full" ones: in 2D (n <= 16) the whole n_c n^2 block approximated by A_1 (x) B_1 +
  * A_2 (x) B_2 with A_k of size n_c n on the (component, y) index and B_k of size n on
- * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI).
+ * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI); in 3D (n <= 6,
+ * with TPP_FEAT_BLOCK_JACOBI) the exact J_full only, tpp_build_factors then returning
+ * TPP_ERR_UNSUPPORTED.
  *
  * tpp_create_system returns an ordinary context whose elements are the (element,
  * component) pairs e * n_c + c: vectors are [E][n_c][n^dim], tpp_num_elem() is

@@ -662,6 +662,40 @@ __global__ void __launch_bounds__(256) k_full_apply(FullApplyArgs P) {
   }
 }
 
+// the whole 3D n_c n^3 x n_c n^3 block (n_c = 5, node (c, k, j, i)), row-major: in each
+// direction d the volume term D[a'][a] cd[c][c'](node at a') and the two own-face terms,
+// the other two node coordinates equal
+__global__ void k_full_bj_assemble_3d(const Tables* T, int n, double hd, const double* cx,
+                                      const double* cy, const double* cz, const double* fo,
+                                      double* LU) {
+  constexpr int NC = 5;
+  const int nn = n * n, n3 = nn * n, nb = NC * n3;
+  const int64_t e = blockIdx.x;
+  const double* fe = fo + e * 6 * NC * NC * nn;
+  const double* cd[3] = {cx, cy, cz};
+  double* Ae = LU + e * (int64_t)nb * nb;
+  for (int64_t q = threadIdx.x; q < (int64_t)nb * nb; q += blockDim.x) {
+    const int row = (int)(q / nb), col = (int)(q % nb);
+    const int c = row / n3, cp = col / n3, rn = row % n3, cn = col % n3;
+    const int r3[3] = {rn % n, (rn / n) % n, rn / nn};
+    const int c3[3] = {cn % n, (cn / n) % n, cn / nn};
+    const int cc = c * NC + cp;
+    double v = 0.0;
+    if (row == col) v += hd * T->w[r3[0]] * T->w[r3[1]] * T->w[r3[2]];
+    for (int d = 0; d < 3; ++d) {
+      const int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+      if (r3[o1] != c3[o1] || r3[o2] != c3[o2]) continue;
+      const int a = r3[d], ap = c3[d];
+      v += T->D[ap * n + a] * cd[d][(e * NC * NC + cc) * (int64_t)n3 + cn];
+      const int lo = (d == 0) ? 1 : 0, hi = (d == 2) ? 1 : 2;
+      const int t = r3[lo] + n * r3[hi];
+      v += T->l0[a] * T->l0[ap] * fe[((2 * d) * NC * NC + cc) * nn + t];
+      v += T->l1[a] * T->l1[ap] * fe[((2 * d + 1) * NC * NC + cc) * nn + t];
+    }
+    Ae[q] = v;
+  }
+}
+
 // the whole n_c n^2 x n_c n^2 block of element e, row-major, for exact block Jacobi
 __global__ void k_full_bj_assemble(const Tables* T, int n, double hd, const double* cx,
                                    const double* cy, const double* fo, double* LU) {
@@ -696,12 +730,21 @@ __global__ void k_full_bj_assemble(const Tables* T, int n, double hd, const doub
 
 namespace tpp {
 
-size_t full_layout(size_t base, int n, int64_t E, bool bj, FullOffsets* out) {
+size_t full_layout(size_t base, int dim, int n, int64_t E, bool bj, FullOffsets* out) {
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t nn = (size_t)n * n, m = (size_t)kNcFull * n, r = (size_t)full_r(n);
-  const size_t nb = (size_t)kNcFull * nn, Ez = (size_t)E;
+  const size_t Ez = (size_t)E;
   FullOffsets L;
   size_t o = al(base);
+  if (dim == 3) {                 // exact full-block Jacobi only: n_c = 5, blocks of 5 n^3
+    const size_t nb = 5 * nn * (size_t)n;
+    L.lu = bj ? o : 0; o += bj ? al(Ez * nb * nb * 8) : 0;
+    L.piv = bj ? o : 0; o += bj ? al(Ez * nb * 4) : 0;
+    L.total = o;
+    if (out) *out = L;
+    return o;
+  }
+  const size_t nb = (size_t)kNcFull * nn;
   L.QB = o; o += al(nn * r * 8);
   L.RB = o; o += al(r * r * 8);
   L.rk = o; o += 256;
@@ -796,21 +839,32 @@ cudaError_t launch_full_apply(const tpp_ctx* c, const double* b, double* x, cons
   return cudaGetLastError();
 }
 
+// rows of a full block: n_c n^dim
+static int full_nb(const tpp_ctx* c) {
+  return c->sys_nc * (c->dim == 2 ? c->n * c->n : c->n * c->n * c->n);
+}
+
 cudaError_t launch_full_bj_build(const tpp_ctx* c, cudaStream_t s) {
   const int n = c->n;
-  k_full_bj_assemble<<<(unsigned)c->sys_E, 256, 0, s>>>(
-      c->p<Tables>(c->L.tables), n, c->prob.h * c->prob.h, c->p<double>(c->sys_cx),
-      c->p<double>(c->sys_cy), c->p<double>(c->sys_fo), c->p<double>(c->fb.lu));
+  const double h = c->prob.h;
+  if (c->dim == 2)
+    k_full_bj_assemble<<<(unsigned)c->sys_E, 256, 0, s>>>(
+        c->p<Tables>(c->L.tables), n, h * h, c->p<double>(c->sys_cx), c->p<double>(c->sys_cy),
+        c->p<double>(c->sys_fo), c->p<double>(c->fb.lu));
+  else
+    k_full_bj_assemble_3d<<<(unsigned)c->sys_E, 256, 0, s>>>(
+        c->p<Tables>(c->L.tables), n, h * h * h, c->p<double>(c->sys_cx),
+        c->p<double>(c->sys_cy), c->p<double>(c->sys_cz), c->p<double>(c->sys_fo),
+        c->p<double>(c->fb.lu));
   count_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_bj_lu(kNcFull * n * n, c->sys_E, c->p<double>(c->fb.lu),
-                      c->p<int32_t>(c->fb.piv), s);
+  return launch_bj_lu(full_nb(c), c->sys_E, c->p<double>(c->fb.lu), c->p<int32_t>(c->fb.piv), s);
 }
 
 cudaError_t launch_full_bj_apply(const tpp_ctx* c, const double* b, double* x,
                                  const int32_t* skip, cudaStream_t s) {
-  return launch_bj_solve(kNcFull * c->n * c->n, c->sys_E, 1, c->p<double>(c->fb.lu),
+  return launch_bj_solve(full_nb(c), c->sys_E, 1, c->p<double>(c->fb.lu),
                          c->p<int32_t>(c->fb.piv), b, x, skip, s);
 }
 

@@ -315,9 +315,13 @@ const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t
   if (features & (TPP_FEAT_MIXED | TPP_FEAT_TIME | TPP_FEAT_LEARNED))
     return "system contexts support TPP_FEAT_TWO_SIDED, TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_BF16 "
            "and TPP_FEAT_FULL_BLOCKS";
-  if ((features & TPP_FEAT_FULL_BLOCKS) &&
-      (p->dim != 2 || p->n > 16 || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16))))
-    return "TPP_FEAT_FULL_BLOCKS: 2D, n <= 16, without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16";
+  if ((features & TPP_FEAT_FULL_BLOCKS) && p->dim == 2 &&
+      (p->n > 16 || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16))))
+    return "TPP_FEAT_FULL_BLOCKS in 2D: n <= 16, without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16";
+  if ((features & TPP_FEAT_FULL_BLOCKS) && p->dim == 3 &&
+      (p->n > 6 || !(features & TPP_FEAT_BLOCK_JACOBI)))
+    return "TPP_FEAT_FULL_BLOCKS in 3D: exact full-block Jacobi (needs TPP_FEAT_BLOCK_JACOBI), "
+           "n <= 6";
   return nullptr;
 }
 
@@ -389,7 +393,8 @@ extern "C" size_t tpp_sys_workspace_bytes(const tpp_sys_problem* p, int32_t max_
   if (base == 0) return 0;
   const size_t tot = sys_layout(base, p->dim, p->n, p->num_elem).total;
   if (!(features & TPP_FEAT_FULL_BLOCKS)) return tot;
-  return full_layout(tot, p->n, p->num_elem, (features & TPP_FEAT_BLOCK_JACOBI) != 0, nullptr);
+  return full_layout(tot, p->dim, p->n, p->num_elem, (features & TPP_FEAT_BLOCK_JACOBI) != 0,
+                     nullptr);
 }
 
 extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
@@ -424,7 +429,8 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
   const SysLayout SL = sys_layout(base, dim, p->n, E);
   FullOffsets FO;
   const size_t need =
-      full ? full_layout(SL.total, p->n, E, (features & TPP_FEAT_BLOCK_JACOBI) != 0, &FO) : SL.total;
+      full ? full_layout(SL.total, dim, p->n, E, (features & TPP_FEAT_BLOCK_JACOBI) != 0, &FO)
+           : SL.total;
   if (base == 0 || ws_bytes < need) {
     set_error("workspace smaller than tpp_sys_workspace_bytes");
     return TPP_ERR_WORKSPACE;
@@ -480,7 +486,7 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
     c->sys_full = true;
     c->sys_full_bj = (features & TPP_FEAT_BLOCK_JACOBI) != 0;
     c->fb = FO;
-    if ((e = launch_full_basis(c, s)) != cudaSuccess) return fail(e, "full-block basis");
+    if (dim == 2 && (e = launch_full_basis(c, s)) != cudaSuccess) return fail(e, "full-block basis");
   }
   *out = c;
   return TPP_OK;

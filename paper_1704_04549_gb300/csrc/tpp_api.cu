@@ -514,6 +514,11 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
   const DevStatus st0 = fresh_status();
   TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
                "reset status");
+  if (c->sys_full && c->dim == 3) {
+    set_error("the full-block Kronecker factors are built in 2D only (3D: TPP_FEAT_FULL_BLOCKS "
+              "gives exact full-block Jacobi)");
+    return TPP_ERR_UNSUPPORTED;
+  }
   if (c->sys_full)
     TPP_TRY_CUDA(launch_full_build(c, s), "k_full (full-block factors)");
   else

@@ -177,7 +177,7 @@ cudaError_t launch_metric_2d(const tpp_ctx* c, const double* jdet, const double*
 cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr, double* y,
                              const int32_t* skip, cudaStream_t s, double mass);
 // full multi-component blocks (k_full.cu); the layout returns its end offset
-size_t full_layout(size_t base, int n, int64_t E, bool bj, FullOffsets* out);
+size_t full_layout(size_t base, int dim, int n, int64_t E, bool bj, FullOffsets* out);
 cudaError_t launch_full_basis(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_full_build(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_full_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,

@@ -319,3 +319,35 @@ def test_3d_small_block_factors_and_gmres(n, nel):
     assert o["converged"] and r["converged"] and abs(r["iters"] - o["iters"]) <= 1
     assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
     print(f"3D Euler n={n}: GMRES K_small {r['iters']} (oracle {o['iters']})")
+
+
+@pytest.mark.parametrize("n,nel", [(2, (2, 2, 2)), (3, (2, 2, 2)), (5, (2, 2, 1))])
+def test_3d_full_block_jacobi(n, nel):
+    """J_full in 3D (Sec. 5.6, the 5 (p+1)^3 blocks): exact LU of every element's whole
+    block against a dense solve with the oracle's, and GMRES iteration parity."""
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS, TppError
+    ctx, ora = _pair3d(n, nel, 0.05, features=TPP_FEAT_FULL_BLOCKS | TPP_FEAT_BLOCK_JACOBI)
+    with pytest.raises(TppError):                 # the full-block Kronecker factors are 2D
+        ctx.tpp_build_factors()
+    ctx.tpp_build_block_jacobi()
+    b = synthetic.rhs(23, ora.ndof)
+    x = to_host(ctx.tpp_apply_block_jacobi(to_dev(b)))
+    bs = ora.bs
+    inv = []
+    for e in range(ora.mesh.num_elem):
+        Se = ora.element_block(e)
+        blk = slice(e * bs, (e + 1) * bs)
+        assert rel(x[blk], np.linalg.solve(Se, b[blk])) <= FP64_TOL * np.linalg.cond(Se), e
+        inv.append(np.linalg.inv(Se))
+
+    def M(vec):
+        out = np.empty_like(vec)
+        for k, Pi in enumerate(inv):
+            out[k * bs:(k + 1) * bs] = Pi @ vec[k * bs:(k + 1) * bs]
+        return out
+    S = ora.global_matrix()
+    _, o = gmres(lambda vec: S @ vec, b, M=M, rtol=1e-8)
+    xg, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_BLOCK_JACOBI, rtol=1e-8)
+    assert o["converged"] and r["converged"] and abs(r["iters"] - o["iters"]) <= 1
+    assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
+    print(f"3D Euler n={n}: GMRES J_full {r['iters']} (oracle {o['iters']})")
