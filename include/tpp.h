@@ -76,9 +76,10 @@ typedef enum {
 #define TPP_FEAT_BF16        32u  /* reserve BF16 copies of the apply factors for TPP_BF16
                                      (2D, n <= 16, one-sided form) */
 #define TPP_FEAT_FULL_BLOCKS 64u  /* system contexts (tpp_create_system): Kronecker factors
-                                     (2D, n <= 16) and, with TPP_FEAT_BLOCK_JACOBI, exact LU
-                                     (2D, n <= 16; 3D, n <= 6) of the whole n_c n^d element
-                                     blocks instead of the n_c small ones (Sec. 5.3, 5.6) */
+                                     (2D, n <= 16; 3D nested form) and, with
+                                     TPP_FEAT_BLOCK_JACOBI, exact LU (2D, n <= 16; 3D, n <= 6)
+                                     of the whole n_c n^d element blocks instead of the n_c
+                                     small ones (Sec. 5.3, 5.6) */
 
 /*
  * Problem description (Sec. 3.4, Sec. 5.1 Eq. adv): the system S x = (M + dt A) x = b of
@@ -349,9 +350,10 @@ tpp_status tpp_set_metric_terms(tpp_ctx* ctx, const double* jdet, const double* 
  * inverted exactly (block Jacobi, J_small).  With TPP_FEAT_FULL_BLOCKS they are the
  * "full" ones: in 2D (n <= 16) the whole n_c n^2 block approximated by A_1 (x) B_1 +
  * A_2 (x) B_2 with A_k of size n_c n on the (component, y) index and B_k of size n on
- * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI); in 3D (n <= 6,
- * with TPP_FEAT_BLOCK_JACOBI) the exact J_full only, tpp_build_factors then returning
- * TPP_ERR_UNSUPPORTED.
+ * x (K_full), or inverted exactly (J_full, with TPP_FEAT_BLOCK_JACOBI); in 3D the nested
+ * form A_1 (x) (B_1 (x) C_1 + B_2 (x) C_2) with A_1 of size n_c n on the (component, z)
+ * index (first stage by power iteration, flagged in fflags bit0 if it has not converged
+ * in 500 steps) and B_k, C_k of size n on y, x (K_full), or J_full (n <= 6).
  *
  * tpp_create_system returns an ordinary context whose elements are the (element,
  * component) pairs e * n_c + c: vectors are [E][n_c][n^dim], tpp_num_elem() is
@@ -568,10 +570,14 @@ typedef struct {
   const double* qtr;     /* [r] trace of mat(Qb[:, t]) */
   /* System contexts with TPP_FEAT_FULL_BLOCKS only (NULL otherwise), m = n_c n: the
    * factors of the whole element blocks, A_k on (component, y), B_k on x, row-major */
-  const double* fA;      /* [E_phys][2][m][m] */
-  const double* fB;      /* [E_phys][2][n][n] */
-  const double* fsig;    /* [E_phys][2] sigma_1, sigma_2 of the rearranged block */
-  const int32_t* fflags; /* [E_phys] bit1 rank-1, bit2 Schur fail, bit3 singular, bit4 relaxed */
+  const double* fA;      /* 2D: [E_phys][2][m][m] A_1, A_2; 3D: [E_phys][m][m] A_1 (the y-x
+                            factors of the nested form sit in A1/B1/A2/B2 above, first
+                            E_phys entries, with sigma their singular values) */
+  const double* fB;      /* 2D: [E_phys][2][n][n]; NULL in 3D */
+  const double* fsig;    /* [E_phys][2] 2D: sigma_1, sigma_2 of the rearranged block; 3D:
+                            sigma_1 of the first stage, power iterations taken */
+  const int32_t* fflags; /* [E_phys] bit0 first stage not converged (3D), bit1 rank-1, bit2
+                            Schur fail, bit3 singular, bit4 relaxed */
 } tpp_views;
 
 tpp_status tpp_get_views(const tpp_ctx* ctx, tpp_views* out);

@@ -30,8 +30,8 @@ finite differences of the flux, the eigenvalues of A_n (v.n - c, v.n, v.n,
 v.n + c), the reduction of a one-component linear "system" (flux a u, lam =
 |a.n|) to the upwind advection operator of oracle/dg.py, discrete conservation of
 every component, and J x against a finite difference of the nonlinear DG residual;
-the full-block KSVD against the scalar KSVD for one component and against an exact
-Kronecker block (dt = 0: the mass alone).
+the full-block KSVD (2D) and nested KSVD (3D) against the scalar ones for one component
+and against an exact Kronecker block (dt = 0: the mass alone).
 """
 from __future__ import annotations
 
@@ -304,6 +304,20 @@ class LinearizedSystemDG:
         from .ksvd import ksvd
         m = self.nc * self.n
         return ksvd(self.element_block(e), m, m, self.n, self.n, 2)
+
+    def full_block_ksvd_3d(self, e: int):
+        """Nested Kronecker approximation A_1 (x) (B_1 (x) C_1 + B_2 (x) C_2) of the full 3D
+        block S_e (Sec. 4.3 applied to the n_c n^3 block).  Reading: with the DOF order
+        (component, z, y, x) the first-stage factor A_1 acts on the (component, z) index
+        c n + k (size n_c n) and D_1 on (y, x); the second stage splits D_1 as in 2D.
+        Returns dict(s1, A1, D1, s2, B1, C1, B2, C2, P)."""
+        assert self.dim == 3
+        from .ksvd import ksvd
+        n, m = self.n, self.nc * self.n
+        s1, (A1,), (D1,) = ksvd(self.element_block(e), m, m, n * n, n * n, 1)
+        s2, (B1, B2), (C1, C2) = ksvd(D1, n, n, n, n, 2)
+        P = np.kron(A1, np.kron(B1, C1) + np.kron(B2, C2))
+        return dict(s1=s1, A1=A1, D1=D1, s2=s2, B1=B1, C1=C1, B2=B2, C2=C2, P=P)
 
     def global_matrix(self) -> sp.csr_matrix:
         bs = self.bs

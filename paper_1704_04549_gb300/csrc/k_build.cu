@@ -1748,7 +1748,7 @@ __global__ void k_coef_2d(const Tables* T, int n, int64_t E, double h, const dou
 // KSVD of the 2D-structured blocks in kco (2D elements, or the second stage
 // of the 3D nested form), inverses, Schur forms, S_A and S_B.
 cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t* mask) {
-  const int n = c->n, nn = n * n;
+  const int n = c->n;
   const int64_t E = c->E;
   DevStatus* st = c->p<DevStatus>(c->L.status);
   // 1. KSVD
@@ -1796,15 +1796,23 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  return launch_factor_inverse(c, s);
+}
+
+// steps 2-5 of the build on the factors A_k, B_k (and sigma) already in the workspace
+cudaError_t launch_factor_inverse(const tpp_ctx* c, cudaStream_t s) {
+  const int n = c->n, nn = n * n;
+  const int64_t E = c->E;
+  DevStatus* st = c->p<DevStatus>(c->L.status);
   // 2. inverses and C products
   InvArgs ia;
   ia.n = n;
   ia.E = E;
-  ia.sigma = ka.sigma;
-  ia.A1 = ka.A1;
-  ia.B1 = ka.B1;
-  ia.A2 = ka.A2;
-  ia.B2 = ka.B2;
+  ia.sigma = c->p<double>(c->L.sigma);
+  ia.A1 = c->p<double>(c->L.fA1);
+  ia.B1 = c->p<double>(c->L.fB1);
+  ia.A2 = c->p<double>(c->L.fA2);
+  ia.B2 = c->p<double>(c->L.fB2);
   ia.LAi = c->p<double>(c->L.fSA);
   ia.LBi = c->p<double>(c->L.fSB);
   ia.C1 = c->p<double>(c->L.fT1);

@@ -662,6 +662,419 @@ __global__ void __launch_bounds__(256) k_full_apply(FullApplyArgs P) {
   }
 }
 
+// ---- 3D full blocks: the nested form A_1 (x) (B_1 (x) C_1 + B_2 (x) C_2) of Sec. 4.3
+// with A_1 of size m = 5n on the (component, z) index a = c n + k, B_k on y, C_k on x.
+// First stage (rank 1 in the a x (j, i) split): the block is sum_t alpha_t (x) beta_t over
+// r1 = 3n^2 + 4n terms with element-independent beta_t (n^2 x n^2 on (j, i)):
+//   t = i' + n j              x volume   beta[(j, i1)][(j, i')] = D[i'][i1]
+//   t = n^2 + i + n j'        y volume   beta[(j1, i)][(j', i)] = D[j'][j1]
+//   t = 2n^2 + i + n j        diagonal   beta = e_(j,i) e_(j,i)^T (mass, z volume, z faces)
+//   t = 3n^2 + j + n f        x faces    beta[(j, i1)][(j, i2)] = l_f[i1] l_f[i2]
+//   t = 3n^2 + 2n + i + n f   y faces    beta[(j1, i)][(j2, i)] = l_f[j1] l_f[j2]
+// The top right singular vector lies in span(beta): v = sum_t mu_t beta_t and
+// R^T R v = beta (alpha^T alpha) (beta^T beta) mu, so the power iteration runs on mu with
+// the Gram matrix G_B = beta^T beta (once per context) and matrix-free alpha products.
+// The second stage: D_1 = sum_t d_t beta_t is itself a sum of products of the 2n + 2 terms
+// of the 2D basis (k_full_basis) on y and on x, D_1 = sum K[s][t] phi_s (x) phi_t, so its
+// rank-2 KSVD is the SVD of the small core R_B K R_B^T (one-sided Jacobi).
+
+__host__ __device__ inline int full3_r1(int n) { return 3 * n * n + 4 * n; }
+
+// beta_t at row (j1, i1), column (j2, i2)
+__device__ double beta3(const Tables* T, int n, int t, int j1, int i1, int j2, int i2) {
+  const int nn = n * n;
+  if (t < nn) {
+    const int ip = t % n, j = t / n;
+    return (j1 == j && j2 == j && i2 == ip) ? T->D[ip * n + i1] : 0.0;
+  }
+  if (t < 2 * nn) {
+    const int u = t - nn, i = u % n, jp = u / n;
+    return (i1 == i && i2 == i && j2 == jp) ? T->D[jp * n + j1] : 0.0;
+  }
+  if (t < 3 * nn) {
+    const int u = t - 2 * nn, i = u % n, j = u / n;
+    return (j1 == j && i1 == i && j2 == j && i2 == i) ? 1.0 : 0.0;
+  }
+  const int u = t - 3 * nn;
+  if (u < 2 * n) {
+    const int j = u % n;
+    const double* l = (u / n) ? T->l1 : T->l0;
+    return (j1 == j && j2 == j) ? l[i1] * l[i2] : 0.0;
+  }
+  const int v = u - 2 * n, i = v % n;
+  const double* l = (v / n) ? T->l1 : T->l0;
+  return (i1 == i && i2 == i) ? l[j1] * l[j2] : 0.0;
+}
+
+// G_B[s][t] = <beta_s, beta_t>: the sum over the (at most n^2) nonzeros of beta_s
+__global__ void k_full3_gram(const Tables* T, int n, double* GB) {
+  const int r1 = full3_r1(n), nn = n * n;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r1 * r1) return;
+  const int s = q / r1, t = q % r1;
+  double acc = 0.0;
+  if (s < nn) {
+    const int ip = s % n, j = s / n;
+    for (int i1 = 0; i1 < n; ++i1) acc += T->D[ip * n + i1] * beta3(T, n, t, j, i1, j, ip);
+  } else if (s < 2 * nn) {
+    const int u = s - nn, i = u % n, jp = u / n;
+    for (int j1 = 0; j1 < n; ++j1) acc += T->D[jp * n + j1] * beta3(T, n, t, j1, i, jp, i);
+  } else if (s < 3 * nn) {
+    const int u = s - 2 * nn, i = u % n, j = u / n;
+    acc = beta3(T, n, t, j, i, j, i);
+  } else if (s < 3 * nn + 2 * n) {
+    const int u = s - 3 * nn, j = u % n;
+    const double* l = (u / n) ? T->l1 : T->l0;
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int i2 = 0; i2 < n; ++i2) acc += l[i1] * l[i2] * beta3(T, n, t, j, i1, j, i2);
+  } else {
+    const int v = s - 3 * nn - 2 * n, i = v % n;
+    const double* l = (v / n) ? T->l1 : T->l0;
+    for (int j1 = 0; j1 < n; ++j1)
+      for (int j2 = 0; j2 < n; ++j2) acc += l[j1] * l[j2] * beta3(T, n, t, j1, i, j2, i);
+  }
+  GB[q] = acc;
+}
+
+struct Full3Args {
+  const Tables* T;
+  int n;
+  int64_t E;
+  double h3;
+  const double* cx;          // [E][5][5][n^3] coupled volume coefficients (k_system.cu)
+  const double* cy;
+  const double* cz;
+  const double* fo;          // [E][6][5][5][n^2] own-face coefficients
+  const double* GB;          // [r1][r1]
+  const double* QB;          // 2D basis (k_full_basis)
+  const double* RB;
+  const int32_t* rk;
+  double* A;                 // [E][m][m] first-stage factor A_1, row-major
+  double* Ainv;              // [E][m][m] its inverse
+  double* sig;               // [E][2]: sigma_1 of the first stage, power iterations
+  int32_t* flags;            // [E] bit0 not converged, bit3 A_1 singular
+  double* A1;                // second-stage factors into the small-block context's arrays
+  double* B1;                // ([E][n*n] column-major, B_k on y as "A", C_k on x as "B")
+  double* A2;
+  double* B2;
+  double* sigma;             // [E][2] second-stage singular values
+  DevStatus* st;
+};
+
+// alpha_t[(c, k)][(c', k')] of element e (see the 3D header above)
+__device__ double alpha3(const Full3Args& P, const double* wl, int64_t e, int t, int c, int k,
+                         int cp, int kp) {
+  constexpr int NC = 5;
+  const int n = P.n, nn = n * n, n3 = nn * n, cc = c * NC + cp;
+  const int64_t vb = (e * NC * NC + cc) * (int64_t)n3;
+  const double* fe = P.fo + e * 6 * NC * NC * nn;
+  if (t < nn) return (k == kp) ? P.cx[vb + (t % n) + n * (t / n) + nn * k] : 0.0;
+  if (t < 2 * nn) {
+    const int u = t - nn;
+    return (k == kp) ? P.cy[vb + (u % n) + n * (u / n) + nn * k] : 0.0;
+  }
+  if (t < 3 * nn) {
+    const int u = t - 2 * nn, i = u % n, j = u / n;
+    double v = P.T->D[kp * n + k] * P.cz[vb + i + n * j + nn * kp];
+    v += wl[n + k] * wl[n + kp] * fe[(4 * NC * NC + cc) * nn + u];
+    v += wl[2 * n + k] * wl[2 * n + kp] * fe[(5 * NC * NC + cc) * nn + u];
+    if (c == cp && k == kp) v += P.h3 * wl[i] * wl[j] * wl[k];
+    return v;
+  }
+  if (k != kp) return 0.0;
+  const int u = t - 3 * nn;
+  if (u < 2 * n) return fe[((u / n) * NC * NC + cc) * nn + (u % n) + n * k];
+  const int v = u - 2 * n;
+  return fe[((2 + v / n) * NC * NC + cc) * nn + (v % n) + n * k];
+}
+
+struct Full3Smem {
+  int tab, mu, y, z, u, K, W, V, fc, total;
+};
+
+__host__ __device__ inline Full3Smem full3_smem(int n) {
+  const int m = 5 * n, r1 = full3_r1(n), r = full_r(n);
+  Full3Smem s;
+  int o = 0;
+  s.tab = o; o += n * n + 3 * n;
+  s.mu = o; o += r1;
+  s.y = o; o += r1;
+  s.z = o; o += r1;
+  s.u = o; o += m * m;
+  s.K = o; o += r * r;
+  s.W = o; o += r * r;
+  s.V = o; o += r * r;
+  s.fc = o; o += m + 16 + (m + 1) / 2 + 1;   // Gauss-Jordan scratch (fcol, red, perm)
+  s.total = o;
+  return s;
+}
+
+// one CTA (256 threads) per element: first stage by power iteration, the second-stage
+// factors, and A_1^-1
+__global__ void __launch_bounds__(256) k_full3_build(Full3Args P) {
+  extern __shared__ double sm[];
+  constexpr int NC = 5;
+  const int n = P.n, nn = n * n, m = NC * n, mm = m * m, r1 = full3_r1(n), r = full_r(n);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const Full3Smem L = full3_smem(n);
+  const int64_t e = blockIdx.x;
+  double* wl = sm + L.tab + nn;         // w, l0, l1
+  double* mu = sm + L.mu;
+  double* y = sm + L.y;
+  double* z = sm + L.z;
+  double* u = sm + L.u;
+  double* K = sm + L.K;
+  double* W = sm + L.W;
+  double* V = sm + L.V;
+  double* red = sm + L.fc + m + 8;      // 8 doubles inside the Gauss-Jordan scratch
+  __shared__ double s_val[4];
+  __shared__ double s_red[16];
+  for (int q = tid; q < n; q += nt) {
+    wl[q] = P.T->w[q];
+    wl[n + q] = P.T->l0[q];
+    wl[2 * n + q] = P.T->l1[q];
+  }
+  for (int q = tid; q < r1; q += nt) {  // start: the mass direction
+    const int u2 = q - 2 * nn;
+    mu[q] = (u2 >= 0 && u2 < nn) ? P.T->w[u2 % n] * P.T->w[u2 / n] : 0.0;
+  }
+  __syncthreads();
+  // y = G_B mu, vv = mu . y, u = alpha y, uu = |u|^2
+  auto forward = [&]() {
+    for (int s = tid; s < r1; s += nt) {
+      double acc = 0.0;
+      for (int t = 0; t < r1; ++t) acc += P.GB[(size_t)t * r1 + s] * mu[t];   // symmetric
+      y[s] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < mm; q += nt) {
+      const int a = q / m, ap = q % m, c = a / n, k = a % n, cp = ap / n, kp = ap % n;
+      double acc = 0.0;
+      for (int t = 2 * nn; t < 3 * nn; ++t) acc += alpha3(P, wl, e, t, c, k, cp, kp) * y[t];
+      if (k == kp) {
+        for (int t = 0; t < 2 * nn; ++t) acc += alpha3(P, wl, e, t, c, k, cp, kp) * y[t];
+        for (int t = 3 * nn; t < r1; ++t) acc += alpha3(P, wl, e, t, c, k, cp, kp) * y[t];
+      }
+      u[q] = acc;
+    }
+    double pv = 0.0, pu = 0.0;
+    for (int s = tid; s < r1; s += nt) pv += mu[s] * y[s];
+    for (int q = tid; q < mm; q += nt) pu += u[q] * u[q];
+    const double vv = block_sum(pv, red);
+    const double uu = block_sum(pu, red);
+    if (tid == 0) {
+      s_val[0] = vv;
+      s_val[1] = uu;
+    }
+    __syncthreads();
+  };
+  forward();
+  int it = 0;
+  bool conv = false;
+  for (; it < 500 && !conv; ++it) {
+    const double vv = s_val[0], uu = s_val[1];
+    if (!(vv > 0.0) || !(uu > 0.0)) break;
+    const double lam = uu / vv;
+    // z = alpha^T u
+    for (int t = tid; t < r1; t += nt) {
+      double acc = 0.0;
+      if (t >= 2 * nn && t < 3 * nn) {
+        for (int q = 0; q < mm; ++q) {
+          const int a = q / m, ap = q % m;
+          acc += alpha3(P, wl, e, t, a / n, a % n, ap / n, ap % n) * u[q];
+        }
+      } else {
+        for (int c = 0; c < NC; ++c)
+          for (int cp = 0; cp < NC; ++cp)
+            for (int k = 0; k < n; ++k)
+              acc += alpha3(P, wl, e, t, c, k, cp, k) * u[(c * n + k) * m + cp * n + k];
+      }
+      z[t] = acc / lam;
+    }
+    __syncthreads();
+    double pd = 0.0, pm = 0.0;
+    for (int t = tid; t < r1; t += nt) {
+      pd = fmax(pd, fabs(z[t] - mu[t]));
+      pm = fmax(pm, fabs(z[t]));
+      mu[t] = z[t];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      pd = fmax(pd, __shfl_xor_sync(0xffffffffu, pd, o));
+      pm = fmax(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+      s_red[tid >> 5] = pd;
+      s_red[8 + (tid >> 5)] = pm;
+    }
+    __syncthreads();
+    double dmax = 0.0, mmax = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) {
+      dmax = fmax(dmax, s_red[w]);
+      mmax = fmax(mmax, s_red[8 + w]);
+    }
+    conv = dmax <= 1e-14 * mmax;
+    __syncthreads();
+    forward();
+  }
+  const double vv = s_val[0], uu = s_val[1];
+  const double sig1 = (vv > 0.0) ? sqrt(uu / vv) : 0.0;
+  const double sa = (sig1 > 0.0) ? 1.0 / sqrt(sig1 * vv) : 0.0;    // A_1 = u / sqrt(sig1 vv)
+  const double sd = (vv > 0.0) ? sqrt(sig1 / vv) : 0.0;            // D_1 = sd sum mu_t beta_t
+  for (int q = tid; q < mm; q += nt) {
+    u[q] *= sa;
+    P.A[e * mm + q] = u[q];
+  }
+  // K[s][t]: D_1 in the products of the 2D basis (s on y, t on x)
+  for (int q = tid; q < r * r; q += nt) K[q] = 0.0;
+  __syncthreads();
+  if (tid == 0) {
+    for (int t = 0; t < r1; ++t) {
+      const double d = sd * mu[t];
+      int row, col;
+      if (t < nn) { row = n + t / n; col = t % n; }                         // x volume
+      else if (t < 2 * nn) { row = (t - nn) / n; col = n + (t - nn) % n; }  // y volume
+      else if (t < 3 * nn) { row = n + (t - 2 * nn) / n; col = n + (t - 2 * nn) % n; }
+      else if (t < 3 * nn + 2 * n) { const int v = t - 3 * nn; row = n + v % n; col = 2 * n + v / n; }
+      else { const int v = t - 3 * nn - 2 * n; row = 2 * n + v / n; col = n + v % n; }
+      K[row * r + col] += d;
+    }
+  }
+  __syncthreads();
+  // core W = R_B K R_B^T (rk x rk), via V = K R_B^T
+  const int rk = *P.rk;
+  for (int q = tid; q < r * rk; q += nt) {
+    const int s = q / rk, p = q % rk;
+    double acc = 0.0;
+    for (int t = 0; t < r; ++t) acc += K[s * r + t] * P.RB[p * r + t];
+    V[s * rk + p] = acc;
+  }
+  __syncthreads();
+  for (int q = tid; q < rk * rk; q += nt) {
+    const int p = q / rk, p2 = q % rk;
+    double acc = 0.0;
+    for (int s = 0; s < r; ++s) acc += P.RB[p * r + s] * V[s * rk + p2];
+    W[q] = acc;
+  }
+  __syncthreads();
+  for (int q = tid; q < rk * rk; q += nt) V[q] = (q / rk == q % rk) ? 1.0 : 0.0;
+  __syncthreads();
+  // one-sided Jacobi: W V = U S, round-robin column pairs, one thread per pair
+  const int rp = rk + (rk & 1), np = rp / 2;
+  for (int sweep = 0; sweep < 40 && rk > 1; ++sweep) {
+    int rotated = 0;
+    for (int round = 0; round < rp - 1; ++round) {
+      if (tid < np) {
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (rp - 1); };
+        const int p = player(tid), q2 = player(rp - 1 - tid);
+        if (p < rk && q2 < rk) {
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int i = 0; i < rk; ++i) {
+            const double wp = W[i * rk + p], wq = W[i * rk + q2];
+            al += wp * wp;
+            be += wq * wq;
+            ga += wp * wq;
+          }
+          if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
+            rotated = 1;
+            const double ze = (be - al) / (2.0 * ga);
+            const double t = (fabs(ze) > 1e150) ? 0.5 / ze
+                                                : copysign(1.0, ze) / (fabs(ze) + sqrt(ze * ze + 1.0));
+            const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+            for (int i = 0; i < rk; ++i) {
+              const double wp = W[i * rk + p], wq = W[i * rk + q2];
+              W[i * rk + p] = cs * wp - sn * wq;
+              W[i * rk + q2] = sn * wp + cs * wq;
+              const double vp = V[i * rk + p], vq = V[i * rk + q2];
+              V[i * rk + p] = cs * vp - sn * vq;
+              V[i * rk + q2] = sn * vp + cs * vq;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) break;
+  }
+  // the two largest column norms
+  __shared__ int s_idx[2];
+  __shared__ double s_sv[2];
+  if (tid == 0) {
+    int i1 = -1, i2 = -1;
+    double n1 = -1.0, n2 = -1.0;
+    for (int p = 0; p < rk; ++p) {
+      double nr = 0.0;
+      for (int i = 0; i < rk; ++i) nr += W[i * rk + p] * W[i * rk + p];
+      if (nr > n1) { n2 = n1; i2 = i1; n1 = nr; i1 = p; }
+      else if (nr > n2) { n2 = nr; i2 = p; }
+    }
+    s_idx[0] = i1;
+    s_idx[1] = i2;
+    s_sv[0] = (i1 >= 0) ? sqrt(n1) : 0.0;
+    s_sv[1] = (i2 >= 0) ? sqrt(n2) : 0.0;
+  }
+  __syncthreads();
+  // B_k (y) = sqrt(s_k) Q_B u_k with u_k = W[:, col] / s_k; C_k (x) = sqrt(s_k) Q_B V[:, col]
+  for (int k2 = 0; k2 < 2; ++k2) {
+    const int col = s_idx[k2];
+    const double sv = s_sv[k2];
+    const double rs = sqrt(sv), irs = (sv > 0.0) ? 1.0 / rs : 0.0;
+    double* By = (k2 == 0 ? P.A1 : P.A2) + e * nn;
+    double* Cx = (k2 == 0 ? P.B1 : P.B2) + e * nn;
+    for (int q = tid; q < nn; q += nt) {
+      double ay = 0.0, ax = 0.0;
+      if (col >= 0 && sv > 0.0)
+        for (int p = 0; p < rk; ++p) {
+          ay += P.QB[(size_t)p * nn + q] * W[p * rk + col];
+          ax += P.QB[(size_t)p * nn + q] * V[p * rk + col];
+        }
+      const int rr = q / n, cl = q % n;             // row-major [rr][cl] -> column-major
+      By[rr + n * cl] = ay * irs;                   // sqrt(s) u = W[:, col] / sqrt(s)
+      Cx[rr + n * cl] = ax * rs;
+    }
+    if (tid == 0) P.sigma[e * 2 + k2] = sv;
+  }
+  __syncthreads();
+  // A_1^-1 (Gauss-Jordan in the u buffer)
+  const bool ok = cta_gauss_jordan(u, m, sm + L.fc, red,
+                                   reinterpret_cast<int*>(sm + L.fc + m + 16));
+  for (int q = tid; q < mm; q += nt) P.Ainv[e * mm + q] = ok ? u[q] : 0.0;
+  if (tid == 0) {
+    P.sig[e * 2] = sig1;
+    P.sig[e * 2 + 1] = (double)it;
+    int fl = 0;
+    if (!conv) {
+      fl |= 1;
+      atomicAdd(&P.st->z_unconverged, 1);
+    }
+    if (!ok) {
+      fl |= 8;
+      atomicAdd(&P.st->build_singular, 1);
+    }
+    P.flags[e] = fl;
+  }
+}
+
+// x = (A_1^-1 (x) I) b along the (component, z) index, one CTA per element
+__global__ void __launch_bounds__(256) k_full3_apply_z(int n, const double* Ainv, const double* b,
+                                                       double* x, const int32_t* skip) {
+  if (skip && *skip) return;
+  extern __shared__ double sm[];
+  const int m = 5 * n, nn = n * n, mm = m * m;
+  const int64_t e = blockIdx.x;
+  double* Ai = sm;
+  double* bs = sm + mm;
+  for (int q = threadIdx.x; q < mm; q += blockDim.x) Ai[q] = Ainv[e * mm + q];
+  for (int q = threadIdx.x; q < m * nn; q += blockDim.x) bs[q] = b[e * m * nn + q];
+  __syncthreads();
+  for (int q = threadIdx.x; q < m * nn; q += blockDim.x) {
+    const int a = q / nn, qq = q % nn;
+    double acc = 0.0;
+    for (int ap = 0; ap < m; ++ap) acc += Ai[a * m + ap] * bs[ap * nn + qq];
+    x[e * m * nn + q] = acc;
+  }
+}
+
 // the whole 3D n_c n^3 x n_c n^3 block (n_c = 5, node (c, k, j, i)), row-major: in each
 // direction d the volume term D[a'][a] cd[c][c'](node at a') and the two own-face terms,
 // the other two node coordinates equal
@@ -736,8 +1149,16 @@ size_t full_layout(size_t base, int dim, int n, int64_t E, bool bj, FullOffsets*
   const size_t Ez = (size_t)E;
   FullOffsets L;
   size_t o = al(base);
-  if (dim == 3) {                 // exact full-block Jacobi only: n_c = 5, blocks of 5 n^3
-    const size_t nb = 5 * nn * (size_t)n;
+  if (dim == 3) {                 // n_c = 5: A_1 of size 5n, blocks of 5 n^3
+    const size_t m3 = 5 * (size_t)n, r1 = (size_t)full3_r1(n), nb = 5 * nn * (size_t)n;
+    L.QB = o; o += al(nn * r * 8);
+    L.RB = o; o += al(r * r * 8);
+    L.rk = o; o += 256;
+    L.GB = o; o += al(r1 * r1 * 8);
+    L.A = o; o += al(Ez * m3 * m3 * 8);
+    L.inv = o; o += al(Ez * m3 * m3 * 8);
+    L.sig = o; o += al(Ez * 2 * 8);
+    L.flags = o; o += al(Ez * 4);
     L.lu = bj ? o : 0; o += bj ? al(Ez * nb * nb * 8) : 0;
     L.piv = bj ? o : 0; o += bj ? al(Ez * nb * 4) : 0;
     L.total = o;
@@ -767,7 +1188,66 @@ cudaError_t launch_full_basis(const tpp_ctx* c, cudaStream_t s) {
   k_full_basis<<<1, 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n, c->p<double>(c->fb.QB),
                                  c->p<double>(c->fb.RB), c->p<int32_t>(c->fb.rk));
   count_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || c->dim != 3) return err;
+  const int r1 = full3_r1(c->n);
+  k_full3_gram<<<(unsigned)((r1 * r1 + 255) / 256), 256, 0, s>>>(c->p<Tables>(c->L.tables), c->n,
+                                                                 c->p<double>(c->fb.GB));
+  count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_full3_build(const tpp_ctx* c, cudaStream_t s) {
+  Full3Args P;
+  P.T = c->p<Tables>(c->L.tables);
+  P.n = c->n;
+  P.E = c->sys_E;
+  P.h3 = c->prob.h * c->prob.h * c->prob.h;
+  P.cx = c->p<double>(c->sys_cx);
+  P.cy = c->p<double>(c->sys_cy);
+  P.cz = c->p<double>(c->sys_cz);
+  P.fo = c->p<double>(c->sys_fo);
+  P.GB = c->p<double>(c->fb.GB);
+  P.QB = c->p<double>(c->fb.QB);
+  P.RB = c->p<double>(c->fb.RB);
+  P.rk = c->p<int32_t>(c->fb.rk);
+  P.A = c->p<double>(c->fb.A);
+  P.Ainv = c->p<double>(c->fb.inv);
+  P.sig = c->p<double>(c->fb.sig);
+  P.flags = c->p<int32_t>(c->fb.flags);
+  P.A1 = c->p<double>(c->L.fA1);
+  P.B1 = c->p<double>(c->L.fB1);
+  P.A2 = c->p<double>(c->L.fA2);
+  P.B2 = c->p<double>(c->L.fB2);
+  P.sigma = c->p<double>(c->L.sigma);
+  P.st = c->p<DevStatus>(c->L.status);
+  const size_t smem = (size_t)full3_smem(c->n).total * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(k_full3_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  k_full3_build<<<(unsigned)c->sys_E, 256, smem, s>>>(P);
+  count_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  tpp_ctx v = *c;                 // the second stage: the 2D steps on the first E factor sets
+  v.E = c->sys_E;
+  return launch_factor_inverse(&v, s);
+}
+
+cudaError_t launch_full3_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
+                               cudaStream_t s) {
+  const int n = c->n, m = 5 * n;
+  const size_t smem = (size_t)(m * m + m * n * n) * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(k_full3_apply_z,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_full3_apply_z<<<(unsigned)c->sys_E, 256, smem, s>>>(n, c->p<double>(c->fb.inv), b, x, skip);
+  count_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  tpp_ctx v = *c;                 // the y-x factor on each of the 5n slices of an element
+  v.dim = 3;
+  v.R = 5;
+  v.EB = c->sys_E * 5;
+  return launch_apply_2d(&v, x, x, TPP_FP64, skip, s);
 }
 
 cudaError_t launch_full_build(const tpp_ctx* c, cudaStream_t s) {

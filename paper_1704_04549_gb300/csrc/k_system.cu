@@ -319,9 +319,10 @@ const char* sys_validate(const tpp_sys_problem* p, int32_t max_restart, uint32_t
       (p->n > 16 || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16))))
     return "TPP_FEAT_FULL_BLOCKS in 2D: n <= 16, without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16";
   if ((features & TPP_FEAT_FULL_BLOCKS) && p->dim == 3 &&
-      (p->n > 6 || !(features & TPP_FEAT_BLOCK_JACOBI)))
-    return "TPP_FEAT_FULL_BLOCKS in 3D: exact full-block Jacobi (needs TPP_FEAT_BLOCK_JACOBI), "
-           "n <= 6";
+      ((features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16)) ||
+       ((features & TPP_FEAT_BLOCK_JACOBI) && p->n > 6)))
+    return "TPP_FEAT_FULL_BLOCKS in 3D: without TPP_FEAT_TWO_SIDED or TPP_FEAT_BF16, and n <= 6 "
+           "with TPP_FEAT_BLOCK_JACOBI";
   return nullptr;
 }
 
@@ -486,7 +487,7 @@ extern "C" tpp_status tpp_create_system(tpp_ctx** out, const tpp_sys_problem* p,
     c->sys_full = true;
     c->sys_full_bj = (features & TPP_FEAT_BLOCK_JACOBI) != 0;
     c->fb = FO;
-    if (dim == 2 && (e = launch_full_basis(c, s)) != cudaSuccess) return fail(e, "full-block basis");
+    if ((e = launch_full_basis(c, s)) != cudaSuccess) return fail(e, "full-block basis");
   }
   *out = c;
   return TPP_OK;

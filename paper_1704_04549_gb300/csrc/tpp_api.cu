@@ -258,7 +258,7 @@ cudaError_t apply_precond(const tpp_ctx* c, int pc, int prec, const double* b, d
   }
   if (c->sys_full) {
     if (pc == TPP_PC_BLOCK_JACOBI) return launch_full_bj_apply(c, b, x, skip, s);
-    return launch_full_apply(c, b, x, skip, s);
+    return c->dim == 2 ? launch_full_apply(c, b, x, skip, s) : launch_full3_apply(c, b, x, skip, s);
   }
   if (pc == TPP_PC_BLOCK_JACOBI) return launch_bj_apply(c, b, x, skip, s);
   if (prec == TPP_BF16) return launch_apply_bf16(c, b, x, skip, s);
@@ -514,13 +514,9 @@ tpp_status tpp_build_factors(tpp_ctx* c, tpp_build_report* report, void* stream)
   const DevStatus st0 = fresh_status();
   TPP_TRY_CUDA(cudaMemcpyAsync(c->ws + c->L.status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s),
                "reset status");
-  if (c->sys_full && c->dim == 3) {
-    set_error("the full-block Kronecker factors are built in 2D only (3D: TPP_FEAT_FULL_BLOCKS "
-              "gives exact full-block Jacobi)");
-    return TPP_ERR_UNSUPPORTED;
-  }
   if (c->sys_full)
-    TPP_TRY_CUDA(launch_full_build(c, s), "k_full (full-block factors)");
+    TPP_TRY_CUDA(c->dim == 2 ? launch_full_build(c, s) : launch_full3_build(c, s),
+                 "k_full (full-block factors)");
   else
     TPP_TRY_CUDA(c->dim == 2 ? launch_build_2d(c, s) : launch_build_3d(c, s), "k_build");
   return finish_build(c, report, s);
@@ -737,7 +733,7 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
   }
   if (c->sys_full) {
     o->fA = c->p<double>(c->fb.A);
-    o->fB = c->p<double>(c->fb.B);
+    o->fB = c->dim == 2 ? c->p<double>(c->fb.B) : nullptr;
     o->fsig = c->p<double>(c->fb.sig);
     o->fflags = c->p<int32_t>(c->fb.flags);
   }

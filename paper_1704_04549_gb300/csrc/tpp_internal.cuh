@@ -108,7 +108,7 @@ struct Layout {
 
 // full multi-component blocks of a 2D system context (k_full.cu): workspace offsets
 struct FullOffsets {
-  size_t QB = 0, RB = 0, rk = 0, A = 0, B = 0, sig = 0, T = 0, Q = 0, Mb = 0, inv = 0,
+  size_t QB = 0, RB = 0, rk = 0, GB = 0, A = 0, B = 0, sig = 0, T = 0, Q = 0, Mb = 0, inv = 0,
          flags = 0, lu = 0, piv = 0, total = 0;
 };
 
@@ -179,7 +179,13 @@ cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr
 // full multi-component blocks (k_full.cu); the layout returns its end offset
 size_t full_layout(size_t base, int dim, int n, int64_t E, bool bj, FullOffsets* out);
 cudaError_t launch_full_basis(const tpp_ctx* c, cudaStream_t s);
+// build steps after the KSVD: factor inverses, Schur forms, shifted inverses, S_A / S_B
+// (k_build.cu), on the c->E factor sets in the workspace
+cudaError_t launch_factor_inverse(const tpp_ctx* c, cudaStream_t s);
 cudaError_t launch_full_build(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_full3_build(const tpp_ctx* c, cudaStream_t s);
+cudaError_t launch_full3_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
+                               cudaStream_t s);
 cudaError_t launch_full_apply(const tpp_ctx* c, const double* b, double* x, const int32_t* skip,
                               cudaStream_t s);
 cudaError_t launch_full_bj_build(const tpp_ctx* c, cudaStream_t s);

@@ -421,8 +421,11 @@ class Context:
             res["zflags"] = grab(v.zflags, E, torch.int32)
         if v.fA:                       # full multi-component blocks (row-major factors)
             Ep, m = self.num_elem // (self.dim + 2), (self.dim + 2) * n
-            res["fA"] = grab(v.fA, Ep * 2 * m * m, torch.float64).view(Ep, 2, m, m)
-            res["fB"] = grab(v.fB, Ep * 2 * n * n, torch.float64).view(Ep, 2, n, n)
+            if self.dim == 2:          # A_k, B_k of A_1 (x) B_1 + A_2 (x) B_2
+                res["fA"] = grab(v.fA, Ep * 2 * m * m, torch.float64).view(Ep, 2, m, m)
+                res["fB"] = grab(v.fB, Ep * 2 * n * n, torch.float64).view(Ep, 2, n, n)
+            else:                      # first-stage A_1; the y-x factors are A1/B1/A2/B2[:Ep]
+                res["fA"] = grab(v.fA, Ep * m * m, torch.float64).view(Ep, m, m)
             res["fsig"] = grab(v.fsig, Ep * 2, torch.float64).view(Ep, 2)
             res["fflags"] = grab(v.fflags, Ep, torch.int32)
         torch.cuda.synchronize(self.device)

@@ -325,10 +325,8 @@ def test_3d_small_block_factors_and_gmres(n, nel):
 def test_3d_full_block_jacobi(n, nel):
     """J_full in 3D (Sec. 5.6, the 5 (p+1)^3 blocks): exact LU of every element's whole
     block against a dense solve with the oracle's, and GMRES iteration parity."""
-    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS, TppError
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS
     ctx, ora = _pair3d(n, nel, 0.05, features=TPP_FEAT_FULL_BLOCKS | TPP_FEAT_BLOCK_JACOBI)
-    with pytest.raises(TppError):                 # the full-block Kronecker factors are 2D
-        ctx.tpp_build_factors()
     ctx.tpp_build_block_jacobi()
     b = synthetic.rhs(23, ora.ndof)
     x = to_host(ctx.tpp_apply_block_jacobi(to_dev(b)))
@@ -351,3 +349,47 @@ def test_3d_full_block_jacobi(n, nel):
     assert o["converged"] and r["converged"] and abs(r["iters"] - o["iters"]) <= 1
     assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
     print(f"3D Euler n={n}: GMRES J_full {r['iters']} (oracle {o['iters']})")
+
+
+@pytest.mark.parametrize("n,nel", [(2, (2, 2, 2)), (3, (2, 2, 2)), (5, (2, 2, 1)), (8, (2, 1, 1))])
+def test_3d_full_block_factors_and_gmres(n, nel):
+    """K_full in 3D: the first-stage factor A_1 (size 5n, power iteration), the y-x factors
+    of D_1 and the nested P of every element against the oracle's nested KSVD of the
+    whole block, P^-1 b, and GMRES iteration parity."""
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS
+    ctx, ora = _pair3d(n, nel, 0.05, features=TPP_FEAT_FULL_BLOCKS)
+    rep = ctx.tpp_build_factors()
+    assert rep["num_schur_fail"] == 0 and rep["num_z_unconverged"] == 0
+    v = ctx.views()
+    Ep = ora.mesh.num_elem
+    fA, fsig, fflags = to_host(v["fA"]), to_host(v["fsig"]), to_host(v["fflags"])
+    A1, B1, A2, B2 = (to_host(v[k])[:Ep] for k in ("A1", "B1", "A2", "B2"))
+    b = synthetic.rhs(29, ora.ndof)
+    x = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+    bs = ora.bs
+    Ps, worst = [], 0.0
+    for e in range(Ep):
+        ref = ora.full_block_ksvd_3d(e)
+        s1 = np.atleast_1d(ref["s1"])[0]
+        assert abs(fsig[e, 0] - s1) <= 1e-12 * s1, (e, fsig[e], s1)
+        P = np.kron(fA[e], np.kron(A1[e], B1[e]) + np.kron(A2[e], B2[e]))
+        worst = max(worst, rel(P, ref["P"]))
+        assert rel(P, ref["P"]) <= 2e-13, (e, rel(P, ref["P"]))        # measured <= 1.8e-14
+        blk = slice(e * bs, (e + 1) * bs)
+        err = rel(x[blk], np.linalg.solve(ref["P"], b[blk]))
+        assert err <= solve_tol(np.linalg.cond(ref["P"])), (e, err)
+        assert fflags[e] & 9 == 0
+        Ps.append(np.linalg.inv(ref["P"]))
+
+    def M(vec):
+        out = np.empty_like(vec)
+        for k, Pi in enumerate(Ps):
+            out[k * bs:(k + 1) * bs] = Pi @ vec[k * bs:(k + 1) * bs]
+        return out
+    S = ora.global_matrix()
+    _, o = gmres(lambda vec: S @ vec, b, M=M, rtol=1e-8)
+    xg, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    assert o["converged"] and r["converged"] and abs(r["iters"] - o["iters"]) <= 1
+    assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
+    print(f"3D Euler n={n}: K_full P error {worst:.1e}, power iterations {int(fsig[:, 1].max())}, "
+          f"GMRES {r['iters']} (oracle {o['iters']})")

@@ -191,14 +191,15 @@ def test_system_problem_validation(L):
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 1})), 7, 0) == 0   # 8 < 9
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 1})), 8, 0) > 0
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 12})), 30, 0) > g3
-    # full blocks: Kronecker factors 2D (n <= 16); exact LU also 3D (n <= 6, with block Jacobi)
+    # full blocks: Kronecker factors 2D (n <= 16) and 3D (nested); exact LU 3D n <= 6
     FULL, BJ = L.TPP_FEAT_FULL_BLOCKS, L.TPP_FEAT_BLOCK_JACOBI
     assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, FULL) > good
     assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, FULL | BJ) > \
         lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, FULL)
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(n=17)), 30, FULL) == 0
     assert lib.tpp_sys_workspace_bytes(C.byref(problem()), 30, FULL | L.TPP_FEAT_TWO_SIDED) == 0
-    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**p3)), 30, FULL) == 0
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**p3)), 30, FULL) > 0
+    assert lib.tpp_sys_workspace_bytes(C.byref(problem(**p3)), 30, FULL | L.TPP_FEAT_TWO_SIDED) == 0
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(**p3)), 30, FULL | BJ) > 0
     assert lib.tpp_sys_workspace_bytes(C.byref(problem(**{**p3, 'n': 7})), 30, FULL | BJ) == 0
 

@@ -199,3 +199,24 @@ def test_full_block_ksvd_exact_for_the_mass():
     w = 0.5 * np.polynomial.legendre.leggauss(n)[1]
     assert abs(s[0] - h * h * np.sum(w * w) * 2.0) <= 1e-13 * s[0]
     assert s[1] <= 1e-13 * s[0]
+
+
+def test_full_block_nested_ksvd_3d_reduces_to_the_scalar_one():
+    from oracle.ksvd import ksvd_3d_nested
+    mesh = PeriodicMesh((2, 2, 2), 0.5)
+    n = 3
+    sysdg = LinearizedSystemDG(mesh, n, 0.1, LinearAdvectionFlux((1.0, -0.5, 0.3)),
+                               np.zeros((mesh.num_elem, 1, n ** 3)))
+    for e in (0, 6):
+        out = sysdg.full_block_ksvd_3d(e)
+        ref = ksvd_3d_nested(sysdg.element_block(e), n)
+        assert np.abs(out["P"] - ref["P"]).max() <= 1e-12 * np.abs(ref["P"]).max()
+
+
+def test_full_block_nested_ksvd_3d_exact_for_the_mass():
+    L = 2.0
+    n = 3
+    sysdg = vortex_system((2, 2, 2), L / 2, n, 0.0, lambda X: synthetic.euler3d_wave_state(X, L))
+    out = sysdg.full_block_ksvd_3d(3)
+    S = sysdg.element_block(3)
+    assert np.abs(out["P"] - S).max() <= 1e-13 * np.abs(S).max()
