@@ -284,14 +284,15 @@ def periodic_warp(X: np.ndarray, L: float, alpha: float = 0.05):
     return x, G
 
 
-# Linearisation state of the 3D Euler workload (Sec. 5.6's smooth periodic case, whose
-# exact solution is a travelling wave): density rho = 1 + 0.2 sin(2 pi (x + y + z) / L)
-# advected by the uniform velocity (1, 0.5, 0.25) at uniform pressure 1 (gamma = 1.4).
+# Linearisation state of the 3D Euler workload: the initial condition of the periodic
+# case of Sec. 5.6 (its exact solution is a travelling wave), density
+# rho = 1 + 0.2 sin(2 pi (x + y + z) / L) (L = 2: sin(pi (x + y + z))) advected by the
+# uniform velocity (1, -1/2, 1) at uniform pressure 1 (gamma = 1.4).
 def euler3d_wave_state(X: np.ndarray, L: float, gamma: float = 1.4) -> np.ndarray:
     """Conserved variables (rho, rho u, rho v, rho w, rho E) [..., 5] at points X [..., 3]."""
     X = np.asarray(X, dtype=np.float64)
     rho = 1.0 + 0.2 * np.sin(2.0 * np.pi * X.sum(-1) / L)
-    V = np.array([1.0, 0.5, 0.25])
+    V = np.array([1.0, -0.5, 1.0])
     p = 1.0
     E = p / ((gamma - 1.0) * rho) + 0.5 * float(V @ V)
     return np.concatenate([rho[..., None], rho[..., None] * V, (rho * E)[..., None]], -1)
