@@ -1198,6 +1198,50 @@ def run_kernels(args):
         torch.cuda.synchronize()
         print(json.dumps({"mode": "kernels", "workload": "euler", "n": n, "dofs": ctx.num_dofs}))
         return 0
+    if args.workload == "euler_full":      # 2D full blocks: vortex, 32 x 32 elements, n = 8
+        import numpy as np
+        from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS, Context
+        n, N, h = 8, 32, 20.0 / 32
+        xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+        cx, cy = np.arange(N * N) % N, np.arange(N * N) // N
+        X = np.stack(np.meshgrid(xg, xg, indexing="xy"), -1).reshape(-1, 2)
+        pts = np.stack([(cx[:, None] + X[None, :, 0]) * h, (cy[:, None] + X[None, :, 1]) * h], -1)
+        state = synthetic.euler_vortex_state(pts).transpose(0, 2, 1)
+        ctx = Context.euler_system(n, (N, N), h, 0.1, state, features=TPP_FEAT_FULL_BLOCKS,
+                                   device="cuda:0")
+        ctx.tpp_build_factors()
+        v = torch.as_tensor(synthetic.rhs(5, ctx.num_dofs), device="cuda:0")
+        y = torch.empty_like(v)
+        for _ in range(4):
+            ctx.tpp_apply_inverse(v, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernels", "workload": "euler_full", "n": n,
+                          "dofs": ctx.num_dofs}))
+        return 0
+    if args.workload == "euler3d":         # 3D periodic case, 8^3 elements, n = 6, full blocks
+        import numpy as np
+        from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS, Context
+        n, N, L = 6, 8, 2.0
+        h = L / N
+        xg = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+        gz, gy, gx = np.meshgrid(xg, xg, xg, indexing="ij")
+        e = np.arange(N ** 3)
+        cx, cy, cz = e % N, (e // N) % N, e // (N * N)
+        pts = np.stack([(cx[:, None] + gx.reshape(-1)[None, :]) * h,
+                        (cy[:, None] + gy.reshape(-1)[None, :]) * h,
+                        (cz[:, None] + gz.reshape(-1)[None, :]) * h], -1)
+        state = synthetic.euler3d_wave_state(pts, L).transpose(0, 2, 1)
+        ctx = Context.euler_system(n, (N, N, N), h, 2.5e-3, state,
+                                   features=TPP_FEAT_FULL_BLOCKS, device="cuda:0")
+        ctx.tpp_build_factors()
+        v = torch.as_tensor(synthetic.rhs(5, ctx.num_dofs), device="cuda:0")
+        y = torch.empty_like(v)
+        for _ in range(4):
+            ctx.tpp_apply_inverse(v, y)
+            ctx.dg_apply_sumfact(v, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernels", "workload": "euler3d", "n": n, "dofs": ctx.num_dofs}))
+        return 0
     from paper_1704_04549_gb300 import TPP_FEAT_MIXED, TPP_FP32, TPP_FP64, Context
     w = workload_3d(args.n if args.n != 16 else 11) if args.workload == "adv3d" else workload(args.n)
     ctx = Context(w["dim"], w["n"], w["nel"], w["h"], w["dt"], w["velocity"], max_restart=30,
@@ -1272,7 +1316,7 @@ def main():
     ap.add_argument("--iter-limit", type=int, default=50,
                     help="learned workload: GMRES iterations before the exact rebuild")
     ap.add_argument("--workload", choices=["adv2d", "adv3d", "batch", "learned", "timestep", "euler",
-                                           "mrhs"],
+                                           "mrhs", "euler_full", "euler3d"],
                     default="adv2d",
                     help="adv3d: the 16^3 hex configuration (apply/operator/build throughput)")
     args = ap.parse_args()
@@ -1290,7 +1334,7 @@ def main():
         return run_timestep(args)
     if args.workload == "mrhs":
         return run_mrhs(args)
-    if args.workload == "euler":
+    if args.workload in ("euler", "euler_full", "euler3d"):
         return run_euler(args)
     return run_ours(args)
 
