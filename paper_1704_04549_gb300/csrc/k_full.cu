@@ -597,7 +597,8 @@ __global__ void __launch_bounds__(256) k_full_apply(FullApplyArgs P) {
   if (P.skip && *P.skip) return;
   extern __shared__ double sm[];
   const int n = P.n, nn = n * n, m = kNcFull * n, mn = m * n;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int sub = tid & 3, rsl = tid >> 2, rows_per_pass = nt >> 2;
   const int64_t e = blockIdx.x;
   double* F = sm;                 // m x n: b, then H = F M_b
   double* H = F + mn;
@@ -636,20 +637,30 @@ __global__ void __launch_bounds__(256) k_full_apply(FullApplyArgs P) {
       rhs[q] = v;
     }
     __syncthreads();
+    // matvecs with four threads per row (two shuffle-adds per row instead of five per
+    // warp-split row: the FP64 pipe, not HBM, bounds this kernel)
     const double* G = inv + (int64_t)k0 * 2 * m * m;
-    for (int row = wid; row < dm; row += nw) {
+    for (int r0 = 0; r0 < dm; r0 += rows_per_pass) {
+      const int row = r0 + rsl;
+      const bool ok = row < dm;
       double acc = 0.0;
-      for (int c = lane; c < dm; c += 32) acc += G[(int64_t)row * dm + c] * rhs[c];
-      acc = warp_sum(acc);
-      if (lane == 0) Z[(row % m) * n + k0 + row / m] = acc;
+      if (ok)
+        for (int c = sub; c < dm; c += 4) acc += G[(int64_t)row * dm + c] * rhs[c];
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (ok && sub == 0) Z[(row % m) * n + k0 + row / m] = acc;
     }
     __syncthreads();
-    for (int row = wid; row < dm; row += nw) {
+    for (int r0 = 0; r0 < dm; r0 += rows_per_pass) {
+      const int row = r0 + rsl;
+      const bool ok = row < dm;
       const int p = row / m, a = row % m;
       double acc = 0.0;
-      for (int c = lane; c < m; c += 32) acc += A2[a * m + c] * Z[c * n + k0 + p];
-      acc = warp_sum(acc);
-      if (lane == 0) U[a * n + k0 + p] = acc;
+      if (ok)
+        for (int c = sub; c < m; c += 4) acc += A2[a * m + c] * Z[c * n + k0 + p];
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (ok && sub == 0) U[a * n + k0 + p] = acc;
     }
     __syncthreads();
     k = k0 - 1;
