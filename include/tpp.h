@@ -75,6 +75,10 @@ typedef enum {
 #define TPP_FEAT_TIME        16u  /* reserve 6 solution-sized vectors for tpp_time_integrate */
 #define TPP_FEAT_BF16        32u  /* reserve BF16 copies of the apply factors for TPP_BF16
                                      (2D, n <= 16, one-sided form) */
+#define TPP_FEAT_F32_SHIFTS 128u  /* with TPP_FEAT_MIXED (one-sided form, n <= 16, mu <= n): the
+                                     build forms the shifted inverses of the one-sided form in
+                                     FP32 only, for the FP32 apply (no 2 n^3 doubles per
+                                     element); Kronecker applies are then TPP_FP32 only */
 #define TPP_FEAT_FULL_BLOCKS 64u  /* system contexts (tpp_create_system): Kronecker factors
                                      (2D, n <= 16; 3D nested form) and, with
                                      TPP_FEAT_BLOCK_JACOBI, exact LU (2D, n <= 16; 3D, n <= 6)

@@ -18,6 +18,7 @@ TPP_FEAT_BLOCK_JACOBI, TPP_FEAT_MIXED, TPP_FEAT_TWO_SIDED, TPP_FEAT_LEARNED = 1,
 TPP_FEAT_TIME = 16
 TPP_FEAT_BF16 = 32
 TPP_FEAT_FULL_BLOCKS = 64
+TPP_FEAT_F32_SHIFTS = 128
 TPP_TS_BACKWARD_EULER, TPP_TS_DIRK3, TPP_TS_RK4 = 0, 1, 2
 
 

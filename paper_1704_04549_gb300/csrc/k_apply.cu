@@ -622,7 +622,7 @@ cudaError_t launch_to_f32(const tpp_ctx* c, cudaStream_t s) {
   if (two) {
     add(F.Q2, c->p<double>(c->L.fQ2), m);
     add(F.T2, c->p<double>(c->L.fT2), m);
-  } else {
+  } else if (!(c->features & TPP_FEAT_F32_SHIFTS)) {   // else formed in FP32 by the build
     add(F.G, c->p<double>(c->L.fG), 2 * m * c->n);
   }
   if (c->dim == 3) add(F.Azi, c->p<double>(c->L.fAzi), m);

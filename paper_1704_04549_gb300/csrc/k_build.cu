@@ -439,8 +439,13 @@ __device__ bool warp_gauss_jordan(double* a, int n, double* fac) {
 // holds, in slot c, entry (kr, piv[c]) of the inverse, kr the step at which row r
 // was the pivot (-1 for lanes >= m).  M FMAs per lane and step (the augmented
 // [A | I] form needs up to 2M).  Pivot search on the magnitude bits (integer pipe).
-template <int M>
-__device__ __forceinline__ int warp_gj_inplace(double (&a)[M], int (&piv)[M], int m, bool& sing) {
+__device__ __forceinline__ int mag_key(float v) { return __float_as_int(v) & 0x7fffffff; }
+__device__ __forceinline__ int mag_key(double v) { return __double2hiint(v) & 0x7fffffff; }
+
+// in-place Gauss-Jordan inverse of an m x m matrix with row l in lane l (T = double or
+// float: the one-sided shifted inverses may be formed in FP32 for the FP32 apply)
+template <int M, typename T = double>
+__device__ __forceinline__ int warp_gj_inplace(T (&a)[M], int (&piv)[M], int m, bool& sing) {
   const int lane = threadIdx.x & 31;
   bool used = lane >= m;
   int kr = -1;
@@ -448,7 +453,7 @@ __device__ __forceinline__ int warp_gj_inplace(double (&a)[M], int (&piv)[M], in
   for (int k = 0; k < M; ++k) {
     piv[k] = 0;
     if (k < m) {
-      const int key = used ? -1 : (__double2hiint(a[k]) & 0x7fffffff);
+      const int key = used ? -1 : mag_key(a[k]);
       const int mx = __reduce_max_sync(0xffffffffu, key);
       unsigned bal = __ballot_sync(0xffffffffu, !used && key == mx);
       if (mx <= 0) {
@@ -456,16 +461,16 @@ __device__ __forceinline__ int warp_gj_inplace(double (&a)[M], int (&piv)[M], in
         bal = __ballot_sync(0xffffffffu, !used);
       }
       const int p = __ffs(bal) - 1;
-      const double pv = __shfl_sync(0xffffffffu, a[k], p);
-      const double ip = (pv != 0.0) ? 1.0 / pv : 0.0;
+      const T pv = __shfl_sync(0xffffffffu, a[k], p);
+      const T ip = (pv != T(0)) ? T(1) / pv : T(0);
       const bool isp = (lane == p);
-      const double f = a[k] * ip;
-      const double s1 = isp ? ip : -f;
+      const T f = a[k] * ip;
+      const T s1 = isp ? ip : -f;
 #pragma unroll
       for (int c = 0; c < M; ++c) {
         if (c == k || c >= m) continue;
-        const double v = __shfl_sync(0xffffffffu, a[c], p);
-        a[c] = fma(s1, v, isp ? 0.0 : a[c]);
+        const T v = __shfl_sync(0xffffffffu, a[c], p);
+        a[c] = fma(s1, v, isp ? T(0) : a[c]);
       }
       a[k] = s1;
       if (isp) {
@@ -480,8 +485,8 @@ __device__ __forceinline__ int warp_gj_inplace(double (&a)[M], int (&piv)[M], in
 
 // Complex version for n <= 16: the n x n complex matrix Y0 = C_2 + mu I with row l's
 // real part in lane l and imaginary part in lane l + 16; same in-place scheme.
-__device__ __forceinline__ int warp_gj_inplace_c(double (&a)[16], uint64_t& piv, int n,
-                                                 bool& sing) {
+template <typename T = double>
+__device__ __forceinline__ int warp_gj_inplace_c(T (&a)[16], uint64_t& piv, int n, bool& sing) {
   const int lane = threadIdx.x & 31, row = lane & 15;
   const bool im = lane >= 16;
   bool used = row >= n;
@@ -490,10 +495,9 @@ __device__ __forceinline__ int warp_gj_inplace_c(double (&a)[16], uint64_t& piv,
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     if (k < n) {
-      const double ak = a[k];
-      const double ao = __shfl_xor_sync(0xffffffffu, ak, 16);
-      const int key = used ? -1 : max(__double2hiint(ak) & 0x7fffffff,
-                                      __double2hiint(ao) & 0x7fffffff);
+      const T ak = a[k];
+      const T ao = __shfl_xor_sync(0xffffffffu, ak, 16);
+      const int key = used ? -1 : max(mag_key(ak), mag_key(ao));
       const int mx = __reduce_max_sync(0xffffffffu, key);
       unsigned bal = __ballot_sync(0xffffffffu, !used && !im && key == mx);
       if (mx <= 0) {
@@ -501,24 +505,24 @@ __device__ __forceinline__ int warp_gj_inplace_c(double (&a)[16], uint64_t& piv,
         bal = __ballot_sync(0xffffffffu, !used && !im);
       }
       const int p = __ffs(bal) - 1;
-      const double pr = __shfl_sync(0xffffffffu, ak, p);
-      const double pi = __shfl_sync(0xffffffffu, ak, p + 16);
-      const double den = pr * pr + pi * pi;
-      const double iden = (den != 0.0) ? 1.0 / den : 0.0;
-      const double ipr = pr * iden, ipi = -pi * iden;
-      const double akr = im ? ao : ak, aki = im ? ak : ao;
-      const double fr = akr * ipr - aki * ipi, fi = akr * ipi + aki * ipr;
+      const T pr = __shfl_sync(0xffffffffu, ak, p);
+      const T pi = __shfl_sync(0xffffffffu, ak, p + 16);
+      const T den = pr * pr + pi * pi;
+      const T iden = (den != T(0)) ? T(1) / den : T(0);
+      const T ipr = pr * iden, ipi = -pi * iden;
+      const T akr = im ? ao : ak, aki = im ? ak : ao;
+      const T fr = akr * ipr - aki * ipi, fi = akr * ipi + aki * ipr;
       const bool isp = (row == p);
       // lane value of row_r - f row_p (re: b - fr vr + fi vi, im: b - fr vi - fi vr);
       // pivot row: ip row_p (re: ipr vr - ipi vi, im: ipr vi + ipi vr)
-      const double s1 = isp ? ipr : -fr;
-      const double s2 = isp ? (im ? ipi : -ipi) : (im ? -fi : fi);
+      const T s1 = isp ? ipr : -fr;
+      const T s2 = isp ? (im ? ipi : -ipi) : (im ? -fi : fi);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         if (c == k || c >= n) continue;
-        const double vr = __shfl_sync(0xffffffffu, a[c], p);
-        const double vi = __shfl_sync(0xffffffffu, a[c], p + 16);
-        a[c] = fma(s1, im ? vi : vr, fma(s2, im ? vr : vi, isp ? 0.0 : a[c]));
+        const T vr = __shfl_sync(0xffffffffu, a[c], p);
+        const T vi = __shfl_sync(0xffffffffu, a[c], p + 16);
+        a[c] = fma(s1, im ? vi : vr, fma(s2, im ? vr : vi, isp ? T(0) : a[c]));
       }
       a[k] = isp ? (im ? ipi : ipr) : (im ? -fi : -fr);
       if (isp) {
@@ -992,8 +996,6 @@ __global__ void __launch_bounds__(64) k_invert_w(InvArgs A) {
 // those of B_1 - alpha B_2, and one in-place Gauss-Jordan pass inverts both.  The
 // candidates are ranked in FP32 (their condition numbers only choose alpha); the
 // chosen pair is then inverted in FP64.
-__device__ __forceinline__ int mag_key(float v) { return __float_as_int(v) & 0x7fffffff; }
-__device__ __forceinline__ int mag_key(double v) { return __double2hiint(v) & 0x7fffffff; }
 
 // dual in-place Gauss-Jordan (see warp_gj_inplace) of two m x m matrices, m <= 16,
 // one per half-warp; pivot rows of step k in bits 4k..4k+3 of piv; returns kr.
@@ -1376,17 +1378,17 @@ __device__ __forceinline__ size_t g_index(int n, int j, int row, int col) {
 // Invert the shifted system of the column block at j (size m) and store its
 // rows in G.  Kept out of line: inside the block loop of the caller the fully
 // unrolled elimination would otherwise not stay in registers.
-template <int M>
+template <int M, typename T = double>
 __device__ __noinline__ bool shift_inv_block(const double* Tg, const double* Cg, bool rank1, int n,
-                                             int j, int m, double* Ge) {
+                                             int j, int m, T* Ge) {
   const int lane = threadIdx.x & 31;
   bool sing = false;
-  double a[M];
+  T a[M];
   int piv[M];
 #pragma unroll
   for (int c = 0; c < M; ++c)
-    a[c] = (lane < m && c < m) ? shifted_entry(Tg, Cg, rank1, n, j, lane, c) : 0.0;
-  const int kr = warp_gj_inplace<M>(a, piv, m, sing);
+    a[c] = (lane < m && c < m) ? (T)shifted_entry(Tg, Cg, rank1, n, j, lane, c) : T(0);
+  const int kr = warp_gj_inplace<M, T>(a, piv, m, sing);
   if (kr >= 0) {
 #pragma unroll
     for (int c = 0; c < M; ++c)
@@ -1403,8 +1405,9 @@ __device__ __noinline__ bool shift_inv_block(const double* Tg, const double* Cg,
 // c_ab = D_a w_a [W^-1]_{0b} / D_b: one complex n x n inverse instead of a real
 // 2n x 2n one.  Returns 0 without writing when the block is not a well-separated
 // complex pair (|Im mu| < 0.0316 |t01'|: W near singular); bit 0 = done, bit 1 = singular.
+template <typename T = double>
 __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg, int n, int j,
-                                             double* Ge) {
+                                             T* Ge) {
   double t00 = Tg[j + n * j], t01 = Tg[j + n * (j + 1)];
   double t10 = Tg[(j + 1) + n * j], t11 = Tg[(j + 1) + n * (j + 1)];
   if (!(t01 * t10 < 0.0)) return 0;
@@ -1417,16 +1420,16 @@ __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg,
 
   const int lane = threadIdx.x & 31, row = lane & 15;
   const bool im = lane >= 16;
-  double a[16];
+  T a[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     double v = 0.0;
     if (row < n && c < n) v = im ? ((c == row) ? y : 0.0) : Cg[row + n * c] + ((c == row) ? x : 0.0);
-    a[c] = v;
+    a[c] = (T)v;
   }
   bool sing = false;
   uint64_t piv;
-  const int kr = warp_gj_inplace_c(a, piv, n, sing);
+  const int kr = warp_gj_inplace_c<T>(a, piv, n, sing);
   // coefficients (recomputed here to keep them out of the elimination's registers):
   // w = (b01, -hd + i y); 1 / det W = i idet, idet = 1 / (2 y b01);
   // u = [W^-1]_{0.} = ((y - i hd) idet, -i b01 idet); c_ab = D_a w_a u_b / D_b
@@ -1455,13 +1458,13 @@ __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg,
   const int ab = im ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
-    const double own = a[c];
-    const double oth = __shfl_xor_sync(0xffffffffu, own, 16);
+    const T own = a[c];
+    const T oth = __shfl_xor_sync(0xffffffffu, own, 16);
     if (c < n && kr >= 0) {
-      const double yr = im ? oth : own, yi = im ? own : oth;
+      const T yr = im ? oth : own, yi = im ? own : oth;
       const int kc = (int)((piv >> (4 * c)) & 15u);
-      Ge[g_index(n, j, ab * n + kr, kc)] = 2.0 * (car0 * yr - cai0 * yi);
-      Ge[g_index(n, j, ab * n + kr, n + kc)] = 2.0 * (car1 * yr - cai1 * yi);
+      Ge[g_index(n, j, ab * n + kr, kc)] = T(2) * ((T)car0 * yr - (T)cai0 * yi);
+      Ge[g_index(n, j, ab * n + kr, n + kc)] = T(2) * ((T)car1 * yr - (T)cai1 * yi);
     }
   }
   return 1 | (sing ? 2 : 0);
@@ -1471,10 +1474,10 @@ __device__ __noinline__ int shift_inv_pair_c(const double* Tg, const double* Cg,
 // own rows); 2x2 blocks: the complex form above, else (nearly defective
 // blocks) a bit in fb[e] for k_shift_inv_fb, which inverts the real 2n x 2n
 // system.
-template <int M>
+template <int M, typename T = double>
 __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const double* T1,
                                                      const double* C2, const uint32_t* masks,
-                                                     int32_t* flags, double* G, uint32_t* fb,
+                                                     int32_t* flags, T* G, uint32_t* fb,
                                                      DevStatus* st) {
   const int nn = n * n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1484,7 +1487,7 @@ __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const dou
   const double* Cg = C2 + e * nn;
   const bool rank1 = (flags[e] & 2) != 0;
   const uint32_t m1 = masks[2 * e];
-  double* Ge = G + (size_t)e * 2 * n * nn;
+  T* Ge = G + (size_t)e * 2 * n * nn;
   // block starts (the same walk as the apply), then Gp of 1x1 blocks is zero
   uint32_t cst = 0;
   for (int r = 0; r < n;) {
@@ -1495,7 +1498,7 @@ __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const dou
   for (int q = lane; q < 2 * n * nn; q += 32) {
     const int j = q / (2 * nn), sblk = (q / nn) & 1;
     const bool pairj = ((cst >> j) & 1u) || (j > 0 && ((cst >> (j - 1)) & 1u));
-    if (sblk == 1 && !pairj) Ge[q] = 0.0;
+    if (sblk == 1 && !pairj) Ge[q] = T(0);
   }
   bool sing = false;
   uint32_t fbits = 0;
@@ -1503,11 +1506,11 @@ __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const dou
   while (j < n) {
     const bool pair = ((m1 >> j) & 1u) && j + 1 < n;
     if (pair) {
-      const int pc = rank1 ? 0 : shift_inv_pair_c(Tg, Cg, n, j, Ge);
+      const int pc = rank1 ? 0 : shift_inv_pair_c<T>(Tg, Cg, n, j, Ge);
       if (pc) sing |= (pc & 2) != 0;
       else fbits |= 1u << j;
     } else {
-      sing |= shift_inv_block<M / 2>(Tg, Cg, rank1, n, j, n, Ge);
+      sing |= shift_inv_block<M / 2, T>(Tg, Cg, rank1, n, j, n, Ge);
     }
     j += pair ? 2 : 1;
   }
@@ -1521,9 +1524,9 @@ __global__ void __launch_bounds__(128) k_shift_inv_r(int n, int64_t E, const dou
 }
 
 // the real 2n x 2n inverses of the 2x2 blocks k_shift_inv_r left (bits of fb[e])
-template <int M>
+template <int M, typename T = double>
 __global__ void __launch_bounds__(128) k_shift_inv_fb(int n, int64_t E, const double* T1,
-                                                      const double* C2, int32_t* flags, double* G,
+                                                      const double* C2, int32_t* flags, T* G,
                                                       const uint32_t* fb, DevStatus* st) {
   const int nn = n * n;
   const int warp = threadIdx.x >> 5;
@@ -1536,7 +1539,7 @@ __global__ void __launch_bounds__(128) k_shift_inv_fb(int n, int64_t E, const do
   while (bits) {
     const int j = __ffs(bits) - 1;
     bits &= bits - 1;
-    sing |= shift_inv_block<M>(T1 + e * nn, C2 + e * nn, rank1, n, j, 2 * n,
+    sing |= shift_inv_block<M, T>(T1 + e * nn, C2 + e * nn, rank1, n, j, 2 * n,
                                G + (size_t)e * 2 * n * nn);
   }
   if ((threadIdx.x & 31) == 0 && sing) {
@@ -1874,7 +1877,18 @@ cudaError_t launch_factor_inverse(const tpp_ctx* c, cudaStream_t s) {
     cudaError_t err;
     uint32_t* fb = reinterpret_cast<uint32_t*>(c->p<int>(c->L.biscr));   // free after the KSVD
     const unsigned gw = (unsigned)((E + 3) / 4);
-    if (n <= 8) {
+    if (c->features & TPP_FEAT_F32_SHIFTS) {   // FP32 inverses straight into the FP32 copies
+      float* G32 = c->p<float>(c->L.f32) + f32_layout(n, c->E, c->dim, false).G;
+      if (n <= 8) {
+        k_shift_inv_r<16, float><<<gw, 128, 0, s>>>(n, E, T1p, C2p, mk, fl, G32, fb, st);
+        count_launch();
+        k_shift_inv_fb<16, float><<<gw, 128, 0, s>>>(n, E, T1p, C2p, fl, G32, fb, st);
+      } else {
+        k_shift_inv_r<32, float><<<gw, 128, 0, s>>>(n, E, T1p, C2p, mk, fl, G32, fb, st);
+        count_launch();
+        k_shift_inv_fb<32, float><<<gw, 128, 0, s>>>(n, E, T1p, C2p, fl, G32, fb, st);
+      }
+    } else if (n <= 8) {
       k_shift_inv_r<16><<<gw, 128, 0, s>>>(n, E, T1p, C2p, mk, fl, Gp, fb, st);
       count_launch();
       k_shift_inv_fb<16><<<gw, 128, 0, s>>>(n, E, T1p, C2p, fl, Gp, fb, st);

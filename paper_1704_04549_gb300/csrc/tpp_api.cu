@@ -188,7 +188,9 @@ Layout compute_layout(const tpp_problem* p, int32_t max_restart, uint32_t featur
     L.sigz = take((size_t)E * 8);
     L.zflags = take((size_t)E * 4);
   }
-  L.fG = two ? 0 : take(fsz * 2 * n);
+  // the one-sided shifted inverses (2 n^3 doubles per element); with TPP_FEAT_F32_SHIFTS
+  // they exist only as the FP32 copies
+  L.fG = (two || (features & TPP_FEAT_F32_SHIFTS)) ? 0 : take(fsz * 2 * n);
   if (features & TPP_FEAT_LEARNED) {
     const size_t r = (size_t)n + rz;
     L.lx = take((size_t)E * (2 * n * n + 1) * 4);
@@ -271,6 +273,20 @@ cudaError_t apply_precond(const tpp_ctx* c, int pc, int prec, const double* b, d
 
 using namespace tpp;
 
+namespace {
+// TPP_FEAT_F32_SHIFTS: the shifted inverses of the one-sided form in FP32 only, for the
+// FP32 apply of the mixed-precision solver
+const char* f32_shifts_invalid(const tpp_problem* prob, uint32_t features) {
+  if (!(features & TPP_FEAT_F32_SHIFTS)) return nullptr;
+  if (!(features & TPP_FEAT_MIXED) || (features & (TPP_FEAT_TWO_SIDED | TPP_FEAT_BF16 |
+                                                   TPP_FEAT_TIME | TPP_FEAT_LEARNED)) ||
+      prob->n > 16 || prob->mu > prob->n)
+    return "TPP_FEAT_F32_SHIFTS needs TPP_FEAT_MIXED and the one-sided form, n <= 16, mu <= n, "
+           "and excludes TPP_FEAT_BF16, TPP_FEAT_TIME and TPP_FEAT_LEARNED";
+  return nullptr;
+}
+}  // namespace
+
 extern "C" {
 
 const char* tpp_last_error(void) { return g_last_error.c_str(); }
@@ -279,6 +295,10 @@ int64_t tpp_kernel_launch_count(void) { return g_launches.load(std::memory_order
 
 size_t tpp_workspace_bytes(const tpp_problem* prob, int32_t max_restart, uint32_t features) {
   if (validate(prob, max_restart)) return 0;
+  if (const char* why = f32_shifts_invalid(prob, features)) {
+    set_error(why);
+    return 0;
+  }
   return compute_layout(prob, max_restart, features, nullptr).total;
 }
 
@@ -301,6 +321,10 @@ tpp_status tpp_create(tpp_ctx** out, const tpp_problem* prob, int32_t max_restar
       (prob->dim != 2 || prob->n > 16 || (features & TPP_FEAT_TWO_SIDED))) {
     set_error("the BF16 tensor-core apply is implemented for 2D, n <= 16, one-sided form");
     return TPP_ERR_UNSUPPORTED;
+  }
+  if (const char* why = f32_shifts_invalid(prob, features)) {
+    set_error(why);
+    return TPP_ERR_INVALID_ARG;
   }
   if (prob->mu > prob->n &&
       (features & (TPP_FEAT_BLOCK_JACOBI | TPP_FEAT_LEARNED | TPP_FEAT_TIME | TPP_FEAT_BF16))) {
@@ -612,6 +636,11 @@ tpp_status tpp_apply_inverse(const tpp_ctx* c, const double* b, double* x, int32
     set_error("TPP_FP32 apply needs a context created with TPP_FEAT_MIXED");
     return TPP_ERR_INVALID_ARG;
   }
+  if (prec == TPP_FP64 && (c->features & TPP_FEAT_F32_SHIFTS)) {
+    set_error("the context keeps its shifted inverses in FP32 only (TPP_FEAT_F32_SHIFTS): "
+              "apply with TPP_FP32");
+    return TPP_ERR_INVALID_ARG;
+  }
   if (prec == TPP_BF16 && !(c->features & TPP_FEAT_BF16)) {
     set_error("TPP_BF16 apply needs a context created with TPP_FEAT_BF16");
     return TPP_ERR_INVALID_ARG;
@@ -714,7 +743,7 @@ tpp_status tpp_get_views(const tpp_ctx* c, tpp_views* o) {
   o->SB = c->p<double>(c->L.fSB);
   o->Q1 = c->p<double>(c->L.fQ1);
   o->Q2 = two_sided(c) ? c->p<double>(c->L.fQ2) : nullptr;
-  o->G = two_sided(c) ? nullptr : c->p<double>(c->L.fG);
+  o->G = (two_sided(c) || !c->L.fG) ? nullptr : c->p<double>(c->L.fG);
   o->T1 = c->p<double>(c->L.fT1);
   o->T2 = c->p<double>(c->L.fT2);
   o->flags = c->p<int32_t>(c->L.flags);
@@ -780,6 +809,12 @@ tpp_status gmres_solve(tpp_ctx* c, const double* b, double* x, const tpp_gmres_o
   }
   if (opts->inner_prec == TPP_BF16 && !(c->features & TPP_FEAT_BF16)) {
     set_error("inner_prec TPP_BF16 needs TPP_FEAT_BF16");
+    return TPP_ERR_INVALID_ARG;
+  }
+  if (opts->pc == TPP_PC_KRON && opts->inner_prec == TPP_FP64 && opts->inner_iters <= 0 &&
+      (c->features & TPP_FEAT_F32_SHIFTS)) {
+    set_error("TPP_FEAT_F32_SHIFTS: the Kronecker preconditioner runs in FP32 (inner_prec "
+              "TPP_FP32, or inner FP32 solves with inner_iters > 0)");
     return TPP_ERR_INVALID_ARG;
   }
   if (opts->inner_prec == TPP_FP32 && !(c->features & TPP_FEAT_MIXED)) {

@@ -403,6 +403,7 @@ class Context:
             # column-major n x n per element -> [E, n, n] with [e, row, col]
             t = grab(getattr(v, name), E * n * n, torch.float64)
             res[name] = None if t is None else t.view(E, n, n).transpose(1, 2)
+        res["G"] = grab(v.G, E * 2 * n ** 3, torch.float64)   # one-sided shifted inverses
         res["flags"] = grab(v.flags, E, torch.int32)
         res["cond"] = grab(v.cond, E, torch.float64)
         res["gl_x"] = grab(v.gl_x, n, torch.float64)

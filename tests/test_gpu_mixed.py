@@ -74,6 +74,43 @@ def test_apply_f32_vs_oracle(n, nel):
     print(f"FP32 apply vs oracle, n={n} {nel}: max element relative error {worst:.2e}")
 
 
+# TPP_FEAT_F32_SHIFTS: the shifted inverses are formed by an FP32 Gauss-Jordan from the
+# FP64 Schur factors (first-order error about n u32 cond(C_2 + lambda I) per inverse).
+# Measured on the GB300 over these cases: at most 4.4e-7 (2D, n = 8 and 16), the same as
+# the FP64-formed inverses rounded to FP32; the asserted bound is about 10x that.
+F32_SHIFTS_BOUND = 5e-6
+
+
+@pytest.mark.parametrize("n,nel", [(8, (4, 4)), (16, (4, 4)), (6, (2, 2, 2)), (11, (2, 2, 2))])
+def test_f32_shift_inverses(n, nel):
+    """Contexts whose one-sided shifted inverses exist only in FP32 (formed on the FP32
+    pipe): the FP32 apply against the oracle's dense LU solve, FP64 Kronecker applies
+    refused, and the nested mixed solver reaching the FP64 true residual 1e-8."""
+    from paper_1704_04549_gb300 import TPP_FEAT_F32_SHIFTS, TppError
+    ctx, dg = make_pair(n, nel, 0.05, _vel(len(nel), 1),
+                        features=TPP_FEAT_MIXED | TPP_FEAT_F32_SHIFTS, h=1.0)
+    ctx.tpp_build_factors()
+    assert ctx.views()["G"] is None
+    b = synthetic.rhs(99, dg.ndof)
+    xd = to_host(ctx.tpp_apply_inverse(to_dev(b), prec=TPP_FP32))
+    nl, worst = dg.nloc, 0.0
+    for e in range(dg.mesh.num_elem):
+        x_ref = apply_dense(_oracle_P(dg, e), b[e * nl:(e + 1) * nl])
+        err = rel(xd[e * nl:(e + 1) * nl], x_ref)
+        worst = max(worst, err)
+        assert err <= F32_SHIFTS_BOUND, (e, err)
+    print(f"FP32-formed shifted inverses, n={n} {nel}: max element relative error {worst:.2e}")
+    with pytest.raises(TppError):
+        ctx.tpp_apply_inverse(to_dev(b))
+    with pytest.raises(TppError):                  # FP64 GMRES with the FP64 apply
+        ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8)
+    x, r = ctx.gmres_solve(to_dev(b), pc=TPP_PC_KRON, rtol=1e-8, inner_iters=12)
+    assert r["converged"] and r["true_rel_res"] <= 1e-8
+    S = dg.global_matrix()
+    assert np.linalg.norm(b - S @ to_host(x)) <= 1.0001e-8 * np.linalg.norm(b)
+    print(f"  mixed solve: {r['iters']} outer, {r['inner_iters']} inner")
+
+
 @pytest.mark.parametrize("n,nel,kmax,kin", [(8, (4, 4), 1, 8), (16, (4, 4), 1, 12),
                                             (16, (64, 64), 4, 16), (5, (3, 3, 3), 4, 10),
                                             (11, (16, 16, 16), 1, 16)])

@@ -224,3 +224,22 @@ def test_batch_and_metric_argument_checks(L):
     om.prec, om.max_outer, om.inner_rtol = L.TPP_FP32, 0, 1e-4
     assert lib.tpp_batch_workspace_bytes(dummy, 1, C.byref(om)) == 0
     assert lib.tpp_set_metric_terms(None, None, None, None, 0.1, None) == 1  # NULL context
+
+
+def test_f32_shifts_feature_validation(L):
+    """TPP_FEAT_F32_SHIFTS: with TPP_FEAT_MIXED and the one-sided form only; the 2 n^3
+    FP64 shifted inverses per element are then not reserved."""
+    lib = L.load()
+    P, _keep = _problem(L, n=16, nel=(4, 4))
+    MIX, F32S = L.TPP_FEAT_MIXED, L.TPP_FEAT_F32_SHIFTS
+    full = lib.tpp_workspace_bytes(C.byref(P), 30, MIX)
+    lean = lib.tpp_workspace_bytes(C.byref(P), 30, MIX | F32S)
+    assert 0 < lean and full - lean >= 16 * 2 * 16 ** 3 * 8
+    for bad in (F32S, F32S | MIX | L.TPP_FEAT_TWO_SIDED, F32S | MIX | L.TPP_FEAT_BF16,
+                F32S | MIX | L.TPP_FEAT_TIME, F32S | MIX | L.TPP_FEAT_LEARNED):
+        assert lib.tpp_workspace_bytes(C.byref(P), 30, bad) == 0, bad
+    assert b"TPP_FEAT_F32_SHIFTS" in lib.tpp_last_error()
+    P17, _k17 = _problem(L, n=17, nel=(2, 2))
+    assert lib.tpp_workspace_bytes(C.byref(P17), 30, MIX | F32S) == 0
+    P3, _k3 = _problem(L, dim=3, n=6, nel=(2, 2, 2))
+    assert lib.tpp_workspace_bytes(C.byref(P3), 30, MIX | F32S) > 0
