@@ -393,3 +393,36 @@ def test_3d_full_block_factors_and_gmres(n, nel):
     assert np.linalg.norm(b - S @ to_host(xg)) <= 1.0001e-8 * np.linalg.norm(b)
     print(f"3D Euler n={n}: K_full P error {worst:.1e}, power iterations {int(fsig[:, 1].max())}, "
           f"GMRES {r['iters']} (oracle {o['iters']})")
+
+
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 5), (3, 1), (3, 4)])
+def test_full_blocks_degenerate_cases(dim, n):
+    """dt = 0: every full block is the mass alone, an exact single Kronecker product, so the
+    full-block preconditioner is exact (P^-1 b = S^-1 b); n = 1: one node per element
+    (D = 0, the face terms only)."""
+    from paper_1704_04549_gb300 import TPP_FEAT_FULL_BLOCKS
+    for dt in (0.0, 0.05):
+        if dim == 2:
+            ctx, ora = _pair(n, (3, 2), 5.0, dt, features=TPP_FEAT_FULL_BLOCKS)
+        else:
+            ctx, ora = _pair3d(n, (2, 2, 2), dt, features=TPP_FEAT_FULL_BLOCKS)
+        rep = ctx.tpp_build_factors()
+        assert rep["num_schur_fail"] == 0
+        b = synthetic.rhs(41, ora.ndof)
+        x = to_host(ctx.tpp_apply_inverse(to_dev(b)))
+        bs = ora.bs
+        for e in range(ora.mesh.num_elem):
+            blk = slice(e * bs, (e + 1) * bs)
+            if dt == 0.0:
+                Se = ora.element_block(e)
+                assert rel(x[blk], np.linalg.solve(Se, b[blk])) <= 1e-13, (dt, e)
+            else:
+                P = (kron_sum(*ora.full_block_ksvd(e)[1:]) if dim == 2
+                     else ora.full_block_ksvd_3d(e)["P"])
+                assert rel(x[blk], np.linalg.solve(P, b[blk])) <= solve_tol(np.linalg.cond(P)), e
+        if dt == 0.0 and dim == 2:
+            # sigma_2 of an exactly rank-1 block through the Gram matrix: a rounding-level
+            # eigenvalue, so about sqrt(eps) sigma_1 (its factors' product stays at eps level,
+            # which the exact apply above shows)
+            fs = to_host(ctx.views()["fsig"])
+            assert np.all(fs[:, 1] <= 1e-6 * fs[:, 0])
