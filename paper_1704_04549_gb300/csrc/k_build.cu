@@ -702,7 +702,13 @@ __device__ int sturm_count_gk(const double* e2, int m, double x) {
   return cnt;
 }
 
+// per-thread shared-memory work of k_ksvd_tri (doubles): squared off-diagonal, the
+// three U diagonals, the L multipliers, the vector (6 m) and the pivots (m ints); odd so
+// that the 32 threads' regions start in different banks
+__host__ __device__ inline int tri_stride(int m) { return (6 * m + (m + 1) / 2 + 1) | 1; }
+
 __global__ void __launch_bounds__(32) k_ksvd_tri(KsvdArgs A) {
+  extern __shared__ double smt[];
   const int n = A.n, rz = A.rz, r = n + rz;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t e = t >> 1;
@@ -717,6 +723,14 @@ __global__ void __launch_bounds__(32) k_ksvd_tri(KsvdArgs A) {
     S[L.scal + k] = 0.0;
     return;
   }
+  // the recurrences below are chains of dependent steps: their operands live in shared
+  // memory, not in the global scratch (an L2 round trip per step)
+  double* my = smt + (size_t)threadIdx.x * tri_stride(m);
+  double* e2 = my;                             // squared scaled off-diagonal
+  double* w0 = my + m;                         // d, du, du2
+  double* dl = my + 4 * m;                     // off-diagonal, then the L multipliers
+  double* zs = my + 5 * m;
+  int* piv = reinterpret_cast<int*>(my + 6 * m);
   double bnd = 0.0;
   for (int i = 0; i < m; ++i) {
     const double a = (i > 0) ? fabs(((i - 1) & 1) ? be[i >> 1] : al[(i - 1) >> 1]) : 0.0;
@@ -730,8 +744,6 @@ __global__ void __launch_bounds__(32) k_ksvd_tri(KsvdArgs A) {
   // itself is the Rayleigh quotient of the converged vector, accurate to the
   // square of the vector's error)
   const int idx = m - k;
-  double* w0 = S + L.total + (size_t)k * 4 * m;
-  double* e2 = w0 + 2 * m;                     // squared scaled off-diagonal (du2 slot)
   for (int i = 0; i < m - 1; ++i) {
     const double es = ((i & 1) ? be[(i + 1) >> 1] : al[i >> 1]) * ib;
     e2[i] = es * es;
@@ -743,18 +755,16 @@ __global__ void __launch_bounds__(32) k_ksvd_tri(KsvdArgs A) {
     else lo = mid;
   }
   const double lam = 0.5 * (lo + hi) * bnd;
-  // eigenvector by inverse iteration on the unscaled tridiagonal, in this thread's
-  // 4m of work (d, du, du2, dl; dl starts as the off-diagonal, which the
-  // factorisation reads entry by entry before overwriting it)
-  int* piv = A.iscr + (size_t)e * 4 * r + (size_t)k * m;
-  double* z = S + (k ? L.z2 : L.z1);
-  double* dl = w0 + 3 * m;
+  // eigenvector by inverse iteration on the unscaled tridiagonal (dl starts as the
+  // off-diagonal, which the factorisation reads entry by entry before overwriting it)
   for (int i = 0; i < m - 1; ++i) dl[i] = (i & 1) ? be[(i + 1) >> 1] : al[i >> 1];
-  for (int i = 0; i < m; ++i) z[i] = splitmix_unit(300 + k, i);
-  inverse_iteration(dl, m, lam, z, w0, w0 + m, w0 + 2 * m, dl, piv, kEps * bnd + 1e-300);
+  for (int i = 0; i < m; ++i) zs[i] = splitmix_unit(300 + k, i);
+  inverse_iteration(dl, m, lam, zs, w0, w0 + m, w0 + 2 * m, dl, piv, kEps * bnd + 1e-300);
   // Rayleigh quotient z^T T z = 2 sum_i ee_i z_i z_{i+1} (|z| = 1; zero diagonal)
   double rq = 0.0;
-  for (int i = 0; i < m - 1; ++i) rq = fma((i & 1) ? be[(i + 1) >> 1] : al[i >> 1], z[i] * z[i + 1], rq);
+  for (int i = 0; i < m - 1; ++i) rq = fma((i & 1) ? be[(i + 1) >> 1] : al[i >> 1], zs[i] * zs[i + 1], rq);
+  double* z = S + (k ? L.z2 : L.z1);
+  for (int i = 0; i < m; ++i) z[i] = zs[i];
   S[L.scal + k] = 2.0 * rq;
 }
 
@@ -1790,7 +1800,10 @@ cudaError_t launch_ksvd_pipeline(const tpp_ctx* c, cudaStream_t s, const int32_t
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // one thread per (element, k): 32-thread CTAs spread the 2 E sequential problems over
     // every SM (the FP64 pipe of an SM, not its warp count, bounds this kernel)
-    k_ksvd_tri<<<(unsigned)((2 * E + 31) / 32), 32, 0, s>>>(ka);
+    const size_t tsm = (size_t)32 * tri_stride(2 * (n + ka.rz)) * sizeof(double);
+    err = cudaFuncSetAttribute(k_ksvd_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+    if (err != cudaSuccess) return err;
+    k_ksvd_tri<<<(unsigned)((2 * E + 31) / 32), 32, tsm, s>>>(ka);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_ksvd_vec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
