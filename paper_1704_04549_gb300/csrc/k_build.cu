@@ -2060,6 +2060,9 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
   double *yu = S + L.yu, *wv = S + L.wv, *cw = S + L.cw, *tmp = S + L.tmp;
   double *al = S + L.al, *be = S + L.be, *yv = S + L.y;
   double* aug = sm1 + (size_t)warp * (2 * nn + n + 40);
+  // per warp: tridiagonal (al, be), the inverse iteration's LU and vector, pivots
+  double* tri = sm1 + (size_t)(blockDim.x >> 5) * (2 * nn + n + 40) + (size_t)warp * 520;
+  double *als = tri, *bes = tri + 65;
   double* fac = aug + 2 * nn;
   double* cfs = fac + n + 8;   // 32 reorthogonalisation coefficients
   const double* fe = A.fa + e * 6 * nn;      // faces -x, +x, -y, +y, -z, +z
@@ -2162,17 +2165,24 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
     __syncwarp();
     const bool check = breakdown || J == Jmax || J == nn || (J >= 8 && (J % 8) == 0);
     if (!check) continue;
-    // top eigenvalue of the J x J tridiagonal by 32-point multisection
+    // top eigenvalue of the J x J tridiagonal by 32-point multisection; the tridiagonal
+    // and the inverse iteration's work sit in this warp's shared memory (their recurrences
+    // are chains of dependent steps)
+    for (int i = lane; i <= J; i += 32) {
+      if (i < J) als[i] = al[i];
+      bes[i] = be[i];
+    }
+    __syncwarp();
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < J; ++i) {
-      const double rad = ((i > 0) ? fabs(be[i]) : 0.0) + ((i + 1 < J) ? fabs(be[i + 1]) : 0.0);
-      lo = fmin(lo, al[i] - rad);
-      hi = fmax(hi, al[i] + rad);
+      const double rad = ((i > 0) ? fabs(bes[i]) : 0.0) + ((i + 1 < J) ? fabs(bes[i + 1]) : 0.0);
+      lo = fmin(lo, als[i] - rad);
+      hi = fmax(hi, als[i] + rad);
     }
     const double tiny = 1e-300 + kEps * fmax(fabs(lo), fabs(hi));
     for (int it = 0; it < 12; ++it) {
       const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
-      const int cnt = sturm_sym(al, be, J, x, tiny);
+      const int cnt = sturm_sym(als, bes, J, x, tiny);
       const unsigned ge = __ballot_sync(0xffffffffu, cnt >= J);
       const int f = ge ? (__ffs(ge) - 1) : 32;
       const double wdt = hi - lo;
@@ -2184,15 +2194,16 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
     lam = 0.5 * (lo + hi);
     // eigenvector by inverse iteration (lane 0; tridiagonal with pivoting)
     if (lane == 0) {
-      double *d = S + L.d, *du = S + L.du, *du2 = S + L.du2, *dl = S + L.dl;
-      int* pv = reinterpret_cast<int*>(S + L.pv);
+      double *d = tri + 130, *du = tri + 194, *du2 = tri + 258, *dl = tri + 322;
+      double* ys = tri + 386;
+      int* pv = reinterpret_cast<int*>(tri + 450);
       for (int i = 0; i < J; ++i) {
-        d[i] = al[i] - lam;
-        du[i] = (i + 1 < J) ? be[i + 1] : 0.0;
-        dl[i] = (i + 1 < J) ? be[i + 1] : 0.0;
+        d[i] = als[i] - lam;
+        du[i] = (i + 1 < J) ? bes[i + 1] : 0.0;
+        dl[i] = (i + 1 < J) ? bes[i + 1] : 0.0;
         du2[i] = 0.0;
         pv[i] = 0;
-        yv[i] = splitmix_unit(11, i);
+        ys[i] = splitmix_unit(11, i);
       }
       for (int i = 0; i + 1 < J; ++i) {
         if (fabs(d[i]) >= fabs(dl[i])) {
@@ -2218,24 +2229,25 @@ __global__ void __launch_bounds__(128) k_stage1_3d(Stage1Args A) {
       for (int it = 0; it < 3; ++it) {
         for (int i = 0; i + 1 < J; ++i) {
           if (pv[i]) {
-            const double t = yv[i];
-            yv[i] = yv[i + 1];
-            yv[i + 1] = t;
+            const double t = ys[i];
+            ys[i] = ys[i + 1];
+            ys[i + 1] = t;
           }
-          yv[i + 1] -= dl[i] * yv[i];
+          ys[i + 1] -= dl[i] * ys[i];
         }
         for (int i = J - 1; i >= 0; --i) {
-          double sv = yv[i];
-          if (i + 1 < J) sv -= du[i] * yv[i + 1];
-          if (i + 2 < J) sv -= du2[i] * yv[i + 2];
-          yv[i] = sv / d[i];
+          double sv = ys[i];
+          if (i + 1 < J) sv -= du[i] * ys[i + 1];
+          if (i + 2 < J) sv -= du2[i] * ys[i + 2];
+          ys[i] = sv / d[i];
         }
         double nr = 0.0;
-        for (int i = 0; i < J; ++i) nr += yv[i] * yv[i];
+        for (int i = 0; i < J; ++i) nr += ys[i] * ys[i];
         nr = 1.0 / sqrt(nr);
-        for (int i = 0; i < J; ++i) yv[i] *= nr;
+        for (int i = 0; i < J; ++i) ys[i] *= nr;
       }
-      tmp[0] = (breakdown ? 0.0 : be[J]) * fabs(yv[J - 1]);   // Ritz residual
+      for (int i = 0; i < J; ++i) yv[i] = ys[i];
+      tmp[0] = (breakdown ? 0.0 : bes[J]) * fabs(ys[J - 1]);   // Ritz residual
     }
     __syncwarp();
     conv = breakdown || tmp[0] <= 1e-14 * fabs(lam) || J == nn;
@@ -2341,7 +2353,7 @@ cudaError_t launch_build_3d(const tpp_ctx* c, cudaStream_t s) {
   a.zflags = c->p<int32_t>(c->L.zflags);
   a.st = c->p<DevStatus>(c->L.status);
   const int warps = 4;
-  const size_t smem = (size_t)warps * (2 * n * n + n + 40) * sizeof(double);
+  const size_t smem = (size_t)warps * (2 * n * n + n + 40 + 520) * sizeof(double);
   k_stage1_3d<<<(unsigned)((c->E + warps - 1) / warps), warps * 32, smem, s>>>(a);
   count_launch();
   cudaError_t err = cudaGetLastError();
