@@ -277,6 +277,80 @@ __global__ void k_sys_apply_3d(const Tables* T, int n, double hd, const double* 
   }
 }
 
+// the same operator with all five components in one pass (n <= 8: the 15 n^3 flux
+// partials and 30 n^2 face fluxes of an element fit in shared memory), two barriers
+// instead of two per component, so every component's coefficient loads are in flight at once
+__global__ void k_sys_apply_3d_all(const Tables* T, int n, double hd, const double* __restrict__ scx,
+                                   const double* __restrict__ scy, const double* __restrict__ scz,
+                                   const double* __restrict__ sfo, const double* __restrict__ sfn,
+                                   const int32_t* __restrict__ nbr, const double* __restrict__ x,
+                                   const double* __restrict__ tr, double* __restrict__ y,
+                                   const int32_t* skip) {
+  constexpr int kNc = 5;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) double sms[];
+  const int nn = n * n, n3 = nn * n, tid = threadIdx.x, nt = blockDim.x;
+  double* Ds = sms;                 // n^2
+  double* wl = Ds + nn;             // w, l0, l1
+  double* xs = wl + 3 * n;          // kNc n^3
+  double* pp = xs + kNc * n3;       // [c][d][n^3], d = x, y, z
+  double* fl = pp + 3 * kNc * n3;   // [c][6][n^2]
+  const int64_t e = blockIdx.x;
+  for (int q = tid; q < nn; q += nt) Ds[q] = T->D[q];
+  for (int q = tid; q < n; q += nt) {
+    wl[q] = T->w[q];
+    wl[n + q] = T->l0[q];
+    wl[2 * n + q] = T->l1[q];
+  }
+  for (int q = tid; q < kNc * n3; q += nt) xs[q] = x[e * kNc * n3 + q];
+  int nbf[6];
+  for (int f = 0; f < 6; ++f) nbf[f] = nbr[e * 6 + f];
+  __syncthreads();
+  for (int q = tid; q < kNc * n3; q += nt) {
+    const int c = q / n3, node = q % n3;
+    double a = 0.0, b = 0.0, d = 0.0;
+    for (int c2 = 0; c2 < kNc; ++c2) {
+      const int64_t o = ((e * kNc + c) * kNc + c2) * n3 + node;
+      const double xv = xs[c2 * n3 + node];
+      a += scx[o] * xv;
+      b += scy[o] * xv;
+      d += scz[o] * xv;
+    }
+    pp[(c * 3 + 0) * n3 + node] = a;
+    pp[(c * 3 + 1) * n3 + node] = b;
+    pp[(c * 3 + 2) * n3 + node] = d;
+  }
+  for (int g = tid; g < kNc * 6 * nn; g += nt) {
+    const int c = g / (6 * nn), f = (g / nn) % 6, t = g % nn;
+    const int nb = nbf[f];
+    double F = 0.0;
+    for (int c2 = 0; c2 < kNc; ++c2) {
+      const int64_t o = (((e * 6 + f) * kNc + c) * kNc + c2) * nn + t;
+      F += sfo[o] * tr[((e * kNc + c2) * 6 + f) * nn + t];
+      if (nb >= 0) F += sfn[o] * tr[(((int64_t)nb * kNc + c2) * 6 + (f ^ 1)) * nn + t];
+    }
+    fl[g] = F;
+  }
+  __syncthreads();
+  for (int q = tid; q < kNc * n3; q += nt) {
+    const int c = q / n3, node = q % n3;
+    const int i = node % n, j = (node / n) % n, k = node / nn;
+    const double* px = pp + (c * 3 + 0) * n3;
+    const double* py = pp + (c * 3 + 1) * n3;
+    const double* pz = pp + (c * 3 + 2) * n3;
+    const double* fc = fl + c * 6 * nn;
+    double acc = hd * wl[i] * wl[j] * wl[k] * xs[c * n3 + node];
+    for (int a = 0; a < n; ++a) acc += Ds[a * n + i] * px[a + n * j + nn * k];
+    for (int b = 0; b < n; ++b) acc += Ds[b * n + j] * py[i + n * b + nn * k];
+    for (int cc = 0; cc < n; ++cc) acc += Ds[cc * n + k] * pz[i + n * j + nn * cc];
+    const int qx = j + n * k, qy = i + n * k, qz = i + n * j;
+    acc += wl[n + i] * fc[0 * nn + qx] + wl[2 * n + i] * fc[1 * nn + qx];
+    acc += wl[n + j] * fc[2 * nn + qy] + wl[2 * n + j] * fc[3 * nn + qy];
+    acc += wl[n + k] * fc[4 * nn + qz] + wl[2 * n + k] * fc[5 * nn + qz];
+    y[(e * kNc + c) * n3 + q % n3] = acc;
+  }
+}
+
 struct SysLayout {
   size_t cx, cy, cz, fo, fn, nbr, total;
 };
@@ -362,6 +436,17 @@ cudaError_t launch_sys_apply(const tpp_ctx* c, const double* x, const double* tr
         c->p<Tables>(c->L.tables), n, mass * c->prob.h * c->prob.h, c->p<double>(c->sys_cx),
         c->p<double>(c->sys_cy), c->p<double>(c->sys_fo), c->p<double>(c->sys_fn),
         c->p<int32_t>(c->sys_nbr), x, tr, y, skip);
+  } else if (n <= 8) {
+    const int n3 = nn * n;
+    const size_t smem = (size_t)(nn + 3 * n + 5 * n3 + 15 * n3 + 30 * nn) * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sys_apply_3d_all,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sys_apply_3d_all<<<(unsigned)c->sys_E, 256, smem, s>>>(
+        c->p<Tables>(c->L.tables), n, mass * c->prob.h * c->prob.h * c->prob.h,
+        c->p<double>(c->sys_cx), c->p<double>(c->sys_cy), c->p<double>(c->sys_cz),
+        c->p<double>(c->sys_fo), c->p<double>(c->sys_fn), c->p<int32_t>(c->sys_nbr), x, tr, y,
+        skip);
   } else {
     const int n3 = nn * n;
     const size_t smem = (size_t)(nn + 3 * n + 5 * n3 + 3 * n3 + 6 * nn) * 8;
