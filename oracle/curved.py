@@ -19,7 +19,10 @@ a face point is computed from the element that owns the face as its lower face, 
 the two sides of a face see s and -s exactly.  The velocity is a(x / L) with the
 field of oracle/dg.py (periodic on the square).
 
-Pinned in tests/test_oracle_curved.py: the identity map reproduces oracle/dg.py
+CurvedAdvectionDG3D is the same construction on hexahedra (synthetic.periodic_warp3), for
+which the CUDA path is not built yet.
+
+Pinned in tests/test_oracle_curved.py (both classes): the identity map reproduces oracle/dg.py
 (collocated and over-integrated), the warp's gradient against finite differences,
 discrete conservation 1^T (S - M) = 0 for the warped map, opposite scaled normal
 velocities on the two sides of every face, the mass of the whole domain equal to the
@@ -146,3 +149,122 @@ class CurvedAdvectionDG:
 
     def mass_matrix(self) -> sp.csr_matrix:
         return sp.block_diag([self.mass_block(e) for e in range(self.mesh.num_elem)]).tocsr()
+
+
+class CurvedAdvectionDG3D:
+    """The same mapped-element discretisation on hexahedra (3D): element e is the image of
+    the Cartesian cell c under the warp Phi of the periodic cube (synthetic.periodic_warp3),
+    J = h grad Phi at the mu^3 quadrature points (x fastest), the contravariant velocity
+    |J| J^-1 a, faces with the scaled normal |J| J^-T N^ computed from the element that owns
+    the face as its lower face.  mass G^T diag(w |J|) G, volume sum_d D_d^T diag(w F~_d) G,
+    upwind faces, S = M - dt J_v + dt (faces)."""
+
+    def __init__(self, mesh: PeriodicMesh, n: int, dt: float, vel, warp, mu: int | None = None):
+        assert mesh.dim == 3
+        self.mesh, self.n, self.dt, self.vel, self.warp = mesh, n, float(dt), vel, warp
+        self.dim = 3
+        self.basis = Basis1D(n, mu)
+        self.mu = self.basis.mu
+        self.L = np.array([N * mesh.h for N in mesh.nel], dtype=np.float64)
+        self.nloc = n ** 3
+        self.ndof = mesh.num_elem * self.nloc
+
+    def velocity(self, x):
+        return velocity_eval(self.vel, np.asarray(x) / self.L)
+
+    def _grid3(self, c):
+        """Reference points of cell c at the mu^3 quadrature points, x fastest."""
+        xs = self.basis.x
+        Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+        h = self.mesh.h
+        return np.stack([(c[0] + X) * h, (c[1] + Y) * h, (c[2] + Z) * h], -1).reshape(-1, 3)
+
+    def volume_geometry(self, e: int):
+        x, G = self.warp(self._grid3(self.mesh.coords(e)))
+        J = self.mesh.h * G
+        det = np.linalg.det(J)
+        Ft = np.einsum("qij,qj->qi", np.linalg.inv(J), self.velocity(x)) * det[:, None]
+        return det, Ft
+
+    def face_an(self, e: int, face: int) -> np.ndarray:
+        """a . (|J| J^-T N^) at the mu^2 points of `face` (the two tangential directions in
+        increasing order, the lower one fastest), geometry from the face's owner."""
+        d, side = divmod(face, 2)
+        c = list(self.mesh.coords(e))
+        tang = [t for t in range(3) if t != d]
+        xs, h = self.basis.x, self.mesh.h
+        B, A = np.meshgrid(xs, xs, indexing="ij")        # A: fast tangential, B: slow
+        X = np.empty(A.shape + (3,))
+        X[..., d] = (c[d] + side) * h                    # not wrapped: X stays continuous
+        X[..., tang[0]] = (c[tang[0]] + A) * h
+        X[..., tang[1]] = (c[tang[1]] + B) * h
+        x, G = self.warp(X.reshape(-1, 3))
+        J = h * G
+        det = np.linalg.det(J)
+        N = np.zeros(3)
+        N[d] = 1.0 if side == 1 else -1.0
+        s = np.einsum("qji,j->qi", np.linalg.inv(J), N) * det[:, None]
+        return np.einsum("qi,qi->q", self.velocity(x), s)
+
+    def _mats(self):
+        b = self.basis
+        G = np.kron(b.G, np.kron(b.G, b.G))
+        D = [np.kron(b.G, np.kron(b.G, b.D)),              # x derivative (x fastest)
+             np.kron(b.G, np.kron(b.D, b.G)),
+             np.kron(b.D, np.kron(b.G, b.G))]
+        w = np.kron(b.w, np.kron(b.w, b.w))
+        return G, D, w
+
+    def _face_eval(self, face: int, own: bool = True) -> np.ndarray:
+        b = self.basis
+        d, side = divmod(face, 2)
+        if not own:
+            side = 1 - side
+        lvec = (b.l1 if side == 1 else b.l0)[None, :]
+        mats = [lvec if t == d else b.G for t in (2, 1, 0)]   # slowest direction first
+        return np.kron(mats[0], np.kron(mats[1], mats[2]))
+
+    def mass_block(self, e: int) -> np.ndarray:
+        G, _, w = self._mats()
+        det, _ = self.volume_geometry(e)
+        return G.T @ np.diag(w * det) @ G
+
+    def volume_jacobian_block(self, e: int) -> np.ndarray:
+        G, D, w = self._mats()
+        _, Ft = self.volume_geometry(e)
+        return sum(D[k].T @ np.diag(w * Ft[:, k]) @ G for k in range(3))
+
+    def face_blocks(self, e: int):
+        wf = np.kron(self.basis.w, self.basis.w)
+        Fdiag = np.zeros((self.nloc, self.nloc))
+        nbrs = {}
+        for face in range(6):
+            an = self.face_an(e, face)
+            E, En = self._face_eval(face, True), self._face_eval(face, False)
+            Fdiag += E.T @ np.diag(wf * np.maximum(an, 0.0)) @ E
+            nbrs[face] = (self.mesh.neighbor(e, face), E.T @ np.diag(wf * np.minimum(an, 0.0)) @ En)
+        return Fdiag, nbrs
+
+    def element_block(self, e: int) -> np.ndarray:
+        Fdiag, _ = self.face_blocks(e)
+        return self.mass_block(e) - self.dt * self.volume_jacobian_block(e) + self.dt * Fdiag
+
+    def global_matrix(self) -> sp.csr_matrix:
+        nl = self.nloc
+        rows, cols, vals = [], [], []
+        for e in range(self.mesh.num_elem):
+            Fdiag, nbrs = self.face_blocks(e)
+            blocks = [(e, self.mass_block(e) - self.dt * self.volume_jacobian_block(e)
+                       + self.dt * Fdiag)]
+            blocks += [(nb, self.dt * B) for nb, B in nbrs.values()]
+            for col, B in blocks:
+                r, c = np.nonzero(B)
+                rows.append(e * nl + r)
+                cols.append(col * nl + c)
+                vals.append(B[r, c])
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.ndof, self.ndof))
+
+    def mass_matrix(self) -> sp.csr_matrix:
+        return sp.block_diag([self.mass_block(e) for e in range(self.mesh.num_elem)]).tocsr()
+

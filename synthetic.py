@@ -284,6 +284,24 @@ def periodic_warp(X: np.ndarray, L: float, alpha: float = 0.05):
     return x, G
 
 
+def periodic_warp3(X: np.ndarray, L: float, alpha: float = 0.03):
+    """3D counterpart of periodic_warp: x = X + alpha L sin(kX) sin(kY) sin(kZ) (1, 1, 1),
+    k = 2 pi / L, a smooth map of the periodic cube onto itself.  Returns (x [..., 3],
+    grad Phi [..., 3, 3] with [..., i, j] = d x_i / d X_j)."""
+    X = np.asarray(X, dtype=np.float64)
+    k = 2.0 * np.pi / L
+    s = np.sin(k * X)
+    c = np.cos(k * X)
+    p = alpha * L * s[..., 0] * s[..., 1] * s[..., 2]
+    x = X + p[..., None]
+    dp = alpha * L * k * np.stack([c[..., 0] * s[..., 1] * s[..., 2],
+                                   s[..., 0] * c[..., 1] * s[..., 2],
+                                   s[..., 0] * s[..., 1] * c[..., 2]], axis=-1)
+    G = np.broadcast_to(np.eye(3), X.shape[:-1] + (3, 3)).copy()
+    G += dp[..., None, :]
+    return x, G
+
+
 # Linearisation state of the 3D Euler workload: the initial condition of the periodic
 # case of Sec. 5.6 (its exact solution is a travelling wave), density
 # rho = 1 + 0.2 sin(2 pi (x + y + z) / L) (L = 2: sin(pi (x + y + z))) advected by the
