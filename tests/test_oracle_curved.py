@@ -154,3 +154,19 @@ def test_3d_free_stream_with_refined_quadrature():
         res.append(np.linalg.norm(D @ np.ones(dg.ndof)) / abs(D).max())
     # measured 3.8e-3, 1.6e-7, 1.2e-14
     assert res[0] > 1e-4 and res[1] < 1e-3 * res[0] and res[2] <= 1e-12, res
+
+
+def test_3d_warp_is_periodic_and_orientation_preserving():
+    """Phi(X + L e_d) = Phi(X) + L e_d with the same gradient (the warped elements conform
+    across the periodic boundary), and det grad Phi > 0 everywhere."""
+    L = 2.0
+    X = np.random.Generator(np.random.PCG64(9)).uniform(0, L, (50, 3))
+    x0, G0 = synthetic.periodic_warp3(X, L, 0.03)
+    for d in range(3):
+        sh = np.zeros(3)
+        sh[d] = L
+        x1, G1 = synthetic.periodic_warp3(X + sh, L, 0.03)
+        assert np.abs(x1 - x0 - sh).max() <= 1e-13 and np.abs(G1 - G0).max() <= 1e-12
+    g = np.linspace(0, L, 17)
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    assert np.linalg.det(synthetic.periodic_warp3(P, L, 0.03)[1]).min() > 0.3
