@@ -1,8 +1,9 @@
-// Full multi-component blocks of the 2D Euler systems (Sec. 5.3, Sec. 5.6): the
+// Full multi-component blocks of the Euler systems (Sec. 5.3, Sec. 5.6).  In 2D: the
 // Kronecker approximation A_1 (x) B_1 + A_2 (x) B_2 of each element's whole
 // n_c n^2 x n_c n^2 Jacobian block, A_k of size n_c n x n_c n acting on the
-// (component, y) index a = c n + j, B_k of size n x n acting on x; and the exact
-// full-block Jacobi comparator (J_full).
+// (component, y) index a = c n + j, B_k of size n x n acting on x.  In 3D: the nested
+// form of Sec. 4.3 with the component on the z factor (second part of this file).  In
+// both: the exact full-block Jacobi comparator (J_full).
 //
 // Rearranged block.  With the collocated coefficients of the coupled operator
 // (k_system.cu) the block is a sum of 2n + 2 Kronecker terms alpha_t (x) beta_t:
